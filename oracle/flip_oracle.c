@@ -1,0 +1,463 @@
+/*
+ * flip_oracle.c — plain FP64 CPU oracle of one FLIP time step.
+ *
+ * TEST INFRASTRUCTURE ONLY: called by the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg, never by the library.  Every function follows
+ * one passage of Centeno & Pereira, "Fluid Implicit Particle Simulation for CPU
+ * and GPU" (arXiv 2404.01931), cited beside it, in the paper's order and with
+ * no blocking, fusion or reordering beyond what the passage states.  OpenMP
+ * only splits independent loops (and sums dot products per thread).
+ *
+ * Parity status: every function here is pinned by the tests in
+ * tests/test_oracle_pins.py (closed forms, invariants, a brute-force gather and
+ * dense solves); see the header of that file for which pin covers which part.
+ */
+#include "flip_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+int oracle_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+int64_t oracle_n_cells(const oracle_params* P) {
+  return (int64_t)P->n[0] * P->n[1] * P->n[2];
+}
+
+/* Face-array extent of component comp along axis ax: one more node along the
+ * component's own axis (MAC grid, Section 3.1.1). */
+static int64_t face_dim(const oracle_params* P, int comp, int ax) {
+  return (int64_t)P->n[ax] + (ax == comp ? 1 : 0);
+}
+
+int64_t oracle_n_faces(const oracle_params* P, int comp) {
+  return face_dim(P, comp, 0) * face_dim(P, comp, 1) * face_dim(P, comp, 2);
+}
+
+static int64_t face_index(const oracle_params* P, int comp, int64_t a, int64_t b, int64_t c) {
+  return a + face_dim(P, comp, 0) * (b + face_dim(P, comp, 1) * c);
+}
+
+static int64_t cell_index(const oracle_params* P, int64_t i, int64_t j, int64_t k) {
+  return i + (int64_t)P->n[0] * (j + (int64_t)P->n[1] * k);
+}
+
+static int64_t clampi(int64_t v, int64_t lo, int64_t hi) {
+  return v < lo ? lo : (v > hi ? hi : v);
+}
+
+static double clampd(double v, double lo, double hi) {
+  return v < lo ? lo : (v > hi ? hi : v);
+}
+
+/* Eq. 4b: h(r) = 1 - |r| on [-1, 1], 0 outside. */
+double oracle_hat(double r) {
+  if (r >= 0.0 && r <= 1.0) return 1.0 - r;
+  if (r >= -1.0 && r < 0.0) return 1.0 + r;
+  return 0.0;
+}
+
+/* Cell index of a point (Section 3.1.5 "raw index"; the paper's 16-bit hash
+ * formula in Section 3.2.2 is garbled, the reading is floor(x/dx) per axis,
+ * taken here as floor(x * (1/dx)) in FP64 and clamped to the grid). */
+void oracle_cell_of(const oracle_params* P, double x, double y, double z, int64_t cell[3]) {
+  const double inv = 1.0 / P->dx;
+  const double pos[3] = {x, y, z};
+  for (int ax = 0; ax < 3; ++ax)
+    cell[ax] = clampi((int64_t)floor(pos[ax] * inv), 0, P->n[ax] - 1);
+}
+
+/* Grid coordinate of a point relative to the face nodes of component comp:
+ * the node of index a sits at (a + off)*dx with off = 0 along the component's
+ * own axis and 1/2 along the other two (MAC layout).  The coordinate is clamped
+ * to the node range, so a point between a wall and the first node samples the
+ * first node only (the paper does not say how transfers treat the half cell
+ * next to a wall; this keeps all eight nodes inside the grid and the weights a
+ * partition of unity). */
+static double sample_coord(const oracle_params* P, int comp, int ax, double pos) {
+  const double off = (ax == comp) ? 0.0 : 0.5;
+  return clampd(pos / P->dx - off, 0.0, (double)(face_dim(P, comp, ax) - 1));
+}
+
+/* Eq. 4a: k(x_P - x_node) = h(.)h(.)h(.) in units of dx. */
+double oracle_weight(const oracle_params* P, int comp, int64_t a, int64_t b, int64_t c,
+                     double x, double y, double z) {
+  const double pos[3] = {x, y, z};
+  const int64_t node[3] = {a, b, c};
+  double w = 1.0;
+  for (int ax = 0; ax < 3; ++ax) w *= oracle_hat(sample_coord(P, comp, ax, pos[ax]) - (double)node[ax]);
+  return w;
+}
+
+/* Section 3.1.5, Fig. 4: compute each particle's raw cell index, sort the
+ * particles by it, and record per cell the offset and count of its particles
+ * (the "space hash").  A stable counting sort: particles keep their relative
+ * order inside a cell. */
+void oracle_bin(const oracle_params* P, int64_t np, const double* x, const double* y,
+                const double* z, int64_t* start, int64_t* order) {
+  const int64_t nc = oracle_n_cells(P);
+  int64_t* cellid = (int64_t*)malloc(sizeof(int64_t) * (size_t)(np > 0 ? np : 1));
+  int64_t* cursor = (int64_t*)malloc(sizeof(int64_t) * (size_t)nc);
+  memset(start, 0, sizeof(int64_t) * (size_t)(nc + 1));
+  for (int64_t p = 0; p < np; ++p) {
+    int64_t c3[3];
+    oracle_cell_of(P, x[p], y[p], z[p], c3);
+    cellid[p] = cell_index(P, c3[0], c3[1], c3[2]);
+    start[cellid[p] + 1] += 1;
+  }
+  for (int64_t c = 0; c < nc; ++c) start[c + 1] += start[c];
+  for (int64_t c = 0; c < nc; ++c) cursor[c] = start[c];
+  for (int64_t p = 0; p < np; ++p) order[cursor[cellid[p]]++] = p;
+  free(cellid);
+  free(cursor);
+}
+
+/* Section 3.1.6: gather form of the particle-to-grid transfer.  For every face
+ * node, loop over the particles that can reach it and form
+ *     u_node = sum_P u_P k(x_P - x_node) / sum_P k(x_P - x_node)
+ * (0 where no particle reaches the node).  A particle reaches a node only if
+ * its sample coordinate is within one node spacing on every axis; with the
+ * half-cell staggering that confines it to cells node-1..node along the
+ * component's own axis and node-1..node+1 along the other two. */
+void oracle_p2g(const oracle_params* P, int comp, const double* x, const double* y,
+                const double* z, const double* vel, const int64_t* start,
+                const int64_t* order, double* grid, double* wsum) {
+  const int64_t fx = face_dim(P, comp, 0), fy = face_dim(P, comp, 1), fz = face_dim(P, comp, 2);
+  const int64_t nf = fx * fy * fz;
+#pragma omp parallel for schedule(dynamic, 1024)
+  for (int64_t f = 0; f < nf; ++f) {
+    const int64_t node[3] = {f % fx, (f / fx) % fy, f / (fx * fy)};
+    int64_t lo[3], hi[3];
+    for (int ax = 0; ax < 3; ++ax) {
+      lo[ax] = clampi(node[ax] - 1, 0, P->n[ax] - 1);
+      hi[ax] = clampi(ax == comp ? node[ax] : node[ax] + 1, 0, P->n[ax] - 1);
+    }
+    double swu = 0.0, sw = 0.0;
+    for (int64_t k = lo[2]; k <= hi[2]; ++k)
+      for (int64_t j = lo[1]; j <= hi[1]; ++j)
+        for (int64_t i = lo[0]; i <= hi[0]; ++i) {
+          const int64_t c = cell_index(P, i, j, k);
+          for (int64_t q = start[c]; q < start[c + 1]; ++q) {
+            const int64_t p = order[q];
+            const double wt = oracle_weight(P, comp, node[0], node[1], node[2], x[p], y[p], z[p]);
+            swu += wt * vel[p];
+            sw += wt;
+          }
+        }
+    grid[f] = sw > 0.0 ? swu / sw : 0.0;
+    if (wsum) wsum[f] = sw;
+  }
+}
+
+/* Section 3.1.5: a cell holds fluid when its particle count is above zero. */
+void oracle_cell_types(const oracle_params* P, const int64_t* start, uint8_t* type) {
+  const int64_t nc = oracle_n_cells(P);
+  for (int64_t c = 0; c < nc; ++c) type[c] = (start[c + 1] > start[c]) ? 1 : 0;
+}
+
+/* Eq. 1 / Section 2.1.3 splitting: the force step adds g*dt to the grid
+ * velocity; then the solid-wall condition (Section 3.1.7) sets the normal
+ * velocity on the six domain planes to zero. */
+void oracle_forces_walls(const oracle_params* P, int comp, const double* u_old, double* u_star) {
+  const int64_t fx = face_dim(P, comp, 0), fy = face_dim(P, comp, 1), fz = face_dim(P, comp, 2);
+  const int64_t nf = fx * fy * fz;
+  const double dv = P->gravity[comp] * P->dt;
+#pragma omp parallel for schedule(static)
+  for (int64_t f = 0; f < nf; ++f) {
+    const int64_t node[3] = {f % fx, (f / fx) % fy, f / (fx * fy)};
+    const int wall = (node[comp] == 0) || (node[comp] == P->n[comp]);
+    u_star[f] = wall ? 0.0 : u_old[f] + dv;
+  }
+}
+
+/* Eq. 6 with central differences on the MAC grid (Section 3.1.7):
+ * b = -div u* in each fluid cell. */
+void oracle_divergence(const oracle_params* P, const double* const u[3], const uint8_t* type,
+                       double* b) {
+  const int64_t nx = P->n[0], ny = P->n[1], nz = P->n[2];
+  const int64_t nc = nx * ny * nz;
+#pragma omp parallel for schedule(static)
+  for (int64_t c = 0; c < nc; ++c) {
+    if (!type[c]) { b[c] = 0.0; continue; }
+    const int64_t i = c % nx, j = (c / nx) % ny, k = c / (nx * ny);
+    const double du = u[0][face_index(P, 0, i + 1, j, k)] - u[0][face_index(P, 0, i, j, k)];
+    const double dv = u[1][face_index(P, 1, i, j + 1, k)] - u[1][face_index(P, 1, i, j, k)];
+    const double dw = u[2][face_index(P, 2, i, j, k + 1)] - u[2][face_index(P, 2, i, j, k)];
+    b[c] = -(du + dv + dw) / P->dx;
+  }
+}
+
+/* Number of a cell's six neighbours that are not solid walls (the domain
+ * planes are the only solids). */
+static int nonsolid_neighbours(const oracle_params* P, int64_t i, int64_t j, int64_t k) {
+  const int64_t idx[3] = {i, j, k};
+  int cnt = 0;
+  for (int ax = 0; ax < 3; ++ax) {
+    if (idx[ax] > 0) ++cnt;
+    if (idx[ax] < P->n[ax] - 1) ++cnt;
+  }
+  return cnt;
+}
+
+/* Section 3.1.7: row of the seven-point Laplacian for fluid cell c,
+ *   (A p)_c = dt/(rho dx^2) * ( n_c p_c - sum_{fluid neighbours m} p_m ),
+ * n_c = number of non-solid neighbours (air neighbours carry p = 0, the free
+ * surface condition; solid neighbours drop out, the wall condition). */
+void oracle_apply_A(const oracle_params* P, const uint8_t* type, const double* p, double* Ap) {
+  const int64_t nx = P->n[0], ny = P->n[1], nz = P->n[2];
+  const int64_t nc = nx * ny * nz;
+  const double s = P->dt / (P->rho * P->dx * P->dx);
+#pragma omp parallel for schedule(static)
+  for (int64_t c = 0; c < nc; ++c) {
+    if (!type[c]) { Ap[c] = 0.0; continue; }
+    const int64_t i = c % nx, j = (c / nx) % ny, k = c / (nx * ny);
+    double off = 0.0;
+    if (i > 0 && type[c - 1]) off += p[c - 1];
+    if (i < nx - 1 && type[c + 1]) off += p[c + 1];
+    if (j > 0 && type[c - nx]) off += p[c - nx];
+    if (j < ny - 1 && type[c + nx]) off += p[c + nx];
+    if (k > 0 && type[c - nx * ny]) off += p[c - nx * ny];
+    if (k < nz - 1 && type[c + nx * ny]) off += p[c + nx * ny];
+    Ap[c] = s * ((double)nonsolid_neighbours(P, i, j, k) * p[c] - off);
+  }
+}
+
+static double dot_fluid(int64_t nc, const uint8_t* type, const double* a, const double* b) {
+  double s = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : s)
+  for (int64_t c = 0; c < nc; ++c)
+    if (type[c]) s += a[c] * b[c];
+  return s;
+}
+
+/* Section 3.1.7: preconditioned conjugate gradient on A p = b (the paper's
+ * CPU solver; it defers the preconditioner to Bridson, read here as the
+ * diagonal (Jacobi) one).  Start p = 0; stop when the recursive residual
+ * satisfies ||r||_2 <= tol * ||b||_2.  Returns the number of A-applications,
+ * or -1 when max_iter is reached first. */
+int oracle_pcg(const oracle_params* P, const uint8_t* type, const double* b, double tol,
+               int max_iter, double* x, double* rel_res) {
+  const int64_t nx = P->n[0], ny = P->n[1];
+  const int64_t nc = oracle_n_cells(P);
+  const double s = P->dt / (P->rho * P->dx * P->dx);
+  double* r = (double*)malloc(sizeof(double) * (size_t)nc);
+  double* zz = (double*)malloc(sizeof(double) * (size_t)nc);
+  double* d = (double*)malloc(sizeof(double) * (size_t)nc);
+  double* q = (double*)malloc(sizeof(double) * (size_t)nc);
+  double* minv = (double*)malloc(sizeof(double) * (size_t)nc);
+  int result = -1;
+#pragma omp parallel for schedule(static)
+  for (int64_t c = 0; c < nc; ++c) {
+    const int64_t i = c % nx, j = (c / nx) % ny, k = c / (nx * ny);
+    x[c] = 0.0;
+    r[c] = type[c] ? b[c] : 0.0;
+    minv[c] = type[c] ? 1.0 / (s * (double)nonsolid_neighbours(P, i, j, k)) : 0.0;
+    zz[c] = minv[c] * r[c];
+    d[c] = zz[c];
+  }
+  const double bnorm = sqrt(dot_fluid(nc, type, r, r));
+  double rz = dot_fluid(nc, type, r, zz);
+  double rnorm = bnorm;
+  if (bnorm == 0.0 || rnorm <= tol * bnorm) {
+    result = 0;
+  } else {
+    for (int it = 1; it <= max_iter; ++it) {
+      oracle_apply_A(P, type, d, q);
+      const double alpha = rz / dot_fluid(nc, type, d, q);
+#pragma omp parallel for schedule(static)
+      for (int64_t c = 0; c < nc; ++c)
+        if (type[c]) {
+          x[c] += alpha * d[c];
+          r[c] -= alpha * q[c];
+        }
+      rnorm = sqrt(dot_fluid(nc, type, r, r));
+      if (rnorm <= tol * bnorm) { result = it; break; }
+#pragma omp parallel for schedule(static)
+      for (int64_t c = 0; c < nc; ++c) zz[c] = minv[c] * r[c];
+      const double rz_new = dot_fluid(nc, type, r, zz);
+      const double beta = rz_new / rz;
+      rz = rz_new;
+#pragma omp parallel for schedule(static)
+      for (int64_t c = 0; c < nc; ++c)
+        if (type[c]) d[c] = zz[c] + beta * d[c];
+    }
+  }
+  if (rel_res) *rel_res = bnorm > 0.0 ? rnorm / bnorm : 0.0;
+  free(r); free(zz); free(d); free(q); free(minv);
+  return result;
+}
+
+/* Eq. 5: u_new = u* - dt/rho * (p_{+} - p_{-})/dx on faces with a fluid cell on
+ * at least one side (air cells carry p = 0); wall faces stay 0; faces between
+ * two air cells keep u*. */
+void oracle_project(const oracle_params* P, int comp, const double* u_star, const double* p,
+                    const uint8_t* type, double* u_new) {
+  const int64_t fx = face_dim(P, comp, 0), fy = face_dim(P, comp, 1), fz = face_dim(P, comp, 2);
+  const int64_t nf = fx * fy * fz;
+  const double scale = P->dt / (P->rho * P->dx);
+#pragma omp parallel for schedule(static)
+  for (int64_t f = 0; f < nf; ++f) {
+    int64_t node[3] = {f % fx, (f / fx) % fy, f / (fx * fy)};
+    if (node[comp] == 0 || node[comp] == P->n[comp]) { u_new[f] = 0.0; continue; }
+    const int64_t cp = cell_index(P, node[0], node[1], node[2]);
+    node[comp] -= 1;
+    const int64_t cm = cell_index(P, node[0], node[1], node[2]);
+    if (type[cp] || type[cm])
+      u_new[f] = u_star[f] - scale * ((type[cp] ? p[cp] : 0.0) - (type[cm] ? p[cm] : 0.0));
+    else
+      u_new[f] = u_star[f];
+  }
+}
+
+/* Section 3.1.8: trilinear interpolation from the eight face nodes around the
+ * point, with the Eq. 4 weights (the same weights the transfer to the grid
+ * uses). */
+double oracle_interp(const oracle_params* P, int comp, const double* field, double x, double y,
+                     double z) {
+  const double pos[3] = {x, y, z};
+  int64_t base[3], dim[3];
+  for (int ax = 0; ax < 3; ++ax) {
+    dim[ax] = face_dim(P, comp, ax);
+    base[ax] = clampi((int64_t)floor(sample_coord(P, comp, ax, pos[ax])), 0,
+                      dim[ax] >= 2 ? dim[ax] - 2 : 0);
+  }
+  double acc = 0.0;
+  for (int dc = 0; dc < 2; ++dc)
+    for (int db = 0; db < 2; ++db)
+      for (int da = 0; da < 2; ++da) {
+        const int64_t a = base[0] + da, b = base[1] + db, c = base[2] + dc;
+        if (a >= dim[0] || b >= dim[1] || c >= dim[2]) continue;
+        acc += oracle_weight(P, comp, a, b, c, x, y, z) * field[face_index(P, comp, a, b, c)];
+      }
+  return acc;
+}
+
+/* Section 3.1.8 then Section 3.1.3.  First the change of the grid velocity,
+ * du = u_new - u_old, is formed and stored; then for each particle the new grid
+ * velocity U and the change dU are interpolated and blended:
+ *     v_P <- r (v_P + dU) + (1 - r) U          (FLIP share r, Section 2.1.4)
+ * Then forward Euler x_P <- x_P + v dt (v = the blended particle velocity, or U
+ * when advect_source = 1) and the clamp back into the domain by the skin width
+ * along each axis. */
+void oracle_g2p(const oracle_params* P, int64_t np, double* x, double* y, double* z, double* u,
+                double* v, double* w, const double* const u_old[3],
+                const double* const u_new[3]) {
+  double* du[3];
+  for (int comp = 0; comp < 3; ++comp) {
+    const int64_t nf = oracle_n_faces(P, comp);
+    du[comp] = (double*)malloc(sizeof(double) * (size_t)nf);
+#pragma omp parallel for schedule(static)
+    for (int64_t f = 0; f < nf; ++f) du[comp][f] = u_new[comp][f] - u_old[comp][f];
+  }
+  const double r = P->flip_ratio;
+  double* vel[3] = {u, v, w};
+  double* pos[3] = {x, y, z};
+#pragma omp parallel for schedule(static)
+  for (int64_t p = 0; p < np; ++p) {
+    double U[3], Vb[3];
+    for (int comp = 0; comp < 3; ++comp) {
+      U[comp] = oracle_interp(P, comp, u_new[comp], x[p], y[p], z[p]);
+      const double dU = oracle_interp(P, comp, du[comp], x[p], y[p], z[p]);
+      Vb[comp] = r * (vel[comp][p] + dU) + (1.0 - r) * U[comp];
+    }
+    for (int ax = 0; ax < 3; ++ax) {
+      vel[ax][p] = Vb[ax];
+      const double adv = (P->advect_source == 1) ? U[ax] : Vb[ax];
+      const double hi = (double)P->n[ax] * P->dx - P->skin;
+      pos[ax][p] = clampd(pos[ax][p] + adv * P->dt, P->skin, hi);
+    }
+  }
+  for (int comp = 0; comp < 3; ++comp) free(du[comp]);
+}
+
+double oracle_div_norm(const oracle_params* P, const double* const u[3], const uint8_t* type) {
+  const int64_t nc = oracle_n_cells(P);
+  double* d = (double*)malloc(sizeof(double) * (size_t)nc);
+  oracle_divergence(P, u, type, d);
+  const double s = sqrt(dot_fluid(nc, type, d, d));
+  free(d);
+  return s;
+}
+
+/* One FLIP step (Section 3 order; gravity enters after the transfer to the
+ * grid, per the force-advect-project splitting of Section 2.1.3):
+ *   bin -> P2G -> cell types -> gravity + walls -> b = -div u* -> PCG ->
+ *   Eq. 5 projection -> G2P blend -> forward Euler + clamp. */
+int oracle_step(const oracle_params* P, int64_t np, double* x, double* y, double* z, double* u,
+                double* v, double* w, oracle_fields* out, oracle_stats* stats) {
+  const int64_t nc = oracle_n_cells(P);
+  int64_t* start = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nc + 1));
+  int64_t* order = (int64_t*)malloc(sizeof(int64_t) * (size_t)(np > 0 ? np : 1));
+  double* uo[3];
+  double* us[3];
+  double* un[3];
+  for (int d = 0; d < 3; ++d) {
+    const size_t nf = (size_t)oracle_n_faces(P, d);
+    uo[d] = (double*)malloc(sizeof(double) * nf);
+    us[d] = (double*)malloc(sizeof(double) * nf);
+    un[d] = (double*)malloc(sizeof(double) * nf);
+  }
+  double* p = (double*)malloc(sizeof(double) * (size_t)nc);
+  double* b = (double*)malloc(sizeof(double) * (size_t)nc);
+  uint8_t* type = (uint8_t*)malloc((size_t)nc);
+  int status = 0;
+  if (!start || !order || !p || !b || !type) status = 3;
+  for (int d = 0; d < 3; ++d)
+    if (!uo[d] || !us[d] || !un[d]) status = 3;
+  if (status == 0) {
+    oracle_bin(P, np, x, y, z, start, order);
+    const double* pv[3] = {u, v, w};
+    for (int d = 0; d < 3; ++d) oracle_p2g(P, d, x, y, z, pv[d], start, order, uo[d], NULL);
+    oracle_cell_types(P, start, type);
+    for (int d = 0; d < 3; ++d) oracle_forces_walls(P, d, uo[d], us[d]);
+    const double* usc[3] = {us[0], us[1], us[2]};
+    oracle_divergence(P, usc, type, b);
+    int64_t nfluid = 0;
+    for (int64_t c = 0; c < nc; ++c) nfluid += type[c];
+    /* A is singular exactly when a connected fluid region has no air
+     * neighbour; with the domain planes as the only solids such a region is
+     * closed under adjacency, i.e. it is the whole grid. */
+    if (nfluid == nc && nc > 0) status = 2;
+    double rel = 0.0;
+    int iters = 0;
+    if (status == 0) {
+      iters = oracle_pcg(P, type, b, P->cg_tol, P->cg_max_iter, p, &rel);
+      if (iters < 0) status = 1;
+      for (int d = 0; d < 3; ++d) oracle_project(P, d, us[d], p, type, un[d]);
+      const double* unc[3] = {un[0], un[1], un[2]};
+      const double* uoc[3] = {uo[0], uo[1], uo[2]};
+      const double d0 = oracle_div_norm(P, usc, type);
+      const double d1 = oracle_div_norm(P, unc, type);
+      if (stats) {
+        stats->cg_iterations = iters;
+        stats->cg_rel_residual = rel;
+        stats->rel_divergence = d0 > 0.0 ? d1 / d0 : 0.0;
+        stats->n_fluid = nfluid;
+      }
+      oracle_g2p(P, np, x, y, z, u, v, w, uoc, unc);
+      if (out) {
+        for (int d = 0; d < 3; ++d) {
+          const size_t nb = sizeof(double) * (size_t)oracle_n_faces(P, d);
+          if (out->u_old[d]) memcpy(out->u_old[d], uo[d], nb);
+          if (out->u_star[d]) memcpy(out->u_star[d], us[d], nb);
+          if (out->u_new[d]) memcpy(out->u_new[d], un[d], nb);
+        }
+        if (out->pressure) memcpy(out->pressure, p, sizeof(double) * (size_t)nc);
+        if (out->rhs) memcpy(out->rhs, b, sizeof(double) * (size_t)nc);
+        if (out->type) memcpy(out->type, type, (size_t)nc);
+      }
+    }
+  }
+  free(start); free(order); free(p); free(b); free(type);
+  for (int d = 0; d < 3; ++d) { free(uo[d]); free(us[d]); free(un[d]); }
+  return status;
+}
