@@ -1,0 +1,335 @@
+"""FLIP step benchmark: particle-steps/s on one GB300 (or N replicas), one JSON line.
+
+Default workload: the drop-into-pool scene on a 256^3 MAC grid (pool depth 0.3 plus a
+sphere of radius 0.15 at (0.5, 0.7, 0.5), 8 particles per fluid cell, 42,266,944
+particles), mixed precision (FP32 PCG inside FP64 iterative refinement to a relative
+residual of 1e-8), dt = 1/240, FLIP ratio 0.95, seed 0.  Inputs are synthetic
+(seeded jittered seeding), generated on the host.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload pool256|dam128|dam32]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+
+A "step" is one full FLIP step (bin, P2G, divergence, PCG, G2P).  Timing: W untimed
+steps, then K steps between CUDA events on the simulation's stream, bracketed by a
+barrier and a synchronize; the max over ranks is reported.  The particle and grid
+arrays (> 1 GB) are larger than the 129 MB L2, so no flush is needed between steps.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "pool256": dict(desc="drop into pool, 256^3, depth 0.3 + sphere r=0.15 at (0.5,0.7,0.5)",
+                    n=256, scene="pool", precision="mixed", cg_tol=1e-4, ir_tol=1e-8),
+    "dam128": dict(desc="dam break, 128^3, block x<0.25 y<0.5", n=128, scene="dam",
+                   precision="fp32", cg_tol=1e-6, ir_tol=1e-8),
+    "dam32": dict(desc="dam break, 32^3, block x<0.25 y<0.5", n=32, scene="dam",
+                  precision="fp32", cg_tol=1e-6, ir_tol=1e-8),
+}
+
+# Algorithmic bytes of the PCG kernel per fluid cell (FP32 vectors, each value read
+# or written once per phase; stencil neighbours come from cache):
+#   phase A: read r, p_old (4+4), type (1); write p_new, q (4+4)      = 17 B
+#   phase B: read x, p_new, r, q (16); write x, r (8)                 = 24 B
+#   mixed-mode refinement, per outer step: phase R read x64, b64 (16), type (1),
+#   write r, d, p_old (12) = 29 B; phase U read x64, d (12), write x64 (8) = 20 B;
+#   once per solve: ||b|| read b64 (8), final float-pair write (read x64 8, write 8).
+PCG_BYTES_PER_ITER = 41
+IR_BYTES_PER_OUTER = 49
+IR_BYTES_PER_SOLVE = 29 + 8 + 16
+
+
+def make_scene(w):
+    from paper_2404_01931_gb300 import scenes as S
+    if w["scene"] == "pool":
+        return S.pool_drop(w["n"])
+    return S.dam_break(w["n"])
+
+
+def make_params(w):
+    from paper_2404_01931_gb300 import flip as F
+    p = F.default_params(w["n"])
+    p.cg_tol = w["cg_tol"]
+    p.ir_tol = w["ir_tol"]
+    if w["precision"] == "mixed":
+        p.precision = F.FLIP_PREC_MIXED_IR
+    return p
+
+
+def read_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "200"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self._t:
+            self._t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(w, budget_s=25.0):
+    """The FP64 oracle timed on this host's cores on a bounded sample of the workload."""
+    import oracle as O
+    from paper_2404_01931_gb300 import scenes as S
+    n = w["n"]
+    # Sample: the same scene shape at the largest grid edge whose oracle step fits the
+    # budget (the full 256^3 step takes longer than the budget on typical hosts).
+    for ns in ([n, n // 2, n // 4, 32] if n > 32 else [n]):
+        sc = S.pool_drop(ns) if w["scene"] == "pool" else S.dam_break(ns)
+        op = O.Params(n=(ns, ns, ns), dx=1.0 / ns, cg_tol=w["ir_tol"] if w["precision"] == "mixed"
+                      else w["cg_tol"])
+        t0 = time.perf_counter()
+        r = O.step(op, *sc.arrays(), fields=False)
+        dt = time.perf_counter() - t0
+        if dt <= budget_s or ns == 32:
+            steps = 1
+            st = [r.x, r.y, r.z, r.u, r.v, r.w]
+            while (time.perf_counter() - t0) + dt <= budget_s and steps < 10:
+                r = O.step(op, *st, fields=False)
+                st = [r.x, r.y, r.z, r.u, r.v, r.w]
+                steps += 1
+            el = time.perf_counter() - t0
+            return {"value": sc.n_particles * steps / el, "unit": "particle-steps/s",
+                    "cores": O.num_threads(), "kind": "oracle",
+                    "sample": f"{steps} oracle step(s) of the same scene at {ns}^3 "
+                              f"({sc.n_particles} particles), FP64, {el:.1f} s"}
+    return None
+
+
+def run_reference(args, w):
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2404_01931_gb300 import scenes as S
+    n = w["n"]
+    # each step: one oracle step of the workload's scene at a bounded grid edge
+    ns = min(n, 64)
+    sc = S.pool_drop(ns) if w["scene"] == "pool" else S.dam_break(ns)
+    op = O.Params(n=(ns, ns, ns), dx=1.0 / ns,
+                  cg_tol=w["ir_tol"] if w["precision"] == "mixed" else w["cg_tol"])
+    st = [a.astype(np.float64) for a in sc.arrays()]
+    for _ in range(args.warmup):
+        r = O.step(op, *st, fields=False)
+        st = [r.x, r.y, r.z, r.u, r.v, r.w]
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r = O.step(op, *st, fields=False)
+        st = [r.x, r.y, r.z, r.u, r.v, r.w]
+    el = time.perf_counter() - t0
+    val = sc.n_particles * args.steps / el
+    sample = f"oracle step of the same scene at {ns}^3 ({sc.n_particles} particles), FP64"
+    out = {"metric": "FLIP particle-steps/s", "value": val, "unit": "particle-steps/s",
+           "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": w["desc"], "grid": [n, n, n], "reference_sample_grid": ns},
+           "cpu_baseline": {"value": val, "unit": "particle-steps/s", "cores": O.num_threads(),
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": val, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="pool256", choices=sorted(WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w)
+    ws, rank, local = dist_setup()
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    if rank == 0 or not os.path.exists(os.path.join(ROOT, "paper_2404_01931_gb300", "_lib",
+                                                    "libflip_gb300.so")):
+        __graft_entry__.build()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist.barrier()
+        __graft_entry__.build()
+    from paper_2404_01931_gb300 import flip as F
+
+    sc = make_scene(w)
+    prm = make_params(w)
+    sim = F.Simulation(prm, *sc.arrays())
+    stream = torch.cuda.ExternalStream(sim.stream)
+    np_ = sc.n_particles
+    if args.warmup > 0:
+        sim.step(args.warmup)
+    sim.sync()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rc, st = sim.step(args.steps, stats=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * np_ * args.steps / (ms / 1e3)
+
+    # end to end: host (pinned) buffers in, one step, host buffers out, every step
+    e2e = None
+    if args.e2e_steps > 0:
+        host = [torch.empty(np_, dtype=torch.float32, pin_memory=True) for _ in range(6)]
+        F.flip_read_particles(sim.h, *host)
+        sim.sync()
+        if ws > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            F.flip_write_particles(sim.h, *host)
+            sim.step(1)
+            F.flip_read_particles(sim.h, *host)
+        el = time.perf_counter() - t0
+        if ws > 1:
+            t = torch.tensor([el], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": ws * np_ * args.e2e_steps / el, "unit": "particle-steps/s",
+               "h2d_bytes_per_step": 24 * np_, "d2h_bytes_per_step": 24 * np_,
+               "steps": args.e2e_steps}
+
+    if rank == 0:
+        peak, peak_kind = read_peaks()
+        nfl = st.n_fluid_cells
+        mixed = w["precision"] == "mixed"
+        pcg_bytes = nfl * (PCG_BYTES_PER_ITER * st.cg_iterations
+                           + (IR_BYTES_PER_OUTER * st.ir_iterations
+                              + IR_BYTES_PER_SOLVE * args.steps if mixed else 0))
+        stage_ms = {"bin": st.ms_bin, "p2g": st.ms_p2g, "divergence": st.ms_divergence,
+                    "pcg": st.ms_pcg, "g2p": st.ms_g2p}
+        achieved = pcg_bytes / (st.ms_pcg / 1e3) / 1e9 if st.ms_pcg > 0 else None
+        out = {
+            "metric": "FLIP particle-steps/s", "value": value, "unit": "particle-steps/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64" if mixed else "f32", "data": "synthetic",
+            "config": {"workload": w["desc"], "grid": [w["n"]] * 3, "particles": np_,
+                       "precision": "mixed IR (FP32 PCG, FP64 outer residual)" if mixed
+                       else "FP32 (FP64-accurate dots)",
+                       "ir_tol": w["ir_tol"], "cg_tol": w["cg_tol"], "dt": 1 / 240,
+                       "flip_ratio": 0.95, "seed": 0,
+                       "parallelism": f"{ws} independent replica(s), one per GPU",
+                       "l2": "inputs larger than L2 (particles + grids > 1 GB); no flush"},
+            "stages_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
+            "cg_iterations_per_step": st.cg_iterations / args.steps,
+            "ir_iterations_per_step": st.ir_iterations / args.steps,
+            "rel_residual": st.cg_rel_residual, "rel_divergence": st.rel_divergence,
+            "n_fluid_cells": nfl, "status": rc,
+            "roofline": {"kernel": "k_pcg (persistent PCG, whole solve per launch)",
+                         "bound": "hbm", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
+                         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                         "algorithmic_bytes_per_launch": pcg_bytes / args.steps,
+                         "traffic": None},
+            "gpu_launches": st.kernel_launches,
+            "clocks": ck,
+            "e2e": e2e,
+        }
+        if not args.no_cpu_baseline and ws == 1:
+            out["cpu_baseline"] = cpu_baseline(w)
+        print(json.dumps(out), flush=True)
+    sim.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

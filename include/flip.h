@@ -1,0 +1,208 @@
+/*
+ * flip.h — C ABI of the GB300 FLIP step library (libflip_gb300.so).
+ *
+ * One simulation step of the FLuid-Implicit-Particle method as described by
+ * Centeno & Pereira, "Fluid Implicit Particle Simulation for CPU and GPU"
+ * (arXiv 2404.01931), Section 3:
+ *
+ *   bin particles by cell (Sec. 3.1.5, 3.2.2)
+ *   -> particle-to-grid transfer onto the MAC grid (Sec. 3.1.6, Eq. 4)
+ *   -> gravity and solid-wall conditions (Eq. 1, Sec. 2.1.3 splitting)
+ *   -> pressure projection: b = -div u* (Eq. 6), A p = b by matrix-free
+ *      preconditioned conjugate gradient (Sec. 3.1.7), u_new = u* - dt/rho grad p (Eq. 5)
+ *   -> grid-to-particle PIC/FLIP blend (Sec. 2.1.4, 3.1.8)
+ *   -> forward-Euler advection and wall clamp (Sec. 3.1.3).
+ *
+ * Everything runs as CUDA kernels for sm_103a on the stream given at creation.
+ * Pointers are plain host or device addresses; sizes are in elements unless a
+ * name says bytes.  No function throws; every function that can fail returns
+ * a status code (FLIP_OK = 0) and flip_last_error() gives a message for the
+ * calling thread's last failure.
+ *
+ * Grid conventions (Sec. 3.1.1, Figs. 1-2): nx*ny*nz cells of edge dx, domain
+ * [0, n*dx) per axis, y up.  Cell (i,j,k) has index i + nx*(j + ny*k).  The
+ * u, v, w face arrays have (nx+1)*ny*nz, nx*(ny+1)*nz and nx*ny*(nz+1)
+ * entries; u[i,j,k] (at x = i*dx) has index i + (nx+1)*(j + ny*k), v[i,j,k]
+ * index i + nx*(j + (ny+1)*k), w[i,j,k] index i + nx*(j + ny*k).  The six
+ * domain planes are solid walls.
+ */
+#ifndef FLIP_GB300_H
+#define FLIP_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FLIP_ABI_VERSION 1
+
+/* ------------------------------------------------------------ status codes */
+enum {
+  FLIP_OK = 0,
+  FLIP_E_ARG = 1,            /* bad argument, or a state the method cannot solve
+                                (every cell fluid: A is singular, Sec. 3.1.7) */
+  FLIP_E_OOM = 2,            /* device allocation failed */
+  FLIP_E_CUDA = 3,           /* a CUDA call failed (message in flip_last_error) */
+  FLIP_E_NOT_CONVERGED = 4,  /* warning: PCG hit its iteration cap; the step was
+                                still taken with the last iterate */
+  FLIP_E_TIMEOUT = 5,        /* a device-side wait gave up; the step's results are
+                                not valid, the handle stays usable */
+  FLIP_E_SIZE = 6,           /* a buffer size does not match the field */
+  FLIP_E_NOGPU = 7           /* no CUDA device, or not an sm_103 device */
+};
+
+/* ------------------------------------------------------------ parameters */
+enum {
+  FLIP_PREC_FP32 = 0,     /* FP32 vectors and SpMV; dot products accumulated
+                             in FP32 pairs per thread, FP64 across threads */
+  FLIP_PREC_MIXED_IR = 1  /* as FP32 inside; FP64 solution and outer residual
+                             r = b - A x in an iterative-refinement loop */
+};
+
+enum {
+  FLIP_ADVECT_PARTICLE = 0, /* x += dt * (blended particle velocity) */
+  FLIP_ADVECT_GRID = 1      /* x += dt * (interpolated projected grid velocity) */
+};
+
+typedef struct {
+  int32_t n[3];          /* cells per axis, each in [2, 2048] */
+  double dx;             /* cell edge; 1/dx must be an integer <= 2^24 so that
+                            the cell of a float32 position is exact */
+  double dt;             /* time step (s) */
+  double gravity[3];     /* body acceleration (m/s^2), e.g. {0, -9.81, 0} */
+  double rho;            /* density (> 0) */
+  double flip_ratio;     /* FLIP share r of the blend r*FLIP + (1-r)*PIC, [0,1] */
+  double skin;           /* wall clamp distance (> 0, < dx) */
+  double cg_tol;         /* FP32 mode: PCG stops at ||r|| <= cg_tol*||b||.
+                            Mixed mode: tolerance of each inner FP32 solve. */
+  double ir_tol;         /* mixed mode: outer stop at ||b - A x|| <= ir_tol*||b|| */
+  int32_t cg_max_iter;   /* PCG iteration cap (per solve; per inner solve in mixed) */
+  int32_t ir_max_iter;   /* mixed mode: outer iteration cap */
+  int32_t precision;     /* FLIP_PREC_* */
+  int32_t advect_source; /* FLIP_ADVECT_* */
+} flip_params;
+
+/* Fills p with the defaults of the 32^3 dam break: dx = 1/n, dt = 1/240,
+ * g = (0, -9.81, 0), rho = 1, r = 0.95, skin = 1e-3*dx, cg_tol = 1e-6,
+ * ir_tol = 1e-8, cg_max_iter = 20*max(n), ir_max_iter = 20, FP32, particle
+ * advection. */
+void flip_default_params(flip_params* p, int32_t nx, int32_t ny, int32_t nz);
+
+/* Optional allocator: when given to flip_create, every device allocation of
+ * the handle goes through it (one arena per handle, freed at flip_destroy).
+ * alloc returns NULL on failure.  stream is the handle's cudaStream_t. */
+typedef struct {
+  void* ctx;
+  void* (*alloc)(void* ctx, size_t bytes, void* stream);
+  void (*free)(void* ctx, void* ptr, size_t bytes, void* stream);
+} flip_alloc;
+
+/* Per-call statistics of flip_step (all times in ms, summed over the steps of
+ * the call, measured with CUDA events on the handle's stream). */
+typedef struct {
+  int64_t steps;              /* steps taken by this call */
+  int64_t n_particles;
+  int64_t n_fluid_cells;      /* fluid cells of the last step */
+  int64_t n_active_bricks;    /* 8x8x8 cell bricks holding fluid, last step */
+  int64_t cg_iterations;      /* PCG iterations, summed over the steps */
+  int32_t ir_iterations;      /* outer refinements, summed over the steps */
+  int32_t kernel_launches;    /* kernels this library launched in the call */
+  double cg_rel_residual;     /* last step: ||r||/||b|| the solver stopped at
+                                 (mixed: the FP64 outer residual) */
+  double rel_divergence;      /* last step: ||div u_new||_2 / ||div u*||_2 over
+                                 fluid cells, FP64 from the stored fields */
+  double max_speed;           /* last step: max particle speed after the blend */
+  double ms_bin, ms_p2g, ms_divergence, ms_pcg, ms_g2p, ms_total;
+} flip_stats;
+
+typedef struct flip_handle flip_handle;
+
+/* Particle and grid fields for flip_read / flip_write. */
+typedef enum {
+  FLIP_FIELD_PX = 0, FLIP_FIELD_PY, FLIP_FIELD_PZ, /* float32[np] positions */
+  FLIP_FIELD_PU, FLIP_FIELD_PV, FLIP_FIELD_PW,     /* float32[np] velocities */
+  FLIP_FIELD_PID,       /* int32[np]: creation index of each particle */
+  FLIP_FIELD_U_OLD, FLIP_FIELD_V_OLD, FLIP_FIELD_W_OLD, /* float32 faces: P2G
+                           result of the last step, before gravity and walls */
+  FLIP_FIELD_U_NEW, FLIP_FIELD_V_NEW, FLIP_FIELD_W_NEW, /* float32 faces: the
+                           projected velocity of the last step (Eq. 5) */
+  FLIP_FIELD_PRESSURE,  /* float32[n_cells], 0 in air */
+  FLIP_FIELD_PRESSURE_F64, /* float64[n_cells] */
+  FLIP_FIELD_RHS,       /* float32[n_cells]: b = -div u* (Eq. 6), 0 off fluid */
+  FLIP_FIELD_CELL_TYPE, /* uint8[n_cells]: 1 fluid, 0 air */
+  FLIP_FIELD_COUNT_
+} flip_field;
+
+int flip_abi_version(void);
+
+/* Creates a scene from np particles (float32 SoA, Sec. 3.2.1).  The arrays are
+ * copied (host memory when src_is_device == 0, device memory otherwise); the
+ * caller keeps ownership.  np must be in [0, 2^31-1].  Device memory is owned
+ * by the handle: taken through *alloc when non-NULL, else with cudaMallocAsync
+ * on the stream.  stream is a cudaStream_t (NULL: the handle creates its own).
+ * Particle i gets id i (FLIP_FIELD_PID).  On success *out is set and the
+ * particles are already binned for the first step. */
+int flip_create(const flip_params* params, const float* x, const float* y, const float* z,
+                const float* u, const float* v, const float* w, int64_t np,
+                int32_t src_is_device, const flip_alloc* alloc, void* stream,
+                flip_handle** out);
+
+/* Advances the scene by nsteps FLIP steps, stream-ordered and asynchronous.
+ * When stats is non-NULL the call waits for the stream and fills *stats, and
+ * the return value carries device-side conditions of the steps
+ * (FLIP_E_NOT_CONVERGED, FLIP_E_TIMEOUT, FLIP_E_ARG for a singular system);
+ * without stats those conditions are reported by the next flip_sync. */
+int flip_step(flip_handle* h, int32_t nsteps, flip_stats* stats);
+
+/* Waits for the handle's stream; returns the device-side condition of the steps
+ * since the last report (FLIP_OK when none). */
+int flip_sync(flip_handle* h);
+
+/* Copies a field into caller memory (dst_is_device: device pointer).  bytes must
+ * equal the field's size (FLIP_E_SIZE otherwise).  Particle fields come in the
+ * handle's current (cell-sorted) order, with FLIP_FIELD_PID telling which
+ * particle each entry is.  Synchronous. */
+int flip_read(flip_handle* h, flip_field which, void* dst, size_t bytes, int32_t dst_is_device);
+
+/* Overwrites a particle field (PX..PW or PID) in the handle's current order and
+ * re-bins the particles.  Synchronous with respect to the source buffer. */
+int flip_write(flip_handle* h, flip_field which, const void* src, size_t bytes,
+               int32_t src_is_device);
+
+/* All six particle arrays (float32[np] each) at once, in the handle's current
+ * order; id (int32[np], nullable) receives the creation index of each entry.
+ * Synchronous. */
+int flip_read_particles(flip_handle* h, float* x, float* y, float* z, float* u, float* v,
+                        float* w, int32_t* id, int32_t dst_is_device);
+
+/* Overwrites all six particle arrays (float32[np] each, the handle's current
+ * order, ids unchanged) and re-bins once.  Synchronous with respect to the
+ * sources. */
+int flip_write_particles(flip_handle* h, const float* x, const float* y, const float* z,
+                         const float* u, const float* v, const float* w, int32_t src_is_device);
+
+/* Size in bytes of a field of this handle. */
+size_t flip_field_bytes(const flip_handle* h, flip_field which);
+
+void flip_destroy(flip_handle* h);
+
+const char* flip_strerror(int status);
+const char* flip_last_error(void);
+
+/* Standalone pressure solve (Sec. 3.1.7): A p = b for the cell types in type.
+ * type: device uint8[n_cells] (1 fluid, anything else air); b: device
+ * float32[n_cells] (read on fluid cells only); p: device float32[n_cells],
+ * written on every cell (0 off fluid).  Uses params->n, dx, dt, rho, cg_tol,
+ * cg_max_iter (FP32 mode; precision must be FLIP_PREC_FP32).  Scratch memory is
+ * allocated and freed with cudaMallocAsync/cudaFreeAsync on stream.  Waits for
+ * the stream before returning; *iterations (nullable) gets the iteration count
+ * and *rel_residual (nullable) the final ||r||/||b||. */
+int flip_solve_pressure(const flip_params* params, const uint8_t* type, const float* b,
+                        float* p, void* stream, int32_t* iterations, double* rel_residual);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

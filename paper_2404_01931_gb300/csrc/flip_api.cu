@@ -1,0 +1,766 @@
+// flip_api.cu — the C ABI of include/flip.h: handle lifetime, device memory,
+// and the stream-ordered sequence of kernels that makes one FLIP step
+// (Sec. 3 of the paper, order: bin -> P2G -> gravity/walls + divergence ->
+// PCG -> G2P blend + advection).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/flip.h"
+#include "flip_kernels.cuh"
+
+using namespace flipk;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  const int code = (e == cudaErrorMemoryAllocation) ? FLIP_E_OOM : FLIP_E_CUDA;
+  return fail(code, std::string(what) + ": " + cudaGetErrorName(e) + " (" +
+                        cudaGetErrorString(e) + ")");
+}
+
+#define FLIP_CUDA(call)                              \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+// Carves sub-buffers out of one arena; first pass measures, second assigns.
+struct Carver {
+  char* base = nullptr;
+  size_t off = 0;
+  template <class T>
+  T* take(size_t count) {
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += align_up(sizeof(T) * std::max<size_t>(count, 1));
+    return p;
+  }
+};
+
+}  // namespace
+
+struct flip_handle {
+  flip_params prm;
+  Grid g;
+  StepConsts K;
+  long long np = 0, ncells = 0, nkeys = 0, nf[3] = {0, 0, 0};
+  unsigned int nbricks = 0;
+  bool mixed = false;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  flip_alloc alloc{};
+  bool has_alloc = false;
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  PartView P[2];
+  int cur = 0;
+  BinView B;
+  uint8_t* type = nullptr;
+  float2* acc[3] = {nullptr, nullptr, nullptr};
+  float* uo[3] = {nullptr, nullptr, nullptr};
+  float* b32 = nullptr;
+  double* b64 = nullptr;
+  float* x32 = nullptr;
+  double* x64 = nullptr;
+  float2* pff = nullptr;
+  float* r = nullptr;
+  float* pa = nullptr;
+  float* pb = nullptr;
+  float* q = nullptr;
+  double* partials = nullptr;
+  unsigned int* bar = nullptr;
+  DevStats* dstats = nullptr;
+  DevStats* hstats = nullptr;  // pinned
+  double* norms = nullptr;
+  void* tmp = nullptr;
+  size_t tmp_bytes = 0;
+  int pcg_blocks = 0, sm_count = 0, p2g_blocks = 0;
+  long long reported_cg = 0, reported_ir = 0;
+  int launches = 0;
+  bool stepped = false;
+};
+
+extern "C" {
+
+int flip_abi_version(void) { return FLIP_ABI_VERSION; }
+
+const char* flip_last_error(void) { return g_last_error.c_str(); }
+
+const char* flip_strerror(int status) {
+  switch (status) {
+    case FLIP_OK: return "ok";
+    case FLIP_E_ARG: return "invalid argument or unsolvable state";
+    case FLIP_E_OOM: return "device allocation failed";
+    case FLIP_E_CUDA: return "CUDA error";
+    case FLIP_E_NOT_CONVERGED: return "pressure solve hit its iteration cap";
+    case FLIP_E_TIMEOUT: return "device-side wait timed out";
+    case FLIP_E_SIZE: return "buffer size does not match the field";
+    case FLIP_E_NOGPU: return "no usable sm_103 CUDA device";
+    default: return "unknown status";
+  }
+}
+
+void flip_default_params(flip_params* p, int32_t nx, int32_t ny, int32_t nz) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->n[0] = nx;
+  p->n[1] = ny;
+  p->n[2] = nz;
+  const int m = std::max(nx, std::max(ny, nz));
+  p->dx = m > 0 ? 1.0 / m : 0.0;
+  p->dt = 1.0 / 240.0;
+  p->gravity[1] = -9.81;
+  p->rho = 1.0;
+  p->flip_ratio = 0.95;
+  p->skin = 1e-3 * p->dx;
+  p->cg_tol = 1e-6;
+  p->ir_tol = 1e-8;
+  p->cg_max_iter = 20 * m;
+  p->ir_max_iter = 20;
+  p->precision = FLIP_PREC_FP32;
+  p->advect_source = FLIP_ADVECT_PARTICLE;
+}
+
+}  // extern "C"
+
+namespace {
+
+int check_params(const flip_params* p, bool need_particles_prm) {
+  if (!p) return fail(FLIP_E_ARG, "params is NULL");
+  for (int a = 0; a < 3; ++a)
+    if (p->n[a] < 2 || p->n[a] > 2048) return fail(FLIP_E_ARG, "n[a] must be in [2, 2048]");
+  const long long nc = (long long)p->n[0] * p->n[1] * p->n[2];
+  const long long nfmax = (long long)(p->n[0] + 1) * (p->n[1] + 1) * (p->n[2] + 1);
+  if (nfmax >= (1LL << 31)) return fail(FLIP_E_ARG, "grid too large (face count >= 2^31)");
+  (void)nc;
+  if (!(p->dx > 0.0) || !std::isfinite(p->dx)) return fail(FLIP_E_ARG, "dx must be > 0");
+  const double inv = 1.0 / p->dx;
+  if (!(inv == std::floor(inv)) || inv > 16777216.0)
+    return fail(FLIP_E_ARG, "1/dx must be an integer <= 2^24");
+  if (!(p->dt > 0.0) || !std::isfinite(p->dt)) return fail(FLIP_E_ARG, "dt must be > 0");
+  if (!(p->rho > 0.0)) return fail(FLIP_E_ARG, "rho must be > 0");
+  if (!(p->cg_tol > 0.0) || p->cg_max_iter < 1) return fail(FLIP_E_ARG, "bad PCG tolerance/cap");
+  if (p->precision != FLIP_PREC_FP32 && p->precision != FLIP_PREC_MIXED_IR)
+    return fail(FLIP_E_ARG, "unknown precision mode");
+  if (p->precision == FLIP_PREC_MIXED_IR && (!(p->ir_tol > 0.0) || p->ir_max_iter < 1))
+    return fail(FLIP_E_ARG, "bad iterative-refinement tolerance/cap");
+  if (need_particles_prm) {
+    if (!(p->flip_ratio >= 0.0 && p->flip_ratio <= 1.0))
+      return fail(FLIP_E_ARG, "flip_ratio must be in [0, 1]");
+    if (!(p->skin > 0.0 && p->skin < p->dx)) return fail(FLIP_E_ARG, "skin must be in (0, dx)");
+    if (p->advect_source != FLIP_ADVECT_PARTICLE && p->advect_source != FLIP_ADVECT_GRID)
+      return fail(FLIP_E_ARG, "unknown advect_source");
+    for (int a = 0; a < 3; ++a)
+      if (!std::isfinite(p->gravity[a])) return fail(FLIP_E_ARG, "gravity must be finite");
+  }
+  return FLIP_OK;
+}
+
+int check_device() {
+  int dev = 0, n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || n == 0) {
+    cudaGetLastError();
+    return fail(FLIP_E_NOGPU, std::string("no CUDA device: ") + cudaGetErrorString(e));
+  }
+  FLIP_CUDA(cudaGetDevice(&dev));
+  int major = 0, minor = 0, coop = 0;
+  FLIP_CUDA(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev));
+  FLIP_CUDA(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev));
+  FLIP_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (major != 10 || minor != 3)
+    return fail(FLIP_E_NOGPU, "this library is built for sm_103a (GB300); device is sm_" +
+                                  std::to_string(major) + std::to_string(minor));
+  if (!coop) return fail(FLIP_E_NOGPU, "device lacks cooperative launch");
+  return FLIP_OK;
+}
+
+Grid make_grid(const flip_params& p) {
+  Grid g{};
+  g.nx = p.n[0];
+  g.ny = p.n[1];
+  g.nz = p.n[2];
+  g.bx = (g.nx + BRICK - 1) / BRICK;
+  g.by = (g.ny + BRICK - 1) / BRICK;
+  g.bz = (g.nz + BRICK - 1) / BRICK;
+  g.inv_dx = (float)(1.0 / p.dx);
+  g.dx = (float)p.dx;
+  for (int a = 0; a < 3; ++a) g.hi[a] = (float)((double)p.n[a] * p.dx - p.skin);
+  g.skin = (float)p.skin;
+  return g;
+}
+
+StepConsts make_consts(const flip_params& p) {
+  StepConsts k{};
+  for (int a = 0; a < 3; ++a) k.gdt[a] = (float)(p.gravity[a] * p.dt);
+  k.pscale = (float)(p.dt / (p.rho * p.dx));
+  k.flip_ratio = (float)p.flip_ratio;
+  k.advect_grid = p.advect_source == FLIP_ADVECT_GRID;
+  k.dt = (float)p.dt;
+  return k;
+}
+
+void fill_pcg_tables(PcgArgs& a, const flip_params& p) {
+  const double s = p.dt / (p.rho * p.dx * p.dx);
+  a.s = (float)s;
+  a.s64 = s;
+  for (int c = 0; c < 8; ++c) {
+    a.diag_tab[c] = (float)(s * c);
+    a.minv_tab[c] = c > 0 ? (float)(1.0 / (s * c)) : 0.0f;
+  }
+}
+
+// Lays out (or measures) every device buffer of a handle.
+void carve(flip_handle* h, Carver& cv) {
+  const size_t np = (size_t)h->np, nc = (size_t)h->ncells, nk = (size_t)h->nkeys,
+               nb = h->nbricks;
+  for (int b = 0; b < 2; ++b) {
+    h->P[b].x = cv.take<float>(np);
+    h->P[b].y = cv.take<float>(np);
+    h->P[b].z = cv.take<float>(np);
+    h->P[b].u = cv.take<float>(np);
+    h->P[b].v = cv.take<float>(np);
+    h->P[b].w = cv.take<float>(np);
+    h->P[b].id = cv.take<int>(np);
+  }
+  h->B.key = cv.take<unsigned int>(np);
+  h->B.rank = cv.take<unsigned int>(np);
+  h->B.cell_count = cv.take<unsigned int>(nk);
+  h->B.local_start = cv.take<unsigned int>(nk);
+  h->B.brick_count = cv.take<unsigned int>(nb);
+  h->B.brick_fluid = cv.take<unsigned int>(nb);
+  h->B.brick_start = cv.take<unsigned int>(nb + 1);
+  h->B.active = cv.take<unsigned int>(nb);
+  h->type = cv.take<uint8_t>(nc);
+  for (int d = 0; d < 3; ++d) {
+    h->acc[d] = cv.take<float2>((size_t)h->nf[d]);
+    h->uo[d] = cv.take<float>((size_t)h->nf[d]);
+  }
+  h->x32 = cv.take<float>(nc);
+  if (h->mixed) {
+    h->b64 = cv.take<double>(nc);
+    h->x64 = cv.take<double>(nc);
+    h->pff = cv.take<float2>(nc);
+  } else {
+    h->b32 = cv.take<float>(nc);
+  }
+  h->r = cv.take<float>(nc);
+  h->pa = cv.take<float>(nc);
+  h->pb = cv.take<float>(nc);
+  h->q = cv.take<float>(nc);
+  h->partials = cv.take<double>((size_t)PCG_SLOTS * (size_t)h->pcg_blocks);
+  h->bar = cv.take<unsigned int>(2);
+  h->dstats = cv.take<DevStats>(1);
+  h->norms = cv.take<double>(2);
+  const size_t nfmax = (size_t)std::max(h->nf[0], std::max(h->nf[1], h->nf[2]));
+  h->tmp_bytes = std::max(nfmax * sizeof(float), nc * sizeof(double));
+  h->tmp = cv.take<char>(h->tmp_bytes);
+}
+
+int upload(void* dst, const void* src, size_t bytes, int src_dev, cudaStream_t s) {
+  if (bytes == 0) return FLIP_OK;
+  if (!src) return fail(FLIP_E_ARG, "source pointer is NULL");
+  FLIP_CUDA(cudaMemcpyAsync(dst, src, bytes,
+                            src_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  return FLIP_OK;
+}
+
+int rebin(flip_handle* h) {
+  FLIP_CUDA(cudaMemsetAsync(h->B.cell_count, 0, sizeof(unsigned int) * (size_t)h->nkeys,
+                            h->stream));
+  launch_rebin(h->g, h->P[h->cur], h->B, h->np, h->stream);
+  FLIP_CUDA(cudaGetLastError());
+  return FLIP_OK;
+}
+
+PcgArgs pcg_args(flip_handle* h) {
+  PcgArgs a{};
+  a.g = h->g;
+  fill_pcg_tables(a, h->prm);
+  a.type = h->type;
+  a.active = h->B.active;
+  a.n_active = &h->dstats->n_active;
+  a.b32 = h->b32;
+  a.b64 = h->b64;
+  a.x32 = h->x32;
+  a.x64 = h->x64;
+  a.pff = h->pff;
+  a.r = h->r;
+  a.pa = h->pa;
+  a.pb = h->pb;
+  a.q = h->q;
+  a.partials = h->partials;
+  a.bar = h->bar;
+  a.status = &h->dstats->status;
+  a.stats = h->dstats;
+  a.tol = h->prm.cg_tol;
+  a.ir_tol = h->prm.ir_tol;
+  a.max_iter = h->prm.cg_max_iter;
+  a.ir_max_iter = h->prm.ir_max_iter;
+  a.check_singular = 1;
+  a.timeout_ns = 5000000000ull;
+  return a;
+}
+
+int status_to_code(int st) {
+  if (st & DEV_TIMEOUT) return fail(FLIP_E_TIMEOUT, "a device-side wait in the PCG timed out");
+  if (st & DEV_SINGULAR)
+    return fail(FLIP_E_ARG, "every cell is fluid: the pressure system is singular");
+  if (st & DEV_NOT_CONVERGED) return fail(FLIP_E_NOT_CONVERGED, "PCG hit its iteration cap");
+  return FLIP_OK;
+}
+
+// Reads and clears the sticky device status; the stream must be idle.
+int take_status(flip_handle* h) {
+  FLIP_CUDA(cudaMemcpyAsync(h->hstats, h->dstats, sizeof(DevStats), cudaMemcpyDeviceToHost,
+                            h->stream));
+  FLIP_CUDA(cudaMemsetAsync(&h->dstats->status, 0, sizeof(int), h->stream));
+  FLIP_CUDA(cudaStreamSynchronize(h->stream));
+  return status_to_code(h->hstats->status);
+}
+
+}  // namespace
+
+extern "C" {
+
+int flip_create(const flip_params* params, const float* x, const float* y, const float* z,
+                const float* u, const float* v, const float* w, int64_t np,
+                int32_t src_is_device, const flip_alloc* alloc, void* stream,
+                flip_handle** out) {
+  if (!out) return fail(FLIP_E_ARG, "out is NULL");
+  *out = nullptr;
+  int rc = check_params(params, true);
+  if (rc) return rc;
+  if (np < 0 || np > 2147483647LL) return fail(FLIP_E_ARG, "np must be in [0, 2^31-1]");
+  if (alloc && (!alloc->alloc || !alloc->free))
+    return fail(FLIP_E_ARG, "flip_alloc needs both alloc and free");
+  rc = check_device();
+  if (rc) return rc;
+
+  flip_handle* h = new (std::nothrow) flip_handle();
+  if (!h) return fail(FLIP_E_OOM, "host allocation failed");
+  h->prm = *params;
+  h->g = make_grid(*params);
+  h->K = make_consts(*params);
+  h->np = np;
+  h->ncells = (long long)h->g.nx * h->g.ny * h->g.nz;
+  h->nbricks = (unsigned)h->g.bx * h->g.by * h->g.bz;
+  h->nkeys = (long long)h->nbricks * BRICK_CELLS;
+  for (int d = 0; d < 3; ++d) h->nf[d] = n_faces(h->g, d);
+  h->mixed = params->precision == FLIP_PREC_MIXED_IR;
+  if (alloc) {
+    h->alloc = *alloc;
+    h->has_alloc = true;
+  }
+  auto cleanup = [&](int code) {
+    flip_destroy(h);
+    return code;
+  };
+  cudaError_t e;
+  if (stream) {
+    h->stream = (cudaStream_t)stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaStreamCreate"));
+    h->own_stream = true;
+  }
+  e = pcg_max_blocks(&h->pcg_blocks, &h->sm_count);
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "occupancy query"));
+  h->p2g_blocks = h->sm_count * 4;
+
+  Carver measure;
+  carve(h, measure);
+  h->arena_bytes = measure.off;
+  if (h->has_alloc) {
+    h->arena = h->alloc.alloc(h->alloc.ctx, h->arena_bytes, (void*)h->stream);
+    if (!h->arena) return cleanup(fail(FLIP_E_OOM, "allocator callback returned NULL"));
+  } else {
+    e = cudaMallocAsync(&h->arena, h->arena_bytes, h->stream);
+    if (e != cudaSuccess) {
+      h->arena = nullptr;
+      return cleanup(cuda_fail(e, "cudaMallocAsync(arena)"));
+    }
+  }
+  Carver assign;
+  assign.base = (char*)h->arena;
+  carve(h, assign);
+  e = cudaMallocHost((void**)&h->hstats, sizeof(DevStats));
+  if (e != cudaSuccess) {
+    h->hstats = nullptr;
+    return cleanup(cuda_fail(e, "cudaMallocHost"));
+  }
+  // Zero everything once: histogram, accumulators, fields, barrier, stats.
+  e = cudaMemsetAsync(h->arena, 0, h->arena_bytes, h->stream);
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaMemsetAsync(arena)"));
+  const size_t pb = sizeof(float) * (size_t)np;
+  const float* src[6] = {x, y, z, u, v, w};
+  float* dst[6] = {h->P[0].x, h->P[0].y, h->P[0].z, h->P[0].u, h->P[0].v, h->P[0].w};
+  for (int a = 0; a < 6; ++a) {
+    rc = upload(dst[a], src[a], pb, src_is_device, h->stream);
+    if (rc) return cleanup(rc);
+  }
+  launch_iota(h->P[0].id, np, h->stream);
+  rc = rebin(h);
+  if (rc) return cleanup(rc);
+  e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "flip_create"));
+  *out = h;
+  return FLIP_OK;
+}
+
+void flip_destroy(flip_handle* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->arena) {
+    if (h->has_alloc) h->alloc.free(h->alloc.ctx, h->arena, h->arena_bytes, (void*)h->stream);
+    else cudaFreeAsync(h->arena, h->stream);
+  }
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->hstats) cudaFreeHost(h->hstats);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+int flip_step(flip_handle* h, int32_t nsteps, flip_stats* stats) {
+  if (!h) return fail(FLIP_E_ARG, "handle is NULL");
+  if (nsteps < 0) return fail(FLIP_E_ARG, "nsteps must be >= 0");
+  const cudaStream_t s = h->stream;
+  const bool timed = stats != nullptr;
+  cudaEvent_t ev[6] = {};
+  float ms[5] = {0, 0, 0, 0, 0};
+  float ms_total = 0.0f;
+  if (timed) {
+    for (auto& e : ev) FLIP_CUDA(cudaEventCreate(&e));
+  }
+  const int launches0 = h->launches;
+  cudaEvent_t t_begin = nullptr, t_end = nullptr;
+  if (timed) {
+    FLIP_CUDA(cudaEventCreate(&t_begin));
+    FLIP_CUDA(cudaEventCreate(&t_end));
+    FLIP_CUDA(cudaEventRecord(t_begin, s));
+  }
+  const float* uo[3] = {h->uo[0], h->uo[1], h->uo[2]};
+  PcgArgs pa = pcg_args(h);
+  int rc = FLIP_OK;
+  for (int st = 0; st < nsteps; ++st) {
+    if (timed) FLIP_CUDA(cudaEventRecord(ev[0], s));
+    launch_bin(h->g, h->B, h->type, h->dstats, s);
+    launch_scatter(h->P[h->cur], h->P[1 - h->cur], h->B, h->np, s);
+    h->cur = 1 - h->cur;
+    h->launches += 2 + (h->np > 0);
+    if (timed) FLIP_CUDA(cudaEventRecord(ev[1], s));
+    launch_p2g(h->g, h->P[h->cur], h->B, h->acc, h->dstats, h->p2g_blocks, s);
+    launch_finalize(h->g, h->acc, h->uo, s);
+    h->launches += 2;
+    if (timed) FLIP_CUDA(cudaEventRecord(ev[2], s));
+    launch_divergence(h->g, h->K, h->type, uo, h->b32, h->b64, h->x32, h->x64, h->pff, h->bar,
+                      h->dstats, s);
+    h->launches += 1;
+    if (timed) FLIP_CUDA(cudaEventRecord(ev[3], s));
+    FLIP_CUDA(launch_pcg(pa, h->mixed, h->pcg_blocks, s));
+    h->launches += 1;
+    if (timed) FLIP_CUDA(cudaEventRecord(ev[4], s));
+    launch_g2p(h->g, h->K, h->P[h->cur], h->B, uo, h->mixed ? nullptr : h->x32, h->pff,
+               h->dstats, h->np, s);
+    h->launches += (h->np > 0);
+    if (timed) FLIP_CUDA(cudaEventRecord(ev[5], s));
+    FLIP_CUDA(cudaGetLastError());
+    if (timed) {
+      FLIP_CUDA(cudaEventSynchronize(ev[5]));
+      for (int q = 0; q < 5; ++q) {
+        float t = 0.0f;
+        FLIP_CUDA(cudaEventElapsedTime(&t, ev[q], ev[q + 1]));
+        ms[q] += t;
+      }
+    }
+    h->stepped = true;
+  }
+  if (timed) {
+    FLIP_CUDA(cudaEventRecord(t_end, s));
+    FLIP_CUDA(cudaEventSynchronize(t_end));
+    FLIP_CUDA(cudaEventElapsedTime(&ms_total, t_begin, t_end));
+    std::memset(stats, 0, sizeof(*stats));
+    FLIP_CUDA(cudaMemsetAsync(h->norms, 0, 2 * sizeof(double), s));
+    if (h->stepped) {
+      launch_div_norms(h->g, h->K, h->type, uo, h->mixed ? nullptr : h->x32, h->x64, h->norms, s);
+      FLIP_CUDA(cudaGetLastError());
+      h->launches += 1;
+    }
+    double norms[2] = {0.0, 0.0};
+    FLIP_CUDA(cudaMemcpyAsync(norms, h->norms, sizeof(norms), cudaMemcpyDeviceToHost, s));
+    rc = take_status(h);
+    const DevStats& d = *h->hstats;
+    stats->steps = nsteps;
+    stats->n_particles = h->np;
+    stats->n_fluid_cells = d.n_fluid;
+    stats->n_active_bricks = d.n_active;
+    stats->cg_iterations = d.cg_iters_total - h->reported_cg;
+    stats->ir_iterations = (int32_t)(d.ir_iters_total - h->reported_ir);
+    h->reported_cg = d.cg_iters_total;
+    h->reported_ir = d.ir_iters_total;
+    stats->kernel_launches = h->launches - launches0;
+    stats->cg_rel_residual = d.rel_res;
+    stats->rel_divergence = norms[0] > 0.0 ? std::sqrt(norms[1] / norms[0]) : 0.0;
+    float ms_f;
+    std::memcpy(&ms_f, &d.max_speed_bits, sizeof(float));
+    stats->max_speed = ms_f;
+    stats->ms_bin = ms[0];
+    stats->ms_p2g = ms[1];
+    stats->ms_divergence = ms[2];
+    stats->ms_pcg = ms[3];
+    stats->ms_g2p = ms[4];
+    stats->ms_total = ms_total;
+    for (auto& e : ev) cudaEventDestroy(e);
+    cudaEventDestroy(t_begin);
+    cudaEventDestroy(t_end);
+  }
+  return rc;
+}
+
+int flip_sync(flip_handle* h) {
+  if (!h) return fail(FLIP_E_ARG, "handle is NULL");
+  FLIP_CUDA(cudaStreamSynchronize(h->stream));
+  return take_status(h);
+}
+
+size_t flip_field_bytes(const flip_handle* h, flip_field which) {
+  if (!h) return 0;
+  switch (which) {
+    case FLIP_FIELD_PX: case FLIP_FIELD_PY: case FLIP_FIELD_PZ:
+    case FLIP_FIELD_PU: case FLIP_FIELD_PV: case FLIP_FIELD_PW:
+    case FLIP_FIELD_PID:
+      return 4 * (size_t)h->np;
+    case FLIP_FIELD_U_OLD: case FLIP_FIELD_U_NEW: return 4 * (size_t)h->nf[0];
+    case FLIP_FIELD_V_OLD: case FLIP_FIELD_V_NEW: return 4 * (size_t)h->nf[1];
+    case FLIP_FIELD_W_OLD: case FLIP_FIELD_W_NEW: return 4 * (size_t)h->nf[2];
+    case FLIP_FIELD_PRESSURE: case FLIP_FIELD_RHS: return 4 * (size_t)h->ncells;
+    case FLIP_FIELD_PRESSURE_F64: return 8 * (size_t)h->ncells;
+    case FLIP_FIELD_CELL_TYPE: return (size_t)h->ncells;
+    default: return 0;
+  }
+}
+
+int flip_read(flip_handle* h, flip_field which, void* dst, size_t bytes, int32_t dst_is_device) {
+  if (!h) return fail(FLIP_E_ARG, "handle is NULL");
+  const size_t need = flip_field_bytes(h, which);
+  if (which < 0 || which >= FLIP_FIELD_COUNT_) return fail(FLIP_E_ARG, "unknown field");
+  if (bytes != need) return fail(FLIP_E_SIZE, "bytes must be " + std::to_string(need));
+  if (need == 0) return FLIP_OK;
+  if (!dst) return fail(FLIP_E_ARG, "dst is NULL");
+  const cudaStream_t s = h->stream;
+  const void* src = nullptr;
+  const PartView& P = h->P[h->cur];
+  switch (which) {
+    case FLIP_FIELD_PX: src = P.x; break;
+    case FLIP_FIELD_PY: src = P.y; break;
+    case FLIP_FIELD_PZ: src = P.z; break;
+    case FLIP_FIELD_PU: src = P.u; break;
+    case FLIP_FIELD_PV: src = P.v; break;
+    case FLIP_FIELD_PW: src = P.w; break;
+    case FLIP_FIELD_PID: src = P.id; break;
+    case FLIP_FIELD_U_OLD: src = h->uo[0]; break;
+    case FLIP_FIELD_V_OLD: src = h->uo[1]; break;
+    case FLIP_FIELD_W_OLD: src = h->uo[2]; break;
+    case FLIP_FIELD_U_NEW: case FLIP_FIELD_V_NEW: case FLIP_FIELD_W_NEW: {
+      const int d = which - FLIP_FIELD_U_NEW;
+      launch_u_new(h->g, h->K, d, h->uo[d], h->mixed ? nullptr : h->x32, h->pff, (float*)h->tmp, s);
+      src = h->tmp;
+      break;
+    }
+    case FLIP_FIELD_PRESSURE:
+      if (h->mixed) {
+        launch_f64_to_f32(h->x64, (float*)h->tmp, h->ncells, s);
+        src = h->tmp;
+      } else {
+        src = h->x32;
+      }
+      break;
+    case FLIP_FIELD_PRESSURE_F64:
+      if (h->mixed) {
+        src = h->x64;
+      } else {
+        launch_f32_to_f64(h->x32, (double*)h->tmp, h->ncells, s);
+        src = h->tmp;
+      }
+      break;
+    case FLIP_FIELD_RHS:
+      if (h->mixed) {
+        launch_f64_to_f32(h->b64, (float*)h->tmp, h->ncells, s);
+        src = h->tmp;
+      } else {
+        src = h->b32;
+      }
+      break;
+    case FLIP_FIELD_CELL_TYPE: src = h->type; break;
+    default: return fail(FLIP_E_ARG, "unknown field");
+  }
+  FLIP_CUDA(cudaGetLastError());
+  FLIP_CUDA(cudaMemcpyAsync(dst, src, need,
+                            dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  FLIP_CUDA(cudaStreamSynchronize(s));
+  return FLIP_OK;
+}
+
+int flip_write(flip_handle* h, flip_field which, const void* src, size_t bytes,
+               int32_t src_is_device) {
+  if (!h) return fail(FLIP_E_ARG, "handle is NULL");
+  if (which < FLIP_FIELD_PX || which > FLIP_FIELD_PID)
+    return fail(FLIP_E_ARG, "only particle fields can be written");
+  const size_t need = flip_field_bytes(h, which);
+  if (bytes != need) return fail(FLIP_E_SIZE, "bytes must be " + std::to_string(need));
+  const PartView& P = h->P[h->cur];
+  void* dst = nullptr;
+  switch (which) {
+    case FLIP_FIELD_PX: dst = P.x; break;
+    case FLIP_FIELD_PY: dst = P.y; break;
+    case FLIP_FIELD_PZ: dst = P.z; break;
+    case FLIP_FIELD_PU: dst = P.u; break;
+    case FLIP_FIELD_PV: dst = P.v; break;
+    case FLIP_FIELD_PW: dst = P.w; break;
+    default: dst = P.id; break;
+  }
+  int rc = upload(dst, src, need, src_is_device, h->stream);
+  if (rc) return rc;
+  if (which <= FLIP_FIELD_PZ) {
+    rc = rebin(h);
+    if (rc) return rc;
+  }
+  FLIP_CUDA(cudaStreamSynchronize(h->stream));
+  return FLIP_OK;
+}
+
+int flip_read_particles(flip_handle* h, float* x, float* y, float* z, float* u, float* v,
+                        float* w, int32_t* id, int32_t dst_is_device) {
+  if (!h) return fail(FLIP_E_ARG, "handle is NULL");
+  const PartView& P = h->P[h->cur];
+  void* dst[7] = {x, y, z, u, v, w, id};
+  const void* src[7] = {P.x, P.y, P.z, P.u, P.v, P.w, P.id};
+  const size_t nb = 4 * (size_t)h->np;
+  for (int a = 0; a < 7; ++a) {
+    if (!dst[a]) {
+      if (a < 6 && nb) return fail(FLIP_E_ARG, "particle destination is NULL");
+      continue;
+    }
+    if (nb)
+      FLIP_CUDA(cudaMemcpyAsync(dst[a], src[a], nb,
+                                dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                h->stream));
+  }
+  FLIP_CUDA(cudaStreamSynchronize(h->stream));
+  return FLIP_OK;
+}
+
+int flip_write_particles(flip_handle* h, const float* x, const float* y, const float* z,
+                         const float* u, const float* v, const float* w, int32_t src_is_device) {
+  if (!h) return fail(FLIP_E_ARG, "handle is NULL");
+  const PartView& P = h->P[h->cur];
+  float* dst[6] = {P.x, P.y, P.z, P.u, P.v, P.w};
+  const float* src[6] = {x, y, z, u, v, w};
+  for (int a = 0; a < 6; ++a) {
+    const int rc = upload(dst[a], src[a], 4 * (size_t)h->np, src_is_device, h->stream);
+    if (rc) return rc;
+  }
+  const int rc = rebin(h);
+  if (rc) return rc;
+  FLIP_CUDA(cudaStreamSynchronize(h->stream));
+  return FLIP_OK;
+}
+
+int flip_solve_pressure(const flip_params* params, const uint8_t* type, const float* b, float* p,
+                        void* stream, int32_t* iterations, double* rel_residual) {
+  int rc = check_params(params, false);
+  if (rc) return rc;
+  if (params->precision != FLIP_PREC_FP32)
+    return fail(FLIP_E_ARG, "flip_solve_pressure runs the FP32 solver only");
+  if (!type || !b || !p) return fail(FLIP_E_ARG, "type, b and p must be device pointers");
+  rc = check_device();
+  if (rc) return rc;
+  const cudaStream_t s = (cudaStream_t)stream;
+  const Grid g = make_grid(*params);
+  const long long nc = (long long)g.nx * g.ny * g.nz;
+  const unsigned int nb = (unsigned)g.bx * g.by * g.bz;
+  int blocks = 0, sms = 0;
+  FLIP_CUDA(pcg_max_blocks(&blocks, &sms));
+  // scratch: r, p_a, p_b, q, brick flags, active list, partials, barrier, stats
+  Carver cv;
+  auto lay = [&](Carver& c, float** r, float** pa, float** pb, float** q, unsigned int** bf,
+                 unsigned int** act, double** part, unsigned int** bar, DevStats** st) {
+    *r = c.take<float>((size_t)nc);
+    *pa = c.take<float>((size_t)nc);
+    *pb = c.take<float>((size_t)nc);
+    *q = c.take<float>((size_t)nc);
+    *bf = c.take<unsigned int>(nb);
+    *act = c.take<unsigned int>(nb);
+    *part = c.take<double>((size_t)PCG_SLOTS * blocks);
+    *bar = c.take<unsigned int>(2);
+    *st = c.take<DevStats>(1);
+  };
+  float *r, *pa_, *pb_, *q;
+  unsigned int *bf, *act, *bar;
+  double* part;
+  DevStats* st;
+  lay(cv, &r, &pa_, &pb_, &q, &bf, &act, &part, &bar, &st);
+  void* arena = nullptr;
+  FLIP_CUDA(cudaMallocAsync(&arena, cv.off, s));
+  Carver as;
+  as.base = (char*)arena;
+  lay(as, &r, &pa_, &pb_, &q, &bf, &act, &part, &bar, &st);
+  DevStats hst{};
+  cudaError_t e = cudaMemsetAsync(arena, 0, cv.off, s);
+  if (e == cudaSuccess) {
+    launch_zero_off_fluid(g, type, p, bar, s);
+    launch_mark_bricks(g, type, bf, s);
+    launch_compact_bricks(g, bf, act, st, s);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    PcgArgs a{};
+    a.g = g;
+    fill_pcg_tables(a, *params);
+    a.type = type;
+    a.active = act;
+    a.n_active = &st->n_active;
+    a.b32 = b;
+    a.x32 = p;
+    a.r = r;
+    a.pa = pa_;
+    a.pb = pb_;
+    a.q = q;
+    a.partials = part;
+    a.bar = bar;
+    a.status = &st->status;
+    a.stats = st;
+    a.tol = params->cg_tol;
+    a.max_iter = params->cg_max_iter;
+    a.check_singular = 1;
+    a.timeout_ns = 5000000000ull;
+    e = launch_pcg(a, false, blocks, s);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hst, st, sizeof(DevStats), cudaMemcpyDeviceToHost, s);
+  cudaError_t e2 = cudaFreeAsync(arena, s);
+  cudaError_t e3 = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "flip_solve_pressure");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
+  if (e3 != cudaSuccess) return cuda_fail(e3, "flip_solve_pressure sync");
+  if (iterations) *iterations = hst.cg_iters;
+  if (rel_residual) *rel_residual = hst.rel_res;
+  return status_to_code(hst.status);
+}
+
+}  // extern "C"

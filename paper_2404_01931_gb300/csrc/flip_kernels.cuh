@@ -1,0 +1,136 @@
+// flip_kernels.cuh — argument structs and host-side launchers of the FLIP kernels.
+#pragma once
+
+#include "flip_internal.cuh"
+
+namespace flipk {
+
+struct PartView {
+  float* x;
+  float* y;
+  float* z;
+  float* u;
+  float* v;
+  float* w;
+  int* id;
+};
+
+struct BinView {
+  unsigned int* cell_count;   // [nkeys] histogram, all zero between steps
+  unsigned int* local_start;  // [nkeys] exclusive scan of the counts inside each brick
+  unsigned int* brick_count;  // [nbricks]
+  unsigned int* brick_fluid;  // [nbricks] fluid cells per brick
+  unsigned int* brick_start;  // [nbricks + 1]
+  unsigned int* active;       // [nbricks] bricks that hold particles, ascending
+  unsigned int* key;          // [np] cell key of each particle (current buffer order)
+  unsigned int* rank;         // [np] rank of the particle inside its cell
+};
+
+struct StepConsts {
+  float gdt[3];      // gravity * dt
+  float pscale;      // dt / (rho dx): pressure-difference to velocity (Eq. 5)
+  float flip_ratio;
+  int advect_grid;   // 1: advect with the grid velocity
+  float dt;
+};
+
+constexpr int PCG_SLOTS = 7;
+
+struct PcgArgs {
+  Grid g;
+  float diag_tab[8];   // dt/(rho dx^2) * count
+  float minv_tab[8];   // 1 / diag
+  float s;             // dt/(rho dx^2)
+  double s64;
+  const uint8_t* type;
+  const unsigned int* active;
+  const unsigned int* n_active;
+  const float* b32;     // FP32 mode right-hand side
+  const double* b64;    // mixed mode right-hand side
+  float* x32;           // FP32 mode solution / mixed inner correction
+  double* x64;          // mixed mode solution
+  float2* pff;          // mixed mode: solution as a float pair (hi, lo) for G2P
+  float* r;
+  float* pa;
+  float* pb;
+  float* q;
+  double* partials;     // [PCG_SLOTS * max_blocks]: one slot per reduced value
+                        // of each phase, so no slot is rewritten before all
+                        // CTAs have read it
+  unsigned int* bar;    // [2] grid barrier
+  int* status;          // DevStats::status
+  DevStats* stats;
+  double tol;           // FP32 stop / mixed inner stop
+  double ir_tol;
+  int max_iter;
+  int ir_max_iter;
+  int check_singular;   // compare n_fluid with the cell count
+  unsigned long long timeout_ns;
+};
+
+// Projected velocity on face node (a,b,c) of component D (Eq. 5 with gravity
+// and the wall condition): 0 on the domain planes, otherwise
+//   u_new = u_old + g_D dt - dt/(rho dx) (p(+) - p(-))
+// with p = 0 in air cells.  The pressure difference is taken in FP32 from the
+// FP32 pressure, or from the float-pair pressure of mixed mode as
+// (hi+ - hi-) + (lo+ - lo-).  G2P and the read-back of U_NEW share this
+// function, so both give the same bits.
+template <int D, bool PAIR>
+__device__ __forceinline__ float face_unew(const Grid& g, const StepConsts& k, float uo, int a,
+                                           int b, int c, const float* p32, const float2* pff) {
+  const int nd = (D == 0) ? a : (D == 1) ? b : c;
+  const int nmax = (D == 0) ? g.nx : (D == 1) ? g.ny : g.nz;
+  if (nd == 0 || nd == nmax) return 0.0f;
+  const int cp = a + g.nx * (b + g.ny * c);
+  const int cm = cp - ((D == 0) ? 1 : (D == 1) ? g.nx : g.nx * g.ny);
+  float dp;
+  if constexpr (PAIR) {
+    const float2 hp = pff[cp], hm = pff[cm];
+    dp = __fadd_rn(__fsub_rn(hp.x, hm.x), __fsub_rn(hp.y, hm.y));
+  } else {
+    dp = __fsub_rn(p32[cp], p32[cm]);
+  }
+  return __fsub_rn(__fadd_rn(uo, k.gdt[D]), __fmul_rn(k.pscale, dp));
+}
+
+// k_bin.cu
+void launch_rebin(const Grid& g, const PartView& p, const BinView& b, long long np,
+                  cudaStream_t s);
+void launch_bin(const Grid& g, const BinView& b, uint8_t* type, DevStats* st, cudaStream_t s);
+void launch_scatter(const PartView& src, const PartView& dst, const BinView& b, long long np,
+                    cudaStream_t s);
+void launch_iota(int* id, long long np, cudaStream_t s);
+
+// k_p2g.cu
+void launch_p2g(const Grid& g, const PartView& p, const BinView& b, float2* const acc[3],
+                const DevStats* st, int nblocks, cudaStream_t s);
+void launch_finalize(const Grid& g, float2* const acc[3], float* const uo[3], cudaStream_t s);
+void launch_divergence(const Grid& g, const StepConsts& k, const uint8_t* type,
+                       const float* const uo[3], float* b32, double* b64, float* x32,
+                       double* x64, float2* pff, unsigned int* bar, DevStats* st,
+                       cudaStream_t s);
+void launch_u_new(const Grid& g, const StepConsts& k, int d, const float* uo, const float* p32,
+                  const float2* pff, float* out, cudaStream_t s);
+void launch_div_norms(const Grid& g, const StepConsts& k, const uint8_t* type,
+                      const float* const uo[3], const float* p32, const double* p64,
+                      double* out2, cudaStream_t s);
+void launch_f64_to_f32(const double* src, float* dst, long long n, cudaStream_t s);
+void launch_f32_to_f64(const float* src, double* dst, long long n, cudaStream_t s);
+
+// k_pcg.cu
+int pcg_block_size();
+cudaError_t pcg_max_blocks(int* max_blocks, int* sm_count);
+cudaError_t launch_pcg(const PcgArgs& a, bool mixed, int nblocks, cudaStream_t s);
+void launch_mark_bricks(const Grid& g, const uint8_t* type, unsigned int* brick_fluid,
+                        cudaStream_t s);
+void launch_compact_bricks(const Grid& g, const unsigned int* brick_fluid,
+                           unsigned int* active, DevStats* st, cudaStream_t s);
+void launch_zero_off_fluid(const Grid& g, const uint8_t* type, float* p, unsigned int* bar,
+                           cudaStream_t s);
+
+// k_g2p.cu
+void launch_g2p(const Grid& g, const StepConsts& k, const PartView& p, const BinView& b,
+                const float* const uo[3], const float* p32, const float2* pff, DevStats* st,
+                long long np, cudaStream_t s);
+
+}  // namespace flipk

@@ -1,0 +1,326 @@
+// k_p2g.cu — particle-to-grid transfer (Sec. 3.1.6, Eq. 4), forces and walls,
+// divergence (Eq. 6), and read-back / diagnostic kernels of the grid fields.
+//
+// P2G computes, for every face node of each component,
+//     u_node = sum_P u_P k(x_P - x_node) / sum_P k(x_P - x_node)     (0 if no P)
+// The paper gathers per grid point; here the sum is split by particle bricks.
+// One CTA takes one active 8x8x8 brick (its particles are one contiguous range
+// after binning).  A thread owns a cell: it sums the weighted velocities and
+// weights of that cell's particles into registers over the 2x3x3 face nodes
+// they can reach, then adds them to a shared-memory tile of the brick plus its
+// halo (9x10x10 nodes per component), and the CTA adds the tile to the global
+// (num, den) accumulators with vector float2 atomics.  The normalisation
+// num/den happens in k_finalize, which also clears the accumulators.
+#include "flip_kernels.cuh"
+
+namespace flipk {
+
+constexpr int P2G_THREADS = 256;
+
+template <int D>
+struct Tile {
+  static constexpr int X = (D == 0) ? 9 : 10;
+  static constexpr int Y = (D == 1) ? 9 : 10;
+  static constexpr int Z = (D == 2) ? 9 : 10;
+  static constexpr int N = X * Y * Z;
+};
+constexpr int TILE_PAD = 904;
+
+// Weights of one axis over the node window of a cell: the component's own axis
+// has 2 nodes (c, c+1); the other axes 3 nodes (c-1, c, c+1).
+template <int NN>
+__device__ __forceinline__ void expand(const AxisW& a, float (&w)[NN]) {
+  if constexpr (NN == 2) {
+    w[0] = a.w0;
+    w[1] = a.w1;
+  } else {
+    const bool lo = (a.off == 0);
+    w[0] = lo ? a.w0 : 0.0f;
+    w[1] = lo ? a.w1 : a.w0;
+    w[2] = lo ? 0.0f : a.w1;
+  }
+}
+
+template <int D>
+__device__ __forceinline__ void p2g_cell(const Grid& g, const PartView& P, unsigned int beg,
+                                         unsigned int end, int ci, int cj, int ck, int li,
+                                         int lj, int lk, float* tnum, float* tden) {
+  constexpr int NX = (D == 0) ? 2 : 3, NY = (D == 1) ? 2 : 3, NZ = (D == 2) ? 2 : 3;
+  constexpr int TX = Tile<D>::X, TY = Tile<D>::Y;
+  float an[NZ][NY][NX], ad[NZ][NY][NX];
+#pragma unroll
+  for (int z = 0; z < NZ; ++z)
+#pragma unroll
+    for (int y = 0; y < NY; ++y)
+#pragma unroll
+      for (int x = 0; x < NX; ++x) an[z][y][x] = ad[z][y][x] = 0.0f;
+  const float* vel = (D == 0) ? P.u : (D == 1) ? P.v : P.w;
+  for (unsigned int q = beg; q < end; ++q) {
+    const float px = P.x[q], py = P.y[q], pz = P.z[q], pv = vel[q];
+    float wx[NX], wy[NY], wz[NZ];
+    expand<NX>(axis_weights<D, 0>(px, g.inv_dx, ci, g.nx), wx);
+    expand<NY>(axis_weights<D, 1>(py, g.inv_dx, cj, g.ny), wy);
+    expand<NZ>(axis_weights<D, 2>(pz, g.inv_dx, ck, g.nz), wz);
+#pragma unroll
+    for (int z = 0; z < NZ; ++z)
+#pragma unroll
+      for (int y = 0; y < NY; ++y) {
+        const float wyz = __fmul_rn(wy[y], wz[z]);
+#pragma unroll
+        for (int x = 0; x < NX; ++x) {
+          const float w = __fmul_rn(wx[x], wyz);
+          an[z][y][x] = __fmaf_rn(w, pv, an[z][y][x]);
+          ad[z][y][x] = __fadd_rn(ad[z][y][x], w);
+        }
+      }
+  }
+#pragma unroll
+  for (int z = 0; z < NZ; ++z)
+#pragma unroll
+    for (int y = 0; y < NY; ++y)
+#pragma unroll
+      for (int x = 0; x < NX; ++x)
+        if (ad[z][y][x] != 0.0f) {
+          const int t = (li + x) + TX * ((lj + y) + TY * (lk + z));
+          atomicAdd(tnum + t, an[z][y][x]);
+          atomicAdd(tden + t, ad[z][y][x]);
+        }
+}
+
+template <int D>
+__device__ __forceinline__ void flush_tile(const Grid& g, int b0, int b1, int b2,
+                                           const float* tnum, const float* tden, float2* acc) {
+  constexpr int TX = Tile<D>::X, TY = Tile<D>::Y, N = Tile<D>::N;
+  const int o0 = (D == 0) ? b0 : b0 - 1, o1 = (D == 1) ? b1 : b1 - 1, o2 = (D == 2) ? b2 : b2 - 1;
+  const int FX = g.nx + (D == 0), FY = g.ny + (D == 1), FZ = g.nz + (D == 2);
+  for (int t = threadIdx.x; t < N; t += P2G_THREADS) {
+    const float dn = tden[t];
+    if (dn == 0.0f) continue;
+    const int a = o0 + t % TX, b = o1 + (t / TX) % TY, c = o2 + t / (TX * TY);
+    if (a < 0 || b < 0 || c < 0 || a >= FX || b >= FY || c >= FZ) continue;
+    atomicAdd(acc + (a + FX * (b + FY * c)), make_float2(tnum[t], dn));
+  }
+}
+
+__global__ void __launch_bounds__(P2G_THREADS) k_p2g(const Grid g, const PartView P,
+                                                     const BinView B, float2* acc0, float2* acc1,
+                                                     float2* acc2, const DevStats* st) {
+  __shared__ float tnum[3][TILE_PAD];
+  __shared__ float tden[3][TILE_PAD];
+  const unsigned int nact = st->n_active;
+  for (unsigned int bi = blockIdx.x; bi < nact; bi += gridDim.x) {
+    const unsigned int brick = B.active[bi];
+    const int b0 = (int)(brick % (unsigned)g.bx) * BRICK;
+    const int b1 = (int)((brick / (unsigned)g.bx) % (unsigned)g.by) * BRICK;
+    const int b2 = (int)(brick / ((unsigned)g.bx * (unsigned)g.by)) * BRICK;
+    for (int t = threadIdx.x; t < 3 * TILE_PAD; t += P2G_THREADS) {
+      (&tnum[0][0])[t] = 0.0f;
+      (&tden[0][0])[t] = 0.0f;
+    }
+    __syncthreads();
+    const unsigned int bstart = B.brick_start[brick], bend = B.brick_start[brick + 1];
+    for (int l = threadIdx.x; l < BRICK_CELLS; l += P2G_THREADS) {
+      const unsigned int key = brick * BRICK_CELLS + (unsigned)l;
+      const unsigned int beg = bstart + B.local_start[key];
+      const unsigned int end = (l < BRICK_CELLS - 1) ? bstart + B.local_start[key + 1] : bend;
+      if (beg == end) continue;
+      const int li = l & 7, lj = (l >> 3) & 7, lk = l >> 6;
+      const int ci = b0 + li, cj = b1 + lj, ck = b2 + lk;
+      p2g_cell<0>(g, P, beg, end, ci, cj, ck, li, lj, lk, tnum[0], tden[0]);
+      p2g_cell<1>(g, P, beg, end, ci, cj, ck, li, lj, lk, tnum[1], tden[1]);
+      p2g_cell<2>(g, P, beg, end, ci, cj, ck, li, lj, lk, tnum[2], tden[2]);
+    }
+    __syncthreads();
+    flush_tile<0>(g, b0, b1, b2, tnum[0], tden[0], acc0);
+    flush_tile<1>(g, b0, b1, b2, tnum[1], tden[1], acc1);
+    flush_tile<2>(g, b0, b1, b2, tnum[2], tden[2], acc2);
+    __syncthreads();
+  }
+}
+
+// u_old = num / den (0 where no particle reached the node); clears the
+// accumulators for the next step.
+__global__ void k_finalize(const Grid g, float2* acc0, float2* acc1, float2* acc2, float* uo0,
+                           float* uo1, float* uo2) {
+  const long long n0 = n_faces(g, 0), n1 = n_faces(g, 1), n2 = n_faces(g, 2);
+  const long long tot = n0 + n1 + n2;
+  for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < tot;
+       f += (long long)gridDim.x * blockDim.x) {
+    float2* acc;
+    float* uo;
+    long long idx;
+    if (f < n0) { acc = acc0; uo = uo0; idx = f; }
+    else if (f < n0 + n1) { acc = acc1; uo = uo1; idx = f - n0; }
+    else { acc = acc2; uo = uo2; idx = f - n0 - n1; }
+    const float2 v = acc[idx];
+    uo[idx] = (v.y != 0.0f) ? __fdiv_rn(v.x, v.y) : 0.0f;
+    acc[idx] = make_float2(0.0f, 0.0f);
+  }
+}
+
+// Gravity + walls give u* on the fly; b = -div u* (Eq. 6) in fluid cells.
+// Also starts the solve from p = 0 (every cell, so air cells hold p = 0) and
+// resets the grid barrier and the per-step max-speed word.
+__global__ void k_divergence(const Grid g, const StepConsts K, const uint8_t* __restrict__ type,
+                             const float* __restrict__ uo0, const float* __restrict__ uo1,
+                             const float* __restrict__ uo2, float* b32, double* b64, float* x32,
+                             double* x64, float2* pff, unsigned int* bar, DevStats* st) {
+  const long long nc = (long long)g.nx * g.ny * g.nz;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    bar[0] = 0u;
+    st->max_speed_bits = 0u;
+  }
+  for (long long cl = blockIdx.x * (long long)blockDim.x + threadIdx.x; cl < nc;
+       cl += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)cl;
+    const int i = c % g.nx, j = (c / g.nx) % g.ny, k = c / (g.nx * g.ny);
+    if (x32) x32[c] = 0.0f;
+    if (x64) x64[c] = 0.0;
+    if (pff) pff[c] = make_float2(0.0f, 0.0f);
+    const bool fluid = (type[c] == 1);
+    const int fu = i + (g.nx + 1) * (j + g.ny * k);
+    const int fv = i + g.nx * (j + (g.ny + 1) * k);
+    const int fw = c;
+    const float uL = (i == 0) ? 0.0f : __fadd_rn(uo0[fu], K.gdt[0]);
+    const float uR = (i + 1 == g.nx) ? 0.0f : __fadd_rn(uo0[fu + 1], K.gdt[0]);
+    const float vB = (j == 0) ? 0.0f : __fadd_rn(uo1[fv], K.gdt[1]);
+    const float vT = (j + 1 == g.ny) ? 0.0f : __fadd_rn(uo1[fv + g.nx], K.gdt[1]);
+    const float wK = (k == 0) ? 0.0f : __fadd_rn(uo2[fw], K.gdt[2]);
+    const float wF = (k + 1 == g.nz) ? 0.0f : __fadd_rn(uo2[fw + g.nx * g.ny], K.gdt[2]);
+    if (b32) {
+      const float d = __fadd_rn(__fadd_rn(__fsub_rn(uR, uL), __fsub_rn(vT, vB)), __fsub_rn(wF, wK));
+      b32[c] = fluid ? -__fmul_rn(d, g.inv_dx) : 0.0f;
+    }
+    if (b64) {
+      const double d = ((double)uR - (double)uL) + ((double)vT - (double)vB) + ((double)wF - (double)wK);
+      b64[c] = fluid ? -d * (double)g.inv_dx : 0.0;
+    }
+  }
+}
+
+template <int D, bool PAIR>
+__global__ void k_u_new(const Grid g, const StepConsts K, const float* __restrict__ uo,
+                        const float* __restrict__ p32, const float2* __restrict__ pff,
+                        float* __restrict__ out) {
+  const int FX = g.nx + (D == 0), FY = g.ny + (D == 1);
+  const long long nf = n_faces(g, D);
+  for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nf;
+       f += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)(f % FX), b = (int)((f / FX) % FY), c = (int)(f / ((long long)FX * FY));
+    out[f] = face_unew<D, PAIR>(g, K, uo[f], a, b, c, p32, pff);
+  }
+}
+
+// ||div u*||^2 and ||div u_new||^2 over fluid cells in FP64, u_new from the
+// stored pressure (FP32 or FP64) by Eq. 5 evaluated in FP64.
+__global__ void k_div_norms(const Grid g, const StepConsts K, const uint8_t* __restrict__ type,
+                            const float* __restrict__ uo0, const float* __restrict__ uo1,
+                            const float* __restrict__ uo2, const float* __restrict__ p32,
+                            const double* __restrict__ p64, double* out2) {
+  const long long nc = (long long)g.nx * g.ny * g.nz;
+  const double ps = (double)K.pscale;
+  double s_star = 0.0, s_new = 0.0;
+  for (long long cl = blockIdx.x * (long long)blockDim.x + threadIdx.x; cl < nc;
+       cl += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)cl;
+    if (type[c] != 1) continue;
+    const int i = c % g.nx, j = (c / g.nx) % g.ny, k = c / (g.nx * g.ny);
+    const int sxy = g.nx * g.ny;
+    auto P = [&](int cc) -> double { return p64 ? p64[cc] : (double)p32[cc]; };
+    const int fu = i + (g.nx + 1) * (j + g.ny * k);
+    const int fv = i + g.nx * (j + (g.ny + 1) * k);
+    const int fw = c;
+    // star and projected values of the six faces (0 on walls)
+    double us[6], un[6];
+    const bool wall[6] = {i == 0, i + 1 == g.nx, j == 0, j + 1 == g.ny, k == 0, k + 1 == g.nz};
+    const float uov[6] = {uo0[fu], uo0[fu + 1], uo1[fv], uo1[fv + g.nx], uo2[fw], uo2[fw + sxy]};
+    const int dm[6] = {c - 1, c, c - g.nx, c, c - sxy, c};
+    const int dp[6] = {c, c + 1, c, c + g.nx, c, c + sxy};
+    for (int f = 0; f < 6; ++f) {
+      if (wall[f]) { us[f] = un[f] = 0.0; continue; }
+      us[f] = (double)__fadd_rn(uov[f], K.gdt[f >> 1]);
+      un[f] = us[f] - ps * (P(dp[f]) - P(dm[f]));
+    }
+    const double d0 = ((us[1] - us[0]) + (us[3] - us[2]) + (us[5] - us[4])) * (double)g.inv_dx;
+    const double d1 = ((un[1] - un[0]) + (un[3] - un[2]) + (un[5] - un[4])) * (double)g.inv_dx;
+    s_star += d0 * d0;
+    s_new += d1 * d1;
+  }
+  s_star = warp_sum(s_star);
+  s_new = warp_sum(s_new);
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(out2, s_star);
+    atomicAdd(out2 + 1, s_new);
+  }
+}
+
+__global__ void k_f64_to_f32(const double* s, float* d, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    d[i] = (float)s[i];
+}
+
+__global__ void k_f32_to_f64(const float* s, double* d, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    d[i] = (double)s[i];
+}
+
+static unsigned int grid_for(long long n, int threads, int cap = 1 << 16) {
+  long long b = (n + threads - 1) / threads;
+  if (b > cap) b = cap;
+  return (unsigned int)(b < 1 ? 1 : b);
+}
+
+void launch_p2g(const Grid& g, const PartView& p, const BinView& b, float2* const acc[3],
+                const DevStats* st, int nblocks, cudaStream_t s) {
+  k_p2g<<<nblocks, P2G_THREADS, 0, s>>>(g, p, b, acc[0], acc[1], acc[2], st);
+}
+
+void launch_finalize(const Grid& g, float2* const acc[3], float* const uo[3], cudaStream_t s) {
+  const long long tot = n_faces(g, 0) + n_faces(g, 1) + n_faces(g, 2);
+  k_finalize<<<grid_for(tot, 256), 256, 0, s>>>(g, acc[0], acc[1], acc[2], uo[0], uo[1], uo[2]);
+}
+
+void launch_divergence(const Grid& g, const StepConsts& k, const uint8_t* type,
+                       const float* const uo[3], float* b32, double* b64, float* x32,
+                       double* x64, float2* pff, unsigned int* bar, DevStats* st,
+                       cudaStream_t s) {
+  const long long nc = (long long)g.nx * g.ny * g.nz;
+  k_divergence<<<grid_for(nc, 256), 256, 0, s>>>(g, k, type, uo[0], uo[1], uo[2], b32, b64, x32,
+                                                 x64, pff, bar, st);
+}
+
+void launch_u_new(const Grid& g, const StepConsts& k, int d, const float* uo, const float* p32,
+                  const float2* pff, float* out, cudaStream_t s) {
+  const bool pair = (pff != nullptr);
+  const unsigned int gb = grid_for(n_faces(g, d), 256);
+  if (d == 0) {
+    if (pair) k_u_new<0, true><<<gb, 256, 0, s>>>(g, k, uo, p32, pff, out);
+    else k_u_new<0, false><<<gb, 256, 0, s>>>(g, k, uo, p32, pff, out);
+  } else if (d == 1) {
+    if (pair) k_u_new<1, true><<<gb, 256, 0, s>>>(g, k, uo, p32, pff, out);
+    else k_u_new<1, false><<<gb, 256, 0, s>>>(g, k, uo, p32, pff, out);
+  } else {
+    if (pair) k_u_new<2, true><<<gb, 256, 0, s>>>(g, k, uo, p32, pff, out);
+    else k_u_new<2, false><<<gb, 256, 0, s>>>(g, k, uo, p32, pff, out);
+  }
+}
+
+void launch_div_norms(const Grid& g, const StepConsts& k, const uint8_t* type,
+                      const float* const uo[3], const float* p32, const double* p64,
+                      double* out2, cudaStream_t s) {
+  const long long nc = (long long)g.nx * g.ny * g.nz;
+  k_div_norms<<<grid_for(nc, 256, 4096), 256, 0, s>>>(g, k, type, uo[0], uo[1], uo[2], p32, p64,
+                                                      out2);
+}
+
+void launch_f64_to_f32(const double* src, float* dst, long long n, cudaStream_t s) {
+  k_f64_to_f32<<<grid_for(n, 256), 256, 0, s>>>(src, dst, n);
+}
+
+void launch_f32_to_f64(const float* src, double* dst, long long n, cudaStream_t s) {
+  k_f32_to_f64<<<grid_for(n, 256), 256, 0, s>>>(src, dst, n);
+}
+
+}  // namespace flipk

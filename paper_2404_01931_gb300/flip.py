@@ -1,0 +1,328 @@
+"""Thin ctypes binding of the C ABI in include/flip.h (libflip_gb300.so).
+
+The functions keep the C names (flip_create, flip_step, flip_read, ...) and only
+marshal arguments: numpy arrays are host buffers, torch tensors on a CUDA
+device are device buffers.  Every step of the FLIP pipeline runs in the
+library's CUDA kernels; there is no Python or CPU fallback.  If the shared
+library has not been built, importing works but the first call raises.
+
+PyTorch supplies device memory (its caching allocator, through the library's
+allocator hook) and streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import warnings
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libflip_gb300.so")
+
+FLIP_OK = 0
+FLIP_E_ARG = 1
+FLIP_E_OOM = 2
+FLIP_E_CUDA = 3
+FLIP_E_NOT_CONVERGED = 4
+FLIP_E_TIMEOUT = 5
+FLIP_E_SIZE = 6
+FLIP_E_NOGPU = 7
+
+FLIP_PREC_FP32 = 0
+FLIP_PREC_MIXED_IR = 1
+FLIP_ADVECT_PARTICLE = 0
+FLIP_ADVECT_GRID = 1
+
+(PX, PY, PZ, PU, PV, PW, PID, U_OLD, V_OLD, W_OLD, U_NEW, V_NEW, W_NEW, PRESSURE,
+ PRESSURE_F64, RHS, CELL_TYPE) = range(17)
+FIELD_DTYPE = {PX: np.float32, PY: np.float32, PZ: np.float32, PU: np.float32, PV: np.float32,
+               PW: np.float32, PID: np.int32, U_OLD: np.float32, V_OLD: np.float32,
+               W_OLD: np.float32, U_NEW: np.float32, V_NEW: np.float32, W_NEW: np.float32,
+               PRESSURE: np.float32, PRESSURE_F64: np.float64, RHS: np.float32,
+               CELL_TYPE: np.uint8}
+
+
+class FlipError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__(f"[{code}] {message}")
+        self.code = code
+
+
+class FlipParams(C.Structure):
+    _fields_ = [("n", C.c_int32 * 3), ("dx", C.c_double), ("dt", C.c_double),
+                ("gravity", C.c_double * 3), ("rho", C.c_double), ("flip_ratio", C.c_double),
+                ("skin", C.c_double), ("cg_tol", C.c_double), ("ir_tol", C.c_double),
+                ("cg_max_iter", C.c_int32), ("ir_max_iter", C.c_int32),
+                ("precision", C.c_int32), ("advect_source", C.c_int32)]
+
+
+class FlipStats(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("n_particles", C.c_int64), ("n_fluid_cells", C.c_int64),
+                ("n_active_bricks", C.c_int64), ("cg_iterations", C.c_int64),
+                ("ir_iterations", C.c_int32), ("kernel_launches", C.c_int32),
+                ("cg_rel_residual", C.c_double), ("rel_divergence", C.c_double),
+                ("max_speed", C.c_double), ("ms_bin", C.c_double), ("ms_p2g", C.c_double),
+                ("ms_divergence", C.c_double), ("ms_pcg", C.c_double), ("ms_g2p", C.c_double),
+                ("ms_total", C.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
+
+
+class FlipAlloc(C.Structure):
+    _fields_ = [("ctx", C.c_void_p), ("alloc", _ALLOC_FN), ("free", _FREE_FN)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libflip_gb300.so is not built ({LIB_PATH}); run "
+                               "__graft_entry__.build() or paper_2404_01931_gb300/build_lib.py")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_size_t
+        PP = C.POINTER(FlipParams)
+        L.flip_abi_version.restype = C.c_int
+        L.flip_default_params.argtypes = [PP, i32, i32, i32]
+        L.flip_default_params.restype = None
+        L.flip_create.argtypes = [PP, vp, vp, vp, vp, vp, vp, i64, i32, C.POINTER(FlipAlloc), vp,
+                                  C.POINTER(vp)]
+        L.flip_step.argtypes = [vp, i32, C.POINTER(FlipStats)]
+        L.flip_sync.argtypes = [vp]
+        L.flip_read.argtypes = [vp, C.c_int, vp, sz, i32]
+        L.flip_write.argtypes = [vp, C.c_int, vp, sz, i32]
+        L.flip_read_particles.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, i32]
+        L.flip_write_particles.argtypes = [vp, vp, vp, vp, vp, vp, vp, i32]
+        L.flip_field_bytes.argtypes = [vp, C.c_int]
+        L.flip_field_bytes.restype = sz
+        L.flip_destroy.argtypes = [vp]
+        L.flip_destroy.restype = None
+        L.flip_strerror.argtypes = [C.c_int]
+        L.flip_strerror.restype = C.c_char_p
+        L.flip_last_error.restype = C.c_char_p
+        L.flip_solve_pressure.argtypes = [PP, vp, vp, vp, vp, C.POINTER(i32),
+                                          C.POINTER(C.c_double)]
+        if L.flip_abi_version() != 1:
+            raise RuntimeError("libflip_gb300 ABI version mismatch")
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().flip_last_error().decode()
+
+
+def _check(rc: int, allow=(FLIP_OK,)) -> int:
+    if rc in allow:
+        return rc
+    if rc == FLIP_E_NOT_CONVERGED:
+        warnings.warn(f"flip: {last_error()}", RuntimeWarning, stacklevel=3)
+        return rc
+    raise FlipError(rc, f"{lib().flip_strerror(rc).decode()}: {last_error()}")
+
+
+def _buf(a, dtype):
+    """(pointer, nbytes, is_device, keepalive) of a numpy array or torch tensor."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != dtype or not a.flags.c_contiguous:
+            raise TypeError(f"expected a C-contiguous {np.dtype(dtype).name} array")
+        return a.ctypes.data, a.nbytes, 0, a
+    import torch
+    if isinstance(a, torch.Tensor):
+        want = {np.float32: torch.float32, np.float64: torch.float64, np.int32: torch.int32,
+                np.uint8: torch.uint8}[np.dtype(dtype).type]
+        if a.dtype != want or not a.is_contiguous():
+            raise TypeError(f"expected a contiguous {want} tensor")
+        return a.data_ptr(), a.numel() * a.element_size(), int(a.is_cuda), a
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def default_params(nx: int, ny: int | None = None, nz: int | None = None, **overrides) -> FlipParams:
+    p = FlipParams()
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    lib().flip_default_params(C.byref(p), nx, ny, nz)
+    for k, v in overrides.items():
+        if k in ("n", "gravity"):
+            for i in range(3):
+                getattr(p, k)[i] = v[i]
+        else:
+            setattr(p, k, v)
+    return p
+
+
+class _TorchAllocator:
+    """Allocator hook backed by PyTorch's CUDA caching allocator."""
+
+    def __init__(self, device: int):
+        import torch
+        self.device = device
+        self._torch = torch
+
+        def _alloc(ctx, nbytes, stream):
+            try:
+                return self._torch.cuda.caching_allocator_alloc(int(nbytes), self.device,
+                                                                int(stream or 0))
+            except Exception:  # out of memory: the library reports FLIP_E_OOM
+                return None
+
+        def _free(ctx, ptr, nbytes, stream):
+            try:
+                self._torch.cuda.caching_allocator_delete(int(ptr))
+            except Exception:
+                pass
+
+        self._fa = _ALLOC_FN(_alloc)
+        self._ff = _FREE_FN(_free)
+        self.struct = FlipAlloc(None, self._fa, self._ff)
+
+
+def flip_create(params: FlipParams, x, y, z, u, v, w, stream=None, allocator="torch"):
+    """Returns (handle, keepalive) for a new scene; see flip_create in include/flip.h."""
+    bufs = [_buf(a, np.float32) for a in (x, y, z, u, v, w)]
+    np_ = bufs[0][1] // 4
+    if any(b[1] != bufs[0][1] for b in bufs) or len({b[2] for b in bufs}) != 1:
+        raise ValueError("particle arrays must have one length and live on one side")
+    keep = [b[3] for b in bufs]
+    alloc_ptr = None
+    if allocator == "torch":
+        import torch
+        if torch.cuda.is_available():
+            ta = _TorchAllocator(torch.cuda.current_device())
+            keep.append(ta)
+            alloc_ptr = C.byref(ta.struct)
+    elif allocator is not None:
+        raise ValueError("allocator must be 'torch' or None")
+    h = C.c_void_p()
+    rc = lib().flip_create(C.byref(params), *[C.c_void_p(b[0]) for b in bufs], np_, bufs[0][2],
+                           alloc_ptr, C.c_void_p(stream or 0), C.byref(h))
+    _check(rc)
+    return h, keep
+
+
+def flip_step(h, nsteps: int = 1, stats: bool = False):
+    """Advances nsteps; returns (status, FlipStats or None)."""
+    st = FlipStats() if stats else None
+    rc = lib().flip_step(h, int(nsteps), C.byref(st) if stats else None)
+    return _check(rc), st
+
+
+def flip_sync(h) -> int:
+    return _check(lib().flip_sync(h))
+
+
+def flip_field_bytes(h, field: int) -> int:
+    return int(lib().flip_field_bytes(h, field))
+
+
+def flip_read(h, field: int, out=None):
+    """Reads a field into out (numpy or torch); allocates a numpy array if out is None."""
+    dtype = FIELD_DTYPE[field]
+    if out is None:
+        out = np.empty(flip_field_bytes(h, field) // np.dtype(dtype).itemsize, dtype)
+    ptr, nbytes, dev, _ = _buf(out, dtype)
+    _check(lib().flip_read(h, field, C.c_void_p(ptr), nbytes, dev))
+    return out
+
+
+def flip_write(h, field: int, src):
+    ptr, nbytes, dev, _ = _buf(src, FIELD_DTYPE[field])
+    _check(lib().flip_write(h, field, C.c_void_p(ptr), nbytes, dev))
+
+
+def flip_read_particles(h, x, y, z, u, v, w, ids=None):
+    """Reads the six particle arrays (and ids) into caller buffers (numpy or torch)."""
+    bufs = [_buf(a, np.float32) for a in (x, y, z, u, v, w)]
+    idb = _buf(ids, np.int32) if ids is not None else None
+    dev = bufs[0][2]
+    _check(lib().flip_read_particles(h, *[C.c_void_p(b[0]) for b in bufs],
+                                     C.c_void_p(idb[0]) if idb else None, dev))
+
+
+def flip_write_particles(h, x, y, z, u, v, w):
+    bufs = [_buf(a, np.float32) for a in (x, y, z, u, v, w)]
+    _check(lib().flip_write_particles(h, *[C.c_void_p(b[0]) for b in bufs], bufs[0][2]))
+
+
+def flip_destroy(h):
+    if h:
+        lib().flip_destroy(h)
+
+
+def flip_solve_pressure(params: FlipParams, type_, b, p, stream=None):
+    """A p = b on device tensors (uint8 types, float32 b and p); returns (status, iters, rel)."""
+    tp, _, tdev, _ = _buf(type_, np.uint8)
+    bp, _, bdev, _ = _buf(b, np.float32)
+    pp, _, pdev, _ = _buf(p, np.float32)
+    if not (tdev and bdev and pdev):
+        raise ValueError("flip_solve_pressure takes device buffers")
+    it = C.c_int32(0)
+    rel = C.c_double(0.0)
+    rc = lib().flip_solve_pressure(C.byref(params), C.c_void_p(tp), C.c_void_p(bp),
+                                   C.c_void_p(pp), C.c_void_p(stream or 0), C.byref(it),
+                                   C.byref(rel))
+    return _check(rc), it.value, rel.value
+
+
+class Simulation:
+    """One scene on the GPU: owns the handle and (by default) a torch CUDA stream."""
+
+    def __init__(self, params: FlipParams, x, y, z, u, v, w, stream=None, allocator="torch"):
+        import torch
+        self._stream_obj = None
+        if stream is None and torch.cuda.is_available():
+            self._stream_obj = torch.cuda.Stream()
+            stream = self._stream_obj.cuda_stream
+        self.stream = stream
+        self.params = params
+        self.h, self._keep = flip_create(params, x, y, z, u, v, w, stream=stream,
+                                         allocator=allocator)
+
+    def step(self, nsteps: int = 1, stats: bool = False):
+        return flip_step(self.h, nsteps, stats)
+
+    def sync(self) -> int:
+        return flip_sync(self.h)
+
+    def read(self, field: int, out=None):
+        return flip_read(self.h, field, out)
+
+    def write(self, field: int, src):
+        flip_write(self.h, field, src)
+
+    def particles(self, by_id: bool = True):
+        """(x, y, z, u, v, w) as float32 numpy arrays, in creation order when by_id."""
+        arrs = [self.read(f) for f in (PX, PY, PZ, PU, PV, PW)]
+        if by_id:
+            ids = self.read(PID)
+            inv = np.empty_like(ids)
+            inv[ids] = np.arange(ids.size, dtype=ids.dtype)
+            arrs = [a[inv] for a in arrs]
+        return arrs
+
+    def close(self):
+        if getattr(self, "h", None):
+            flip_destroy(self.h)
+            self.h = None
+            self._keep = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

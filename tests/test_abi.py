@@ -1,0 +1,98 @@
+"""The C-ABI library builds, loads and exports every function include/flip.h declares;
+host-side argument checks work without a GPU (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def F():
+    from paper_2404_01931_gb300 import build_lib
+    build_lib.build()
+    from paper_2404_01931_gb300 import flip
+    flip.lib()
+    return flip
+
+
+def declared_functions():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b(flip_\w+)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for fn in ("flip_create", "flip_step", "flip_read", "flip_write", "flip_destroy",
+               "flip_strerror", "flip_solve_pressure", "flip_sync"):
+        assert fn in names
+
+
+def test_every_declared_symbol_is_exported(F):
+    lib = ctypes.CDLL(F.LIB_PATH)
+    missing = [n for n in sorted(declared_functions()) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_abi_version_and_strerror(F):
+    L = F.lib()
+    assert L.flip_abi_version() == 1
+    for code in range(8):
+        assert L.flip_strerror(code).decode()
+    assert L.flip_strerror(99).decode() == "unknown status"
+
+
+def test_struct_layouts_match_header(F):
+    # flip_params: 3 int32 + 10 double + 4 int32, natural alignment
+    assert ctypes.sizeof(F.FlipParams) == 12 + 4 + 10 * 8 + 16
+    assert ctypes.sizeof(F.FlipStats) == 5 * 8 + 2 * 4 + 9 * 8
+
+
+def test_default_params(F):
+    p = F.default_params(64, 32, 48)
+    assert list(p.n) == [64, 32, 48] and p.dx == 1 / 64 and p.dt == 1 / 240
+    assert p.gravity[1] == -9.81 and p.flip_ratio == 0.95 and p.cg_max_iter == 20 * 64
+    assert p.skin == pytest.approx(1e-3 / 64)
+
+
+@pytest.mark.parametrize("field,value,code", [
+    ("dx", 0.3, 1), ("dt", 0.0, 1), ("flip_ratio", 1.5, 1), ("skin", 0.0, 1),
+    ("precision", 7, 1), ("cg_max_iter", 0, 1), ("rho", -1.0, 1)])
+def test_argument_checks_before_any_device_call(F, field, value, code):
+    p = F.default_params(16)
+    setattr(p, field, value)
+    x = np.zeros(4, np.float32)
+    with pytest.raises(F.FlipError) as ei:
+        F.flip_create(p, x, x, x, x, x, x, allocator=None)
+    assert ei.value.code == code
+
+
+def test_grid_size_checks(F):
+    p = F.default_params(16)
+    p.n[0] = 1
+    x = np.zeros(4, np.float32)
+    with pytest.raises(F.FlipError):
+        F.flip_create(p, x, x, x, x, x, x, allocator=None)
+
+
+def test_mismatched_particle_arrays(F):
+    p = F.default_params(16)
+    with pytest.raises(ValueError):
+        F.flip_create(p, *[np.zeros(4, np.float32)] * 5, np.zeros(5, np.float32),
+                      allocator=None)
+
+
+def test_wrong_dtype_rejected(F):
+    p = F.default_params(16)
+    with pytest.raises(TypeError):
+        F.flip_create(p, *[np.zeros(4, np.float64)] * 6, allocator=None)

@@ -1,0 +1,293 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (the spec bar, FP32 path vs FP64 oracle): grid velocities and
+pressure at relative L2 <= 1e-5 per step (velocity norms floored at g*dt*sqrt(n_faces)
+because a fluid at rest has |u| ~ 0), particle positions within 1e-4 of a cell after
+10 free-running steps.  Integer outputs (cell types, particle counts, ids) are exact.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2404_01931_gb300 import flip as F
+from paper_2404_01931_gb300 import scenes as S
+
+from parity_util import face_floor, gpu_step, matched, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # collected on CPU machines too; skipped there
+    pytestmark = [pytest.mark.gpu, pytest.mark.skip(reason="needs a CUDA GPU")]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _compare_fields(ref, got, n, tol=1e-5, ptol=1e-5, label=""):
+    fl = face_floor(n)
+    assert np.array_equal(got["type"].reshape(ref.type.shape), ref.type), label
+    for d in range(3):
+        e = rel_l2(got["u_old"][d], ref.u_old[d], fl)
+        assert e <= tol, f"{label} u_old[{d}] rel L2 {e:.3e}"
+    e = rel_l2(got["rhs"], ref.rhs)
+    assert e <= tol, f"{label} rhs rel L2 {e:.3e}"
+    e = rel_l2(got["p"], ref.pressure)
+    assert e <= ptol, f"{label} pressure rel L2 {e:.3e}"
+    for d in range(3):
+        e = rel_l2(got["u_new"][d], ref.u_new[d], fl)
+        assert e <= tol, f"{label} u_new[{d}] rel L2 {e:.3e}"
+
+
+def _compare_particles(ref, got, dx, pos_cells=1e-4, vel_tol=1e-5, vfloor=9.81 / 240):
+    x, y, z, u, v, w = got["particles"]
+    pos = np.stack([x, y, z]).astype(np.float64)
+    rpos = np.stack([ref.x, ref.y, ref.z])
+    err = np.abs(pos - rpos).max() / dx
+    assert err <= pos_cells, f"positions off by {err:.3e} cells"
+    vel = np.stack([u, v, w]).astype(np.float64)
+    rvel = np.stack([ref.u, ref.v, ref.w])
+    e = rel_l2(vel, rvel, vfloor * np.sqrt(vel.size))
+    assert e <= vel_tol, f"velocity rel L2 {e:.3e}"
+
+
+# ------------------------------------------------------------- single steps
+
+def test_dam_break_32_single_step():
+    sc = S.dam_break(32)
+    op, fp = matched(32)
+    ref = O.step(op, *sc.arrays())
+    got = gpu_step(fp, sc.arrays())
+    assert got["rc"] == F.FLIP_OK
+    assert got["stats"].n_fluid_cells == ref.n_fluid == 4096
+    _compare_fields(ref, got, 32, label="C1")
+    _compare_particles(ref, got, 1 / 32)
+
+
+def test_random_velocity_box_single_step():
+    sc = S.random_velocities(S.box(24, (0.1, 0.0, 0.2), (0.7, 0.55, 0.9), seed=11), 0.8, 3)
+    op, fp = matched(24)
+    ref = O.step(op, *sc.arrays())
+    got = gpu_step(fp, sc.arrays())
+    _compare_fields(ref, got, 24, label="random box")
+    _compare_particles(ref, got, 1 / 24)
+
+
+def test_ragged_grid_not_multiple_of_brick():
+    n = (20, 13, 17)
+    sc = S.random_velocities(S.box(n, (0.0, 0.0, 0.0), (0.55, 0.5, 0.8), seed=5), 0.5, 4)
+    op, fp = matched(n)
+    ref = O.step(op, *sc.arrays())
+    got = gpu_step(fp, sc.arrays())
+    _compare_fields(ref, got, n, label="ragged")
+    _compare_particles(ref, got, 1 / 20)
+
+
+def test_grid_advection_source():
+    sc = S.random_velocities(S.dam_break(16, 0.5, 0.5, seed=2), 0.5, 8)
+    op, fp = matched(16, advect_source=1)
+    ref = O.step(op, *sc.arrays())
+    got = gpu_step(fp, sc.arrays())
+    _compare_particles(ref, got, 1 / 16)
+
+
+@pytest.mark.parametrize("ratio", [0.0, 1.0])
+def test_pure_pic_and_pure_flip(ratio):
+    sc = S.random_velocities(S.dam_break(16, 0.5, 0.5, seed=1), 0.5, 9)
+    op, fp = matched(16, flip_ratio=ratio)
+    ref = O.step(op, *sc.arrays())
+    got = gpu_step(fp, sc.arrays())
+    _compare_particles(ref, got, 1 / 16)
+
+
+# ------------------------------------------------------------- multi-step
+
+def test_dam_break_32_per_step_parity_10_steps():
+    """Each step restarts from the oracle's float32-rounded state (single-step mode)."""
+    sc = S.dam_break(32)
+    op, fp = matched(32)
+    state = [a.astype(np.float32) for a in sc.arrays()]
+    for s in range(10):
+        ref = O.step(op, *state)
+        got = gpu_step(fp, state)
+        _compare_fields(ref, got, 32, label=f"step {s}")
+        state = [np.asarray(a, np.float32) for a in (ref.x, ref.y, ref.z, ref.u, ref.v, ref.w)]
+
+
+def test_dam_break_32_free_running_10_steps():
+    sc = S.dam_break(32)
+    op, fp = matched(32)
+    st = [a.astype(np.float64) for a in sc.arrays()]
+    for _ in range(10):
+        r = O.step(op, *st, fields=False)
+        st = [r.x, r.y, r.z, r.u, r.v, r.w]
+    got = gpu_step(fp, sc.arrays(), nsteps=10, fields=False)
+    x, y, z, _, _, _ = got["particles"]
+    err = np.abs(np.stack([x, y, z]) - np.stack(st[:3])).max() * 32
+    assert err <= 1e-4, f"positions after 10 steps off by {err:.3e} cells"
+
+
+# ------------------------------------------------------------- closed forms on the GPU
+
+def test_hydrostatic_column_gpu():
+    n = 32
+    sc = S.layer(n, 16, seed=4)
+    op, fp = matched(n, cg_tol=1e-7)
+    got = gpu_step(fp, sc.arrays(), nsteps=10)
+    g, dx, dt = 9.81, 1 / n, 1 / 240
+    jj = np.arange(n)
+    want = np.where(jj < 16, g * (16 - jj) * dx, 0.0)[None, :, None]
+    p = got["p"].reshape(n, n, n)
+    assert rel_l2(p, np.broadcast_to(want, p.shape)) <= 1e-5
+    x, y, z, u, v, w = got["particles"]
+    speed = np.sqrt(u.astype(np.float64) ** 2 + v ** 2 + w ** 2)
+    assert speed.max() <= 1e-4 * g * dt
+    x0 = np.clip(np.stack(sc.arrays()[:3]).astype(np.float64), 1e-3 * dx, 1 - 1e-3 * dx)
+    assert np.abs(np.stack([x, y, z]) - x0).max() <= 1e-5 * dx
+
+
+def test_ballistic_blob_gpu():
+    n = 16
+    v0 = np.array([0.3, 0.5, -0.2])
+    sc = S.box(n, (0.3, 0.4, 0.3), (0.6, 0.7, 0.55), seed=2, velocity=v0)
+    dt, g = 1 / 240, np.array([0.0, -9.81, 0.0])
+    op, fp = matched(n)
+    steps = 5
+    got = gpu_step(fp, sc.arrays(), nsteps=steps, fields=False)
+    x, y, z, u, v, w = got["particles"]
+    vel = np.stack([u, v, w], 1)
+    np.testing.assert_allclose(vel, np.broadcast_to(v0 + steps * g * dt, vel.shape), atol=2e-6)
+    x0 = np.stack(sc.arrays()[:3], 1).astype(np.float64)
+    want = x0 + steps * dt * v0 + g * dt * dt * steps * (steps + 1) / 2
+    np.testing.assert_allclose(np.stack([x, y, z], 1), want, atol=1e-6)
+
+
+# ------------------------------------------------------------- edge cases
+
+def test_empty_scene():
+    fp = matched(8)[1]
+    e = np.zeros(0, np.float32)
+    with F.Simulation(fp, e, e, e, e, e, e) as sim:
+        rc, st = sim.step(3, stats=True)
+        assert rc == F.FLIP_OK and st.n_fluid_cells == 0 and st.cg_iterations == 0
+        assert sim.read(F.CELL_TYPE).sum() == 0
+
+
+def test_single_particle_and_boundary_positions():
+    n = 8
+    dx = 1 / n
+    pts = np.array([[0.0, 0.0, 0.0], [dx, 2 * dx, 3 * dx], [1.0 - 1e-7, 0.5, 0.5],
+                    [0.5, 1.0 - 1e-7, 0.25], [4 * dx, 4 * dx, 4 * dx]], np.float32)
+    vel = np.array([[0.1, 0.2, -0.3], [0.0, 0.0, 0.0], [-0.5, 0.0, 0.1], [0.0, -1.0, 0.0],
+                    [0.2, 0.2, 0.2]], np.float32)
+    arrs = [np.ascontiguousarray(pts[:, a]) for a in range(3)] + \
+           [np.ascontiguousarray(vel[:, a]) for a in range(3)]
+    op, fp = matched(n)
+    ref = O.step(op, *arrs)
+    got = gpu_step(fp, arrs)
+    _compare_fields(ref, got, n, label="boundary points")
+    _compare_particles(ref, got, dx)
+    one = [a[:1].copy() for a in arrs]
+    ref1 = O.step(op, *one)
+    got1 = gpu_step(fp, one)
+    _compare_particles(ref1, got1, dx)
+
+
+def test_all_particles_in_one_cell():
+    n = 8
+    rng = np.random.default_rng(3)
+    pts = (3 + rng.uniform(0, 1, (200, 3))) / n
+    arrs = [pts[:, a].astype(np.float32) for a in range(3)] + \
+           [rng.normal(size=200).astype(np.float32) for _ in range(3)]
+    op, fp = matched(n)
+    ref = O.step(op, *arrs)
+    got = gpu_step(fp, arrs)
+    _compare_fields(ref, got, n, label="one cell")
+    _compare_particles(ref, got, 1 / n)
+
+
+def test_singular_full_box_is_refused():
+    sc = S.box(8, (0, 0, 0), (1, 1, 1), seed=1)
+    fp = matched(8)[1]
+    with F.Simulation(fp, *sc.arrays()) as sim:
+        with pytest.raises(F.FlipError) as ei:
+            sim.step(1, stats=True)
+        assert ei.value.code == F.FLIP_E_ARG
+
+
+def test_read_size_mismatch_and_ids():
+    sc = S.dam_break(16)
+    fp = matched(16)[1]
+    with F.Simulation(fp, *sc.arrays()) as sim:
+        sim.step(2)
+        with pytest.raises(F.FlipError) as ei:
+            sim.read(F.PX, np.zeros(3, np.float32))
+        assert ei.value.code == F.FLIP_E_SIZE
+        ids = sim.read(F.PID)
+        assert np.array_equal(np.sort(ids), np.arange(sc.n_particles))
+
+
+def test_device_inputs_match_host_inputs():
+    sc = S.random_velocities(S.dam_break(16, 0.5, 0.5), 0.3, 2)
+    fp = matched(16)[1]
+    dev = [torch.from_numpy(a).cuda() for a in sc.arrays()]
+    a = gpu_step(fp, sc.arrays(), fields=False)["particles"]
+    b = gpu_step(fp, dev, fields=False)["particles"]
+    for p, q in zip(a, b):
+        np.testing.assert_allclose(p, q, atol=1e-6)
+
+
+def test_checkpoint_resume():
+    """read -> destroy -> create -> step equals an uninterrupted run (within FP32 noise)."""
+    sc = S.dam_break(16, 0.5, 0.5)
+    fp = matched(16)[1]
+    full = gpu_step(fp, sc.arrays(), nsteps=4, fields=False)["particles"]
+    with F.Simulation(fp, *sc.arrays()) as sim:
+        sim.step(2)
+        mid = sim.particles()
+    res = gpu_step(fp, [np.ascontiguousarray(a) for a in mid], nsteps=2, fields=False)["particles"]
+    for p, q in zip(full, res):
+        np.testing.assert_allclose(p, q, atol=2e-5)
+
+
+# ------------------------------------------------------------- solver alone
+
+@pytest.mark.parametrize("n,seed", [((4, 4, 4), 1), ((8, 8, 8), 2), ((13, 9, 11), 3)])
+def test_solve_pressure_vs_dense(n, seed):
+    op = O.Params(n=n, dx=1.0 / max(n))
+    t = S.random_mask(n, 0.7, seed).astype(np.uint8)
+    rng = np.random.default_rng(seed)
+    b = (rng.normal(size=t.shape) * t).astype(np.float32)
+    xo, it, _ = O.pcg(op, t, b.astype(np.float64), tol=1e-14, max_iter=100000)
+    fp = F.default_params(*n)
+    fp.dx = 1.0 / max(n)
+    fp.cg_tol = 1e-7
+    td = torch.from_numpy(t.ravel()).cuda()
+    bd = torch.from_numpy(b.ravel()).cuda()
+    pd = torch.full((t.size,), 7.0, dtype=torch.float32, device="cuda")
+    rc, iters, rel = F.flip_solve_pressure(fp, td, bd, pd)
+    p = pd.cpu().numpy().reshape(t.shape)
+    assert rc == F.FLIP_OK and rel <= 1e-7 and iters > 0
+    assert np.all(p[t == 0] == 0)
+    assert rel_l2(p, xo) <= 1e-5
+
+
+# ------------------------------------------------------------- mixed precision
+
+def test_mixed_ir_pool_drop_48():
+    n = 48
+    sc = S.pool_drop(n)
+    op, fp = matched(n, cg_tol=1e-13, cg_max_iter=100000)
+    ref = O.step(op, *sc.arrays())
+    fp.cg_tol = 1e-4
+    fp.ir_tol = 1e-8
+    fp.cg_max_iter = 20 * n
+    got = gpu_step(fp, sc.arrays(), precision=F.FLIP_PREC_MIXED_IR)
+    st = got["stats"]
+    assert got["rc"] == F.FLIP_OK and st.cg_rel_residual <= 1e-8 and st.ir_iterations >= 1
+    assert st.rel_divergence <= 1e-6
+    _compare_fields(ref, got, n, label="mixed 48", ptol=1e-5)
+    _compare_particles(ref, got, 1 / n)
