@@ -33,6 +33,8 @@ sys.path.insert(0, ROOT)
 WORKLOADS = {
     "pool256": dict(desc="drop into pool, 256^3, depth 0.3 + sphere r=0.15 at (0.5,0.7,0.5)",
                     n=256, scene="pool", precision="mixed", cg_tol=1e-4, ir_tol=1e-8),
+    "pool128": dict(desc="drop into pool, 128^3, depth 0.3 + sphere r=0.15 at (0.5,0.7,0.5)",
+                    n=128, scene="pool", precision="mixed", cg_tol=1e-4, ir_tol=1e-8),
     "dam128": dict(desc="dam break, 128^3, block x<0.25 y<0.5", n=128, scene="dam",
                    precision="fp32", cg_tol=1e-6, ir_tol=1e-8),
     "dam32": dict(desc="dam break, 32^3, block x<0.25 y<0.5", n=32, scene="dam",

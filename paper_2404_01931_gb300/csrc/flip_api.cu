@@ -210,6 +210,7 @@ StepConsts make_consts(const flip_params& p) {
   StepConsts k{};
   for (int a = 0; a < 3; ++a) k.gdt[a] = (float)(p.gravity[a] * p.dt);
   k.pscale = (float)(p.dt / (p.rho * p.dx));
+  k.pscale64 = p.dt / (p.rho * p.dx);
   k.flip_ratio = (float)p.flip_ratio;
   k.advect_grid = p.advect_source == FLIP_ADVECT_GRID;
   k.dt = (float)p.dt;

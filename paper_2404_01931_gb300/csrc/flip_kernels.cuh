@@ -29,6 +29,7 @@ struct BinView {
 struct StepConsts {
   float gdt[3];      // gravity * dt
   float pscale;      // dt / (rho dx): pressure-difference to velocity (Eq. 5)
+  double pscale64;   // the same in FP64, for the FP64 divergence diagnostic
   float flip_ratio;
   int advect_grid;   // 1: advect with the grid velocity
   float dt;

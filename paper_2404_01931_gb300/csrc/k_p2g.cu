@@ -218,7 +218,7 @@ __global__ void k_div_norms(const Grid g, const StepConsts K, const uint8_t* __r
                             const float* __restrict__ uo2, const float* __restrict__ p32,
                             const double* __restrict__ p64, double* out2) {
   const long long nc = (long long)g.nx * g.ny * g.nz;
-  const double ps = (double)K.pscale;
+  const double ps = K.pscale64;
   double s_star = 0.0, s_new = 0.0;
   for (long long cl = blockIdx.x * (long long)blockDim.x + threadIdx.x; cl < nc;
        cl += (long long)gridDim.x * blockDim.x) {
