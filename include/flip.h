@@ -202,6 +202,31 @@ const char* flip_last_error(void);
 int flip_solve_pressure(const flip_params* params, const uint8_t* type, const float* b,
                         float* p, void* stream, int32_t* iterations, double* rel_residual);
 
+/* Allocation-free variant of flip_solve_pressure, for callers that cannot
+ * allocate device memory while they run: a plug-in whose device memory belongs
+ * to its host application's allocator under a fixed budget, or a latency-critical
+ * loop in which cudaMalloc/cudaFree are not allowed because they can synchronise
+ * the whole device.  The paper has no counterpart; this is a deployment aid.
+ *
+ * Same arguments, results and status codes as flip_solve_pressure, but the
+ * scratch (CG vectors, brick list, reduction slots, barrier, statistics) lives in
+ * one fixed-size array in device memory owned by the library, so the call
+ * allocates and frees nothing.  Limits: at most FLIP_NOALLOC_MAX_CELLS cells and
+ * FLIP_NOALLOC_MAX_BRICKS 8x8x8 bricks; larger grids return FLIP_E_SIZE before
+ * any device work (flip_last_error names the limit).  The array (about 4.3 MB) is
+ * reserved on every GPU that loads the library and held until the process exits.
+ * The first call on a device looks up the array's device address with that
+ * device current (a one-time set-up per device); make that first call before any
+ * stream capture.  Every call shares the one array per device and leaves its
+ * contents behind (each call clears what it needs at the start), so calls that
+ * overlap on the GPU race: serialise them, e.g. on one stream.  Waits for the
+ * stream before returning. */
+#define FLIP_NOALLOC_MAX_CELLS 262144
+#define FLIP_NOALLOC_MAX_BRICKS 4096
+int flip_solve_pressure_noalloc(const flip_params* params, const uint8_t* type, const float* b,
+                                float* p, void* stream, int32_t* iterations,
+                                double* rel_residual);
+
 #ifdef __cplusplus
 }
 #endif

@@ -96,6 +96,8 @@ struct flip_handle {
   bool stepped = false;
 };
 
+void flip_set_last_error_(const std::string& msg) { g_last_error = msg; }
+
 extern "C" {
 
 int flip_abi_version(void) { return FLIP_ABI_VERSION; }

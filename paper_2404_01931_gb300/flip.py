@@ -111,6 +111,8 @@ def lib():
         L.flip_last_error.restype = C.c_char_p
         L.flip_solve_pressure.argtypes = [PP, vp, vp, vp, vp, C.POINTER(i32),
                                           C.POINTER(C.c_double)]
+        L.flip_solve_pressure_noalloc.argtypes = [PP, vp, vp, vp, vp, C.POINTER(i32),
+                                                  C.POINTER(C.c_double)]
         if L.flip_abi_version() != 1:
             raise RuntimeError("libflip_gb300 ABI version mismatch")
         _lib = L
@@ -271,6 +273,27 @@ def flip_solve_pressure(params: FlipParams, type_, b, p, stream=None):
                                    C.c_void_p(pp), C.c_void_p(stream or 0), C.byref(it),
                                    C.byref(rel))
     return _check(rc), it.value, rel.value
+
+
+def flip_solve_pressure_noalloc(params: FlipParams, type_, b, p, stream=None):
+    """As flip_solve_pressure, with no device allocation: for callers that cannot
+    allocate while they run (memory owned by a host application's allocator, or
+    loops where cudaMalloc/cudaFree may not synchronise the device).  Grids up to
+    FLIP_NOALLOC_MAX_CELLS cells.  Returns (status, iterations, rel_residual)."""
+    tp, _, tdev, _ = _buf(type_, np.uint8)
+    bp, _, bdev, _ = _buf(b, np.float32)
+    pp, _, pdev, _ = _buf(p, np.float32)
+    if not (tdev and bdev and pdev):
+        raise ValueError("flip_solve_pressure_noalloc takes device buffers")
+    it = C.c_int32(0)
+    rel = C.c_double(0.0)
+    rc = lib().flip_solve_pressure_noalloc(C.byref(params), C.c_void_p(tp), C.c_void_p(bp),
+                                           C.c_void_p(pp), C.c_void_p(stream or 0),
+                                           C.byref(it), C.byref(rel))
+    return _check(rc), it.value, rel.value
+
+
+FLIP_NOALLOC_MAX_CELLS = 262144
 
 
 class Simulation:
