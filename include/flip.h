@@ -58,7 +58,8 @@ enum {
   FLIP_PREC_FP32 = 0,     /* FP32 vectors and SpMV; dot products accumulated
                              in FP32 pairs per thread, FP64 across threads */
   FLIP_PREC_MIXED_IR = 1  /* as FP32 inside; FP64 solution and outer residual
-                             r = b - A x in an iterative-refinement loop */
+                             r = b - A x, refined without restarting the
+                             Krylov direction (reliable updates) */
 };
 
 enum {
@@ -76,17 +77,20 @@ typedef struct {
   double flip_ratio;     /* FLIP share r of the blend r*FLIP + (1-r)*PIC, [0,1] */
   double skin;           /* wall clamp distance (> 0, < dx) */
   double cg_tol;         /* FP32 mode: PCG stops at ||r|| <= cg_tol*||b||.
-                            Mixed mode: tolerance of each inner FP32 solve. */
+                            Mixed mode: refinement trigger in (0,1): the FP32
+                            correction is folded into the FP64 solution and the
+                            residual recomputed in FP64 whenever the recursive
+                            residual has dropped by this factor (e.g. 0.1). */
   double ir_tol;         /* mixed mode: outer stop at ||b - A x|| <= ir_tol*||b|| */
   int32_t cg_max_iter;   /* PCG iteration cap (per solve; per inner solve in mixed) */
-  int32_t ir_max_iter;   /* mixed mode: outer iteration cap */
+  int32_t ir_max_iter;   /* mixed mode: cap on the FP64 refinements per solve */
   int32_t precision;     /* FLIP_PREC_* */
   int32_t advect_source; /* FLIP_ADVECT_* */
 } flip_params;
 
 /* Fills p with the defaults of the 32^3 dam break: dx = 1/n, dt = 1/240,
  * g = (0, -9.81, 0), rho = 1, r = 0.95, skin = 1e-3*dx, cg_tol = 1e-6,
- * ir_tol = 1e-8, cg_max_iter = 20*max(n), ir_max_iter = 20, FP32, particle
+ * ir_tol = 1e-8, cg_max_iter = 20*max(n), ir_max_iter = 100, FP32, particle
  * advection. */
 void flip_default_params(flip_params* p, int32_t nx, int32_t ny, int32_t nz);
 

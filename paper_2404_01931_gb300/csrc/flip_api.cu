@@ -134,7 +134,7 @@ void flip_default_params(flip_params* p, int32_t nx, int32_t ny, int32_t nz) {
   p->cg_tol = 1e-6;
   p->ir_tol = 1e-8;
   p->cg_max_iter = 20 * m;
-  p->ir_max_iter = 20;
+  p->ir_max_iter = 100;
   p->precision = FLIP_PREC_FP32;
   p->advect_source = FLIP_ADVECT_PARTICLE;
 }
@@ -160,8 +160,8 @@ int check_params(const flip_params* p, bool need_particles_prm) {
   if (!(p->cg_tol > 0.0) || p->cg_max_iter < 1) return fail(FLIP_E_ARG, "bad PCG tolerance/cap");
   if (p->precision != FLIP_PREC_FP32 && p->precision != FLIP_PREC_MIXED_IR)
     return fail(FLIP_E_ARG, "unknown precision mode");
-  if (p->precision == FLIP_PREC_MIXED_IR && (!(p->ir_tol > 0.0) || p->ir_max_iter < 1))
-    return fail(FLIP_E_ARG, "bad iterative-refinement tolerance/cap");
+  if (p->precision == FLIP_PREC_MIXED_IR && (!(p->ir_tol > 0.0) || !(p->cg_tol < 1.0)))
+    return fail(FLIP_E_ARG, "mixed mode needs ir_tol > 0 and a refinement trigger cg_tol < 1");
   if (need_particles_prm) {
     if (!(p->flip_ratio >= 0.0 && p->flip_ratio <= 1.0))
       return fail(FLIP_E_ARG, "flip_ratio must be in [0, 1]");

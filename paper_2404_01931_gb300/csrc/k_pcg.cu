@@ -2,27 +2,97 @@
 // (Sec. 3.1.7: 7-point Laplacian over fluid cells, p = 0 in air, walls
 // dropped), as one persistent cooperative kernel per solve.
 //
-// All CTAs stay resident for the whole solve and meet at bounded grid barriers
-// (two per iteration).  Work is the list of active 8x8x8 bricks, assigned to
-// CTAs round-robin and kept by the same CTA in every phase, so a thread always
-// owns the same cells.  Per iteration:
+// One CTA of 1024 threads per SM stays resident for the whole solve; CTAs meet
+// at bounded grid barriers (two per iteration).  The cells of the active bricks
+// form one index space (brick slot * 512 + local cell) that is cut into equal
+// contiguous chunks, one per CTA, so every thread owns the same cells in every
+// phase.  Per iteration:
 //   phase A  p_new = z + beta p_old, q = A p_new, partial p.q
 //            (the p update of the previous iteration is folded into the stencil:
 //             each neighbour's p_new is recomputed from its r and p_old, so p
 //             needs no barrier of its own; p is double-buffered)
 //   phase B  x += alpha p, r -= alpha q, z = r / diag, partials r.r and r.z
-// Reductions are deterministic: per-thread float-pair accumulation, then FP64
-// warp/block sums, one partial per CTA, and every CTA adds the partials in the
-// same order after the barrier, so all CTAs take identical decisions.
+// Reductions run on the FP32 pipes: each thread, then each warp and the CTA,
+// sums exact float pairs (FMA-split products, TwoSum additions); CTAs publish one
+// pair each, and after the barrier every CTA adds the published pairs in the
+// same order, so all CTAs take identical decisions.  Only thread 0 turns the
+// sums into the FP64 scalars alpha, beta and the stopping test.
 //
-// Mixed mode (FLIP_PREC_MIXED_IR) wraps the FP32 solve in iterative
-// refinement: r = b - A x in FP64 with x in FP64, the FP32 PCG solves A d = r,
-// x += d, until ||b - A x|| <= ir_tol ||b||.
+// Mixed mode (FLIP_PREC_MIXED_IR): the same FP32 iteration works on a
+// correction d; whenever the recursive residual has dropped by the factor
+// delta = cg_tol since the last refinement (or reaches the target), the correction is
+// folded into the FP64 solution (x += d, d = 0) and the residual is replaced by
+// the true one, r = b - A x, evaluated in FP64 — iterative refinement without
+// restarting the Krylov direction.  The solve stops when the FP64 residual
+// satisfies ||b - A x|| <= ir_tol ||b||.
 #include "flip_kernels.cuh"
 
 namespace flipk {
 
-constexpr int PCG_THREADS = 256;
+constexpr int PCG_THREADS = 1024;
+constexpr int PCG_WARPS = PCG_THREADS / 32;
+
+// ------------------------------------------------------------ float pairs
+
+struct F2 {
+  float hi, lo;
+};
+
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bv = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bv)), __fsub_rn(b.hi, bv));
+  const float lo = __fadd_rn(__fadd_rn(a.lo, b.lo), e);
+  const float hi = __fadd_rn(s, lo);
+  return F2{hi, __fsub_rn(lo, __fsub_rn(hi, s))};
+}
+
+__device__ __forceinline__ F2 f2_of(const FF& f) { return F2{f.hi, f.lo}; }
+
+__device__ __forceinline__ F2 f2_warp_sum(F2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    F2 w;
+    w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+    w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+    v = f2_add(v, w);
+  }
+  return v;
+}
+
+// CTA-wide sum of K float pairs; the result is valid in thread 0 only.
+template <int K>
+__device__ __forceinline__ void cta_sum(F2 (&v)[K], F2* scratch) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < K; ++q) v[q] = f2_warp_sum(v[q]);
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < K; ++q) scratch[q * PCG_WARPS + warp] = v[q];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      F2 s = scratch[q * PCG_WARPS + lane];
+      v[q] = f2_warp_sum(s);
+    }
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------ cell ownership
+
+struct Chunk {
+  unsigned int begin, end;  // slots of the active-cell index space
+};
+
+__device__ __forceinline__ Chunk my_chunk(unsigned int nact) {
+  const unsigned int total = nact * BRICK_CELLS;
+  unsigned int per = (total + gridDim.x - 1) / gridDim.x;
+  per = (per + 31u) & ~31u;
+  const unsigned int b = min(total, blockIdx.x * per);
+  return Chunk{b, min(total, b + per)};
+}
 
 struct CellRef {
   int i, j, k;
@@ -30,248 +100,321 @@ struct CellRef {
 };
 
 template <class F>
-__device__ __forceinline__ void for_fluid_cells(const PcgArgs& A, unsigned int nact, F&& f) {
+__device__ __forceinline__ void for_my_cells(const PcgArgs& A, const Chunk& ch, F&& f) {
   const Grid& g = A.g;
-  for (unsigned int bi = blockIdx.x; bi < nact; bi += gridDim.x) {
-    const unsigned int brick = A.active[bi];
-    const int b0 = (int)(brick % (unsigned)g.bx) * BRICK;
-    const int b1 = (int)((brick / (unsigned)g.bx) % (unsigned)g.by) * BRICK;
-    const int b2 = (int)(brick / ((unsigned)g.bx * (unsigned)g.by)) * BRICK;
-    for (int l = threadIdx.x; l < BRICK_CELLS; l += PCG_THREADS) {
-      const int i = b0 + (l & 7), j = b1 + ((l >> 3) & 7), k = b2 + (l >> 6);
-      if (i >= g.nx || j >= g.ny || k >= g.nz) continue;
-      const int c = i + g.nx * (j + g.ny * k);
-      if (A.type[c] != 1) continue;
-      f(CellRef{i, j, k, c});
-    }
+  for (unsigned int e = ch.begin + threadIdx.x; e < ch.end; e += PCG_THREADS) {
+    const unsigned int brick = A.active[e >> 9];
+    const int l = (int)(e & 511u);
+    const int i = (int)(brick % (unsigned)g.bx) * BRICK + (l & 7);
+    const int j = (int)((brick / (unsigned)g.bx) % (unsigned)g.by) * BRICK + ((l >> 3) & 7);
+    const int k = (int)(brick / ((unsigned)g.bx * (unsigned)g.by)) * BRICK + (l >> 6);
+    if (i >= g.nx || j >= g.ny || k >= g.nz) continue;
+    const int c = i + g.nx * (j + g.ny * k);
+    if (A.type[c] != 1) continue;
+    f(CellRef{i, j, k, c});
   }
 }
 
-__device__ __forceinline__ bool is_fluid(const PcgArgs& A, int c) { return A.type[c] == 1; }
+// The six neighbours of a cell: index (the cell itself when outside the grid)
+// and whether it is a fluid cell.  All loads are issued before any is used.
+struct Nbrs {
+  int idx[6];
+  bool fl[6];
+  int cnt[6];
+};
 
-// p_new of cell n = z_n + beta p_old_n with z_n = r_n / diag_n.  Written once
-// here so that the owner of a cell and its neighbours compute the same bits.
-__device__ __forceinline__ float p_update(const PcgArgs& A, const float* pold, int n, int cnt,
-                                          float beta) {
-  return __fmaf_rn(beta, __ldcg(pold + n), __fmul_rn(__ldcg(A.r + n), A.minv_tab[cnt]));
+__device__ __forceinline__ Nbrs neighbours(const PcgArgs& A, const CellRef& cr) {
+  const Grid& g = A.g;
+  const int sy = g.nx, sz = g.nx * g.ny;
+  Nbrs n;
+  const bool in[6] = {cr.i > 0, cr.i < g.nx - 1, cr.j > 0, cr.j < g.ny - 1, cr.k > 0,
+                      cr.k < g.nz - 1};
+  const int off[6] = {-1, 1, -sy, sy, -sz, sz};
+#pragma unroll
+  for (int q = 0; q < 6; ++q) n.idx[q] = in[q] ? cr.c + off[q] : cr.c;
+  uint8_t t[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) t[q] = A.type[n.idx[q]];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) n.fl[q] = in[q] && t[q] == 1;
+  n.cnt[0] = nonsolid_count(g, cr.i - 1, cr.j, cr.k);
+  n.cnt[1] = nonsolid_count(g, cr.i + 1, cr.j, cr.k);
+  n.cnt[2] = nonsolid_count(g, cr.i, cr.j - 1, cr.k);
+  n.cnt[3] = nonsolid_count(g, cr.i, cr.j + 1, cr.k);
+  n.cnt[4] = nonsolid_count(g, cr.i, cr.j, cr.k - 1);
+  n.cnt[5] = nonsolid_count(g, cr.i, cr.j, cr.k + 1);
+  return n;
 }
 
-// Phase A for one fluid cell: returns p_new(c) and writes q(c).
+// p_new of a cell = z + beta p_old with z = r / diag.  One expression, so the
+// owner of a cell and its neighbours compute the same bits.
+__device__ __forceinline__ float p_update(float r, float pold, float minv, float beta) {
+  return __fmaf_rn(beta, pold, __fmul_rn(r, minv));
+}
+
 __device__ __forceinline__ void phase_a_cell(const PcgArgs& A, const CellRef& cr,
                                              const float* pold, float* pnew, float beta,
                                              FF& pq) {
-  const Grid& g = A.g;
-  const int i = cr.i, j = cr.j, k = cr.k, c = cr.c;
-  const int sx = 1, sy = g.nx, sz = g.nx * g.ny;
-  const int cnt = nonsolid_count(g, i, j, k);
-  const float pc = p_update(A, pold, c, cnt, beta);
+  const Nbrs n = neighbours(A, cr);
+  const int cnt = nonsolid_count(A.g, cr.i, cr.j, cr.k);
+  float rv[6], pv[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    rv[q] = A.r[n.idx[q]];
+    pv[q] = pold[n.idx[q]];
+  }
+  const float pc = p_update(A.r[cr.c], pold[cr.c], A.minv_tab[cnt], beta);
   float nb = 0.0f;
-  if (i > 0 && is_fluid(A, c - sx)) nb += p_update(A, pold, c - sx, nonsolid_count(g, i - 1, j, k), beta);
-  if (i < g.nx - 1 && is_fluid(A, c + sx)) nb += p_update(A, pold, c + sx, nonsolid_count(g, i + 1, j, k), beta);
-  if (j > 0 && is_fluid(A, c - sy)) nb += p_update(A, pold, c - sy, nonsolid_count(g, i, j - 1, k), beta);
-  if (j < g.ny - 1 && is_fluid(A, c + sy)) nb += p_update(A, pold, c + sy, nonsolid_count(g, i, j + 1, k), beta);
-  if (k > 0 && is_fluid(A, c - sz)) nb += p_update(A, pold, c - sz, nonsolid_count(g, i, j, k - 1), beta);
-  if (k < g.nz - 1 && is_fluid(A, c + sz)) nb += p_update(A, pold, c + sz, nonsolid_count(g, i, j, k + 1), beta);
+#pragma unroll
+  for (int q = 0; q < 6; ++q)
+    nb += n.fl[q] ? p_update(rv[q], pv[q], A.minv_tab[n.cnt[q]], beta) : 0.0f;
   const float qc = __fmaf_rn(A.diag_tab[cnt], pc, -__fmul_rn(A.s, nb));
-  pnew[c] = pc;
-  A.q[c] = qc;
+  pnew[cr.c] = pc;
+  A.q[cr.c] = qc;
   pq.add_prod(pc, qc);
 }
 
-template <int K>
-__device__ __forceinline__ void publish_partials(const PcgArgs& A, int slot, double (&v)[K],
-                                                 double* scratch) {
-  block_sum<K>(v, scratch);
-  if (threadIdx.x == 0)
+// FP64 residual of one cell for the refinement: b - A x with x in FP64.
+__device__ __forceinline__ double residual64(const PcgArgs& A, const CellRef& cr) {
+  const Nbrs n = neighbours(A, cr);
+  double xv[6];
 #pragma unroll
-    for (int q = 0; q < K; ++q) A.partials[(size_t)(slot + q) * gridDim.x + blockIdx.x] = v[q];
+  for (int q = 0; q < 6; ++q) xv[q] = A.x64[n.idx[q]];
+  double nb = 0.0;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) nb += n.fl[q] ? xv[q] : 0.0;
+  const int cnt = nonsolid_count(A.g, cr.i, cr.j, cr.k);
+  return A.b64[cr.c] - A.s64 * ((double)cnt * A.x64[cr.c] - nb);
 }
 
+// ------------------------------------------------------------ reductions
+
+struct Shared {
+  F2 scratch[3 * PCG_WARPS];
+  float alpha, beta;
+  int flag;
+  double dscal[4];
+};
+
 template <int K>
-__device__ __forceinline__ void gather_partials(const PcgArgs& A, int slot, double (&out)[K],
-                                                double* scratch) {
-  double v[K];
+__device__ __forceinline__ void publish(const PcgArgs& A, int slot, F2 (&v)[K], Shared& sh) {
+  cta_sum<K>(v, sh.scratch);
+  if (threadIdx.x == 0) {
+    float2* part = reinterpret_cast<float2*>(A.partials);
 #pragma unroll
-  for (int q = 0; q < K; ++q) v[q] = 0.0;
-  for (unsigned int j = threadIdx.x; j < gridDim.x; j += PCG_THREADS)
-#pragma unroll
-    for (int q = 0; q < K; ++q) v[q] += __ldcg(A.partials + (size_t)(slot + q) * gridDim.x + j);
-  block_sum<K>(v, scratch);
-#pragma unroll
-  for (int q = 0; q < K; ++q) out[q] = v[q];
+    for (int q = 0; q < K; ++q)
+      part[(size_t)(slot + q) * gridDim.x + blockIdx.x] = make_float2(v[q].hi, v[q].lo);
+  }
 }
 
-// FP32 PCG on A x32 = r (r, x32 = 0 and p_old = 0 already set on fluid cells;
-// rz0 = r.z, rnorm0 = ||r||).  Returns false if a barrier failed.
-__device__ bool pcg_fp32(const PcgArgs& A, unsigned int nact, double rz0, double rnorm0,
-                         double tol, int max_iter, int* iters_out, bool* conv_out,
-                         double* rel_out, double* scratch) {
-  double rz = rz0;
-  float beta = 0.0f;
+// After a barrier: the grid-wide sums of the published pairs, in FP64, valid in
+// thread 0.  Every CTA adds the same pairs in the same order.
+template <int K>
+__device__ __forceinline__ void gather(const PcgArgs& A, int slot, double (&out)[K], Shared& sh) {
+  const float2* part = reinterpret_cast<const float2*>(A.partials);
+  F2 v[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) v[q] = F2{0.0f, 0.0f};
+  if (threadIdx.x < 32) {
+    for (unsigned int j = threadIdx.x; j < gridDim.x; j += 32)
+#pragma unroll
+      for (int q = 0; q < K; ++q) {
+        const float2 p = part[(size_t)(slot + q) * gridDim.x + j];
+        v[q] = f2_add(v[q], F2{p.x, p.y});
+      }
+#pragma unroll
+    for (int q = 0; q < K; ++q) v[q] = f2_warp_sum(v[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < K; ++q) out[q] = (double)v[q].hi + (double)v[q].lo;
+  (void)sh;
+}
+
+// ------------------------------------------------------------ the solve
+
+struct SolveState {
+  int iters = 0;
+  int refinements = 0;
+  bool conv = false;
+  bool ok = true;
+  double rel = 0.0;
+  double bnorm = 0.0;
+};
+
+// Partial-sum slots (float pairs): 0 = p.q; 1,2 = r.r, r.z (phase B and the FP32
+// start); 3,4 = ||b||^2 and r.z of the mixed start; 5,6 = FP64 residual norm and
+// r.z after a refinement.  A slot's readers always pass one more barrier before
+// the slot is written again.
+template <bool MIXED>
+__device__ void solve(const PcgArgs& A, const Chunk& ch, Shared& sh, SolveState& S) {
+  float* x = A.x32;
+  // ---- start: r = b (or float(b)), x = 0, p_old = 0; ||b||, r.z
+  {
+    FF bb, rz;
+    for_my_cells(A, ch, [&](const CellRef& cr) {
+      const float bc = MIXED ? (float)A.b64[cr.c] : A.b32[cr.c];
+      A.r[cr.c] = bc;
+      x[cr.c] = 0.0f;
+      A.pa[cr.c] = 0.0f;
+      bb.add_prod(bc, bc);
+      rz.add_prod(bc, __fmul_rn(bc, A.minv_tab[nonsolid_count(A.g, cr.i, cr.j, cr.k)]));
+    });
+    F2 v[2] = {f2_of(bb), f2_of(rz)};
+    publish<2>(A, 1, v, sh);
+  }
+  if (!grid_barrier(A.bar, A.status, gridDim.x, A.timeout_ns)) { S.ok = false; return; }
+  double s0[2];
+  gather<2>(A, 1, s0, sh);
+  // thread 0 owns the scalars
+  double rz = s0[1];
+  double bnorm = sqrt(fmax(s0[0], 0.0));
+  double rnorm = bnorm, rmax = bnorm;
+  const double target = MIXED ? A.ir_tol : A.tol;
+  if (threadIdx.x == 0) {
+    sh.flag = (bnorm == 0.0) ? 1 : 0;
+    sh.beta = 0.0f;
+  }
+  __syncthreads();
+  S.bnorm = bnorm;
+  bool conv = sh.flag != 0;
+  int it = 0, refinements = 0;
   float* pold = A.pa;
   float* pnew = A.pb;
-  int it = 0;
-  bool conv = (rnorm0 == 0.0);
-  double rnorm = rnorm0;
-  while (!conv && it < max_iter) {
+  while (!conv && it < A.max_iter) {
     ++it;
+    const float beta = sh.beta;
+    // ---- phase A
     FF pq;
-    for_fluid_cells(A, nact, [&](const CellRef& cr) { phase_a_cell(A, cr, pold, pnew, beta, pq); });
-    double va[1] = {pq.value()};
-    publish_partials<1>(A, 0, va, scratch);
-    if (!grid_barrier(A.bar, A.status, gridDim.x, A.timeout_ns)) return false;
-    double pqs[1];
-    gather_partials<1>(A, 0, pqs, scratch);
-    const float alpha = (float)(rz / pqs[0]);
+    for_my_cells(A, ch, [&](const CellRef& cr) { phase_a_cell(A, cr, pold, pnew, beta, pq); });
+    {
+      F2 v[1] = {f2_of(pq)};
+      publish<1>(A, 0, v, sh);
+    }
+    if (!grid_barrier(A.bar, A.status, gridDim.x, A.timeout_ns)) { S.ok = false; return; }
+    {
+      double s[1];
+      gather<1>(A, 0, s, sh);
+      if (threadIdx.x == 0) sh.alpha = (float)(rz / s[0]);
+    }
+    __syncthreads();
+    const float alpha = sh.alpha;
+    // ---- phase B
     FF rr, rzn;
-    for_fluid_cells(A, nact, [&](const CellRef& cr) {
+    for_my_cells(A, ch, [&](const CellRef& cr) {
       const int c = cr.c;
-      const int cnt = nonsolid_count(A.g, cr.i, cr.j, cr.k);
-      A.x32[c] = __fmaf_rn(alpha, pnew[c], A.x32[c]);
+      x[c] = __fmaf_rn(alpha, pnew[c], x[c]);
       const float rc = __fmaf_rn(-alpha, A.q[c], A.r[c]);
       A.r[c] = rc;
-      const float zc = __fmul_rn(rc, A.minv_tab[cnt]);
       rr.add_prod(rc, rc);
-      rzn.add_prod(rc, zc);
+      rzn.add_prod(rc, __fmul_rn(rc, A.minv_tab[nonsolid_count(A.g, cr.i, cr.j, cr.k)]));
     });
-    double vb[2] = {rr.value(), rzn.value()};
-    publish_partials<2>(A, 1, vb, scratch);
-    if (!grid_barrier(A.bar, A.status, gridDim.x, A.timeout_ns)) return false;
-    double sb[2];
-    gather_partials<2>(A, 1, sb, scratch);
-    rnorm = sqrt(fmax(sb[0], 0.0));
-    if (rnorm <= tol * rnorm0) { conv = true; break; }
-    beta = (float)(sb[1] / rz);
-    rz = sb[1];
+    {
+      F2 v[2] = {f2_of(rr), f2_of(rzn)};
+      publish<2>(A, 1, v, sh);
+    }
+    if (!grid_barrier(A.bar, A.status, gridDim.x, A.timeout_ns)) { S.ok = false; return; }
+    {
+      double s[2];
+      gather<2>(A, 1, s, sh);
+      if (threadIdx.x == 0) {
+        rnorm = sqrt(fmax(s[0], 0.0));
+        int f = 0;  // 0 continue, 1 converged, 2 refine
+        if (rnorm <= target * bnorm) f = MIXED ? 2 : 1;
+        else if (MIXED && rnorm <= A.tol * rmax) f = 2;
+        if (f == 0) {
+          sh.beta = (float)(s[1] / rz);
+          rz = s[1];
+        }
+        sh.flag = f;
+      }
+    }
+    __syncthreads();
+    int f = sh.flag;
+    if constexpr (MIXED) {
+      if (f == 2) {
+        // ---- refinement: x64 += d, d = 0; then r = b - A x64 in FP64
+        for_my_cells(A, ch, [&](const CellRef& cr) {
+          A.x64[cr.c] += (double)x[cr.c];
+          x[cr.c] = 0.0f;
+        });
+        if (!grid_barrier(A.bar, A.status, gridDim.x, A.timeout_ns)) { S.ok = false; return; }
+        FF rr64, rz2;  // the norm of the FP64 residual is accumulated from its float value
+        double rr_exact = 0.0;
+        for_my_cells(A, ch, [&](const CellRef& cr) {
+          const double rc = residual64(A, cr);
+          const float r32 = (float)rc;
+          A.r[cr.c] = r32;
+          rr64.add_prod(r32, r32);
+          rz2.add_prod(r32, __fmul_rn(r32, A.minv_tab[nonsolid_count(A.g, cr.i, cr.j, cr.k)]));
+        });
+        (void)rr_exact;
+        F2 v[2] = {f2_of(rr64), f2_of(rz2)};
+        publish<2>(A, 5, v, sh);
+        if (!grid_barrier(A.bar, A.status, gridDim.x, A.timeout_ns)) { S.ok = false; return; }
+        double s[2];
+        gather<2>(A, 5, s, sh);
+        ++refinements;
+        if (threadIdx.x == 0) {
+          rnorm = sqrt(fmax(s[0], 0.0));
+          rmax = rnorm;
+          if (rnorm <= target * bnorm) {
+            sh.flag = 1;
+          } else if (refinements >= A.ir_max_iter) {
+            sh.flag = 3;  // refinement cap: stop with the current solution
+          } else {
+            sh.flag = 0;
+            sh.beta = (float)(s[1] / rz);
+            rz = s[1];
+          }
+        }
+        __syncthreads();
+        f = sh.flag;
+      }
+    }
+    if (f == 1) { conv = true; break; }
+    if (f == 3) break;
     float* t = pold; pold = pnew; pnew = t;
   }
-  *iters_out = it;
-  *conv_out = conv;
-  *rel_out = rnorm0 > 0.0 ? rnorm / rnorm0 : 0.0;
-  return true;
+  if constexpr (MIXED) {
+    if (!conv) {  // cap reached: keep the last iterate
+      for_my_cells(A, ch, [&](const CellRef& cr) {
+        A.x64[cr.c] += (double)x[cr.c];
+        x[cr.c] = 0.0f;
+      });
+    }
+    // the solution as a float pair for the G2P pressure gradient
+    for_my_cells(A, ch, [&](const CellRef& cr) {
+      const double xv = A.x64[cr.c];
+      const float hi = __double2float_rn(xv);
+      const float lo = __double2float_rn(xv - (double)hi);
+      A.pff[cr.c] = make_float2(hi, lo);
+    });
+  }
+  S.iters = it;
+  S.refinements = refinements;
+  S.conv = conv;
+  S.rel = bnorm > 0.0 ? rnorm / bnorm : 0.0;
 }
 
 template <bool MIXED>
-__global__ void __launch_bounds__(PCG_THREADS) k_pcg(const __grid_constant__ PcgArgs A) {
-  __shared__ double scratch[32 * 3];
+__global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(const __grid_constant__ PcgArgs A) {
+  __shared__ Shared sh;
   const unsigned int nact = *A.n_active;
   const long long ncells = (long long)A.g.nx * A.g.ny * A.g.nz;
-  bool singular = false;
-  if (A.check_singular) singular = ((long long)A.stats->n_fluid == ncells);
-  int iters = 0, outer = 0;
-  bool conv = false;
-  double rel = 0.0, bnorm = 0.0;
-  bool ok = true;
-
-  if (!singular) {
-    if constexpr (!MIXED) {
-      // Phase I: r = b, x = 0, p_old = 0; ||b||^2 and r.z.
-      FF bb, rz;
-      for_fluid_cells(A, nact, [&](const CellRef& cr) {
-        const float bc = A.b32[cr.c];
-        A.r[cr.c] = bc;
-        A.x32[cr.c] = 0.0f;
-        A.pa[cr.c] = 0.0f;
-        bb.add_prod(bc, bc);
-        rz.add_prod(bc, __fmul_rn(bc, A.minv_tab[nonsolid_count(A.g, cr.i, cr.j, cr.k)]));
-      });
-      double v[2] = {bb.value(), rz.value()};
-      publish_partials<2>(A, 1, v, scratch);
-      ok = grid_barrier(A.bar, A.status, gridDim.x, A.timeout_ns);
-      if (ok) {
-        double s[2];
-        gather_partials<2>(A, 1, s, scratch);
-        bnorm = sqrt(fmax(s[0], 0.0));
-        ok = pcg_fp32(A, nact, s[1], bnorm, A.tol, A.max_iter, &iters, &conv, &rel, scratch);
-      }
-    } else {
-      // ||b||^2 in FP64 (once per solve).
-      double bb = 0.0;
-      for_fluid_cells(A, nact, [&](const CellRef& cr) {
-        const double bc = A.b64[cr.c];
-        bb = fma(bc, bc, bb);
-      });
-      double v0[1] = {bb};
-      publish_partials<1>(A, 3, v0, scratch);
-      ok = grid_barrier(A.bar, A.status, gridDim.x, A.timeout_ns);
-      if (ok) {
-        double s0[1];
-        gather_partials<1>(A, 3, s0, scratch);
-        bnorm = sqrt(fmax(s0[0], 0.0));
-      }
-      bool outer_conv = (bnorm == 0.0);
-      while (ok && !outer_conv) {
-        // Phase R: r = b - A x in FP64; inner start d = 0, p_old = 0.
-        double rr64 = 0.0;
-        FF rr32, rz32;
-        const Grid& g = A.g;
-        const int sy = g.nx, sz = g.nx * g.ny;
-        for_fluid_cells(A, nact, [&](const CellRef& cr) {
-          const int c = cr.c, i = cr.i, j = cr.j, k = cr.k;
-          double nb = 0.0;
-          if (i > 0 && is_fluid(A, c - 1)) nb += __ldcg(A.x64 + c - 1);
-          if (i < g.nx - 1 && is_fluid(A, c + 1)) nb += __ldcg(A.x64 + c + 1);
-          if (j > 0 && is_fluid(A, c - sy)) nb += __ldcg(A.x64 + c - sy);
-          if (j < g.ny - 1 && is_fluid(A, c + sy)) nb += __ldcg(A.x64 + c + sy);
-          if (k > 0 && is_fluid(A, c - sz)) nb += __ldcg(A.x64 + c - sz);
-          if (k < g.nz - 1 && is_fluid(A, c + sz)) nb += __ldcg(A.x64 + c + sz);
-          const int cnt = nonsolid_count(g, i, j, k);
-          const double ax = A.s64 * ((double)cnt * __ldcg(A.x64 + c) - nb);
-          const double rc = A.b64[c] - ax;
-          rr64 = fma(rc, rc, rr64);
-          const float r32 = (float)rc;
-          A.r[c] = r32;
-          A.x32[c] = 0.0f;
-          A.pa[c] = 0.0f;
-          rr32.add_prod(r32, r32);
-          rz32.add_prod(r32, __fmul_rn(r32, A.minv_tab[cnt]));
-        });
-        double v[3] = {rr64, rr32.value(), rz32.value()};
-        // Slots 4..6 are phase R's own: their previous readers finished before
-        // the first barrier of the inner solve that followed.
-        publish_partials<3>(A, 4, v, scratch);
-        if (!(ok = grid_barrier(A.bar, A.status, gridDim.x, A.timeout_ns))) break;
-        double s[3];
-        gather_partials<3>(A, 4, s, scratch);
-        rel = sqrt(fmax(s[0], 0.0)) / bnorm;
-        if (rel <= A.ir_tol) { outer_conv = true; break; }
-        if (outer >= A.ir_max_iter) break;
-        ++outer;
-        int it_in = 0;
-        bool c_in = false;
-        double rel_in = 0.0;
-        ok = pcg_fp32(A, nact, s[2], sqrt(fmax(s[1], 0.0)), A.tol, A.max_iter, &it_in, &c_in,
-                      &rel_in, scratch);
-        iters += it_in;
-        if (!ok) break;
-        // Phase U: x += d.
-        for_fluid_cells(A, nact, [&](const CellRef& cr) {
-          A.x64[cr.c] += (double)A.x32[cr.c];
-        });
-        if (!(ok = grid_barrier(A.bar, A.status, gridDim.x, A.timeout_ns))) break;
-      }
-      conv = outer_conv;
-      // Phase F: the solution as a float pair for the G2P gradient.
-      for_fluid_cells(A, nact, [&](const CellRef& cr) {
-        const double xv = A.x64[cr.c];
-        const float hi = __double2float_rn(xv);
-        const float lo = __double2float_rn(xv - (double)hi);
-        A.pff[cr.c] = make_float2(hi, lo);
-      });
-    }
-  }
-
+  const bool singular = A.check_singular && ((long long)A.stats->n_fluid == ncells);
+  SolveState S;
+  if (!singular) solve<MIXED>(A, my_chunk(nact), sh, S);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     int st = 0;
     if (singular) st |= DEV_SINGULAR;
-    else if (ok && !conv) st |= DEV_NOT_CONVERGED;
+    else if (S.ok && !S.conv) st |= DEV_NOT_CONVERGED;
     if (st) atomicOr(A.status, st);
-    A.stats->cg_iters = iters;
-    A.stats->ir_iters = outer;
-    A.stats->cg_iters_total += iters;
-    A.stats->ir_iters_total += outer;
-    A.stats->rel_res = rel;
-    A.stats->bnorm = bnorm;
+    A.stats->cg_iters = S.iters;
+    A.stats->ir_iters = S.refinements;
+    A.stats->cg_iters_total += S.iters;
+    A.stats->ir_iters_total += S.refinements;
+    A.stats->rel_res = S.rel;
+    A.stats->bnorm = S.bnorm;
   }
 }
 
@@ -287,9 +430,9 @@ cudaError_t pcg_max_blocks(int* max_blocks, int* sm_count) {
   if (e != cudaSuccess) return e;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, k_pcg<true>, PCG_THREADS, 0);
   if (e != cudaSuccess) return e;
-  int per_sm = per_sm_a < per_sm_b ? per_sm_a : per_sm_b;
-  if (per_sm > 4) per_sm = 4;  // fewer partials per reduction; 1024 threads per SM
-  *max_blocks = per_sm * sms;
+  const int per_sm = per_sm_a < per_sm_b ? per_sm_a : per_sm_b;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  *max_blocks = sms;  // one CTA per SM
   *sm_count = sms;
   return cudaSuccess;
 }

@@ -282,7 +282,7 @@ def test_mixed_ir_pool_drop_48():
     sc = S.pool_drop(n)
     op, fp = matched(n, cg_tol=1e-13, cg_max_iter=100000)
     ref = O.step(op, *sc.arrays())
-    fp.cg_tol = 1e-4
+    fp.cg_tol = 0.1
     fp.ir_tol = 1e-8
     fp.cg_max_iter = 20 * n
     got = gpu_step(fp, sc.arrays(), precision=F.FLIP_PREC_MIXED_IR)
@@ -291,3 +291,72 @@ def test_mixed_ir_pool_drop_48():
     assert st.rel_divergence <= 1e-6
     _compare_fields(ref, got, n, label="mixed 48", ptol=1e-5)
     _compare_particles(ref, got, 1 / n)
+
+
+# ------------------------------------------------------------- full sizes, bench launch config
+
+def fp32_pressure_tol(block_cells):
+    """Attainable relative accuracy of an FP32-stored pressure: u32 * kappa(A) (the
+    forward error of a backward-stable solve in precision u is about u * kappa).  For a
+    fluid box of (nx, ny, nz) cells against walls on x=0, y=0, z=0 and z=N, with air on
+    its +x and +y sides, A separates into 1-D paths whose spectra are closed-form:
+    Neumann-Dirichlet 2-2cos(pi(2k+1)/(2m+1)) in x and y, Neumann-Neumann 2-2cos(pi k/m)
+    in z (smallest 0); lambda_max < 12 (in units of dt/(rho dx^2))."""
+    bx, by, _ = block_cells
+    lmin = (2 - 2 * np.cos(np.pi / (2 * bx + 1))) + (2 - 2 * np.cos(np.pi / (2 * by + 1)))
+    return float(np.finfo(np.float32).eps / 2 * 12.0 / lmin)
+
+
+@pytest.mark.slow
+def test_dam_break_128_full_size_two_steps():
+    """The 128^3 dam break (2,097,152 particles) in the plain FP32 mode bench.py runs:
+    velocities at the 1e-5 bar, pressure at the FP32 attainable accuracy u32*kappa
+    (reading O9: FP32 storage floors the true residual on a 64-cell-deep column)."""
+    sc = S.dam_break(128)
+    op, fp = matched(128)
+    ptol = fp32_pressure_tol((32, 64, 128))
+    assert 1e-4 < ptol < 3e-4
+    st = [a.astype(np.float64) for a in sc.arrays()]
+    r1 = O.step(op, *st)
+    st1 = [np.asarray(a, np.float32) for a in (r1.x, r1.y, r1.z, r1.u, r1.v, r1.w)]
+    got = gpu_step(fp, sc.arrays())
+    _compare_fields(r1, got, 128, label="128^3 step 1", ptol=ptol)
+    # particle velocities carry the pressure gradient's error: same tier
+    _compare_particles(r1, got, 1 / 128, vel_tol=ptol)
+    r2 = O.step(op, *st1)
+    got2 = gpu_step(fp, st1)
+    _compare_fields(r2, got2, 128, label="128^3 step 2", ptol=ptol)
+
+
+@pytest.mark.slow
+def test_dam_break_128_mixed_meets_the_1e5_bar():
+    """Same scene in mixed precision: pressure within 1e-5 of the oracle's tight solve."""
+    sc = S.dam_break(128)
+    op, fp = matched(128, cg_tol=1e-11, cg_max_iter=100000)
+    ref = O.step(op, *sc.arrays())
+    fp.cg_tol, fp.ir_tol = 0.1, 1e-8
+    got = gpu_step(fp, sc.arrays(), precision=F.FLIP_PREC_MIXED_IR)
+    assert got["stats"].cg_rel_residual <= 1e-8
+    _compare_fields(ref, got, 128, label="128^3 mixed")
+    _compare_particles(ref, got, 1 / 128)
+
+
+@pytest.mark.slow
+def test_pool_drop_256_full_size_mixed():
+    """The bench workload itself: 256^3 pool, 42,266,944 particles, mixed precision to
+    1e-8, one step vs the oracle's FP64 step with a tight solve."""
+    sc = S.pool_drop(256)
+    op, fp = matched(256, cg_tol=1e-11, cg_max_iter=100000)
+    ref = O.step(op, *sc.arrays())
+    fp.cg_tol, fp.ir_tol = 0.1, 1e-8
+    got = gpu_step(fp, sc.arrays(), precision=F.FLIP_PREC_MIXED_IR)
+    st = got["stats"]
+    # 5,283,368 seeded cells; a particle rounded to float32 can land on its cell's upper
+    # face and bin into the next cell, which both sides then count as fluid
+    assert got["rc"] == F.FLIP_OK and st.n_fluid_cells == ref.n_fluid
+    assert 5283368 <= ref.n_fluid <= 5283368 + 16
+    assert st.cg_rel_residual <= 1e-8 and st.rel_divergence <= 1e-6
+    _compare_fields(ref, got, 256, label="256^3 mixed")
+    _compare_particles(ref, got, 1 / 256)
+    ids = got["particles"]  # creation order restored through the ids
+    assert all(a.shape[0] == 42266944 for a in ids)
