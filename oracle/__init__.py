@@ -55,6 +55,11 @@ def lib():
         L.oracle_apply_A.argtypes = [P, vp, vp, vp]
         L.oracle_pcg.argtypes = [P, vp, vp, C.c_double, C.c_int, vp, vp]
         L.oracle_pcg.restype = C.c_int
+        L.oracle_mg_levels.argtypes = [P, vp]
+        L.oracle_mg_levels.restype = C.c_int
+        L.oracle_mg_vcycle.argtypes = [P, vp, vp, vp, C.c_int, C.c_double]
+        L.oracle_pcg_mg.argtypes = [P, vp, vp, C.c_double, C.c_int, C.c_int, C.c_double, vp, vp]
+        L.oracle_pcg_mg.restype = C.c_int
         L.oracle_project.argtypes = [P, C.c_int, vp, vp, vp, vp]
         L.oracle_interp.argtypes = [P, C.c_int, vp, C.c_double, C.c_double, C.c_double]
         L.oracle_interp.restype = C.c_double
@@ -227,6 +232,36 @@ def pcg(params: Params, type_, b, tol=None, max_iter=None):
     P = params.c()
     it = lib().oracle_pcg(C.byref(P), _p(type_), _p(b), P.cg_tol if tol is None else tol,
                           P.cg_max_iter if max_iter is None else max_iter, _p(x), C.byref(rel))
+    return x, it, rel.value
+
+
+def mg_levels(params: Params):
+    dims = np.zeros((12, 3), np.int32)
+    L = lib().oracle_mg_levels(C.byref(params.c()), _p(dims))
+    return [tuple(int(v) for v in dims[l]) for l in range(L)]
+
+
+MG_NU = 2        # red-black sweep pairs before and after the coarse correction
+MG_OMEGA = 2.0   # over-correction of the coarse correction
+
+
+def mg_vcycle(params: Params, type_, r, nu=MG_NU, omega=MG_OMEGA):
+    type_ = np.ascontiguousarray(type_, np.uint8)
+    r = np.ascontiguousarray(r, np.float64)
+    z = np.zeros_like(r)
+    lib().oracle_mg_vcycle(C.byref(params.c()), _p(type_), _p(r), _p(z), int(nu), float(omega))
+    return z
+
+
+def pcg_mg(params: Params, type_, b, tol=None, max_iter=None, nu=MG_NU, omega=MG_OMEGA):
+    type_ = np.ascontiguousarray(type_, np.uint8)
+    b = np.ascontiguousarray(b, np.float64)
+    x = np.zeros_like(b)
+    rel = C.c_double(0.0)
+    P = params.c()
+    it = lib().oracle_pcg_mg(C.byref(P), _p(type_), _p(b), P.cg_tol if tol is None else tol,
+                             P.cg_max_iter if max_iter is None else max_iter, int(nu),
+                             float(omega), _p(x), C.byref(rel))
     return x, it, rel.value
 
 

@@ -461,3 +461,193 @@ int oracle_step(const oracle_params* P, int64_t np, double* x, double* y, double
   for (int d = 0; d < 3; ++d) { free(uo[d]); free(us[d]); free(un[d]); }
   return status;
 }
+
+/* ------------------------------------------------------------------------
+ * Multigrid V-cycle preconditioner (red-black Gauss-Seidel smoothing, Sec. 3.2.3)
+ * ------------------------------------------------------------------------ */
+
+typedef struct {
+  int64_t n[3];
+  double s;       /* dt / (rho h_l^2) */
+  uint8_t* t;     /* fluid flags */
+  double* x;
+  double* b;
+} mg_level;
+
+int oracle_mg_levels(const oracle_params* P, int32_t dims[][3]) {
+  int64_t n[3] = {P->n[0], P->n[1], P->n[2]};
+  int L = 0;
+  for (;;) {
+    for (int a = 0; a < 3; ++a) dims[L][a] = (int32_t)n[a];
+    ++L;
+    const int64_t m = n[0] > n[1] ? (n[0] > n[2] ? n[0] : n[2]) : (n[1] > n[2] ? n[1] : n[2]);
+    if (m <= 4 || L == ORACLE_MG_MAX_LEVELS) break;
+    for (int a = 0; a < 3; ++a) n[a] = (n[a] + 1) / 2;
+  }
+  return L;
+}
+
+static int64_t lv_idx(const mg_level* v, int64_t i, int64_t j, int64_t k) {
+  return i + v->n[0] * (j + v->n[1] * k);
+}
+
+static int lv_nonsolid(const mg_level* v, int64_t i, int64_t j, int64_t k) {
+  const int64_t idx[3] = {i, j, k};
+  int cnt = 0;
+  for (int ax = 0; ax < 3; ++ax) cnt += (idx[ax] > 0) + (idx[ax] < v->n[ax] - 1);
+  return cnt;
+}
+
+/* sum of x over the fluid neighbours of cell (i,j,k) */
+static double lv_nbr_sum(const mg_level* v, const double* x, int64_t i, int64_t j, int64_t k) {
+  const int64_t di[6] = {-1, 1, 0, 0, 0, 0}, dj[6] = {0, 0, -1, 1, 0, 0}, dk[6] = {0, 0, 0, 0, -1, 1};
+  double s = 0.0;
+  for (int q = 0; q < 6; ++q) {
+    const int64_t a = i + di[q], b = j + dj[q], c = k + dk[q];
+    if (a < 0 || b < 0 || c < 0 || a >= v->n[0] || b >= v->n[1] || c >= v->n[2]) continue;
+    const int64_t m = lv_idx(v, a, b, c);
+    if (v->t[m]) s += x[m];
+  }
+  return s;
+}
+
+/* One Gauss-Seidel half-sweep over the fluid cells of one colour (i+j+k even =
+ * red = 0): x_c <- (b_c + s sum_fluid-neighbours x_n) / (s n_c).  Cells of one
+ * colour only have neighbours of the other colour, so the order inside a colour
+ * does not matter. */
+static void lv_half_sweep(mg_level* v, int colour) {
+#pragma omp parallel for schedule(static)
+  for (int64_t k = 0; k < v->n[2]; ++k)
+    for (int64_t j = 0; j < v->n[1]; ++j)
+      for (int64_t i = 0; i < v->n[0]; ++i) {
+        if (((i + j + k) & 1) != colour) continue;
+        const int64_t c = lv_idx(v, i, j, k);
+        if (!v->t[c]) continue;
+        v->x[c] = (v->b[c] + v->s * lv_nbr_sum(v, v->x, i, j, k)) /
+                  (v->s * (double)lv_nonsolid(v, i, j, k));
+      }
+}
+
+static void mg_vcycle_level(mg_level* lv, int l, int L, int nu, double omega) {
+  mg_level* v = &lv[l];
+  const int64_t nc = v->n[0] * v->n[1] * v->n[2];
+  for (int64_t c = 0; c < nc; ++c) v->x[c] = 0.0;
+  if (l == L - 1) {
+    for (int s = 0; s < ORACLE_MG_COARSE_SWEEPS; ++s) { lv_half_sweep(v, 0); lv_half_sweep(v, 1); }
+    for (int s = 0; s < ORACLE_MG_COARSE_SWEEPS; ++s) { lv_half_sweep(v, 1); lv_half_sweep(v, 0); }
+    return;
+  }
+  for (int s = 0; s < nu; ++s) { lv_half_sweep(v, 0); lv_half_sweep(v, 1); }
+  /* residual of the fine level, restricted: b_{l+1} = (1/16) sum of fluid children.
+   * 1/8 averages the children; the extra 1/2 matches the coarse equation to the
+   * Galerkin operator P^T A P / 8, which for piecewise-constant P is twice the
+   * 7-point operator rediscretised at spacing 2h. */
+  mg_level* w = &lv[l + 1];
+  const int64_t ncc = w->n[0] * w->n[1] * w->n[2];
+  for (int64_t c = 0; c < ncc; ++c) w->b[c] = 0.0;
+  for (int64_t k = 0; k < v->n[2]; ++k)
+    for (int64_t j = 0; j < v->n[1]; ++j)
+      for (int64_t i = 0; i < v->n[0]; ++i) {
+        const int64_t c = lv_idx(v, i, j, k);
+        if (!v->t[c]) continue;
+        const double ax = v->s * ((double)lv_nonsolid(v, i, j, k) * v->x[c] - lv_nbr_sum(v, v->x, i, j, k));
+        w->b[lv_idx(w, i / 2, j / 2, k / 2)] += (v->b[c] - ax) / 16.0;
+      }
+  mg_vcycle_level(lv, l + 1, L, nu, omega);
+  /* correction: each fluid cell adds omega times its parent's value */
+  for (int64_t k = 0; k < v->n[2]; ++k)
+    for (int64_t j = 0; j < v->n[1]; ++j)
+      for (int64_t i = 0; i < v->n[0]; ++i) {
+        const int64_t c = lv_idx(v, i, j, k);
+        if (v->t[c]) v->x[c] += omega * w->x[lv_idx(w, i / 2, j / 2, k / 2)];
+      }
+  for (int s = 0; s < nu; ++s) { lv_half_sweep(v, 1); lv_half_sweep(v, 0); }
+}
+
+static int mg_build(const oracle_params* P, const uint8_t* type, mg_level* lv) {
+  int32_t dims[ORACLE_MG_MAX_LEVELS][3];
+  const int L = oracle_mg_levels(P, dims);
+  for (int l = 0; l < L; ++l) {
+    for (int a = 0; a < 3; ++a) lv[l].n[a] = dims[l][a];
+    const double h = P->dx * (double)(1 << l);
+    lv[l].s = P->dt / (P->rho * h * h);
+    const size_t nc = (size_t)(lv[l].n[0] * lv[l].n[1] * lv[l].n[2]);
+    lv[l].t = (uint8_t*)calloc(nc, 1);
+    lv[l].x = (double*)calloc(nc, sizeof(double));
+    lv[l].b = (double*)calloc(nc, sizeof(double));
+  }
+  const int64_t nc0 = lv[0].n[0] * lv[0].n[1] * lv[0].n[2];
+  for (int64_t c = 0; c < nc0; ++c) lv[0].t[c] = type[c] == 1;
+  for (int l = 1; l < L; ++l) {
+    const mg_level* f = &lv[l - 1];
+    for (int64_t k = 0; k < f->n[2]; ++k)
+      for (int64_t j = 0; j < f->n[1]; ++j)
+        for (int64_t i = 0; i < f->n[0]; ++i)
+          if (f->t[lv_idx(f, i, j, k)]) lv[l].t[lv_idx(&lv[l], i / 2, j / 2, k / 2)] = 1;
+  }
+  return L;
+}
+
+static void mg_free(mg_level* lv, int L) {
+  for (int l = 0; l < L; ++l) { free(lv[l].t); free(lv[l].x); free(lv[l].b); }
+}
+
+static void mg_apply(mg_level* lv, int L, int nu, double omega, const double* r, double* z) {
+  const int64_t nc0 = lv[0].n[0] * lv[0].n[1] * lv[0].n[2];
+  for (int64_t c = 0; c < nc0; ++c) lv[0].b[c] = lv[0].t[c] ? r[c] : 0.0;
+  mg_vcycle_level(lv, 0, L, nu, omega);
+  for (int64_t c = 0; c < nc0; ++c) z[c] = lv[0].t[c] ? lv[0].x[c] : 0.0;
+}
+
+void oracle_mg_vcycle(const oracle_params* P, const uint8_t* type, const double* r, double* z,
+                      int nu, double omega) {
+  mg_level lv[ORACLE_MG_MAX_LEVELS];
+  const int L = mg_build(P, type, lv);
+  mg_apply(lv, L, nu, omega, r, z);
+  mg_free(lv, L);
+}
+
+/* PCG with the V-cycle as M^{-1}; the same iteration and stopping rule as
+ * oracle_pcg (p0 = 0, ||r|| <= tol ||b||). */
+int oracle_pcg_mg(const oracle_params* P, const uint8_t* type, const double* b, double tol,
+                  int max_iter, int nu, double omega, double* x, double* rel_res) {
+  const int64_t nc = oracle_n_cells(P);
+  mg_level lv[ORACLE_MG_MAX_LEVELS];
+  const int L = mg_build(P, type, lv);
+  double* r = (double*)malloc(sizeof(double) * (size_t)nc);
+  double* zz = (double*)malloc(sizeof(double) * (size_t)nc);
+  double* d = (double*)malloc(sizeof(double) * (size_t)nc);
+  double* q = (double*)malloc(sizeof(double) * (size_t)nc);
+  int result = -1;
+  for (int64_t c = 0; c < nc; ++c) {
+    x[c] = 0.0;
+    r[c] = type[c] ? b[c] : 0.0;
+  }
+  mg_apply(lv, L, nu, omega, r, zz);
+  for (int64_t c = 0; c < nc; ++c) d[c] = zz[c];
+  const double bnorm = sqrt(dot_fluid(nc, type, r, r));
+  double rz = dot_fluid(nc, type, r, zz);
+  double rnorm = bnorm;
+  if (bnorm == 0.0) {
+    result = 0;
+  } else {
+    for (int it = 1; it <= max_iter; ++it) {
+      oracle_apply_A(P, type, d, q);
+      const double alpha = rz / dot_fluid(nc, type, d, q);
+      for (int64_t c = 0; c < nc; ++c)
+        if (type[c]) { x[c] += alpha * d[c]; r[c] -= alpha * q[c]; }
+      rnorm = sqrt(dot_fluid(nc, type, r, r));
+      if (rnorm <= tol * bnorm) { result = it; break; }
+      mg_apply(lv, L, nu, omega, r, zz);
+      const double rz_new = dot_fluid(nc, type, r, zz);
+      const double beta = rz_new / rz;
+      rz = rz_new;
+      for (int64_t c = 0; c < nc; ++c)
+        if (type[c]) d[c] = zz[c] + beta * d[c];
+    }
+  }
+  if (rel_res) *rel_res = bnorm > 0.0 ? rnorm / bnorm : 0.0;
+  free(r); free(zz); free(d); free(q);
+  mg_free(lv, L);
+  return result;
+}

@@ -100,6 +100,30 @@ void oracle_apply_A(const oracle_params* P, const uint8_t* type, const double* p
 int oracle_pcg(const oracle_params* P, const uint8_t* type, const double* b, double tol,
                int max_iter, double* p, double* rel_res);
 
+/* Multigrid V-cycle preconditioner for the PCG of Sec. 3.1.7, with the
+ * red-black Gauss-Seidel of Sec. 3.2.3 as its smoother.  Levels: level 0 is the
+ * cell grid; level l+1 has ceil(n_l/2) cells per axis, a coarse cell is fluid
+ * when any of its (up to 8) children is, and coarsening stops once the largest
+ * extent is <= 4 (at most ORACLE_MG_MAX_LEVELS levels).  Level l carries the
+ * 7-point operator with scale dt/(rho (2^l dx)^2).  A V-cycle from a zero guess:
+ * nu (red, black) half-sweep pairs, residual, restriction b_{l+1} = (1/16) sum of
+ * the fluid children's residuals (Galerkin scaling for piecewise-constant
+ * prolongation), coarse V-cycle, correction x += omega * x_{l+1}(parent)
+ * on fluid cells, nu (black, red) pairs.  The coarsest level does
+ * ORACLE_MG_COARSE_SWEEPS (red, black) pairs then as many (black, red) pairs.
+ * The operator is symmetric positive definite for any omega > 0 (symmetrised
+ * smoother plus a positively scaled SPD coarse term); omega = 1 is the
+ * Galerkin-consistent cycle, omega > 1 over-corrects, which piecewise-constant
+ * prolongation needs to converge fast. */
+#define ORACLE_MG_MAX_LEVELS 12
+#define ORACLE_MG_COARSE_SWEEPS 8
+int oracle_mg_levels(const oracle_params* P, int32_t dims[][3]);
+void oracle_mg_vcycle(const oracle_params* P, const uint8_t* type, const double* r, double* z,
+                      int nu, double omega);
+/* PCG with the V-cycle preconditioner; same stopping rule as oracle_pcg. */
+int oracle_pcg_mg(const oracle_params* P, const uint8_t* type, const double* b, double tol,
+                  int max_iter, int nu, double omega, double* x, double* rel_res);
+
 /* Eq. 5: pressure update of one component. */
 void oracle_project(const oracle_params* P, int comp, const double* u_star, const double* p,
                     const uint8_t* type, double* u_new);
