@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define FLIP_ABI_VERSION 1
+#define FLIP_ABI_VERSION 2
 
 /* ------------------------------------------------------------ status codes */
 enum {
@@ -67,6 +67,15 @@ enum {
   FLIP_ADVECT_GRID = 1      /* x += dt * (interpolated projected grid velocity) */
 };
 
+enum {
+  FLIP_PRECOND_JACOBI = 0, /* diagonal preconditioner */
+  FLIP_PRECOND_MG = 1      /* one multigrid V-cycle per iteration: levels coarsened 2x
+                              per axis to an extent <= 4, red-black Gauss-Seidel
+                              smoothing (Sec. 3.2.3), restriction (1/16) x sum of
+                              the fluid children's residuals, correction 2x the
+                              parent's value; symmetric positive definite */
+};
+
 typedef struct {
   int32_t n[3];          /* cells per axis, each in [2, 2048] */
   double dx;             /* cell edge; 1/dx must be an integer <= 2^24 so that
@@ -86,12 +95,16 @@ typedef struct {
   int32_t ir_max_iter;   /* mixed mode: cap on the FP64 refinements per solve */
   int32_t precision;     /* FLIP_PREC_* */
   int32_t advect_source; /* FLIP_ADVECT_* */
+  int32_t preconditioner; /* FLIP_PRECOND_* (flip_step; flip_solve_pressure and
+                             its no-alloc variant always use Jacobi) */
+  int32_t mg_smooth;     /* multigrid: red-black sweep pairs before and after the
+                            coarse correction, in [1, 8] */
 } flip_params;
 
 /* Fills p with the defaults of the 32^3 dam break: dx = 1/n, dt = 1/240,
  * g = (0, -9.81, 0), rho = 1, r = 0.95, skin = 1e-3*dx, cg_tol = 1e-6,
  * ir_tol = 1e-8, cg_max_iter = 20*max(n), ir_max_iter = 100, FP32, particle
- * advection. */
+ * advection, multigrid preconditioner with 2 sweep pairs. */
 void flip_default_params(flip_params* p, int32_t nx, int32_t ny, int32_t nz);
 
 /* Optional allocator: when given to flip_create, every device allocation of
@@ -199,7 +212,8 @@ const char* flip_last_error(void);
  * type: device uint8[n_cells] (1 fluid, anything else air); b: device
  * float32[n_cells] (read on fluid cells only); p: device float32[n_cells],
  * written on every cell (0 off fluid).  Uses params->n, dx, dt, rho, cg_tol,
- * cg_max_iter (FP32 mode; precision must be FLIP_PREC_FP32).  Scratch memory is
+ * cg_max_iter (FP32 mode; precision must be FLIP_PREC_FP32; Jacobi preconditioner
+ * whatever params->preconditioner says).  Scratch memory is
  * allocated and freed with cudaMallocAsync/cudaFreeAsync on stream.  Waits for
  * the stream before returning; *iterations (nullable) gets the iteration count
  * and *rel_residual (nullable) the final ||r||/||b||. */

@@ -20,7 +20,8 @@ class OracleParams(C.Structure):
     _fields_ = [("n", C.c_int32 * 3), ("dx", C.c_double), ("dt", C.c_double),
                 ("gravity", C.c_double * 3), ("rho", C.c_double), ("flip_ratio", C.c_double),
                 ("skin", C.c_double), ("cg_tol", C.c_double), ("cg_max_iter", C.c_int32),
-                ("advect_source", C.c_int32)]
+                ("advect_source", C.c_int32), ("preconditioner", C.c_int32), ("mg_nu", C.c_int32),
+                ("mg_omega", C.c_double)]
 
 
 class OracleStats(C.Structure):
@@ -91,6 +92,9 @@ class Params:
     cg_tol: float = 1e-6
     cg_max_iter: int = 0       # default 20 * max(n)
     advect_source: int = 0
+    preconditioner: int = 1    # 0 Jacobi, 1 multigrid V-cycle
+    mg_nu: int = 2
+    mg_omega: float = 2.0
 
     def c(self) -> OracleParams:
         p = OracleParams()
@@ -103,6 +107,9 @@ class Params:
         p.cg_tol = float(self.cg_tol)
         p.cg_max_iter = int(self.cg_max_iter or 20 * max(self.n))
         p.advect_source = int(self.advect_source)
+        p.preconditioner = int(self.preconditioner)
+        p.mg_nu = int(self.mg_nu)
+        p.mg_omega = float(self.mg_omega)
         return p
 
 

@@ -430,7 +430,9 @@ int oracle_step(const oracle_params* P, int64_t np, double* x, double* y, double
     double rel = 0.0;
     int iters = 0;
     if (status == 0) {
-      iters = oracle_pcg(P, type, b, P->cg_tol, P->cg_max_iter, p, &rel);
+      iters = (P->preconditioner == 1)
+                  ? oracle_pcg_mg(P, type, b, P->cg_tol, P->cg_max_iter, P->mg_nu, P->mg_omega, p, &rel)
+                  : oracle_pcg(P, type, b, P->cg_tol, P->cg_max_iter, p, &rel);
       if (iters < 0) status = 1;
       for (int d = 0; d < 3; ++d) oracle_project(P, d, us[d], p, type, un[d]);
       const double* unc[3] = {un[0], un[1], un[2]};

@@ -40,6 +40,9 @@ typedef struct {
   double cg_tol;       /* PCG stop: ||r||_2 <= cg_tol * ||b||_2 */
   int32_t cg_max_iter; /* PCG iteration cap */
   int32_t advect_source; /* 0: advect with the blended particle velocity; 1: with the grid velocity */
+  int32_t preconditioner; /* 0: Jacobi (oracle_pcg); 1: multigrid V-cycle (oracle_pcg_mg) */
+  int32_t mg_nu;          /* multigrid: red-black sweep pairs before and after the correction */
+  double mg_omega;        /* multigrid: over-correction of the coarse correction */
 } oracle_params;
 
 typedef struct {

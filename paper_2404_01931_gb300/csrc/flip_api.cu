@@ -84,6 +84,8 @@ struct flip_handle {
   float* pb = nullptr;
   float* q = nullptr;
   double* partials = nullptr;
+  MgArgs mg{};            // level shapes and scales (pointers filled by carve)
+  int mg_dims[MG_MAX_LEVELS][3] = {};
   unsigned int* bar = nullptr;
   DevStats* dstats = nullptr;
   DevStats* hstats = nullptr;  // pinned
@@ -137,6 +139,8 @@ void flip_default_params(flip_params* p, int32_t nx, int32_t ny, int32_t nz) {
   p->ir_max_iter = 100;
   p->precision = FLIP_PREC_FP32;
   p->advect_source = FLIP_ADVECT_PARTICLE;
+  p->preconditioner = FLIP_PRECOND_MG;
+  p->mg_smooth = 2;
 }
 
 }  // extern "C"
@@ -163,6 +167,10 @@ int check_params(const flip_params* p, bool need_particles_prm) {
   if (p->precision == FLIP_PREC_MIXED_IR && (!(p->ir_tol > 0.0) || !(p->cg_tol < 1.0)))
     return fail(FLIP_E_ARG, "mixed mode needs ir_tol > 0 and a refinement trigger cg_tol < 1");
   if (need_particles_prm) {
+    if (p->preconditioner != FLIP_PRECOND_JACOBI && p->preconditioner != FLIP_PRECOND_MG)
+      return fail(FLIP_E_ARG, "unknown preconditioner");
+    if (p->preconditioner == FLIP_PRECOND_MG && (p->mg_smooth < 1 || p->mg_smooth > 8))
+      return fail(FLIP_E_ARG, "mg_smooth must be in [1, 8]");
     if (!(p->flip_ratio >= 0.0 && p->flip_ratio <= 1.0))
       return fail(FLIP_E_ARG, "flip_ratio must be in [0, 1]");
     if (!(p->skin > 0.0 && p->skin < p->dx)) return fail(FLIP_E_ARG, "skin must be in (0, dx)");
@@ -219,6 +227,28 @@ StepConsts make_consts(const flip_params& p) {
   return k;
 }
 
+// Level shapes and scales of the multigrid hierarchy (pointers left empty).
+void setup_mg(MgArgs& m, int dims[MG_MAX_LEVELS][3], const flip_params& p) {
+  m.nlev = mg_level_dims(p.n[0], p.n[1], p.n[2], dims);
+  m.nu = p.mg_smooth;
+  m.omega = MG_OMEGA;
+  for (int c = 0; c < 8; ++c) m.inv_cnt[c] = c > 0 ? 1.0f / (float)c : 0.0f;
+  m.lgrid = m.nlev;
+  for (int l = 0; l < m.nlev; ++l) {
+    MgLevel& L = m.lv[l];
+    L.nx = dims[l][0];
+    L.ny = dims[l][1];
+    L.nz = dims[l][2];
+    L.ncells = L.nx * L.ny * L.nz;
+    const double h = p.dx * (double)(1 << l);
+    const double s = p.dt / (p.rho * h * h);
+    L.s = (float)s;
+    for (int c = 0; c < 8; ++c) L.inv_scnt[c] = c > 0 ? (float)(1.0 / (s * c)) : 0.0f;
+    if (l >= 1 && L.ncells <= MG_CTA_CELLS && m.lgrid == m.nlev) m.lgrid = l;
+  }
+  if (m.nlev == 1) m.lgrid = 1;
+}
+
 void fill_pcg_tables(PcgArgs& a, const flip_params& p) {
   const double s = p.dt / (p.rho * p.dx * p.dx);
   a.s = (float)s;
@@ -268,6 +298,15 @@ void carve(flip_handle* h, Carver& cv) {
   h->pb = cv.take<float>(nc);
   h->q = cv.take<float>(nc);
   h->partials = cv.take<double>((size_t)PCG_SLOTS * (size_t)h->pcg_blocks);
+  if (h->prm.preconditioner == FLIP_PRECOND_MG) {
+    h->mg.lv[0].x = cv.take<float>(nc);
+    for (int l = 1; l < h->mg.nlev; ++l) {
+      const size_t n = (size_t)h->mg.lv[l].ncells;
+      h->mg.lv[l].x = cv.take<float>(n);
+      h->mg.lv[l].b = cv.take<float>(n);
+      h->mg.lv[l].t = cv.take<uint8_t>(n);
+    }
+  }
   h->bar = cv.take<unsigned int>(2);
   h->dstats = cv.take<DevStats>(1);
   h->norms = cv.take<double>(2);
@@ -318,6 +357,11 @@ PcgArgs pcg_args(flip_handle* h) {
   a.ir_max_iter = h->prm.ir_max_iter;
   a.check_singular = 1;
   a.timeout_ns = 5000000000ull;
+  a.precond = h->prm.preconditioner;
+  if (a.precond == FLIP_PRECOND_MG) {
+    a.mg = h->mg;
+    a.mg.lv[0].t = h->type;
+  }
   return a;
 }
 
@@ -385,6 +429,11 @@ int flip_create(const flip_params* params, const float* x, const float* y, const
   }
   e = pcg_max_blocks(&h->pcg_blocks, &h->sm_count);
   if (e != cudaSuccess) return cleanup(cuda_fail(e, "occupancy query"));
+  if (params->preconditioner == FLIP_PRECOND_MG) {
+    e = pcg_mg_check_occupancy();
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "multigrid kernel occupancy"));
+    setup_mg(h->mg, h->mg_dims, *params);
+  }
   h->p2g_blocks = h->sm_count * 4;
 
   Carver measure;
@@ -476,7 +525,8 @@ int flip_step(flip_handle* h, int32_t nsteps, flip_stats* stats) {
                       h->dstats, s);
     h->launches += 1;
     if (timed) FLIP_CUDA(cudaEventRecord(ev[3], s));
-    FLIP_CUDA(launch_pcg(pa, h->mixed, h->pcg_blocks, s));
+    if (pa.precond == FLIP_PRECOND_MG) FLIP_CUDA(launch_pcg_mg(pa, h->mixed, h->pcg_blocks, s));
+    else FLIP_CUDA(launch_pcg(pa, h->mixed, h->pcg_blocks, s));
     h->launches += 1;
     if (timed) FLIP_CUDA(cudaEventRecord(ev[4], s));
     launch_g2p(h->g, h->K, h->P[h->cur], h->B, uo, h->mixed ? nullptr : h->x32, h->pff,

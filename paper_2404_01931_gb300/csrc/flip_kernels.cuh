@@ -37,6 +37,31 @@ struct StepConsts {
 
 constexpr int PCG_SLOTS = 7;
 
+// Multigrid V-cycle preconditioner (levels coarsened 2x per axis until the
+// largest extent is <= 4; red-black Gauss-Seidel smoothing).
+constexpr int MG_MAX_LEVELS = 12;
+constexpr int MG_COARSE_SWEEPS = 8;   // red-black pairs each way on the coarsest level
+constexpr int MG_CTA_CELLS = 4096;    // levels this small run inside one CTA
+constexpr float MG_OMEGA = 2.0f;      // over-correction of the coarse correction
+
+struct MgLevel {
+  int nx, ny, nz, ncells;
+  float inv_scnt[8];  // 1 / (s_l * count), s_l = dt / (rho (2^l dx)^2)
+  float s;
+  float* x;           // level solution (level 0: the preconditioned residual z)
+  float* b;           // level right-hand side (level 0: unused, the CG residual is read)
+  uint8_t* t;         // fluid flags (level 0: the cell types)
+};
+
+struct MgArgs {
+  int nlev;           // levels, >= 1
+  int lgrid;          // levels [lgrid, nlev) run inside CTA 0
+  int nu;             // red-black pairs before and after the coarse correction
+  float omega;
+  float inv_cnt[8];   // 1 / count
+  MgLevel lv[MG_MAX_LEVELS];
+};
+
 struct PcgArgs {
   Grid g;
   float diag_tab[8];   // dt/(rho dx^2) * count
@@ -67,7 +92,13 @@ struct PcgArgs {
   int ir_max_iter;
   int check_singular;   // compare n_fluid with the cell count
   unsigned long long timeout_ns;
+  int precond;          // 0 Jacobi, 1 multigrid
+  MgArgs mg;
 };
+
+// Level shapes of the multigrid hierarchy for an (nx, ny, nz) grid; returns the
+// number of levels (dims[l] = ceil(dims[l-1] / 2) until max extent <= 4).
+int mg_level_dims(int nx, int ny, int nz, int dims[MG_MAX_LEVELS][3]);
 
 // Projected velocity on face node (a,b,c) of component D (Eq. 5 with gravity
 // and the wall condition): 0 on the domain planes, otherwise
@@ -122,6 +153,10 @@ void launch_f32_to_f64(const float* src, double* dst, long long n, cudaStream_t 
 int pcg_block_size();
 cudaError_t pcg_max_blocks(int* max_blocks, int* sm_count);
 cudaError_t launch_pcg(const PcgArgs& a, bool mixed, int nblocks, cudaStream_t s);
+
+// k_mg.cu
+cudaError_t launch_pcg_mg(const PcgArgs& a, bool mixed, int nblocks, cudaStream_t s);
+cudaError_t pcg_mg_check_occupancy();
 void launch_mark_bricks(const Grid& g, const uint8_t* type, unsigned int* brick_fluid,
                         cudaStream_t s);
 void launch_compact_bricks(const Grid& g, const unsigned int* brick_fluid,

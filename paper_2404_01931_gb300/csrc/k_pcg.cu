@@ -25,210 +25,9 @@
 // the true one, r = b - A x, evaluated in FP64 — iterative refinement without
 // restarting the Krylov direction.  The solve stops when the FP64 residual
 // satisfies ||b - A x|| <= ir_tol ||b||.
-#include "flip_kernels.cuh"
+#include "pcg_common.cuh"
 
 namespace flipk {
-
-constexpr int PCG_THREADS = 1024;
-constexpr int PCG_WARPS = PCG_THREADS / 32;
-
-// ------------------------------------------------------------ float pairs
-
-struct F2 {
-  float hi, lo;
-};
-
-__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
-  const float s = __fadd_rn(a.hi, b.hi);
-  const float bv = __fsub_rn(s, a.hi);
-  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bv)), __fsub_rn(b.hi, bv));
-  const float lo = __fadd_rn(__fadd_rn(a.lo, b.lo), e);
-  const float hi = __fadd_rn(s, lo);
-  return F2{hi, __fsub_rn(lo, __fsub_rn(hi, s))};
-}
-
-__device__ __forceinline__ F2 f2_of(const FF& f) { return F2{f.hi, f.lo}; }
-
-__device__ __forceinline__ F2 f2_warp_sum(F2 v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    F2 w;
-    w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
-    w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
-    v = f2_add(v, w);
-  }
-  return v;
-}
-
-// CTA-wide sum of K float pairs; the result is valid in thread 0 only.
-template <int K>
-__device__ __forceinline__ void cta_sum(F2 (&v)[K], F2* scratch) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int q = 0; q < K; ++q) v[q] = f2_warp_sum(v[q]);
-  if (lane == 0)
-#pragma unroll
-    for (int q = 0; q < K; ++q) scratch[q * PCG_WARPS + warp] = v[q];
-  __syncthreads();
-  if (warp == 0) {
-#pragma unroll
-    for (int q = 0; q < K; ++q) {
-      F2 s = scratch[q * PCG_WARPS + lane];
-      v[q] = f2_warp_sum(s);
-    }
-  }
-  __syncthreads();
-}
-
-// ------------------------------------------------------------ cell ownership
-
-struct Chunk {
-  unsigned int begin, end;  // slots of the active-cell index space
-};
-
-__device__ __forceinline__ Chunk my_chunk(unsigned int nact) {
-  const unsigned int total = nact * BRICK_CELLS;
-  unsigned int per = (total + gridDim.x - 1) / gridDim.x;
-  per = (per + 31u) & ~31u;
-  const unsigned int b = min(total, blockIdx.x * per);
-  return Chunk{b, min(total, b + per)};
-}
-
-struct CellRef {
-  int i, j, k;
-  int c;
-};
-
-template <class F>
-__device__ __forceinline__ void for_my_cells(const PcgArgs& A, const Chunk& ch, F&& f) {
-  const Grid& g = A.g;
-  for (unsigned int e = ch.begin + threadIdx.x; e < ch.end; e += PCG_THREADS) {
-    const unsigned int brick = A.active[e >> 9];
-    const int l = (int)(e & 511u);
-    const int i = (int)(brick % (unsigned)g.bx) * BRICK + (l & 7);
-    const int j = (int)((brick / (unsigned)g.bx) % (unsigned)g.by) * BRICK + ((l >> 3) & 7);
-    const int k = (int)(brick / ((unsigned)g.bx * (unsigned)g.by)) * BRICK + (l >> 6);
-    if (i >= g.nx || j >= g.ny || k >= g.nz) continue;
-    const int c = i + g.nx * (j + g.ny * k);
-    if (A.type[c] != 1) continue;
-    f(CellRef{i, j, k, c});
-  }
-}
-
-// The six neighbours of a cell: index (the cell itself when outside the grid)
-// and whether it is a fluid cell.  All loads are issued before any is used.
-struct Nbrs {
-  int idx[6];
-  bool fl[6];
-  int cnt[6];
-};
-
-__device__ __forceinline__ Nbrs neighbours(const PcgArgs& A, const CellRef& cr) {
-  const Grid& g = A.g;
-  const int sy = g.nx, sz = g.nx * g.ny;
-  Nbrs n;
-  const bool in[6] = {cr.i > 0, cr.i < g.nx - 1, cr.j > 0, cr.j < g.ny - 1, cr.k > 0,
-                      cr.k < g.nz - 1};
-  const int off[6] = {-1, 1, -sy, sy, -sz, sz};
-#pragma unroll
-  for (int q = 0; q < 6; ++q) n.idx[q] = in[q] ? cr.c + off[q] : cr.c;
-  uint8_t t[6];
-#pragma unroll
-  for (int q = 0; q < 6; ++q) t[q] = A.type[n.idx[q]];
-#pragma unroll
-  for (int q = 0; q < 6; ++q) n.fl[q] = in[q] && t[q] == 1;
-  n.cnt[0] = nonsolid_count(g, cr.i - 1, cr.j, cr.k);
-  n.cnt[1] = nonsolid_count(g, cr.i + 1, cr.j, cr.k);
-  n.cnt[2] = nonsolid_count(g, cr.i, cr.j - 1, cr.k);
-  n.cnt[3] = nonsolid_count(g, cr.i, cr.j + 1, cr.k);
-  n.cnt[4] = nonsolid_count(g, cr.i, cr.j, cr.k - 1);
-  n.cnt[5] = nonsolid_count(g, cr.i, cr.j, cr.k + 1);
-  return n;
-}
-
-// p_new of a cell = z + beta p_old with z = r / diag.  One expression, so the
-// owner of a cell and its neighbours compute the same bits.
-__device__ __forceinline__ float p_update(float r, float pold, float minv, float beta) {
-  return __fmaf_rn(beta, pold, __fmul_rn(r, minv));
-}
-
-__device__ __forceinline__ void phase_a_cell(const PcgArgs& A, const CellRef& cr,
-                                             const float* pold, float* pnew, float beta,
-                                             FF& pq) {
-  const Nbrs n = neighbours(A, cr);
-  const int cnt = nonsolid_count(A.g, cr.i, cr.j, cr.k);
-  float rv[6], pv[6];
-#pragma unroll
-  for (int q = 0; q < 6; ++q) {
-    rv[q] = A.r[n.idx[q]];
-    pv[q] = pold[n.idx[q]];
-  }
-  const float pc = p_update(A.r[cr.c], pold[cr.c], A.minv_tab[cnt], beta);
-  float nb = 0.0f;
-#pragma unroll
-  for (int q = 0; q < 6; ++q)
-    nb += n.fl[q] ? p_update(rv[q], pv[q], A.minv_tab[n.cnt[q]], beta) : 0.0f;
-  const float qc = __fmaf_rn(A.diag_tab[cnt], pc, -__fmul_rn(A.s, nb));
-  pnew[cr.c] = pc;
-  A.q[cr.c] = qc;
-  pq.add_prod(pc, qc);
-}
-
-// FP64 residual of one cell for the refinement: b - A x with x in FP64.
-__device__ __forceinline__ double residual64(const PcgArgs& A, const CellRef& cr) {
-  const Nbrs n = neighbours(A, cr);
-  double xv[6];
-#pragma unroll
-  for (int q = 0; q < 6; ++q) xv[q] = A.x64[n.idx[q]];
-  double nb = 0.0;
-#pragma unroll
-  for (int q = 0; q < 6; ++q) nb += n.fl[q] ? xv[q] : 0.0;
-  const int cnt = nonsolid_count(A.g, cr.i, cr.j, cr.k);
-  return A.b64[cr.c] - A.s64 * ((double)cnt * A.x64[cr.c] - nb);
-}
-
-// ------------------------------------------------------------ reductions
-
-struct Shared {
-  F2 scratch[3 * PCG_WARPS];
-  float alpha, beta;
-  int flag;
-  double dscal[4];
-};
-
-template <int K>
-__device__ __forceinline__ void publish(const PcgArgs& A, int slot, F2 (&v)[K], Shared& sh) {
-  cta_sum<K>(v, sh.scratch);
-  if (threadIdx.x == 0) {
-    float2* part = reinterpret_cast<float2*>(A.partials);
-#pragma unroll
-    for (int q = 0; q < K; ++q)
-      part[(size_t)(slot + q) * gridDim.x + blockIdx.x] = make_float2(v[q].hi, v[q].lo);
-  }
-}
-
-// After a barrier: the grid-wide sums of the published pairs, in FP64, valid in
-// thread 0.  Every CTA adds the same pairs in the same order.
-template <int K>
-__device__ __forceinline__ void gather(const PcgArgs& A, int slot, double (&out)[K], Shared& sh) {
-  const float2* part = reinterpret_cast<const float2*>(A.partials);
-  F2 v[K];
-#pragma unroll
-  for (int q = 0; q < K; ++q) v[q] = F2{0.0f, 0.0f};
-  if (threadIdx.x < 32) {
-    for (unsigned int j = threadIdx.x; j < gridDim.x; j += 32)
-#pragma unroll
-      for (int q = 0; q < K; ++q) {
-        const float2 p = part[(size_t)(slot + q) * gridDim.x + j];
-        v[q] = f2_add(v[q], F2{p.x, p.y});
-      }
-#pragma unroll
-    for (int q = 0; q < K; ++q) v[q] = f2_warp_sum(v[q]);
-  }
-#pragma unroll
-  for (int q = 0; q < K; ++q) out[q] = (double)v[q].hi + (double)v[q].lo;
-  (void)sh;
-}
 
 // ------------------------------------------------------------ the solve
 

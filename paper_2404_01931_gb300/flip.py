@@ -33,6 +33,8 @@ FLIP_PREC_FP32 = 0
 FLIP_PREC_MIXED_IR = 1
 FLIP_ADVECT_PARTICLE = 0
 FLIP_ADVECT_GRID = 1
+FLIP_PRECOND_JACOBI = 0
+FLIP_PRECOND_MG = 1
 
 (PX, PY, PZ, PU, PV, PW, PID, U_OLD, V_OLD, W_OLD, U_NEW, V_NEW, W_NEW, PRESSURE,
  PRESSURE_F64, RHS, CELL_TYPE) = range(17)
@@ -54,7 +56,8 @@ class FlipParams(C.Structure):
                 ("gravity", C.c_double * 3), ("rho", C.c_double), ("flip_ratio", C.c_double),
                 ("skin", C.c_double), ("cg_tol", C.c_double), ("ir_tol", C.c_double),
                 ("cg_max_iter", C.c_int32), ("ir_max_iter", C.c_int32),
-                ("precision", C.c_int32), ("advect_source", C.c_int32)]
+                ("precision", C.c_int32), ("advect_source", C.c_int32),
+                ("preconditioner", C.c_int32), ("mg_smooth", C.c_int32)]
 
 
 class FlipStats(C.Structure):
@@ -113,7 +116,7 @@ def lib():
                                           C.POINTER(C.c_double)]
         L.flip_solve_pressure_noalloc.argtypes = [PP, vp, vp, vp, vp, C.POINTER(i32),
                                                   C.POINTER(C.c_double)]
-        if L.flip_abi_version() != 1:
+        if L.flip_abi_version() != 2:
             raise RuntimeError("libflip_gb300 ABI version mismatch")
         _lib = L
     return _lib

@@ -36,7 +36,8 @@ def flip_params(n, dx=None, **kw) -> F.FlipParams:
 def matched(n, **kw):
     """(oracle params, library params) describing the same scene settings."""
     okw = {k: v for k, v in kw.items() if k in ("dt", "gravity", "rho", "flip_ratio", "cg_tol",
-                                                "cg_max_iter", "advect_source", "skin")}
+                                                "cg_max_iter", "advect_source", "skin",
+                                                "preconditioner")}
     fkw = {k: v for k, v in kw.items() if k not in ("skin",)}
     fp = flip_params(n, **fkw)
     if "skin" in kw:
@@ -44,6 +45,8 @@ def matched(n, **kw):
     op = oracle_params(n, **okw)
     if "cg_max_iter" not in kw:
         op.cg_max_iter = fp.cg_max_iter
+    op.preconditioner = fp.preconditioner
+    op.mg_nu = fp.mg_smooth
     return op, fp
 
 

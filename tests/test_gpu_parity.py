@@ -56,16 +56,57 @@ def _compare_particles(ref, got, dx, pos_cells=1e-4, vel_tol=1e-5, vfloor=9.81 /
 
 # ------------------------------------------------------------- single steps
 
-def test_dam_break_32_single_step():
+@pytest.mark.parametrize("precond", [F.FLIP_PRECOND_JACOBI, F.FLIP_PRECOND_MG])
+def test_dam_break_32_single_step(precond):
     sc = S.dam_break(32)
-    op, fp = matched(32)
+    op, fp = matched(32, preconditioner=precond)
     ref = O.step(op, *sc.arrays())
     got = gpu_step(fp, sc.arrays())
     assert got["rc"] == F.FLIP_OK
     assert got["stats"].n_fluid_cells == ref.n_fluid == 4096
+    # same algorithm on both sides: the iteration counts agree (FP32 vs FP64 rounding
+    # may move the stopping iteration by one)
+    assert abs(got["stats"].cg_iterations - ref.cg_iterations) <= 1
     _compare_fields(ref, got, 32, label="C1")
     _compare_particles(ref, got, 1 / 32)
 
+
+@pytest.mark.parametrize("n", [64, (40, 24, 56)])
+@pytest.mark.parametrize("k", [1, 4])
+def test_multigrid_pcg_iterates_match_the_oracle(n, k):
+    """The GPU V-cycle is the oracle's V-cycle: after exactly k MG-PCG iterations
+    (tolerance out of reach, iteration cap k on both sides) the pressure iterates
+    agree to FP32-vs-FP64 rounding; a different preconditioner would change the
+    early iterates at O(1)."""
+    sc = S.pool_drop(n) if np.isscalar(n) else S.random_velocities(
+        S.box(n, (0.0, 0.0, 0.0), (0.6, 0.45, 0.9), seed=3), 0.3, 5)
+    op, fp = matched(n, cg_tol=1e-30, cg_max_iter=k)
+    ref = O.step(op, *sc.arrays())
+    assert ref.cg_iterations == -1  # the cap was reached
+    with pytest.warns(RuntimeWarning):
+        got = gpu_step(fp, sc.arrays())
+    assert got["rc"] == F.FLIP_E_NOT_CONVERGED and got["stats"].cg_iterations == k
+    e = rel_l2(got["p"], ref.pressure)
+    assert e <= 1e-5, f"pressure after {k} MG-PCG iterations: rel L2 {e:.3e}"
+
+
+@pytest.mark.parametrize("n,mixed", [(64, False), (96, True)])
+def test_multigrid_iteration_counts_match_the_oracle(n, mixed):
+    """Same tolerance, same right-hand side: iteration counts within a few, and (mixed
+    mode, converged to 1e-8) the same solution as the oracle's tight solve."""
+    sc = S.pool_drop(n)
+    tol = 1e-8 if mixed else 1e-6
+    op, fp = matched(n, cg_tol=tol)
+    ref = O.step(op, *sc.arrays())
+    if mixed:
+        fp.cg_tol, fp.ir_tol = 0.1, 1e-8
+    got = gpu_step(fp, sc.arrays(), precision=F.FLIP_PREC_MIXED_IR if mixed else None)
+    st = got["stats"]
+    assert ref.cg_iterations <= 25
+    assert abs(st.cg_iterations - ref.cg_iterations) <= 3, (st.cg_iterations, ref.cg_iterations)
+    if mixed:
+        tight = O.step(matched(n, cg_tol=1e-12)[0], *sc.arrays())
+        _compare_fields(tight, got, n, label=f"mg {n} mixed")
 
 def test_random_velocity_box_single_step():
     sc = S.random_velocities(S.box(24, (0.1, 0.0, 0.2), (0.7, 0.55, 0.9), seed=11), 0.8, 3)
