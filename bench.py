@@ -32,9 +32,9 @@ sys.path.insert(0, ROOT)
 
 WORKLOADS = {
     "pool256": dict(desc="drop into pool, 256^3, depth 0.3 + sphere r=0.15 at (0.5,0.7,0.5)",
-                    n=256, scene="pool", precision="mixed", cg_tol=0.1, ir_tol=1e-8),
+                    n=256, scene="pool", precision="mixed", cg_tol=1e-3, ir_tol=1e-8),
     "pool128": dict(desc="drop into pool, 128^3, depth 0.3 + sphere r=0.15 at (0.5,0.7,0.5)",
-                    n=128, scene="pool", precision="mixed", cg_tol=0.1, ir_tol=1e-8),
+                    n=128, scene="pool", precision="mixed", cg_tol=1e-3, ir_tol=1e-8),
     "dam128": dict(desc="dam break, 128^3, block x<0.25 y<0.5", n=128, scene="dam",
                    precision="fp32", cg_tol=1e-6, ir_tol=1e-8),
     "dam32": dict(desc="dam break, 32^3, block x<0.25 y<0.5", n=32, scene="dam",
@@ -217,8 +217,12 @@ def main():
     ap.add_argument("--workload", default="pool256", choices=sorted(WORKLOADS))
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cg-tol", type=float, default=None,
+                    help="override the workload's cg_tol (mixed mode: refinement trigger)")
     args = ap.parse_args()
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    if args.cg_tol is not None:
+        w["cg_tol"] = args.cg_tol
     if args.impl == "reference":
         return run_reference(args, w)
     ws, rank, local = dist_setup()

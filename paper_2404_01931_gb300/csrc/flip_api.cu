@@ -307,7 +307,7 @@ void carve(flip_handle* h, Carver& cv) {
       h->mg.lv[l].t = cv.take<uint8_t>(n);
     }
   }
-  h->bar = cv.take<unsigned int>(2);
+  h->bar = cv.take<unsigned int>(BAR_WORDS);
   h->dstats = cv.take<DevStats>(1);
   h->norms = cv.take<double>(2);
   const size_t nfmax = (size_t)std::max(h->nf[0], std::max(h->nf[1], h->nf[2]));
@@ -761,7 +761,7 @@ int flip_solve_pressure(const flip_params* params, const uint8_t* type, const fl
     *bf = c.take<unsigned int>(nb);
     *act = c.take<unsigned int>(nb);
     *part = c.take<double>((size_t)PCG_SLOTS * blocks);
-    *bar = c.take<unsigned int>(2);
+    *bar = c.take<unsigned int>(BAR_WORDS);
     *st = c.take<DevStats>(1);
   };
   float *r, *pa_, *pb_, *q;

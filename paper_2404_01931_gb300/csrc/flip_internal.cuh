@@ -161,10 +161,13 @@ __device__ __forceinline__ void st_release_gpu(unsigned int* p, unsigned int v) 
 }
 
 // Grid-wide barrier for a cooperative launch (all CTAs co-resident).  bar[0]
-// counts arrivals, bar[1] is the generation.  Every wait is bounded: after
-// timeout_ns without progress the CTA sets DEV_TIMEOUT in *status and returns
-// false; a CTA that sees another one's failure returns false too.  Callers stop
-// their loop on false, so no CTA is left waiting.
+// counts arrivals, bar[1] is the generation; the rest of the BAR_WORDS-word block
+// is spare and kept zero.  Every wait is bounded: after timeout_ns without
+// progress the CTA sets DEV_TIMEOUT in *status and returns false; a CTA that sees
+// another one's failure returns false too.  Callers stop their loop on false, so
+// no CTA is left waiting.
+constexpr unsigned int BAR_WORDS = 64;
+
 __device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* status, unsigned int nblocks,
                                              unsigned long long timeout_ns) {
   __shared__ int s_ok;

@@ -83,7 +83,7 @@ struct PcgArgs {
   double* partials;     // [PCG_SLOTS * max_blocks]: one slot per reduced value
                         // of each phase, so no slot is rewritten before all
                         // CTAs have read it
-  unsigned int* bar;    // [2] grid barrier
+  unsigned int* bar;    // [BAR_WORDS] grid barrier
   int* status;          // DevStats::status
   DevStats* stats;
   double tol;           // FP32 stop / mixed inner stop

@@ -38,7 +38,7 @@ constexpr size_t kOffBrickFluid = kOffQ + al(sizeof(float) * kMaxCells);
 constexpr size_t kOffActive = kOffBrickFluid + al(sizeof(unsigned int) * kMaxBricks);
 constexpr size_t kOffPartials = kOffActive + al(sizeof(unsigned int) * kMaxBricks);
 constexpr size_t kOffBar = kOffPartials + al(sizeof(double) * PCG_SLOTS * kMaxBlocks);
-constexpr size_t kOffStats = kOffBar + al(sizeof(unsigned int) * 2);
+constexpr size_t kOffStats = kOffBar + al(sizeof(unsigned int) * BAR_WORDS);
 constexpr size_t kScratchBytes = kOffStats + al(sizeof(DevStats));
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];

@@ -136,26 +136,54 @@ __device__ __forceinline__ float level_residual(const MgLevel& L, const float* b
 
 // ---------------------------------------------------------------- sweeps
 
-// Half-sweep of one colour over level l >= 1 (dense partition).
+// Half-sweep of one colour over level l >= 1.  Threads map onto the cells of
+// the sweep colour: each x-row has ceil(nx/2) slots, slot q of row (j, k) is
+// x = 2q + parity (skipped when it falls off an odd-length row).
 template <int MODE>
 __device__ __forceinline__ void sweep_level(const MgArgs& M, int l, int colour, bool cta_local) {
   const MgLevel& L = M.lv[l];
-  for_level_cells(L, level_part(L.ncells, cta_local), [&](const LCell& e) {
-    if (((e.i + e.j + e.k) & 1) != colour) return;
-    L.x[e.c] = gs_value<MODE>(M, l, e.i, e.j, e.k, e.c, L.b[e.c]);
-  });
+  const int hx = (L.nx + 1) >> 1;
+  const Part p = level_part(hx * L.ny * L.nz, cta_local);
+  for (int e = p.begin; e < p.end; e += p.stride) {
+    const int row = e / hx, q = e - row * hx;
+    const int j = row % L.ny, k = row / L.ny;
+    const int i = 2 * q + ((colour + j + k) & 1);
+    if (i >= L.nx) continue;
+    const int c = i + L.nx * row;
+    if (L.t[c] != 1) continue;
+    L.x[c] = gs_value<MODE>(M, l, i, j, k, c, L.b[c]);
+  }
 }
 
-// Half-sweep of one colour over level 0 (the CG's active-cell chunk); the
-// right-hand side is the CG residual r.
+// Half-sweep of one colour over level 0; the right-hand side is the CG residual
+// r.  Threads map straight onto the cells of the sweep colour: slot e of the
+// colour's index space (256 cells per brick) is brick e/256, row m/4 of the
+// brick (y fastest within z) and x position 2(m%4) + parity, so no lane idles on
+// a cell of the other colour.  Slices are contiguous per CTA as for the CG.
 template <int MODE>
 __device__ __forceinline__ void sweep_level0(const PcgArgs& A, const Chunk& ch, int colour) {
+  (void)ch;
   const MgArgs& M = A.mg;
   const MgLevel& L = M.lv[0];
-  for_my_cells(A, ch, [&](const CellRef& cr) {
-    if (((cr.i + cr.j + cr.k) & 1) != colour) return;
-    L.x[cr.c] = gs_value<MODE>(M, 0, cr.i, cr.j, cr.k, cr.c, A.r[cr.c]);
-  });
+  const Grid& g = A.g;
+  const unsigned int nact = *A.n_active;
+  const unsigned int total = nact * (BRICK_CELLS / 2);
+  unsigned int per = (total + gridDim.x - 1) / gridDim.x;
+  per = (per + 31u) & ~31u;
+  const unsigned int b = min(total, blockIdx.x * per), e_end = min(total, b + per);
+  for (unsigned int e = b + threadIdx.x; e < e_end; e += PCG_THREADS) {
+    const unsigned int brick = A.active[e >> 8];
+    const int m = (int)(e & 255u);
+    const int lj = (m >> 2) & 7, lk = m >> 5;
+    const int li = 2 * (m & 3) + ((colour + lj + lk) & 1);
+    const int i = (int)(brick % (unsigned)g.bx) * BRICK + li;
+    const int j = (int)((brick / (unsigned)g.bx) % (unsigned)g.by) * BRICK + lj;
+    const int k = (int)(brick / ((unsigned)g.bx * (unsigned)g.by)) * BRICK + lk;
+    if (i >= g.nx || j >= g.ny || k >= g.nz) continue;
+    const int c = i + g.nx * (j + g.ny * k);
+    if (A.type[c] != 1) continue;
+    L.x[c] = gs_value<MODE>(M, 0, i, j, k, c, A.r[c]);
+  }
 }
 
 // b_{l+1} = (1/16) sum over fluid children of the level-l residual.
