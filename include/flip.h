@@ -208,6 +208,33 @@ void flip_destroy(flip_handle* h);
 const char* flip_strerror(int status);
 const char* flip_last_error(void);
 
+/* ---------------------------------------------------------------- batches
+ * Many independent scenes advanced together.  Per step: every scene's binning,
+ * P2G and right-hand side run on the scene's own stream (concurrently across
+ * scenes); then the pressure solves of all scenes run in one cooperative
+ * launch per (precision, preconditioner) group, each scene on its own team of
+ * CTAs sized by its particle count, with per-scene barriers, reductions and
+ * convergence; then every scene's G2P runs on its own stream.  A scene's
+ * results are those of flip_step up to the order of floating-point sums. */
+typedef struct flip_batch flip_batch;
+
+/* A batch runner for up to capacity scenes (capacity <= 4096).  It owns small
+ * device buffers for the per-scene solver arguments and the stream the batched
+ * solves run on (stream: a cudaStream_t, NULL to create one); it owns no
+ * scene. */
+int flip_batch_create(int32_t capacity, void* stream, flip_batch** out);
+
+/* Advances the n distinct scenes hs[0..n-1] (n <= capacity, all on the current
+ * device) by nsteps steps each.  Stream-ordered with respect to each scene's
+ * stream.  stats (nullable) receives n entries, as flip_step's per scene, with
+ * ms_total the wall time of the whole call and ms_pcg the time of the batched
+ * solves; when stats is given the call waits and returns the first device-side
+ * condition of any scene. */
+int flip_batch_step(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t nsteps,
+                    flip_stats* stats);
+
+void flip_batch_destroy(flip_batch* b);
+
 /* Standalone pressure solve (Sec. 3.1.7): A p = b for the cell types in type.
  * type: device uint8[n_cells] (1 fluid, anything else air); b: device
  * float32[n_cells] (read on fluid cells only); p: device float32[n_cells],

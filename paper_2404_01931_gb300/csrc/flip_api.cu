@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <vector>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -734,6 +735,295 @@ int flip_write_particles(flip_handle* h, const float* x, const float* y, const f
   FLIP_CUDA(cudaStreamSynchronize(h->stream));
   return FLIP_OK;
 }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- batches
+
+struct flip_batch {
+  int capacity = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  PcgArgs* d_args = nullptr;     // [capacity]
+  int* d_block_scene = nullptr;  // [max CTAs]
+  int* d_team_first = nullptr;   // [capacity + 1]
+  int max_blocks = 0;
+  std::vector<cudaEvent_t> ev;   // one per scene slot
+  cudaEvent_t ev_begin = nullptr, ev_pcg0 = nullptr, ev_pcg1 = nullptr, ev_end = nullptr;
+  cudaEvent_t ev_solved = nullptr;
+};
+
+namespace {
+
+// Splits max_blocks CTAs over scenes in proportion to their particle counts,
+// at least one each (n <= max_blocks).  first has n+1 entries.
+void assign_teams(const std::vector<flip_handle*>& hs, int max_blocks, std::vector<int>& first) {
+  const int n = (int)hs.size();
+  std::vector<double> w(n);
+  double tot = 0.0;
+  for (int s = 0; s < n; ++s) {
+    w[s] = (double)std::max<long long>(hs[s]->np, 1);
+    tot += w[s];
+  }
+  std::vector<int> cnt(n, 1);
+  int left = max_blocks - n;
+  std::vector<std::pair<double, int>> rem;
+  for (int s = 0; s < n; ++s) {
+    const double share = left * w[s] / tot;
+    const int extra = (int)std::floor(share);
+    cnt[s] += extra;
+    rem.push_back({share - extra, s});
+  }
+  int used = 0;
+  for (int s = 0; s < n; ++s) used += cnt[s];
+  std::sort(rem.begin(), rem.end(), [](auto& x, auto& y) { return x.first > y.first; });
+  for (size_t q = 0; q < rem.size() && used < max_blocks; ++q, ++used) cnt[rem[q].second] += 1;
+  first.assign(n + 1, 0);
+  for (int s = 0; s < n; ++s) first[s + 1] = first[s] + cnt[s];
+}
+
+}  // namespace
+
+extern "C" {
+
+int flip_batch_create(int32_t capacity, void* stream, flip_batch** out) {
+  if (!out) return fail(FLIP_E_ARG, "out is NULL");
+  *out = nullptr;
+  if (capacity < 1 || capacity > 4096) return fail(FLIP_E_ARG, "capacity must be in [1, 4096]");
+  int rc = check_device();
+  if (rc) return rc;
+  flip_batch* b = new (std::nothrow) flip_batch();
+  if (!b) return fail(FLIP_E_OOM, "host allocation failed");
+  b->capacity = capacity;
+  int sms = 0;
+  cudaError_t e = pcg_max_blocks(&b->max_blocks, &sms);
+  auto bail = [&](cudaError_t err, const char* what) {
+    flip_batch_destroy(b);
+    return cuda_fail(err, what);
+  };
+  if (e != cudaSuccess) return bail(e, "occupancy query");
+  if (stream) {
+    b->stream = (cudaStream_t)stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(e, "cudaStreamCreate");
+    b->own_stream = true;
+  }
+  if ((e = cudaMalloc(&b->d_args, sizeof(PcgArgs) * (size_t)capacity)) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_block_scene, sizeof(int) * (size_t)b->max_blocks)) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_team_first, sizeof(int) * (size_t)(capacity + 1))) != cudaSuccess)
+    return bail(e, "cudaMalloc(batch)");
+  b->ev.resize(capacity, nullptr);
+  for (auto& ev : b->ev)
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+      return bail(e, "cudaEventCreate");
+  if ((e = cudaEventCreate(&b->ev_begin)) != cudaSuccess ||
+      (e = cudaEventCreate(&b->ev_pcg0)) != cudaSuccess ||
+      (e = cudaEventCreate(&b->ev_pcg1)) != cudaSuccess ||
+      (e = cudaEventCreate(&b->ev_end)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&b->ev_solved, cudaEventDisableTiming)) != cudaSuccess)
+    return bail(e, "cudaEventCreate");
+  *out = b;
+  return FLIP_OK;
+}
+
+void flip_batch_destroy(flip_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  for (auto ev : b->ev)
+    if (ev) cudaEventDestroy(ev);
+  for (cudaEvent_t ev : {b->ev_begin, b->ev_pcg0, b->ev_pcg1, b->ev_end, b->ev_solved})
+    if (ev) cudaEventDestroy(ev);
+  if (b->d_args) cudaFree(b->d_args);
+  if (b->d_block_scene) cudaFree(b->d_block_scene);
+  if (b->d_team_first) cudaFree(b->d_team_first);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+int flip_batch_step(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t nsteps,
+                    flip_stats* stats) {
+  if (!b || (!hs && n > 0)) return fail(FLIP_E_ARG, "batch or handles are NULL");
+  if (n < 0 || n > b->capacity) return fail(FLIP_E_ARG, "n must be in [0, capacity]");
+  if (nsteps < 0) return fail(FLIP_E_ARG, "nsteps must be >= 0");
+  for (int s = 0; s < n; ++s) {
+    if (!hs[s]) return fail(FLIP_E_ARG, "a handle is NULL");
+    for (int t = 0; t < s; ++t)
+      if (hs[t] == hs[s]) return fail(FLIP_E_ARG, "a scene appears twice in the batch");
+  }
+  if (n == 0) return FLIP_OK;
+  const cudaStream_t bs = b->stream;
+  // Group the scenes by solver kernel (precision x preconditioner); each group is
+  // one cooperative launch, in chunks of at most max_blocks scenes.
+  struct Launch {
+    bool mixed, mg;
+    std::vector<int> scenes;
+    int arg0;  // offset of the group's argument blocks
+  };
+  std::vector<Launch> launches;
+  for (int g = 0; g < 4; ++g) {
+    const bool mixed = g & 1, mg = g & 2;
+    std::vector<int> sc;
+    for (int s = 0; s < n; ++s)
+      if (hs[s]->mixed == mixed && (hs[s]->prm.preconditioner == FLIP_PRECOND_MG) == mg)
+        sc.push_back(s);
+    for (size_t c = 0; c < sc.size(); c += (size_t)b->max_blocks) {
+      Launch L{mixed, mg, {}, 0};
+      L.scenes.assign(sc.begin() + c, sc.begin() + std::min(sc.size(), c + (size_t)b->max_blocks));
+      launches.push_back(L);
+    }
+  }
+  // Argument blocks, CTA->scene tables: uploaded once for the call.
+  std::vector<PcgArgs> args;
+  std::vector<int> block_scene_all, first_all;
+  std::vector<int> bs_off, tf_off;
+  for (auto& L : launches) {
+    L.arg0 = (int)args.size();
+    std::vector<flip_handle*> hv;
+    for (int s : L.scenes) {
+      hv.push_back(hs[s]);
+      args.push_back(pcg_args(hs[s]));
+    }
+    std::vector<int> first;
+    assign_teams(hv, b->max_blocks, first);
+    bs_off.push_back((int)block_scene_all.size());
+    tf_off.push_back((int)first_all.size());
+    for (int t = 0; t < (int)hv.size(); ++t)
+      for (int c = first[t]; c < first[t + 1]; ++c) block_scene_all.push_back(t);
+    first_all.insert(first_all.end(), first.begin(), first.end());
+  }
+  if ((int)block_scene_all.size() > b->max_blocks * (int)launches.size() ||
+      (int)first_all.size() > b->capacity + 1 + (int)launches.size())
+    return fail(FLIP_E_ARG, "batch tables overflow");
+  // one table region per launch: block_scene entries need max_blocks per launch
+  std::vector<int*> d_bs(launches.size()), d_tf(launches.size());
+  std::vector<int*> tmp_alloc;
+  for (size_t q = 0; q < launches.size(); ++q) {
+    if (q == 0) {
+      d_bs[q] = b->d_block_scene;
+      d_tf[q] = b->d_team_first;
+    } else {  // rare: mixed groups in one call; small stream-ordered buffers
+      int* p1 = nullptr;
+      int* p2 = nullptr;
+      FLIP_CUDA(cudaMallocAsync(&p1, sizeof(int) * (size_t)b->max_blocks, bs));
+      FLIP_CUDA(cudaMallocAsync(&p2, sizeof(int) * (size_t)(b->capacity + 1), bs));
+      tmp_alloc.push_back(p1);
+      tmp_alloc.push_back(p2);
+      d_bs[q] = p1;
+      d_tf[q] = p2;
+    }
+    const size_t nb = (q + 1 < launches.size() ? bs_off[q + 1] : block_scene_all.size()) - bs_off[q];
+    const size_t nf = (q + 1 < launches.size() ? tf_off[q + 1] : first_all.size()) - tf_off[q];
+    FLIP_CUDA(cudaMemcpyAsync(d_bs[q], block_scene_all.data() + bs_off[q], sizeof(int) * nb,
+                              cudaMemcpyHostToDevice, bs));
+    FLIP_CUDA(cudaMemcpyAsync(d_tf[q], first_all.data() + tf_off[q], sizeof(int) * nf,
+                              cudaMemcpyHostToDevice, bs));
+  }
+  FLIP_CUDA(cudaMemcpyAsync(b->d_args, args.data(), sizeof(PcgArgs) * args.size(),
+                            cudaMemcpyHostToDevice, bs));
+  const bool timed = stats != nullptr;
+  std::vector<int> launches0(n);
+  for (int s = 0; s < n; ++s) launches0[s] = hs[s]->launches;
+  int batch_launches = 0;
+  if (timed) FLIP_CUDA(cudaEventRecord(b->ev_begin, bs));
+  // every scene stream starts after the call's uploads (and the begin event)
+  FLIP_CUDA(cudaEventRecord(b->ev_solved, bs));
+  for (int s = 0; s < n; ++s) FLIP_CUDA(cudaStreamWaitEvent(hs[s]->stream, b->ev_solved, 0));
+  float ms_pcg = 0.0f;
+  for (int st = 0; st < nsteps; ++st) {
+    for (int s = 0; s < n; ++s) {
+      flip_handle* h = hs[s];
+      const float* uo[3] = {h->uo[0], h->uo[1], h->uo[2]};
+      launch_bin(h->g, h->B, h->type, h->dstats, h->stream);
+      launch_scatter(h->P[h->cur], h->P[1 - h->cur], h->B, h->np, h->stream);
+      h->cur = 1 - h->cur;
+      launch_p2g(h->g, h->P[h->cur], h->B, h->acc, h->dstats, h->p2g_blocks, h->stream);
+      launch_finalize(h->g, h->acc, h->uo, h->stream);
+      launch_divergence(h->g, h->K, h->type, uo, h->b32, h->b64, h->x32, h->x64, h->pff, h->bar,
+                        h->dstats, h->stream);
+      h->launches += 5 + (h->np > 0);
+      FLIP_CUDA(cudaEventRecord(b->ev[s], h->stream));
+      FLIP_CUDA(cudaStreamWaitEvent(bs, b->ev[s], 0));
+    }
+    if (timed) FLIP_CUDA(cudaEventRecord(b->ev_pcg0, bs));
+    for (size_t q = 0; q < launches.size(); ++q) {
+      const Launch& L = launches[q];
+      PcgBatch pb{b->d_args + L.arg0, d_bs[q], d_tf[q], (int)L.scenes.size()};
+      const int nblk = first_all[tf_off[q] + (int)L.scenes.size()];
+      if (L.mg) FLIP_CUDA(launch_pcg_mg_batch(pb, L.mixed, nblk, bs));
+      else FLIP_CUDA(launch_pcg_batch(pb, L.mixed, nblk, bs));
+      ++batch_launches;
+    }
+    if (timed) FLIP_CUDA(cudaEventRecord(b->ev_pcg1, bs));
+    FLIP_CUDA(cudaEventRecord(b->ev_solved, bs));
+    for (int s = 0; s < n; ++s) {
+      flip_handle* h = hs[s];
+      const float* uo[3] = {h->uo[0], h->uo[1], h->uo[2]};
+      FLIP_CUDA(cudaStreamWaitEvent(h->stream, b->ev_solved, 0));
+      launch_g2p(h->g, h->K, h->P[h->cur], h->B, uo, h->mixed ? nullptr : h->x32, h->pff,
+                 h->dstats, h->np, h->stream);
+      h->launches += (h->np > 0);
+      h->stepped = true;
+    }
+    FLIP_CUDA(cudaGetLastError());
+    if (timed) {
+      FLIP_CUDA(cudaEventSynchronize(b->ev_pcg1));
+      float t = 0.0f;
+      FLIP_CUDA(cudaEventElapsedTime(&t, b->ev_pcg0, b->ev_pcg1));
+      ms_pcg += t;
+    }
+  }
+  for (void* p : tmp_alloc) FLIP_CUDA(cudaFreeAsync(p, bs));
+  // the batch stream joins every scene stream at the end of the call
+  for (int s = 0; s < n; ++s) {
+    FLIP_CUDA(cudaEventRecord(b->ev[s], hs[s]->stream));
+    FLIP_CUDA(cudaStreamWaitEvent(bs, b->ev[s], 0));
+  }
+  if (!timed) return FLIP_OK;
+  FLIP_CUDA(cudaEventRecord(b->ev_end, bs));
+  FLIP_CUDA(cudaEventSynchronize(b->ev_end));
+  float ms_total = 0.0f;
+  FLIP_CUDA(cudaEventElapsedTime(&ms_total, b->ev_begin, b->ev_end));
+  int first_rc = FLIP_OK;
+  for (int s = 0; s < n; ++s) {
+    flip_handle* h = hs[s];
+    flip_stats* o = stats + s;
+    std::memset(o, 0, sizeof(*o));
+    const float* uo[3] = {h->uo[0], h->uo[1], h->uo[2]};
+    FLIP_CUDA(cudaMemsetAsync(h->norms, 0, 2 * sizeof(double), h->stream));
+    if (h->stepped) {
+      launch_div_norms(h->g, h->K, h->type, uo, h->mixed ? nullptr : h->x32, h->x64, h->norms,
+                       h->stream);
+      h->launches += 1;
+    }
+    double norms[2] = {0.0, 0.0};
+    FLIP_CUDA(cudaMemcpyAsync(norms, h->norms, sizeof(norms), cudaMemcpyDeviceToHost, h->stream));
+    const int rc = take_status(h);
+    if (rc != FLIP_OK && first_rc == FLIP_OK) first_rc = rc;
+    const DevStats& d = *h->hstats;
+    o->steps = nsteps;
+    o->n_particles = h->np;
+    o->n_fluid_cells = d.n_fluid;
+    o->n_active_bricks = d.n_active;
+    o->cg_iterations = d.cg_iters_total - h->reported_cg;
+    o->ir_iterations = (int32_t)(d.ir_iters_total - h->reported_ir);
+    h->reported_cg = d.cg_iters_total;
+    h->reported_ir = d.ir_iters_total;
+    o->kernel_launches = h->launches - launches0[s] + (s == 0 ? batch_launches : 0);
+    o->cg_rel_residual = d.rel_res;
+    o->rel_divergence = norms[0] > 0.0 ? std::sqrt(norms[1] / norms[0]) : 0.0;
+    float msf;
+    std::memcpy(&msf, &d.max_speed_bits, sizeof(float));
+    o->max_speed = msf;
+    o->ms_pcg = ms_pcg;
+    o->ms_total = ms_total;
+  }
+  return first_rc;
+}
+
+}  // extern "C"
+
+extern "C" {
 
 int flip_solve_pressure(const flip_params* params, const uint8_t* type, const float* b, float* p,
                         void* stream, int32_t* iterations, double* rel_residual) {

@@ -96,6 +96,16 @@ struct PcgArgs {
   MgArgs mg;
 };
 
+// Several scenes' solves in one cooperative launch: args[s] is scene s's
+// argument block (device memory), CTA b works on scene block_scene[b] in the
+// team of CTAs team_first[s] .. team_first[s+1]-1.
+struct PcgBatch {
+  const PcgArgs* args;
+  const int* block_scene;
+  const int* team_first;
+  int nscenes;
+};
+
 // Level shapes of the multigrid hierarchy for an (nx, ny, nz) grid; returns the
 // number of levels (dims[l] = ceil(dims[l-1] / 2) until max extent <= 4).
 int mg_level_dims(int nx, int ny, int nz, int dims[MG_MAX_LEVELS][3]);
@@ -154,8 +164,11 @@ int pcg_block_size();
 cudaError_t pcg_max_blocks(int* max_blocks, int* sm_count);
 cudaError_t launch_pcg(const PcgArgs& a, bool mixed, int nblocks, cudaStream_t s);
 
+cudaError_t launch_pcg_batch(const PcgBatch& b, bool mixed, int nblocks, cudaStream_t s);
+
 // k_mg.cu
 cudaError_t launch_pcg_mg(const PcgArgs& a, bool mixed, int nblocks, cudaStream_t s);
+cudaError_t launch_pcg_mg_batch(const PcgBatch& b, bool mixed, int nblocks, cudaStream_t s);
 cudaError_t pcg_mg_check_occupancy();
 void launch_mark_bricks(const Grid& g, const uint8_t* type, unsigned int* brick_fluid,
                         cudaStream_t s);

@@ -36,9 +36,9 @@ struct Part {
 // (grid-wide levels) or all cells by CTA 0's threads (CTA-local levels).
 __device__ __forceinline__ Part level_part(int ncells, bool cta_local) {
   if (cta_local) return Part{(int)threadIdx.x, ncells, PCG_THREADS};
-  int per = (ncells + (int)gridDim.x - 1) / (int)gridDim.x;
+  int per = (ncells + (int)team_size() - 1) / (int)team_size();
   per = (per + 31) & ~31;
-  const int b = min(ncells, (int)blockIdx.x * per);
+  const int b = min(ncells, (int)team_rank() * per);
   return Part{b + (int)threadIdx.x, min(ncells, b + per), PCG_THREADS};
 }
 
@@ -168,9 +168,9 @@ __device__ __forceinline__ void sweep_level0(const PcgArgs& A, const Chunk& ch, 
   const Grid& g = A.g;
   const unsigned int nact = *A.n_active;
   const unsigned int total = nact * (BRICK_CELLS / 2);
-  unsigned int per = (total + gridDim.x - 1) / gridDim.x;
+  unsigned int per = (total + team_size() - 1) / team_size();
   per = (per + 31u) & ~31u;
-  const unsigned int b = min(total, blockIdx.x * per), e_end = min(total, b + per);
+  const unsigned int b = min(total, team_rank() * per), e_end = min(total, b + per);
   for (unsigned int e = b + threadIdx.x; e < e_end; e += PCG_THREADS) {
     const unsigned int brick = A.active[e >> 8];
     const int m = (int)(e & 255u);
@@ -220,7 +220,7 @@ struct Sync {
       __syncthreads();
       return true;
     }
-    return grid_barrier(A->bar, A->status, gridDim.x, A->timeout_ns);
+    return grid_barrier(A->bar, A->status, team_size(), A->timeout_ns);
   }
 };
 
@@ -330,7 +330,7 @@ __device__ bool vcycle_rest(const PcgArgs& A, const Chunk& ch, FF& rz) {
     if (!gsync()) return false;
     for (int l = 1; l < M.lgrid; ++l)
       if (!down_level(A, l, false)) return false;
-    if (blockIdx.x == 0) cta_cycle(A);
+    if (team_rank() == 0) cta_cycle(A);
     if (!gsync()) return false;
     for (int l = M.lgrid - 1; l >= 1; --l)
       if (!up_level(A, l, false)) return false;
@@ -401,7 +401,7 @@ __device__ bool build_levels(const PcgArgs& A) {
       }
       C.t[c] = f;
     }
-    if (!grid_barrier(A.bar, A.status, gridDim.x, A.timeout_ns)) return false;
+    if (!grid_barrier(A.bar, A.status, team_size(), A.timeout_ns)) return false;
   }
   return true;
 }
@@ -438,7 +438,7 @@ __device__ void solve_mg(const PcgArgs& A, const Chunk& ch, Shared& sh, SolveSta
     F2 v[1] = {f2_of(bb)};
     publish<1>(A, 4, v, sh);
   }
-  if (!grid_barrier(A.bar, A.status, gridDim.x, A.timeout_ns)) { S.ok = false; return; }
+  if (!grid_barrier(A.bar, A.status, team_size(), A.timeout_ns)) { S.ok = false; return; }
   double rz = 0.0, bnorm = 0.0, rnorm = 0.0, rmax = 0.0;
   const double target = MIXED ? A.ir_tol : A.tol;
   {
@@ -462,7 +462,7 @@ __device__ void solve_mg(const PcgArgs& A, const Chunk& ch, Shared& sh, SolveSta
       F2 v[1] = {f2_of(rzp)};
       publish<1>(A, 3, v, sh);
     }
-    if (!grid_barrier(A.bar, A.status, gridDim.x, A.timeout_ns)) { S.ok = false; return; }
+    if (!grid_barrier(A.bar, A.status, team_size(), A.timeout_ns)) { S.ok = false; return; }
     {
       double s[1];
       gather<1>(A, 3, s, sh);
@@ -485,7 +485,7 @@ __device__ void solve_mg(const PcgArgs& A, const Chunk& ch, Shared& sh, SolveSta
       F2 v[1] = {f2_of(pq)};
       publish<1>(A, 0, v, sh);
     }
-    if (!grid_barrier(A.bar, A.status, gridDim.x, A.timeout_ns)) { S.ok = false; return; }
+    if (!grid_barrier(A.bar, A.status, team_size(), A.timeout_ns)) { S.ok = false; return; }
     {
       double s[1];
       gather<1>(A, 0, s, sh);
@@ -507,7 +507,7 @@ __device__ void solve_mg(const PcgArgs& A, const Chunk& ch, Shared& sh, SolveSta
       F2 v[1] = {f2_of(rr)};
       publish<1>(A, 1, v, sh);
     }
-    if (!grid_barrier(A.bar, A.status, gridDim.x, A.timeout_ns)) { S.ok = false; return; }
+    if (!grid_barrier(A.bar, A.status, team_size(), A.timeout_ns)) { S.ok = false; return; }
     {
       double s[1];
       gather<1>(A, 1, s, sh);
@@ -528,7 +528,7 @@ __device__ void solve_mg(const PcgArgs& A, const Chunk& ch, Shared& sh, SolveSta
           A.x64[cr.c] += (double)x[cr.c];
           x[cr.c] = 0.0f;
         });
-        if (!grid_barrier(A.bar, A.status, gridDim.x, A.timeout_ns)) { S.ok = false; return; }
+        if (!grid_barrier(A.bar, A.status, team_size(), A.timeout_ns)) { S.ok = false; return; }
         FF rr64;
         for_my_cells(A, ch, [&](const CellRef& cr) {
           const float r32 = (float)residual64(A, cr);
@@ -539,7 +539,7 @@ __device__ void solve_mg(const PcgArgs& A, const Chunk& ch, Shared& sh, SolveSta
         });
         F2 v[1] = {f2_of(rr64)};
         publish<1>(A, 5, v, sh);
-        if (!grid_barrier(A.bar, A.status, gridDim.x, A.timeout_ns)) { S.ok = false; return; }
+        if (!grid_barrier(A.bar, A.status, team_size(), A.timeout_ns)) { S.ok = false; return; }
         double s[1];
         gather<1>(A, 5, s, sh);
         ++refinements;
@@ -580,14 +580,13 @@ __device__ void solve_mg(const PcgArgs& A, const Chunk& ch, Shared& sh, SolveSta
 }
 
 template <bool MIXED>
-__global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg_mg(const __grid_constant__ PcgArgs A) {
-  __shared__ Shared sh;
+__device__ void solve_scene_mg(const PcgArgs& A, Shared& sh) {
   const unsigned int nact = *A.n_active;
   const long long ncells = (long long)A.g.nx * A.g.ny * A.g.nz;
   const bool singular = A.check_singular && ((long long)A.stats->n_fluid == ncells);
   SolveState S;
   if (!singular) solve_mg<MIXED>(A, my_chunk(nact), sh, S);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (team_rank() == 0 && threadIdx.x == 0) {
     int st = 0;
     if (singular) st |= DEV_SINGULAR;
     else if (S.ok && !S.conv) st |= DEV_NOT_CONVERGED;
@@ -599,6 +598,23 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg_mg(const __grid_constant
     A.stats->rel_res = S.rel;
     A.stats->bnorm = S.bnorm;
   }
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg_mg(const __grid_constant__ PcgArgs A) {
+  __shared__ Shared sh;
+  team_enter(blockIdx.x, gridDim.x);
+  solve_scene_mg<MIXED>(A, sh);
+}
+
+// Several scenes in one launch: CTA b works on scene block_scene[b], in the team
+// of CTAs team_first[s] .. team_first[s+1]-1.
+template <bool MIXED>
+__global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg_mg_batch(const __grid_constant__ PcgBatch B) {
+  __shared__ Shared sh;
+  const int s = B.block_scene[blockIdx.x];
+  team_enter(blockIdx.x - B.team_first[s], B.team_first[s + 1] - B.team_first[s]);
+  solve_scene_mg<MIXED>(B.args[s], sh);
 }
 
 }  // namespace
@@ -622,6 +638,15 @@ cudaError_t launch_pcg_mg(const PcgArgs& a, bool mixed, int nblocks, cudaStream_
     return cudaLaunchCooperativeKernel((const void*)k_pcg_mg<true>, dim3(nblocks),
                                        dim3(PCG_THREADS), args, 0, s);
   return cudaLaunchCooperativeKernel((const void*)k_pcg_mg<false>, dim3(nblocks),
+                                     dim3(PCG_THREADS), args, 0, s);
+}
+
+cudaError_t launch_pcg_mg_batch(const PcgBatch& b, bool mixed, int nblocks, cudaStream_t s) {
+  void* args[] = {const_cast<PcgBatch*>(&b)};
+  if (mixed)
+    return cudaLaunchCooperativeKernel((const void*)k_pcg_mg_batch<true>, dim3(nblocks),
+                                       dim3(PCG_THREADS), args, 0, s);
+  return cudaLaunchCooperativeKernel((const void*)k_pcg_mg_batch<false>, dim3(nblocks),
                                      dim3(PCG_THREADS), args, 0, s);
 }
 

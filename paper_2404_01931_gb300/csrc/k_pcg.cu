@@ -61,7 +61,7 @@ __device__ void solve(const PcgArgs& A, const Chunk& ch, Shared& sh, SolveState&
     F2 v[2] = {f2_of(bb), f2_of(rz)};
     publish<2>(A, 1, v, sh);
   }
-  if (!grid_barrier(A.bar, A.status, gridDim.x, A.timeout_ns)) { S.ok = false; return; }
+  if (!grid_barrier(A.bar, A.status, team_size(), A.timeout_ns)) { S.ok = false; return; }
   double s0[2];
   gather<2>(A, 1, s0, sh);
   // thread 0 owns the scalars
@@ -89,7 +89,7 @@ __device__ void solve(const PcgArgs& A, const Chunk& ch, Shared& sh, SolveState&
       F2 v[1] = {f2_of(pq)};
       publish<1>(A, 0, v, sh);
     }
-    if (!grid_barrier(A.bar, A.status, gridDim.x, A.timeout_ns)) { S.ok = false; return; }
+    if (!grid_barrier(A.bar, A.status, team_size(), A.timeout_ns)) { S.ok = false; return; }
     {
       double s[1];
       gather<1>(A, 0, s, sh);
@@ -111,7 +111,7 @@ __device__ void solve(const PcgArgs& A, const Chunk& ch, Shared& sh, SolveState&
       F2 v[2] = {f2_of(rr), f2_of(rzn)};
       publish<2>(A, 1, v, sh);
     }
-    if (!grid_barrier(A.bar, A.status, gridDim.x, A.timeout_ns)) { S.ok = false; return; }
+    if (!grid_barrier(A.bar, A.status, team_size(), A.timeout_ns)) { S.ok = false; return; }
     {
       double s[2];
       gather<2>(A, 1, s, sh);
@@ -136,7 +136,7 @@ __device__ void solve(const PcgArgs& A, const Chunk& ch, Shared& sh, SolveState&
           A.x64[cr.c] += (double)x[cr.c];
           x[cr.c] = 0.0f;
         });
-        if (!grid_barrier(A.bar, A.status, gridDim.x, A.timeout_ns)) { S.ok = false; return; }
+        if (!grid_barrier(A.bar, A.status, team_size(), A.timeout_ns)) { S.ok = false; return; }
         FF rr64, rz2;  // the norm of the FP64 residual is accumulated from its float value
         double rr_exact = 0.0;
         for_my_cells(A, ch, [&](const CellRef& cr) {
@@ -149,7 +149,7 @@ __device__ void solve(const PcgArgs& A, const Chunk& ch, Shared& sh, SolveState&
         (void)rr_exact;
         F2 v[2] = {f2_of(rr64), f2_of(rz2)};
         publish<2>(A, 5, v, sh);
-        if (!grid_barrier(A.bar, A.status, gridDim.x, A.timeout_ns)) { S.ok = false; return; }
+        if (!grid_barrier(A.bar, A.status, team_size(), A.timeout_ns)) { S.ok = false; return; }
         double s[2];
         gather<2>(A, 5, s, sh);
         ++refinements;
@@ -196,14 +196,13 @@ __device__ void solve(const PcgArgs& A, const Chunk& ch, Shared& sh, SolveState&
 }
 
 template <bool MIXED>
-__global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(const __grid_constant__ PcgArgs A) {
-  __shared__ Shared sh;
+__device__ void solve_scene(const PcgArgs& A, Shared& sh) {
   const unsigned int nact = *A.n_active;
   const long long ncells = (long long)A.g.nx * A.g.ny * A.g.nz;
   const bool singular = A.check_singular && ((long long)A.stats->n_fluid == ncells);
   SolveState S;
   if (!singular) solve<MIXED>(A, my_chunk(nact), sh, S);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (team_rank() == 0 && threadIdx.x == 0) {
     int st = 0;
     if (singular) st |= DEV_SINGULAR;
     else if (S.ok && !S.conv) st |= DEV_NOT_CONVERGED;
@@ -215,6 +214,22 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(const __grid_constant__ 
     A.stats->rel_res = S.rel;
     A.stats->bnorm = S.bnorm;
   }
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(const __grid_constant__ PcgArgs A) {
+  __shared__ Shared sh;
+  team_enter(blockIdx.x, gridDim.x);
+  solve_scene<MIXED>(A, sh);
+}
+
+// Several scenes in one launch (see k_pcg_mg_batch).
+template <bool MIXED>
+__global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg_batch(const __grid_constant__ PcgBatch B) {
+  __shared__ Shared sh;
+  const int s = B.block_scene[blockIdx.x];
+  team_enter(blockIdx.x - B.team_first[s], B.team_first[s + 1] - B.team_first[s]);
+  solve_scene<MIXED>(B.args[s], sh);
 }
 
 int pcg_block_size() { return PCG_THREADS; }
@@ -243,6 +258,15 @@ cudaError_t launch_pcg(const PcgArgs& a, bool mixed, int nblocks, cudaStream_t s
                                        args, 0, s);
   return cudaLaunchCooperativeKernel((const void*)k_pcg<false>, dim3(nblocks), dim3(PCG_THREADS),
                                      args, 0, s);
+}
+
+cudaError_t launch_pcg_batch(const PcgBatch& b, bool mixed, int nblocks, cudaStream_t s) {
+  void* args[] = {const_cast<PcgBatch*>(&b)};
+  if (mixed)
+    return cudaLaunchCooperativeKernel((const void*)k_pcg_batch<true>, dim3(nblocks),
+                                       dim3(PCG_THREADS), args, 0, s);
+  return cudaLaunchCooperativeKernel((const void*)k_pcg_batch<false>, dim3(nblocks),
+                                     dim3(PCG_THREADS), args, 0, s);
 }
 
 // ---- helpers of the standalone solve: active bricks straight from cell types

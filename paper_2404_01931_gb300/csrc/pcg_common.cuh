@@ -9,6 +9,23 @@
 namespace flipk {
 
 constexpr int PCG_THREADS = 1024;
+
+// The CTAs that solve one scene form a team: the whole grid for a single scene,
+// a slice of it when several scenes share one launch.  A CTA's rank and the
+// team size are set once at kernel entry; barriers, reductions and the
+// ownership of cells all use them instead of blockIdx / gridDim.
+__shared__ unsigned int s_team_rank, s_team_size;
+
+__device__ __forceinline__ unsigned int team_rank() { return s_team_rank; }
+__device__ __forceinline__ unsigned int team_size() { return s_team_size; }
+
+__device__ __forceinline__ void team_enter(unsigned int rank, unsigned int size) {
+  if (threadIdx.x == 0) {
+    s_team_rank = rank;
+    s_team_size = size;
+  }
+  __syncthreads();
+}
 constexpr int PCG_WARPS = PCG_THREADS / 32;
 
 // ------------------------------------------------------------ float pairs
@@ -67,9 +84,9 @@ struct Chunk {
 
 __device__ __forceinline__ Chunk my_chunk(unsigned int nact) {
   const unsigned int total = nact * BRICK_CELLS;
-  unsigned int per = (total + gridDim.x - 1) / gridDim.x;
+  unsigned int per = (total + team_size() - 1) / team_size();
   per = (per + 31u) & ~31u;
-  const unsigned int b = min(total, blockIdx.x * per);
+  const unsigned int b = min(total, team_rank() * per);
   return Chunk{b, min(total, b + per)};
 }
 
@@ -194,7 +211,7 @@ __device__ __forceinline__ void publish(const PcgArgs& A, int slot, F2 (&v)[K], 
     float2* part = reinterpret_cast<float2*>(A.partials);
 #pragma unroll
     for (int q = 0; q < K; ++q)
-      part[(size_t)(slot + q) * gridDim.x + blockIdx.x] = make_float2(v[q].hi, v[q].lo);
+      part[(size_t)(slot + q) * team_size() + team_rank()] = make_float2(v[q].hi, v[q].lo);
   }
 }
 
@@ -207,10 +224,10 @@ __device__ __forceinline__ void gather(const PcgArgs& A, int slot, double (&out)
 #pragma unroll
   for (int q = 0; q < K; ++q) v[q] = F2{0.0f, 0.0f};
   if (threadIdx.x < 32) {
-    for (unsigned int j = threadIdx.x; j < gridDim.x; j += 32)
+    for (unsigned int j = threadIdx.x; j < team_size(); j += 32)
 #pragma unroll
       for (int q = 0; q < K; ++q) {
-        const float2 p = part[(size_t)(slot + q) * gridDim.x + j];
+        const float2 p = part[(size_t)(slot + q) * team_size() + j];
         v[q] = f2_add(v[q], F2{p.x, p.y});
       }
 #pragma unroll

@@ -114,6 +114,10 @@ def lib():
         L.flip_last_error.restype = C.c_char_p
         L.flip_solve_pressure.argtypes = [PP, vp, vp, vp, vp, C.POINTER(i32),
                                           C.POINTER(C.c_double)]
+        L.flip_batch_create.argtypes = [i32, vp, C.POINTER(vp)]
+        L.flip_batch_step.argtypes = [vp, C.POINTER(vp), i32, i32, C.POINTER(FlipStats)]
+        L.flip_batch_destroy.argtypes = [vp]
+        L.flip_batch_destroy.restype = None
         L.flip_solve_pressure_noalloc.argtypes = [PP, vp, vp, vp, vp, C.POINTER(i32),
                                                   C.POINTER(C.c_double)]
         if L.flip_abi_version() != 2:
@@ -297,6 +301,53 @@ def flip_solve_pressure_noalloc(params: FlipParams, type_, b, p, stream=None):
 
 
 FLIP_NOALLOC_MAX_CELLS = 262144
+
+
+def flip_batch_create(capacity: int, stream=None):
+    b = C.c_void_p()
+    _check(lib().flip_batch_create(int(capacity), C.c_void_p(stream or 0), C.byref(b)))
+    return b
+
+
+def flip_batch_step(b, handles, nsteps: int = 1, stats: bool = False):
+    """Advances the scenes (handles) together; returns (status, [FlipStats] or None)."""
+    n = len(handles)
+    arr = (C.c_void_p * max(n, 1))(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
+    st = (FlipStats * max(n, 1))() if stats else None
+    rc = lib().flip_batch_step(b, arr, n, int(nsteps), st)
+    return _check(rc), (list(st)[:n] if stats else None)
+
+
+def flip_batch_destroy(b):
+    if b:
+        lib().flip_batch_destroy(b)
+
+
+class Batch:
+    """Batch runner: advances several Simulations together (see flip_batch_step)."""
+
+    def __init__(self, capacity: int, stream=None):
+        self.b = flip_batch_create(capacity, stream)
+
+    def step(self, sims, nsteps: int = 1, stats: bool = False):
+        return flip_batch_step(self.b, [s.h for s in sims], nsteps, stats)
+
+    def close(self):
+        if getattr(self, "b", None):
+            flip_batch_destroy(self.b)
+            self.b = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Simulation:

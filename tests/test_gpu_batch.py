@@ -1,0 +1,101 @@
+"""Batched scenes: one cooperative solve launch for many uneven scenes.
+
+A scene's results in a batch equal its results alone (up to the order of
+floating-point sums: P2G atomics and the per-team reductions), and match the
+oracle like a scene stepped alone."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2404_01931_gb300 import flip as F
+from paper_2404_01931_gb300 import scenes as S
+
+from parity_util import matched, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytestmark = [pytest.mark.gpu, pytest.mark.skip(reason="needs a CUDA GPU")]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _mix():
+    """Uneven scenes: sizes, a ragged grid, both precisions, both preconditioners."""
+    out = []
+    for n, mixed, pre in [(32, False, 1), (40, False, 1), (24, True, 1), (48, False, 0),
+                          ((20, 13, 17), False, 1), (32, True, 0)]:
+        if np.isscalar(n):
+            sc = S.random_velocities(S.dam_break(n, 0.4, 0.5, seed=n), 0.2, n)
+        else:
+            sc = S.random_velocities(S.box(n, (0.0, 0.0, 0.0), (0.55, 0.5, 0.8), seed=5), 0.3, 4)
+        op, fp = matched(n, preconditioner=pre)
+        if mixed:
+            fp.precision = F.FLIP_PREC_MIXED_IR
+            fp.cg_tol, fp.ir_tol = 1e-3, 1e-8
+        out.append((n, sc, op, fp))
+    return out
+
+
+def _fields(sim):
+    return sim.particles() + [sim.read(F.PRESSURE_F64)]
+
+
+def test_batch_equals_alone():
+    mix = _mix()
+    alone = []
+    for n, sc, op, fp in mix:
+        with F.Simulation(fp, *sc.arrays()) as sim:
+            sim.step(3)
+            alone.append(_fields(sim))
+    sims = [F.Simulation(fp, *sc.arrays()) for n, sc, op, fp in mix]
+    try:
+        with F.Batch(len(sims)) as b:
+            rc, st = b.step(sims, 3, stats=True)
+            assert rc == F.FLIP_OK and len(st) == len(sims)
+            assert all(s.steps == 3 and s.cg_iterations > 0 for s in st)
+        for (n, *_), sim, ref in zip(mix, sims, alone):
+            got = _fields(sim)
+            dx = 1.0 / (n if np.isscalar(n) else max(n))
+            pos = np.abs(np.stack(got[:3]) - np.stack(ref[:3])).max() / dx
+            assert pos <= 1e-4, (n, pos)
+            assert rel_l2(np.stack(got[3:6]), np.stack(ref[3:6]), 1e-3) <= 1e-4, n
+            assert rel_l2(got[6], ref[6]) <= 1e-4, n
+    finally:
+        for s in sims:
+            s.close()
+
+
+def test_batched_scene_matches_the_oracle():
+    n = 32
+    sc = S.dam_break(n)
+    op, fp = matched(n)
+    ref = O.step(op, *sc.arrays())
+    other = S.dam_break(40, 0.3, 0.6, seed=9)
+    with F.Simulation(fp, *sc.arrays()) as a, \
+            F.Simulation(matched(40)[1], *other.arrays()) as o, F.Batch(4) as b:
+        rc, _ = b.step([o, a], 1, stats=True)
+        assert rc == F.FLIP_OK
+        x, y, z, u, v, w = a.particles()
+        p = a.read(F.PRESSURE_F64)
+    assert np.abs(np.stack([x, y, z]) - np.stack([ref.x, ref.y, ref.z])).max() * n <= 1e-4
+    assert rel_l2(p, ref.pressure) <= 1e-5
+
+
+def test_batch_argument_checks():
+    sc = S.dam_break(16)
+    fp = matched(16)[1]
+    with F.Simulation(fp, *sc.arrays()) as a, F.Batch(2) as b:
+        with pytest.raises(F.FlipError) as ei:
+            b.step([a, a], 1)
+        assert ei.value.code == F.FLIP_E_ARG
+        with F.Simulation(fp, *sc.arrays()) as c, F.Simulation(fp, *sc.arrays()) as d:
+            with pytest.raises(F.FlipError):
+                b.step([a, c, d], 1)  # more than the capacity
+        rc, _ = b.step([], 1)
+        assert rc == F.FLIP_OK
