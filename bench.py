@@ -51,6 +51,17 @@ WORKLOADS = {
 PCG_BYTES_PER_ITER = 41
 IR_BYTES_PER_OUTER = 49
 IR_BYTES_PER_SOLVE = 29 + 8 + 16
+# With the multigrid preconditioner, per fluid cell of level 0 and iteration:
+#   phase A 17 B; phase B 24 B + the fused red half-sweep's z writes (2 B);
+#   V-cycle at level 0 with nu = 2: six half-sweeps reading r and writing z for
+#   half the cells (4 B each), the restriction reading r, z, type (9 B), the last
+#   red half-sweep reading r, z and writing half of z (10 B); coarser levels add
+#   about a seventh of level 0's cycle (6 B)                      => 92 B
+#   refinement: x64 += d (24 B), r = b - A x64 in FP64 (23 B)     => 47 B
+#   per solve: ||b|| (8 B), float-pair pressure (16 B)            => 24 B
+MG_PCG_BYTES_PER_ITER = 92
+MG_IR_BYTES_PER_OUTER = 47
+MG_IR_BYTES_PER_SOLVE = 24
 
 
 def make_scene(w):
@@ -208,6 +219,116 @@ def run_reference(args, w):
     print(json.dumps(out), flush=True)
 
 
+def run_batch(args):
+    """64 independent dam-break scenes, edges {32,48,64,80,96} and fluid fraction
+    0.2-0.5 by seed, stepped together (one batched solve launch per step)."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2404_01931_gb300 import flip as F
+    from paper_2404_01931_gb300 import scenes as S
+    torch.cuda.set_device(0)
+    scenes = S.batch_scenes(args.batch, seed=0)
+    sims = []
+    for sc in scenes:
+        p = F.default_params(sc.n[0])
+        sims.append(F.Simulation(p, *sc.arrays()))
+    npart = sum(sc.n_particles for sc in scenes)
+    stream = torch.cuda.Stream()  # the batched solves run here; it joins every scene
+    b = F.Batch(len(sims), stream=stream.cuda_stream)
+    if args.warmup:
+        b.step(sims, args.warmup)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rc, st = b.step(sims, args.steps, stats=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    edges = sorted({sc.n[0] for sc in scenes})
+    out = {"metric": "FLIP particle-steps/s", "value": npart * args.steps / (ms / 1e3),
+           "unit": "particle-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"batch of {len(scenes)} dam-break scenes, edges {edges}, "
+                                  "fluid fraction 0.2-0.5 by seed", "particles": npart,
+                      "cells": sum(int(np.prod(sc.n)) for sc in scenes),
+                      "precision": "FP32 (FP64-accurate dots)", "preconditioner": "multigrid"},
+           "cg_iterations_per_scene_step": sum(s.cg_iterations for s in st) / len(st) / args.steps,
+           "ms_pcg_per_step": st[0].ms_pcg / args.steps,
+           "max_rel_residual": max(s.cg_rel_residual for s in st), "status": rc,
+           "gpu_launches": sum(s.kernel_launches for s in st), "clocks": ck}
+    print(json.dumps(out), flush=True)
+    b.close()
+    for s in sims:
+        s.close()
+
+
+def run_serve(args):
+    """Step requests arriving as a Poisson process over resident scenes of uneven
+    size, served by the continuous-batching server."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2404_01931_gb300 import flip as F
+    from paper_2404_01931_gb300 import scenes as S
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(0)
+    lo, hi = 48, args.serve_max_edge
+    t_gen = time.perf_counter()
+    srv = F.Server(int(args.budget_gb * (1 << 30)), args.max_batch)
+    ids, npart = [], []
+    for k in range(args.serve):
+        n = int(round(np.exp(rng.uniform(np.log(lo), np.log(hi)))))
+        f = rng.uniform(0.2, 0.5)
+        side = float(np.sqrt(f))
+        sc = S.dam_break(n, side, side, seed=k)
+        p = F.default_params(n)
+        p.precision = F.FLIP_PREC_MIXED_IR
+        p.cg_tol, p.ir_tol = 1e-3, 1e-8
+        ids.append(srv.add_scene(p, *sc.arrays()))
+        npart.append(sc.n_particles)
+    srv.drain()
+    t_gen = time.perf_counter() - t_gen
+    resident, used = srv.usage()
+    # Poisson arrivals, uniform scene choice
+    gaps = rng.exponential(1.0 / args.rate, args.requests)
+    start = srv.now() + 0.2
+    arrivals = start + np.cumsum(gaps)
+    choice = rng.integers(0, len(ids), args.requests)
+    clocks = ClockSampler(0)
+    clocks.start()
+    tickets = [srv.submit(ids[c], float(t)) for c, t in zip(choice, arrivals)]
+    infos = [srv.wait(t) for t in tickets]
+    ck = clocks.stop()
+    lat = np.array([i.t_done - i.t_arrival for i in infos]) * 1e3
+    served = sum(npart[c] for c in choice)
+    span = max(i.t_done for i in infos) - float(arrivals[0])
+    out = {"metric": "FLIP particle-steps/s", "value": served / span, "unit": "particle-steps/s",
+           "n_gpus": 1, "steps": args.requests, "warmup": 0,
+           "ms_per_step": span * 1e3 / args.requests, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+           "config": {"workload": f"serving: {args.serve} resident dam-break scenes, edges "
+                                  f"log-uniform in [{lo}, {hi}], Poisson arrivals at "
+                                  f"{args.rate}/s, uniform scene choice, mixed precision",
+                      "budget_gb": args.budget_gb, "max_batch": args.max_batch,
+                      "resident_scenes": resident, "resident_gb": used / (1 << 30),
+                      "particles_total": int(sum(npart)), "setup_s": round(t_gen, 1)},
+           "latency_ms": {"p50": float(np.percentile(lat, 50)),
+                          "p99": float(np.percentile(lat, 99)), "max": float(lat.max())},
+           "mean_batch": float(np.mean([i.batch_size for i in infos])),
+           "failed": int(sum(i.status != F.FLIP_OK for i in infos)), "clocks": ck}
+    print(json.dumps(out), flush=True)
+    srv.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -217,6 +338,15 @@ def main():
     ap.add_argument("--workload", default="pool256", choices=sorted(WORKLOADS))
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="run the batched form: this many dam-break scenes stepped together")
+    ap.add_argument("--serve", type=int, default=0,
+                    help="run the serving form over this many resident scenes")
+    ap.add_argument("--serve-max-edge", type=int, default=192)
+    ap.add_argument("--rate", type=float, default=2000.0, help="request arrivals per second")
+    ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--budget-gb", type=float, default=180.0)
+    ap.add_argument("--max-batch", type=int, default=64)
     ap.add_argument("--cg-tol", type=float, default=None,
                     help="override the workload's cg_tol (mixed mode: refinement trigger)")
     args = ap.parse_args()
@@ -225,6 +355,10 @@ def main():
         w["cg_tol"] = args.cg_tol
     if args.impl == "reference":
         return run_reference(args, w)
+    if args.batch:
+        return run_batch(args)
+    if args.serve:
+        return run_serve(args)
     ws, rank, local = dist_setup()
     import torch
     import torch.distributed as dist
@@ -296,9 +430,9 @@ def main():
         peak, peak_kind = read_peaks()
         nfl = st.n_fluid_cells
         mixed = w["precision"] == "mixed"
-        pcg_bytes = nfl * (PCG_BYTES_PER_ITER * st.cg_iterations
-                           + (IR_BYTES_PER_OUTER * st.ir_iterations
-                              + IR_BYTES_PER_SOLVE * args.steps if mixed else 0))
+        pcg_bytes = nfl * (MG_PCG_BYTES_PER_ITER * st.cg_iterations
+                           + (MG_IR_BYTES_PER_OUTER * st.ir_iterations
+                              + MG_IR_BYTES_PER_SOLVE * args.steps if mixed else 0))
         stage_ms = {"bin": st.ms_bin, "p2g": st.ms_p2g, "divergence": st.ms_divergence,
                     "pcg": st.ms_pcg, "g2p": st.ms_g2p}
         achieved = pcg_bytes / (st.ms_pcg / 1e3) / 1e9 if st.ms_pcg > 0 else None
@@ -319,7 +453,8 @@ def main():
             "ir_iterations_per_step": st.ir_iterations / args.steps,
             "rel_residual": st.cg_rel_residual, "rel_divergence": st.rel_divergence,
             "n_fluid_cells": nfl, "status": rc,
-            "roofline": {"kernel": "k_pcg (persistent PCG, whole solve per launch)",
+            "roofline": {"kernel": "k_pcg_mg (persistent multigrid-preconditioned CG, "
+                                   "whole solve per launch)",
                          "bound": "hbm", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",

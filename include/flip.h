@@ -200,6 +200,11 @@ int flip_read_particles(flip_handle* h, float* x, float* y, float* z, float* u, 
 int flip_write_particles(flip_handle* h, const float* x, const float* y, const float* z,
                          const float* u, const float* v, const float* w, int32_t src_is_device);
 
+/* Device bytes a scene with these parameters and np particles holds (its arena;
+ * what flip_create allocates).  0 when the parameters are invalid or no device
+ * is usable.  Allocates nothing. */
+size_t flip_footprint_bytes(const flip_params* params, int64_t np);
+
 /* Size in bytes of a field of this handle. */
 size_t flip_field_bytes(const flip_handle* h, flip_field which);
 

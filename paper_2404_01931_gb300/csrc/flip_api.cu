@@ -157,8 +157,10 @@ int check_params(const flip_params* p, bool need_particles_prm) {
   if (nfmax >= (1LL << 31)) return fail(FLIP_E_ARG, "grid too large (face count >= 2^31)");
   (void)nc;
   if (!(p->dx > 0.0) || !std::isfinite(p->dx)) return fail(FLIP_E_ARG, "dx must be > 0");
+  // 1/dx must be an integer (to rounding: 1/(1/n) need not give n exactly in FP64)
   const double inv = 1.0 / p->dx;
-  if (!(inv == std::floor(inv)) || inv > 16777216.0)
+  const double inv_int = std::round(inv);
+  if (!(std::fabs(inv - inv_int) <= 1e-9 * inv_int) || inv_int < 1.0 || inv_int > 16777216.0)
     return fail(FLIP_E_ARG, "1/dx must be an integer <= 2^24");
   if (!(p->dt > 0.0) || !std::isfinite(p->dt)) return fail(FLIP_E_ARG, "dt must be > 0");
   if (!(p->rho > 0.0)) return fail(FLIP_E_ARG, "rho must be > 0");
@@ -210,7 +212,7 @@ Grid make_grid(const flip_params& p) {
   g.bx = (g.nx + BRICK - 1) / BRICK;
   g.by = (g.ny + BRICK - 1) / BRICK;
   g.bz = (g.nz + BRICK - 1) / BRICK;
-  g.inv_dx = (float)(1.0 / p.dx);
+  g.inv_dx = (float)std::round(1.0 / p.dx);  // an integer: the binning is exact
   g.dx = (float)p.dx;
   for (int a = 0; a < 3; ++a) g.hi[a] = (float)((double)p.n[a] * p.dx - p.skin);
   g.skin = (float)p.skin;
@@ -585,6 +587,25 @@ int flip_step(flip_handle* h, int32_t nsteps, flip_stats* stats) {
     cudaEventDestroy(t_end);
   }
   return rc;
+}
+
+size_t flip_footprint_bytes(const flip_params* params, int64_t np) {
+  if (check_params(params, true) != FLIP_OK || np < 0 || np > 2147483647LL) return 0;
+  if (check_device() != FLIP_OK) return 0;
+  flip_handle tmp;
+  tmp.prm = *params;
+  tmp.g = make_grid(*params);
+  tmp.np = np;
+  tmp.ncells = (long long)tmp.g.nx * tmp.g.ny * tmp.g.nz;
+  tmp.nbricks = (unsigned)tmp.g.bx * tmp.g.by * tmp.g.bz;
+  tmp.nkeys = (long long)tmp.nbricks * BRICK_CELLS;
+  for (int d = 0; d < 3; ++d) tmp.nf[d] = n_faces(tmp.g, d);
+  tmp.mixed = params->precision == FLIP_PREC_MIXED_IR;
+  if (pcg_max_blocks(&tmp.pcg_blocks, &tmp.sm_count) != cudaSuccess) return 0;
+  if (params->preconditioner == FLIP_PRECOND_MG) setup_mg(tmp.mg, tmp.mg_dims, *params);
+  Carver measure;
+  carve(&tmp, measure);
+  return measure.off;
 }
 
 int flip_sync(flip_handle* h) {

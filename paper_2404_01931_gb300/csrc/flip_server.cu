@@ -1,0 +1,348 @@
+// flip_server.cu — continuous-batching step server over resident scenes
+// (include/flip_server.h).  Host code only: a worker thread admits scenes by
+// footprint, forms batches from the requests that have arrived and runs them
+// with flip_batch_step; callers submit and wait through the C ABI.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <set>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/flip_server.h"
+
+void flip_set_last_error_(const std::string& msg);
+
+namespace {
+
+struct Scene {
+  flip_params prm{};
+  std::vector<float> host[6];  // particle arrays until the scene is admitted
+  int64_t np = 0;
+  size_t footprint = 0;
+  flip_handle* h = nullptr;    // resident when non-null
+  int create_status = FLIP_OK; // failure of the admission, if any
+  bool remove = false;
+  bool in_flight = false;
+  int pending = 0;             // requests queued or running
+};
+
+struct Request {
+  int scene = -1;
+  double t_arrival = 0.0, t_start = -1.0, t_done = -1.0;
+  int status = FLIP_OK;
+  int batch_size = 0;
+  bool done = false;
+};
+
+}  // namespace
+
+struct flip_server {
+  size_t budget = 0;
+  int max_batch = 1;
+  int device = 0;
+  std::chrono::steady_clock::time_point t0;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::map<int, Scene> scenes;
+  int next_scene = 0;
+  std::deque<int> admit_queue;
+  std::map<int64_t, Request> reqs;
+  std::deque<int64_t> queue;
+  int64_t next_ticket = 0;
+  int64_t outstanding = 0;
+  size_t used = 0;
+  int resident = 0;
+  bool stop = false;
+  flip_batch* batch = nullptr;
+  std::thread worker;
+
+  double now() const {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+
+  // Admits waiting scenes in arrival order while they fit; called with mu held.
+  void admit_locked() {
+    while (!admit_queue.empty()) {
+      const int id = admit_queue.front();
+      auto it = scenes.find(id);
+      if (it == scenes.end() || it->second.remove) {
+        admit_queue.pop_front();
+        continue;
+      }
+      Scene& sc = it->second;
+      if (used + sc.footprint > budget) break;
+      flip_handle* h = nullptr;
+      const int rc = flip_create(&sc.prm, sc.host[0].data(), sc.host[1].data(), sc.host[2].data(),
+                                 sc.host[3].data(), sc.host[4].data(), sc.host[5].data(), sc.np,
+                                 0, nullptr, nullptr, &h);
+      admit_queue.pop_front();
+      for (auto& v : sc.host) std::vector<float>().swap(v);
+      if (rc != FLIP_OK) {
+        sc.create_status = rc;
+        continue;
+      }
+      sc.h = h;
+      used += sc.footprint;
+      ++resident;
+    }
+  }
+
+  // Frees removed scenes that have nothing pending; called with mu held.
+  bool reap_locked() {
+    bool freed = false;
+    for (auto it = scenes.begin(); it != scenes.end();) {
+      Scene& sc = it->second;
+      if (sc.remove && sc.pending == 0) {
+        if (sc.h) {
+          flip_destroy(sc.h);
+          used -= sc.footprint;
+          --resident;
+          freed = true;
+        }
+        it = scenes.erase(it);
+      } else {
+        ++it;
+      }
+    }
+    return freed;
+  }
+
+  void complete_locked(int64_t ticket, int status, double t_done, int batch_size) {
+    Request& r = reqs[ticket];
+    r.status = status;
+    r.t_done = t_done;
+    r.batch_size = batch_size;
+    r.done = true;
+    auto it = scenes.find(r.scene);
+    if (it != scenes.end()) it->second.pending -= 1;
+    outstanding -= 1;
+  }
+
+  void run() {
+    cudaSetDevice(device);
+    std::unique_lock<std::mutex> lk(mu);
+    for (;;) {
+      if (reap_locked()) cv_done.notify_all();
+      admit_locked();
+      // requests of scenes that failed admission finish with that status
+      for (auto q = queue.begin(); q != queue.end();) {
+        auto sit = scenes.find(reqs[*q].scene);
+        if (sit != scenes.end() && sit->second.create_status != FLIP_OK) {
+          complete_locked(*q, sit->second.create_status, now(), 0);
+          q = queue.erase(q);
+          cv_done.notify_all();
+        } else {
+          ++q;
+        }
+      }
+      const double t = now();
+      std::vector<int64_t> pick;
+      std::vector<flip_handle*> hs;
+      std::set<int> in_batch;
+      double next_arrival = -1.0;
+      for (auto q = queue.begin(); q != queue.end() && (int)pick.size() < max_batch;) {
+        const Request& r = reqs[*q];
+        Scene& sc = scenes[r.scene];
+        const bool ready = sc.h && !sc.in_flight && !in_batch.count(r.scene);
+        if (ready && r.t_arrival <= t) {
+          pick.push_back(*q);
+          hs.push_back(sc.h);
+          in_batch.insert(r.scene);
+          q = queue.erase(q);
+        } else {
+          if (ready && (next_arrival < 0.0 || r.t_arrival < next_arrival)) next_arrival = r.t_arrival;
+          ++q;
+        }
+      }
+      if (pick.empty()) {
+        if (stop) {
+          // no request can run any more: finish the rest as refused
+          for (int64_t q : queue) complete_locked(q, FLIP_E_ARG, now(), 0);
+          queue.clear();
+          cv_done.notify_all();
+          break;
+        }
+        if (next_arrival >= 0.0)
+          cv_work.wait_for(lk, std::chrono::duration<double>(std::max(0.0, next_arrival - t)));
+        else
+          cv_work.wait(lk);
+        continue;
+      }
+      for (size_t k = 0; k < pick.size(); ++k) {
+        reqs[pick[k]].t_start = t;
+        scenes[reqs[pick[k]].scene].in_flight = true;
+      }
+      lk.unlock();
+      int rc = flip_batch_step(batch, hs.data(), (int32_t)hs.size(), 1, nullptr);
+      std::vector<int> st(hs.size(), rc);
+      for (size_t k = 0; k < hs.size(); ++k) {
+        const int s2 = flip_sync(hs[k]);
+        if (rc == FLIP_OK) st[k] = s2;
+      }
+      const double t_done = now();
+      lk.lock();
+      for (size_t k = 0; k < pick.size(); ++k) {
+        scenes[reqs[pick[k]].scene].in_flight = false;
+        complete_locked(pick[k], st[k], t_done, (int)pick.size());
+      }
+      cv_done.notify_all();
+    }
+  }
+};
+
+extern "C" {
+
+int flip_server_create(size_t budget_bytes, int32_t max_batch, flip_server** out) {
+  if (!out) return FLIP_E_ARG;
+  *out = nullptr;
+  if (max_batch < 1 || max_batch > 4096) {
+    flip_set_last_error_("max_batch must be in [1, 4096]");
+    return FLIP_E_ARG;
+  }
+  flip_server* s = new (std::nothrow) flip_server();
+  if (!s) return FLIP_E_OOM;
+  s->budget = budget_bytes;
+  s->max_batch = max_batch;
+  s->t0 = std::chrono::steady_clock::now();
+  if (cudaGetDevice(&s->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete s;
+    flip_set_last_error_("no CUDA device");
+    return FLIP_E_NOGPU;
+  }
+  const int rc = flip_batch_create(max_batch, nullptr, &s->batch);
+  if (rc != FLIP_OK) {
+    delete s;
+    return rc;
+  }
+  s->worker = std::thread([s] { s->run(); });
+  *out = s;
+  return FLIP_OK;
+}
+
+int flip_server_add_scene(flip_server* s, const flip_params* params, const float* x,
+                          const float* y, const float* z, const float* u, const float* v,
+                          const float* w, int64_t np, int32_t* scene_id) {
+  if (!s || !params || !scene_id) return FLIP_E_ARG;
+  if (np < 0 || (np > 0 && (!x || !y || !z || !u || !v || !w))) return FLIP_E_ARG;
+  const size_t fp = flip_footprint_bytes(params, np);
+  if (fp == 0) return FLIP_E_ARG;
+  if (fp > s->budget) {
+    flip_set_last_error_("the scene's footprint exceeds the server's whole budget");
+    return FLIP_E_OOM;
+  }
+  Scene sc;
+  sc.prm = *params;
+  sc.np = np;
+  sc.footprint = fp;
+  const float* src[6] = {x, y, z, u, v, w};
+  for (int a = 0; a < 6; ++a) sc.host[a].assign(src[a], src[a] + np);
+  std::lock_guard<std::mutex> lk(s->mu);
+  const int id = s->next_scene++;
+  s->scenes.emplace(id, std::move(sc));
+  s->admit_queue.push_back(id);
+  *scene_id = id;
+  s->cv_work.notify_one();
+  return FLIP_OK;
+}
+
+int flip_server_submit(flip_server* s, int32_t scene, double t_arrival, int64_t* ticket) {
+  if (!s || !ticket) return FLIP_E_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->scenes.find(scene);
+  if (it == s->scenes.end() || it->second.remove) return FLIP_E_ARG;
+  const int64_t t = s->next_ticket++;
+  Request r;
+  r.scene = scene;
+  r.t_arrival = t_arrival < 0.0 ? s->now() : t_arrival;
+  s->reqs[t] = r;
+  s->queue.push_back(t);
+  it->second.pending += 1;
+  s->outstanding += 1;
+  *ticket = t;
+  s->cv_work.notify_one();
+  return FLIP_OK;
+}
+
+int flip_server_wait(flip_server* s, int64_t ticket, flip_request_info* info) {
+  if (!s) return FLIP_E_ARG;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return FLIP_E_ARG;
+  s->cv_done.wait(lk, [&] { return s->reqs[ticket].done; });
+  const Request& r = s->reqs[ticket];
+  if (info) {
+    info->scene = r.scene;
+    info->status = r.status;
+    info->t_arrival = r.t_arrival;
+    info->t_start = r.t_start;
+    info->t_done = r.t_done;
+    info->batch_size = r.batch_size;
+    info->reserved = 0;
+  }
+  const int st = r.status;
+  s->reqs.erase(ticket);
+  return st == FLIP_E_NOT_CONVERGED ? FLIP_OK : st;
+}
+
+int flip_server_drain(flip_server* s) {
+  if (!s) return FLIP_E_ARG;
+  std::unique_lock<std::mutex> lk(s->mu);
+  s->cv_work.notify_one();
+  s->cv_done.wait(lk, [&] { return s->outstanding == 0; });
+  return FLIP_OK;
+}
+
+double flip_server_now(const flip_server* s) { return s ? s->now() : 0.0; }
+
+int flip_server_usage(flip_server* s, int32_t* resident, size_t* bytes) {
+  if (!s) return FLIP_E_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (resident) *resident = s->resident;
+  if (bytes) *bytes = s->used;
+  return FLIP_OK;
+}
+
+int flip_server_scene_handle(flip_server* s, int32_t scene, flip_handle** h) {
+  if (!s || !h) return FLIP_E_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->scenes.find(scene);
+  if (it == s->scenes.end() || !it->second.h) return FLIP_E_ARG;
+  *h = it->second.h;
+  return FLIP_OK;
+}
+
+int flip_server_remove_scene(flip_server* s, int32_t scene) {
+  if (!s) return FLIP_E_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->scenes.find(scene);
+  if (it == s->scenes.end()) return FLIP_E_ARG;
+  it->second.remove = true;
+  s->cv_work.notify_one();
+  return FLIP_OK;
+}
+
+void flip_server_destroy(flip_server* s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+    s->cv_work.notify_one();
+  }
+  if (s->worker.joinable()) s->worker.join();
+  for (auto& kv : s->scenes)
+    if (kv.second.h) flip_destroy(kv.second.h);
+  flip_batch_destroy(s->batch);
+  delete s;
+}
+
+}  // extern "C"

@@ -73,6 +73,12 @@ class FlipStats(C.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class RequestInfo(C.Structure):
+    _fields_ = [("scene", C.c_int32), ("status", C.c_int32), ("t_arrival", C.c_double),
+                ("t_start", C.c_double), ("t_done", C.c_double), ("batch_size", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
 _FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
 
@@ -118,6 +124,20 @@ def lib():
         L.flip_batch_step.argtypes = [vp, C.POINTER(vp), i32, i32, C.POINTER(FlipStats)]
         L.flip_batch_destroy.argtypes = [vp]
         L.flip_batch_destroy.restype = None
+        L.flip_footprint_bytes.argtypes = [PP, i64]
+        L.flip_footprint_bytes.restype = sz
+        L.flip_server_create.argtypes = [sz, i32, C.POINTER(vp)]
+        L.flip_server_add_scene.argtypes = [vp, PP, vp, vp, vp, vp, vp, vp, i64, C.POINTER(i32)]
+        L.flip_server_submit.argtypes = [vp, i32, C.c_double, C.POINTER(i64)]
+        L.flip_server_wait.argtypes = [vp, i64, C.POINTER(RequestInfo)]
+        L.flip_server_drain.argtypes = [vp]
+        L.flip_server_now.argtypes = [vp]
+        L.flip_server_now.restype = C.c_double
+        L.flip_server_usage.argtypes = [vp, C.POINTER(i32), C.POINTER(sz)]
+        L.flip_server_scene_handle.argtypes = [vp, i32, C.POINTER(vp)]
+        L.flip_server_remove_scene.argtypes = [vp, i32]
+        L.flip_server_destroy.argtypes = [vp]
+        L.flip_server_destroy.restype = None
         L.flip_solve_pressure_noalloc.argtypes = [PP, vp, vp, vp, vp, C.POINTER(i32),
                                                   C.POINTER(C.c_double)]
         if L.flip_abi_version() != 2:
@@ -336,6 +356,81 @@ class Batch:
         if getattr(self, "b", None):
             flip_batch_destroy(self.b)
             self.b = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def flip_footprint_bytes(params: FlipParams, np_: int) -> int:
+    return int(lib().flip_footprint_bytes(C.byref(params), int(np_)))
+
+
+class Server:
+    """Continuous-batching step server (include/flip_server.h)."""
+
+    def __init__(self, budget_bytes: int, max_batch: int):
+        self.s = C.c_void_p()
+        _check(lib().flip_server_create(int(budget_bytes), int(max_batch), C.byref(self.s)))
+
+    def add_scene(self, params: FlipParams, x, y, z, u, v, w) -> int:
+        bufs = [_buf(np.ascontiguousarray(a, np.float32), np.float32) for a in (x, y, z, u, v, w)]
+        sid = C.c_int32(-1)
+        _check(lib().flip_server_add_scene(self.s, C.byref(params),
+                                           *[C.c_void_p(b[0]) for b in bufs], bufs[0][1] // 4,
+                                           C.byref(sid)))
+        return sid.value
+
+    def submit(self, scene: int, t_arrival: float = -1.0) -> int:
+        t = C.c_int64(-1)
+        _check(lib().flip_server_submit(self.s, int(scene), float(t_arrival), C.byref(t)))
+        return t.value
+
+    def wait(self, ticket: int) -> RequestInfo:
+        info = RequestInfo()
+        _check(lib().flip_server_wait(self.s, int(ticket), C.byref(info)))
+        return info
+
+    def drain(self):
+        _check(lib().flip_server_drain(self.s))
+
+    def now(self) -> float:
+        return float(lib().flip_server_now(self.s))
+
+    def usage(self):
+        r, b = C.c_int32(0), C.c_size_t(0)
+        _check(lib().flip_server_usage(self.s, C.byref(r), C.byref(b)))
+        return r.value, b.value
+
+    def handle(self, scene: int):
+        h = C.c_void_p()
+        _check(lib().flip_server_scene_handle(self.s, int(scene), C.byref(h)))
+        return h
+
+    def particles(self, scene: int):
+        """A resident scene's particles in creation order (call when it is idle)."""
+        h = self.handle(scene)
+        arrs = [flip_read(h, f) for f in (PX, PY, PZ, PU, PV, PW)]
+        ids = flip_read(h, PID)
+        inv = np.empty_like(ids)
+        inv[ids] = np.arange(ids.size, dtype=ids.dtype)
+        return [a[inv] for a in arrs]
+
+    def remove_scene(self, scene: int):
+        _check(lib().flip_server_remove_scene(self.s, int(scene)))
+
+    def close(self):
+        if getattr(self, "s", None):
+            lib().flip_server_destroy(self.s)
+            self.s = None
 
     def __enter__(self):
         return self

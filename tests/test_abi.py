@@ -98,3 +98,27 @@ def test_wrong_dtype_rejected(F):
     p = F.default_params(16)
     with pytest.raises(TypeError):
         F.flip_create(p, *[np.zeros(4, np.float64)] * 6, allocator=None)
+
+
+def test_server_and_batch_need_a_gpu(F):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("host-only check")
+    with pytest.raises(F.FlipError) as ei:
+        F.Server(1 << 30, 4)
+    assert ei.value.code == F.FLIP_E_NOGPU
+    with pytest.raises(F.FlipError) as ei:
+        F.flip_batch_create(4)
+    assert ei.value.code == F.FLIP_E_NOGPU
+    assert F.flip_footprint_bytes(F.default_params(16), 100) == 0  # no device to size for
+
+
+@pytest.mark.parametrize("n", [48, 49, 57, 83, 97, 191])
+def test_default_params_are_valid_for_every_edge(F, n):
+    """1/(1/n) is not always n in FP64; the defaults must still pass the checks (the
+    create call then fails only for want of a GPU)."""
+    p = F.default_params(n)
+    x = np.zeros(4, np.float32)
+    with pytest.raises(F.FlipError) as ei:
+        F.flip_create(p, x, x, x, x, x, x, allocator=None)
+    assert ei.value.code == F.FLIP_E_NOGPU

@@ -1,0 +1,90 @@
+"""The continuous-batching server: a scene's results are the same served amid other
+scenes' requests as stepped alone; scenes are admitted by footprint within the
+budget; requests arriving while a batch runs join later batches."""
+import numpy as np
+import pytest
+
+from paper_2404_01931_gb300 import flip as F
+from paper_2404_01931_gb300 import scenes as S
+
+from parity_util import matched
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytestmark = [pytest.mark.gpu, pytest.mark.skip(reason="needs a CUDA GPU")]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _scene(n, seed, mixed=False):
+    sc = S.random_velocities(S.dam_break(n, 0.45, 0.5, seed=seed), 0.2, seed)
+    fp = matched(n)[1]
+    if mixed:
+        fp.precision = F.FLIP_PREC_MIXED_IR
+        fp.cg_tol, fp.ir_tol = 1e-3, 1e-8
+    return sc, fp
+
+
+def test_served_scene_equals_alone():
+    scenes = [_scene(32, 1), _scene(40, 2, mixed=True), _scene(24, 3), _scene(48, 4)]
+    alone = []
+    for sc, fp in scenes:
+        with F.Simulation(fp, *sc.arrays()) as sim:
+            sim.step(3)
+            alone.append(sim.particles())
+    with F.Server(budget_bytes=8 << 30, max_batch=8) as srv:
+        ids = [srv.add_scene(fp, *sc.arrays()) for sc, fp in scenes]
+        t0 = srv.now() + 0.05
+        rng = np.random.default_rng(0)
+        tickets = []
+        # three steps per scene, interleaved, arriving over ~30 ms
+        order = [i for i in ids for _ in range(3)]
+        rng.shuffle(order)
+        for k, sid in enumerate(order):
+            tickets.append(srv.submit(sid, t0 + 0.0025 * k))
+        infos = [srv.wait(t) for t in tickets]
+        assert all(i.status == F.FLIP_OK for i in infos)
+        assert all(i.t_arrival <= i.t_start + 1e-9 and i.t_start <= i.t_done for i in infos)
+        for sid, (sc, fp), ref in zip(ids, scenes, alone):
+            got = srv.particles(sid)
+            dx = 1.0 / sc.n[0]
+            assert np.abs(np.stack(got[:3]) - np.stack(ref[:3])).max() / dx <= 1e-4
+            assert np.abs(np.stack(got[3:]) - np.stack(ref[3:])).max() <= 1e-4
+
+
+def test_requests_arriving_together_share_a_batch():
+    scenes = [_scene(24, s) for s in range(6)]
+    with F.Server(budget_bytes=8 << 30, max_batch=16) as srv:
+        ids = [srv.add_scene(fp, *sc.arrays()) for sc, fp in scenes]
+        srv.drain()
+        t = srv.now() + 0.05
+        tickets = [srv.submit(i, t) for i in ids]
+        infos = [srv.wait(k) for k in tickets]
+        assert max(i.batch_size for i in infos) > 1
+        assert all(i.t_done >= t for i in infos)
+
+
+def test_admission_by_footprint():
+    (sa, fa), (sb, fb) = _scene(32, 5), _scene(32, 6)
+    need = F.flip_footprint_bytes(fa, sa.n_particles)
+    assert need > 0
+    with F.Server(budget_bytes=int(need * 1.5), max_batch=4) as srv:
+        a = srv.add_scene(fa, *sa.arrays())
+        b = srv.add_scene(fb, *sb.arrays())
+        ta = srv.submit(a)
+        assert srv.wait(ta).status == F.FLIP_OK
+        assert srv.usage()[0] == 1           # b does not fit next to a
+        tb = srv.submit(b)                   # waits for memory
+        srv.remove_scene(a)                  # frees a's memory: b is admitted
+        info = srv.wait(tb)
+        assert info.status == F.FLIP_OK and srv.usage()[0] == 1
+        big, fbig = _scene(64, 7)
+        with pytest.raises(F.FlipError) as ei:
+            srv.add_scene(fbig, *big.arrays())
+        assert ei.value.code == F.FLIP_E_OOM
