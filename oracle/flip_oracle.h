@@ -119,7 +119,7 @@ int oracle_pcg(const oracle_params* P, const uint8_t* type, const double* b, dou
  * Galerkin-consistent cycle, omega > 1 over-corrects, which piecewise-constant
  * prolongation needs to converge fast. */
 #define ORACLE_MG_MAX_LEVELS 12
-#define ORACLE_MG_COARSE_SWEEPS 8
+#define ORACLE_MG_COARSE_SWEEPS 2
 int oracle_mg_levels(const oracle_params* P, int32_t dims[][3]);
 void oracle_mg_vcycle(const oracle_params* P, const uint8_t* type, const double* r, double* z,
                       int nu, double omega);

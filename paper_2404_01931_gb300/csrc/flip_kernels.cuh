@@ -40,7 +40,7 @@ constexpr int PCG_SLOTS = 7;
 // Multigrid V-cycle preconditioner (levels coarsened 2x per axis until the
 // largest extent is <= 4; red-black Gauss-Seidel smoothing).
 constexpr int MG_MAX_LEVELS = 12;
-constexpr int MG_COARSE_SWEEPS = 8;   // red-black pairs each way on the coarsest level
+constexpr int MG_COARSE_SWEEPS = 2;   // red-black pairs each way on the coarsest level
 constexpr int MG_CTA_CELLS = 4096;    // levels this small run inside one CTA
 constexpr float MG_OMEGA = 2.0f;      // over-correction of the coarse correction
 

@@ -186,7 +186,10 @@ __device__ __forceinline__ void sweep_level0(const PcgArgs& A, const Chunk& ch, 
   }
 }
 
-// b_{l+1} = (1/16) sum over fluid children of the level-l residual.
+// b_{l+1} = (1/16) sum over fluid children of the level-l residual.  The
+// restriction follows the pre-smoothing, whose last half-sweep is black: a black
+// cell's update solves its own equation against the red neighbours it read, so
+// its residual is exactly zero and only the red children contribute.
 __device__ __forceinline__ void restrict_level(const PcgArgs& A, int l, bool cta_local) {
   const MgArgs& M = A.mg;
   const MgLevel& F = M.lv[l];
@@ -197,15 +200,15 @@ __device__ __forceinline__ void restrict_level(const PcgArgs& A, int l, bool cta
 #pragma unroll
     for (int dz = 0; dz < 2; ++dz)
 #pragma unroll
-      for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-        for (int dx = 0; dx < 2; ++dx) {
-          const int i = 2 * e.i + dx, j = 2 * e.j + dy, k = 2 * e.k + dz;
-          if (i >= F.nx || j >= F.ny || k >= F.nz) continue;
-          const int c = i + F.nx * (j + F.ny * k);
-          if (F.t[c] != 1) continue;
-          sum = __fadd_rn(sum, level_residual(F, fb, i, j, k, c));
-        }
+      for (int dy = 0; dy < 2; ++dy) {
+        // the red child of row (dy, dz): x offset making 2I+dx+2J+dy+2K+dz even
+        const int dx = (dy + dz) & 1;
+        const int i = 2 * e.i + dx, j = 2 * e.j + dy, k = 2 * e.k + dz;
+        if (i >= F.nx || j >= F.ny || k >= F.nz) continue;
+        const int c = i + F.nx * (j + F.ny * k);
+        if (F.t[c] != 1) continue;
+        sum = __fadd_rn(sum, level_residual(F, fb, i, j, k, c));
+      }
     C.b[e.c] = __fmul_rn(sum, 0.0625f);
   });
 }
