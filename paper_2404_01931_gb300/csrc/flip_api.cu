@@ -93,7 +93,7 @@ struct flip_handle {
   double* norms = nullptr;
   void* tmp = nullptr;
   size_t tmp_bytes = 0;
-  int pcg_blocks = 0, sm_count = 0, p2g_blocks = 0;
+  int pcg_blocks = 0, sm_count = 0, p2g_blocks = 0, g2p_blocks = 0;
   long long reported_cg = 0, reported_ir = 0;
   int launches = 0;
   bool stepped = false;
@@ -247,7 +247,13 @@ void setup_mg(MgArgs& m, int dims[MG_MAX_LEVELS][3], const flip_params& p) {
     const double s = p.dt / (p.rho * h * h);
     L.s = (float)s;
     for (int c = 0; c < 8; ++c) L.inv_scnt[c] = c > 0 ? (float)(1.0 / (s * c)) : 0.0f;
-    if (l >= 1 && L.ncells <= MG_CTA_CELLS && m.lgrid == m.nlev) m.lgrid = l;
+  }
+  // the CTA-local levels: the longest tail of levels whose cells fit in MG_CTA_CELLS
+  long long tail = 0;
+  for (int l = m.nlev - 1; l >= 1; --l) {
+    tail += m.lv[l].ncells;
+    if (tail > MG_CTA_CELLS) break;
+    m.lgrid = l;
   }
   if (m.nlev == 1) m.lgrid = 1;
 }
@@ -303,11 +309,13 @@ void carve(flip_handle* h, Carver& cv) {
   h->partials = cv.take<double>((size_t)PCG_SLOTS * (size_t)h->pcg_blocks);
   if (h->prm.preconditioner == FLIP_PRECOND_MG) {
     h->mg.lv[0].x = cv.take<float>(nc);
+    h->mg.lv[0].code = cv.take<uint8_t>(nc);
     for (int l = 1; l < h->mg.nlev; ++l) {
       const size_t n = (size_t)h->mg.lv[l].ncells;
       h->mg.lv[l].x = cv.take<float>(n);
       h->mg.lv[l].b = cv.take<float>(n);
       h->mg.lv[l].t = cv.take<uint8_t>(n);
+      h->mg.lv[l].code = cv.take<uint8_t>(n);
     }
   }
   h->bar = cv.take<unsigned int>(BAR_WORDS);
@@ -438,6 +446,7 @@ int flip_create(const flip_params* params, const float* x, const float* y, const
     setup_mg(h->mg, h->mg_dims, *params);
   }
   h->p2g_blocks = h->sm_count * 4;
+  h->g2p_blocks = g2p_blocks(h->sm_count);
 
   Carver measure;
   carve(h, measure);
@@ -533,7 +542,7 @@ int flip_step(flip_handle* h, int32_t nsteps, flip_stats* stats) {
     h->launches += 1;
     if (timed) FLIP_CUDA(cudaEventRecord(ev[4], s));
     launch_g2p(h->g, h->K, h->P[h->cur], h->B, uo, h->mixed ? nullptr : h->x32, h->pff,
-               h->dstats, h->np, s);
+               h->dstats, h->np, h->g2p_blocks, s);
     h->launches += (h->np > 0);
     if (timed) FLIP_CUDA(cudaEventRecord(ev[5], s));
     FLIP_CUDA(cudaGetLastError());
@@ -982,7 +991,7 @@ int flip_batch_step(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t ns
       const float* uo[3] = {h->uo[0], h->uo[1], h->uo[2]};
       FLIP_CUDA(cudaStreamWaitEvent(h->stream, b->ev_solved, 0));
       launch_g2p(h->g, h->K, h->P[h->cur], h->B, uo, h->mixed ? nullptr : h->x32, h->pff,
-                 h->dstats, h->np, h->stream);
+                 h->dstats, h->np, h->g2p_blocks, h->stream);
       h->launches += (h->np > 0);
       h->stepped = true;
     }

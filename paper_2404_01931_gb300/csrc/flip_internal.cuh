@@ -161,12 +161,22 @@ __device__ __forceinline__ void st_release_gpu(unsigned int* p, unsigned int v) 
 }
 
 // Grid-wide barrier for a cooperative launch (all CTAs co-resident).  bar[0]
-// counts arrivals, bar[1] is the generation; the rest of the BAR_WORDS-word block
-// is spare and kept zero.  Every wait is bounded: after timeout_ns without
-// progress the CTA sets DEV_TIMEOUT in *status and returns false; a CTA that sees
-// another one's failure returns false too.  Callers stop their loop on false, so
-// no CTA is left waiting.
+// counts arrivals and is never reset inside a launch: the k-th barrier of a CTA
+// ends when the counter reaches k * nblocks, which the CTA learns from the value
+// its own arrival returned.  Arrival is a release add and the wait an acquire
+// load, so every write before the barrier (ordered by __syncthreads before
+// thread 0's release) is visible to every thread after it.  The caller resets
+// bar[0] to 0 before the launch; the rest of the BAR_WORDS-word block is spare.
+// Every wait is bounded: after timeout_ns without progress the CTA sets
+// DEV_TIMEOUT in *status and returns false; a CTA that sees another one's failure
+// returns false too.  Callers stop their loop on false, so no CTA is left waiting.
 constexpr unsigned int BAR_WORDS = 64;
+
+__device__ __forceinline__ unsigned int atom_add_release_gpu(unsigned int* p, unsigned int v) {
+  unsigned int old;
+  asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
 
 __device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* status, unsigned int nblocks,
                                              unsigned long long timeout_ns) {
@@ -174,26 +184,18 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* status, uns
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    const unsigned int gen = ld_acquire_gpu(bar + 1);
-    __threadfence();
-    const unsigned int arrived = atomicAdd(bar, 1u);
-    if (arrived == nblocks - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      st_release_gpu(bar + 1, gen + 1);
-    } else {
-      const unsigned long long t0 = global_timer_ns();
-      while (ld_acquire_gpu(bar + 1) == gen) {
-        if (*(volatile int*)status & DEV_TIMEOUT) { ok = 0; break; }
-        if (global_timer_ns() - t0 > timeout_ns) {
-          atomicOr(status, DEV_TIMEOUT);
-          ok = 0;
-          break;
-        }
-        __nanosleep(32);
+    const unsigned int old = atom_add_release_gpu(bar, 1u);
+    const unsigned int target = (old / nblocks + 1u) * nblocks;
+    const unsigned long long t0 = global_timer_ns();
+    while ((int)(ld_acquire_gpu(bar) - target) < 0) {
+      if (*(volatile int*)status & DEV_TIMEOUT) { ok = 0; break; }
+      if (global_timer_ns() - t0 > timeout_ns) {
+        atomicOr(status, DEV_TIMEOUT);
+        ok = 0;
+        break;
       }
+      __nanosleep(20);
     }
-    __threadfence();
     s_ok = ok;
   }
   __syncthreads();

@@ -41,7 +41,8 @@ constexpr int PCG_SLOTS = 7;
 // largest extent is <= 4; red-black Gauss-Seidel smoothing).
 constexpr int MG_MAX_LEVELS = 12;
 constexpr int MG_COARSE_SWEEPS = 2;   // red-black pairs each way on the coarsest level
-constexpr int MG_CTA_CELLS = 4096;    // levels this small run inside one CTA
+constexpr int MG_CTA_CELLS = 4800;    // the coarsest levels, up to this many cells in
+                                      // total, run inside one CTA in shared memory
 constexpr float MG_OMEGA = 2.0f;      // over-correction of the coarse correction
 
 struct MgLevel {
@@ -51,6 +52,10 @@ struct MgLevel {
   float* x;           // level solution (level 0: the preconditioned residual z)
   float* b;           // level right-hand side (level 0: unused, the CG residual is read)
   uint8_t* t;         // fluid flags (level 0: the cell types)
+  uint8_t* code;      // per cell: bit q (0..5 = -x,+x,-y,+y,-z,+z) set when that
+                      // neighbour is in the grid and fluid, bit 6 when the cell is
+                      // fluid; built at the start of every solve (level 0: only
+                      // the cells of active bricks)
 };
 
 struct MgArgs {
@@ -178,8 +183,9 @@ void launch_zero_off_fluid(const Grid& g, const uint8_t* type, float* p, unsigne
                            cudaStream_t s);
 
 // k_g2p.cu
+int g2p_blocks(int sm_count);
 void launch_g2p(const Grid& g, const StepConsts& k, const PartView& p, const BinView& b,
                 const float* const uo[3], const float* p32, const float2* pff, DevStats* st,
-                long long np, cudaStream_t s);
+                long long np, int nblocks, cudaStream_t s);
 
 }  // namespace flipk

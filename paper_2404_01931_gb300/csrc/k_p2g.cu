@@ -167,7 +167,7 @@ __global__ void k_divergence(const Grid g, const StepConsts K, const uint8_t* __
                              double* x64, float2* pff, unsigned int* bar, DevStats* st) {
   const long long nc = (long long)g.nx * g.ny * g.nz;
   if (blockIdx.x == 0 && threadIdx.x < BAR_WORDS) {
-    if (threadIdx.x != 1) bar[threadIdx.x] = 0u;  // counters (the generation may keep its value)
+    bar[threadIdx.x] = 0u;  // the grid barrier's arrival counter and spare words
     if (threadIdx.x == 0) st->max_speed_bits = 0u;
   }
   for (long long cl = blockIdx.x * (long long)blockDim.x + threadIdx.x; cl < nc;

@@ -329,7 +329,7 @@ __global__ void k_zero_off_fluid(const Grid g, const uint8_t* __restrict__ type,
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
        c += (long long)gridDim.x * blockDim.x)
     p[c] = 0.0f;
-  if (blockIdx.x == 0 && threadIdx.x < BAR_WORDS && threadIdx.x != 1) bar[threadIdx.x] = 0u;
+  if (blockIdx.x == 0 && threadIdx.x < BAR_WORDS) bar[threadIdx.x] = 0u;
   (void)type;
 }
 

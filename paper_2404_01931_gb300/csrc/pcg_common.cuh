@@ -8,7 +8,7 @@
 
 namespace flipk {
 
-constexpr int PCG_THREADS = 1024;
+constexpr int PCG_THREADS = 512;
 
 // The CTAs that solve one scene form a team: the whole grid for a single scene,
 // a slice of it when several scenes share one launch.  A CTA's rank and the
@@ -69,7 +69,7 @@ __device__ __forceinline__ void cta_sum(F2 (&v)[K], F2* scratch) {
   if (warp == 0) {
 #pragma unroll
     for (int q = 0; q < K; ++q) {
-      F2 s = scratch[q * PCG_WARPS + lane];
+      F2 s = (lane < PCG_WARPS) ? scratch[q * PCG_WARPS + lane] : F2{0.0f, 0.0f};
       v[q] = f2_warp_sum(s);
     }
   }
