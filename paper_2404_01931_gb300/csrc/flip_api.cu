@@ -256,6 +256,18 @@ void setup_mg(MgArgs& m, int dims[MG_MAX_LEVELS][3], const flip_params& p) {
     m.lgrid = l;
   }
   if (m.nlev == 1) m.lgrid = 1;
+  // the grid-wide levels are stored colour-split (MgLevel)
+  for (int l = 0; l < m.nlev; ++l) {
+    MgLevel& L = m.lv[l];
+    L.split = l < m.lgrid;
+    L.hx = (L.nx + 1) / 2;
+    L.margin = L.hx * L.ny + 1;
+    L.half = L.hx * L.ny * L.nz + 2 * L.margin;
+    L.nw = (L.hx + 31) / 32;
+    L.nbx = (L.nx + 7) / 8;
+    L.nby = (L.ny + 7) / 8;
+    L.nbz = (L.nz + 7) / 8;
+  }
 }
 
 void fill_pcg_tables(PcgArgs& a, const flip_params& p) {
@@ -302,21 +314,42 @@ void carve(flip_handle* h, Carver& cv) {
   } else {
     h->b32 = cv.take<float>(nc);
   }
-  h->r = cv.take<float>(nc);
-  h->pa = cv.take<float>(nc);
-  h->pb = cv.take<float>(nc);
-  h->q = cv.take<float>(nc);
   h->partials = cv.take<double>((size_t)PCG_SLOTS * (size_t)h->pcg_blocks);
   if (h->prm.preconditioner == FLIP_PRECOND_MG) {
-    h->mg.lv[0].x = cv.take<float>(nc);
-    h->mg.lv[0].code = cv.take<uint8_t>(nc);
-    for (int l = 1; l < h->mg.nlev; ++l) {
-      const size_t n = (size_t)h->mg.lv[l].ncells;
-      h->mg.lv[l].x = cv.take<float>(n);
-      h->mg.lv[l].b = cv.take<float>(n);
-      h->mg.lv[l].t = cv.take<uint8_t>(n);
-      h->mg.lv[l].code = cv.take<uint8_t>(n);
+    MgArgs& m = h->mg;
+    for (int l = 0; l < m.nlev; ++l) {
+      MgLevel& L = m.lv[l];
+      const size_t n = (size_t)L.ncells;
+      if (L.split) {
+        const size_t ns = 2 * (size_t)L.half;
+        L.x = cv.take<float>(ns);
+        L.b = cv.take<float>(ns);
+        L.code16 = cv.take<uint16_t>(ns);
+        L.seg = cv.take<int4>((size_t)L.nw * L.ny * L.nz);
+        L.nseg = cv.take<unsigned int>(1);
+        if (l > 0) {
+          L.t = cv.take<uint8_t>(n);
+          L.bflag = cv.take<uint8_t>((size_t)L.nbx * L.nby * L.nbz);
+        }
+        if (l == 0) {
+          m.pa0 = cv.take<float>(ns);
+          m.pb0 = cv.take<float>(ns);
+          m.q0 = cv.take<float>(ns);
+          m.d0 = cv.take<float>(ns);
+        }
+      } else {
+        L.x = cv.take<float>(n);
+        L.b = cv.take<float>(n);
+        L.t = cv.take<uint8_t>(n);
+        L.code = cv.take<uint8_t>(n);
+      }
     }
+    m.segcount = cv.take<unsigned int>((size_t)MG_MAX_LEVELS * (size_t)h->pcg_blocks);
+  } else {
+    h->r = cv.take<float>(nc);
+    h->pa = cv.take<float>(nc);
+    h->pb = cv.take<float>(nc);
+    h->q = cv.take<float>(nc);
   }
   h->bar = cv.take<unsigned int>(BAR_WORDS);
   h->dstats = cv.take<DevStats>(1);
@@ -349,6 +382,7 @@ PcgArgs pcg_args(flip_handle* h) {
   a.type = h->type;
   a.active = h->B.active;
   a.n_active = &h->dstats->n_active;
+  a.brick_fluid = h->B.brick_fluid;
   a.b32 = h->b32;
   a.b64 = h->b64;
   a.x32 = h->x32;

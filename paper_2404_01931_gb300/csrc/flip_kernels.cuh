@@ -45,17 +45,38 @@ constexpr int MG_CTA_CELLS = 4800;    // the coarsest levels, up to this many ce
                                       // total, run inside one CTA in shared memory
 constexpr float MG_OMEGA = 2.0f;      // over-correction of the coarse correction
 
+// One level of the hierarchy.  The grid-wide levels (l < lgrid) are stored
+// colour-split: cell (i, j, k) of colour c = (i+j+k) & 1 sits at
+//     c * half + margin + hx * (j + ny * k) + (i >> 1),   hx = ceil(nx / 2),
+// so the cells of one colour form contiguous runs along x and the six
+// neighbours of a cell are contiguous runs of the other colour at fixed
+// offsets.  margin = hx * ny + 1 slots before and after each colour's half keep
+// every neighbour address inside the array.  The CTA-local levels (l >= lgrid)
+// use the natural x-fastest layout.
 struct MgLevel {
   int nx, ny, nz, ncells;
   float inv_scnt[8];  // 1 / (s_l * count), s_l = dt / (rho (2^l dx)^2)
   float s;
   float* x;           // level solution (level 0: the preconditioned residual z)
-  float* b;           // level right-hand side (level 0: unused, the CG residual is read)
-  uint8_t* t;         // fluid flags (level 0: the cell types)
-  uint8_t* code;      // per cell: bit q (0..5 = -x,+x,-y,+y,-z,+z) set when that
-                      // neighbour is in the grid and fluid, bit 6 when the cell is
-                      // fluid; built at the start of every solve (level 0: only
-                      // the cells of active bricks)
+  float* b;           // level right-hand side (level 0: the CG residual r)
+  uint8_t* t;         // fluid flags, natural layout (level 0: the cell types)
+  uint8_t* code;      // CTA-local levels: per cell, bit q (0..5 = -x,+x,-y,+y,-z,+z)
+                      // set when that neighbour is in the grid and fluid, bit 6
+                      // when the cell is fluid; built at the start of every solve
+  // colour-split levels
+  int split;          // 1 for the grid-wide levels
+  int hx;             // slots per row and colour
+  int half;           // one colour's slots: hx * ny * nz + 2 * margin
+  int margin;         // hx * ny + 1
+  int nw;             // segments per row: ceil(hx / 32); a segment is 32 slots
+                      // of each colour, i.e. 64 cells of a row
+  int nbx, nby, nbz;  // 8x8x8 blocks of this level's cells
+  uint16_t* code16;   // per slot: the code bits above plus the count of
+                      // neighbours inside the grid in bits 8..10
+  int4* seg;          // active segments {row j + ny k, segment in row, j, k}
+  unsigned int* nseg; // their number (device)
+  uint8_t* bflag;     // levels >= 1: block holds a fluid cell (level 0 reads the
+                      // brick fluid counts of the binning)
 };
 
 struct MgArgs {
@@ -64,6 +85,11 @@ struct MgArgs {
   int nu;             // red-black pairs before and after the coarse correction
   float omega;
   float inv_cnt[8];   // 1 / count
+  float* pa0;         // level-0 CG vectors, colour-split like level 0: search
+  float* pb0;         // direction (double-buffered), A p, and the solution /
+  float* q0;          // mixed-mode correction d
+  float* d0;
+  unsigned int* segcount;  // [MG_MAX_LEVELS * max_blocks] per-CTA segment counts
   MgLevel lv[MG_MAX_LEVELS];
 };
 
@@ -76,6 +102,7 @@ struct PcgArgs {
   const uint8_t* type;
   const unsigned int* active;
   const unsigned int* n_active;
+  const unsigned int* brick_fluid;  // fluid cells per brick, from the binning
   const float* b32;     // FP32 mode right-hand side
   const double* b64;    // mixed mode right-hand side
   float* x32;           // FP32 mode solution / mixed inner correction

@@ -13,21 +13,25 @@
 // (black, red) pairs; the coarsest level does MG_COARSE_SWEEPS pairs each way.
 // The cycle is a symmetric positive-definite operator, as CG requires.
 //
-// Levels with more than MG_CTA_CELLS cells are processed by all CTAs with grid
-// barriers between half-sweeps; the small levels run inside CTA 0 with
-// __syncthreads.  The correction is never written: the first post-smoothing
-// half-sweep (black) reads its red neighbours plus omega times their parents'
-// values, and the red half-sweep that follows overwrites the red cells anyway.
-// The first red half-sweep from zero only needs the residual, so at level 0 it
-// is fused into the phase that produces the residual.
+// Layout and work split.  The grid-wide levels (l < lgrid) are stored
+// colour-split (see MgLevel): a half-sweep reads and writes contiguous runs of
+// one colour and its six neighbour runs of the other colour, so it moves half
+// the bytes of a natural-layout sweep, every access coalesced.  Work is a list
+// of active segments per level (64 cells of a row that meet a block holding
+// fluid), built at the start of every solve; a warp takes one segment, a lane
+// one slot, and each CTA a contiguous slice of the list.  Per cell one 16-bit
+// code carries the fluid neighbours and the neighbour count, so value loads
+// never wait on flags, and each warp loads several segments before it computes
+// (memory-level parallelism).  The small coarsest levels (at most MG_CTA_CELLS
+// cells together) run inside CTA 0 from shared memory with __syncthreads; the
+// others use grid barriers between half-sweeps.
 //
-// Memory-level parallelism: the passes are latency-bound (a thread owns many
-// cells and each cell needs ~8 independent loads), so every pass handles U
-// cells per thread at a time: it issues the loads of all U cells, then does the
-// arithmetic and the stores.  The neighbour structure comes from one code byte
-// per cell (built at the start of the solve), so the value loads never wait on
-// neighbour flags.  The arithmetic and the per-thread order of the reductions
-// are those of one cell at a time.
+// The correction is never written: the first post-smoothing half-sweep (black)
+// reads its red neighbours plus omega times their parents' values, and the red
+// half-sweep that follows overwrites the red cells anyway.  The first red
+// half-sweep from zero only needs the residual, so at level 0 it is fused into
+// the phase that produces the residual.  The last black and the last red
+// half-sweeps of level 0 also accumulate r.z.
 #include "pcg_common.cuh"
 
 namespace flipk {
@@ -35,11 +39,52 @@ namespace flipk {
 namespace {
 
 constexpr unsigned int CODE_SELF = 64u;
+constexpr int SEG_SLOTS = 32;  // slots of one colour per segment (a warp)
 
-// Runs slots first, first + stride, ... < end in batches of U: pre(e, ok)
-// returns a state with the slot's first loads, load(state) adds the loads that
+// Gauss-Seidel coefficients per level, copied to shared memory at kernel start:
+// s_inv_scnt[l][n] = 1 / (s_l n), s_inv_cnt[n] = 1 / n.
+__shared__ float s_inv_scnt[MG_MAX_LEVELS][8];
+__shared__ float s_inv_cnt[8];
+
+__device__ __forceinline__ void load_tables(const MgArgs& M) {
+  if (threadIdx.x < MG_MAX_LEVELS * 8) {
+    const int l = threadIdx.x >> 3, n = threadIdx.x & 7;
+    s_inv_scnt[l][n] = l < M.nlev ? M.lv[l].inv_scnt[n] : 0.0f;
+  }
+  if (threadIdx.x < 8) s_inv_cnt[threadIdx.x] = M.inv_cnt[threadIdx.x];
+  __syncthreads();
+}
+
+// The fields of a colour-split level a pass uses, read once into registers at
+// the start of the pass (the level descriptions live in parameter or shared
+// memory and would otherwise be re-read through generic pointers per cell).
+struct SV {
+  float* x;
+  float* b;
+  uint16_t* code;
+  const int4* seg;
+  int nx, ny, hx, half, margin, pl;
+  float s;
+};
+
+__device__ __forceinline__ SV sview(const MgLevel& L) {
+  return SV{L.x, L.b, L.code16, L.seg, L.nx, L.ny, L.hx, L.half, L.margin, L.hx * L.ny, L.s};
+}
+
+// The same for the level whose x a correction reads (colour-split or natural).
+struct PV {
+  const float* x;
+  int split, nx, ny, hx, half, margin;
+};
+
+__device__ __forceinline__ PV pview(const MgLevel& C) {
+  return PV{C.x, C.split, C.nx, C.ny, C.hx, C.half, C.margin};
+}
+
+// Runs items first, first + stride, ... < end in batches of U: pre(e, ok)
+// returns a state with the item's first loads, load(state) adds the loads that
 // depend on them, apply(state) computes and stores.  All loads of a batch come
-// before its first store.  Slots past the end are handed to pre() as 'first'
+// before its first store.  Items past the end are handed to pre() as 'first'
 // with ok = false (valid addresses; apply must skip them).
 template <int U, class Pre, class Load, class Apply>
 __device__ __forceinline__ void run_batched(unsigned int first, unsigned int end,
@@ -61,64 +106,79 @@ __device__ __forceinline__ void run_batched(unsigned int first, unsigned int end
   }
 }
 
-// ---------------------------------------------------------------- cells
+// ---------------------------------------------------------------- indexing
+
+// Index of cell (i, j, k) of a level in its storage (colour-split or natural).
+__device__ __forceinline__ int level_index(const PV& C, int i, int j, int k) {
+  if (C.split) return ((i + j + k) & 1) * C.half + C.margin + C.hx * (j + C.ny * k) + (i >> 1);
+  return i + C.nx * (j + C.ny * k);
+}
+
+// A slot of a colour-split level: cell (i, j, k) of row r = j + ny k, its
+// storage index and the base index of its neighbours in the other colour.
+struct SCell {
+  int i, j, k, r;
+  int idx, ob;
+  int par;  // i & 1
+  bool ok;
+};
+
+// Lane 'lane' of colour c in segment sg = {row, segment in row, j, k}.
+template <class LV>
+__device__ __forceinline__ SCell scell(const LV& L, int4 sg, int c, int lane) {
+  SCell e;
+  const int s = sg.y * SEG_SLOTS + lane;
+  e.j = sg.z;
+  e.k = sg.w;
+  e.r = sg.x;
+  e.par = (c + e.j + e.k) & 1;
+  e.i = 2 * s + e.par;
+  e.ok = s < L.hx && e.i < L.nx;
+  e.idx = c * L.half + L.margin + L.hx * e.r + min(s, L.hx - 1);
+  e.ob = e.idx + (1 - 2 * c) * L.half;
+  return e;
+}
+
+// Storage indices of the six neighbours (-x, +x, -y, +y, -z, +z), all in the
+// other colour's half; addresses of neighbours off the grid are valid but their
+// values are never used (the code bit is clear).
+template <class LV>
+__device__ __forceinline__ void snbr(const LV& L, const SCell& e, int (&nb)[6]) {
+  const int pl = L.hx * L.ny;
+  nb[0] = e.ob - 1 + e.par;
+  nb[1] = e.ob + e.par;
+  nb[2] = e.ob - L.hx;
+  nb[3] = e.ob + L.hx;
+  nb[4] = e.ob - pl;
+  nb[5] = e.ob + pl;
+}
+
+// This CTA's slice [q0, q1) of a level's active segments.
+__device__ __forceinline__ int2 seg_slice(const MgLevel& L) {
+  const int n = (int)*L.nseg;
+  const int per = (n + (int)team_size() - 1) / (int)team_size();
+  const int q0 = min(n, (int)team_rank() * per);
+  return make_int2(q0, min(n, q0 + per));
+}
+
+// Items (segment, colour) of this CTA for ncol colours: item t is segment
+// t / ncol, colour t % ncol (ncol = 2) or the pass's colour (ncol = 1).  Each
+// warp takes items first, first + PCG_WARPS, ...
+struct Items {
+  unsigned int first, end;
+};
+
+__device__ __forceinline__ Items seg_items(const MgLevel& L, int ncol) {
+  const int2 q = seg_slice(L);
+  return Items{(unsigned)(q.x * ncol + (int)(threadIdx.x >> 5)), (unsigned)(q.y * ncol)};
+}
+
+// ---------------------------------------------------------------- natural levels
 
 struct Cell {
   int i, j, k, c;
   bool ok;
 };
-
-// Slot e of level 0's active-cell index space (512 slots per active brick).
-__device__ __forceinline__ Cell slot_dense0(const PcgArgs& A, unsigned int e) {
-  const Grid& g = A.g;
-  const unsigned int brick = A.active[e >> 9];
-  const int l = (int)(e & 511u);
-  int i = (int)(brick % (unsigned)g.bx) * BRICK + (l & 7);
-  int j = (int)((brick / (unsigned)g.bx) % (unsigned)g.by) * BRICK + ((l >> 3) & 7);
-  int k = (int)(brick / ((unsigned)g.bx * (unsigned)g.by)) * BRICK + (l >> 6);
-  const bool ok = i < g.nx && j < g.ny && k < g.nz;
-  i = min(i, g.nx - 1);
-  j = min(j, g.ny - 1);
-  k = min(k, g.nz - 1);
-  return Cell{i, j, k, i + g.nx * (j + g.ny * k), ok};
-}
-
-// Slot e of one colour's index space of level 0 (256 slots per active brick):
-// brick e/256, row m/4 of the brick (y fastest within z), x position
-// 2(m%4) + parity, so no lane idles on a cell of the other colour.
-__device__ __forceinline__ Cell slot_colour0(const PcgArgs& A, unsigned int e, int colour) {
-  const Grid& g = A.g;
-  const unsigned int brick = A.active[e >> 8];
-  const int m = (int)(e & 255u);
-  const int lj = (m >> 2) & 7, lk = m >> 5;
-  const int li = 2 * (m & 3) + ((colour + lj + lk) & 1);
-  int i = (int)(brick % (unsigned)g.bx) * BRICK + li;
-  int j = (int)((brick / (unsigned)g.bx) % (unsigned)g.by) * BRICK + lj;
-  int k = (int)(brick / ((unsigned)g.bx * (unsigned)g.by)) * BRICK + lk;
-  const bool ok = i < g.nx && j < g.ny && k < g.nz;
-  i = min(i, g.nx - 1);
-  j = min(j, g.ny - 1);
-  k = min(k, g.nz - 1);
-  return Cell{i, j, k, i + g.nx * (j + g.ny * k), ok};
-}
-
-// Slot e of one colour's index space of a dense level: each x-row has
-// ceil(nx/2) slots, slot q of row (j, k) is x = 2q + parity.
-__device__ __forceinline__ Cell slot_colour(const MgLevel& L, int e, int colour) {
-  const int hx = (L.nx + 1) >> 1;
-  const int row = e / hx, q = e - row * hx;
-  const int j = row % L.ny, k = row / L.ny;
-  int i = 2 * q + ((colour + j + k) & 1);
-  const bool ok = i < L.nx;
-  i = min(i, L.nx - 1);
-  return Cell{i, j, k, i + L.nx * row, ok};
-}
-
-__device__ __forceinline__ Cell cell_at(const MgLevel& L, int c) {
-  return Cell{c % L.nx, (c / L.nx) % L.ny, c / (L.nx * L.ny), c, true};
-}
-
-// ---------------------------------------------------------------- partitions
 
 struct Part {
   int begin, end, stride;
@@ -134,72 +194,54 @@ __device__ __forceinline__ Part level_part(int n, bool cta_local) {
   return Part{b + (int)threadIdx.x, min(n, b + per), PCG_THREADS};
 }
 
-// This thread's slots of level 0's colour index space: [first, end) step
-// PCG_THREADS, a contiguous slice per CTA.
-__device__ __forceinline__ Part colour_part0(const PcgArgs& A) {
-  const unsigned int total = *A.n_active * (BRICK_CELLS / 2);
-  unsigned int per = (total + team_size() - 1) / team_size();
-  per = (per + 31u) & ~31u;
-  const unsigned int b = min(total, team_rank() * per);
-  return Part{(int)(b + threadIdx.x), (int)min(total, b + per), PCG_THREADS};
+__device__ __forceinline__ Cell cell_at(const MgLevel& L, int c) {
+  return Cell{c % L.nx, (c / L.nx) % L.ny, c / (L.nx * L.ny), c, true};
 }
 
-__device__ __forceinline__ int lcount(const MgLevel& L, int i, int j, int k) {
-  return (i > 0) + (i < L.nx - 1) + (j > 0) + (j < L.ny - 1) + (k > 0) + (k < L.nz - 1);
-}
-
-// Indices of the six neighbours (-x, +x, -y, +y, -z, +z); the cell itself
-// where a neighbour is off the grid.
-__device__ __forceinline__ void nbr_index(const MgLevel& L, const Cell& cl, int (&idx)[6]) {
+// Neighbour code of cell (i, j, k) from natural fluid flags fl (value 1 = fluid):
+// bits 0..5 fluid neighbours inside the grid, bit 6 the cell itself, bits 8..10
+// the number of neighbours inside the grid.
+__device__ __forceinline__ unsigned int make_code(const MgLevel& L, const uint8_t* fl, int i, int j,
+                                                  int k) {
+  const int c = i + L.nx * (j + L.ny * k);
   const int sy = L.nx, sz = L.nx * L.ny;
-  idx[0] = cl.i > 0 ? cl.c - 1 : cl.c;
-  idx[1] = cl.i < L.nx - 1 ? cl.c + 1 : cl.c;
-  idx[2] = cl.j > 0 ? cl.c - sy : cl.c;
-  idx[3] = cl.j < L.ny - 1 ? cl.c + sy : cl.c;
-  idx[4] = cl.k > 0 ? cl.c - sz : cl.c;
-  idx[5] = cl.k < L.nz - 1 ? cl.c + sz : cl.c;
-}
-
-__device__ __forceinline__ uint8_t make_code(const MgLevel& L, const uint8_t* fl, const Cell& cl) {
-  const bool in[6] = {cl.i > 0, cl.i < L.nx - 1, cl.j > 0, cl.j < L.ny - 1, cl.k > 0,
-                      cl.k < L.nz - 1};
-  int idx[6];
-  nbr_index(L, cl, idx);
-  unsigned int code = (fl[cl.c] == 1) ? CODE_SELF : 0u;
+  const bool in[6] = {i > 0, i < L.nx - 1, j > 0, j < L.ny - 1, k > 0, k < L.nz - 1};
+  const int off[6] = {-1, 1, -sy, sy, -sz, sz};
+  unsigned int code = (fl[c] == 1) ? CODE_SELF : 0u;
+  int cnt = 0;
 #pragma unroll
-  for (int q = 0; q < 6; ++q)
-    if (in[q] && fl[idx[q]] == 1) code |= 1u << q;
-  return (uint8_t)code;
-}
-
-// Index of the parent (level l+1 cell) of the level-l cell (i, j, k).
-__device__ __forceinline__ int parent_index(const MgLevel& C, int i, int j, int k) {
-  return (i >> 1) + C.nx * ((j >> 1) + C.ny * (k >> 1));
+  for (int q = 0; q < 6; ++q) {
+    cnt += in[q];
+    if (in[q] && fl[c + off[q]] == 1) code |= 1u << q;
+  }
+  return code | ((unsigned)cnt << 8);
 }
 
 // ---------------------------------------------------------------- arithmetic
 
 enum SweepMode { FIRST = 0, NORMAL = 1, CORRECT = 2 };
 
-// One Gauss-Seidel update of a cell: x_c = b_c / (s n_c) + (sum of fluid
-// neighbours' x) / n_c, with n_c the count of neighbours inside the grid.
-__device__ __forceinline__ float gs_first(const MgLevel& L, int cnt, float bc) {
-  return __fmul_rn(bc, L.inv_scnt[cnt]);
+__device__ __forceinline__ int code_cnt(unsigned int code) { return (int)((code >> 8) & 7u); }
+
+// One Gauss-Seidel update of a cell of level l: x_c = b_c / (s_l n_c) + (sum of
+// fluid neighbours' x) / n_c, with n_c the count of neighbours inside the grid.
+__device__ __forceinline__ float gs_first(int l, int cnt, float bc) {
+  return __fmul_rn(bc, s_inv_scnt[l][cnt]);
 }
 
-__device__ __forceinline__ float gs_sum(const MgArgs& M, const MgLevel& L, int cnt,
-                                        unsigned int code, float bc, const float (&xv)[6]) {
-  const float base = __fmul_rn(bc, L.inv_scnt[cnt]);
+__device__ __forceinline__ float gs_sum(int l, int cnt, unsigned int code, float bc,
+                                        const float (&xv)[6]) {
+  const float base = __fmul_rn(bc, s_inv_scnt[l][cnt]);
   float sum = 0.0f;
 #pragma unroll
   for (int q = 0; q < 6; ++q) sum += ((code >> q) & 1u) ? xv[q] : 0.0f;
-  return __fmaf_rn(sum, M.inv_cnt[cnt], base);
+  return __fmaf_rn(sum, s_inv_cnt[cnt], base);
 }
 
 // Residual b - A x of a fluid cell, A x in difference form
 // s (sum_fluid (x_c - x_n) + n_air x_c).
-__device__ __forceinline__ float resid(const MgLevel& L, int cnt, unsigned int code, float bc,
-                                       float xc, const float (&xv)[6]) {
+__device__ __forceinline__ float resid(float s, int cnt, unsigned int code, float bc, float xc,
+                                       const float (&xv)[6]) {
   float d = 0.0f;
   int nfl = 0;
 #pragma unroll
@@ -208,279 +250,372 @@ __device__ __forceinline__ float resid(const MgLevel& L, int cnt, unsigned int c
     d += f ? __fsub_rn(xc, xv[q]) : 0.0f;
     nfl += f;
   }
-  return __fsub_rn(bc, __fmul_rn(L.s, __fmaf_rn((float)(cnt - nfl), xc, d)));
+  return __fsub_rn(bc, __fmul_rn(s, __fmaf_rn((float)(cnt - nfl), xc, d)));
 }
 
 // ---------------------------------------------------------------- sweeps
 
 struct GsIn {
-  Cell cl;
+  int i, j, k, idx;
+  bool ok;
   unsigned int code;
   float b;
   float xv[6];
   float pv[6];  // CORRECT: the neighbours' parents on the next coarser level
 };
 
-// Loads of a Gauss-Seidel update on level L (b from bsrc; C is the next coarser
-// level, read in CORRECT mode).  COND: skip the value loads of cells that are
-// not fluid (worth it where many slots are air).
-template <int MODE, bool COND>
-__device__ __forceinline__ void gs_load(const MgLevel& L, const MgLevel& C, const float* bsrc,
-                                        GsIn& s) {
-  if (COND && !(s.code & CODE_SELF)) return;
-  s.b = bsrc[s.cl.c];
-  if constexpr (MODE != FIRST) {
-    int idx[6];
-    nbr_index(L, s.cl, idx);
+// Parents on level C of the six neighbours of cell (i, j, k) of a level with
+// extents (nx, ny, nz); a neighbour off the grid is replaced by the cell itself
+// (its value is unused).
+__device__ __forceinline__ void parent_values(const PV& C, int nx, int ny, int nz, int i, int j,
+                                              int k, float (&pv)[6]) {
+  const int pi[6] = {max(i - 1, 0), min(i + 1, nx - 1), i, i, i, i};
+  const int pj[6] = {j, j, max(j - 1, 0), min(j + 1, ny - 1), j, j};
+  const int pk[6] = {k, k, k, k, max(k - 1, 0), min(k + 1, nz - 1)};
 #pragma unroll
-    for (int q = 0; q < 6; ++q) s.xv[q] = L.x[idx[q]];
-  }
-  if constexpr (MODE == CORRECT) {
-    const int i = s.cl.i, j = s.cl.j, k = s.cl.k;
-    const int pi[6] = {max(i - 1, 0), min(i + 1, L.nx - 1), i, i, i, i};
-    const int pj[6] = {j, j, max(j - 1, 0), min(j + 1, L.ny - 1), j, j};
-    const int pk[6] = {k, k, k, k, max(k - 1, 0), min(k + 1, L.nz - 1)};
-#pragma unroll
-    for (int q = 0; q < 6; ++q) s.pv[q] = C.x[parent_index(C, pi[q], pj[q], pk[q])];
-  }
+  for (int q = 0; q < 6; ++q) pv[q] = C.x[level_index(C, pi[q] >> 1, pj[q] >> 1, pk[q] >> 1)];
 }
 
-// The update of a loaded cell; returns false for slots that are not fluid cells.
 template <int MODE>
-__device__ __forceinline__ bool gs_apply(const MgArgs& M, const MgLevel& L, GsIn& s, float& v) {
-  if (!s.cl.ok || !(s.code & CODE_SELF)) return false;
-  const int cnt = lcount(L, s.cl.i, s.cl.j, s.cl.k);
+__device__ __forceinline__ bool gs_apply(float* x, int l, float omega, GsIn& s, float& v) {
+  if (!s.ok || !(s.code & CODE_SELF)) return false;
+  const int cnt = code_cnt(s.code);
   if constexpr (MODE == FIRST) {
-    v = gs_first(L, cnt, s.b);
+    v = gs_first(l, cnt, s.b);
   } else {
     if constexpr (MODE == CORRECT) {
 #pragma unroll
       for (int q = 0; q < 6; ++q)
-        if ((s.code >> q) & 1u) s.xv[q] = __fmaf_rn(M.omega, s.pv[q], s.xv[q]);
+        if ((s.code >> q) & 1u) s.xv[q] = __fmaf_rn(omega, s.pv[q], s.xv[q]);
     }
-    v = gs_sum(M, L, cnt, s.code, s.b, s.xv);
+    v = gs_sum(l, cnt, s.code, s.b, s.xv);
   }
-  L.x[s.cl.c] = v;
+  x[s.idx] = v;
   return true;
 }
 
-// Half-sweep of one colour over level 0; the right-hand side is the CG residual.
-// With rz, also accumulates r z over the updated cells (the last half-sweep of
-// each colour gives the final z of that colour).
+// Half-sweep of one colour over colour-split level l (description L; C is level
+// l+1, read in CORRECT mode).  With rz, also accumulates b x over the updated
+// cells.
 template <int MODE>
-__device__ __noinline__ void sweep_level0(const PcgArgs& A, int colour, FF* rz) {
+__device__ __noinline__ void sweep_split(const MgArgs& M, const MgLevel& L, const MgLevel& C,
+                                         int l, int colour, FF* rz) {
   constexpr int U = (MODE == CORRECT) ? 2 : 4;
-  const MgArgs& M = A.mg;
-  const MgLevel& L0 = M.lv[0];
-  const MgLevel& L1 = M.lv[M.nlev > 1 ? 1 : 0];
-  const Part p = colour_part0(A);
+  const int lane = threadIdx.x & 31;
+  const SV v = sview(L);
+  const PV cv = pview(C);
+  const int nz = L.nz;
+  const float omega = M.omega;
+  const Items it = seg_items(L, 1);
   FF acc;
   run_batched<U>(
-      (unsigned)p.begin, (unsigned)p.end, (unsigned)p.stride,
-      [&](unsigned int e, bool ok) {
+      it.first, it.end, PCG_WARPS,
+      [&](unsigned int t, bool ok) {
+        const SCell e = scell(v, v.seg[t], colour, lane);
         GsIn s;
-        s.cl = slot_colour0(A, e, colour);
-        s.cl.ok &= ok;
-        s.code = L0.code[s.cl.c];
+        s.i = e.i;
+        s.j = e.j;
+        s.k = e.k;
+        s.idx = e.idx;
+        s.ok = e.ok && ok;
+        s.code = v.code[e.idx];
+        s.b = v.b[e.idx];
+        if constexpr (MODE != FIRST) {
+          int nb[6];
+          snbr(v, e, nb);
+#pragma unroll
+          for (int q = 0; q < 6; ++q) s.xv[q] = v.x[nb[q]];
+        }
+        if constexpr (MODE == CORRECT)
+          parent_values(cv, v.nx, v.ny, nz, min(e.i, v.nx - 1), e.j, e.k, s.pv);
         return s;
       },
-      [&](GsIn& s) { gs_load<MODE, false>(L0, L1, A.r, s); },
+      [&](GsIn&) {},
       [&](GsIn& s) {
-        float v;
-        if (gs_apply<MODE>(M, L0, s, v) && rz) acc.add_prod(s.b, v);
+        float xv;
+        if (gs_apply<MODE>(v.x, l, omega, s, xv) && rz) acc.add_prod(s.b, xv);
       });
   if (rz) {
-    // fold this pass's pair into the caller's accumulator
     rz->add_prod(acc.hi, 1.0f);
     rz->add_prod(acc.lo, 1.0f);
   }
 }
 
-// Half-sweep of one colour over a coarse level L (next coarser level C).
+// The fields of a natural-layout (CTA-local) level, in registers.
+struct NV {
+  float* x;
+  float* b;
+  const uint8_t* code;
+  int nx, ny, nz;
+  float s;
+};
+
+__device__ __forceinline__ NV nview(const MgLevel& L) {
+  return NV{L.x, L.b, L.code, L.nx, L.ny, L.nz, L.s};
+}
+
+__device__ __forceinline__ int ncount(const NV& L, int i, int j, int k) {
+  return (i > 0) + (i < L.nx - 1) + (j > 0) + (j < L.ny - 1) + (k > 0) + (k < L.nz - 1);
+}
+
+__device__ __forceinline__ void nnbr(const NV& L, int i, int j, int k, int c, int (&idx)[6]) {
+  const int sy = L.nx, sz = L.nx * L.ny;
+  idx[0] = i > 0 ? c - 1 : c;
+  idx[1] = i < L.nx - 1 ? c + 1 : c;
+  idx[2] = j > 0 ? c - sy : c;
+  idx[3] = j < L.ny - 1 ? c + sy : c;
+  idx[4] = k > 0 ? c - sz : c;
+  idx[5] = k < L.nz - 1 ? c + sz : c;
+}
+
+// Half-sweep of one colour over natural-layout (CTA-local) level l: each x-row
+// has ceil(nx/2) slots, slot q of row (j, k) is x = 2q + parity.
 template <int MODE>
-__device__ __noinline__ void sweep_level(const MgArgs& M, const MgLevel& L, const MgLevel& C,
-                                         int colour, bool cta_local) {
+__device__ __noinline__ void sweep_nat(const MgArgs& M, const MgLevel& L, const MgLevel& C, int l,
+                                       int colour) {
   constexpr int U = (MODE == CORRECT) ? 2 : 4;
-  const Part p = level_part(((L.nx + 1) >> 1) * L.ny * L.nz, cta_local);
+  const NV v = nview(L);
+  const PV cv = pview(C);
+  const float omega = M.omega;
+  const int hx = (v.nx + 1) >> 1;
+  const Part p = level_part(hx * v.ny * v.nz, true);
   run_batched<U>(
       (unsigned)p.begin, (unsigned)p.end, (unsigned)p.stride,
       [&](unsigned int e, bool ok) {
+        const int row = (int)e / hx, q = (int)e - row * hx;
+        const int j = row % v.ny, k = row / v.ny;
+        int i = 2 * q + ((colour + j + k) & 1);
         GsIn s;
-        s.cl = slot_colour(L, (int)e, colour);
-        s.cl.ok &= ok;
-        s.code = L.code[s.cl.c];
+        s.ok = ok && i < v.nx;
+        i = min(i, v.nx - 1);
+        s.i = i;
+        s.j = j;
+        s.k = k;
+        s.idx = i + v.nx * row;
+        s.code = v.code[s.idx] | ((unsigned)ncount(v, i, j, k) << 8);
         return s;
       },
-      [&](GsIn& s) { gs_load<MODE, true>(L, C, L.b, s); },
       [&](GsIn& s) {
-        float v;
-        gs_apply<MODE>(M, L, s, v);
+        if (!(s.code & CODE_SELF)) return;
+        s.b = v.b[s.idx];
+        if constexpr (MODE != FIRST) {
+          int nb[6];
+          nnbr(v, s.i, s.j, s.k, s.idx, nb);
+#pragma unroll
+          for (int q = 0; q < 6; ++q) s.xv[q] = v.x[nb[q]];
+        }
+        if constexpr (MODE == CORRECT) parent_values(cv, v.nx, v.ny, v.nz, s.i, s.j, s.k, s.pv);
+      },
+      [&](GsIn& s) {
+        float xv;
+        gs_apply<MODE>(v.x, l, omega, s, xv);
       });
 }
 
 // ---------------------------------------------------------------- restriction
 
-// Residual of the red child (dy, dz) of coarse cell (I, J, K): the x offset
-// makes 2I+dx + 2J+dy + 2K+dz even.
+// Residual of the red child (dy, dz) of coarse cell (I, J, K) on the
+// colour-split fine level F.  The child's x offset dx makes its colour red:
+// 2I+dx + 2J+dy + 2K+dz even, so its red slot is I.
 struct ChildIn {
-  Cell cl;
+  bool ok;
   unsigned int code;
   float b, xc;
   float xv[6];
 };
 
-__device__ __forceinline__ void child_load(const MgLevel& F, const float* fb, const Cell& p,
-                                           int dy, int dz, ChildIn& s) {
+__device__ __forceinline__ void child_load(const SV& F, int fnz, int I, int J, int K, int dy,
+                                           int dz, ChildIn& s) {
   const int dx = (dy + dz) & 1;
-  int i = 2 * p.i + dx, j = 2 * p.j + dy, k = 2 * p.k + dz;
-  s.cl.ok = i < F.nx && j < F.ny && k < F.nz;
-  i = min(i, F.nx - 1);
-  j = min(j, F.ny - 1);
-  k = min(k, F.nz - 1);
-  s.cl.i = i;
-  s.cl.j = j;
-  s.cl.k = k;
-  s.cl.c = i + F.nx * (j + F.ny * k);
-  s.code = F.code[s.cl.c];
-  s.b = fb[s.cl.c];
-  s.xc = F.x[s.cl.c];
-  int idx[6];
-  nbr_index(F, s.cl, idx);
+  const int i = 2 * I + dx, j = 2 * J + dy, k = 2 * K + dz;
+  s.ok = i < F.nx && j < F.ny && k < fnz;
+  const int jj = min(j, F.ny - 1), kk = min(k, fnz - 1);
+  const int idx = F.margin + F.hx * (jj + F.ny * kk) + min(I, F.hx - 1);
+  const int ob = idx + F.half;
+  s.code = F.code[idx];
+  s.b = F.b[idx];
+  s.xc = F.x[idx];
+  const int nb[6] = {ob - 1 + dx, ob + dx, ob - F.hx, ob + F.hx, ob - F.pl, ob + F.pl};
 #pragma unroll
-  for (int q = 0; q < 6; ++q) s.xv[q] = F.x[idx[q]];
+  for (int q = 0; q < 6; ++q) s.xv[q] = F.x[nb[q]];
 }
 
-// b_{l+1} = (1/16) sum over fluid children of the level-l residual.  The
+// b_C(I,J,K) = (1/16) sum over fluid children of the fine residual.  The
 // restriction follows the pre-smoothing, whose last half-sweep is black: a black
 // cell's update solves its own equation against the red neighbours it read, so
 // its residual is exactly zero and only the red children contribute.  The four
 // red children are loaded two at a time and summed in the order (dy, dz) =
 // (0,0), (1,0), (0,1), (1,1).
-__device__ __forceinline__ void restrict_cell(const MgLevel& F, const MgLevel& C, const float* fb,
-                                              const Cell& p) {
+__device__ __forceinline__ float restrict_sum(const SV& F, int fnz, int I, int J, int K) {
   float sum = 0.0f;
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     ChildIn ch[2];
 #pragma unroll
-    for (int q = 0; q < 2; ++q) child_load(F, fb, p, q, h, ch[q]);
+    for (int q = 0; q < 2; ++q) child_load(F, fnz, I, J, K, q, h, ch[q]);
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       const ChildIn& c = ch[q];
-      if (!c.cl.ok || !(c.code & CODE_SELF)) continue;
-      sum = __fadd_rn(sum, resid(F, lcount(F, c.cl.i, c.cl.j, c.cl.k), c.code, c.b, c.xc, c.xv));
+      if (!c.ok || !(c.code & CODE_SELF)) continue;
+      sum = __fadd_rn(sum, resid(F.s, code_cnt(c.code), c.code, c.b, c.xc, c.xv));
     }
   }
-  C.b[p.c] = __fmul_rn(sum, 0.0625f);
+  return __fmul_rn(sum, 0.0625f);
 }
 
-// Level 0 -> 1.  Coarse cells are taken per active fine brick (a 4x4x4 block of
-// level 1 whose children all lie in that brick), so no slot falls in the air
-// outside the active bricks.
-__device__ __noinline__ void restrict_level0(const PcgArgs& A) {
-  const MgArgs& M = A.mg;
-  const MgLevel& F = M.lv[0];
-  const MgLevel& C = M.lv[1];
-  const Grid& g = A.g;
-  const unsigned int total = *A.n_active * 64u;
-  unsigned int per = (total + team_size() - 1) / team_size();
-  per = (per + 31u) & ~31u;
-  const unsigned int b = min(total, team_rank() * per), end = min(total, b + per);
-  for (unsigned int e = b + threadIdx.x; e < end; e += PCG_THREADS) {
-    const unsigned int brick = A.active[e >> 6];
-    const int m = (int)(e & 63u);
-    const int i = (int)(brick % (unsigned)g.bx) * (BRICK / 2) + (m & 3);
-    const int j = (int)((brick / (unsigned)g.bx) % (unsigned)g.by) * (BRICK / 2) + ((m >> 2) & 3);
-    const int k = (int)(brick / ((unsigned)g.bx * (unsigned)g.by)) * (BRICK / 2) + (m >> 4);
-    if (i >= C.nx || j >= C.ny || k >= C.nz) continue;
-    const Cell p{i, j, k, i + C.nx * (j + C.ny * k), true};
-    if (!(C.code[p.c] & CODE_SELF)) continue;
-    restrict_cell(F, C, A.r, p);
+// Colour-split F -> colour-split C, over C's active segments; lanes take the
+// segment's 64 cells in x order (so the fine red slots they read are contiguous).
+__device__ __noinline__ void restrict_split(const MgLevel& Fl, const MgLevel& Cl) {
+  const int lane = threadIdx.x & 31;
+  const SV F = sview(Fl), C = sview(Cl);
+  const int fnz = Fl.nz;
+  const Items it = seg_items(Cl, 1);
+  for (unsigned int t = it.first; t < it.end; t += PCG_WARPS) {
+    const int4 sg = C.seg[t];
+    const int J = sg.z, K = sg.w;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int I = sg.y * (2 * SEG_SLOTS) + h * 32 + lane;
+      if (I >= C.nx) continue;
+      const int ci = ((I + J + K) & 1) * C.half + C.margin + C.hx * sg.x + (I >> 1);
+      if (!(C.code[ci] & CODE_SELF)) continue;
+      C.b[ci] = restrict_sum(F, fnz, I, J, K);
+    }
   }
 }
 
-// Coarse level F -> C, over C's cells.
-__device__ __noinline__ void restrict_level(const MgLevel& F, const MgLevel& C, bool cta_local) {
-  const Part p = level_part(C.ncells, cta_local);
+// Colour-split F -> natural-layout C (the first CTA-local level, in global
+// memory), over all of C's cells.
+__device__ __noinline__ void restrict_split_nat(const MgLevel& Fl, const MgLevel& Cl) {
+  const SV F = sview(Fl);
+  const NV C = nview(Cl);
+  const int fnz = Fl.nz;
+  const Part p = level_part(C.nx * C.ny * C.nz, false);
   for (int c = p.begin; c < p.end; c += p.stride) {
     if (!(C.code[c] & CODE_SELF)) continue;
-    restrict_cell(F, C, F.b, cell_at(C, c));
+    const int i = c % C.nx, j = (c / C.nx) % C.ny, k = c / (C.nx * C.ny);
+    C.b[c] = restrict_sum(F, fnz, i, j, k);
+  }
+}
+
+// Natural F -> natural C (CTA-local levels in shared memory).
+__device__ __noinline__ void restrict_nat(const MgLevel& Fl, const MgLevel& Cl) {
+  const NV F = nview(Fl), C = nview(Cl);
+  const Part p = level_part(C.nx * C.ny * C.nz, true);
+  for (int c = p.begin; c < p.end; c += p.stride) {
+    if (!(C.code[c] & CODE_SELF)) continue;
+    const int I = c % C.nx, J = (c / C.nx) % C.ny, K = c / (C.nx * C.ny);
+    float sum = 0.0f;
+    for (int q = 0; q < 4; ++q) {
+      const int dy = q & 1, dz = q >> 1, dx = (dy + dz) & 1;
+      const int i = 2 * I + dx, j = 2 * J + dy, k = 2 * K + dz;
+      if (i >= F.nx || j >= F.ny || k >= F.nz) continue;
+      const int fc = i + F.nx * (j + F.ny * k);
+      const unsigned int code = F.code[fc];
+      if (!(code & CODE_SELF)) continue;
+      int nb[6];
+      nnbr(F, i, j, k, fc, nb);
+      float xv[6];
+#pragma unroll
+      for (int u = 0; u < 6; ++u) xv[u] = F.x[nb[u]];
+      sum = __fadd_rn(sum, resid(F.s, ncount(F, i, j, k), code, F.b[fc], F.x[fc], xv));
+    }
+    C.b[c] = __fmul_rn(sum, 0.0625f);
   }
 }
 
 // ---------------------------------------------------------------- cycle pieces
 
-struct Sync {
-  const PcgArgs* A;
-  bool cta_local;
-  __device__ __forceinline__ bool operator()() const {
-    if (cta_local) {
-      __syncthreads();
-      return true;
-    }
-    return grid_barrier(A->bar, A->status, team_size(), A->timeout_ns);
-  }
-};
-
-// Pre-smoothing of coarse level L from zero, then restriction to C.
-__device__ __forceinline__ bool down_level(const PcgArgs& A, const MgLevel& L, const MgLevel& C,
-                                           bool cta_local) {
-  const MgArgs& M = A.mg;
-  const Sync sync{&A, cta_local};
-  sweep_level<FIRST>(M, L, C, 0, cta_local);
-  if (!sync()) return false;
-  sweep_level<NORMAL>(M, L, C, 1, cta_local);
-  if (!sync()) return false;
-  for (int s = 1; s < M.nu; ++s) {
-    sweep_level<NORMAL>(M, L, C, 0, cta_local);
-    if (!sync()) return false;
-    sweep_level<NORMAL>(M, L, C, 1, cta_local);
-    if (!sync()) return false;
-  }
-  restrict_level(L, C, cta_local);
-  return sync();
+__device__ __forceinline__ bool gsync(const PcgArgs& A) {
+  return grid_barrier(A.bar, A.status, team_size(), A.timeout_ns);
 }
 
-// Coarse correction from C + post-smoothing of coarse level L.
-__device__ __forceinline__ bool up_level(const PcgArgs& A, const MgLevel& L, const MgLevel& C,
-                                         bool cta_local) {
+// Pre-smoothing from zero and restriction, colour-split level l -> l+1.
+__device__ __forceinline__ bool down_split(const PcgArgs& A, int l) {
   const MgArgs& M = A.mg;
-  const Sync sync{&A, cta_local};
-  sweep_level<CORRECT>(M, L, C, 1, cta_local);
-  if (!sync()) return false;
-  sweep_level<NORMAL>(M, L, C, 0, cta_local);
-  if (!sync()) return false;
+  const MgLevel& L = M.lv[l];
+  const MgLevel& C = M.lv[l + 1];
+  sweep_split<FIRST>(M, L, C, l, 0, nullptr);
+  if (!gsync(A)) return false;
+  sweep_split<NORMAL>(M, L, C, l, 1, nullptr);
+  if (!gsync(A)) return false;
   for (int s = 1; s < M.nu; ++s) {
-    sweep_level<NORMAL>(M, L, C, 1, cta_local);
-    if (!sync()) return false;
-    sweep_level<NORMAL>(M, L, C, 0, cta_local);
-    if (!sync()) return false;
+    sweep_split<NORMAL>(M, L, C, l, 0, nullptr);
+    if (!gsync(A)) return false;
+    sweep_split<NORMAL>(M, L, C, l, 1, nullptr);
+    if (!gsync(A)) return false;
+  }
+  if (C.split) restrict_split(L, C);
+  else restrict_split_nat(L, C);
+  return gsync(A);
+}
+
+// Coarse correction from level l+1 and post-smoothing, colour-split level l.
+__device__ __forceinline__ bool up_split(const PcgArgs& A, int l) {
+  const MgArgs& M = A.mg;
+  const MgLevel& L = M.lv[l];
+  const MgLevel& C = M.lv[l + 1];
+  sweep_split<CORRECT>(M, L, C, l, 1, nullptr);
+  if (!gsync(A)) return false;
+  sweep_split<NORMAL>(M, L, C, l, 0, nullptr);
+  if (!gsync(A)) return false;
+  for (int s = 1; s < M.nu; ++s) {
+    sweep_split<NORMAL>(M, L, C, l, 1, nullptr);
+    if (!gsync(A)) return false;
+    sweep_split<NORMAL>(M, L, C, l, 0, nullptr);
+    if (!gsync(A)) return false;
   }
   return true;
 }
 
-// The coarsest level: MG_COARSE_SWEEPS (red, black) pairs from zero, then as many
-// (black, red) pairs.
-__device__ __forceinline__ bool coarsest_level(const PcgArgs& A, const MgLevel& L, bool cta_local) {
-  const MgArgs& M = A.mg;
-  const Sync sync{&A, cta_local};
-  sweep_level<FIRST>(M, L, L, 0, cta_local);
-  if (!sync()) return false;
-  sweep_level<NORMAL>(M, L, L, 1, cta_local);
-  if (!sync()) return false;
+// The same for a CTA-local level (descriptions in shared memory).
+__device__ __forceinline__ void down_nat(const MgArgs& M, const MgLevel* lv, int l) {
+  sweep_nat<FIRST>(M, lv[l], lv[l + 1], l, 0);
+  __syncthreads();
+  sweep_nat<NORMAL>(M, lv[l], lv[l + 1], l, 1);
+  __syncthreads();
+  for (int s = 1; s < M.nu; ++s) {
+    sweep_nat<NORMAL>(M, lv[l], lv[l + 1], l, 0);
+    __syncthreads();
+    sweep_nat<NORMAL>(M, lv[l], lv[l + 1], l, 1);
+    __syncthreads();
+  }
+  restrict_nat(lv[l], lv[l + 1]);
+  __syncthreads();
+}
+
+__device__ __forceinline__ void up_nat(const MgArgs& M, const MgLevel* lv, int l) {
+  sweep_nat<CORRECT>(M, lv[l], lv[l + 1], l, 1);
+  __syncthreads();
+  sweep_nat<NORMAL>(M, lv[l], lv[l + 1], l, 0);
+  __syncthreads();
+  for (int s = 1; s < M.nu; ++s) {
+    sweep_nat<NORMAL>(M, lv[l], lv[l + 1], l, 1);
+    __syncthreads();
+    sweep_nat<NORMAL>(M, lv[l], lv[l + 1], l, 0);
+    __syncthreads();
+  }
+}
+
+// The coarsest level (CTA-local): MG_COARSE_SWEEPS (red, black) pairs from
+// zero, then as many (black, red) pairs.
+__device__ __forceinline__ void coarsest_nat(const MgArgs& M, const MgLevel* lv, int l) {
+  sweep_nat<FIRST>(M, lv[l], lv[l], l, 0);
+  __syncthreads();
+  sweep_nat<NORMAL>(M, lv[l], lv[l], l, 1);
+  __syncthreads();
   for (int s = 1; s < MG_COARSE_SWEEPS; ++s) {
-    sweep_level<NORMAL>(M, L, L, 0, cta_local);
-    if (!sync()) return false;
-    sweep_level<NORMAL>(M, L, L, 1, cta_local);
-    if (!sync()) return false;
+    sweep_nat<NORMAL>(M, lv[l], lv[l], l, 0);
+    __syncthreads();
+    sweep_nat<NORMAL>(M, lv[l], lv[l], l, 1);
+    __syncthreads();
   }
   for (int s = 0; s < MG_COARSE_SWEEPS; ++s) {
-    sweep_level<NORMAL>(M, L, L, 1, cta_local);
-    if (!sync()) return false;
-    sweep_level<NORMAL>(M, L, L, 0, cta_local);
-    if (!sync()) return false;
+    sweep_nat<NORMAL>(M, lv[l], lv[l], l, 1);
+    __syncthreads();
+    sweep_nat<NORMAL>(M, lv[l], lv[l], l, 0);
+    __syncthreads();
   }
-  return true;
 }
 
 // The CTA-local levels [lgrid, nlev) live in shared memory of CTA 0: x, b and
@@ -520,9 +655,9 @@ __device__ __noinline__ void cta_cycle(const PcgArgs& A, CtaMg& sm) {
   const int lg = M.lgrid;
   for (int c = threadIdx.x; c < M.lv[lg].ncells; c += PCG_THREADS) sm.lv[lg].b[c] = M.lv[lg].b[c];
   __syncthreads();
-  for (int l = lg; l < M.nlev - 1; ++l) down_level(A, sm.lv[l], sm.lv[l + 1], true);
-  coarsest_level(A, sm.lv[M.nlev - 1], true);
-  for (int l = M.nlev - 2; l >= lg; --l) up_level(A, sm.lv[l], sm.lv[l + 1], true);
+  for (int l = lg; l < M.nlev - 1; ++l) down_nat(M, sm.lv, l);
+  coarsest_nat(M, sm.lv, M.nlev - 1);
+  for (int l = M.nlev - 2; l >= lg; --l) up_nat(M, sm.lv, l);
   for (int c = threadIdx.x; c < M.lv[lg].ncells; c += PCG_THREADS) M.lv[lg].x[c] = sm.lv[lg].x[c];
 }
 
@@ -533,98 +668,103 @@ __device__ __noinline__ void cta_cycle(const PcgArgs& A, CtaMg& sm) {
 // Returns false if a barrier failed.
 __device__ bool vcycle_rest(const PcgArgs& A, CtaMg& sm, FF& rz) {
   const MgArgs& M = A.mg;
-  const Sync gsync{&A, false};
+  const MgLevel& L0 = M.lv[0];
   if (M.nlev == 1) {  // level 0 is the coarsest level
     // rest of the pre pairs (red, black) after the fused first red half-sweep
     for (int s = 0; s < MG_COARSE_SWEEPS; ++s) {
-      sweep_level0<NORMAL>(A, 1, nullptr);
-      if (!gsync()) return false;
+      sweep_split<NORMAL>(M, L0, L0, 0, 1, nullptr);
+      if (!gsync(A)) return false;
       if (s + 1 < MG_COARSE_SWEEPS) {
-        sweep_level0<NORMAL>(A, 0, nullptr);
-        if (!gsync()) return false;
+        sweep_split<NORMAL>(M, L0, L0, 0, 0, nullptr);
+        if (!gsync(A)) return false;
       }
     }
     // post pairs (black, red); the last black and the last red give r.z
     for (int s = 0; s < MG_COARSE_SWEEPS; ++s) {
-      sweep_level0<NORMAL>(A, 1, s + 1 == MG_COARSE_SWEEPS ? &rz : nullptr);
-      if (!gsync()) return false;
+      sweep_split<NORMAL>(M, L0, L0, 0, 1, s + 1 == MG_COARSE_SWEEPS ? &rz : nullptr);
+      if (!gsync(A)) return false;
       if (s + 1 < MG_COARSE_SWEEPS) {
-        sweep_level0<NORMAL>(A, 0, nullptr);
-        if (!gsync()) return false;
+        sweep_split<NORMAL>(M, L0, L0, 0, 0, nullptr);
+        if (!gsync(A)) return false;
       }
     }
-    sweep_level0<NORMAL>(A, 0, &rz);
+    sweep_split<NORMAL>(M, L0, L0, 0, 0, &rz);
     return true;
   }
-  sweep_level0<NORMAL>(A, 1, nullptr);
-  if (!gsync()) return false;
+  const MgLevel& L1 = M.lv[1];
+  sweep_split<NORMAL>(M, L0, L1, 0, 1, nullptr);
+  if (!gsync(A)) return false;
   for (int s = 1; s < M.nu; ++s) {
-    sweep_level0<NORMAL>(A, 0, nullptr);
-    if (!gsync()) return false;
-    sweep_level0<NORMAL>(A, 1, nullptr);
-    if (!gsync()) return false;
+    sweep_split<NORMAL>(M, L0, L1, 0, 0, nullptr);
+    if (!gsync(A)) return false;
+    sweep_split<NORMAL>(M, L0, L1, 0, 1, nullptr);
+    if (!gsync(A)) return false;
   }
-  restrict_level0(A);
-  if (!gsync()) return false;
+  if (L1.split) restrict_split(L0, L1);
+  else restrict_split_nat(L0, L1);
+  if (!gsync(A)) return false;
   for (int l = 1; l < M.lgrid; ++l)
-    if (!down_level(A, M.lv[l], M.lv[l + 1], false)) return false;
+    if (!down_split(A, l)) return false;
   if (team_rank() == 0) cta_cycle(A, sm);
-  if (!gsync()) return false;
+  if (!gsync(A)) return false;
   for (int l = M.lgrid - 1; l >= 1; --l)
-    if (!up_level(A, M.lv[l], M.lv[l + 1], false)) return false;
-  sweep_level0<CORRECT>(A, 1, M.nu == 1 ? &rz : nullptr);
-  if (!gsync()) return false;
+    if (!up_split(A, l)) return false;
+  sweep_split<CORRECT>(M, L0, L1, 0, 1, M.nu == 1 ? &rz : nullptr);
+  if (!gsync(A)) return false;
   for (int s = 1; s < M.nu; ++s) {
-    sweep_level0<NORMAL>(A, 0, nullptr);
-    if (!gsync()) return false;
-    sweep_level0<NORMAL>(A, 1, s + 1 == M.nu ? &rz : nullptr);
-    if (!gsync()) return false;
+    sweep_split<NORMAL>(M, L0, L1, 0, 0, nullptr);
+    if (!gsync(A)) return false;
+    sweep_split<NORMAL>(M, L0, L1, 0, 1, s + 1 == M.nu ? &rz : nullptr);
+    if (!gsync(A)) return false;
   }
-  sweep_level0<NORMAL>(A, 0, &rz);  // the last red half-sweep
+  sweep_split<NORMAL>(M, L0, L1, 0, 0, &rz);  // the last red half-sweep
   return true;
 }
 
 // ---------------------------------------------------------------- level-0 passes
 
-// This thread's slots of level 0's active-cell index space.
-__device__ __forceinline__ Part dense_part0(const Chunk& ch) {
-  return Part{(int)(ch.begin + threadIdx.x), (int)ch.end, PCG_THREADS};
-}
-
 // Phase A with z from the V-cycle: p_new = z + beta p_old (recomputed for the
-// neighbours), q = A p_new in difference form, partial p.q.
-__device__ __noinline__ void phase_a(const PcgArgs& A, const Chunk& ch, const float* z,
-                                        const float* pold, float* pnew, float beta, FF& pq) {
-  const MgLevel& L0 = A.mg.lv[0];
-  const Part p = dense_part0(ch);
+// neighbours), q = A p_new in difference form, partial p.q.  Both colours.
+__device__ __noinline__ void phase_a(const PcgArgs& A, const float* pold, float* pnew, float beta,
+                                     FF& pq) {
+  const MgArgs& M = A.mg;
+  const SV v = sview(M.lv[0]);
+  const float* z = v.x;
+  float* q0 = M.q0;
+  const float s_a = A.s;
+  const int lane = threadIdx.x & 31;
+  const Items it = seg_items(M.lv[0], 2);
   struct S {
-    Cell cl;
+    int idx;
+    bool ok;
     unsigned int code;
     float zc, pc;
     float zv[6], pv[6];
   };
+  FF acc;
   run_batched<2>(
-      (unsigned)p.begin, (unsigned)p.end, (unsigned)p.stride,
-      [&](unsigned int e, bool ok) {
+      it.first, it.end, PCG_WARPS,
+      [&](unsigned int t, bool ok) {
+        const SCell e = scell(v, v.seg[t >> 1], (int)(t & 1u), lane);
         S s;
-        s.cl = slot_dense0(A, e);
-        s.cl.ok &= ok;
-        s.code = L0.code[s.cl.c];
-        s.zc = z[s.cl.c];
-        s.pc = pold[s.cl.c];
-        int idx[6];
-        nbr_index(L0, s.cl, idx);
+        s.idx = e.idx;
+        s.ok = e.ok && ok;
+        s.code = v.code[e.idx];
+        s.zc = z[e.idx];
+        s.pc = pold[e.idx];
+        int nb[6];
+        snbr(v, e, nb);
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
-          s.zv[q] = z[idx[q]];
-          s.pv[q] = pold[idx[q]];
+          s.zv[q] = z[nb[q]];
+          s.pv[q] = pold[nb[q]];
         }
         return s;
       },
       [&](S&) {},
       [&](S& s) {
-        if (!s.cl.ok || !(s.code & CODE_SELF)) return;
-        const int cnt = lcount(L0, s.cl.i, s.cl.j, s.cl.k);
+        if (!s.ok || !(s.code & CODE_SELF)) return;
+        const int cnt = code_cnt(s.code);
         const float pc = __fmaf_rn(beta, s.pc, s.zc);
         float d = 0.0f;
         int nfl = 0;
@@ -634,72 +774,85 @@ __device__ __noinline__ void phase_a(const PcgArgs& A, const Chunk& ch, const fl
           d += f ? __fsub_rn(pc, __fmaf_rn(beta, s.pv[q], s.zv[q])) : 0.0f;
           nfl += f;
         }
-        const float qc = __fmul_rn(A.s, __fmaf_rn((float)(cnt - nfl), pc, d));
-        pnew[s.cl.c] = pc;
-        A.q[s.cl.c] = qc;
-        pq.add_prod(pc, qc);
+        const float qc = __fmul_rn(s_a, __fmaf_rn((float)(cnt - nfl), pc, d));
+        pnew[s.idx] = pc;
+        q0[s.idx] = qc;
+        acc.add_prod(pc, qc);
       });
+  pq.add_prod(acc.hi, 1.0f);
+  pq.add_prod(acc.lo, 1.0f);
 }
 
-// Phase B: x += alpha p, r -= alpha q, partial r.r, and the next V-cycle's first
-// red half-sweep (from zero) z = r / (s n) on red cells.
-__device__ __noinline__ void phase_b(const PcgArgs& A, const Chunk& ch, float* x, float* z,
-                                        const float* pnew, float alpha, FF& rr) {
-  const MgLevel& L0 = A.mg.lv[0];
-  const Part p = dense_part0(ch);
+// Phase B: d += alpha p, r -= alpha q, partial r.r, and the next V-cycle's first
+// red half-sweep (from zero) z = r / (s n) on red cells.  Both colours.
+__device__ __noinline__ void phase_b(const PcgArgs& A, const float* pnew, float alpha, FF& rr) {
+  const MgArgs& M = A.mg;
+  const SV v = sview(M.lv[0]);
+  float* d0 = M.d0;
+  const float* q0 = M.q0;
+  const int lane = threadIdx.x & 31;
+  const Items it = seg_items(M.lv[0], 2);
   struct S {
-    Cell cl;
+    int idx, c;
+    bool ok;
     unsigned int code;
-    float x, p, q, r;
+    float d, p, q, r;
   };
+  FF acc;
   run_batched<4>(
-      (unsigned)p.begin, (unsigned)p.end, (unsigned)p.stride,
-      [&](unsigned int e, bool ok) {
+      it.first, it.end, PCG_WARPS,
+      [&](unsigned int t, bool ok) {
+        const SCell e = scell(v, v.seg[t >> 1], (int)(t & 1u), lane);
         S s;
-        s.cl = slot_dense0(A, e);
-        s.cl.ok &= ok;
-        s.code = L0.code[s.cl.c];
-        s.x = x[s.cl.c];
-        s.p = pnew[s.cl.c];
-        s.q = A.q[s.cl.c];
-        s.r = A.r[s.cl.c];
+        s.idx = e.idx;
+        s.c = (int)(t & 1u);
+        s.ok = e.ok && ok;
+        s.code = v.code[e.idx];
+        s.d = d0[e.idx];
+        s.p = pnew[e.idx];
+        s.q = q0[e.idx];
+        s.r = v.b[e.idx];
         return s;
       },
       [&](S&) {},
       [&](S& s) {
-        if (!s.cl.ok || !(s.code & CODE_SELF)) return;
-        const int c = s.cl.c;
-        x[c] = __fmaf_rn(alpha, s.p, s.x);
+        if (!s.ok || !(s.code & CODE_SELF)) return;
+        d0[s.idx] = __fmaf_rn(alpha, s.p, s.d);
         const float rc = __fmaf_rn(-alpha, s.q, s.r);
-        A.r[c] = rc;
-        if (((s.cl.i + s.cl.j + s.cl.k) & 1) == 0)
-          z[c] = gs_first(L0, lcount(L0, s.cl.i, s.cl.j, s.cl.k), rc);
-        rr.add_prod(rc, rc);
+        v.b[s.idx] = rc;
+        if (s.c == 0) v.x[s.idx] = gs_first(0, code_cnt(s.code), rc);
+        acc.add_prod(rc, rc);
       });
+  rr.add_prod(acc.hi, 1.0f);
+  rr.add_prod(acc.lo, 1.0f);
 }
 
-// One pass over this thread's fluid cells of level 0 (start of the solve and the
-// rare refinement passes; not batched).
+// One pass over this thread's fluid cells of level 0, both colours (start of the
+// solve, the refinements and the end: not batched).  f(e, code, n) gets the slot,
+// its code and the natural index n of the cell.
 template <class F>
-__device__ __forceinline__ void for_fluid0(const PcgArgs& A, const Chunk& ch, F&& f) {
+__device__ __forceinline__ void for_fluid0(const PcgArgs& A, F&& f) {
   const MgLevel& L0 = A.mg.lv[0];
-  for (unsigned int e = ch.begin + threadIdx.x; e < ch.end; e += PCG_THREADS) {
-    const Cell cl = slot_dense0(A, e);
-    if (!cl.ok || !(L0.code[cl.c] & CODE_SELF)) continue;
-    f(cl);
+  const int lane = threadIdx.x & 31;
+  const Items it = seg_items(L0, 2);
+  for (unsigned int t = it.first; t < it.end; t += PCG_WARPS) {
+    const SCell e = scell(L0, L0.seg[t >> 1], (int)(t & 1u), lane);
+    if (!e.ok) continue;
+    const unsigned int code = L0.code16[e.idx];
+    if (!(code & CODE_SELF)) continue;
+    f(e, code, e.i + L0.nx * e.r);
   }
 }
 
-// FP64 residual of one cell for the refinement: b - A x with x in FP64.
-__device__ __forceinline__ double residual64(const PcgArgs& A, const Cell& cl) {
-  const MgLevel& L0 = A.mg.lv[0];
-  const unsigned int code = L0.code[cl.c];
-  int idx[6];
-  nbr_index(L0, cl, idx);
-  const double xc = A.x64[cl.c];
+// FP64 residual of one cell for the refinement: b - A x with x in FP64 (natural
+// layout).
+__device__ __forceinline__ double residual64(const PcgArgs& A, unsigned int code, int n) {
+  const Grid& g = A.g;
+  const int off[6] = {-1, 1, -g.nx, g.nx, -g.nx * g.ny, g.nx * g.ny};
+  const double xc = A.x64[n];
   double xv[6];
 #pragma unroll
-  for (int q = 0; q < 6; ++q) xv[q] = A.x64[idx[q]];
+  for (int q = 0; q < 6; ++q) xv[q] = A.x64[((code >> q) & 1u) ? n + off[q] : n];
   double d = 0.0;
   int nfl = 0;
 #pragma unroll
@@ -708,20 +861,42 @@ __device__ __forceinline__ double residual64(const PcgArgs& A, const Cell& cl) {
     d += f ? xc - xv[q] : 0.0;
     nfl += f;
   }
-  const int cnt = lcount(L0, cl.i, cl.j, cl.k);
-  return A.b64[cl.c] - A.s64 * ((double)(cnt - nfl) * xc + d);
+  return A.b64[n] - A.s64 * ((double)(code_cnt(code) - nfl) * xc + d);
 }
 
-// Builds the neighbour codes of level 0 (cells of active bricks), the fluid flags
-// of levels 1.. (a coarse cell is fluid when any child is) and their codes.
-// Ends with a grid barrier.
-__device__ __noinline__ bool build_levels(const PcgArgs& A, const Chunk& ch) {
-  const MgArgs& M = A.mg;
-  const MgLevel& L0 = M.lv[0];
-  for (unsigned int e = ch.begin + threadIdx.x; e < ch.end; e += PCG_THREADS) {
-    const Cell cl = slot_dense0(A, e);
-    if (cl.ok) L0.code[cl.c] = make_code(L0, A.type, cl);
+// ---------------------------------------------------------------- set-up
+
+// Whether segment g (flat: row g / nw, segment g % nw) of split level L meets a
+// block holding fluid; sg receives {row, segment in row, j, k}.  Level 0 reads
+// the binning's brick fluid counts.
+__device__ __forceinline__ bool seg_active(const PcgArgs& A, const MgLevel& L, int l, int g,
+                                           int4& sg) {
+  const int r = g / L.nw, w = g - r * L.nw;
+  const int j = r % L.ny, k = r / L.ny;
+  sg = make_int4(r, w, j, k);
+  const int by = j >> 3, bz = k >> 3;
+  const int b0 = w * 8, b1 = min(L.nbx, b0 + 8);
+  bool any = false;
+  for (int bx = b0; bx < b1; ++bx) {
+    const int bi = bx + L.nbx * (by + L.nby * bz);
+    any |= (l == 0) ? (A.brick_fluid[bi] > 0u) : (L.bflag[bi] != 0);
   }
+  return any;
+}
+
+// Builds, once per solve: the fluid flags of levels 1.. (a coarse cell is fluid
+// when any child is) with their block flags, the active-segment lists of the
+// colour-split levels (in segment order, so the work split is deterministic),
+// the codes of every level.  Ends with a grid barrier.
+__device__ __noinline__ bool build_levels(const PcgArgs& A, Shared& sh) {
+  const MgArgs& M = A.mg;
+  // block flags of the split coarse levels start clear
+  for (int l = 1; l < M.lgrid; ++l) {
+    const MgLevel& L = M.lv[l];
+    const Part p = level_part(L.nbx * L.nby * L.nbz, false);
+    for (int c = p.begin; c < p.end; c += p.stride) L.bflag[c] = 0;
+  }
+  if (!gsync(A)) return false;
   for (int l = 1; l < M.nlev; ++l) {
     const MgLevel& F = M.lv[l - 1];
     const MgLevel& C = M.lv[l];
@@ -734,15 +909,93 @@ __device__ __noinline__ bool build_levels(const PcgArgs& A, const Chunk& ch) {
         if (fi < F.nx && fj < F.ny && fk < F.nz && F.t[fi + F.nx * (fj + F.ny * fk)] == 1) f = 1;
       }
       C.t[c] = f;
+      if (f && C.split) C.bflag[(i >> 3) + C.nbx * ((j >> 3) + C.nby * (k >> 3))] = 1;
     }
-    if (!grid_barrier(A.bar, A.status, team_size(), A.timeout_ns)) return false;
+    if (!gsync(A)) return false;
   }
-  for (int l = 1; l < M.nlev; ++l) {
-    const MgLevel& C = M.lv[l];
-    const Part p = level_part(C.ncells, false);
-    for (int c = p.begin; c < p.end; c += p.stride) C.code[c] = make_code(C, C.t, cell_at(C, c));
+  // active segments: count per CTA, then write them in segment order
+  __shared__ unsigned int s_wsum[PCG_WARPS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int l = 0; l < M.lgrid; ++l) {
+    const MgLevel& L = M.lv[l];
+    const int nsegs = L.nw * L.ny * L.nz;
+    const int per = (nsegs + (int)team_size() - 1) / (int)team_size();
+    const int g0 = min(nsegs, (int)team_rank() * per), g1 = min(nsegs, g0 + per);
+    unsigned int cnt = 0;
+    for (int g = g0 + (int)threadIdx.x; g < g1; g += PCG_THREADS) {
+      int4 sg;
+      cnt += seg_active(A, L, l, g, sg);
+    }
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
+    if (lane == 0) s_wsum[warp] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned int tot = 0;
+      for (int w = 0; w < PCG_WARPS; ++w) tot += s_wsum[w];
+      M.segcount[l * team_size() + team_rank()] = tot;
+    }
+    __syncthreads();
   }
-  return grid_barrier(A.bar, A.status, team_size(), A.timeout_ns);
+  if (!gsync(A)) return false;
+  for (int l = 0; l < M.lgrid; ++l) {
+    const MgLevel& L = M.lv[l];
+    const int nsegs = L.nw * L.ny * L.nz;
+    const int per = (nsegs + (int)team_size() - 1) / (int)team_size();
+    const int g0 = min(nsegs, (int)team_rank() * per), g1 = min(nsegs, g0 + per);
+    // this CTA's offset: the counts of the CTAs before it
+    if (warp == 0) {
+      unsigned int before = 0, total = 0;
+      for (unsigned int t = lane; t < team_size(); t += 32) {
+        const unsigned int v = M.segcount[l * team_size() + t];
+        total += v;
+        before += (t < team_rank()) ? v : 0u;
+      }
+      before = __reduce_add_sync(0xffffffffu, before);
+      total = __reduce_add_sync(0xffffffffu, total);
+      if (lane == 0) {
+        sh.dscal[0] = (double)before;
+        if (team_rank() == 0) *L.nseg = total;
+      }
+    }
+    __syncthreads();
+    unsigned int base = (unsigned int)sh.dscal[0];
+    __syncthreads();
+    for (int g00 = g0; g00 < g1; g00 += PCG_THREADS) {
+      const int g = g00 + (int)threadIdx.x;
+      int4 sg = make_int4(0, 0, 0, 0);
+      const bool act = g < g1 && seg_active(A, L, l, g, sg);
+      const unsigned int bal = __ballot_sync(0xffffffffu, act);
+      if (lane == 0) s_wsum[warp] = __popc(bal);
+      __syncthreads();
+      unsigned int off = 0, tot = 0;
+      for (int w = 0; w < PCG_WARPS; ++w) {
+        off += (w < warp) ? s_wsum[w] : 0u;
+        tot += s_wsum[w];
+      }
+      if (act) L.seg[base + off + __popc(bal & ((1u << lane) - 1u))] = sg;
+      base += tot;
+      __syncthreads();
+    }
+  }
+  if (!gsync(A)) return false;
+  // codes: split levels over their active segments, CTA-local levels over all cells
+  for (int l = 0; l < M.lgrid; ++l) {
+    const MgLevel& L = M.lv[l];
+    const Items it = seg_items(L, 2);
+    for (unsigned int t = it.first; t < it.end; t += PCG_WARPS) {
+      const SCell e = scell(L, L.seg[t >> 1], (int)(t & 1u), lane);
+      if (e.ok) L.code16[e.idx] = (uint16_t)make_code(L, L.t, e.i, e.j, e.k);
+    }
+  }
+  for (int l = M.lgrid; l < M.nlev; ++l) {
+    const MgLevel& L = M.lv[l];
+    const Part p = level_part(L.ncells, false);
+    for (int c = p.begin; c < p.end; c += p.stride) {
+      const Cell cl = cell_at(L, c);
+      L.code[c] = (uint8_t)(make_code(L, L.t, cl.i, cl.j, cl.k) & 0x7fu);
+    }
+  }
+  return gsync(A);
 }
 
 struct SolveState {
@@ -759,28 +1012,29 @@ struct SolveState {
 // (refinement).  A slot's readers always pass another barrier before the slot
 // is written again.
 template <bool MIXED>
-__device__ void solve_mg(const PcgArgs& A, const Chunk& ch, Shared& sh, CtaMg& sm,
-                         SolveState& S) {
-  float* x = A.x32;
-  float* z = A.mg.lv[0].x;
-  const MgLevel& L0 = A.mg.lv[0];
-  if (!build_levels(A, ch)) { S.ok = false; return; }
-  if (A.mg.nlev > 1 && team_rank() == 0) cta_levels_init(A.mg, sm);
-  // ---- start: r = b, x = 0, p_old = 0, first red half-sweep of the V-cycle
+__device__ void solve_mg(const PcgArgs& A, Shared& sh, CtaMg& sm, SolveState& S) {
+  const MgArgs& M = A.mg;
+  const MgLevel& L0 = M.lv[0];
+  float* d = M.d0;
+  float* z = L0.x;
+  float* r = L0.b;
+  if (!build_levels(A, sh)) { S.ok = false; return; }
+  if (M.nlev > 1 && team_rank() == 0) cta_levels_init(M, sm);
+  // ---- start: r = b, d = 0, p_old = 0, first red half-sweep of the V-cycle
   {
     FF bb;
-    for_fluid0(A, ch, [&](const Cell& cl) {
-      const float bc = MIXED ? (float)A.b64[cl.c] : A.b32[cl.c];
-      A.r[cl.c] = bc;
-      x[cl.c] = 0.0f;
-      A.pa[cl.c] = 0.0f;
-      if (((cl.i + cl.j + cl.k) & 1) == 0) z[cl.c] = gs_first(L0, lcount(L0, cl.i, cl.j, cl.k), bc);
+    for_fluid0(A, [&](const SCell& e, unsigned int code, int n) {
+      const float bc = MIXED ? (float)A.b64[n] : A.b32[n];
+      r[e.idx] = bc;
+      d[e.idx] = 0.0f;
+      M.pa0[e.idx] = 0.0f;
+      if (e.idx < L0.half) z[e.idx] = gs_first(0, code_cnt(code), bc);
       bb.add_prod(bc, bc);
     });
     F2 v[1] = {f2_of(bb)};
     publish<1>(A, 4, v, sh);
   }
-  if (!grid_barrier(A.bar, A.status, team_size(), A.timeout_ns)) { S.ok = false; return; }
+  if (!gsync(A)) { S.ok = false; return; }
   double rz = 0.0, bnorm = 0.0, rnorm = 0.0, rmax = 0.0;
   const double target = MIXED ? A.ir_tol : A.tol;
   {
@@ -795,8 +1049,8 @@ __device__ void solve_mg(const PcgArgs& A, const Chunk& ch, Shared& sh, CtaMg& s
   __syncthreads();
   int it = 0, refinements = 0;
   bool conv = sh.flag == 1, first = true;
-  float* pold = A.pa;
-  float* pnew = A.pb;
+  float* pold = M.pa0;
+  float* pnew = M.pb0;
   while (!conv) {
     FF rzp;
     if (!vcycle_rest(A, sm, rzp)) { S.ok = false; return; }
@@ -804,7 +1058,7 @@ __device__ void solve_mg(const PcgArgs& A, const Chunk& ch, Shared& sh, CtaMg& s
       F2 v[1] = {f2_of(rzp)};
       publish<1>(A, 3, v, sh);
     }
-    if (!grid_barrier(A.bar, A.status, team_size(), A.timeout_ns)) { S.ok = false; return; }
+    if (!gsync(A)) { S.ok = false; return; }
     {
       double s[1];
       gather<1>(A, 3, s, sh);
@@ -822,12 +1076,12 @@ __device__ void solve_mg(const PcgArgs& A, const Chunk& ch, Shared& sh, CtaMg& s
     const float beta = sh.beta;
     // ---- phase A
     FF pq;
-    phase_a(A, ch, z, pold, pnew, beta, pq);
+    phase_a(A, pold, pnew, beta, pq);
     {
       F2 v[1] = {f2_of(pq)};
       publish<1>(A, 0, v, sh);
     }
-    if (!grid_barrier(A.bar, A.status, team_size(), A.timeout_ns)) { S.ok = false; return; }
+    if (!gsync(A)) { S.ok = false; return; }
     {
       double s[1];
       gather<1>(A, 0, s, sh);
@@ -837,12 +1091,12 @@ __device__ void solve_mg(const PcgArgs& A, const Chunk& ch, Shared& sh, CtaMg& s
     const float alpha = sh.alpha;
     // ---- phase B (+ the next V-cycle's first red half-sweep)
     FF rr;
-    phase_b(A, ch, x, z, pnew, alpha, rr);
+    phase_b(A, pnew, alpha, rr);
     {
       F2 v[1] = {f2_of(rr)};
       publish<1>(A, 1, v, sh);
     }
-    if (!grid_barrier(A.bar, A.status, team_size(), A.timeout_ns)) { S.ok = false; return; }
+    if (!gsync(A)) { S.ok = false; return; }
     {
       double s[1];
       gather<1>(A, 1, s, sh);
@@ -859,22 +1113,21 @@ __device__ void solve_mg(const PcgArgs& A, const Chunk& ch, Shared& sh, CtaMg& s
     if constexpr (MIXED) {
       if (sh.flag == 2) {
         // ---- refinement: x64 += d, d = 0; r = b - A x64 in FP64 (+ first red half-sweep)
-        for_fluid0(A, ch, [&](const Cell& cl) {
-          A.x64[cl.c] += (double)x[cl.c];
-          x[cl.c] = 0.0f;
+        for_fluid0(A, [&](const SCell& e, unsigned int, int n) {
+          A.x64[n] += (double)d[e.idx];
+          d[e.idx] = 0.0f;
         });
-        if (!grid_barrier(A.bar, A.status, team_size(), A.timeout_ns)) { S.ok = false; return; }
+        if (!gsync(A)) { S.ok = false; return; }
         FF rr64;
-        for_fluid0(A, ch, [&](const Cell& cl) {
-          const float r32 = (float)residual64(A, cl);
-          A.r[cl.c] = r32;
-          if (((cl.i + cl.j + cl.k) & 1) == 0)
-            z[cl.c] = gs_first(L0, lcount(L0, cl.i, cl.j, cl.k), r32);
+        for_fluid0(A, [&](const SCell& e, unsigned int code, int n) {
+          const float r32 = (float)residual64(A, code, n);
+          r[e.idx] = r32;
+          if (e.idx < L0.half) z[e.idx] = gs_first(0, code_cnt(code), r32);
           rr64.add_prod(r32, r32);
         });
         F2 v[1] = {f2_of(rr64)};
         publish<1>(A, 5, v, sh);
-        if (!grid_barrier(A.bar, A.status, team_size(), A.timeout_ns)) { S.ok = false; return; }
+        if (!gsync(A)) { S.ok = false; return; }
         double s[1];
         gather<1>(A, 5, s, sh);
         ++refinements;
@@ -893,19 +1146,21 @@ __device__ void solve_mg(const PcgArgs& A, const Chunk& ch, Shared& sh, CtaMg& s
     }
     if (sh.flag == 1) { conv = true; break; }
   }
+  // ---- the solution in natural layout: the FP32 pressure, or x64 and its pair
   if constexpr (MIXED) {
-    if (!conv) {
-      for_fluid0(A, ch, [&](const Cell& cl) {
-        A.x64[cl.c] += (double)x[cl.c];
-        x[cl.c] = 0.0f;
-      });
-    }
-    for_fluid0(A, ch, [&](const Cell& cl) {
-      const double xv = A.x64[cl.c];
+    for_fluid0(A, [&](const SCell& e, unsigned int, int n) {
+      double xv = A.x64[n];
+      if (!conv) {
+        xv += (double)d[e.idx];
+        A.x64[n] = xv;
+        d[e.idx] = 0.0f;
+      }
       const float hi = __double2float_rn(xv);
       const float lo = __double2float_rn(xv - (double)hi);
-      A.pff[cl.c] = make_float2(hi, lo);
+      A.pff[n] = make_float2(hi, lo);
     });
+  } else {
+    for_fluid0(A, [&](const SCell& e, unsigned int, int n) { A.x32[n] = d[e.idx]; });
   }
   S.iters = it;
   S.refinements = refinements;
@@ -916,11 +1171,10 @@ __device__ void solve_mg(const PcgArgs& A, const Chunk& ch, Shared& sh, CtaMg& s
 
 template <bool MIXED>
 __device__ void solve_scene_mg(const PcgArgs& A, Shared& sh, CtaMg& sm) {
-  const unsigned int nact = *A.n_active;
   const long long ncells = (long long)A.g.nx * A.g.ny * A.g.nz;
   const bool singular = A.check_singular && ((long long)A.stats->n_fluid == ncells);
   SolveState S;
-  if (!singular) solve_mg<MIXED>(A, my_chunk(nact), sh, sm, S);
+  if (!singular) solve_mg<MIXED>(A, sh, sm, S);
   if (team_rank() == 0 && threadIdx.x == 0) {
     int st = 0;
     if (singular) st |= DEV_SINGULAR;
@@ -940,6 +1194,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg_mg(const __grid_constant
   __shared__ Shared sh;
   __shared__ CtaMg sm;
   team_enter(blockIdx.x, gridDim.x);
+  load_tables(A.mg);
   solve_scene_mg<MIXED>(A, sh, sm);
 }
 
@@ -951,6 +1206,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg_mg_batch(const __grid_co
   __shared__ CtaMg sm;
   const int s = B.block_scene[blockIdx.x];
   team_enter(blockIdx.x - B.team_first[s], B.team_first[s + 1] - B.team_first[s]);
+  load_tables(B.args[s].mg);
   solve_scene_mg<MIXED>(B.args[s], sh, sm);
 }
 
