@@ -336,6 +336,10 @@ void carve(flip_handle* h, Carver& cv) {
           m.pb0 = cv.take<float>(ns);
           m.q0 = cv.take<float>(ns);
           m.d0 = cv.take<float>(ns);
+          if (h->mixed) {
+            m.x2 = cv.take<float2>(ns);
+            m.b2 = cv.take<float2>(ns);
+          }
         }
       } else {
         L.x = cv.take<float>(n);

@@ -89,6 +89,8 @@ struct MgArgs {
   float* pb0;         // direction (double-buffered), A p, and the solution /
   float* q0;          // mixed-mode correction d
   float* d0;
+  float2* x2;         // mixed mode: the solution as a float pair (hi, lo), and
+  float2* b2;         // the right-hand side as a float pair, colour-split like level 0
   unsigned int* segcount;  // [MG_MAX_LEVELS * max_blocks] per-CTA segment counts
   MgLevel lv[MG_MAX_LEVELS];
 };

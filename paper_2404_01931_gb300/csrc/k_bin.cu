@@ -5,7 +5,7 @@
 // built by the atomics of the step that moved the particles (the G2P epilogue,
 // or k_rebin after creation / a write), whose return value is the particle's
 // rank inside its cell.  Then:
-//   k_cell_local_scan  one CTA per 8x8x8 brick: exclusive scan of its 512
+//   k_cell_local_scan  one warp per 8x8x8 brick: exclusive scan of its 512
 //                      counts (local offsets), the brick total, cell types
 //                      (fluid = count > 0), and clears the counts for the next
 //                      step's atomics
@@ -30,35 +30,71 @@ __global__ void k_rebin(const Grid g, const PartView p, const BinView b, long lo
   b.rank[i] = atomicAdd(b.cell_count + key, 1u);
 }
 
-__global__ void __launch_bounds__(BRICK_CELLS) k_cell_local_scan(const Grid g, const BinView b,
-                                                                   uint8_t* __restrict__ type) {
-  __shared__ unsigned int warp_tot[BRICK_CELLS / 32];
-  const unsigned int brick = blockIdx.x;
-  const int l = threadIdx.x, lane = l & 31, warp = l >> 5;
-  const unsigned int key = brick * BRICK_CELLS + (unsigned)l;
-  const unsigned int cnt = b.cell_count[key];
-  b.cell_count[key] = 0u;
-  unsigned int incl = cnt;
+// One warp per brick: lane l owns the 16 consecutive keys 16l .. 16l+15 (two
+// x-rows of the brick), read and written as four 16-byte vectors.
+constexpr int SCAN_THREADS = 256;
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_cell_local_scan(const Grid g, const BinView b,
+                                                                    uint8_t* __restrict__ type,
+                                                                    unsigned int nb) {
+  const int lane = threadIdx.x & 31;
+  const unsigned int brick = blockIdx.x * (SCAN_THREADS / 32) + (threadIdx.x >> 5);
+  if (brick >= nb) return;
+  const unsigned int key0 = brick * BRICK_CELLS + 16u * (unsigned)lane;
+  uint4* cnt4 = reinterpret_cast<uint4*>(b.cell_count + key0);
+  uint4* st4 = reinterpret_cast<uint4*>(b.local_start + key0);
+  unsigned int c[16];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const uint4 t = cnt4[v];
+    c[4 * v] = t.x;
+    c[4 * v + 1] = t.y;
+    c[4 * v + 2] = t.z;
+    c[4 * v + 3] = t.w;
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) cnt4[v] = make_uint4(0u, 0u, 0u, 0u);
+  unsigned int tot = 0;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) tot += c[q];
+  unsigned int incl = tot;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const unsigned int t = __shfl_up_sync(0xffffffffu, incl, o);
     if (lane >= o) incl += t;
   }
-  if (lane == 31) warp_tot[warp] = incl;
-  __syncthreads();
-  unsigned int woff = 0;
+  unsigned int run = incl - tot;
+  unsigned int ex[16];
 #pragma unroll
-  for (int w = 0; w < BRICK_CELLS / 32; ++w) woff += (w < warp) ? warp_tot[w] : 0u;
-  const unsigned int excl = woff + incl - cnt;
-  b.local_start[key] = excl;
-  if (l == BRICK_CELLS - 1) b.brick_count[brick] = excl + cnt;
-  const int i = (int)(brick % (unsigned)g.bx) * BRICK + (l & 7);
-  const int j = (int)((brick / (unsigned)g.bx) % (unsigned)g.by) * BRICK + ((l >> 3) & 7);
-  const int k = (int)(brick / ((unsigned)g.bx * (unsigned)g.by)) * BRICK + (l >> 6);
-  const bool inside = (i < g.nx && j < g.ny && k < g.nz);
-  if (inside) type[i + g.nx * (j + g.ny * k)] = (cnt > 0u) ? 1 : 0;
-  const int nfl = __syncthreads_count(inside && cnt > 0u);
-  if (l == 0) b.brick_fluid[brick] = (unsigned)nfl;
+  for (int q = 0; q < 16; ++q) {
+    ex[q] = run;
+    run += c[q];
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) st4[v] = make_uint4(ex[4 * v], ex[4 * v + 1], ex[4 * v + 2], ex[4 * v + 3]);
+  if (lane == 31) b.brick_count[brick] = incl;
+  // cell types of the two rows (fluid = count > 0) and the brick's fluid count
+  const int i0 = (int)(brick % (unsigned)g.bx) * BRICK;
+  const int j0 = (int)((brick / (unsigned)g.bx) % (unsigned)g.by) * BRICK;
+  const int k0 = (int)(brick / ((unsigned)g.bx * (unsigned)g.by)) * BRICK;
+  const int k = k0 + (lane >> 2);
+  int nfl = 0;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int j = j0 + ((2 * lane + h) & 7);
+    if (j >= g.ny || k >= g.nz) continue;
+    uint8_t* row = type + (size_t)g.nx * (j + (size_t)g.ny * k);
+#pragma unroll
+    for (int x = 0; x < 8; ++x) {
+      const int i = i0 + x;
+      if (i >= g.nx) continue;
+      const bool f = c[8 * h + x] > 0u;
+      row[i] = f ? 1 : 0;
+      nfl += f;
+    }
+  }
+  nfl = __reduce_add_sync(0xffffffffu, (unsigned)nfl);
+  if (lane == 0) b.brick_fluid[brick] = (unsigned)nfl;
 }
 
 // One CTA of 1024 threads walks all bricks in chunks: exclusive scan of the
@@ -105,18 +141,35 @@ __global__ void __launch_bounds__(1024) k_brick_scan(const Grid g, const BinView
   }
 }
 
+// Two particles per thread (i and i + stride), so each thread has two
+// dependent gather chains (key -> offsets -> 7 moves) in flight.
 __global__ void k_scatter(const PartView src, const PartView dst, const BinView b, long long np) {
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= np) return;
-  const unsigned int key = b.key[i];
-  const unsigned int d = b.brick_start[key / BRICK_CELLS] + b.local_start[key] + b.rank[i];
-  dst.x[d] = src.x[i];
-  dst.y[d] = src.y[i];
-  dst.z[d] = src.z[i];
-  dst.u[d] = src.u[i];
-  dst.v[d] = src.v[i];
-  dst.w[d] = src.w[i];
-  dst.id[d] = src.id[i];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  unsigned int d[2];
+  bool ok[2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const long long i = i0 + u * stride;
+    ok[u] = i < np;
+    const unsigned int key = ok[u] ? b.key[i] : 0u;
+    d[u] = ok[u] ? b.brick_start[key / BRICK_CELLS] + b.local_start[key] + b.rank[i] : 0u;
+  }
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    if (!ok[u]) continue;
+    const long long i = i0 + u * stride;
+    const float x = src.x[i], y = src.y[i], z = src.z[i];
+    const float vu = src.u[i], vv = src.v[i], vw = src.w[i];
+    const int id = src.id[i];
+    dst.x[d[u]] = x;
+    dst.y[d[u]] = y;
+    dst.z[d[u]] = z;
+    dst.u[d[u]] = vu;
+    dst.v[d[u]] = vv;
+    dst.w[d[u]] = vw;
+    dst.id[d[u]] = id;
+  }
 }
 
 __global__ void k_iota(int* id, long long np) {
@@ -136,13 +189,14 @@ void launch_rebin(const Grid& g, const PartView& p, const BinView& b, long long 
 
 void launch_bin(const Grid& g, const BinView& b, uint8_t* type, DevStats* st, cudaStream_t s) {
   const unsigned int nb = (unsigned)g.bx * g.by * g.bz;
-  k_cell_local_scan<<<nb, BRICK_CELLS, 0, s>>>(g, b, type);
+  k_cell_local_scan<<<(nb + SCAN_THREADS / 32 - 1) / (SCAN_THREADS / 32), SCAN_THREADS, 0, s>>>(
+      g, b, type, nb);
   k_brick_scan<<<1, 1024, 0, s>>>(g, b, st);
 }
 
 void launch_scatter(const PartView& src, const PartView& dst, const BinView& b, long long np,
                     cudaStream_t s) {
-  if (np > 0) k_scatter<<<blocks_for(np, 256), 256, 0, s>>>(src, dst, b, np);
+  if (np > 0) k_scatter<<<blocks_for((np + 1) / 2, 256), 256, 0, s>>>(src, dst, b, np);
 }
 
 void launch_iota(int* id, long long np, cudaStream_t s) {

@@ -844,24 +844,56 @@ __device__ __forceinline__ void for_fluid0(const PcgArgs& A, F&& f) {
   }
 }
 
-// FP64 residual of one cell for the refinement: b - A x with x in FP64 (natural
-// layout).
-__device__ __forceinline__ double residual64(const PcgArgs& A, unsigned int code, int n) {
-  const Grid& g = A.g;
-  const int off[6] = {-1, 1, -g.nx, g.nx, -g.nx * g.ny, g.nx * g.ny};
-  const double xc = A.x64[n];
-  double xv[6];
+// ---------------------------------------------------------------- float pairs
+
+// Error-free transforms (Knuth's TwoSum, Dekker's FastTwoSum, the FMA product):
+// a value is carried as hi + lo, ~48 significant bits, all on the FP32 pipes
+// (GB300's FP64 pipe is narrow, and the refinement touches every fluid cell).
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bv = __fsub_rn(s, a);
+  return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bv)), __fsub_rn(b, bv)));
+}
+
+__device__ __forceinline__ float2 fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+
+__device__ __forceinline__ float2 pair_add(float2 x, float2 y) {
+  const float2 t = two_sum(x.x, y.x);
+  return fast_two_sum(t.x, __fadd_rn(t.y, __fadd_rn(x.y, y.y)));
+}
+
+__device__ __forceinline__ float2 pair_neg(float2 x) { return make_float2(-x.x, -x.y); }
+
+// (hi, lo) * f for a float f, with the exact product of the hi parts.
+__device__ __forceinline__ float2 pair_mul(float2 x, float f) {
+  const float p = __fmul_rn(x.x, f);
+  const float e = __fmaf_rn(x.x, f, -p);
+  return fast_two_sum(p, __fmaf_rn(x.y, f, e));
+}
+
+// Residual b - A x of one level-0 cell with x and b as float pairs (split
+// layout), A x in difference form s ((cnt - nfl) x_c + sum_fluid (x_c - x_n)).
+__device__ __forceinline__ float2 residual_pair(const SV& v, const float2* x2, const float2* b2,
+                                                const SCell& e, unsigned int code, float s) {
+  int nb[6];
+  snbr(v, e, nb);
+  const float2 xc = x2[e.idx];
+  float2 xn[6];
 #pragma unroll
-  for (int q = 0; q < 6; ++q) xv[q] = A.x64[((code >> q) & 1u) ? n + off[q] : n];
-  double d = 0.0;
+  for (int q = 0; q < 6; ++q) xn[q] = x2[nb[q]];
+  float2 acc = make_float2(0.0f, 0.0f);
   int nfl = 0;
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
-    const bool f = (code >> q) & 1u;
-    d += f ? xc - xv[q] : 0.0;
-    nfl += f;
+    if (!((code >> q) & 1u)) continue;
+    acc = pair_add(acc, pair_add(xc, pair_neg(xn[q])));
+    ++nfl;
   }
-  return A.b64[n] - A.s64 * ((double)(code_cnt(code) - nfl) * xc + d);
+  acc = pair_add(acc, pair_mul(xc, (float)(code_cnt(code) - nfl)));
+  return pair_add(b2[e.idx], pair_neg(pair_mul(acc, s)));
 }
 
 // ---------------------------------------------------------------- set-up
@@ -1020,11 +1052,20 @@ __device__ void solve_mg(const PcgArgs& A, Shared& sh, CtaMg& sm, SolveState& S)
   float* r = L0.b;
   if (!build_levels(A, sh)) { S.ok = false; return; }
   if (M.nlev > 1 && team_rank() == 0) cta_levels_init(M, sm);
-  // ---- start: r = b, d = 0, p_old = 0, first red half-sweep of the V-cycle
+  // ---- start: r = b, d = 0, p_old = 0, first red half-sweep of the V-cycle;
+  // mixed mode: b and x = 0 as float pairs
   {
     FF bb;
     for_fluid0(A, [&](const SCell& e, unsigned int code, int n) {
-      const float bc = MIXED ? (float)A.b64[n] : A.b32[n];
+      float bc;
+      if constexpr (MIXED) {
+        const double b64 = A.b64[n];
+        bc = __double2float_rn(b64);
+        M.b2[e.idx] = make_float2(bc, __double2float_rn(b64 - (double)bc));
+        M.x2[e.idx] = make_float2(0.0f, 0.0f);
+      } else {
+        bc = A.b32[n];
+      }
       r[e.idx] = bc;
       d[e.idx] = 0.0f;
       M.pa0[e.idx] = 0.0f;
@@ -1112,15 +1153,20 @@ __device__ void solve_mg(const PcgArgs& A, Shared& sh, CtaMg& sm, SolveState& S)
     float* t = pold; pold = pnew; pnew = t;
     if constexpr (MIXED) {
       if (sh.flag == 2) {
-        // ---- refinement: x64 += d, d = 0; r = b - A x64 in FP64 (+ first red half-sweep)
-        for_fluid0(A, [&](const SCell& e, unsigned int, int n) {
-          A.x64[n] += (double)d[e.idx];
+        // ---- refinement: x += d, d = 0; r = b - A x in float pairs (+ first red
+        // half-sweep)
+        for_fluid0(A, [&](const SCell& e, unsigned int, int) {
+          const float2 t = two_sum(M.x2[e.idx].x, d[e.idx]);
+          M.x2[e.idx] = fast_two_sum(t.x, __fadd_rn(t.y, M.x2[e.idx].y));
           d[e.idx] = 0.0f;
         });
         if (!gsync(A)) { S.ok = false; return; }
         FF rr64;
-        for_fluid0(A, [&](const SCell& e, unsigned int code, int n) {
-          const float r32 = (float)residual64(A, code, n);
+        const SV v0 = sview(L0);
+        const float s_a = A.s;
+        for_fluid0(A, [&](const SCell& e, unsigned int code, int) {
+          const float2 rp = residual_pair(v0, M.x2, M.b2, e, code, s_a);
+          const float r32 = __fadd_rn(rp.x, rp.y);
           r[e.idx] = r32;
           if (e.idx < L0.half) z[e.idx] = gs_first(0, code_cnt(code), r32);
           rr64.add_prod(r32, r32);
@@ -1146,18 +1192,18 @@ __device__ void solve_mg(const PcgArgs& A, Shared& sh, CtaMg& sm, SolveState& S)
     }
     if (sh.flag == 1) { conv = true; break; }
   }
-  // ---- the solution in natural layout: the FP32 pressure, or x64 and its pair
+  // ---- the solution in natural layout: the FP32 pressure, or the float pair
+  // (for G2P) and its FP64 value
   if constexpr (MIXED) {
     for_fluid0(A, [&](const SCell& e, unsigned int, int n) {
-      double xv = A.x64[n];
+      float2 xp = M.x2[e.idx];
       if (!conv) {
-        xv += (double)d[e.idx];
-        A.x64[n] = xv;
+        const float2 t = two_sum(xp.x, d[e.idx]);
+        xp = fast_two_sum(t.x, __fadd_rn(t.y, xp.y));
         d[e.idx] = 0.0f;
       }
-      const float hi = __double2float_rn(xv);
-      const float lo = __double2float_rn(xv - (double)hi);
-      A.pff[n] = make_float2(hi, lo);
+      A.pff[n] = xp;
+      A.x64[n] = (double)xp.x + (double)xp.y;
     });
   } else {
     for_fluid0(A, [&](const SCell& e, unsigned int, int n) { A.x32[n] = d[e.idx]; });

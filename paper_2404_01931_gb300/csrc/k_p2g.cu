@@ -192,8 +192,13 @@ __global__ void k_divergence(const Grid g, const StepConsts K, const uint8_t* __
       b32[c] = fluid ? -__fmul_rn(d, g.inv_dx) : 0.0f;
     }
     if (b64) {
-      const double d = ((double)uR - (double)uL) + ((double)vT - (double)vB) + ((double)wF - (double)wK);
-      b64[c] = fluid ? -d * (double)g.inv_dx : 0.0;
+      // the FP64 pipe is narrow: warps without a fluid cell skip the FP64 work
+      double v = 0.0;
+      if (__ballot_sync(__activemask(), fluid)) {
+        const double d = ((double)uR - (double)uL) + ((double)vT - (double)vB) + ((double)wF - (double)wK);
+        v = fluid ? -d * (double)g.inv_dx : 0.0;
+      }
+      b64[c] = v;
     }
   }
 }
