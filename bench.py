@@ -41,27 +41,24 @@ WORKLOADS = {
                   precision="fp32", cg_tol=1e-6, ir_tol=1e-8),
 }
 
-# Algorithmic bytes of the PCG kernel per fluid cell (FP32 vectors, each value read
-# or written once per phase; stencil neighbours come from cache):
-#   phase A: read r, p_old (4+4), type (1); write p_new, q (4+4)      = 17 B
-#   phase B: read x, p_new, r, q (16); write x, r (8)                 = 24 B
-#   mixed-mode refinement, per outer step: phase R read x64, b64 (16), type (1),
-#   write r, d, p_old (12) = 29 B; phase U read x64, d (12), write x64 (8) = 20 B;
-#   once per solve: ||b|| read b64 (8), final float-pair write (read x64 8, write 8).
-PCG_BYTES_PER_ITER = 41
-IR_BYTES_PER_OUTER = 49
-IR_BYTES_PER_SOLVE = 29 + 8 + 16
-# With the multigrid preconditioner, per fluid cell of level 0 and iteration:
-#   phase A 17 B; phase B 24 B + the fused red half-sweep's z writes (2 B);
-#   V-cycle at level 0 with nu = 2: six half-sweeps reading r and writing z for
-#   half the cells (4 B each), the restriction reading r, z, type (9 B), the last
-#   red half-sweep reading r, z and writing half of z (10 B); coarser levels add
-#   about a seventh of level 0's cycle (6 B)                      => 92 B
-#   refinement: x64 += d (24 B), r = b - A x64 in FP64 (23 B)     => 47 B
-#   per solve: ||b|| (8 B), float-pair pressure (16 B)            => 24 B
+# With the multigrid preconditioner, per fluid cell of level 0 and iteration
+# (colour-split FP32 vectors, 16-bit neighbour codes):
+#   phase A: read z, p_old, code (10 B); write p_new, q (8 B)        = 18 B
+#   phase B: read d, p_new, q, r, code (18 B); write d, r, half of z = 26 B
+#   V-cycle at level 0 with nu = 2: seven half-sweeps, each reading r, code and
+#   the other colour's z and writing its colour's z for half the cells (~5 B),
+#   the restriction reading r, z, code of the red cells (~5 B); coarser levels
+#   add about a seventh of level 0's cycle                         ~ 92 B in all
+#   refinement (float pairs): x += d (read x, d, write x, d: 24 B),
+#   r = b - A x (read x, b, code, write r, half of z: 23 B)       => 47 B
+#   per solve: b as a float pair from b64 (16 B), the solution out (x64, pff: 24 B)
 MG_PCG_BYTES_PER_ITER = 92
 MG_IR_BYTES_PER_OUTER = 47
-MG_IR_BYTES_PER_SOLVE = 24
+MG_IR_BYTES_PER_SOLVE = 40
+# DRAM traffic of one k_pcg_mg launch on the 256^3 pool (dram__bytes_read.sum +
+# dram__bytes_write.sum of the first timed step's solve, a single-pass capture);
+# see profiles/k_pcg_mg_pool256_dram.md.  Reported for that workload only.
+PCG_DRAM_BYTES_POOL256 = 6.181e9
 
 
 def make_scene(w):
@@ -440,10 +437,11 @@ def main():
             "metric": "FLIP particle-steps/s", "value": value, "unit": "particle-steps/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64" if mixed else "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w["desc"], "grid": [w["n"]] * 3, "particles": np_,
-                       "precision": "mixed IR (FP32 PCG, FP64 outer residual)" if mixed
-                       else "FP32 (FP64-accurate dots)",
+                       "precision": "mixed: FP32 PCG with float-pair (~48-bit) solution and "
+                       "residual replacement, FP64 right-hand side and result" if mixed
+                       else "FP32 (float-pair dot products)",
                        "ir_tol": w["ir_tol"], "cg_tol": w["cg_tol"], "dt": 1 / 240,
                        "flip_ratio": 0.95, "seed": 0,
                        "parallelism": f"{ws} independent replica(s), one per GPU",
@@ -459,7 +457,8 @@ def main():
                          "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                          "algorithmic_bytes_per_launch": pcg_bytes / args.steps,
-                         "traffic": None},
+                         "traffic": PCG_DRAM_BYTES_POOL256 if args.workload == "pool256"
+                         else None},
             "gpu_launches": st.kernel_launches,
             "clocks": ck,
             "e2e": e2e,
