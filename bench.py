@@ -256,7 +256,7 @@ def run_batch(args):
            "config": {"workload": f"batch of {len(scenes)} dam-break scenes, edges {edges}, "
                                   "fluid fraction 0.2-0.5 by seed", "particles": npart,
                       "cells": sum(int(np.prod(sc.n)) for sc in scenes),
-                      "precision": "FP32 (FP64-accurate dots)", "preconditioner": "multigrid"},
+                      "precision": "FP32 (float-pair dot products)", "preconditioner": "multigrid"},
            "cg_iterations_per_scene_step": sum(s.cg_iterations for s in st) / len(st) / args.steps,
            "ms_pcg_per_step": st[0].ms_pcg / args.steps,
            "max_rel_residual": max(s.cg_rel_residual for s in st), "status": rc,
@@ -311,7 +311,7 @@ def run_serve(args):
     out = {"metric": "FLIP particle-steps/s", "value": served / span, "unit": "particle-steps/s",
            "n_gpus": 1, "steps": args.requests, "warmup": 0,
            "ms_per_step": span * 1e3 / args.requests, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": f"serving: {args.serve} resident dam-break scenes, edges "
                                   f"log-uniform in [{lo}, {hi}], Poisson arrivals at "
                                   f"{args.rate}/s, uniform scene choice, mixed precision",

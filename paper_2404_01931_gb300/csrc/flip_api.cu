@@ -94,7 +94,6 @@ struct flip_handle {
   void* tmp = nullptr;
   size_t tmp_bytes = 0;
   int pcg_blocks = 0, sm_count = 0, p2g_blocks = 0, g2p_blocks = 0;
-  long long reported_cg = 0, reported_ir = 0;
   int launches = 0;
   bool stepped = false;
 };
@@ -556,6 +555,8 @@ int flip_step(flip_handle* h, int32_t nsteps, flip_stats* stats) {
     FLIP_CUDA(cudaEventCreate(&t_begin));
     FLIP_CUDA(cudaEventCreate(&t_end));
     FLIP_CUDA(cudaEventRecord(t_begin, s));
+    FLIP_CUDA(cudaMemcpyAsync(&h->dstats->cg_iters_mark, &h->dstats->cg_iters_total,
+                              2 * sizeof(long long), cudaMemcpyDeviceToDevice, s));
   }
   const float* uo[3] = {h->uo[0], h->uo[1], h->uo[2]};
   PcgArgs pa = pcg_args(h);
@@ -613,10 +614,8 @@ int flip_step(flip_handle* h, int32_t nsteps, flip_stats* stats) {
     stats->n_particles = h->np;
     stats->n_fluid_cells = d.n_fluid;
     stats->n_active_bricks = d.n_active;
-    stats->cg_iterations = d.cg_iters_total - h->reported_cg;
-    stats->ir_iterations = (int32_t)(d.ir_iters_total - h->reported_ir);
-    h->reported_cg = d.cg_iters_total;
-    h->reported_ir = d.ir_iters_total;
+    stats->cg_iterations = d.cg_iters_total - d.cg_iters_mark;
+    stats->ir_iterations = (int32_t)(d.ir_iters_total - d.ir_iters_mark);
     stats->kernel_launches = h->launches - launches0;
     stats->cg_rel_residual = d.rel_res;
     stats->rel_divergence = norms[0] > 0.0 ? std::sqrt(norms[1] / norms[0]) : 0.0;
@@ -993,7 +992,12 @@ int flip_batch_step(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t ns
   std::vector<int> launches0(n);
   for (int s = 0; s < n; ++s) launches0[s] = hs[s]->launches;
   int batch_launches = 0;
-  if (timed) FLIP_CUDA(cudaEventRecord(b->ev_begin, bs));
+  if (timed) {
+    FLIP_CUDA(cudaEventRecord(b->ev_begin, bs));
+    for (int s = 0; s < n; ++s)
+      FLIP_CUDA(cudaMemcpyAsync(&hs[s]->dstats->cg_iters_mark, &hs[s]->dstats->cg_iters_total,
+                                2 * sizeof(long long), cudaMemcpyDeviceToDevice, bs));
+  }
   // every scene stream starts after the call's uploads (and the begin event)
   FLIP_CUDA(cudaEventRecord(b->ev_solved, bs));
   for (int s = 0; s < n; ++s) FLIP_CUDA(cudaStreamWaitEvent(hs[s]->stream, b->ev_solved, 0));
@@ -1073,10 +1077,8 @@ int flip_batch_step(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t ns
     o->n_particles = h->np;
     o->n_fluid_cells = d.n_fluid;
     o->n_active_bricks = d.n_active;
-    o->cg_iterations = d.cg_iters_total - h->reported_cg;
-    o->ir_iterations = (int32_t)(d.ir_iters_total - h->reported_ir);
-    h->reported_cg = d.cg_iters_total;
-    h->reported_ir = d.ir_iters_total;
+    o->cg_iterations = d.cg_iters_total - d.cg_iters_mark;
+    o->ir_iterations = (int32_t)(d.ir_iters_total - d.ir_iters_mark);
     o->kernel_launches = h->launches - launches0[s] + (s == 0 ? batch_launches : 0);
     o->cg_rel_residual = d.rel_res;
     o->rel_divergence = norms[0] > 0.0 ? std::sqrt(norms[1] / norms[0]) : 0.0;

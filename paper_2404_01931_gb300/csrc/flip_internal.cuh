@@ -32,8 +32,10 @@ struct DevStats {
   unsigned int n_fluid;       // fluid cells, last binning
   unsigned int n_active;      // active bricks, last binning
   unsigned int max_speed_bits;  // float bits of the last step's max speed
-  long long cg_iters_total;   // running sums (host takes differences)
+  long long cg_iters_total;   // running sums
   long long ir_iters_total;
+  long long cg_iters_mark;    // the running sums at the start of the last call
+  long long ir_iters_mark;    // that asked for statistics (copied on the stream)
   double rel_res;             // last solve's stopping residual ||r||/||b||
   double bnorm;               // last solve's ||b||
 };
