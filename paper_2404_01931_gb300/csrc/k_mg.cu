@@ -341,77 +341,6 @@ __device__ __noinline__ void sweep_split(const MgArgs& M, const MgLevel& L, cons
   }
 }
 
-// The fields of a natural-layout (CTA-local) level, in registers.
-struct NV {
-  float* x;
-  float* b;
-  const uint8_t* code;
-  int nx, ny, nz;
-  float s;
-};
-
-__device__ __forceinline__ NV nview(const MgLevel& L) {
-  return NV{L.x, L.b, L.code, L.nx, L.ny, L.nz, L.s};
-}
-
-__device__ __forceinline__ int ncount(const NV& L, int i, int j, int k) {
-  return (i > 0) + (i < L.nx - 1) + (j > 0) + (j < L.ny - 1) + (k > 0) + (k < L.nz - 1);
-}
-
-__device__ __forceinline__ void nnbr(const NV& L, int i, int j, int k, int c, int (&idx)[6]) {
-  const int sy = L.nx, sz = L.nx * L.ny;
-  idx[0] = i > 0 ? c - 1 : c;
-  idx[1] = i < L.nx - 1 ? c + 1 : c;
-  idx[2] = j > 0 ? c - sy : c;
-  idx[3] = j < L.ny - 1 ? c + sy : c;
-  idx[4] = k > 0 ? c - sz : c;
-  idx[5] = k < L.nz - 1 ? c + sz : c;
-}
-
-// Half-sweep of one colour over natural-layout (CTA-local) level l: each x-row
-// has ceil(nx/2) slots, slot q of row (j, k) is x = 2q + parity.
-template <int MODE>
-__device__ __noinline__ void sweep_nat(const MgArgs& M, const MgLevel& L, const MgLevel& C, int l,
-                                       int colour) {
-  constexpr int U = (MODE == CORRECT) ? 2 : 4;
-  const NV v = nview(L);
-  const PV cv = pview(C);
-  const float omega = M.omega;
-  const int hx = (v.nx + 1) >> 1;
-  const Part p = level_part(hx * v.ny * v.nz, true);
-  run_batched<U>(
-      (unsigned)p.begin, (unsigned)p.end, (unsigned)p.stride,
-      [&](unsigned int e, bool ok) {
-        const int row = (int)e / hx, q = (int)e - row * hx;
-        const int j = row % v.ny, k = row / v.ny;
-        int i = 2 * q + ((colour + j + k) & 1);
-        GsIn s;
-        s.ok = ok && i < v.nx;
-        i = min(i, v.nx - 1);
-        s.i = i;
-        s.j = j;
-        s.k = k;
-        s.idx = i + v.nx * row;
-        s.code = v.code[s.idx] | ((unsigned)ncount(v, i, j, k) << 8);
-        return s;
-      },
-      [&](GsIn& s) {
-        if (!(s.code & CODE_SELF)) return;
-        s.b = v.b[s.idx];
-        if constexpr (MODE != FIRST) {
-          int nb[6];
-          nnbr(v, s.i, s.j, s.k, s.idx, nb);
-#pragma unroll
-          for (int q = 0; q < 6; ++q) s.xv[q] = v.x[nb[q]];
-        }
-        if constexpr (MODE == CORRECT) parent_values(cv, v.nx, v.ny, v.nz, s.i, s.j, s.k, s.pv);
-      },
-      [&](GsIn& s) {
-        float xv;
-        gs_apply<MODE>(v.x, l, omega, s, xv);
-      });
-}
-
 // ---------------------------------------------------------------- restriction
 
 // Residual of the red child (dy, dz) of coarse cell (I, J, K) on the
@@ -488,39 +417,15 @@ __device__ __noinline__ void restrict_split(const MgLevel& Fl, const MgLevel& Cl
 // memory), over all of C's cells.
 __device__ __noinline__ void restrict_split_nat(const MgLevel& Fl, const MgLevel& Cl) {
   const SV F = sview(Fl);
-  const NV C = nview(Cl);
   const int fnz = Fl.nz;
-  const Part p = level_part(C.nx * C.ny * C.nz, false);
+  const int nx = Cl.nx, ny = Cl.ny;
+  float* cb = Cl.b;
+  const uint8_t* code = Cl.code;
+  const Part p = level_part(Cl.ncells, false);
   for (int c = p.begin; c < p.end; c += p.stride) {
-    if (!(C.code[c] & CODE_SELF)) continue;
-    const int i = c % C.nx, j = (c / C.nx) % C.ny, k = c / (C.nx * C.ny);
-    C.b[c] = restrict_sum(F, fnz, i, j, k);
-  }
-}
-
-// Natural F -> natural C (CTA-local levels in shared memory).
-__device__ __noinline__ void restrict_nat(const MgLevel& Fl, const MgLevel& Cl) {
-  const NV F = nview(Fl), C = nview(Cl);
-  const Part p = level_part(C.nx * C.ny * C.nz, true);
-  for (int c = p.begin; c < p.end; c += p.stride) {
-    if (!(C.code[c] & CODE_SELF)) continue;
-    const int I = c % C.nx, J = (c / C.nx) % C.ny, K = c / (C.nx * C.ny);
-    float sum = 0.0f;
-    for (int q = 0; q < 4; ++q) {
-      const int dy = q & 1, dz = q >> 1, dx = (dy + dz) & 1;
-      const int i = 2 * I + dx, j = 2 * J + dy, k = 2 * K + dz;
-      if (i >= F.nx || j >= F.ny || k >= F.nz) continue;
-      const int fc = i + F.nx * (j + F.ny * k);
-      const unsigned int code = F.code[fc];
-      if (!(code & CODE_SELF)) continue;
-      int nb[6];
-      nnbr(F, i, j, k, fc, nb);
-      float xv[6];
-#pragma unroll
-      for (int u = 0; u < 6; ++u) xv[u] = F.x[nb[u]];
-      sum = __fadd_rn(sum, resid(F.s, ncount(F, i, j, k), code, F.b[fc], F.x[fc], xv));
-    }
-    C.b[c] = __fmul_rn(sum, 0.0625f);
+    if (!(code[c] & CODE_SELF)) continue;
+    const int i = c % nx, j = (c / nx) % ny, k = c / (nx * ny);
+    cb[c] = restrict_sum(F, fnz, i, j, k);
   }
 }
 
@@ -568,83 +473,218 @@ __device__ __forceinline__ bool up_split(const PcgArgs& A, int l) {
   return true;
 }
 
-// The same for a CTA-local level (descriptions in shared memory).
-__device__ __forceinline__ void down_nat(const MgArgs& M, const MgLevel* lv, int l) {
-  sweep_nat<FIRST>(M, lv[l], lv[l + 1], l, 0);
-  __syncthreads();
-  sweep_nat<NORMAL>(M, lv[l], lv[l + 1], l, 1);
-  __syncthreads();
-  for (int s = 1; s < M.nu; ++s) {
-    sweep_nat<NORMAL>(M, lv[l], lv[l + 1], l, 0);
-    __syncthreads();
-    sweep_nat<NORMAL>(M, lv[l], lv[l + 1], l, 1);
-    __syncthreads();
-  }
-  restrict_nat(lv[l], lv[l + 1]);
-  __syncthreads();
-}
+// ---------------------------------------------------------------- CTA-local levels
 
-__device__ __forceinline__ void up_nat(const MgArgs& M, const MgLevel* lv, int l) {
-  sweep_nat<CORRECT>(M, lv[l], lv[l + 1], l, 1);
-  __syncthreads();
-  sweep_nat<NORMAL>(M, lv[l], lv[l + 1], l, 0);
-  __syncthreads();
-  for (int s = 1; s < M.nu; ++s) {
-    sweep_nat<NORMAL>(M, lv[l], lv[l + 1], l, 1);
-    __syncthreads();
-    sweep_nat<NORMAL>(M, lv[l], lv[l + 1], l, 0);
-    __syncthreads();
-  }
-}
-
-// The coarsest level (CTA-local): MG_COARSE_SWEEPS (red, black) pairs from
-// zero, then as many (black, red) pairs.
-__device__ __forceinline__ void coarsest_nat(const MgArgs& M, const MgLevel* lv, int l) {
-  sweep_nat<FIRST>(M, lv[l], lv[l], l, 0);
-  __syncthreads();
-  sweep_nat<NORMAL>(M, lv[l], lv[l], l, 1);
-  __syncthreads();
-  for (int s = 1; s < MG_COARSE_SWEEPS; ++s) {
-    sweep_nat<NORMAL>(M, lv[l], lv[l], l, 0);
-    __syncthreads();
-    sweep_nat<NORMAL>(M, lv[l], lv[l], l, 1);
-    __syncthreads();
-  }
-  for (int s = 0; s < MG_COARSE_SWEEPS; ++s) {
-    sweep_nat<NORMAL>(M, lv[l], lv[l], l, 1);
-    __syncthreads();
-    sweep_nat<NORMAL>(M, lv[l], lv[l], l, 0);
-    __syncthreads();
-  }
-}
-
-// The CTA-local levels [lgrid, nlev) live in shared memory of CTA 0: x, b and
-// the codes of every such level (MG_CTA_CELLS cells in total at most).
+// The CTA-local levels [lgrid, nlev) live in CTA 0's (dynamic) shared memory:
+// x, b and the neighbour codes of every such level (MG_CTA_CELLS cells in all),
+// and per level and colour the list of its fluid cells, each as the packed
+// coordinates i | j << bx | k << (bx + by) with bx, by the bits of nx - 1 and
+// ny - 1 (at most 16 bits, since a CTA-local level has fewer than 2^13 cells).
+// A half-sweep then visits exactly the fluid cells of its colour, with no
+// divisions and no idle slots.
 struct CtaMg {
   float x[MG_CTA_CELLS];
   float b[MG_CTA_CELLS];
   uint8_t code[MG_CTA_CELLS];
-  MgLevel lv[MG_MAX_LEVELS];  // level descriptions pointing into the arrays above
+  uint16_t list[MG_CTA_CELLS];
+  int off[MG_MAX_LEVELS][3];   // list of level l: colour 0 [off0, off1), colour 1 [off1, off2)
+  int base[MG_MAX_LEVELS];     // first cell of level l in x, b, code
+  int nx[MG_MAX_LEVELS], ny[MG_MAX_LEVELS], nz[MG_MAX_LEVELS];
+  int bx[MG_MAX_LEVELS], by[MG_MAX_LEVELS];
+  float s[MG_MAX_LEVELS];
 };
 
-// Points the shared level descriptions at the shared arrays and loads the codes
-// (once per solve, after build_levels).  CTA 0 only.
+__device__ __forceinline__ int bits_for(int n) {  // bits of n - 1 (0 for n = 1)
+  return n > 1 ? 32 - __clz(n - 1) : 0;
+}
+
+struct CtaCell {
+  int i, j, k, c;
+};
+
+__device__ __forceinline__ CtaCell cta_cell(const CtaMg& sm, int l, unsigned int e) {
+  const int bx = sm.bx[l], by = sm.by[l];
+  CtaCell r;
+  r.i = (int)(e & ((1u << bx) - 1u));
+  r.j = (int)((e >> bx) & ((1u << by) - 1u));
+  r.k = (int)(e >> (bx + by));
+  r.c = r.i + sm.nx[l] * (r.j + sm.ny[l] * r.k);
+  return r;
+}
+
+// Half-sweep of one colour over CTA-local level l (parents on level l + 1).
+template <int MODE>
+__device__ __noinline__ void sweep_cta(const MgArgs& M, CtaMg& sm, int l, int colour) {
+  const int nx = sm.nx[l], ny = sm.ny[l], nz = sm.nz[l], sy = nx, sz = nx * ny;
+  float* x = sm.x + sm.base[l];
+  const float* b = sm.b + sm.base[l];
+  const uint8_t* code = sm.code + sm.base[l];
+  const int e1 = sm.off[l][colour + 1];
+  const float omega = M.omega;
+  for (int e = sm.off[l][colour] + (int)threadIdx.x; e < e1; e += PCG_THREADS) {
+    const CtaCell p = cta_cell(sm, l, sm.list[e]);
+    const int cnt = (p.i > 0) + (p.i < nx - 1) + (p.j > 0) + (p.j < ny - 1) + (p.k > 0) +
+                    (p.k < nz - 1);
+    if constexpr (MODE == FIRST) {
+      x[p.c] = gs_first(l, cnt, b[p.c]);
+    } else {
+      const unsigned int cd = code[p.c];
+      const int off[6] = {-1, 1, -sy, sy, -sz, sz};
+      float xv[6];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) xv[q] = ((cd >> q) & 1u) ? x[p.c + off[q]] : 0.0f;
+      if constexpr (MODE == CORRECT) {
+        const float* px = sm.x + sm.base[l + 1];
+        const int pnx = sm.nx[l + 1], pny = sm.ny[l + 1];
+        const int di[6] = {-1, 1, 0, 0, 0, 0}, dj[6] = {0, 0, -1, 1, 0, 0}, dk[6] = {0, 0, 0, 0, -1, 1};
+#pragma unroll
+        for (int q = 0; q < 6; ++q)
+          if ((cd >> q) & 1u) {
+            const int pi = (p.i + di[q]) >> 1, pj = (p.j + dj[q]) >> 1, pk = (p.k + dk[q]) >> 1;
+            xv[q] = __fmaf_rn(omega, px[pi + pnx * (pj + pny * pk)], xv[q]);
+          }
+      }
+      x[p.c] = gs_sum(l, cnt, cd, b[p.c], xv);
+    }
+  }
+}
+
+// b_{l+1} = (1/16) sum of the red fluid children's residuals, over level l+1's
+// fluid cells (both colours).
+__device__ __noinline__ void restrict_cta(CtaMg& sm, int l) {
+  const int nx = sm.nx[l], ny = sm.ny[l], nz = sm.nz[l], sy = nx, sz = nx * ny;
+  const float* x = sm.x + sm.base[l];
+  const float* b = sm.b + sm.base[l];
+  const uint8_t* code = sm.code + sm.base[l];
+  float* cb = sm.b + sm.base[l + 1];
+  const float sl = sm.s[l];
+  const int e1 = sm.off[l + 1][2];
+  for (int e = sm.off[l + 1][0] + (int)threadIdx.x; e < e1; e += PCG_THREADS) {
+    const CtaCell P = cta_cell(sm, l + 1, sm.list[e]);
+    float sum = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int dy = q & 1, dz = q >> 1, dx = (dy + dz) & 1;
+      const int i = 2 * P.i + dx, j = 2 * P.j + dy, k = 2 * P.k + dz;
+      if (i >= nx || j >= ny || k >= nz) continue;
+      const int fc = i + nx * (j + ny * k);
+      const unsigned int cd = code[fc];
+      if (!(cd & CODE_SELF)) continue;
+      const int off[6] = {-1, 1, -sy, sy, -sz, sz};
+      float xv[6];
+#pragma unroll
+      for (int u = 0; u < 6; ++u) xv[u] = ((cd >> u) & 1u) ? x[fc + off[u]] : 0.0f;
+      const int cnt = (i > 0) + (i < nx - 1) + (j > 0) + (j < ny - 1) + (k > 0) + (k < nz - 1);
+      sum = __fadd_rn(sum, resid(sl, cnt, cd, b[fc], x[fc], xv));
+    }
+    cb[P.c] = __fmul_rn(sum, 0.0625f);
+  }
+}
+
+// Points the shared level descriptions at the shared arrays, loads the codes and
+// builds the fluid-cell lists (once per solve, after build_levels).  CTA 0 only.
 __device__ __noinline__ void cta_levels_init(const MgArgs& M, CtaMg& sm) {
+  __shared__ unsigned int s_wc[PCG_WARPS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
     int off = 0;
     for (int l = M.lgrid; l < M.nlev; ++l) {
-      sm.lv[l] = M.lv[l];
-      sm.lv[l].x = sm.x + off;
-      sm.lv[l].b = sm.b + off;
-      sm.lv[l].code = sm.code + off;
-      sm.lv[l].t = nullptr;
+      sm.base[l] = off;
+      sm.nx[l] = M.lv[l].nx;
+      sm.ny[l] = M.lv[l].ny;
+      sm.nz[l] = M.lv[l].nz;
+      sm.bx[l] = bits_for(M.lv[l].nx);
+      sm.by[l] = bits_for(M.lv[l].ny);
+      sm.s[l] = M.lv[l].s;
       off += M.lv[l].ncells;
     }
   }
   __syncthreads();
-  for (int l = M.lgrid; l < M.nlev; ++l)
-    for (int c = threadIdx.x; c < M.lv[l].ncells; c += PCG_THREADS) sm.lv[l].code[c] = M.lv[l].code[c];
+  int pos = 0;  // next free list entry (same value in every thread)
+  for (int l = M.lgrid; l < M.nlev; ++l) {
+    const int n = M.lv[l].ncells, nx = sm.nx[l], ny = sm.ny[l];
+    for (int c = threadIdx.x; c < n; c += PCG_THREADS) sm.code[sm.base[l] + c] = M.lv[l].code[c];
+    __syncthreads();
+    for (int colour = 0; colour < 2; ++colour) {
+      if (threadIdx.x == 0) sm.off[l][colour] = pos;
+      for (int c0 = 0; c0 < n; c0 += PCG_THREADS) {
+        const int c = c0 + (int)threadIdx.x;
+        int i = 0, j = 0, k = 0;
+        bool f = false;
+        if (c < n) {
+          i = c % nx;
+          j = (c / nx) % ny;
+          k = c / (nx * ny);
+          f = (sm.code[sm.base[l] + c] & CODE_SELF) && ((i + j + k) & 1) == colour;
+        }
+        const unsigned int bal = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) s_wc[warp] = __popc(bal);
+        __syncthreads();
+        int before = 0, tot = 0;
+        for (int w = 0; w < PCG_WARPS; ++w) {
+          before += (w < warp) ? (int)s_wc[w] : 0;
+          tot += (int)s_wc[w];
+        }
+        if (f)
+          sm.list[pos + before + __popc(bal & ((1u << lane) - 1u))] =
+              (uint16_t)(i | (j << sm.bx[l]) | (k << (sm.bx[l] + sm.by[l])));
+        pos += tot;
+        __syncthreads();
+      }
+    }
+    if (threadIdx.x == 0) sm.off[l][2] = pos;
+  }
   __syncthreads();
+}
+
+// The same cycle pieces as for the grid-wide levels, inside CTA 0.
+__device__ __forceinline__ void down_cta(const MgArgs& M, CtaMg& sm, int l) {
+  sweep_cta<FIRST>(M, sm, l, 0);
+  __syncthreads();
+  sweep_cta<NORMAL>(M, sm, l, 1);
+  __syncthreads();
+  for (int s = 1; s < M.nu; ++s) {
+    sweep_cta<NORMAL>(M, sm, l, 0);
+    __syncthreads();
+    sweep_cta<NORMAL>(M, sm, l, 1);
+    __syncthreads();
+  }
+  restrict_cta(sm, l);
+  __syncthreads();
+}
+
+__device__ __forceinline__ void up_cta(const MgArgs& M, CtaMg& sm, int l) {
+  sweep_cta<CORRECT>(M, sm, l, 1);
+  __syncthreads();
+  sweep_cta<NORMAL>(M, sm, l, 0);
+  __syncthreads();
+  for (int s = 1; s < M.nu; ++s) {
+    sweep_cta<NORMAL>(M, sm, l, 1);
+    __syncthreads();
+    sweep_cta<NORMAL>(M, sm, l, 0);
+    __syncthreads();
+  }
+}
+
+// The coarsest level: MG_COARSE_SWEEPS (red, black) pairs from zero, then as many
+// (black, red) pairs.
+__device__ __forceinline__ void coarsest_cta(const MgArgs& M, CtaMg& sm, int l) {
+  sweep_cta<FIRST>(M, sm, l, 0);
+  __syncthreads();
+  sweep_cta<NORMAL>(M, sm, l, 1);
+  __syncthreads();
+  for (int s = 1; s < MG_COARSE_SWEEPS; ++s) {
+    sweep_cta<NORMAL>(M, sm, l, 0);
+    __syncthreads();
+    sweep_cta<NORMAL>(M, sm, l, 1);
+    __syncthreads();
+  }
+  for (int s = 0; s < MG_COARSE_SWEEPS; ++s) {
+    sweep_cta<NORMAL>(M, sm, l, 1);
+    __syncthreads();
+    sweep_cta<NORMAL>(M, sm, l, 0);
+    __syncthreads();
+  }
 }
 
 // Levels [lgrid, nlev) inside CTA 0, from the right-hand side that the grid-wide
@@ -653,12 +693,15 @@ __device__ __noinline__ void cta_levels_init(const MgArgs& M, CtaMg& sm) {
 __device__ __noinline__ void cta_cycle(const PcgArgs& A, CtaMg& sm) {
   const MgArgs& M = A.mg;
   const int lg = M.lgrid;
-  for (int c = threadIdx.x; c < M.lv[lg].ncells; c += PCG_THREADS) sm.lv[lg].b[c] = M.lv[lg].b[c];
+  const int n = M.lv[lg].ncells;
+  const float* gb = M.lv[lg].b;
+  float* gx = M.lv[lg].x;
+  for (int c = threadIdx.x; c < n; c += PCG_THREADS) sm.b[sm.base[lg] + c] = gb[c];
   __syncthreads();
-  for (int l = lg; l < M.nlev - 1; ++l) down_nat(M, sm.lv, l);
-  coarsest_nat(M, sm.lv, M.nlev - 1);
-  for (int l = M.nlev - 2; l >= lg; --l) up_nat(M, sm.lv, l);
-  for (int c = threadIdx.x; c < M.lv[lg].ncells; c += PCG_THREADS) M.lv[lg].x[c] = sm.lv[lg].x[c];
+  for (int l = lg; l < M.nlev - 1; ++l) down_cta(M, sm, l);
+  coarsest_cta(M, sm, M.nlev - 1);
+  for (int l = M.nlev - 2; l >= lg; --l) up_cta(M, sm, l);
+  for (int c = threadIdx.x; c < n; c += PCG_THREADS) gx[c] = sm.x[sm.base[lg] + c];
 }
 
 // z = V(r), given that the first red half-sweep of level 0 (from zero) has been
@@ -1238,7 +1281,8 @@ __device__ void solve_scene_mg(const PcgArgs& A, Shared& sh, CtaMg& sm) {
 template <bool MIXED>
 __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg_mg(const __grid_constant__ PcgArgs A) {
   __shared__ Shared sh;
-  __shared__ CtaMg sm;
+  extern __shared__ __align__(16) unsigned char mg_dyn[];
+  CtaMg& sm = *reinterpret_cast<CtaMg*>(mg_dyn);
   team_enter(blockIdx.x, gridDim.x);
   load_tables(A.mg);
   solve_scene_mg<MIXED>(A, sh, sm);
@@ -1249,7 +1293,8 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg_mg(const __grid_constant
 template <bool MIXED>
 __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg_mg_batch(const __grid_constant__ PcgBatch B) {
   __shared__ Shared sh;
-  __shared__ CtaMg sm;
+  extern __shared__ __align__(16) unsigned char mg_dyn[];
+  CtaMg& sm = *reinterpret_cast<CtaMg*>(mg_dyn);
   const int s = B.block_scene[blockIdx.x];
   team_enter(blockIdx.x - B.team_first[s], B.team_first[s + 1] - B.team_first[s]);
   load_tables(B.args[s].mg);
@@ -1275,27 +1320,35 @@ cudaError_t launch_pcg_mg(const PcgArgs& a, bool mixed, int nblocks, cudaStream_
   void* args[] = {const_cast<PcgArgs*>(&a)};
   if (mixed)
     return cudaLaunchCooperativeKernel((const void*)k_pcg_mg<true>, dim3(nblocks),
-                                       dim3(PCG_THREADS), args, 0, s);
+                                       dim3(PCG_THREADS), args, sizeof(CtaMg), s);
   return cudaLaunchCooperativeKernel((const void*)k_pcg_mg<false>, dim3(nblocks),
-                                     dim3(PCG_THREADS), args, 0, s);
+                                     dim3(PCG_THREADS), args, sizeof(CtaMg), s);
 }
 
 cudaError_t launch_pcg_mg_batch(const PcgBatch& b, bool mixed, int nblocks, cudaStream_t s) {
   void* args[] = {const_cast<PcgBatch*>(&b)};
   if (mixed)
     return cudaLaunchCooperativeKernel((const void*)k_pcg_mg_batch<true>, dim3(nblocks),
-                                       dim3(PCG_THREADS), args, 0, s);
+                                       dim3(PCG_THREADS), args, sizeof(CtaMg), s);
   return cudaLaunchCooperativeKernel((const void*)k_pcg_mg_batch<false>, dim3(nblocks),
-                                     dim3(PCG_THREADS), args, 0, s);
+                                     dim3(PCG_THREADS), args, sizeof(CtaMg), s);
 }
 
+// Opts the kernels in to the dynamic shared memory of the CTA-local levels and
+// checks that one CTA per SM fits.
 cudaError_t pcg_mg_check_occupancy() {
-  int a = 0, b = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pcg_mg<false>, PCG_THREADS, 0);
-  if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pcg_mg<true>, PCG_THREADS, 0);
-  if (e != cudaSuccess) return e;
-  return (a >= 1 && b >= 1) ? cudaSuccess : cudaErrorInvalidConfiguration;
+  const void* fns[4] = {(const void*)k_pcg_mg<false>, (const void*)k_pcg_mg<true>,
+                        (const void*)k_pcg_mg_batch<false>, (const void*)k_pcg_mg_batch<true>};
+  for (const void* f : fns) {
+    cudaError_t e =
+        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CtaMg));
+    if (e != cudaSuccess) return e;
+    int a = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, f, PCG_THREADS, sizeof(CtaMg));
+    if (e != cudaSuccess) return e;
+    if (a < 1) return cudaErrorInvalidConfiguration;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace flipk
