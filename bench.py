@@ -61,6 +61,30 @@ MG_IR_BYTES_PER_SOLVE = 40
 PCG_DRAM_BYTES_POOL256 = 6.181e9
 
 
+def stage_roofline(w, np_, nfl, stage_ms, steps, peak):
+    """Achieved HBM GB/s of the other stages: algorithmic bytes (models below) over
+    the live CUDA-event stage time, against the measured copy bandwidth.
+      bin:        scatter 64 B per particle (key, rank, 28 B read, 28 B write) +
+                  13 B per key (count read and clear, local start, cell type)
+      P2G:        24 B per particle (positions and velocities, read once) +
+                  20 B per face (accumulator read and clear, u_old write)
+      divergence: 41 B per cell (type, 3 faces, b in FP64, solution zeroed)
+      G2P:        56 B per particle (24 B in, 24 B out, key and rank)"""
+    n = w["n"]
+    cells = n ** 3
+    keys = (-(-n // 8) * 8) ** 3
+    faces = 3 * (n + 1) * n * n
+    model = {"bin": 64 * np_ + 13 * keys, "p2g": 24 * np_ + 20 * faces,
+             "divergence": 41 * cells, "g2p": 56 * np_}
+    out = {}
+    for k, b in model.items():
+        t = stage_ms[k] / steps / 1e3
+        gbs = b / t / 1e9 if t > 0 else None
+        out[k] = {"achieved_gbs": gbs, "frac": gbs / peak if gbs else None,
+                  "algorithmic_bytes": b}
+    return out
+
+
 def make_scene(w):
     from paper_2404_01931_gb300 import scenes as S
     if w["scene"] == "pool":
@@ -249,6 +273,14 @@ def run_batch(args):
     ck = clocks.stop()
     ms = e0.elapsed_time(e1)
     edges = sorted({sc.n[0] for sc in scenes})
+    # the same scenes stepped one at a time through flip_step (the plain per-scene form)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for sim in sims:
+        sim.step(args.steps)
+        sim.sync()
+    seq_s = time.perf_counter() - t0
+    seq_value = npart * args.steps / seq_s
     out = {"metric": "FLIP particle-steps/s", "value": npart * args.steps / (ms / 1e3),
            "unit": "particle-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -260,7 +292,10 @@ def run_batch(args):
            "cg_iterations_per_scene_step": sum(s.cg_iterations for s in st) / len(st) / args.steps,
            "ms_pcg_per_step": st[0].ms_pcg / args.steps,
            "max_rel_residual": max(s.cg_rel_residual for s in st), "status": rc,
-           "gpu_launches": sum(s.kernel_launches for s in st), "clocks": ck}
+           "gpu_launches": sum(s.kernel_launches for s in st), "clocks": ck,
+           "per_scene_sequential": {"value": seq_value, "unit": "particle-steps/s",
+                                    "what": "the same scenes, one flip_step call per scene "
+                                            "after another (host-timed, synchronised)"}}
     print(json.dumps(out), flush=True)
     b.close()
     for s in sims:
@@ -459,6 +494,7 @@ def main():
                          "algorithmic_bytes_per_launch": pcg_bytes / args.steps,
                          "traffic": PCG_DRAM_BYTES_POOL256 if args.workload == "pool256"
                          else None},
+            "stage_roofline": stage_roofline(w, np_, nfl, stage_ms, args.steps, peak),
             "gpu_launches": st.kernel_launches,
             "clocks": ck,
             "e2e": e2e,

@@ -300,7 +300,7 @@ __device__ __forceinline__ bool gs_apply(float* x, int l, float omega, GsIn& s, 
 template <int MODE>
 __device__ __noinline__ void sweep_split(const MgArgs& M, const MgLevel& L, const MgLevel& C,
                                          int l, int colour, FF* rz) {
-  constexpr int U = (MODE == CORRECT) ? 2 : 4;
+  constexpr int U = (MODE == CORRECT) ? 1 : 2;
   const int lane = threadIdx.x & 31;
   const SV v = sview(L);
   const PV cv = pview(C);
@@ -785,7 +785,7 @@ __device__ __noinline__ void phase_a(const PcgArgs& A, const float* pold, float*
     float zv[6], pv[6];
   };
   FF acc;
-  run_batched<2>(
+  run_batched<1>(
       it.first, it.end, PCG_WARPS,
       [&](unsigned int t, bool ok) {
         const SCell e = scell(v, v.seg[t >> 1], (int)(t & 1u), lane);
@@ -842,7 +842,7 @@ __device__ __noinline__ void phase_b(const PcgArgs& A, const float* pnew, float 
     float d, p, q, r;
   };
   FF acc;
-  run_batched<4>(
+  run_batched<2>(
       it.first, it.end, PCG_WARPS,
       [&](unsigned int t, bool ok) {
         const SCell e = scell(v, v.seg[t >> 1], (int)(t & 1u), lane);

@@ -8,7 +8,7 @@
 
 namespace flipk {
 
-constexpr int PCG_THREADS = 512;
+constexpr int PCG_THREADS = 1024;
 
 // The CTAs that solve one scene form a team: the whole grid for a single scene,
 // a slice of it when several scenes share one launch.  A CTA's rank and the
