@@ -259,8 +259,8 @@ void setup_mg(MgArgs& m, int dims[MG_MAX_LEVELS][3], const flip_params& p) {
   for (int l = 0; l < m.nlev; ++l) {
     MgLevel& L = m.lv[l];
     L.split = l < m.lgrid;
-    L.hx = (L.nx + 1) / 2;
-    L.margin = L.hx * L.ny + 1;
+    L.hx = ((L.nx + 1) / 2 + 1) & ~1;  // even, so pairs of slots are 8-byte aligned
+    L.margin = L.hx * L.ny + 2;
     L.half = L.hx * L.ny * L.nz + 2 * L.margin;
     L.nw = (L.hx + 31) / 32;
     L.nbx = (L.nx + 7) / 8;

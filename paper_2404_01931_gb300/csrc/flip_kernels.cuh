@@ -47,12 +47,13 @@ constexpr float MG_OMEGA = 2.0f;      // over-correction of the coarse correctio
 
 // One level of the hierarchy.  The grid-wide levels (l < lgrid) are stored
 // colour-split: cell (i, j, k) of colour c = (i+j+k) & 1 sits at
-//     c * half + margin + hx * (j + ny * k) + (i >> 1),   hx = ceil(nx / 2),
-// so the cells of one colour form contiguous runs along x and the six
-// neighbours of a cell are contiguous runs of the other colour at fixed
-// offsets.  margin = hx * ny + 1 slots before and after each colour's half keep
-// every neighbour address inside the array.  The CTA-local levels (l >= lgrid)
-// use the natural x-fastest layout.
+//     c * half + margin + hx * (j + ny * k) + (i >> 1),
+// hx = ceil(nx / 2) rounded up to even, so the cells of one colour form
+// contiguous runs along x, the six neighbours of a cell are contiguous runs of
+// the other colour at fixed offsets, and every even slot starts an 8-byte pair.
+// margin = hx * ny + 2 slots before and after each colour's half keep every
+// neighbour address inside the array.  The CTA-local levels (l >= lgrid) use the
+// natural x-fastest layout.
 struct MgLevel {
   int nx, ny, nz, ncells;
   float inv_scnt[8];  // 1 / (s_l * count), s_l = dt / (rho (2^l dx)^2)
@@ -65,9 +66,9 @@ struct MgLevel {
                       // when the cell is fluid; built at the start of every solve
   // colour-split levels
   int split;          // 1 for the grid-wide levels
-  int hx;             // slots per row and colour
+  int hx;             // slots per row and colour (even)
   int half;           // one colour's slots: hx * ny * nz + 2 * margin
-  int margin;         // hx * ny + 1
+  int margin;         // hx * ny + 2
   int nw;             // segments per row: ceil(hx / 32); a segment is 32 slots
                       // of each colour, i.e. 64 cells of a row
   int nbx, nby, nbz;  // 8x8x8 blocks of this level's cells

@@ -173,6 +173,77 @@ __device__ __forceinline__ Items seg_items(const MgLevel& L, int ncol) {
   return Items{(unsigned)(q.x * ncol + (int)(threadIdx.x >> 5)), (unsigned)(q.y * ncol)};
 }
 
+// Vectorised passes: a warp takes two segments (lanes 0-15 and 16-31), a lane two
+// adjacent slots s, s + 1 of one colour (s even), read and written as 8-byte
+// pairs.  Items are (segment pair, colour); item t is pair t / ncol.
+__device__ __forceinline__ Items pair_items(int2 q, int ncol) {
+  const int npairs = (q.y - q.x + 1) >> 1;
+  return Items{(unsigned)(threadIdx.x >> 5), (unsigned)(npairs * ncol)};
+}
+
+// The two cells of a lane: slots s and s + 1 of colour c in one row.
+struct PCell {
+  int j, k, r, s, par;
+  int iA;         // x of the first cell (the second is iA + 2)
+  int idx, ob;    // storage index of slot s (even) and of slot s in the other colour
+  bool okA, okB;  // inside the grid (and the lane's segment exists)
+};
+
+template <class LV>
+__device__ __forceinline__ PCell pcell(const LV& L, const int4* seg, int2 q, unsigned int pair,
+                                       int c, int lane) {
+  int sq = q.x + 2 * (int)pair + (lane >> 4);
+  const bool seg_ok = sq < q.y;
+  if (!seg_ok) sq = q.x;
+  const int4 sg = seg[sq];
+  PCell e;
+  e.j = sg.z;
+  e.k = sg.w;
+  e.r = sg.x;
+  e.s = sg.y * SEG_SLOTS + 2 * (lane & 15);
+  e.par = (c + e.j + e.k) & 1;
+  e.iA = 2 * e.s + e.par;
+  const bool s_ok = seg_ok && e.s < L.hx;
+  e.okA = s_ok && e.iA < L.nx;
+  e.okB = s_ok && e.iA + 2 < L.nx;
+  e.idx = c * L.half + L.margin + L.hx * e.r + min(e.s, L.hx - 2);
+  e.ob = e.idx + (1 - 2 * c) * L.half;
+  return e;
+}
+
+// The other colour's values around a slot pair: xm/xp the -x/+x neighbours of
+// cells A and B, ym, yp, zm, zp the pairs in the rows and planes next door.
+struct Nbr2 {
+  float xmA, xpA, xmB, xpB;
+  float2 ym, yp, zm, zp;
+};
+
+template <class LV>
+__device__ __forceinline__ Nbr2 load_nbr2(const LV& L, const float* x, const PCell& e) {
+  const float2 m = *reinterpret_cast<const float2*>(x + e.ob);
+  const float ex = x[e.ob - 1 + 3 * e.par];  // slot s - 1 (par 0) or s + 2 (par 1)
+  Nbr2 n;
+  if (e.par == 0) {
+    n.xmA = ex; n.xpA = m.x; n.xmB = m.x; n.xpB = m.y;
+  } else {
+    n.xmA = m.x; n.xpA = m.y; n.xmB = m.y; n.xpB = ex;
+  }
+  const int pl = L.hx * L.ny;
+  n.ym = *reinterpret_cast<const float2*>(x + e.ob - L.hx);
+  n.yp = *reinterpret_cast<const float2*>(x + e.ob + L.hx);
+  n.zm = *reinterpret_cast<const float2*>(x + e.ob - pl);
+  n.zp = *reinterpret_cast<const float2*>(x + e.ob + pl);
+  return n;
+}
+
+__device__ __forceinline__ void nbr_of(const Nbr2& n, int which, float (&xv)[6]) {
+  if (which == 0) {
+    xv[0] = n.xmA; xv[1] = n.xpA; xv[2] = n.ym.x; xv[3] = n.yp.x; xv[4] = n.zm.x; xv[5] = n.zp.x;
+  } else {
+    xv[0] = n.xmB; xv[1] = n.xpB; xv[2] = n.ym.y; xv[3] = n.yp.y; xv[4] = n.zm.y; xv[5] = n.zp.y;
+  }
+}
+
 // ---------------------------------------------------------------- natural levels
 
 struct Cell {
@@ -296,9 +367,81 @@ __device__ __forceinline__ bool gs_apply(float* x, int l, float omega, GsIn& s, 
 
 // Half-sweep of one colour over colour-split level l (description L; C is level
 // l+1, read in CORRECT mode).  With rz, also accumulates b x over the updated
-// cells.
+// cells.  Paired form: slots that are not fluid cells of the grid get 0.
 template <int MODE>
-__device__ __noinline__ void sweep_split(const MgArgs& M, const MgLevel& L, const MgLevel& C,
+__device__ __noinline__ void sweep_split_v(const MgArgs& M, const MgLevel& L, const MgLevel& C,
+                                         int l, int colour, FF* rz) {
+  constexpr int U = (MODE == CORRECT) ? 1 : 2;
+  const int lane = threadIdx.x & 31;
+  const SV v = sview(L);
+  const PV cv = pview(C);
+  const int nz = L.nz;
+  const float omega = M.omega;
+  const int2 q = seg_slice(L);
+  const Items it = pair_items(q, 1);
+  struct S {
+    PCell e;
+    unsigned int code2;
+    float2 b;
+    Nbr2 n;
+    float pvA[6], pvB[6];
+  };
+  FF acc;
+  run_batched<U>(
+      it.first, it.end, PCG_WARPS,
+      [&](unsigned int t, bool ok) {
+        S st;
+        st.e = pcell(v, v.seg, q, t, colour, lane);
+        st.e.okA &= ok;
+        st.e.okB &= ok;
+        st.code2 = *reinterpret_cast<const unsigned int*>(v.code + st.e.idx);
+        st.b = *reinterpret_cast<const float2*>(v.b + st.e.idx);
+        if constexpr (MODE != FIRST) st.n = load_nbr2(v, v.x, st.e);
+        if constexpr (MODE == CORRECT) {
+          parent_values(cv, v.nx, v.ny, nz, min(st.e.iA, v.nx - 1), st.e.j, st.e.k, st.pvA);
+          parent_values(cv, v.nx, v.ny, nz, min(st.e.iA + 2, v.nx - 1), st.e.j, st.e.k, st.pvB);
+        }
+        return st;
+      },
+      [&](S&) {},
+      [&](S& st) {
+        float out[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const unsigned int code = h == 0 ? (st.code2 & 0xffffu) : (st.code2 >> 16);
+          const bool ok = (h == 0 ? st.e.okA : st.e.okB) && (code & CODE_SELF);
+          const float bc = h == 0 ? st.b.x : st.b.y;
+          const int cnt = code_cnt(code);
+          float val;
+          if constexpr (MODE == FIRST) {
+            val = gs_first(l, cnt, bc);
+          } else {
+            float xv[6];
+            nbr_of(st.n, h, xv);
+            if constexpr (MODE == CORRECT) {
+#pragma unroll
+              for (int u = 0; u < 6; ++u)
+                if ((code >> u) & 1u)
+                  xv[u] = __fmaf_rn(omega, h == 0 ? st.pvA[u] : st.pvB[u], xv[u]);
+            }
+            val = gs_sum(l, cnt, code, bc, xv);
+          }
+          out[h] = ok ? val : 0.0f;
+          if (ok && rz) acc.add_prod(bc, val);
+        }
+        if (st.e.okA || st.e.okB)
+          *reinterpret_cast<float2*>(v.x + st.e.idx) = make_float2(out[0], out[1]);
+      });
+  if (rz) {
+    rz->add_prod(acc.hi, 1.0f);
+    rz->add_prod(acc.lo, 1.0f);
+  }
+}
+
+// Scalar form: a lane takes one slot (levels with few segments per CTA, where
+// more items in flight matter more than wider loads).
+template <int MODE>
+__device__ __noinline__ void sweep_split_s(const MgArgs& M, const MgLevel& L, const MgLevel& C,
                                          int l, int colour, FF* rz) {
   constexpr int U = (MODE == CORRECT) ? 1 : 2;
   const int lane = threadIdx.x & 31;
@@ -339,6 +482,21 @@ __device__ __noinline__ void sweep_split(const MgArgs& M, const MgLevel& L, cons
     rz->add_prod(acc.hi, 1.0f);
     rz->add_prod(acc.lo, 1.0f);
   }
+}
+
+// Levels with many segments per CTA take the paired form (8-byte accesses, half
+// the load instructions); the others the scalar form.
+constexpr int VEC_SEGS_PER_CTA = 256;
+
+__device__ __forceinline__ bool use_pairs(const MgLevel& L) {
+  return *L.nseg >= (unsigned)VEC_SEGS_PER_CTA * team_size();
+}
+
+template <int MODE>
+__device__ __forceinline__ void sweep_split(const MgArgs& M, const MgLevel& L, const MgLevel& C,
+                                            int l, int colour, FF* rz) {
+  if (use_pairs(L)) sweep_split_v<MODE>(M, L, C, l, colour, rz);
+  else sweep_split_s<MODE>(M, L, C, l, colour, rz);
 }
 
 // ---------------------------------------------------------------- restriction
@@ -767,8 +925,117 @@ __device__ bool vcycle_rest(const PcgArgs& A, CtaMg& sm, FF& rz) {
 // ---------------------------------------------------------------- level-0 passes
 
 // Phase A with z from the V-cycle: p_new = z + beta p_old (recomputed for the
+// neighbours), q = A p_new in difference form, partial p.q.  Both colours; paired
+// form.
+__device__ __noinline__ void phase_a_v(const PcgArgs& A, const float* pold, float* pnew, float beta,
+                                     FF& pq) {
+  const MgArgs& M = A.mg;
+  const SV v = sview(M.lv[0]);
+  const float* z = v.x;
+  float* q0 = M.q0;
+  const float s_a = A.s;
+  const int lane = threadIdx.x & 31;
+  const int2 q = seg_slice(M.lv[0]);
+  const Items it = pair_items(q, 2);
+  FF acc;
+  for (unsigned int t = it.first; t < it.end; t += PCG_WARPS) {
+    const PCell e = pcell(v, v.seg, q, t >> 1, (int)(t & 1u), lane);
+    const unsigned int code2 = *reinterpret_cast<const unsigned int*>(v.code + e.idx);
+    const float2 zc = *reinterpret_cast<const float2*>(z + e.idx);
+    const float2 pc = *reinterpret_cast<const float2*>(pold + e.idx);
+    const Nbr2 nz = load_nbr2(v, z, e);
+    const Nbr2 np = load_nbr2(v, pold, e);
+    float pn[2], qn[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const unsigned int code = h == 0 ? (code2 & 0xffffu) : (code2 >> 16);
+      const bool ok = (h == 0 ? e.okA : e.okB) && (code & CODE_SELF);
+      float zv[6], pv[6];
+      nbr_of(nz, h, zv);
+      nbr_of(np, h, pv);
+      const float p_c = __fmaf_rn(beta, h == 0 ? pc.x : pc.y, h == 0 ? zc.x : zc.y);
+      float d = 0.0f;
+      int nfl = 0;
+#pragma unroll
+      for (int u = 0; u < 6; ++u) {
+        const bool f = (code >> u) & 1u;
+        d += f ? __fsub_rn(p_c, __fmaf_rn(beta, pv[u], zv[u])) : 0.0f;
+        nfl += f;
+      }
+      const float q_c = __fmul_rn(s_a, __fmaf_rn((float)(code_cnt(code) - nfl), p_c, d));
+      pn[h] = ok ? p_c : 0.0f;
+      qn[h] = ok ? q_c : 0.0f;
+      if (ok) acc.add_prod(p_c, q_c);
+    }
+    if (e.okA || e.okB) {
+      *reinterpret_cast<float2*>(pnew + e.idx) = make_float2(pn[0], pn[1]);
+      *reinterpret_cast<float2*>(q0 + e.idx) = make_float2(qn[0], qn[1]);
+    }
+  }
+  pq.add_prod(acc.hi, 1.0f);
+  pq.add_prod(acc.lo, 1.0f);
+}
+
+// Phase B: d += alpha p, r -= alpha q, partial r.r, and the next V-cycle's first
+// red half-sweep (from zero) z = r / (s n) on red cells.  Both colours.
+__device__ __noinline__ void phase_b_v(const PcgArgs& A, const float* pnew, float alpha, FF& rr) {
+  const MgArgs& M = A.mg;
+  const SV v = sview(M.lv[0]);
+  float* d0 = M.d0;
+  const float* q0 = M.q0;
+  const int lane = threadIdx.x & 31;
+  const int2 q = seg_slice(M.lv[0]);
+  const Items it = pair_items(q, 2);
+  struct S {
+    PCell e;
+    int c;
+    unsigned int code2;
+    float2 d, p, qq, r;
+  };
+  FF acc;
+  run_batched<2>(
+      it.first, it.end, PCG_WARPS,
+      [&](unsigned int t, bool ok) {
+        S st;
+        st.c = (int)(t & 1u);
+        st.e = pcell(v, v.seg, q, t >> 1, st.c, lane);
+        st.e.okA &= ok;
+        st.e.okB &= ok;
+        st.code2 = *reinterpret_cast<const unsigned int*>(v.code + st.e.idx);
+        st.d = *reinterpret_cast<const float2*>(d0 + st.e.idx);
+        st.p = *reinterpret_cast<const float2*>(pnew + st.e.idx);
+        st.qq = *reinterpret_cast<const float2*>(q0 + st.e.idx);
+        st.r = *reinterpret_cast<const float2*>(v.b + st.e.idx);
+        return st;
+      },
+      [&](S&) {},
+      [&](S& st) {
+        float dn[2], rn[2], zn[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const unsigned int code = h == 0 ? (st.code2 & 0xffffu) : (st.code2 >> 16);
+          const bool ok = (h == 0 ? st.e.okA : st.e.okB) && (code & CODE_SELF);
+          const float dd = h == 0 ? st.d.x : st.d.y, pp = h == 0 ? st.p.x : st.p.y;
+          const float qq = h == 0 ? st.qq.x : st.qq.y, r0 = h == 0 ? st.r.x : st.r.y;
+          const float rc = __fmaf_rn(-alpha, qq, r0);
+          dn[h] = ok ? __fmaf_rn(alpha, pp, dd) : dd;
+          rn[h] = ok ? rc : r0;
+          zn[h] = ok ? gs_first(0, code_cnt(code), rc) : 0.0f;
+          if (ok) acc.add_prod(rc, rc);
+        }
+        if (st.e.okA || st.e.okB) {
+          *reinterpret_cast<float2*>(d0 + st.e.idx) = make_float2(dn[0], dn[1]);
+          *reinterpret_cast<float2*>(v.b + st.e.idx) = make_float2(rn[0], rn[1]);
+          if (st.c == 0) *reinterpret_cast<float2*>(v.x + st.e.idx) = make_float2(zn[0], zn[1]);
+        }
+      });
+  rr.add_prod(acc.hi, 1.0f);
+  rr.add_prod(acc.lo, 1.0f);
+}
+
+// Phase A with z from the V-cycle: p_new = z + beta p_old (recomputed for the
 // neighbours), q = A p_new in difference form, partial p.q.  Both colours.
-__device__ __noinline__ void phase_a(const PcgArgs& A, const float* pold, float* pnew, float beta,
+__device__ __noinline__ void phase_a_s(const PcgArgs& A, const float* pold, float* pnew, float beta,
                                      FF& pq) {
   const MgArgs& M = A.mg;
   const SV v = sview(M.lv[0]);
@@ -828,7 +1095,7 @@ __device__ __noinline__ void phase_a(const PcgArgs& A, const float* pold, float*
 
 // Phase B: d += alpha p, r -= alpha q, partial r.r, and the next V-cycle's first
 // red half-sweep (from zero) z = r / (s n) on red cells.  Both colours.
-__device__ __noinline__ void phase_b(const PcgArgs& A, const float* pnew, float alpha, FF& rr) {
+__device__ __noinline__ void phase_b_s(const PcgArgs& A, const float* pnew, float alpha, FF& rr) {
   const MgArgs& M = A.mg;
   const SV v = sview(M.lv[0]);
   float* d0 = M.d0;
@@ -868,6 +1135,17 @@ __device__ __noinline__ void phase_b(const PcgArgs& A, const float* pnew, float 
       });
   rr.add_prod(acc.hi, 1.0f);
   rr.add_prod(acc.lo, 1.0f);
+}
+
+__device__ __forceinline__ void phase_a(const PcgArgs& A, const float* pold, float* pnew,
+                                        float beta, FF& pq) {
+  if (use_pairs(A.mg.lv[0])) phase_a_v(A, pold, pnew, beta, pq);
+  else phase_a_s(A, pold, pnew, beta, pq);
+}
+
+__device__ __forceinline__ void phase_b(const PcgArgs& A, const float* pnew, float alpha, FF& rr) {
+  if (use_pairs(A.mg.lv[0])) phase_b_v(A, pnew, alpha, rr);
+  else phase_b_s(A, pnew, alpha, rr);
 }
 
 // One pass over this thread's fluid cells of level 0, both colours (start of the
