@@ -66,11 +66,11 @@ __device__ __forceinline__ void p2g_cell(const Grid& g, const PartView& P, unsig
 #pragma unroll
       for (int y = 0; y < NY; ++y) {
         const float wyz = __fmul_rn(wy[y], wz[z]);
+        const float t = __fmul_rn(wyz, pv);
 #pragma unroll
         for (int x = 0; x < NX; ++x) {
-          const float w = __fmul_rn(wx[x], wyz);
-          an[z][y][x] = __fmaf_rn(w, pv, an[z][y][x]);
-          ad[z][y][x] = __fadd_rn(ad[z][y][x], w);
+          an[z][y][x] = __fmaf_rn(wx[x], t, an[z][y][x]);
+          ad[z][y][x] = __fmaf_rn(wx[x], wyz, ad[z][y][x]);
         }
       }
   }
@@ -102,7 +102,7 @@ __device__ __forceinline__ void flush_tile(const Grid& g, int b0, int b1, int b2
   }
 }
 
-__global__ void __launch_bounds__(P2G_THREADS) k_p2g(const Grid g, const PartView P,
+__global__ void __launch_bounds__(P2G_THREADS, 4) k_p2g(const Grid g, const PartView P,
                                                      const BinView B, float2* acc0, float2* acc1,
                                                      float2* acc2, const DevStats* st) {
   __shared__ float tnum[3][TILE_PAD];
@@ -154,7 +154,7 @@ __global__ void k_finalize(const Grid g, float2* acc0, float2* acc1, float2* acc
     else { acc = acc2; uo = uo2; idx = f - n0 - n1; }
     const float2 v = acc[idx];
     uo[idx] = (v.y != 0.0f) ? __fdiv_rn(v.x, v.y) : 0.0f;
-    acc[idx] = make_float2(0.0f, 0.0f);
+    if (v.x != 0.0f || v.y != 0.0f) acc[idx] = make_float2(0.0f, 0.0f);  // empty faces stay clear
   }
 }
 
