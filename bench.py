@@ -379,6 +379,8 @@ def main():
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--budget-gb", type=float, default=180.0)
     ap.add_argument("--max-batch", type=int, default=64)
+    ap.add_argument("--warm-start", action="store_true",
+                    help="start every solve from the last solve's pressure (flip_params.warm_start)")
     ap.add_argument("--cg-tol", type=float, default=None,
                     help="override the workload's cg_tol (mixed mode: refinement trigger)")
     args = ap.parse_args()
@@ -408,6 +410,7 @@ def main():
 
     sc = make_scene(w)
     prm = make_params(w)
+    prm.warm_start = 1 if args.warm_start else 0
     sim = F.Simulation(prm, *sc.arrays())
     stream = torch.cuda.ExternalStream(sim.stream)
     np_ = sc.n_particles
@@ -480,7 +483,9 @@ def main():
                        "ir_tol": w["ir_tol"], "cg_tol": w["cg_tol"], "dt": 1 / 240,
                        "flip_ratio": 0.95, "seed": 0,
                        "parallelism": f"{ws} independent replica(s), one per GPU",
-                       "l2": "inputs larger than L2 (particles + grids > 1 GB); no flush"},
+                       "l2": "inputs larger than L2 (particles + grids > 1 GB); no flush",
+                       "pressure_start": "last solve's pressure (warm start)" if args.warm_start
+                       else "zero (cold start)"},
             "stages_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
             "cg_iterations_per_step": st.cg_iterations / args.steps,
             "ir_iterations_per_step": st.ir_iterations / args.steps,

@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define FLIP_ABI_VERSION 2
+#define FLIP_ABI_VERSION 3
 
 /* ------------------------------------------------------------ status codes */
 enum {
@@ -87,24 +87,32 @@ typedef struct {
   double skin;           /* wall clamp distance (> 0, < dx) */
   double cg_tol;         /* FP32 mode: PCG stops at ||r|| <= cg_tol*||b||.
                             Mixed mode: refinement trigger in (0,1): the FP32
-                            correction is folded into the FP64 solution and the
-                            residual recomputed in FP64 whenever the recursive
-                            residual has dropped by this factor (e.g. 0.1). */
+                            correction is folded into the float-pair (~48-bit)
+                            solution and the residual recomputed in float pairs
+                            whenever the recursive residual has dropped by this
+                            factor (e.g. 1e-3). */
   double ir_tol;         /* mixed mode: outer stop at ||b - A x|| <= ir_tol*||b|| */
   int32_t cg_max_iter;   /* PCG iteration cap (per solve; per inner solve in mixed) */
-  int32_t ir_max_iter;   /* mixed mode: cap on the FP64 refinements per solve */
+  int32_t ir_max_iter;   /* mixed mode: cap on the refinements per solve */
   int32_t precision;     /* FLIP_PREC_* */
   int32_t advect_source; /* FLIP_ADVECT_* */
   int32_t preconditioner; /* FLIP_PRECOND_* (flip_step; flip_solve_pressure and
                              its no-alloc variant always use Jacobi) */
   int32_t mg_smooth;     /* multigrid: red-black sweep pairs before and after the
                             coarse correction, in [1, 8] */
+  int32_t warm_start;    /* 0: every solve starts from p = 0 (the pinned reading).
+                            1 (multigrid only): it starts from the pressure of the
+                            last solve on this handle (values of cells that were not
+                            fluid then are whatever the storage holds); the stopping
+                            rule ||r|| <= tol*||b|| is unchanged, so the result is the
+                            same solution to the same tolerance, usually in fewer
+                            iterations.  Not in the paper (a standard device). */
 } flip_params;
 
 /* Fills p with the defaults of the 32^3 dam break: dx = 1/n, dt = 1/240,
  * g = (0, -9.81, 0), rho = 1, r = 0.95, skin = 1e-3*dx, cg_tol = 1e-6,
  * ir_tol = 1e-8, cg_max_iter = 20*max(n), ir_max_iter = 100, FP32, particle
- * advection, multigrid preconditioner with 2 sweep pairs. */
+ * advection, multigrid preconditioner with 2 sweep pairs, no warm start. */
 void flip_default_params(flip_params* p, int32_t nx, int32_t ny, int32_t nz);
 
 /* Optional allocator: when given to flip_create, every device allocation of

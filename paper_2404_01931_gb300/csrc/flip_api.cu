@@ -141,6 +141,7 @@ void flip_default_params(flip_params* p, int32_t nx, int32_t ny, int32_t nz) {
   p->advect_source = FLIP_ADVECT_PARTICLE;
   p->preconditioner = FLIP_PRECOND_MG;
   p->mg_smooth = 2;
+  p->warm_start = 0;
 }
 
 }  // extern "C"
@@ -173,6 +174,8 @@ int check_params(const flip_params* p, bool need_particles_prm) {
       return fail(FLIP_E_ARG, "unknown preconditioner");
     if (p->preconditioner == FLIP_PRECOND_MG && (p->mg_smooth < 1 || p->mg_smooth > 8))
       return fail(FLIP_E_ARG, "mg_smooth must be in [1, 8]");
+    if (p->warm_start != 0 && p->warm_start != 1)
+      return fail(FLIP_E_ARG, "warm_start must be 0 or 1");
     if (!(p->flip_ratio >= 0.0 && p->flip_ratio <= 1.0))
       return fail(FLIP_E_ARG, "flip_ratio must be in [0, 1]");
     if (!(p->skin > 0.0 && p->skin < p->dx)) return fail(FLIP_E_ARG, "skin must be in (0, dx)");
@@ -406,6 +409,7 @@ PcgArgs pcg_args(flip_handle* h) {
   a.check_singular = 1;
   a.timeout_ns = 5000000000ull;
   a.precond = h->prm.preconditioner;
+  a.warm_start = h->prm.warm_start;
   if (a.precond == FLIP_PRECOND_MG) {
     a.mg = h->mg;
     a.mg.lv[0].t = h->type;

@@ -128,6 +128,7 @@ struct PcgArgs {
   int check_singular;   // compare n_fluid with the cell count
   unsigned long long timeout_ns;
   int precond;          // 0 Jacobi, 1 multigrid
+  int warm_start;       // multigrid: start from the last solve's solution
   MgArgs mg;
 };
 

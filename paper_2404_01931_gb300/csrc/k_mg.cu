@@ -1361,8 +1361,8 @@ struct SolveState {
 };
 
 // Partial-sum slots (float pairs): 0 = p.q (phase A), 1 = r.r (phase B),
-// 3 = r.z (end of the V-cycle), 4 = ||b||^2 (start), 5 = FP64 residual norm
-// (refinement).  A slot's readers always pass another barrier before the slot
+// 3 = r.z (end of the V-cycle), 4 and 5 = ||b||^2 and ||r_0||^2 (start), 5 = the
+// recomputed residual's norm (refinement).  A slot's readers always pass another barrier before the slot
 // is written again.
 template <bool MIXED>
 __device__ void solve_mg(const PcgArgs& A, Shared& sh, CtaMg& sm, SolveState& S) {
@@ -1373,39 +1373,70 @@ __device__ void solve_mg(const PcgArgs& A, Shared& sh, CtaMg& sm, SolveState& S)
   float* r = L0.b;
   if (!build_levels(A, sh)) { S.ok = false; return; }
   if (M.nlev > 1 && team_rank() == 0) cta_levels_init(M, sm);
-  // ---- start: r = b, d = 0, p_old = 0, first red half-sweep of the V-cycle;
-  // mixed mode: b and x = 0 as float pairs
+  // ---- start: r = b (cold) or b - A x0 (warm start from the last solve's x),
+  // p_old = 0, first red half-sweep of the V-cycle; mixed mode: b as a float pair,
+  // the correction d = 0, and x = 0 unless warm
+  const bool warm = A.warm_start != 0;
   {
-    FF bb;
-    for_fluid0(A, [&](const SCell& e, unsigned int code, int n) {
-      float bc;
-      if constexpr (MIXED) {
+    FF bb, rr0;
+    const SV v0 = sview(L0);
+    const float s_a = A.s;
+    if (warm && MIXED) {  // b as a pair first: the residual pass below reads it
+      for_fluid0(A, [&](const SCell& e, unsigned int, int n) {
         const double b64 = A.b64[n];
-        bc = __double2float_rn(b64);
-        M.b2[e.idx] = make_float2(bc, __double2float_rn(b64 - (double)bc));
-        M.x2[e.idx] = make_float2(0.0f, 0.0f);
+        const float bh = __double2float_rn(b64);
+        M.b2[e.idx] = make_float2(bh, __double2float_rn(b64 - (double)bh));
+      });
+      if (!gsync(A)) { S.ok = false; return; }
+    }
+    for_fluid0(A, [&](const SCell& e, unsigned int code, int n) {
+      float bc, rc;
+      if constexpr (MIXED) {
+        if (warm) {
+          bc = M.b2[e.idx].x;
+          const float2 rp = residual_pair(v0, M.x2, M.b2, e, code, s_a);
+          rc = __fadd_rn(rp.x, rp.y);
+        } else {
+          const double b64 = A.b64[n];
+          bc = __double2float_rn(b64);
+          M.b2[e.idx] = make_float2(bc, __double2float_rn(b64 - (double)bc));
+          M.x2[e.idx] = make_float2(0.0f, 0.0f);
+          rc = bc;
+        }
+        d[e.idx] = 0.0f;
       } else {
         bc = A.b32[n];
+        rc = bc;
+        if (warm) {
+          int nb[6];
+          snbr(v0, e, nb);
+          float xv[6];
+#pragma unroll
+          for (int q = 0; q < 6; ++q) xv[q] = d[nb[q]];
+          rc = resid(s_a, code_cnt(code), code, bc, d[e.idx], xv);
+        } else {
+          d[e.idx] = 0.0f;
+        }
       }
-      r[e.idx] = bc;
-      d[e.idx] = 0.0f;
+      r[e.idx] = rc;
       M.pa0[e.idx] = 0.0f;
-      if (e.idx < L0.half) z[e.idx] = gs_first(0, code_cnt(code), bc);
+      if (e.idx < L0.half) z[e.idx] = gs_first(0, code_cnt(code), rc);
       bb.add_prod(bc, bc);
+      rr0.add_prod(rc, rc);
     });
-    F2 v[1] = {f2_of(bb)};
-    publish<1>(A, 4, v, sh);
+    F2 v[2] = {f2_of(bb), f2_of(rr0)};
+    publish<2>(A, 4, v, sh);
   }
   if (!gsync(A)) { S.ok = false; return; }
   double rz = 0.0, bnorm = 0.0, rnorm = 0.0, rmax = 0.0;
   const double target = MIXED ? A.ir_tol : A.tol;
   {
-    double s0[1];
-    gather<1>(A, 4, s0, sh);
+    double s0[2];
+    gather<2>(A, 4, s0, sh);
     if (threadIdx.x == 0) {
       bnorm = sqrt(fmax(s0[0], 0.0));
-      rnorm = rmax = bnorm;
-      sh.flag = (bnorm == 0.0) ? 1 : 0;
+      rnorm = rmax = sqrt(fmax(s0[1], 0.0));
+      sh.flag = (bnorm == 0.0 || rnorm <= target * bnorm) ? 1 : 0;
     }
   }
   __syncthreads();

@@ -57,7 +57,8 @@ class FlipParams(C.Structure):
                 ("skin", C.c_double), ("cg_tol", C.c_double), ("ir_tol", C.c_double),
                 ("cg_max_iter", C.c_int32), ("ir_max_iter", C.c_int32),
                 ("precision", C.c_int32), ("advect_source", C.c_int32),
-                ("preconditioner", C.c_int32), ("mg_smooth", C.c_int32)]
+                ("preconditioner", C.c_int32), ("mg_smooth", C.c_int32),
+                ("warm_start", C.c_int32)]
 
 
 class FlipStats(C.Structure):
@@ -140,7 +141,7 @@ def lib():
         L.flip_server_destroy.restype = None
         L.flip_solve_pressure_noalloc.argtypes = [PP, vp, vp, vp, vp, C.POINTER(i32),
                                                   C.POINTER(C.c_double)]
-        if L.flip_abi_version() != 2:
+        if L.flip_abi_version() != 3:
             raise RuntimeError("libflip_gb300 ABI version mismatch")
         _lib = L
     return _lib

@@ -401,3 +401,34 @@ def test_pool_drop_256_full_size_mixed():
     _compare_particles(ref, got, 1 / 256)
     ids = got["particles"]  # creation order restored through the ids
     assert all(a.shape[0] == 42266944 for a in ids)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("mixed", [False, True])
+def test_warm_start_reaches_the_cold_start_solution(mixed):
+    """flip_params.warm_start starts each solve from the previous pressure: the
+    stopping rule is unchanged, so after each step the pressure equals the cold-start
+    one to the solve's tolerance, in fewer iterations once the flow is steady."""
+    n = 48
+    sc = S.pool_drop(n)
+    runs = {}
+    for warm in (0, 1):
+        p = F.default_params(n)
+        if mixed:
+            p.precision = F.FLIP_PREC_MIXED_IR
+            p.cg_tol, p.ir_tol = 1e-3, 1e-8
+        p.warm_start = warm
+        with F.Simulation(p, *sc.arrays()) as sim:
+            iters, press = [], []
+            for _ in range(4):
+                rc, st = sim.step(1, stats=True)
+                assert rc == F.FLIP_OK
+                iters.append(st.cg_iterations)
+                press.append(sim.read(F.PRESSURE_F64 if mixed else F.PRESSURE).astype(np.float64))
+            runs[warm] = (iters, press)
+    tol = 1e-6 if mixed else 2e-4
+    for k in range(4):
+        e = rel_l2(runs[1][1][k], runs[0][1][k])
+        assert e <= tol, (k, e)
+    assert abs(runs[1][0][0] - runs[0][0][0]) <= 1  # the first solve starts from zero either way
+    assert sum(runs[1][0][1:]) < sum(runs[0][0][1:]), (runs[1][0], runs[0][0])
