@@ -461,9 +461,28 @@ def main():
                "h2d_bytes_per_step": 24 * np_, "d2h_bytes_per_step": 24 * np_,
                "steps": args.e2e_steps}
 
+    # energy diagnostic (Sec. 4, Fig. 10), outside the timed region: 24 B per
+    # particle; each call ends with a host synchronisation, included in its time
+    diag = None
+    if rank == 0:
+        m = prm.rho * prm.dx ** 3 / 8
+        sim.energy(m)
+        t = []
+        for _ in range(5):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            energy = sim.energy(m)
+            b.record(stream)
+            b.synchronize()
+            t.append(a.elapsed_time(b))
+        diag = {"energy_ms": min(t), "energy_bytes": 24 * np_, "energy_total": energy[2]}
+
     if rank == 0:
         peak, peak_kind = read_peaks()
         nfl = st.n_fluid_cells
+        if diag:
+            diag["energy_frac_of_measured_hbm"] = diag["energy_bytes"] / (diag["energy_ms"] / 1e3) / 1e9 / peak
         mixed = w["precision"] == "mixed"
         pcg_bytes = nfl * (MG_PCG_BYTES_PER_ITER * st.cg_iterations
                            + (MG_IR_BYTES_PER_OUTER * st.ir_iterations
@@ -501,6 +520,7 @@ def main():
                          else None},
             "stage_roofline": stage_roofline(w, np_, nfl, stage_ms, args.steps, peak),
             "gpu_launches": st.kernel_launches,
+            "diagnostics": diag,
             "clocks": ck,
             "e2e": e2e,
         }

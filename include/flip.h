@@ -208,6 +208,18 @@ int flip_read_particles(flip_handle* h, float* x, float* y, float* z, float* u, 
 int flip_write_particles(flip_handle* h, const float* x, const float* y, const float* z,
                          const float* u, const float* v, const float* w, int32_t src_is_device);
 
+/* Total mechanical energy of the particles, the quantity the paper follows over
+ * a run to compare its CPU and GPU versions (Sec. 4, Fig. 10).  With particle
+ * mass m = particle_mass and the handle's gravity g:
+ *   out[0] kinetic   = m/2 * sum_p |v_p|^2
+ *   out[1] potential = -m * sum_p g . x_p      (zero at the origin)
+ *   out[2] total     = out[0] + out[1]
+ * The sums are accurate to FP64 rounding (float pairs per thread, FP64 across
+ * threads); their order follows the particle buffer, so the last bits may vary
+ * from run to run.  Synchronous.  FLIP_E_ARG for a NULL handle or out, or a
+ * negative or non-finite mass. */
+int flip_energy(flip_handle* h, double particle_mass, double out[3]);
+
 /* Device bytes a scene with these parameters and np particles holds (its arena;
  * what flip_create allocates).  0 when the parameters are invalid or no device
  * is usable.  Allocates nothing. */

@@ -70,6 +70,8 @@ def lib():
                                   C.POINTER(OracleFields), C.POINTER(OracleStats)]
         L.oracle_step.restype = C.c_int
         L.oracle_num_threads.restype = C.c_int
+        L.oracle_energy.argtypes = [C.c_int64, vp, vp, vp, vp, vp, vp, vp, C.c_double, vp]
+        L.oracle_energy.restype = None
         _lib = L
     return _lib
 
@@ -319,6 +321,15 @@ def cell_of(params: Params, x, y, z):
     out = np.zeros(3, np.int64)
     lib().oracle_cell_of(C.byref(params.c()), float(x), float(y), float(z), _p(out))
     return out
+
+
+def energy(gravity, mass, x, y, z, u, v, w):
+    """(kinetic, potential, total) of a particle set of equal masses (Sec. 4, Fig. 10)."""
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, z, u, v, w)]
+    g = np.asarray(gravity, dtype=np.float64)
+    out = np.zeros(3)
+    lib().oracle_energy(arrs[0].shape[0], *[_p(a) for a in arrs], _p(g), float(mass), _p(out))
+    return tuple(float(t) for t in out)
 
 
 def num_threads() -> int:

@@ -653,3 +653,17 @@ int oracle_pcg_mg(const oracle_params* P, const uint8_t* type, const double* b, 
   mg_free(lv, L);
   return result;
 }
+
+/* Sec. 4, Fig. 10: kinetic plus potential energy, summed particle by particle. */
+void oracle_energy(int64_t np, const double* x, const double* y, const double* z,
+                   const double* u, const double* v, const double* w, const double g[3],
+                   double m, double out[3]) {
+  double ke = 0.0, pe = 0.0;
+  for (int64_t p = 0; p < np; ++p) {
+    ke += 0.5 * m * (u[p] * u[p] + v[p] * v[p] + w[p] * w[p]);
+    pe -= m * (g[0] * x[p] + g[1] * y[p] + g[2] * z[p]);
+  }
+  out[0] = ke;
+  out[1] = pe;
+  out[2] = ke + pe;
+}

@@ -149,6 +149,13 @@ double oracle_div_norm(const oracle_params* P, const double* const u[3], const u
 int oracle_step(const oracle_params* P, int64_t np, double* x, double* y, double* z, double* u,
                 double* v, double* w, oracle_fields* out, oracle_stats* stats);
 
+/* Total mechanical energy of a particle set (Sec. 4, Fig. 10), each particle of
+ * mass m: out[0] = m/2 sum |v|^2, out[1] = -m sum g . x (zero at the origin),
+ * out[2] = out[0] + out[1].  Plain sequential FP64 sums. */
+void oracle_energy(int64_t np, const double* x, const double* y, const double* z,
+                   const double* u, const double* v, const double* w, const double g[3],
+                   double m, double out[3]);
+
 int oracle_num_threads(void);
 
 #ifdef __cplusplus

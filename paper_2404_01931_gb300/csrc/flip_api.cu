@@ -91,6 +91,7 @@ struct flip_handle {
   DevStats* dstats = nullptr;
   DevStats* hstats = nullptr;  // pinned
   double* norms = nullptr;
+  double* diag = nullptr;      // energy sums: 4 per CTA, then the 4 totals
   void* tmp = nullptr;
   size_t tmp_bytes = 0;
   int pcg_blocks = 0, sm_count = 0, p2g_blocks = 0, g2p_blocks = 0;
@@ -360,6 +361,7 @@ void carve(flip_handle* h, Carver& cv) {
   h->bar = cv.take<unsigned int>(BAR_WORDS);
   h->dstats = cv.take<DevStats>(1);
   h->norms = cv.take<double>(2);
+  h->diag = cv.take<double>(4 * (size_t)energy_blocks(h->sm_count) + 4);
   const size_t nfmax = (size_t)std::max(h->nf[0], std::max(h->nf[1], h->nf[2]));
   h->tmp_bytes = std::max(nfmax * sizeof(float), nc * sizeof(double));
   h->tmp = cv.take<char>(h->tmp_bytes);
@@ -637,6 +639,28 @@ int flip_step(flip_handle* h, int32_t nsteps, flip_stats* stats) {
     cudaEventDestroy(t_end);
   }
   return rc;
+}
+
+int flip_energy(flip_handle* h, double particle_mass, double out[3]) {
+  if (!h) return fail(FLIP_E_ARG, "handle is NULL");
+  if (!out) return fail(FLIP_E_ARG, "out is NULL");
+  if (!(particle_mass >= 0.0) || !std::isfinite(particle_mass))
+    return fail(FLIP_E_ARG, "particle_mass must be finite and >= 0");
+  double sums[4] = {0.0, 0.0, 0.0, 0.0};
+  if (h->np > 0) {
+    const int nb = energy_blocks(h->sm_count);
+    double* tot = h->diag + 4 * (size_t)nb;
+    launch_energy(h->P[h->cur], h->np, h->diag, nb, tot, h->stream);
+    FLIP_CUDA(cudaGetLastError());
+    h->launches += 2;
+    FLIP_CUDA(cudaMemcpyAsync(sums, tot, sizeof(sums), cudaMemcpyDeviceToHost, h->stream));
+  }
+  FLIP_CUDA(cudaStreamSynchronize(h->stream));
+  const double* g = h->prm.gravity;
+  out[0] = 0.5 * particle_mass * sums[0];
+  out[1] = -particle_mass * (g[0] * sums[1] + g[1] * sums[2] + g[2] * sums[3]);
+  out[2] = out[0] + out[1];
+  return FLIP_OK;
 }
 
 size_t flip_footprint_bytes(const flip_params* params, int64_t np) {

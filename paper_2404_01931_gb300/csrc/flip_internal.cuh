@@ -117,6 +117,13 @@ struct FF {
     hi = t;
     lo = __fadd_rn(lo, __fadd_rn(e, pe));
   }
+  __device__ __forceinline__ void add(float t) {
+    const float s = __fadd_rn(hi, t);
+    const float bv = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(t, bv));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+  }
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 

@@ -219,4 +219,11 @@ void launch_g2p(const Grid& g, const StepConsts& k, const PartView& p, const Bin
                 const float* const uo[3], const float* p32, const float2* pff, DevStats* st,
                 long long np, int nblocks, cudaStream_t s);
 
+// k_diag.cu
+// Sums over the particles (FP64): out[0] = sum |v|^2, out[1..3] = sum x, y, z.
+// partials holds 4 * nblocks doubles.
+int energy_blocks(int sm_count);
+void launch_energy(const PartView& p, long long np, double* partials, int nblocks, double* out,
+                   cudaStream_t s);
+
 }  // namespace flipk

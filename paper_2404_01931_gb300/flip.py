@@ -141,6 +141,7 @@ def lib():
         L.flip_server_destroy.restype = None
         L.flip_solve_pressure_noalloc.argtypes = [PP, vp, vp, vp, vp, C.POINTER(i32),
                                                   C.POINTER(C.c_double)]
+        L.flip_energy.argtypes = [vp, C.c_double, C.POINTER(C.c_double)]
         if L.flip_abi_version() != 3:
             raise RuntimeError("libflip_gb300 ABI version mismatch")
         _lib = L
@@ -281,6 +282,13 @@ def flip_read_particles(h, x, y, z, u, v, w, ids=None):
 def flip_write_particles(h, x, y, z, u, v, w):
     bufs = [_buf(a, np.float32) for a in (x, y, z, u, v, w)]
     _check(lib().flip_write_particles(h, *[C.c_void_p(b[0]) for b in bufs], bufs[0][2]))
+
+
+def flip_energy(h, particle_mass: float):
+    """(kinetic, potential, total) energy of the handle's particles (Sec. 4, Fig. 10)."""
+    out = (C.c_double * 3)()
+    _check(lib().flip_energy(h, float(particle_mass), out))
+    return float(out[0]), float(out[1]), float(out[2])
 
 
 def flip_destroy(h):
@@ -471,6 +479,10 @@ class Simulation:
 
     def write(self, field: int, src):
         flip_write(self.h, field, src)
+
+    def energy(self, particle_mass: float):
+        """(kinetic, potential, total) energy of the particles (Sec. 4, Fig. 10)."""
+        return flip_energy(self.h, particle_mass)
 
     def particles(self, by_id: bool = True):
         """(x, y, z, u, v, w) as float32 numpy arrays, in creation order when by_id."""

@@ -21,9 +21,10 @@ rounded to float32 once; both the CUDA path and the oracle receive those float32
 arrays.
 
 Scenes named after the paper's benchmarks (Table 1): ``dam_break`` (fluid block
-against the x=0 wall) and ``pool_drop`` (a pool plus a falling sphere, the "water
-drop").  The paper gives no geometry for either; the shapes used here are the
-synthetic stand-ins this project measures on.
+against the x=0 wall), ``double_dam_break`` (two blocks against the opposite x
+walls), ``water_drop`` (a free sphere falling to the floor) and ``pool_drop`` (a
+pool plus a falling sphere).  The paper names the scenes but gives no geometry;
+the shapes used here are the synthetic stand-ins this project measures on.
 """
 from __future__ import annotations
 
@@ -125,6 +126,24 @@ def pool_drop(n: int, depth: float = 0.3, centre=(0.5, 0.7, 0.5), radius: float 
     sphere = (cx - centre[0]) ** 2 + (cy - centre[1]) ** 2 + (cz - centre[2]) ** 2 < radius ** 2
     mask = (cy < depth) | sphere
     return seed_mask(mask, dx, density, seed, name=f"pool_drop_{n}")
+
+
+def double_dam_break(n: int, frac_x: float = 0.2, frac_y: float = 0.5, density: int = 2,
+                     seed: int = 0) -> Scene:
+    """Two fluid blocks ``x < frac_x`` and ``x > 1 - frac_x`` (``y < frac_y``, full z)."""
+    dx = 1.0 / n
+    cx, cy, _ = cell_centres((n, n, n), dx)
+    mask = ((cx < frac_x) | (cx > 1.0 - frac_x)) & (cy < frac_y)
+    return seed_mask(mask, dx, density, seed, name=f"double_dam_break_{n}")
+
+
+def water_drop(n: int, centre=(0.5, 0.6, 0.5), radius: float = 0.2, density: int = 2,
+               seed: int = 0) -> Scene:
+    """A sphere of fluid at rest, free to fall onto the floor."""
+    dx = 1.0 / n
+    cx, cy, cz = cell_centres((n, n, n), dx)
+    mask = (cx - centre[0]) ** 2 + (cy - centre[1]) ** 2 + (cz - centre[2]) ** 2 < radius ** 2
+    return seed_mask(mask, dx, density, seed, name=f"water_drop_{n}")
 
 
 def layer(n, height_cells: int, density: int = 2, seed: int = 0) -> Scene:
