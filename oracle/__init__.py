@@ -72,6 +72,15 @@ def lib():
         L.oracle_num_threads.restype = C.c_int
         L.oracle_energy.argtypes = [C.c_int64, vp, vp, vp, vp, vp, vp, vp, C.c_double, vp]
         L.oracle_energy.restype = None
+        L.oracle_blobby_kernel.argtypes = [C.c_double]
+        L.oracle_blobby_kernel.restype = C.c_double
+        L.oracle_sdf.argtypes = [C.c_int64, vp, vp, vp, vp, vp, C.c_double, C.c_double,
+                                 C.c_double, vp]
+        L.oracle_sdf.restype = None
+        L.oracle_mc_count.argtypes = [vp, vp, C.c_double, vp]
+        L.oracle_mc_count.restype = C.c_int64
+        L.oracle_mc.argtypes = [vp, vp, C.c_double, vp, C.c_double, vp, vp, vp, vp]
+        L.oracle_mc.restype = None
         _lib = L
     return _lib
 
@@ -330,6 +339,45 @@ def energy(gravity, mass, x, y, z, u, v, w):
     out = np.zeros(3)
     lib().oracle_energy(arrs[0].shape[0], *[_p(a) for a in arrs], _p(g), float(mass), _p(out))
     return tuple(float(t) for t in out)
+
+
+def blobby_kernel(s: float) -> float:
+    """k(s) = max(0, (1 - s^2)^3) of Sec. 3.3.1."""
+    return float(lib().oracle_blobby_kernel(float(s)))
+
+
+def sdf(x, y, z, n, origin, h, radius, search_radius):
+    """Sec. 3.3.1 scalar field at the (n+1)^3 sampling corners; shape (nz+1, ny+1, nx+1)."""
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, z)]
+    n3 = np.asarray(n, dtype=np.int32)
+    o = np.asarray(origin, dtype=np.float64)
+    phi = np.zeros((n3[2] + 1, n3[1] + 1, n3[0] + 1))
+    lib().oracle_sdf(arrs[0].shape[0], *[_p(a) for a in arrs], _p(n3), _p(o), float(h),
+                     float(radius), float(search_radius), _p(phi))
+    return phi
+
+
+@dataclass
+class Mesh:
+    vertices: np.ndarray   # (nv, 3) float64
+    normals: np.ndarray    # (nv, 3)
+    triangles: np.ndarray  # (nt, 3) int32
+    vertex_edge: np.ndarray  # (nv,) int64
+
+
+def marching_cubes(phi, origin, h, iso=0.0) -> Mesh:
+    """Sec. 3.3.2 on a corner field of shape (nz+1, ny+1, nx+1)."""
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    n3 = np.array([phi.shape[2] - 1, phi.shape[1] - 1, phi.shape[0] - 1], dtype=np.int32)
+    o = np.asarray(origin, dtype=np.float64)
+    nt = C.c_int64(0)
+    L = lib()
+    nv = L.oracle_mc_count(_p(n3), _p(phi), float(iso), C.byref(nt))
+    m = Mesh(np.zeros((nv, 3)), np.zeros((nv, 3)), np.zeros((nt.value, 3), np.int32),
+             np.zeros(nv, np.int64))
+    L.oracle_mc(_p(n3), _p(o), float(h), _p(phi), float(iso), _p(m.vertices), _p(m.vertex_edge),
+                _p(m.triangles), _p(m.normals))
+    return m
 
 
 def num_threads() -> int:

@@ -156,6 +156,18 @@ void oracle_energy(int64_t np, const double* x, const double* y, const double* z
                    const double* u, const double* v, const double* w, const double g[3],
                    double m, double out[3]);
 
+/* Surface reconstruction (Sec. 3.3), surface_oracle.c.  Sampling corners
+ * (i,j,k) in [0,n[0]] x [0,n[1]] x [0,n[2]] at origin + h*(i,j,k), x fastest. */
+double oracle_blobby_kernel(double s);
+void oracle_sdf(int64_t np, const double* x, const double* y, const double* z,
+                const int32_t n[3], const double origin[3], double h, double r, double R,
+                double* phi);
+/* Vertex count (returned) and triangle count of the marching-cubes mesh. */
+int64_t oracle_mc_count(const int32_t n[3], const double* phi, double iso, int64_t* n_triangles);
+/* The mesh: vert[3 nv], vedge[nv] (3 * corner + axis), tri[3 nt], nrm[3 nv]. */
+void oracle_mc(const int32_t n[3], const double origin[3], double h, const double* phi,
+               double iso, double* vert, int64_t* vedge, int32_t* tri, double* nrm);
+
 int oracle_num_threads(void);
 
 #ifdef __cplusplus

@@ -1205,3 +1205,14 @@ int flip_solve_pressure(const flip_params* params, const uint8_t* type, const fl
 }
 
 }  // extern "C"
+
+namespace flipk {
+// The current particle buffer of a handle and its stream (for k_surface.cu).
+bool handle_particles(flip_handle* h, PartView* p, long long* np, cudaStream_t* s) {
+  if (!h) return false;
+  *p = h->P[h->cur];
+  *np = h->np;
+  *s = h->stream;
+  return true;
+}
+}  // namespace flipk

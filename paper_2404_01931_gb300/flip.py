@@ -84,6 +84,15 @@ _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
 _FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
 
 
+class FlipSurfaceParams(C.Structure):
+    _fields_ = [("n", C.c_int32 * 3), ("origin", C.c_double * 3), ("h", C.c_double),
+                ("radius", C.c_double), ("search_radius", C.c_double), ("iso", C.c_double)]
+
+
+SURF_FIELD, SURF_VERTICES, SURF_NORMALS, SURF_TRIANGLES, SURF_VERTEX_EDGE = range(5)
+SURF_MAX_TRI = 12
+
+
 class FlipAlloc(C.Structure):
     _fields_ = [("ctx", C.c_void_p), ("alloc", _ALLOC_FN), ("free", _FREE_FN)]
 
@@ -142,6 +151,19 @@ def lib():
         L.flip_solve_pressure_noalloc.argtypes = [PP, vp, vp, vp, vp, C.POINTER(i32),
                                                   C.POINTER(C.c_double)]
         L.flip_energy.argtypes = [vp, C.c_double, C.POINTER(C.c_double)]
+        SP = C.POINTER(FlipSurfaceParams)
+        L.flip_surface_default_params.argtypes = [PP, SP]
+        L.flip_surface_default_params.restype = None
+        L.flip_surface_create.argtypes = [SP, vp, C.POINTER(vp)]
+        L.flip_surface_sdf.argtypes = [vp, vp]
+        L.flip_surface_set_field.argtypes = [vp, vp, i32]
+        L.flip_surface_mesh.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
+        L.flip_surface_bytes.argtypes = [vp, C.c_int]
+        L.flip_surface_bytes.restype = sz
+        L.flip_surface_read.argtypes = [vp, C.c_int, vp, sz, i32]
+        L.flip_surface_destroy.argtypes = [vp]
+        L.flip_surface_destroy.restype = None
+        L.flip_surface_case_table.argtypes = [vp, vp]
         if L.flip_abi_version() != 3:
             raise RuntimeError("libflip_gb300 ABI version mismatch")
         _lib = L
@@ -440,6 +462,73 @@ class Server:
         if getattr(self, "s", None):
             lib().flip_server_destroy(self.s)
             self.s = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def surface_default_params(params: FlipParams) -> FlipSurfaceParams:
+    sp = FlipSurfaceParams()
+    lib().flip_surface_default_params(C.byref(params), C.byref(sp))
+    return sp
+
+
+def surface_case_table():
+    """(ntri[256], tri[256, 12, 3]) local-edge triangles of the library's case table."""
+    ntri = np.zeros(256, np.uint8)
+    tri = np.zeros((256, SURF_MAX_TRI, 3), np.uint8)
+    _check(lib().flip_surface_case_table(ntri.ctypes.data, tri.ctypes.data))
+    return ntri, tri
+
+
+class Surface:
+    """Surface reconstruction (Sec. 3.3) on a sampling grid: scalar field, marching
+    cubes, vertex normals.  Owns a flip_surface object."""
+
+    def __init__(self, sp: FlipSurfaceParams, stream=None):
+        self.params = sp
+        self.n = tuple(int(sp.n[a]) for a in range(3))
+        out = C.c_void_p()
+        _check(lib().flip_surface_create(C.byref(sp), stream, C.byref(out)))
+        self.h = out
+        self.nv = self.nt = 0
+
+    def sdf(self, sim):
+        _check(lib().flip_surface_sdf(self.h, sim.h if hasattr(sim, "h") else sim))
+
+    def set_field(self, phi):
+        a = np.ascontiguousarray(phi, dtype=np.float32)
+        assert a.size == (self.n[0] + 1) * (self.n[1] + 1) * (self.n[2] + 1)
+        _check(lib().flip_surface_set_field(self.h, a.ctypes.data, 0))
+
+    def mesh(self):
+        nv, nt = C.c_int64(0), C.c_int64(0)
+        _check(lib().flip_surface_mesh(self.h, C.byref(nv), C.byref(nt)))
+        self.nv, self.nt = nv.value, nt.value
+        return self.nv, self.nt
+
+    def read(self, which: int):
+        shapes = {SURF_FIELD: ((self.n[2] + 1, self.n[1] + 1, self.n[0] + 1), np.float32),
+                  SURF_VERTICES: ((self.nv, 3), np.float32), SURF_NORMALS: ((self.nv, 3), np.float32),
+                  SURF_TRIANGLES: ((self.nt, 3), np.int32), SURF_VERTEX_EDGE: ((self.nv,), np.int64)}
+        shape, dt = shapes[which]
+        out = np.empty(shape, dt)
+        _check(lib().flip_surface_read(self.h, which, out.ctypes.data, out.nbytes, 0))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().flip_surface_destroy(self.h)
+            self.h = None
 
     def __enter__(self):
         return self

@@ -204,3 +204,32 @@ def batch_scenes(count: int, edges=(32, 48, 64, 80, 96), frac_range=(0.2, 0.5),
         side = float(np.sqrt(f))
         out.append(dam_break(n, side, side, density, seed + s))
     return out
+
+
+def corner_field_sphere(n, h: float, centre, radius: float, noise: float = 0.0,
+                        seed: int = 0) -> np.ndarray:
+    """Float32 corner field (shape (nz+1, ny+1, nx+1)) of a sphere's distance function
+    |x - centre| - radius sampled at h*(i,j,k), plus uniform noise in [-noise, noise)
+    from the counter-based generator (a meshing input, not a simulation)."""
+    if np.isscalar(n):
+        n = (n, n, n)
+    g = [np.arange(n[a] + 1) * h for a in range(3)]
+    Z, Y, X = np.meshgrid(g[2], g[1], g[0], indexing="ij")
+    phi = np.sqrt((X - centre[0]) ** 2 + (Y - centre[1]) ** 2 + (Z - centre[2]) ** 2) - radius
+    if noise:
+        c = np.arange(phi.size, dtype=np.int64)
+        phi = phi + ((uniform01(c, seed + 31337) * 2.0 - 1.0) * noise).reshape(phi.shape)
+    return phi.astype(np.float32)
+
+
+def corner_field_random(n, seed: int, bias: float = 0.0, closed: bool = True) -> np.ndarray:
+    """Float32 corner field of i.i.d. uniform values in [-1 + bias, 1 + bias); with
+    ``closed`` the corners on the box boundary are set to 1 (outside)."""
+    if np.isscalar(n):
+        n = (n, n, n)
+    shape = (n[2] + 1, n[1] + 1, n[0] + 1)
+    c = np.arange(int(np.prod(shape)), dtype=np.int64)
+    phi = (uniform01(c, seed + 271828) * 2.0 - 1.0 + bias).reshape(shape)
+    if closed:
+        phi[0], phi[-1], phi[:, 0], phi[:, -1], phi[:, :, 0], phi[:, :, -1] = (1.0,) * 6
+    return phi.astype(np.float32)

@@ -56,6 +56,16 @@ def test_struct_layouts_match_header(F):
     # flip_params: 3 int32 + 10 double + 6 int32, natural alignment
     assert ctypes.sizeof(F.FlipParams) == 12 + 4 + 10 * 8 + 28 + 4  # int tail padded to 8
     assert ctypes.sizeof(F.FlipStats) == 5 * 8 + 2 * 4 + 9 * 8
+    # flip_surface_params: 3 int32 (+4 padding) + 7 double
+    assert ctypes.sizeof(F.FlipSurfaceParams) == 12 + 4 + 7 * 8
+
+
+def test_surface_default_params(F):
+    p = F.default_params(40, 24, 32)
+    sp = F.surface_default_params(p)
+    assert list(sp.n) == [40, 24, 32] and list(sp.origin) == [0.0, 0.0, 0.0]
+    assert sp.h == p.dx and sp.radius == 0.5 * p.dx and sp.search_radius == 2 * p.dx
+    assert sp.iso == 0.0
 
 
 def test_default_params(F):
