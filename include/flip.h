@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define FLIP_ABI_VERSION 3
+#define FLIP_ABI_VERSION 4
 
 /* ------------------------------------------------------------ status codes */
 enum {
@@ -107,12 +107,19 @@ typedef struct {
                             rule ||r|| <= tol*||b|| is unchanged, so the result is the
                             same solution to the same tolerance, usually in fewer
                             iterations.  Not in the paper (a standard device). */
+  double cfl;            /* CFL number alpha of Sec. 3.1.4 (the paper takes 3).  0:
+                            every step takes dt.  > 0: step n takes
+                            dt_n = min(dt, alpha * dx / v_max), v_max the largest
+                            particle speed at the start of the step (dt when all
+                            particles rest); the pressure solve then runs on
+                            q = dt_n p / (rho dx^2), and reads give p. */
 } flip_params;
 
 /* Fills p with the defaults of the 32^3 dam break: dx = 1/n, dt = 1/240,
  * g = (0, -9.81, 0), rho = 1, r = 0.95, skin = 1e-3*dx, cg_tol = 1e-6,
  * ir_tol = 1e-8, cg_max_iter = 20*max(n), ir_max_iter = 100, FP32, particle
- * advection, multigrid preconditioner with 2 sweep pairs, no warm start. */
+ * advection, multigrid preconditioner with 2 sweep pairs, no warm start,
+ * fixed time step (cfl = 0). */
 void flip_default_params(flip_params* p, int32_t nx, int32_t ny, int32_t nz);
 
 /* Optional allocator: when given to flip_create, every device allocation of
@@ -140,6 +147,7 @@ typedef struct {
                                  fluid cells, FP64 from the stored fields */
   double max_speed;           /* last step: max particle speed after the blend */
   double ms_bin, ms_p2g, ms_divergence, ms_pcg, ms_g2p, ms_total;
+  double dt_last;             /* time step of the last step (dt, or the adaptive one) */
 } flip_stats;
 
 typedef struct flip_handle flip_handle;

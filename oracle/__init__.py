@@ -21,12 +21,12 @@ class OracleParams(C.Structure):
                 ("gravity", C.c_double * 3), ("rho", C.c_double), ("flip_ratio", C.c_double),
                 ("skin", C.c_double), ("cg_tol", C.c_double), ("cg_max_iter", C.c_int32),
                 ("advect_source", C.c_int32), ("preconditioner", C.c_int32), ("mg_nu", C.c_int32),
-                ("mg_omega", C.c_double)]
+                ("mg_omega", C.c_double), ("cfl", C.c_double)]
 
 
 class OracleStats(C.Structure):
     _fields_ = [("cg_iterations", C.c_int32), ("cg_rel_residual", C.c_double),
-                ("rel_divergence", C.c_double), ("n_fluid", C.c_int64)]
+                ("rel_divergence", C.c_double), ("n_fluid", C.c_int64), ("dt", C.c_double)]
 
 
 class OracleFields(C.Structure):
@@ -106,6 +106,7 @@ class Params:
     preconditioner: int = 1    # 0 Jacobi, 1 multigrid V-cycle
     mg_nu: int = 2
     mg_omega: float = 2.0
+    cfl: float = 0.0           # Sec. 3.1.4 CFL number; 0: fixed dt
 
     def c(self) -> OracleParams:
         p = OracleParams()
@@ -121,6 +122,7 @@ class Params:
         p.preconditioner = int(self.preconditioner)
         p.mg_nu = int(self.mg_nu)
         p.mg_omega = float(self.mg_omega)
+        p.cfl = float(self.cfl)
         return p
 
 
@@ -153,6 +155,7 @@ class StepResult:
     cg_rel_residual: float = 0.0
     rel_divergence: float = 0.0
     n_fluid: int = 0
+    dt: float = 0.0
 
 
 def step(params: Params, x, y, z, u, v, w, fields: bool = True) -> StepResult:
@@ -184,6 +187,7 @@ def step(params: Params, x, y, z, u, v, w, fields: bool = True) -> StepResult:
     res.cg_rel_residual = S.cg_rel_residual
     res.rel_divergence = S.rel_divergence
     res.n_fluid = S.n_fluid
+    res.dt = S.dt
     return res
 
 

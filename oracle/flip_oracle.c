@@ -392,8 +392,37 @@ double oracle_div_norm(const oracle_params* P, const double* const u[3], const u
  * grid, per the force-advect-project splitting of Section 2.1.3):
  *   bin -> P2G -> cell types -> gravity + walls -> b = -div u* -> PCG ->
  *   Eq. 5 projection -> G2P blend -> forward Euler + clamp. */
+static int step_with_dt(const oracle_params* P, int64_t np, double* x, double* y, double* z,
+                        double* u, double* v, double* w, oracle_fields* out,
+                        oracle_stats* stats);
+
+/* Sec. 3.1.4: with a CFL number alpha > 0 the step takes
+ * dt = min(dt_max, alpha dx / max_p |v_p|) from the particle velocities at its
+ * start (dt_max when every particle rests). */
+double oracle_cfl_dt(const oracle_params* P, int64_t np, const double* u, const double* v,
+                     const double* w) {
+  if (!(P->cfl > 0.0)) return P->dt;
+  double vmax = 0.0;
+  for (int64_t q = 0; q < np; ++q) {
+    const double s = sqrt(u[q] * u[q] + v[q] * v[q] + w[q] * w[q]);
+    if (s > vmax) vmax = s;
+  }
+  if (vmax <= 0.0) return P->dt;
+  const double dt = P->cfl * P->dx / vmax;
+  return dt < P->dt ? dt : P->dt;
+}
+
 int oracle_step(const oracle_params* P, int64_t np, double* x, double* y, double* z, double* u,
                 double* v, double* w, oracle_fields* out, oracle_stats* stats) {
+  oracle_params Q = *P;
+  Q.dt = oracle_cfl_dt(P, np, u, v, w);
+  if (stats) stats->dt = Q.dt;
+  return step_with_dt(&Q, np, x, y, z, u, v, w, out, stats);
+}
+
+static int step_with_dt(const oracle_params* P, int64_t np, double* x, double* y, double* z,
+                        double* u, double* v, double* w, oracle_fields* out,
+                        oracle_stats* stats) {
   const int64_t nc = oracle_n_cells(P);
   int64_t* start = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nc + 1));
   int64_t* order = (int64_t*)malloc(sizeof(int64_t) * (size_t)(np > 0 ? np : 1));

@@ -43,6 +43,7 @@ typedef struct {
   int32_t preconditioner; /* 0: Jacobi (oracle_pcg); 1: multigrid V-cycle (oracle_pcg_mg) */
   int32_t mg_nu;          /* multigrid: red-black sweep pairs before and after the correction */
   double mg_omega;        /* multigrid: over-correction of the coarse correction */
+  double cfl;             /* Sec. 3.1.4 CFL number; 0: fixed dt */
 } oracle_params;
 
 typedef struct {
@@ -50,6 +51,7 @@ typedef struct {
   double cg_rel_residual;  /* recursive ||r||/||b|| at exit */
   double rel_divergence;   /* ||div u_new||_2 / ||div u*||_2 over fluid cells */
   int64_t n_fluid;         /* fluid cells this step */
+  double dt;               /* time step taken */
 } oracle_stats;
 
 /* Optional outputs of oracle_step; any pointer may be NULL. */
@@ -167,6 +169,10 @@ int64_t oracle_mc_count(const int32_t n[3], const double* phi, double iso, int64
 /* The mesh: vert[3 nv], vedge[nv] (3 * corner + axis), tri[3 nt], nrm[3 nv]. */
 void oracle_mc(const int32_t n[3], const double origin[3], double h, const double* phi,
                double iso, double* vert, int64_t* vedge, int32_t* tri, double* nrm);
+
+/* Sec. 3.1.4: the step's dt for a CFL number P->cfl (P->dt when cfl is 0). */
+double oracle_cfl_dt(const oracle_params* P, int64_t np, const double* u, const double* v,
+                     const double* w);
 
 int oracle_num_threads(void);
 

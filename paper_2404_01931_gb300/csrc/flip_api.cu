@@ -177,6 +177,8 @@ int check_params(const flip_params* p, bool need_particles_prm) {
       return fail(FLIP_E_ARG, "mg_smooth must be in [1, 8]");
     if (p->warm_start != 0 && p->warm_start != 1)
       return fail(FLIP_E_ARG, "warm_start must be 0 or 1");
+    if (!(p->cfl >= 0.0) || !std::isfinite(p->cfl))
+      return fail(FLIP_E_ARG, "cfl must be finite and >= 0");
     if (!(p->flip_ratio >= 0.0 && p->flip_ratio <= 1.0))
       return fail(FLIP_E_ARG, "flip_ratio must be in [0, 1]");
     if (!(p->skin > 0.0 && p->skin < p->dx)) return fail(FLIP_E_ARG, "skin must be in (0, dx)");
@@ -222,11 +224,22 @@ Grid make_grid(const flip_params& p) {
   return g;
 }
 
+// The parameters the pressure solve and Eq. 5 see.  With an adaptive time step
+// (cfl > 0) they run on q = dt p / (rho dx^2), which is what a solve with
+// dt = rho dx^2 produces: L q = b and u_new = u* - dx (q+ - q-), free of the
+// step's dt.  The pressure is p = q rho dx^2 / dt when it is read.
+flip_params solver_params(const flip_params& p) {
+  flip_params q = p;
+  if (p.cfl > 0.0) q.dt = p.rho * p.dx * p.dx;
+  return q;
+}
+
 StepConsts make_consts(const flip_params& p) {
   StepConsts k{};
+  const flip_params q = solver_params(p);
   for (int a = 0; a < 3; ++a) k.gdt[a] = (float)(p.gravity[a] * p.dt);
-  k.pscale = (float)(p.dt / (p.rho * p.dx));
-  k.pscale64 = p.dt / (p.rho * p.dx);
+  k.pscale = (float)(q.dt / (q.rho * q.dx));
+  k.pscale64 = q.dt / (q.rho * q.dx);
   k.flip_ratio = (float)p.flip_ratio;
   k.advect_grid = p.advect_source == FLIP_ADVECT_GRID;
   k.dt = (float)p.dt;
@@ -378,7 +391,8 @@ int upload(void* dst, const void* src, size_t bytes, int src_dev, cudaStream_t s
 int rebin(flip_handle* h) {
   FLIP_CUDA(cudaMemsetAsync(h->B.cell_count, 0, sizeof(unsigned int) * (size_t)h->nkeys,
                             h->stream));
-  launch_rebin(h->g, h->P[h->cur], h->B, h->np, h->stream);
+  FLIP_CUDA(cudaMemsetAsync(&h->dstats->max_speed_bits, 0, sizeof(unsigned int), h->stream));
+  launch_rebin(h->g, h->P[h->cur], h->B, h->np, &h->dstats->max_speed_bits, h->stream);
   FLIP_CUDA(cudaGetLastError());
   return FLIP_OK;
 }
@@ -386,7 +400,7 @@ int rebin(flip_handle* h) {
 PcgArgs pcg_args(flip_handle* h) {
   PcgArgs a{};
   a.g = h->g;
-  fill_pcg_tables(a, h->prm);
+  fill_pcg_tables(a, solver_params(h->prm));
   a.type = h->type;
   a.active = h->B.active;
   a.n_active = &h->dstats->n_active;
@@ -417,6 +431,27 @@ PcgArgs pcg_args(flip_handle* h) {
     a.mg.lv[0].t = h->type;
   }
   return a;
+}
+
+// Adaptive time step (Sec. 3.1.4): the step's dt from the particles' largest
+// speed, before anything of the step uses it.
+void launch_step_dt(flip_handle* h) {
+  if (h->prm.cfl <= 0.0) return;
+  launch_cfl_dt(h->dstats, h->prm.gravity, h->prm.dt, h->prm.cfl * h->prm.dx, h->stream);
+  h->launches += 1;
+}
+
+// Pressure units of the stored solution: 1, or rho dx^2 / dt of the last step
+// when the solve runs on q (adaptive time step).  Synchronises the stream.
+int pressure_factor(flip_handle* h, double* f) {
+  *f = 1.0;
+  if (h->prm.cfl <= 0.0) return FLIP_OK;
+  double dt = 0.0;
+  FLIP_CUDA(cudaMemcpyAsync(&dt, &h->dstats->dt_cur, sizeof(double), cudaMemcpyDeviceToHost,
+                            h->stream));
+  FLIP_CUDA(cudaStreamSynchronize(h->stream));
+  if (dt > 0.0) *f = h->prm.rho * h->prm.dx * h->prm.dx / dt;
+  return FLIP_OK;
 }
 
 int status_to_code(int st) {
@@ -486,7 +521,7 @@ int flip_create(const flip_params* params, const float* x, const float* y, const
   if (params->preconditioner == FLIP_PRECOND_MG) {
     e = pcg_mg_check_occupancy();
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "multigrid kernel occupancy"));
-    setup_mg(h->mg, h->mg_dims, *params);
+    setup_mg(h->mg, h->mg_dims, solver_params(*params));
   }
   h->p2g_blocks = h->sm_count * 4;
   h->g2p_blocks = g2p_blocks(h->sm_count);
@@ -507,6 +542,7 @@ int flip_create(const flip_params* params, const float* x, const float* y, const
   Carver assign;
   assign.base = (char*)h->arena;
   carve(h, assign);
+  h->K.dyn = params->cfl > 0.0 ? h->dstats->dyn : nullptr;
   e = cudaMallocHost((void**)&h->hstats, sizeof(DevStats));
   if (e != cudaSuccess) {
     h->hstats = nullptr;
@@ -569,6 +605,7 @@ int flip_step(flip_handle* h, int32_t nsteps, flip_stats* stats) {
   int rc = FLIP_OK;
   for (int st = 0; st < nsteps; ++st) {
     if (timed) FLIP_CUDA(cudaEventRecord(ev[0], s));
+    launch_step_dt(h);
     launch_bin(h->g, h->B, h->type, h->dstats, s);
     launch_scatter(h->P[h->cur], h->P[1 - h->cur], h->B, h->np, s);
     h->cur = 1 - h->cur;
@@ -628,6 +665,7 @@ int flip_step(flip_handle* h, int32_t nsteps, flip_stats* stats) {
     float ms_f;
     std::memcpy(&ms_f, &d.max_speed_bits, sizeof(float));
     stats->max_speed = ms_f;
+    stats->dt_last = h->prm.cfl > 0.0 ? d.dt_cur : h->prm.dt;
     stats->ms_bin = ms[0];
     stats->ms_p2g = ms[1];
     stats->ms_divergence = ms[2];
@@ -732,22 +770,38 @@ int flip_read(flip_handle* h, flip_field which, void* dst, size_t bytes, int32_t
       src = h->tmp;
       break;
     }
-    case FLIP_FIELD_PRESSURE:
+    case FLIP_FIELD_PRESSURE: {
+      double f = 1.0;
+      if (int rc = pressure_factor(h, &f)) return rc;
       if (h->mixed) {
         launch_f64_to_f32(h->x64, (float*)h->tmp, h->ncells, s);
+        src = h->tmp;
+      } else if (f != 1.0) {
+        FLIP_CUDA(cudaMemcpyAsync(h->tmp, h->x32, sizeof(float) * h->ncells,
+                                  cudaMemcpyDeviceToDevice, s));
         src = h->tmp;
       } else {
         src = h->x32;
       }
+      if (f != 1.0) launch_scale((float*)h->tmp, h->ncells, f, s);
       break;
-    case FLIP_FIELD_PRESSURE_F64:
-      if (h->mixed) {
+    }
+    case FLIP_FIELD_PRESSURE_F64: {
+      double f = 1.0;
+      if (int rc = pressure_factor(h, &f)) return rc;
+      if (h->mixed && f == 1.0) {
         src = h->x64;
       } else {
-        launch_f32_to_f64(h->x32, (double*)h->tmp, h->ncells, s);
+        if (h->mixed)
+          FLIP_CUDA(cudaMemcpyAsync(h->tmp, h->x64, sizeof(double) * h->ncells,
+                                    cudaMemcpyDeviceToDevice, s));
+        else
+          launch_f32_to_f64(h->x32, (double*)h->tmp, h->ncells, s);
+        if (f != 1.0) launch_scale((double*)h->tmp, h->ncells, f, s);
         src = h->tmp;
       }
       break;
+    }
     case FLIP_FIELD_RHS:
       if (h->mixed) {
         launch_f64_to_f32(h->b64, (float*)h->tmp, h->ncells, s);
@@ -1034,6 +1088,7 @@ int flip_batch_step(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t ns
     for (int s = 0; s < n; ++s) {
       flip_handle* h = hs[s];
       const float* uo[3] = {h->uo[0], h->uo[1], h->uo[2]};
+      launch_step_dt(h);
       launch_bin(h->g, h->B, h->type, h->dstats, h->stream);
       launch_scatter(h->P[h->cur], h->P[1 - h->cur], h->B, h->np, h->stream);
       h->cur = 1 - h->cur;
@@ -1113,6 +1168,7 @@ int flip_batch_step(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t ns
     float msf;
     std::memcpy(&msf, &d.max_speed_bits, sizeof(float));
     o->max_speed = msf;
+    o->dt_last = h->prm.cfl > 0.0 ? d.dt_cur : h->prm.dt;
     o->ms_pcg = ms_pcg;
     o->ms_total = ms_total;
   }

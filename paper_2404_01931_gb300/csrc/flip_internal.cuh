@@ -38,6 +38,9 @@ struct DevStats {
   long long ir_iters_mark;    // that asked for statistics (copied on the stream)
   double rel_res;             // last solve's stopping residual ||r||/||b||
   double bnorm;               // last solve's ||b||
+  double dt_cur;              // adaptive time step: dt of the current / last step
+  float dyn[4];               // adaptive time step: g * dt (3 components) and dt,
+                              // rounded to float, for the step's kernels
 };
 
 struct Grid {

@@ -33,7 +33,24 @@ struct StepConsts {
   float flip_ratio;
   int advect_grid;   // 1: advect with the grid velocity
   float dt;
+  const float* dyn;  // adaptive time step (Sec. 3.1.4): device words {g*dt, dt}
+                     // written by the step's first kernel, which replace gdt and
+                     // dt; nullptr for a fixed step.  The solve then runs on the
+                     // dt-free unknown q = dt p / (rho dx^2) (pscale = dx).
 };
+
+// The step constants a kernel uses: the host values, with g*dt and dt taken
+// from device memory when the time step is adaptive.
+__device__ __forceinline__ StepConsts step_consts(const StepConsts& K) {
+  StepConsts k = K;
+  if (K.dyn) {
+    k.gdt[0] = K.dyn[0];
+    k.gdt[1] = K.dyn[1];
+    k.gdt[2] = K.dyn[2];
+    k.dt = K.dyn[3];
+  }
+  return k;
+}
 
 constexpr int PCG_SLOTS = 7;
 
@@ -172,7 +189,10 @@ __device__ __forceinline__ float face_unew(const Grid& g, const StepConsts& k, f
 }
 
 // k_bin.cu
+// Histogram and ranks of the particles' cells; also the largest particle speed
+// (atomic max into *st_speed, float bits, which the caller clears).
 void launch_rebin(const Grid& g, const PartView& p, const BinView& b, long long np,
+                  unsigned int* st_speed,
                   cudaStream_t s);
 void launch_bin(const Grid& g, const BinView& b, uint8_t* type, DevStats* st, cudaStream_t s);
 void launch_scatter(const PartView& src, const PartView& dst, const BinView& b, long long np,
@@ -220,6 +240,13 @@ void launch_g2p(const Grid& g, const StepConsts& k, const PartView& p, const Bin
                 long long np, int nblocks, cudaStream_t s);
 
 // k_diag.cu
+// Adaptive time step (Sec. 3.1.4): dt = min(dt_max, alpha dx / v_max), v_max the
+// largest particle speed (DevStats::max_speed_bits); writes st->dt_cur and st->dyn.
+void launch_cfl_dt(DevStats* st, const double g[3], double dt_max, double alpha_dx,
+                   cudaStream_t s);
+// out[i] *= f for i < n (device arrays).
+void launch_scale(float* out, long long n, double f, cudaStream_t s);
+void launch_scale(double* out, long long n, double f, cudaStream_t s);
 // Sums over the particles (FP64): out[0] = sum |v|^2, out[1..3] = sum x, y, z.
 // partials holds 4 * nblocks doubles.
 int energy_blocks(int sm_count);

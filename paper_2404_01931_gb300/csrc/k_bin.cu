@@ -19,15 +19,24 @@
 
 namespace flipk {
 
-__global__ void k_rebin(const Grid g, const PartView p, const BinView b, long long np) {
+__global__ void k_rebin(const Grid g, const PartView p, const BinView b, long long np,
+                        unsigned int* __restrict__ st_speed) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= np) return;
-  const int ci = cell_of(p.x[i], g.inv_dx, g.nx);
-  const int cj = cell_of(p.y[i], g.inv_dx, g.ny);
-  const int ck = cell_of(p.z[i], g.inv_dx, g.nz);
-  const unsigned int key = brick_key(g, ci, cj, ck);
-  b.key[i] = key;
-  b.rank[i] = atomicAdd(b.cell_count + key, 1u);
+  float s2 = 0.0f;
+  if (i < np) {
+    const int ci = cell_of(p.x[i], g.inv_dx, g.nx);
+    const int cj = cell_of(p.y[i], g.inv_dx, g.ny);
+    const int ck = cell_of(p.z[i], g.inv_dx, g.nz);
+    const unsigned int key = brick_key(g, ci, cj, ck);
+    b.key[i] = key;
+    b.rank[i] = atomicAdd(b.cell_count + key, 1u);
+    const float u = p.u[i], v = p.v[i], w = p.w[i];
+    s2 = u * u + v * v + w * w;
+  }
+  // the particles' largest speed: the first adaptive time step's input
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s2 = fmaxf(s2, __shfl_xor_sync(0xffffffffu, s2, o));
+  if ((threadIdx.x & 31) == 0 && s2 > 0.0f) atomicMax(st_speed, __float_as_uint(sqrtf(s2)));
 }
 
 // One warp per brick: lane l owns the 16 consecutive keys 16l .. 16l+15 (two
@@ -183,8 +192,9 @@ static unsigned int blocks_for(long long n, int t) {
 }
 
 void launch_rebin(const Grid& g, const PartView& p, const BinView& b, long long np,
+                  unsigned int* st_speed,
                   cudaStream_t s) {
-  if (np > 0) k_rebin<<<blocks_for(np, 256), 256, 0, s>>>(g, p, b, np);
+  if (np > 0) k_rebin<<<blocks_for(np, 256), 256, 0, s>>>(g, p, b, np, st_speed);
 }
 
 void launch_bin(const Grid& g, const BinView& b, uint8_t* type, DevStats* st, cudaStream_t s) {

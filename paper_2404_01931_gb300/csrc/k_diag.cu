@@ -10,6 +10,8 @@
 // particles' terms up to ~2^-48 relative, without FP64 arithmetic per particle.
 // The pairs are then summed in FP64, per CTA and then over CTAs in a fixed
 // order.  Particles are read as 16-byte vectors: 24 bytes per particle, one pass.
+#include <algorithm>
+
 #include "flip_kernels.cuh"
 
 namespace flipk {
@@ -62,6 +64,38 @@ __global__ void k_energy_final(const double* __restrict__ partials, int nblocks,
   double s = 0.0;
   for (int b = 0; b < nblocks; ++b) s += partials[(size_t)q * nblocks + b];
   out[q] = s;
+}
+
+__global__ void k_cfl_dt(DevStats* st, double g0, double g1, double g2, double dt_max,
+                         double alpha_dx) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const float vmax = __uint_as_float(st->max_speed_bits);
+  double dt = dt_max;
+  if (vmax > 0.0f) dt = fmin(dt_max, alpha_dx / (double)vmax);
+  st->dt_cur = dt;
+  st->dyn[0] = (float)(g0 * dt);
+  st->dyn[1] = (float)(g1 * dt);
+  st->dyn[2] = (float)(g2 * dt);
+  st->dyn[3] = (float)dt;
+}
+
+void launch_cfl_dt(DevStats* st, const double g[3], double dt_max, double alpha_dx,
+                   cudaStream_t s) {
+  k_cfl_dt<<<1, 32, 0, s>>>(st, g[0], g[1], g[2], dt_max, alpha_dx);
+}
+
+template <class T>
+__global__ void k_scale(T* out, long long n, double f) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = (T)((double)out[i] * f);
+}
+
+void launch_scale(float* out, long long n, double f, cudaStream_t s) {
+  if (n > 0) k_scale<float><<<(unsigned)std::min<long long>((n + 255) / 256, 65535), 256, 0, s>>>(out, n, f);
+}
+void launch_scale(double* out, long long n, double f, cudaStream_t s) {
+  if (n > 0) k_scale<double><<<(unsigned)std::min<long long>((n + 255) / 256, 65535), 256, 0, s>>>(out, n, f);
 }
 
 int energy_blocks(int sm_count) { return sm_count > 0 ? sm_count : 1; }

@@ -115,7 +115,7 @@ __device__ __forceinline__ void interp_tile(const Grid& g, float px, float py, f
 }
 
 template <bool PAIR>
-__global__ void __launch_bounds__(G2P_THREADS) k_g2p(const Grid g, const StepConsts K,
+__global__ void __launch_bounds__(G2P_THREADS) k_g2p(const Grid g, const StepConsts K0,
                                                      const PartView P, const BinView B,
                                                      const float* __restrict__ uo0,
                                                      const float* __restrict__ uo1,
@@ -123,6 +123,7 @@ __global__ void __launch_bounds__(G2P_THREADS) k_g2p(const Grid g, const StepCon
                                                      const float* __restrict__ p32,
                                                      const float2* __restrict__ pff,
                                                      DevStats* st) {
+  const StepConsts K = step_consts(K0);
   using PT = typename PTile<PAIR>::T;
   __shared__ PT sp[G2P_PTILE];
   __shared__ float su[3][G2P_TILE];

@@ -161,10 +161,11 @@ __global__ void k_finalize(const Grid g, float2* acc0, float2* acc1, float2* acc
 // Gravity + walls give u* on the fly; b = -div u* (Eq. 6) in fluid cells.
 // Also starts the solve from p = 0 (every cell, so air cells hold p = 0) and
 // resets the grid barrier and the per-step max-speed word.
-__global__ void k_divergence(const Grid g, const StepConsts K, const uint8_t* __restrict__ type,
+__global__ void k_divergence(const Grid g, const StepConsts K0, const uint8_t* __restrict__ type,
                              const float* __restrict__ uo0, const float* __restrict__ uo1,
                              const float* __restrict__ uo2, float* b32, double* b64, float* x32,
                              double* x64, float2* pff, unsigned int* bar, DevStats* st) {
+  const StepConsts K = step_consts(K0);
   const long long nc = (long long)g.nx * g.ny * g.nz;
   if (blockIdx.x == 0 && threadIdx.x < BAR_WORDS) {
     bar[threadIdx.x] = 0u;  // the grid barrier's arrival counter and spare words
@@ -204,9 +205,10 @@ __global__ void k_divergence(const Grid g, const StepConsts K, const uint8_t* __
 }
 
 template <int D, bool PAIR>
-__global__ void k_u_new(const Grid g, const StepConsts K, const float* __restrict__ uo,
+__global__ void k_u_new(const Grid g, const StepConsts K0, const float* __restrict__ uo,
                         const float* __restrict__ p32, const float2* __restrict__ pff,
                         float* __restrict__ out) {
+  const StepConsts K = step_consts(K0);
   const int FX = g.nx + (D == 0), FY = g.ny + (D == 1);
   const long long nf = n_faces(g, D);
   for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nf;
@@ -218,10 +220,11 @@ __global__ void k_u_new(const Grid g, const StepConsts K, const float* __restric
 
 // ||div u*||^2 and ||div u_new||^2 over fluid cells in FP64, u_new from the
 // stored pressure (FP32 or FP64) by Eq. 5 evaluated in FP64.
-__global__ void k_div_norms(const Grid g, const StepConsts K, const uint8_t* __restrict__ type,
+__global__ void k_div_norms(const Grid g, const StepConsts K0, const uint8_t* __restrict__ type,
                             const float* __restrict__ uo0, const float* __restrict__ uo1,
                             const float* __restrict__ uo2, const float* __restrict__ p32,
                             const double* __restrict__ p64, double* out2) {
+  const StepConsts K = step_consts(K0);
   const long long nc = (long long)g.nx * g.ny * g.nz;
   const double ps = K.pscale64;
   double s_star = 0.0, s_new = 0.0;

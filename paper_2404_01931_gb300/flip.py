@@ -58,7 +58,7 @@ class FlipParams(C.Structure):
                 ("cg_max_iter", C.c_int32), ("ir_max_iter", C.c_int32),
                 ("precision", C.c_int32), ("advect_source", C.c_int32),
                 ("preconditioner", C.c_int32), ("mg_smooth", C.c_int32),
-                ("warm_start", C.c_int32)]
+                ("warm_start", C.c_int32), ("cfl", C.c_double)]
 
 
 class FlipStats(C.Structure):
@@ -68,7 +68,7 @@ class FlipStats(C.Structure):
                 ("cg_rel_residual", C.c_double), ("rel_divergence", C.c_double),
                 ("max_speed", C.c_double), ("ms_bin", C.c_double), ("ms_p2g", C.c_double),
                 ("ms_divergence", C.c_double), ("ms_pcg", C.c_double), ("ms_g2p", C.c_double),
-                ("ms_total", C.c_double)]
+                ("ms_total", C.c_double), ("dt_last", C.c_double)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -164,7 +164,7 @@ def lib():
         L.flip_surface_destroy.argtypes = [vp]
         L.flip_surface_destroy.restype = None
         L.flip_surface_case_table.argtypes = [vp, vp]
-        if L.flip_abi_version() != 3:
+        if L.flip_abi_version() != 4:
             raise RuntimeError("libflip_gb300 ABI version mismatch")
         _lib = L
     return _lib
