@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define FLIP_ABI_VERSION 4
+#define FLIP_ABI_VERSION 5
 
 /* ------------------------------------------------------------ status codes */
 enum {
@@ -50,7 +50,10 @@ enum {
   FLIP_E_TIMEOUT = 5,        /* a device-side wait gave up; the step's results are
                                 not valid, the handle stays usable */
   FLIP_E_SIZE = 6,           /* a buffer size does not match the field */
-  FLIP_E_NOGPU = 7           /* no CUDA device, or not an sm_103 device */
+  FLIP_E_NOGPU = 7,          /* no CUDA device, or not an sm_103 device */
+  FLIP_E_CAPACITY = 8        /* warning: reseeding wanted more particles than
+                                max_particles holds; the step was committed with
+                                the particles that fit */
 };
 
 /* ------------------------------------------------------------ parameters */
@@ -113,6 +116,24 @@ typedef struct {
                             particle speed at the start of the step (dt when all
                             particles rest); the pressure solve then runs on
                             q = dt_n p / (rho dx^2), and reads give p. */
+  /* Reseeding (Sec. 3.1.2: a fluid cell should hold between three and twelve
+   * particles, and a cell that falls short is reseeded).  Off when both are 0.
+   *   ppc_min in [1, 64]: after every step, each cell holding 1..ppc_min-1
+   *     particles gets new ones up to ppc_min, placed uniformly in the cell by
+   *     SplitMix64 (reseed_seed, counter ((step * n_cells + cell) * 64 + slot) * 3
+   *     + axis; top 53 bits as a double in [0,1), x = (i + U) dx rounded to
+   *     float and clamped like the advection), with the projected grid
+   *     velocity interpolated at their position (Eq. 4 weights), and new ids
+   *     from the running count.  "step" counts this handle's steps from 0.
+   *   ppc_max (0 or >= max(ppc_min, 1)): at the start of every step, a cell
+   *     holding more particles keeps ppc_max of them (which ones is unspecified).
+   * The particle count then varies; it is bounded by max_particles. */
+  int32_t ppc_min;
+  int32_t ppc_max;
+  int64_t max_particles;   /* particle capacity, >= np (0: np without reseeding,
+                              else max(2 np, np + ppc_min * min(np, n_cells),
+                              1024)) */
+  uint64_t reseed_seed;
 } flip_params;
 
 /* Fills p with the defaults of the 32^3 dam break: dx = 1/n, dt = 1/240,
@@ -148,6 +169,8 @@ typedef struct {
   double max_speed;           /* last step: max particle speed after the blend */
   double ms_bin, ms_p2g, ms_divergence, ms_pcg, ms_g2p, ms_total;
   double dt_last;             /* time step of the last step (dt, or the adaptive one) */
+  int64_t particles_added;    /* reseeding: particles created by this call */
+  int64_t particles_removed;  /* reseeding: particles dropped by this call */
 } flip_stats;
 
 typedef struct flip_handle flip_handle;

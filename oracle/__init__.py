@@ -21,12 +21,14 @@ class OracleParams(C.Structure):
                 ("gravity", C.c_double * 3), ("rho", C.c_double), ("flip_ratio", C.c_double),
                 ("skin", C.c_double), ("cg_tol", C.c_double), ("cg_max_iter", C.c_int32),
                 ("advect_source", C.c_int32), ("preconditioner", C.c_int32), ("mg_nu", C.c_int32),
-                ("mg_omega", C.c_double), ("cfl", C.c_double)]
+                ("mg_omega", C.c_double), ("cfl", C.c_double), ("ppc_min", C.c_int32),
+                ("ppc_max", C.c_int32), ("reseed_seed", C.c_uint64), ("reseed_step", C.c_int64)]
 
 
 class OracleStats(C.Structure):
     _fields_ = [("cg_iterations", C.c_int32), ("cg_rel_residual", C.c_double),
-                ("rel_divergence", C.c_double), ("n_fluid", C.c_int64), ("dt", C.c_double)]
+                ("rel_divergence", C.c_double), ("n_fluid", C.c_int64), ("dt", C.c_double),
+                ("added", C.c_int64), ("removed", C.c_int64)]
 
 
 class OracleFields(C.Structure):
@@ -69,6 +71,9 @@ def lib():
         L.oracle_step.argtypes = [P, C.c_int64, vp, vp, vp, vp, vp, vp,
                                   C.POINTER(OracleFields), C.POINTER(OracleStats)]
         L.oracle_step.restype = C.c_int
+        L.oracle_step_ex.argtypes = [P, C.POINTER(C.c_int64), C.c_int64, vp, vp, vp, vp, vp, vp,
+                                     C.POINTER(OracleFields), C.POINTER(OracleStats)]
+        L.oracle_step_ex.restype = C.c_int
         L.oracle_num_threads.restype = C.c_int
         L.oracle_energy.argtypes = [C.c_int64, vp, vp, vp, vp, vp, vp, vp, C.c_double, vp]
         L.oracle_energy.restype = None
@@ -107,6 +112,9 @@ class Params:
     mg_nu: int = 2
     mg_omega: float = 2.0
     cfl: float = 0.0           # Sec. 3.1.4 CFL number; 0: fixed dt
+    ppc_min: int = 0           # Sec. 3.1.2 reseeding bounds (0: off)
+    ppc_max: int = 0
+    reseed_seed: int = 0
 
     def c(self) -> OracleParams:
         p = OracleParams()
@@ -123,6 +131,9 @@ class Params:
         p.mg_nu = int(self.mg_nu)
         p.mg_omega = float(self.mg_omega)
         p.cfl = float(self.cfl)
+        p.ppc_min = int(self.ppc_min)
+        p.ppc_max = int(self.ppc_max)
+        p.reseed_seed = int(self.reseed_seed)
         return p
 
 
@@ -156,14 +167,25 @@ class StepResult:
     rel_divergence: float = 0.0
     n_fluid: int = 0
     dt: float = 0.0
+    added: int = 0
+    removed: int = 0
 
 
-def step(params: Params, x, y, z, u, v, w, fields: bool = True) -> StepResult:
-    """One oracle step; particle arrays are copied to float64 and returned in the same order."""
+def step(params: Params, x, y, z, u, v, w, fields: bool = True, step_index: int = 0,
+         capacity: int | None = None) -> StepResult:
+    """One oracle step; particle arrays are copied to float64 and returned in the same
+    order (with reseeding: the survivors in order, then the new particles)."""
     L = lib()
     P = params.c()
-    arrs = [np.array(a, dtype=np.float64, copy=True) for a in (x, y, z, u, v, w)]
-    np_ = arrs[0].shape[0]
+    P.reseed_step = int(step_index)
+    reseed = params.ppc_min > 0 or params.ppc_max > 0
+    np_ = int(np.asarray(x).shape[0])
+    cap = np_ if not reseed else (capacity or np_ + params.ppc_min * int(np.prod(params.n)))
+    arrs = []
+    for a in (x, y, z, u, v, w):
+        buf = np.zeros(cap, dtype=np.float64)
+        buf[:np_] = a
+        arrs.append(buf)
     res = StepResult(*arrs)
     F = OracleFields()
     if fields:
@@ -181,13 +203,22 @@ def step(params: Params, x, y, z, u, v, w, fields: bool = True) -> StepResult:
         F.rhs = res.rhs.ctypes.data
         F.type = res.type.ctypes.data
     S = OracleStats()
-    res.status = L.oracle_step(C.byref(P), np_, *[_p(a) for a in arrs],
-                               C.byref(F) if fields else None, C.byref(S))
+    if reseed:
+        n_io = C.c_int64(np_)
+        res.status = L.oracle_step_ex(C.byref(P), C.byref(n_io), cap, *[_p(a) for a in arrs],
+                                      C.byref(F) if fields else None, C.byref(S))
+        for name, a in zip(("x", "y", "z", "u", "v", "w"), arrs):
+            setattr(res, name, a[:n_io.value].copy())
+    else:
+        res.status = L.oracle_step(C.byref(P), np_, *[_p(a) for a in arrs],
+                                   C.byref(F) if fields else None, C.byref(S))
     res.cg_iterations = S.cg_iterations
     res.cg_rel_residual = S.cg_rel_residual
     res.rel_divergence = S.rel_divergence
     res.n_fluid = S.n_fluid
     res.dt = S.dt
+    res.added = S.added
+    res.removed = S.removed
     return res
 
 

@@ -696,3 +696,113 @@ void oracle_energy(int64_t np, const double* x, const double* y, const double* z
   out[1] = pe;
   out[2] = ke + pe;
 }
+
+/* SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): output number `counter` of
+ * the stream that starts at seed * G. */
+static uint64_t splitmix64(uint64_t seed, uint64_t counter) {
+  const uint64_t G = 0x9E3779B97F4A7C15ull;
+  uint64_t z = seed * G + (counter + 1u) * G;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+/* coordinate of a new particle on axis ax of cell index i (see oracle_step_ex) */
+static double spawn_coordinate(const oracle_params* P, int ax, int64_t i, double U) {
+  float xf = (float)(((double)i + U) * P->dx);
+  int64_t cell[3];
+  for (;;) {
+    const double q[3] = {ax == 0 ? xf : 0.0, ax == 1 ? xf : 0.0, ax == 2 ? xf : 0.0};
+    oracle_cell_of(P, q[0], q[1], q[2], cell);
+    if (cell[ax] > i) xf = nextafterf(xf, 0.0f);
+    else if (cell[ax] < i) xf = nextafterf(xf, 3.0e38f);
+    else break;
+  }
+  const float lo = (float)P->skin, hi = (float)((double)P->n[ax] * P->dx - P->skin);
+  xf = fminf(fmaxf(xf, lo), hi);
+  return (double)xf;
+}
+
+int oracle_step_ex(const oracle_params* P, int64_t* np_io, int64_t capacity, double* x, double* y,
+                   double* z, double* u, double* v, double* w, oracle_fields* out,
+                   oracle_stats* stats) {
+  int64_t np = *np_io;
+  const int64_t nc = oracle_n_cells(P);
+  oracle_params Q = *P;
+  Q.dt = oracle_cfl_dt(P, np, u, v, w);
+  int64_t removed = 0, added = 0;
+  double* arr[6] = {x, y, z, u, v, w};
+  if (P->ppc_max > 0 && np > 0) {
+    int64_t* start = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nc + 1));
+    int64_t* order = (int64_t*)malloc(sizeof(int64_t) * (size_t)np);
+    char* keep = (char*)malloc((size_t)np);
+    oracle_bin(P, np, x, y, z, start, order);
+    for (int64_t c = 0; c < nc; ++c)
+      for (int64_t t = start[c]; t < start[c + 1]; ++t) keep[order[t]] = (t - start[c]) < P->ppc_max;
+    int64_t m = 0;
+    for (int64_t q = 0; q < np; ++q)
+      if (keep[q]) {
+        for (int a = 0; a < 6; ++a) arr[a][m] = arr[a][q];
+        ++m;
+      }
+    removed = np - m;
+    np = m;
+    free(start);
+    free(order);
+    free(keep);
+  }
+  /* the step, keeping u_new for the new particles' velocities */
+  oracle_fields F;
+  memset(&F, 0, sizeof(F));
+  if (out) F = *out;
+  double* un_own[3] = {NULL, NULL, NULL};
+  for (int d = 0; d < 3; ++d)
+    if (!F.u_new[d]) {
+      un_own[d] = (double*)malloc(sizeof(double) * (size_t)oracle_n_faces(P, d));
+      F.u_new[d] = un_own[d];
+    }
+  oracle_stats S;
+  memset(&S, 0, sizeof(S));
+  int status = step_with_dt(&Q, np, x, y, z, u, v, w, &F, &S);
+  if (status == 0 && P->ppc_min > 0) {
+    int64_t* start = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nc + 1));
+    int64_t* order = (int64_t*)malloc(sizeof(int64_t) * (size_t)(np > 0 ? np : 1));
+    oracle_bin(P, np, x, y, z, start, order);
+    const double* un[3] = {F.u_new[0], F.u_new[1], F.u_new[2]};
+    for (int64_t c = 0; c < nc && status == 0; ++c) {
+      const int64_t cnt = start[c + 1] - start[c];
+      if (cnt == 0 || cnt >= P->ppc_min) continue;
+      const int64_t ijk[3] = {c % P->n[0], (c / P->n[0]) % P->n[1], c / ((int64_t)P->n[0] * P->n[1])};
+      for (int64_t s = 0; s < P->ppc_min - cnt; ++s) {
+        if (np >= capacity) {
+          status = 4;
+          break;
+        }
+        const uint64_t ctr =
+            (((uint64_t)P->reseed_step * (uint64_t)nc + (uint64_t)c) * 64u + (uint64_t)(cnt + s)) * 3u;
+        double pos[3];
+        for (int a = 0; a < 3; ++a) {
+          const double U = (double)(splitmix64(P->reseed_seed, ctr + (uint64_t)a) >> 11) * 0x1.0p-53;
+          pos[a] = spawn_coordinate(P, a, ijk[a], U);
+        }
+        x[np] = pos[0];
+        y[np] = pos[1];
+        z[np] = pos[2];
+        u[np] = oracle_interp(P, 0, un[0], pos[0], pos[1], pos[2]);
+        v[np] = oracle_interp(P, 1, un[1], pos[0], pos[1], pos[2]);
+        w[np] = oracle_interp(P, 2, un[2], pos[0], pos[1], pos[2]);
+        ++np;
+        ++added;
+      }
+    }
+    free(start);
+    free(order);
+  }
+  for (int d = 0; d < 3; ++d) free(un_own[d]);
+  S.dt = Q.dt;
+  S.added = added;
+  S.removed = removed;
+  if (stats) *stats = S;
+  *np_io = np;
+  return status;
+}

@@ -44,6 +44,10 @@ typedef struct {
   int32_t mg_nu;          /* multigrid: red-black sweep pairs before and after the correction */
   double mg_omega;        /* multigrid: over-correction of the coarse correction */
   double cfl;             /* Sec. 3.1.4 CFL number; 0: fixed dt */
+  int32_t ppc_min;        /* Sec. 3.1.2 reseeding: refill cells below this (0: off) */
+  int32_t ppc_max;        /* cells above this lose the excess at the step start (0: off) */
+  uint64_t reseed_seed;   /* SplitMix64 seed of the new particles' positions */
+  int64_t reseed_step;    /* the step's index (part of the generator's counter) */
 } oracle_params;
 
 typedef struct {
@@ -52,6 +56,7 @@ typedef struct {
   double rel_divergence;   /* ||div u_new||_2 / ||div u*||_2 over fluid cells */
   int64_t n_fluid;         /* fluid cells this step */
   double dt;               /* time step taken */
+  int64_t added, removed;  /* reseeding: particles created / dropped */
 } oracle_stats;
 
 /* Optional outputs of oracle_step; any pointer may be NULL. */
@@ -173,6 +178,23 @@ void oracle_mc(const int32_t n[3], const double origin[3], double h, const doubl
 /* Sec. 3.1.4: the step's dt for a CFL number P->cfl (P->dt when cfl is 0). */
 double oracle_cfl_dt(const oracle_params* P, int64_t np, const double* u, const double* v,
                      const double* w);
+
+/* One step with reseeding (Sec. 3.1.2).  The arrays hold `capacity` entries
+ * and *np particles, updated in place:
+ *   1. (ppc_max > 0) a cell holding more than ppc_max particles at the step
+ *      start keeps the ppc_max of lowest index (the CFL dt is taken before this);
+ *   2. the step of oracle_step;
+ *   3. (ppc_min > 0) each cell holding 1..ppc_min-1 particles after the
+ *      advection gets ppc_min - c new ones, cells in x-fastest order, appended:
+ *      slot q = c + s, counter ((reseed_step * n_cells + cell) * 64 + q) * 3 +
+ *      axis into SplitMix64(reseed_seed), U = top 53 bits * 2^-53, coordinate
+ *      (i + U) dx rounded to float, moved by one float at a time back into the
+ *      cell, clamped to [skin, n dx - skin] in float; velocity = the projected
+ *      grid velocity interpolated there (oracle_interp of u_new).
+ * Returns oracle_step's codes, or 4 when capacity stopped the reseeding. */
+int oracle_step_ex(const oracle_params* P, int64_t* np, int64_t capacity, double* x, double* y,
+                   double* z, double* u, double* v, double* w, oracle_fields* out,
+                   oracle_stats* stats);
 
 int oracle_num_threads(void);
 

@@ -61,6 +61,8 @@ struct flip_handle {
   Grid g;
   StepConsts K;
   long long np = 0, ncells = 0, nkeys = 0, nf[3] = {0, 0, 0};
+  long long cap = 0;          // particle capacity (np, or more when reseeding)
+  long long steps_done = 0;   // steps taken (the reseeding generator's step index)
   unsigned int nbricks = 0;
   bool mixed = false;
   cudaStream_t stream = nullptr;
@@ -179,6 +181,11 @@ int check_params(const flip_params* p, bool need_particles_prm) {
       return fail(FLIP_E_ARG, "warm_start must be 0 or 1");
     if (!(p->cfl >= 0.0) || !std::isfinite(p->cfl))
       return fail(FLIP_E_ARG, "cfl must be finite and >= 0");
+    if (p->ppc_min < 0 || p->ppc_min > 64) return fail(FLIP_E_ARG, "ppc_min must be in [0, 64]");
+    if (p->ppc_max < 0 || (p->ppc_max > 0 && p->ppc_max < std::max(p->ppc_min, 1)))
+      return fail(FLIP_E_ARG, "ppc_max must be 0 or >= max(ppc_min, 1)");
+    if (p->max_particles < 0 || p->max_particles > 2147483647LL)
+      return fail(FLIP_E_ARG, "max_particles must be in [0, 2^31-1]");
     if (!(p->flip_ratio >= 0.0 && p->flip_ratio <= 1.0))
       return fail(FLIP_E_ARG, "flip_ratio must be in [0, 1]");
     if (!(p->skin > 0.0 && p->skin < p->dx)) return fail(FLIP_E_ARG, "skin must be in (0, dx)");
@@ -298,7 +305,7 @@ void fill_pcg_tables(PcgArgs& a, const flip_params& p) {
 
 // Lays out (or measures) every device buffer of a handle.
 void carve(flip_handle* h, Carver& cv) {
-  const size_t np = (size_t)h->np, nc = (size_t)h->ncells, nk = (size_t)h->nkeys,
+  const size_t np = (size_t)h->cap, nc = (size_t)h->ncells, nk = (size_t)h->nkeys,
                nb = h->nbricks;
   for (int b = 0; b < 2; ++b) {
     h->P[b].x = cv.take<float>(np);
@@ -388,7 +395,42 @@ int upload(void* dst, const void* src, size_t bytes, int src_dev, cudaStream_t s
   return FLIP_OK;
 }
 
+bool reseeding(const flip_handle* h) { return h->prm.ppc_min > 0 || h->prm.ppc_max > 0; }
+
+// Particle capacity: max_particles, or np without reseeding, or room for a full
+// refill of every occupied cell (np + ppc_min * min(np, cells)), at least 2 np.
+long long default_capacity(const flip_params& p, long long np) {
+  if (p.max_particles > 0) return std::max<long long>(p.max_particles, np);
+  if (p.ppc_min <= 0 && p.ppc_max <= 0) return np;
+  const long long cells = (long long)p.n[0] * p.n[1] * p.n[2];
+  const long long want = std::max<long long>(
+      {2 * np, np + (long long)p.ppc_min * std::min(np, cells), 1024LL});
+  return std::min<long long>(want, 2147483647LL);
+}
+
+unsigned int cell_cap(const flip_handle* h) {
+  return h->prm.ppc_max > 0 ? (unsigned int)h->prm.ppc_max : ~0u;
+}
+
+// The particle count: with reseeding it lives on the device (read back here,
+// synchronising the stream), otherwise it is np.
+int refresh_np(flip_handle* h) {
+  if (!reseeding(h)) return FLIP_OK;
+  long long v = 0;
+  FLIP_CUDA(cudaMemcpyAsync(&v, &h->dstats->np_buffer, sizeof(v), cudaMemcpyDeviceToHost,
+                            h->stream));
+  FLIP_CUDA(cudaStreamSynchronize(h->stream));
+  h->np = v;
+  return FLIP_OK;
+}
+
 int rebin(flip_handle* h) {
+  if (reseeding(h)) {  // the buffer holds h->np particles, all of them binned below
+    FLIP_CUDA(cudaMemcpyAsync(&h->dstats->np_layout, &h->np, sizeof(long long),
+                              cudaMemcpyHostToDevice, h->stream));
+    FLIP_CUDA(cudaMemcpyAsync(&h->dstats->np_buffer, &h->np, sizeof(long long),
+                              cudaMemcpyHostToDevice, h->stream));
+  }
   FLIP_CUDA(cudaMemsetAsync(h->B.cell_count, 0, sizeof(unsigned int) * (size_t)h->nkeys,
                             h->stream));
   FLIP_CUDA(cudaMemsetAsync(&h->dstats->max_speed_bits, 0, sizeof(unsigned int), h->stream));
@@ -454,7 +496,38 @@ int pressure_factor(flip_handle* h, double* f) {
   return FLIP_OK;
 }
 
+// The front of a step: adaptive dt, binning (with reseeding's upper bound) and
+// the counting-sort scatter into the other buffer.
+void launch_front(flip_handle* h, cudaStream_t s) {
+  launch_step_dt(h);
+  launch_bin(h->g, h->B, h->type, h->dstats, s, cell_cap(h));
+  if (reseeding(h))
+    launch_scatter(h->P[h->cur], h->P[1 - h->cur], h->B, h->cap, s, &h->dstats->np_buffer,
+                   cell_cap(h));
+  else
+    launch_scatter(h->P[h->cur], h->P[1 - h->cur], h->B, h->np, s);
+  h->cur = 1 - h->cur;
+  h->launches += 2 + (h->np > 0 || reseeding(h));
+}
+
+// Particles G2P walks (its launch is skipped for 0).
+long long g2p_count(const flip_handle* h) { return reseeding(h) ? h->cap : h->np; }
+
+// The back of a step, after G2P: reseeding's spawn into under-filled cells.
+void launch_back(flip_handle* h, cudaStream_t s) {
+  if (reseeding(h)) {
+    const float* uo[3] = {h->uo[0], h->uo[1], h->uo[2]};
+    ReseedArgs r{h->prm.ppc_min, h->prm.reseed_seed, h->steps_done, h->cap, h->prm.dx};
+    launch_spawn(h->g, h->K, h->P[h->cur], h->B, uo, h->mixed ? nullptr : h->x32, h->pff,
+                 h->dstats, r, h->nkeys, s);
+    h->launches += 1 + (h->prm.ppc_min > 0);
+  }
+  ++h->steps_done;
+}
+
 int status_to_code(int st) {
+  if (st & DEV_CAPACITY && !(st & (DEV_TIMEOUT | DEV_SINGULAR | DEV_NOT_CONVERGED)))
+    return fail(FLIP_E_CAPACITY, "reseeding reached max_particles; some new particles were skipped");
   if (st & DEV_TIMEOUT) return fail(FLIP_E_TIMEOUT, "a device-side wait in the PCG timed out");
   if (st & DEV_SINGULAR)
     return fail(FLIP_E_ARG, "every cell is fluid: the pressure system is singular");
@@ -468,6 +541,7 @@ int take_status(flip_handle* h) {
                             h->stream));
   FLIP_CUDA(cudaMemsetAsync(&h->dstats->status, 0, sizeof(int), h->stream));
   FLIP_CUDA(cudaStreamSynchronize(h->stream));
+  if (reseeding(h)) h->np = h->hstats->np_buffer;
   return status_to_code(h->hstats->status);
 }
 
@@ -484,6 +558,8 @@ int flip_create(const flip_params* params, const float* x, const float* y, const
   int rc = check_params(params, true);
   if (rc) return rc;
   if (np < 0 || np > 2147483647LL) return fail(FLIP_E_ARG, "np must be in [0, 2^31-1]");
+  if (params->max_particles > 0 && params->max_particles < np)
+    return fail(FLIP_E_ARG, "max_particles must be >= np");
   if (alloc && (!alloc->alloc || !alloc->free))
     return fail(FLIP_E_ARG, "flip_alloc needs both alloc and free");
   rc = check_device();
@@ -495,6 +571,7 @@ int flip_create(const flip_params* params, const float* x, const float* y, const
   h->g = make_grid(*params);
   h->K = make_consts(*params);
   h->np = np;
+  h->cap = default_capacity(*params, np);
   h->ncells = (long long)h->g.nx * h->g.ny * h->g.nz;
   h->nbricks = (unsigned)h->g.bx * h->g.by * h->g.bz;
   h->nkeys = (long long)h->nbricks * BRICK_CELLS;
@@ -559,6 +636,12 @@ int flip_create(const flip_params* params, const float* x, const float* y, const
     if (rc) return cleanup(rc);
   }
   launch_iota(h->P[0].id, np, h->stream);
+  {
+    long long next_id = np;  // pageable source: the copy is staged before the call returns
+    e = cudaMemcpyAsync(&h->dstats->next_id, &next_id, sizeof(next_id), cudaMemcpyHostToDevice,
+                        h->stream);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaMemcpyAsync(next_id)"));
+  }
   rc = rebin(h);
   if (rc) return cleanup(rc);
   e = cudaStreamSynchronize(h->stream);
@@ -599,6 +682,8 @@ int flip_step(flip_handle* h, int32_t nsteps, flip_stats* stats) {
     FLIP_CUDA(cudaEventRecord(t_begin, s));
     FLIP_CUDA(cudaMemcpyAsync(&h->dstats->cg_iters_mark, &h->dstats->cg_iters_total,
                               2 * sizeof(long long), cudaMemcpyDeviceToDevice, s));
+    FLIP_CUDA(cudaMemcpyAsync(&h->dstats->added_mark, &h->dstats->added_total,
+                              2 * sizeof(long long), cudaMemcpyDeviceToDevice, s));
   }
   const float* uo[3] = {h->uo[0], h->uo[1], h->uo[2]};
   PcgArgs pa = pcg_args(h);
@@ -606,10 +691,7 @@ int flip_step(flip_handle* h, int32_t nsteps, flip_stats* stats) {
   for (int st = 0; st < nsteps; ++st) {
     if (timed) FLIP_CUDA(cudaEventRecord(ev[0], s));
     launch_step_dt(h);
-    launch_bin(h->g, h->B, h->type, h->dstats, s);
-    launch_scatter(h->P[h->cur], h->P[1 - h->cur], h->B, h->np, s);
-    h->cur = 1 - h->cur;
-    h->launches += 2 + (h->np > 0);
+    launch_front(h, s);
     if (timed) FLIP_CUDA(cudaEventRecord(ev[1], s));
     launch_p2g(h->g, h->P[h->cur], h->B, h->acc, h->dstats, h->p2g_blocks, s);
     launch_finalize(h->g, h->acc, h->uo, s);
@@ -624,8 +706,9 @@ int flip_step(flip_handle* h, int32_t nsteps, flip_stats* stats) {
     h->launches += 1;
     if (timed) FLIP_CUDA(cudaEventRecord(ev[4], s));
     launch_g2p(h->g, h->K, h->P[h->cur], h->B, uo, h->mixed ? nullptr : h->x32, h->pff,
-               h->dstats, h->np, h->g2p_blocks, s);
-    h->launches += (h->np > 0);
+               h->dstats, g2p_count(h), h->g2p_blocks, s);
+    h->launches += (g2p_count(h) > 0);
+    launch_back(h, s);
     if (timed) FLIP_CUDA(cudaEventRecord(ev[5], s));
     FLIP_CUDA(cudaGetLastError());
     if (timed) {
@@ -655,6 +738,8 @@ int flip_step(flip_handle* h, int32_t nsteps, flip_stats* stats) {
     const DevStats& d = *h->hstats;
     stats->steps = nsteps;
     stats->n_particles = h->np;
+    stats->particles_added = d.added_total - d.added_mark;
+    stats->particles_removed = d.removed_total - d.removed_mark;
     stats->n_fluid_cells = d.n_fluid;
     stats->n_active_bricks = d.n_active;
     stats->cg_iterations = d.cg_iters_total - d.cg_iters_mark;
@@ -684,6 +769,7 @@ int flip_energy(flip_handle* h, double particle_mass, double out[3]) {
   if (!out) return fail(FLIP_E_ARG, "out is NULL");
   if (!(particle_mass >= 0.0) || !std::isfinite(particle_mass))
     return fail(FLIP_E_ARG, "particle_mass must be finite and >= 0");
+  if (int rc = refresh_np(h)) return rc;
   double sums[4] = {0.0, 0.0, 0.0, 0.0};
   if (h->np > 0) {
     const int nb = energy_blocks(h->sm_count);
@@ -708,6 +794,7 @@ size_t flip_footprint_bytes(const flip_params* params, int64_t np) {
   tmp.prm = *params;
   tmp.g = make_grid(*params);
   tmp.np = np;
+  tmp.cap = default_capacity(*params, np);
   tmp.ncells = (long long)tmp.g.nx * tmp.g.ny * tmp.g.nz;
   tmp.nbricks = (unsigned)tmp.g.bx * tmp.g.by * tmp.g.bz;
   tmp.nkeys = (long long)tmp.nbricks * BRICK_CELLS;
@@ -728,6 +815,7 @@ int flip_sync(flip_handle* h) {
 
 size_t flip_field_bytes(const flip_handle* h, flip_field which) {
   if (!h) return 0;
+  if (which <= FLIP_FIELD_PID && refresh_np(const_cast<flip_handle*>(h)) != FLIP_OK) return 0;
   switch (which) {
     case FLIP_FIELD_PX: case FLIP_FIELD_PY: case FLIP_FIELD_PZ:
     case FLIP_FIELD_PU: case FLIP_FIELD_PV: case FLIP_FIELD_PW:
@@ -851,6 +939,7 @@ int flip_write(flip_handle* h, flip_field which, const void* src, size_t bytes,
 int flip_read_particles(flip_handle* h, float* x, float* y, float* z, float* u, float* v,
                         float* w, int32_t* id, int32_t dst_is_device) {
   if (!h) return fail(FLIP_E_ARG, "handle is NULL");
+  if (int rc = refresh_np(h)) return rc;
   const PartView& P = h->P[h->cur];
   void* dst[7] = {x, y, z, u, v, w, id};
   const void* src[7] = {P.x, P.y, P.z, P.u, P.v, P.w, P.id};
@@ -872,6 +961,7 @@ int flip_read_particles(flip_handle* h, float* x, float* y, float* z, float* u, 
 int flip_write_particles(flip_handle* h, const float* x, const float* y, const float* z,
                          const float* u, const float* v, const float* w, int32_t src_is_device) {
   if (!h) return fail(FLIP_E_ARG, "handle is NULL");
+  if (int rc = refresh_np(h)) return rc;
   const PartView& P = h->P[h->cur];
   float* dst[6] = {P.x, P.y, P.z, P.u, P.v, P.w};
   const float* src[6] = {x, y, z, u, v, w};
@@ -1076,9 +1166,12 @@ int flip_batch_step(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t ns
   int batch_launches = 0;
   if (timed) {
     FLIP_CUDA(cudaEventRecord(b->ev_begin, bs));
-    for (int s = 0; s < n; ++s)
+    for (int s = 0; s < n; ++s) {
       FLIP_CUDA(cudaMemcpyAsync(&hs[s]->dstats->cg_iters_mark, &hs[s]->dstats->cg_iters_total,
                                 2 * sizeof(long long), cudaMemcpyDeviceToDevice, bs));
+      FLIP_CUDA(cudaMemcpyAsync(&hs[s]->dstats->added_mark, &hs[s]->dstats->added_total,
+                                2 * sizeof(long long), cudaMemcpyDeviceToDevice, bs));
+    }
   }
   // every scene stream starts after the call's uploads (and the begin event)
   FLIP_CUDA(cudaEventRecord(b->ev_solved, bs));
@@ -1088,15 +1181,12 @@ int flip_batch_step(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t ns
     for (int s = 0; s < n; ++s) {
       flip_handle* h = hs[s];
       const float* uo[3] = {h->uo[0], h->uo[1], h->uo[2]};
-      launch_step_dt(h);
-      launch_bin(h->g, h->B, h->type, h->dstats, h->stream);
-      launch_scatter(h->P[h->cur], h->P[1 - h->cur], h->B, h->np, h->stream);
-      h->cur = 1 - h->cur;
+      launch_front(h, h->stream);
       launch_p2g(h->g, h->P[h->cur], h->B, h->acc, h->dstats, h->p2g_blocks, h->stream);
       launch_finalize(h->g, h->acc, h->uo, h->stream);
       launch_divergence(h->g, h->K, h->type, uo, h->b32, h->b64, h->x32, h->x64, h->pff, h->bar,
                         h->dstats, h->stream);
-      h->launches += 5 + (h->np > 0);
+      h->launches += 3;
       FLIP_CUDA(cudaEventRecord(b->ev[s], h->stream));
       FLIP_CUDA(cudaStreamWaitEvent(bs, b->ev[s], 0));
     }
@@ -1116,8 +1206,9 @@ int flip_batch_step(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t ns
       const float* uo[3] = {h->uo[0], h->uo[1], h->uo[2]};
       FLIP_CUDA(cudaStreamWaitEvent(h->stream, b->ev_solved, 0));
       launch_g2p(h->g, h->K, h->P[h->cur], h->B, uo, h->mixed ? nullptr : h->x32, h->pff,
-                 h->dstats, h->np, h->g2p_blocks, h->stream);
-      h->launches += (h->np > 0);
+                 h->dstats, g2p_count(h), h->g2p_blocks, h->stream);
+      h->launches += (g2p_count(h) > 0);
+      launch_back(h, h->stream);
       h->stepped = true;
     }
     FLIP_CUDA(cudaGetLastError());
@@ -1158,6 +1249,8 @@ int flip_batch_step(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t ns
     const DevStats& d = *h->hstats;
     o->steps = nsteps;
     o->n_particles = h->np;
+    o->particles_added = d.added_total - d.added_mark;
+    o->particles_removed = d.removed_total - d.removed_mark;
     o->n_fluid_cells = d.n_fluid;
     o->n_active_bricks = d.n_active;
     o->cg_iterations = d.cg_iters_total - d.cg_iters_mark;
@@ -1265,7 +1358,7 @@ int flip_solve_pressure(const flip_params* params, const uint8_t* type, const fl
 namespace flipk {
 // The current particle buffer of a handle and its stream (for k_surface.cu).
 bool handle_particles(flip_handle* h, PartView* p, long long* np, cudaStream_t* s) {
-  if (!h) return false;
+  if (!h || refresh_np(h) != FLIP_OK) return false;
   *p = h->P[h->cur];
   *np = h->np;
   *s = h->stream;

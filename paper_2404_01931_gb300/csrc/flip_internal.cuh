@@ -23,7 +23,7 @@ constexpr int BRICK = 8;
 constexpr int BRICK_CELLS = 512;
 
 // Sticky device-side condition bits (DevStats::status).
-enum : int { DEV_TIMEOUT = 1, DEV_NOT_CONVERGED = 2, DEV_SINGULAR = 4 };
+enum : int { DEV_TIMEOUT = 1, DEV_NOT_CONVERGED = 2, DEV_SINGULAR = 4, DEV_CAPACITY = 8 };
 
 struct DevStats {
   int status;                 // DEV_* bits, cleared by the host when reported
@@ -41,6 +41,14 @@ struct DevStats {
   double dt_cur;              // adaptive time step: dt of the current / last step
   float dyn[4];               // adaptive time step: g * dt (3 components) and dt,
                               // rounded to float, for the step's kernels
+  // particle counts when reseeding makes them vary (otherwise np throughout)
+  long long np_layout;        // particles in the binned layout of the current step
+  long long np_buffer;        // particles in the current buffer: the layout plus
+                              // the ones the last spawn appended
+  unsigned long long spawn_req;  // spawn requests of the running step
+  long long next_id;          // id of the next created particle
+  long long added_total, removed_total;  // running sums
+  long long added_mark, removed_mark;    // the sums at the start of a stats call
 };
 
 struct Grid {

@@ -194,9 +194,14 @@ __device__ __forceinline__ float face_unew(const Grid& g, const StepConsts& k, f
 void launch_rebin(const Grid& g, const PartView& p, const BinView& b, long long np,
                   unsigned int* st_speed,
                   cudaStream_t s);
-void launch_bin(const Grid& g, const BinView& b, uint8_t* type, DevStats* st, cudaStream_t s);
+// cmax: reseeding's per-cell upper bound (~0u: none).
+void launch_bin(const Grid& g, const BinView& b, uint8_t* type, DevStats* st, cudaStream_t s,
+                unsigned int cmax = ~0u);
+// np: source particles (with np_dev non-null: at most np, bounded by *np_dev);
+// particles of rank >= rank_max in their cell are dropped.
 void launch_scatter(const PartView& src, const PartView& dst, const BinView& b, long long np,
-                    cudaStream_t s);
+                    cudaStream_t s, const long long* np_dev = nullptr,
+                    unsigned int rank_max = ~0u);
 void launch_iota(int* id, long long np, cudaStream_t s);
 
 // k_p2g.cu
@@ -232,6 +237,20 @@ void launch_compact_bricks(const Grid& g, const unsigned int* brick_fluid,
                            unsigned int* active, DevStats* st, cudaStream_t s);
 void launch_zero_off_fluid(const Grid& g, const uint8_t* type, float* p, unsigned int* bar,
                            cudaStream_t s);
+
+// k_reseed.cu (Sec. 3.1.2 reseeding)
+struct ReseedArgs {
+  int ppc_min;
+  unsigned long long seed;
+  long long step;          // the handle's step index
+  long long capacity;
+  double dx;               // cell edge in FP64 (the parameter, not 1/inv_dx)
+};
+// After G2P: cells holding 1..ppc_min-1 particles (the next step's histogram)
+// get new particles appended to p up to ppc_min, with their keys and ranks.
+void launch_spawn(const Grid& g, const StepConsts& k, const PartView& p, const BinView& b,
+                  const float* const uo[3], const float* p32, const float2* pff, DevStats* st,
+                  const ReseedArgs& r, long long nkeys, cudaStream_t s);
 
 // k_g2p.cu
 int g2p_blocks(int sm_count);

@@ -43,9 +43,13 @@ __global__ void k_rebin(const Grid g, const PartView p, const BinView b, long lo
 // x-rows of the brick), read and written as four 16-byte vectors.
 constexpr int SCAN_THREADS = 256;
 
+// cmax: particles a cell keeps (reseeding's upper bound; ~0u when off); the
+// excess is counted into st->removed_total and dropped by the scatter.
 __global__ void __launch_bounds__(SCAN_THREADS) k_cell_local_scan(const Grid g, const BinView b,
                                                                     uint8_t* __restrict__ type,
-                                                                    unsigned int nb) {
+                                                                    unsigned int nb,
+                                                                    unsigned int cmax,
+                                                                    DevStats* st) {
   const int lane = threadIdx.x & 31;
   const unsigned int brick = blockIdx.x * (SCAN_THREADS / 32) + (threadIdx.x >> 5);
   if (brick >= nb) return;
@@ -63,6 +67,17 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_cell_local_scan(const Grid g, 
   }
 #pragma unroll
   for (int v = 0; v < 4; ++v) cnt4[v] = make_uint4(0u, 0u, 0u, 0u);
+  if (cmax != ~0u) {
+    unsigned int drop = 0;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const unsigned int keep = min(c[q], cmax);
+      drop += c[q] - keep;
+      c[q] = keep;
+    }
+    drop = __reduce_add_sync(0xffffffffu, drop);
+    if (lane == 0 && drop) atomicAdd((unsigned long long*)&st->removed_total, (unsigned long long)drop);
+  }
   unsigned int tot = 0;
 #pragma unroll
   for (int q = 0; q < 16; ++q) tot += c[q];
@@ -147,12 +162,17 @@ __global__ void __launch_bounds__(1024) k_brick_scan(const Grid g, const BinView
     b.brick_start[nb] = run;
     st->n_active = run_act;
     st->n_fluid = fl_tot;
+    st->np_layout = run;
   }
 }
 
 // Two particles per thread (i and i + stride), so each thread has two
 // dependent gather chains (key -> offsets -> 7 moves) in flight.
-__global__ void k_scatter(const PartView src, const PartView dst, const BinView b, long long np) {
+// np_dev (nullable): the source count in device memory, bounding np; particles
+// of rank >= rank_max in their cell are dropped (reseeding's upper bound).
+__global__ void k_scatter(const PartView src, const PartView dst, const BinView b, long long np,
+                          const long long* np_dev, unsigned int rank_max) {
+  if (np_dev) np = min(np, *np_dev);
   const long long stride = (long long)gridDim.x * blockDim.x;
   const long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   unsigned int d[2];
@@ -162,7 +182,9 @@ __global__ void k_scatter(const PartView src, const PartView dst, const BinView 
     const long long i = i0 + u * stride;
     ok[u] = i < np;
     const unsigned int key = ok[u] ? b.key[i] : 0u;
-    d[u] = ok[u] ? b.brick_start[key / BRICK_CELLS] + b.local_start[key] + b.rank[i] : 0u;
+    const unsigned int r = ok[u] ? b.rank[i] : 0u;
+    ok[u] = ok[u] && r < rank_max;
+    d[u] = ok[u] ? b.brick_start[key / BRICK_CELLS] + b.local_start[key] + r : 0u;
   }
 #pragma unroll
   for (int u = 0; u < 2; ++u) {
@@ -197,16 +219,18 @@ void launch_rebin(const Grid& g, const PartView& p, const BinView& b, long long 
   if (np > 0) k_rebin<<<blocks_for(np, 256), 256, 0, s>>>(g, p, b, np, st_speed);
 }
 
-void launch_bin(const Grid& g, const BinView& b, uint8_t* type, DevStats* st, cudaStream_t s) {
+void launch_bin(const Grid& g, const BinView& b, uint8_t* type, DevStats* st, cudaStream_t s,
+                unsigned int cmax) {
   const unsigned int nb = (unsigned)g.bx * g.by * g.bz;
   k_cell_local_scan<<<(nb + SCAN_THREADS / 32 - 1) / (SCAN_THREADS / 32), SCAN_THREADS, 0, s>>>(
-      g, b, type, nb);
+      g, b, type, nb, cmax, st);
   k_brick_scan<<<1, 1024, 0, s>>>(g, b, st);
 }
 
 void launch_scatter(const PartView& src, const PartView& dst, const BinView& b, long long np,
-                    cudaStream_t s) {
-  if (np > 0) k_scatter<<<blocks_for((np + 1) / 2, 256), 256, 0, s>>>(src, dst, b, np);
+                    cudaStream_t s, const long long* np_dev, unsigned int rank_max) {
+  if (np > 0)
+    k_scatter<<<blocks_for((np + 1) / 2, 256), 256, 0, s>>>(src, dst, b, np, np_dev, rank_max);
 }
 
 void launch_iota(int* id, long long np, cudaStream_t s) {

@@ -28,6 +28,7 @@ FLIP_E_NOT_CONVERGED = 4
 FLIP_E_TIMEOUT = 5
 FLIP_E_SIZE = 6
 FLIP_E_NOGPU = 7
+FLIP_E_CAPACITY = 8
 
 FLIP_PREC_FP32 = 0
 FLIP_PREC_MIXED_IR = 1
@@ -58,7 +59,9 @@ class FlipParams(C.Structure):
                 ("cg_max_iter", C.c_int32), ("ir_max_iter", C.c_int32),
                 ("precision", C.c_int32), ("advect_source", C.c_int32),
                 ("preconditioner", C.c_int32), ("mg_smooth", C.c_int32),
-                ("warm_start", C.c_int32), ("cfl", C.c_double)]
+                ("warm_start", C.c_int32), ("cfl", C.c_double), ("ppc_min", C.c_int32),
+                ("ppc_max", C.c_int32), ("max_particles", C.c_int64),
+                ("reseed_seed", C.c_uint64)]
 
 
 class FlipStats(C.Structure):
@@ -68,7 +71,8 @@ class FlipStats(C.Structure):
                 ("cg_rel_residual", C.c_double), ("rel_divergence", C.c_double),
                 ("max_speed", C.c_double), ("ms_bin", C.c_double), ("ms_p2g", C.c_double),
                 ("ms_divergence", C.c_double), ("ms_pcg", C.c_double), ("ms_g2p", C.c_double),
-                ("ms_total", C.c_double), ("dt_last", C.c_double)]
+                ("ms_total", C.c_double), ("dt_last", C.c_double),
+                ("particles_added", C.c_int64), ("particles_removed", C.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -164,7 +168,7 @@ def lib():
         L.flip_surface_destroy.argtypes = [vp]
         L.flip_surface_destroy.restype = None
         L.flip_surface_case_table.argtypes = [vp, vp]
-        if L.flip_abi_version() != 4:
+        if L.flip_abi_version() != 5:
             raise RuntimeError("libflip_gb300 ABI version mismatch")
         _lib = L
     return _lib
@@ -177,7 +181,7 @@ def last_error() -> str:
 def _check(rc: int, allow=(FLIP_OK,)) -> int:
     if rc in allow:
         return rc
-    if rc == FLIP_E_NOT_CONVERGED:
+    if rc in (FLIP_E_NOT_CONVERGED, FLIP_E_CAPACITY):
         warnings.warn(f"flip: {last_error()}", RuntimeWarning, stacklevel=3)
         return rc
     raise FlipError(rc, f"{lib().flip_strerror(rc).decode()}: {last_error()}")

@@ -46,16 +46,16 @@ def test_every_declared_symbol_is_exported(F):
 
 def test_abi_version_and_strerror(F):
     L = F.lib()
-    assert L.flip_abi_version() == 4
+    assert L.flip_abi_version() == 5
     for code in range(8):
         assert L.flip_strerror(code).decode()
     assert L.flip_strerror(99).decode() == "unknown status"
 
 
 def test_struct_layouts_match_header(F):
-    # flip_params: 3 int32 (+4) + 10 double + 7 int32 (+4) + cfl
-    assert ctypes.sizeof(F.FlipParams) == 12 + 4 + 10 * 8 + 28 + 4 + 8
-    assert ctypes.sizeof(F.FlipStats) == 5 * 8 + 2 * 4 + 10 * 8
+    # flip_params: 3 int32 (+4) + 10 double + 7 int32 (+4) + cfl + 2 int32 + 2 int64
+    assert ctypes.sizeof(F.FlipParams) == 12 + 4 + 10 * 8 + 28 + 4 + 8 + 8 + 16
+    assert ctypes.sizeof(F.FlipStats) == 5 * 8 + 2 * 4 + 10 * 8 + 2 * 8
     # flip_surface_params: 3 int32 (+4 padding) + 7 double
     assert ctypes.sizeof(F.FlipSurfaceParams) == 12 + 4 + 7 * 8
 
@@ -74,13 +74,14 @@ def test_default_params(F):
     assert p.gravity[1] == -9.81 and p.flip_ratio == 0.95 and p.cg_max_iter == 20 * 64
     assert p.skin == pytest.approx(1e-3 / 64)
     assert p.preconditioner == F.FLIP_PRECOND_MG and p.mg_smooth == 2 and p.warm_start == 0
-    assert p.cfl == 0.0
+    assert p.cfl == 0.0 and p.ppc_min == 0 and p.ppc_max == 0 and p.max_particles == 0
 
 
 @pytest.mark.parametrize("field,value,code", [
     ("dx", 0.3, 1), ("dt", 0.0, 1), ("flip_ratio", 1.5, 1), ("skin", 0.0, 1),
     ("precision", 7, 1), ("cg_max_iter", 0, 1), ("rho", -1.0, 1), ("preconditioner", 5, 1),
-    ("mg_smooth", 0, 1), ("warm_start", 2, 1), ("cfl", -1.0, 1), ("cfl", float("inf"), 1)])
+    ("mg_smooth", 0, 1), ("warm_start", 2, 1), ("cfl", -1.0, 1), ("cfl", float("inf"), 1),
+    ("ppc_min", 65, 1), ("ppc_max", -1, 1), ("max_particles", -5, 1)])
 def test_argument_checks_before_any_device_call(F, field, value, code):
     p = F.default_params(16)
     setattr(p, field, value)
