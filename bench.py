@@ -379,6 +379,10 @@ def main():
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--budget-gb", type=float, default=180.0)
     ap.add_argument("--max-batch", type=int, default=64)
+    ap.add_argument("--cfl", type=float, default=0.0,
+                    help="adaptive time step with this CFL number (0: fixed dt = 1/240)")
+    ap.add_argument("--ppc", type=int, nargs=2, default=(0, 0), metavar=("MIN", "MAX"),
+                    help="reseed cells to at least MIN and at most MAX particles (0 0: off)")
     ap.add_argument("--no-surface", dest="surface", action="store_false",
                     help="skip the surface-reconstruction measurement")
     ap.add_argument("--warm-start", action="store_true",
@@ -413,6 +417,8 @@ def main():
     sc = make_scene(w)
     prm = make_params(w)
     prm.warm_start = 1 if args.warm_start else 0
+    prm.cfl = args.cfl
+    prm.ppc_min, prm.ppc_max = args.ppc
     sim = F.Simulation(prm, *sc.arrays())
     stream = torch.cuda.ExternalStream(sim.stream)
     np_ = sc.n_particles
@@ -439,11 +445,12 @@ def main():
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
+    np_ = st.n_particles if args.ppc[0] or args.ppc[1] else np_
     value = ws * np_ * args.steps / (ms / 1e3)
 
     # end to end: host (pinned) buffers in, one step, host buffers out, every step
     e2e = None
-    if args.e2e_steps > 0:
+    if args.e2e_steps > 0 and not (args.ppc[0] or args.ppc[1]):
         host = [torch.empty(np_, dtype=torch.float32, pin_memory=True) for _ in range(6)]
         F.flip_read_particles(sim.h, *host)
         sim.sync()
@@ -530,7 +537,13 @@ def main():
                        "parallelism": f"{ws} independent replica(s), one per GPU",
                        "l2": "inputs larger than L2 (particles + grids > 1 GB); no flush",
                        "pressure_start": "last solve's pressure (warm start)" if args.warm_start
-                       else "zero (cold start)"},
+                       else "zero (cold start)",
+                       "time_step": f"adaptive, CFL number {args.cfl}" if args.cfl > 0
+                       else "fixed 1/240",
+                       "reseeding": f"{args.ppc[0]}..{args.ppc[1]} particles per cell"
+                       if args.ppc[0] or args.ppc[1] else "off"},
+            "dt_last": st.dt_last, "particles_added": st.particles_added,
+            "particles_removed": st.particles_removed,
             "stages_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
             "cg_iterations_per_step": st.cg_iterations / args.steps,
             "ir_iterations_per_step": st.ir_iterations / args.steps,

@@ -227,15 +227,17 @@ int flip_read(flip_handle* h, flip_field which, void* dst, size_t bytes, int32_t
 int flip_write(flip_handle* h, flip_field which, const void* src, size_t bytes,
                int32_t src_is_device);
 
-/* All six particle arrays (float32[np] each) at once, in the handle's current
- * order; id (int32[np], nullable) receives the creation index of each entry.
+/* All six particle arrays (float32[n] each) at once, in the handle's current
+ * order; id (int32[n], nullable) receives the creation index of each entry.
+ * n is the current particle count, flip_field_bytes(h, FLIP_FIELD_PX) / 4
+ * (np unless reseeding changed it); the caller's arrays must hold n entries.
  * Synchronous. */
 int flip_read_particles(flip_handle* h, float* x, float* y, float* z, float* u, float* v,
                         float* w, int32_t* id, int32_t dst_is_device);
 
-/* Overwrites all six particle arrays (float32[np] each, the handle's current
- * order, ids unchanged) and re-bins once.  Synchronous with respect to the
- * sources. */
+/* Overwrites all six particle arrays (float32[n] each, n the current count as
+ * above; the handle's current order, ids unchanged) and re-bins once.
+ * Synchronous with respect to the sources. */
 int flip_write_particles(flip_handle* h, const float* x, const float* y, const float* z,
                          const float* u, const float* v, const float* w, int32_t src_is_device);
 

@@ -300,13 +300,24 @@ def flip_read_particles(h, x, y, z, u, v, w, ids=None):
     """Reads the six particle arrays (and ids) into caller buffers (numpy or torch)."""
     bufs = [_buf(a, np.float32) for a in (x, y, z, u, v, w)]
     idb = _buf(ids, np.int32) if ids is not None else None
+    _check_particle_sizes(h, bufs + ([idb] if idb else []))
     dev = bufs[0][2]
     _check(lib().flip_read_particles(h, *[C.c_void_p(b[0]) for b in bufs],
                                      C.c_void_p(idb[0]) if idb else None, dev))
 
 
+def _check_particle_sizes(h, bufs):
+    """Every buffer must hold the current particle count (it varies with reseeding)."""
+    need = lib().flip_field_bytes(h, PX)
+    for b in bufs:
+        if b[1] != need:
+            raise ValueError(f"particle buffer of {b[1]} bytes; the handle holds {need // 4} "
+                             "particles")
+
+
 def flip_write_particles(h, x, y, z, u, v, w):
     bufs = [_buf(a, np.float32) for a in (x, y, z, u, v, w)]
+    _check_particle_sizes(h, bufs)
     _check(lib().flip_write_particles(h, *[C.c_void_p(b[0]) for b in bufs], bufs[0][2]))
 
 
