@@ -7,8 +7,9 @@
 //                   the histogram atomic returns its rank in the bin
 //   scan            exclusive scan of the bin counts (tile scan below)
 //   k_sbin_scatter  positions into bin order as float4
-//   k_sdf           one thread per corner: the bins that meet the ball of radius
-//                   R, kernel sums of k and k (x_i - x), phi = |sum k d| / sum k - r
+//   k_sdf           one warp per 4 corners along x: the bin rows that meet their
+//                   balls of radius R, read as coalesced particle ranges; kernel
+//                   sums of k and k (x_i - x), phi = |sum k d| / sum k - r
 // Pipeline of flip_surface_mesh:
 //   tile scan over corners of one packed count per corner: (vertices on the
 //   corner's 3 outgoing edges) + (triangles of the cube it is the lowest corner
@@ -364,59 +365,128 @@ __global__ void k_sbin_scatter(const PartView p, long long np, const int* __rest
   pos[start[b] + prank[i]] = make_float4(p.x[i], p.y[i], p.z[i], 0.0f);
 }
 
+// One warp per group of SDF_G corners consecutive along x (same j, k).  With bins
+// of edge R/2 the balls meet at most 5 bins along y and along z, so at most 25 bin
+// rows (fixed y, z bin): lane r finds row r's particle range (the row's bins
+// within the balls' x extent are one contiguous range), a warp scan lays the rows
+// end to end in a per-warp shared table, and the lanes stride over that flat
+// range, so every load is independent and a warp's loads are consecutive
+// float4s.  Each particle is tested against all SDF_G corners, whose sums stay in
+// registers until a warp reduction.  A bin whose nearest point is R or farther
+// from the corners holds no particle closer than R and is skipped.
+constexpr int SDF_G = 4;
 constexpr int SDF_THREADS = 256;
+constexpr int SDF_WARPS = SDF_THREADS / 32;
 
 __global__ void __launch_bounds__(SDF_THREADS) k_sdf(const SGrid g, const SBins B,
                                                      const unsigned int* __restrict__ start,
                                                      const float4* __restrict__ pos,
                                                      float* __restrict__ phi) {
-  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= g.ncorners) return;
-  int ijk[3];
-  corner_ijk(g, c, ijk[0], ijk[1], ijk[2]);
-  float x[3];
-  int lo[3], hi[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    x[a] = g.o[a] + g.h * (float)ijk[a];
-    const float rel = (x[a] - B.o[a]) * B.inv_b;
-    lo[a] = max(0, (int)floorf(rel - B.R * B.inv_b - 0.01f));
-    hi[a] = min(B.nb[a] - 1, (int)floorf(rel + B.R * B.inv_b + 0.01f));
-  }
-  float sk = 0.0f, sd0 = 0.0f, sd1 = 0.0f, sd2 = 0.0f;
-  for (int bz = lo[2]; bz <= hi[2]; ++bz) {
-    const float dz = fmaxf(fmaxf(B.o[2] + B.b * bz - x[2], x[2] - (B.o[2] + B.b * (bz + 1))), 0.0f);
-    for (int by = lo[1]; by <= hi[1]; ++by) {
-      const float dy = fmaxf(fmaxf(B.o[1] + B.b * by - x[1], x[1] - (B.o[1] + B.b * (by + 1))), 0.0f);
+  __shared__ unsigned int s_end[SDF_WARPS][32], s_beg[SDF_WARPS][32], s_p0[SDF_WARPS][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int gx = (g.c[0] + SDF_G - 1) / SDF_G;
+  const long long ngroups = (long long)gx * g.c[1] * g.c[2];
+  const long long warps = (long long)gridDim.x * SDF_WARPS;
+  constexpr float Rb = 2.0f;  // R in bins (the bin edge is R/2)
+  for (long long grp = blockIdx.x * (long long)SDF_WARPS + wid; grp < ngroups; grp += warps) {
+    const int i0 = (int)(grp % gx) * SDF_G;
+    const int j = (int)((grp / gx) % g.c[1]);
+    const int k = (int)(grp / ((long long)gx * g.c[1]));
+    const int ng = min(SDF_G, g.c[0] - i0);
+    const float x0 = g.o[0] + g.h * (float)i0, xl = g.o[0] + g.h * (float)(i0 + ng - 1);
+    const float yc = g.o[1] + g.h * (float)j, zc = g.o[2] + g.h * (float)k;
+    const float ry = (yc - B.o[1]) * B.inv_b, rz = (zc - B.o[2]) * B.inv_b;
+    const int by0 = max(0, (int)floorf(ry - Rb)), by1 = min(B.nb[1] - 1, (int)floorf(ry + Rb));
+    const int bz0 = max(0, (int)floorf(rz - Rb)), bz1 = min(B.nb[2] - 1, (int)floorf(rz + Rb));
+    const int nyr = max(by1 - by0 + 1, 1);
+    const int nrows = min(nyr * (bz1 - bz0 + 1), 32);
+    unsigned int p0 = 0, cnt = 0;
+    if (lane < nrows) {
+      const int by = by0 + lane % nyr, bz = bz0 + lane / nyr;
+      const float dy = fmaxf(fmaxf(B.o[1] + B.b * by - yc, yc - (B.o[1] + B.b * (by + 1))), 0.0f);
+      const float dz = fmaxf(fmaxf(B.o[2] + B.b * bz - zc, zc - (B.o[2] + B.b * (bz + 1))), 0.0f);
       const float dyz = dy * dy + dz * dz;
-      if (dyz > B.R2 * 1.001f) continue;
-      const long long row = (long long)B.nb[0] * (by + (long long)B.nb[1] * bz);
-      // the bins of this row within the ball's x extent: one contiguous range
-      const float rx = sqrtf(fmaxf(B.R2 - dyz, 0.0f)) * B.inv_b;
-      const float rel = (x[0] - B.o[0]) * B.inv_b;
-      const int bx0 = max(lo[0], (int)floorf(rel - rx - 0.01f));
-      const int bx1 = min(hi[0], (int)floorf(rel + rx + 0.01f));
-      if (bx0 > bx1) continue;
-      const unsigned int p0 = start[row + bx0], p1 = start[row + bx1 + 1];
-      for (unsigned int q = p0; q < p1; ++q) {
-        const float4 P = pos[q];
-        const float d0 = P.x - x[0], d1 = P.y - x[1], d2 = P.z - x[2];
-        const float dd = d0 * d0 + d1 * d1 + d2 * d2;
-        if (dd < B.R2) {
-          const float t = 1.0f - dd * B.inv_R2;
-          const float kk = t * t * t;
-          sk += kk;
-          sd0 += kk * d0;
-          sd1 += kk * d1;
-          sd2 += kk * d2;
+      if (dyz < B.R2) {
+        const float rx = sqrtf(B.R2 - dyz) * B.inv_b;
+        const int bx0 = max(0, (int)floorf((x0 - B.o[0]) * B.inv_b - rx));
+        const int bx1 = min(B.nb[0] - 1, (int)floorf((xl - B.o[0]) * B.inv_b + rx));
+        if (bx0 <= bx1) {
+          const long long row = (long long)B.nb[0] * (by + (long long)B.nb[1] * bz);
+          p0 = start[row + bx0];
+          cnt = start[row + bx1 + 1] - p0;
         }
       }
     }
+    unsigned int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
+    __syncwarp();
+    s_end[wid][lane] = incl;
+    s_beg[wid][lane] = incl - cnt;
+    s_p0[wid][lane] = p0;
+    __syncwarp();
+    float sk[SDF_G], s0[SDF_G], s1[SDF_G], s2[SDF_G];
+#pragma unroll
+    for (int q = 0; q < SDF_G; ++q) sk[q] = s0[q] = s1[q] = s2[q] = 0.0f;
+    int r = 0;  // this lane's current row: only moves forward
+    for (unsigned int f = lane; f < total; f += 32) {
+      while (f >= s_end[wid][r]) ++r;
+      const float4 P = pos[s_p0[wid][r] + (f - s_beg[wid][r])];
+      const float ey = P.y - yc, ez = P.z - zc;
+      const float r2 = ey * ey + ez * ez;
+#pragma unroll
+      for (int q = 0; q < SDF_G; ++q) {
+        const float ex = P.x - (x0 + g.h * (float)q);
+        const float dd = ex * ex + r2;
+        if (q < ng && dd < B.R2) {
+          const float t = 1.0f - dd * B.inv_R2;
+          const float kk = t * t * t;
+          sk[q] += kk;
+          s0[q] += kk * ex;
+          s1[q] += kk * ey;
+          s2[q] += kk * ez;
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < SDF_G; ++q) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sk[q] += __shfl_xor_sync(0xffffffffu, sk[q], o);
+        s0[q] += __shfl_xor_sync(0xffffffffu, s0[q], o);
+        s1[q] += __shfl_xor_sync(0xffffffffu, s1[q], o);
+        s2[q] += __shfl_xor_sync(0xffffffffu, s2[q], o);
+      }
+    }
+    if (lane < ng) {
+      float a = 0.0f, b0 = 0.0f, b1 = 0.0f, b2 = 0.0f;
+#pragma unroll
+      for (int q = 0; q < SDF_G; ++q)
+        if (q == lane) {
+          a = sk[q];
+          b0 = s0[q];
+          b1 = s1[q];
+          b2 = s2[q];
+        }
+      const float v = (a > 0.0f) ? sqrtf(b0 * b0 + b1 * b1 + b2 * b2) / a - B.r : B.R - B.r;
+      phi[(i0 + lane) + (long long)g.c[0] * (j + (long long)g.c[1] * k)] = v;
+    }
   }
-  float v;
-  if (sk > 0.0f) v = sqrtf(sd0 * sd0 + sd1 * sd1 + sd2 * sd2) / sk - B.r;
-  else v = B.R - B.r;
-  phi[c] = v;
+}
+
+int sdf_blocks() {
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sdf, SDF_THREADS, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 152 * 8;
+  }
+  return std::max(1, sms * std::max(per, 1));
 }
 
 // ------------------------------------------------------------------ marching cubes
@@ -772,8 +842,7 @@ int flip_surface_sdf(flip_surface* s, flip_handle* h) {
     k_sbin_scatter<<<blocks_for(np, 256), 256, 0, st>>>(P, np, s->pbin, s->prank, s->bin_start,
                                                         s->pos);
   }
-  k_sdf<<<blocks_for(s->g.ncorners, SDF_THREADS), SDF_THREADS, 0, st>>>(s->g, s->B, s->bin_start,
-                                                                         s->pos, s->phi);
+  k_sdf<<<sdf_blocks(), SDF_THREADS, 0, st>>>(s->g, s->B, s->bin_start, s->pos, s->phi);
   SURF_CUDA(cudaGetLastError());
   return FLIP_OK;
 }
