@@ -383,6 +383,8 @@ def main():
                     help="adaptive time step with this CFL number (0: fixed dt = 1/240)")
     ap.add_argument("--ppc", type=int, nargs=2, default=(0, 0), metavar=("MIN", "MAX"),
                     help="reseed cells to at least MIN and at most MAX particles (0 0: off)")
+    ap.add_argument("--mg-smooth", type=int, default=2,
+                    help="multigrid red-black sweep pairs before and after the correction")
     ap.add_argument("--no-surface", dest="surface", action="store_false",
                     help="skip the surface-reconstruction measurement")
     ap.add_argument("--warm-start", action="store_true",
@@ -418,6 +420,7 @@ def main():
     prm = make_params(w)
     prm.warm_start = 1 if args.warm_start else 0
     prm.cfl = args.cfl
+    prm.mg_smooth = args.mg_smooth
     prm.ppc_min, prm.ppc_max = args.ppc
     sim = F.Simulation(prm, *sc.arrays())
     stream = torch.cuda.ExternalStream(sim.stream)
@@ -538,6 +541,7 @@ def main():
                        "l2": "inputs larger than L2 (particles + grids > 1 GB); no flush",
                        "pressure_start": "last solve's pressure (warm start)" if args.warm_start
                        else "zero (cold start)",
+                       "mg_smooth": args.mg_smooth,
                        "time_step": f"adaptive, CFL number {args.cfl}" if args.cfl > 0
                        else "fixed 1/240",
                        "reseeding": f"{args.ppc[0]}..{args.ppc[1]} particles per cell"
