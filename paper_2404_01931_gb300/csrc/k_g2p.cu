@@ -115,7 +115,7 @@ __device__ __forceinline__ void interp_tile(const Grid& g, float px, float py, f
 }
 
 template <bool PAIR>
-__global__ void __launch_bounds__(G2P_THREADS) k_g2p(const Grid g, const StepConsts K0,
+__global__ void __launch_bounds__(G2P_THREADS, 6) k_g2p(const Grid g, const StepConsts K0,
                                                      const PartView P, const BinView B,
                                                      const float* __restrict__ uo0,
                                                      const float* __restrict__ uo1,
