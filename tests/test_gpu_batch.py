@@ -99,3 +99,41 @@ def test_batch_argument_checks():
                 b.step([a, c, d], 1)  # more than the capacity
         rc, _ = b.step([], 1)
         assert rc == F.FLIP_OK
+
+
+def test_batch_with_adaptive_step_and_reseeding():
+    """Scenes with the adaptive time step and reseeding in one batch: each takes the
+    dt, particle count and per-cell counts it takes alone."""
+    specs = [(24, 3.0, (3, 12)), (32, 0.0, (3, 0)), (16, 0.01, (0, 6))]
+    scenes, params = [], []
+    for n, cfl, (lo, hi) in specs:
+        sc = S.random_velocities(S.box(n, (0.1, 0.0, 0.1), (0.7, 0.6, 0.8), density=1, seed=n), 20.0, n)
+        fp = matched(n)[1]
+        fp.cfl, fp.ppc_min, fp.ppc_max = cfl, lo, hi
+        fp.max_particles = 40 * sc.n_particles   # fast lone particles spread into many cells
+        scenes.append(sc)
+        params.append(fp)
+
+    def cells(n, sim):
+        x, y, z = (sim.read(f).astype(np.float64) for f in (F.PX, F.PY, F.PZ))
+        c = lambda a: np.clip(np.floor(a * n).astype(int), 0, n - 1)
+        return np.bincount(c(x) + n * (c(y) + n * c(z)), minlength=n ** 3)
+
+    alone = []
+    for (n, _, _), sc, fp in zip(specs, scenes, params):
+        with F.Simulation(fp, *sc.arrays()) as sim:
+            rc, st = sim.step(3, stats=True)
+            assert rc == F.FLIP_OK
+            alone.append((st.dt_last, st.n_particles, cells(n, sim)))
+    sims = [F.Simulation(fp, *sc.arrays()) for sc, fp in zip(scenes, params)]
+    try:
+        with F.Batch(len(sims)) as b:
+            rc, sts = b.step(sims, 3, stats=True)
+        assert rc == F.FLIP_OK
+        for (n, _, _), sim, st, (dt, npart, cnt) in zip(specs, sims, sts, alone):
+            assert st.dt_last == pytest.approx(dt, rel=1e-6)
+            assert st.n_particles == npart
+            assert np.abs(cells(n, sim) - cnt).sum() <= 2
+    finally:
+        for s in sims:
+            s.close()
