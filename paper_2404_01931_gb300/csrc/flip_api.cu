@@ -119,6 +119,7 @@ const char* flip_strerror(int status) {
     case FLIP_E_TIMEOUT: return "device-side wait timed out";
     case FLIP_E_SIZE: return "buffer size does not match the field";
     case FLIP_E_NOGPU: return "no usable sm_103 CUDA device";
+    case FLIP_E_CAPACITY: return "reseeding reached the particle capacity (warning)";
     default: return "unknown status";
   }
 }
