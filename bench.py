@@ -258,8 +258,10 @@ def run_batch(args):
     npart = sum(sc.n_particles for sc in scenes)
     stream = torch.cuda.Stream()  # the batched solves run here; it joins every scene
     b = F.Batch(len(sims), stream=stream.cuda_stream)
+    # warm-up, then the autotuner picks the solve-team split on real steps
     if args.warmup:
         b.step(sims, args.warmup)
+    exponent = b.autotune(sims, 1) if args.autotune else 1.0
     torch.cuda.synchronize()
     clocks = ClockSampler(0)
     clocks.start()
@@ -267,11 +269,14 @@ def run_batch(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    rc, st = b.step(sims, args.steps, stats=True)
+    rc, _ = b.step(sims, args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
     ck = clocks.stop()
     ms = e0.elapsed_time(e1)
+    # iteration counts and the solve time from one more step with statistics (untimed)
+    rc_st, st = b.step(sims, 1, stats=True)
+    rc = rc or rc_st
     edges = sorted({sc.n[0] for sc in scenes})
     # the same scenes stepped one at a time through flip_step (the plain per-scene form)
     torch.cuda.synchronize()
@@ -289,10 +294,11 @@ def run_batch(args):
                                   "fluid fraction 0.2-0.5 by seed", "particles": npart,
                       "cells": sum(int(np.prod(sc.n)) for sc in scenes),
                       "precision": "FP32 (float-pair dot products)", "preconditioner": "multigrid"},
-           "cg_iterations_per_scene_step": sum(s.cg_iterations for s in st) / len(st) / args.steps,
-           "ms_pcg_per_step": st[0].ms_pcg / args.steps,
+           "team_exponent": exponent,
+           "cg_iterations_per_scene_step": sum(s.cg_iterations for s in st) / len(st),
+           "ms_pcg_per_step": st[0].ms_pcg,
            "max_rel_residual": max(s.cg_rel_residual for s in st), "status": rc,
-           "gpu_launches": sum(s.kernel_launches for s in st), "clocks": ck,
+           "gpu_launches": sum(s.kernel_launches for s in st) * args.steps, "clocks": ck,
            "per_scene_sequential": {"value": seq_value, "unit": "particle-steps/s",
                                     "what": "the same scenes, one flip_step call per scene "
                                             "after another (host-timed, synchronised)"}}
@@ -385,6 +391,8 @@ def main():
                     help="reseed cells to at least MIN and at most MAX particles (0 0: off)")
     ap.add_argument("--mg-smooth", type=int, default=2,
                     help="multigrid red-black sweep pairs before and after the correction")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="batch mode: keep the default solve-team split")
     ap.add_argument("--no-surface", dest="surface", action="store_false",
                     help="skip the surface-reconstruction measurement")
     ap.add_argument("--warm-start", action="store_true",

@@ -291,6 +291,19 @@ int flip_batch_create(int32_t capacity, void* stream, flip_batch** out);
 int flip_batch_step(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t nsteps,
                     flip_stats* stats);
 
+/* How the batched solves split their CTAs: each scene's team is proportional to
+ * its particle count raised to `exponent` (default 1; in [0, 3]). */
+int flip_batch_set_team_exponent(flip_batch* b, double exponent);
+
+/* Autotuner of that split: for each exponent in {0.5, 0.75, 1, 1.25, 1.5, 2,
+ * 2.5} it advances the scenes by steps_per_candidate real steps through
+ * flip_batch_step, timing the batched solves with CUDA events, and keeps the
+ * exponent whose solves took least time (written to *exponent, nullable).  The
+ * scenes advance by 7 * steps_per_candidate steps in all.  Returns the first
+ * error, else the first warning, else FLIP_OK. */
+int flip_batch_autotune(flip_batch* b, flip_handle* const* hs, int32_t n,
+                        int32_t steps_per_candidate, double* exponent);
+
 void flip_batch_destroy(flip_batch* b);
 
 /* Standalone pressure solve (Sec. 3.1.7): A p = b for the cell types in type.

@@ -991,18 +991,21 @@ struct flip_batch {
   std::vector<cudaEvent_t> ev;   // one per scene slot
   cudaEvent_t ev_begin = nullptr, ev_pcg0 = nullptr, ev_pcg1 = nullptr, ev_end = nullptr;
   cudaEvent_t ev_solved = nullptr;
+  double team_exponent = 1.0;    // team size proportional to particles^exponent
 };
 
 namespace {
 
-// Splits max_blocks CTAs over scenes in proportion to their particle counts,
-// at least one each (n <= max_blocks).  first has n+1 entries.
-void assign_teams(const std::vector<flip_handle*>& hs, int max_blocks, std::vector<int>& first) {
+// Splits max_blocks CTAs over scenes in proportion to their particle counts
+// raised to `exponent`, at least one each (n <= max_blocks).  first has n+1
+// entries.
+void assign_teams(const std::vector<flip_handle*>& hs, int max_blocks, std::vector<int>& first,
+                  double exponent) {
   const int n = (int)hs.size();
   std::vector<double> w(n);
   double tot = 0.0;
   for (int s = 0; s < n; ++s) {
-    w[s] = (double)std::max<long long>(hs[s]->np, 1);
+    w[s] = std::pow((double)std::max<long long>(hs[s]->np, 1), exponent);
     tot += w[s];
   }
   std::vector<int> cnt(n, 1);
@@ -1067,6 +1070,44 @@ int flip_batch_create(int32_t capacity, void* stream, flip_batch** out) {
   return FLIP_OK;
 }
 
+int flip_batch_set_team_exponent(flip_batch* b, double exponent) {
+  if (!b) return fail(FLIP_E_ARG, "batch is NULL");
+  if (!(exponent >= 0.0 && exponent <= 3.0)) return fail(FLIP_E_ARG, "exponent must be in [0, 3]");
+  b->team_exponent = exponent;
+  return FLIP_OK;
+}
+
+int flip_batch_autotune(flip_batch* b, flip_handle* const* hs, int32_t n,
+                        int32_t steps_per_candidate, double* exponent) {
+  if (!b) return fail(FLIP_E_ARG, "batch is NULL");
+  if (steps_per_candidate < 1) return fail(FLIP_E_ARG, "steps_per_candidate must be >= 1");
+  static const double cand[] = {0.5, 0.75, 1.0, 1.25, 1.5, 2.0, 2.5};
+  std::vector<flip_stats> st((size_t)std::max(n, 1));
+  double best = b->team_exponent;
+  float best_ms = 0.0f;
+  bool have = false;
+  int first_warning = FLIP_OK;
+  for (double a : cand) {
+    b->team_exponent = a;
+    const int rc = flip_batch_step(b, hs, n, steps_per_candidate, st.data());
+    if (rc == FLIP_E_NOT_CONVERGED || rc == FLIP_E_CAPACITY) {
+      if (first_warning == FLIP_OK) first_warning = rc;
+    } else if (rc != FLIP_OK) {
+      b->team_exponent = best;
+      return rc;
+    }
+    const float ms = n > 0 ? (float)st[0].ms_pcg : 0.0f;
+    if (!have || ms < best_ms) {
+      best = a;
+      best_ms = ms;
+      have = true;
+    }
+  }
+  b->team_exponent = best;
+  if (exponent) *exponent = best;
+  return first_warning;
+}
+
 void flip_batch_destroy(flip_batch* b) {
   if (!b) return;
   if (b->stream) cudaStreamSynchronize(b->stream);
@@ -1125,7 +1166,7 @@ int flip_batch_step(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t ns
       args.push_back(pcg_args(hs[s]));
     }
     std::vector<int> first;
-    assign_teams(hv, b->max_blocks, first);
+    assign_teams(hv, b->max_blocks, first, b->team_exponent);
     bs_off.push_back((int)block_scene_all.size());
     tf_off.push_back((int)first_all.size());
     for (int t = 0; t < (int)hv.size(); ++t)

@@ -155,6 +155,8 @@ def lib():
         L.flip_solve_pressure_noalloc.argtypes = [PP, vp, vp, vp, vp, C.POINTER(i32),
                                                   C.POINTER(C.c_double)]
         L.flip_energy.argtypes = [vp, C.c_double, C.POINTER(C.c_double)]
+        L.flip_batch_set_team_exponent.argtypes = [vp, C.c_double]
+        L.flip_batch_autotune.argtypes = [vp, C.POINTER(vp), i32, i32, C.POINTER(C.c_double)]
         SP = C.POINTER(FlipSurfaceParams)
         L.flip_surface_default_params.argtypes = [PP, SP]
         L.flip_surface_default_params.restype = None
@@ -397,6 +399,19 @@ class Batch:
 
     def step(self, sims, nsteps: int = 1, stats: bool = False):
         return flip_batch_step(self.b, [s.h for s in sims], nsteps, stats)
+
+    def set_team_exponent(self, exponent: float):
+        _check(lib().flip_batch_set_team_exponent(self.b, float(exponent)))
+
+    def autotune(self, sims, steps_per_candidate: int = 1) -> float:
+        """Chooses the solve-team split by timing real steps (the scenes advance)."""
+        hs = [s.h for s in sims]
+        arr = (C.c_void_p * max(len(hs), 1))(*[h.value if isinstance(h, C.c_void_p) else h
+                                                for h in hs])
+        out = C.c_double(0.0)
+        _check(lib().flip_batch_autotune(self.b, arr, len(hs), int(steps_per_candidate),
+                                         C.byref(out)))
+        return float(out.value)
 
     def close(self):
         if getattr(self, "b", None):
