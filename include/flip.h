@@ -291,6 +291,17 @@ int flip_batch_create(int32_t capacity, void* stream, flip_batch** out);
 int flip_batch_step(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t nsteps,
                     flip_stats* stats);
 
+/* With enable = 1, untimed flip_batch_step calls of two or more steps run their
+ * steps in pairs as one captured CUDA graph (scenes without reseeding, whose
+ * step index the graph would freeze), cached for the same scenes and CTA split;
+ * the remaining step, and any call the capture cannot serve, runs as usual.
+ * Default 0: on GB300 the replays measured slower than stream-ordered launches
+ * (64 dam breaks: 12.2 against 11.5 ms per step). */
+int flip_batch_set_graphs(flip_batch* b, int32_t enable);
+
+/* 1 when a captured graph is cached (the last graph-eligible call used it). */
+int flip_batch_graph_active(const flip_batch* b);
+
 /* How the batched solves split their CTAs: each scene's team is proportional to
  * its particle count raised to `exponent` (default 1; in [0, 3]). */
 int flip_batch_set_team_exponent(flip_batch* b, double exponent);

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <vector>
 #include <cstdio>
@@ -38,6 +39,13 @@ int cuda_fail(cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
   } while (0)
 
+// The same, for functions that return a count or -status.
+#define FLIP_CUDA_NEG(call)                               \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return -cuda_fail(e_, #call);  \
+  } while (0)
+
 constexpr size_t kAlign = 256;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
@@ -63,6 +71,7 @@ struct flip_handle {
   long long np = 0, ncells = 0, nkeys = 0, nf[3] = {0, 0, 0};
   long long cap = 0;          // particle capacity (np, or more when reseeding)
   long long steps_done = 0;   // steps taken (the reseeding generator's step index)
+  long long serial = 0;       // creation number (distinguishes a handle reusing an address)
   unsigned int nbricks = 0;
   bool mixed = false;
   cudaStream_t stream = nullptr;
@@ -569,6 +578,10 @@ int flip_create(const flip_params* params, const float* x, const float* y, const
   flip_handle* h = new (std::nothrow) flip_handle();
   if (!h) return fail(FLIP_E_OOM, "host allocation failed");
   h->prm = *params;
+  {
+    static std::atomic<long long> next_serial{1};
+    h->serial = next_serial.fetch_add(1);
+  }
   h->g = make_grid(*params);
   h->K = make_consts(*params);
   h->np = np;
@@ -992,9 +1005,105 @@ struct flip_batch {
   cudaEvent_t ev_begin = nullptr, ev_pcg0 = nullptr, ev_pcg1 = nullptr, ev_end = nullptr;
   cudaEvent_t ev_solved = nullptr;
   double team_exponent = 1.0;    // team size proportional to particles^exponent
+  // two steps of a fixed set of scenes captured as one CUDA graph (untimed calls)
+  cudaGraphExec_t graph = nullptr;
+  std::vector<unsigned long long> graph_key;
+  std::vector<int> graph_launches;  // kernel launches per scene in the captured pair
+  int graph_batch_launches = 0;
+  bool graph_off = false;           // capture failed once: use the plain path
+  bool graphs = false;              // graph replay requested (flip_batch_set_graphs)
 };
 
 namespace {
+
+// Runs `pairs` pairs of batched steps as a CUDA graph: two steps of the scenes
+// captured from enqueue_step (the particle double buffers are back in place
+// after two steps), cached on the batch for the same scenes, buffer parity and
+// CTA split.  Host-side state the capture moved (buffer index, step and launch
+// counters) is restored and advanced per replay.  Returns the steps done (0 when
+// the graph path is unavailable: the caller steps normally), or -status.
+template <class F>
+int batch_graph_steps(flip_batch* b, flip_handle* const* hs, int n, int pairs,
+                      const std::vector<int>& first_all, F& enqueue_step, int* batch_launches) {
+  const cudaStream_t bs = b->stream;
+  std::vector<unsigned long long> key;
+  key.push_back((unsigned long long)n);
+  for (int s = 0; s < n; ++s) {
+    key.push_back((unsigned long long)(uintptr_t)hs[s]);
+    key.push_back((unsigned long long)hs[s]->serial);
+    key.push_back((unsigned long long)hs[s]->cur);
+  }
+  for (int v : first_all) key.push_back((unsigned long long)v);
+  // the batch stream starts after every scene stream's earlier work
+  for (int s = 0; s < n; ++s) {
+    FLIP_CUDA_NEG(cudaEventRecord(b->ev[s], hs[s]->stream));
+    FLIP_CUDA_NEG(cudaStreamWaitEvent(bs, b->ev[s], 0));
+  }
+  if (!b->graph || b->graph_key != key) {
+    if (b->graph) {
+      cudaGraphExecDestroy(b->graph);
+      b->graph = nullptr;
+    }
+    std::vector<int> cur(n), launches(n);
+    std::vector<long long> steps(n);
+    std::vector<char> stepped(n);
+    for (int s = 0; s < n; ++s) {
+      cur[s] = hs[s]->cur;
+      launches[s] = hs[s]->launches;
+      steps[s] = hs[s]->steps_done;
+      stepped[s] = hs[s]->stepped;
+    }
+    const int bl0 = *batch_launches;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal);
+    int rc = FLIP_OK;
+    if (e == cudaSuccess) {
+      // fork the scene streams into the capture, two steps, join them back
+      e = cudaEventRecord(b->ev_solved, bs);
+      for (int s = 0; s < n && e == cudaSuccess; ++s)
+        e = cudaStreamWaitEvent(hs[s]->stream, b->ev_solved, 0);
+      if (e == cudaSuccess) rc = enqueue_step();
+      if (e == cudaSuccess && rc == FLIP_OK) rc = enqueue_step();
+      for (int s = 0; s < n && e == cudaSuccess && rc == FLIP_OK; ++s) {
+        e = cudaEventRecord(b->ev[s], hs[s]->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(bs, b->ev[s], 0);
+      }
+      const cudaError_t e2 = cudaStreamEndCapture(bs, &g);
+      if (e == cudaSuccess) e = e2;
+    }
+    b->graph_launches.assign(n, 0);
+    for (int s = 0; s < n; ++s) {
+      b->graph_launches[s] = hs[s]->launches - launches[s];
+      hs[s]->cur = cur[s];
+      hs[s]->launches = launches[s];
+      hs[s]->steps_done = steps[s];
+      hs[s]->stepped = stepped[s];
+    }
+    b->graph_batch_launches = *batch_launches - bl0;
+    *batch_launches = bl0;
+    if (e == cudaSuccess && rc == FLIP_OK && g)
+      e = cudaGraphInstantiate(&b->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess || rc != FLIP_OK || !b->graph) {
+      cudaGetLastError();  // not sticky: the plain path takes over
+      b->graph = nullptr;
+      b->graph_off = true;
+      return 0;
+    }
+    b->graph_key = key;
+  }
+  for (int p = 0; p < pairs; ++p) FLIP_CUDA_NEG(cudaGraphLaunch(b->graph, bs));
+  for (int s = 0; s < n; ++s) {
+    hs[s]->launches += pairs * b->graph_launches[s];
+    hs[s]->steps_done += 2LL * pairs;
+    hs[s]->stepped = true;
+  }
+  *batch_launches += pairs * b->graph_batch_launches;
+  // every scene stream continues after the graph
+  FLIP_CUDA_NEG(cudaEventRecord(b->ev_solved, bs));
+  for (int s = 0; s < n; ++s) FLIP_CUDA_NEG(cudaStreamWaitEvent(hs[s]->stream, b->ev_solved, 0));
+  return 2 * pairs;
+}
 
 // Splits max_blocks CTAs over scenes in proportion to their particle counts
 // raised to `exponent`, at least one each (n <= max_blocks).  first has n+1
@@ -1070,6 +1179,14 @@ int flip_batch_create(int32_t capacity, void* stream, flip_batch** out) {
   return FLIP_OK;
 }
 
+int flip_batch_graph_active(const flip_batch* b) { return (b && b->graph) ? 1 : 0; }
+
+int flip_batch_set_graphs(flip_batch* b, int32_t enable) {
+  if (!b) return fail(FLIP_E_ARG, "batch is NULL");
+  b->graphs = enable != 0;
+  return FLIP_OK;
+}
+
 int flip_batch_set_team_exponent(flip_batch* b, double exponent) {
   if (!b) return fail(FLIP_E_ARG, "batch is NULL");
   if (!(exponent >= 0.0 && exponent <= 3.0)) return fail(FLIP_E_ARG, "exponent must be in [0, 3]");
@@ -1115,6 +1232,7 @@ void flip_batch_destroy(flip_batch* b) {
     if (ev) cudaEventDestroy(ev);
   for (cudaEvent_t ev : {b->ev_begin, b->ev_pcg0, b->ev_pcg1, b->ev_end, b->ev_solved})
     if (ev) cudaEventDestroy(ev);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
   if (b->d_args) cudaFree(b->d_args);
   if (b->d_block_scene) cudaFree(b->d_block_scene);
   if (b->d_team_first) cudaFree(b->d_team_first);
@@ -1219,7 +1337,8 @@ int flip_batch_step(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t ns
   FLIP_CUDA(cudaEventRecord(b->ev_solved, bs));
   for (int s = 0; s < n; ++s) FLIP_CUDA(cudaStreamWaitEvent(hs[s]->stream, b->ev_solved, 0));
   float ms_pcg = 0.0f;
-  for (int st = 0; st < nsteps; ++st) {
+  // One step of every scene, enqueued on the scene streams and the batch stream.
+  auto enqueue_step = [&]() -> int {
     for (int s = 0; s < n; ++s) {
       flip_handle* h = hs[s];
       const float* uo[3] = {h->uo[0], h->uo[1], h->uo[2]};
@@ -1260,7 +1379,20 @@ int flip_batch_step(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t ns
       FLIP_CUDA(cudaEventElapsedTime(&t, b->ev_pcg0, b->ev_pcg1));
       ms_pcg += t;
     }
+    return FLIP_OK;
+  };
+  int done = 0;
+  if (b->graphs && !timed && nsteps >= 2 && tmp_alloc.empty() && !b->graph_off) {
+    bool reseed = false;
+    for (int s = 0; s < n; ++s) reseed |= reseeding(hs[s]);
+    if (!reseed) {
+      int rc = batch_graph_steps(b, hs, n, nsteps / 2, first_all, enqueue_step, &batch_launches);
+      if (rc < 0) return -rc;
+      done = rc;
+    }
   }
+  for (int st = done; st < nsteps; ++st)
+    if (int rc = enqueue_step()) return rc;
   for (void* p : tmp_alloc) FLIP_CUDA(cudaFreeAsync(p, bs));
   // the batch stream joins every scene stream at the end of the call
   for (int s = 0; s < n; ++s) {

@@ -156,6 +156,8 @@ def lib():
                                                   C.POINTER(C.c_double)]
         L.flip_energy.argtypes = [vp, C.c_double, C.POINTER(C.c_double)]
         L.flip_batch_set_team_exponent.argtypes = [vp, C.c_double]
+        L.flip_batch_graph_active.argtypes = [vp]
+        L.flip_batch_set_graphs.argtypes = [vp, i32]
         L.flip_batch_autotune.argtypes = [vp, C.POINTER(vp), i32, i32, C.POINTER(C.c_double)]
         SP = C.POINTER(FlipSurfaceParams)
         L.flip_surface_default_params.argtypes = [PP, SP]
@@ -399,6 +401,12 @@ class Batch:
 
     def step(self, sims, nsteps: int = 1, stats: bool = False):
         return flip_batch_step(self.b, [s.h for s in sims], nsteps, stats)
+
+    def set_graphs(self, enable: bool):
+        _check(lib().flip_batch_set_graphs(self.b, int(bool(enable))))
+
+    def graph_active(self) -> bool:
+        return bool(lib().flip_batch_graph_active(self.b))
 
     def set_team_exponent(self, exponent: float):
         _check(lib().flip_batch_set_team_exponent(self.b, float(exponent)))

@@ -164,3 +164,29 @@ def test_autotune_picks_a_candidate_and_keeps_results():
     finally:
         for s in sims:
             s.close()
+
+
+def test_graph_replay_equals_plain_steps():
+    """Pairs of batched steps replayed as a captured CUDA graph give the results of
+    the same steps launched one by one (up to the order of floating-point sums).
+    One solver group (FP32, multigrid): batches of several groups keep the plain
+    path."""
+    mix = [m for m in _mix() if m[3].precision == F.FLIP_PREC_FP32 and m[3].preconditioner == 1]
+    assert len(mix) >= 3
+    plain, graph = [], []
+    for store, use in ((plain, False), (graph, True)):
+        sims = [F.Simulation(fp, *sc.arrays()) for n, sc, op, fp in mix]
+        try:
+            with F.Batch(len(sims)) as b:
+                b.set_graphs(use)
+                b.step(sims, 5)                  # two captured pairs and one plain step
+                b.step(sims, 4)                  # the cached graph, twice
+                assert b.graph_active() == use
+                for s in sims:
+                    store.append(_fields(s))
+        finally:
+            for s in sims:
+                s.close()
+    for a, b_ in zip(plain, graph):
+        for x, y in zip(a, b_):
+            assert rel_l2(y, x, 1e-3) <= 1e-4
