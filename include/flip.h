@@ -241,6 +241,19 @@ int flip_read_particles(flip_handle* h, float* x, float* y, float* z, float* u, 
 int flip_write_particles(flip_handle* h, const float* x, const float* y, const float* z,
                          const float* u, const float* v, const float* w, int32_t src_is_device);
 
+/* CTAs of the scene's persistent solve kernel, in [1, the co-resident maximum]
+ * (0, the default: one per SM).  Fewer CTAs mean fewer arrivals at each grid
+ * barrier, which pays on small grids; the solution is the same up to the order
+ * of floating-point sums.  FLIP_E_ARG outside the range. */
+int flip_set_solver_blocks(flip_handle* h, int32_t nblocks);
+
+/* Autotuner of that count: for each of m, m/2, m/4, m/8 CTAs (m the maximum) it
+ * takes steps_per_candidate real steps through flip_step, timing the solves with
+ * CUDA events, and keeps the fastest (written to *nblocks, nullable).  The scene
+ * advances by 4 * steps_per_candidate steps.  Returns the first error, else the
+ * first warning, else FLIP_OK. */
+int flip_autotune_solver(flip_handle* h, int32_t steps_per_candidate, int32_t* nblocks);
+
 /* Total mechanical energy of the particles, the quantity the paper follows over
  * a run to compare its CPU and GPU versions (Sec. 4, Fig. 10).  With particle
  * mass m = particle_mass and the handle's gravity g:

@@ -106,6 +106,7 @@ struct flip_handle {
   void* tmp = nullptr;
   size_t tmp_bytes = 0;
   int pcg_blocks = 0, sm_count = 0, p2g_blocks = 0, g2p_blocks = 0;
+  int solver_blocks = 0;      // CTAs of a single solve (0: pcg_blocks)
   int launches = 0;
   bool stepped = false;
 };
@@ -715,8 +716,9 @@ int flip_step(flip_handle* h, int32_t nsteps, flip_stats* stats) {
                       h->dstats, s);
     h->launches += 1;
     if (timed) FLIP_CUDA(cudaEventRecord(ev[3], s));
-    if (pa.precond == FLIP_PRECOND_MG) FLIP_CUDA(launch_pcg_mg(pa, h->mixed, h->pcg_blocks, s));
-    else FLIP_CUDA(launch_pcg(pa, h->mixed, h->pcg_blocks, s));
+    const int nsb = h->solver_blocks > 0 ? h->solver_blocks : h->pcg_blocks;
+    if (pa.precond == FLIP_PRECOND_MG) FLIP_CUDA(launch_pcg_mg(pa, h->mixed, nsb, s));
+    else FLIP_CUDA(launch_pcg(pa, h->mixed, nsb, s));
     h->launches += 1;
     if (timed) FLIP_CUDA(cudaEventRecord(ev[4], s));
     launch_g2p(h->g, h->K, h->P[h->cur], h->B, uo, h->mixed ? nullptr : h->x32, h->pff,
@@ -776,6 +778,41 @@ int flip_step(flip_handle* h, int32_t nsteps, flip_stats* stats) {
     cudaEventDestroy(t_end);
   }
   return rc;
+}
+
+int flip_set_solver_blocks(flip_handle* h, int32_t nblocks) {
+  if (!h) return fail(FLIP_E_ARG, "handle is NULL");
+  if (nblocks < 0 || nblocks > h->pcg_blocks)
+    return fail(FLIP_E_ARG, "nblocks must be in [0, " + std::to_string(h->pcg_blocks) + "]");
+  h->solver_blocks = nblocks;
+  return FLIP_OK;
+}
+
+int flip_autotune_solver(flip_handle* h, int32_t steps_per_candidate, int32_t* nblocks) {
+  if (!h) return fail(FLIP_E_ARG, "handle is NULL");
+  if (steps_per_candidate < 1) return fail(FLIP_E_ARG, "steps_per_candidate must be >= 1");
+  const int m = h->pcg_blocks;
+  const int cand[4] = {m, std::max(1, m / 2), std::max(1, m / 4), std::max(1, m / 8)};
+  int best = h->solver_blocks > 0 ? h->solver_blocks : m, first_warning = FLIP_OK;
+  double best_ms = -1.0;
+  for (int c : cand) {
+    h->solver_blocks = c;
+    flip_stats st;
+    const int rc = flip_step(h, steps_per_candidate, &st);
+    if (rc == FLIP_E_NOT_CONVERGED || rc == FLIP_E_CAPACITY) {
+      if (first_warning == FLIP_OK) first_warning = rc;
+    } else if (rc != FLIP_OK) {
+      h->solver_blocks = best;
+      return rc;
+    }
+    if (best_ms < 0.0 || st.ms_pcg < best_ms) {
+      best_ms = st.ms_pcg;
+      best = c;
+    }
+  }
+  h->solver_blocks = best;
+  if (nblocks) *nblocks = best;
+  return first_warning;
 }
 
 int flip_energy(flip_handle* h, double particle_mass, double out[3]) {

@@ -155,6 +155,8 @@ def lib():
         L.flip_solve_pressure_noalloc.argtypes = [PP, vp, vp, vp, vp, C.POINTER(i32),
                                                   C.POINTER(C.c_double)]
         L.flip_energy.argtypes = [vp, C.c_double, C.POINTER(C.c_double)]
+        L.flip_set_solver_blocks.argtypes = [vp, i32]
+        L.flip_autotune_solver.argtypes = [vp, i32, C.POINTER(i32)]
         L.flip_batch_set_team_exponent.argtypes = [vp, C.c_double]
         L.flip_batch_graph_active.argtypes = [vp]
         L.flip_batch_set_graphs.argtypes = [vp, i32]
@@ -606,6 +608,15 @@ class Simulation:
 
     def write(self, field: int, src):
         flip_write(self.h, field, src)
+
+    def set_solver_blocks(self, nblocks: int):
+        _check(lib().flip_set_solver_blocks(self.h, int(nblocks)))
+
+    def autotune_solver(self, steps_per_candidate: int = 1) -> int:
+        """Chooses the solve's CTA count by timing real steps (the scene advances)."""
+        out = C.c_int32(0)
+        _check(lib().flip_autotune_solver(self.h, int(steps_per_candidate), C.byref(out)))
+        return int(out.value)
 
     def energy(self, particle_mass: float):
         """(kinetic, potential, total) energy of the particles (Sec. 4, Fig. 10)."""

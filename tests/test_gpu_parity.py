@@ -432,3 +432,19 @@ def test_warm_start_reaches_the_cold_start_solution(mixed):
         assert e <= tol, (k, e)
     assert abs(runs[1][0][0] - runs[0][0][0]) <= 1  # the first solve starts from zero either way
     assert sum(runs[1][0][1:]) < sum(runs[0][0][1:]), (runs[1][0], runs[0][0])
+
+
+def test_solver_block_count_keeps_the_solution():
+    """The solve's CTA count (set or autotuned) changes only the order of sums."""
+    sc = S.pool_drop(48)
+    op, fp = matched(48)
+    ref = O.step(op, *sc.arrays())
+    with F.Simulation(fp, *sc.arrays()) as sim:
+        sim.set_solver_blocks(19)
+        rc, st = sim.step(1, stats=True)
+        assert rc == F.FLIP_OK
+        assert rel_l2(sim.read(F.PRESSURE_F64), ref.pressure) <= 1e-5
+        with pytest.raises(F.FlipError):
+            sim.set_solver_blocks(100000)
+        nb = sim.autotune_solver(1)
+        assert nb >= 1
