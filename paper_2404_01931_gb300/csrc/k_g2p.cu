@@ -3,7 +3,8 @@
 // the histogram of the next step's binning.
 //
 // One CTA takes one active 8x8x8 brick at a time (its particles are one
-// contiguous range after binning).  It first stages in shared memory the
+// contiguous range after binning; they stream into shared memory by bulk copies,
+// see below).  It first stages in shared memory the
 // pressure of the brick plus a one-cell halo, then, for every component, the
 // face nodes any of the brick's particles can reach (the 9x10x10 tile P2G also
 // uses): u_new (Eq. 5 with gravity and walls, face_unew's arithmetic) and
@@ -41,6 +42,75 @@ template <>
 struct PTile<false> {
   using T = float;
 };
+
+// ---------------------------------------------------------------- bulk copies
+// Particles stream into shared memory in chunks of G2P_THREADS (one per thread)
+// by cp.async.bulk (the Blackwell/Hopper bulk-copy engine), double-buffered and
+// tracked by an mbarrier per buffer, so a chunk's loads are in flight while the
+// previous chunk is processed.  A bulk copy starts and ends on 16-byte
+// boundaries: a chunk [q0, q1) is copied as [q0 & ~3, (q1 + 3) & ~3), which stays
+// inside its array (every array of the arena is padded to 256 bytes).
+constexpr int G2P_CHUNK_PAD = G2P_THREADS + 8;
+constexpr unsigned long long G2P_WAIT_NS = 1000000000ull;  // a copy that takes longer
+                                                           // is reported as a timeout
+
+__device__ __forceinline__ unsigned int smem_u32(const void* p) {
+  return (unsigned int)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned int bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned int parity) {
+  unsigned int ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for phase `parity` of the barrier; false after G2P_WAIT_NS.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned int parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_timer_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_timer_ns() - t0 > G2P_WAIT_NS) return false;
+  return true;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned int bytes,
+                                         unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// One thread: copy particles [q0, q1) of x, y, z, u, v, w into `dst` (the
+// buffer then starts at particle q0 rounded down to 4), completing on `bar`.
+__device__ __forceinline__ void issue_chunk(const PartView& P, unsigned int q0, unsigned int q1,
+                                            float (*dst)[G2P_CHUNK_PAD],
+                                            unsigned long long* bar) {
+  const unsigned int a0 = q0 & ~3u, a1 = (q1 + 3u) & ~3u;
+  const unsigned int bytes = 4u * (a1 - a0);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  mbar_expect_tx(bar, 6u * bytes);
+  const float* src[6] = {P.x, P.y, P.z, P.u, P.v, P.w};
+#pragma unroll
+  for (int a = 0; a < 6; ++a) bulk_g2s(dst[a], src[a] + a0, bytes, bar);
+}
 
 // Pressure difference p(+) - p(-) in the arithmetic of face_unew.
 __device__ __forceinline__ float pdiff(float2 hp, float2 hm) {
@@ -115,7 +185,7 @@ __device__ __forceinline__ void interp_tile(const Grid& g, float px, float py, f
 }
 
 template <bool PAIR>
-__global__ void __launch_bounds__(G2P_THREADS, 6) k_g2p(const Grid g, const StepConsts K0,
+__global__ void __launch_bounds__(G2P_THREADS, 5) k_g2p(const Grid g, const StepConsts K0,
                                                      const PartView P, const BinView B,
                                                      const float* __restrict__ uo0,
                                                      const float* __restrict__ uo1,
@@ -128,14 +198,33 @@ __global__ void __launch_bounds__(G2P_THREADS, 6) k_g2p(const Grid g, const Step
   __shared__ PT sp[G2P_PTILE];
   __shared__ float su[3][G2P_TILE];
   __shared__ float sd[3][G2P_TILE];
+  __shared__ __align__(16) float pbuf[2][6][G2P_CHUNK_PAD];
+  __shared__ __align__(8) unsigned long long bar[2];
+  __shared__ int s_abort;
   const int lane = threadIdx.x & 31;
   const unsigned int nact = st->n_active;
   float speed2 = 0.0f;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
+  }
+  __syncthreads();
+  unsigned int phase[2] = {0u, 0u};
+  unsigned int kbuf = 0;  // buffer of the next chunk
+  bool pending = false;   // a chunk copy is in flight
   for (unsigned int bi = blockIdx.x; bi < nact; bi += gridDim.x) {
     const unsigned int brick = B.active[bi];
     const int b0 = (int)(brick % (unsigned)g.bx) * BRICK;
     const int b1 = (int)((brick / (unsigned)g.bx) % (unsigned)g.by) * BRICK;
     const int b2 = (int)(brick / ((unsigned)g.bx * (unsigned)g.by)) * BRICK;
+    const unsigned int bstart = B.brick_start[brick], bend = B.brick_start[brick + 1];
+    // the brick's first chunk streams in while the tiles are staged
+    if (threadIdx.x == 0 && bstart < bend) {
+      issue_chunk(P, bstart, min(bend, bstart + G2P_THREADS), pbuf[kbuf], &bar[kbuf]);
+      pending = true;
+    }
     // pressure of cells [b - 1, b + 8] per axis (0 outside the grid: never used)
     for (int t = threadIdx.x; t < G2P_PTILE; t += G2P_THREADS) {
       const int i = b0 - 1 + t % 10, j = b1 - 1 + (t / 10) % 10, k = b2 - 1 + t / 100;
@@ -152,15 +241,30 @@ __global__ void __launch_bounds__(G2P_THREADS, 6) k_g2p(const Grid g, const Step
     stage_faces<1, PAIR>(g, K, b0, b1, b2, uo1, sp, su[1], sd[1]);
     stage_faces<2, PAIR>(g, K, b0, b1, b2, uo2, sp, su[2], sd[2]);
     __syncthreads();
-    const unsigned int bstart = B.brick_start[brick], bend = B.brick_start[brick + 1];
-    // warp-uniform trip count, so every lane takes part in the key match
-    for (unsigned int base = bstart + (threadIdx.x & ~31u); base < bend; base += G2P_THREADS) {
-      const unsigned int q = base + (unsigned)lane;
-      const bool valid = q < bend;
+    // chunk loop: CTA-uniform trip count, so every lane takes part in the key match
+    for (unsigned int c0 = bstart; c0 < bend; c0 += G2P_THREADS) {
+      const unsigned int cur = kbuf;
+      kbuf ^= 1u;
+      // the next chunk goes into the other buffer, whose readers passed the
+      // __syncthreads that ended the previous chunk
+      const unsigned int n0 = c0 + G2P_THREADS;
+      if (threadIdx.x == 0 && n0 < bend)
+        issue_chunk(P, n0, min(bend, n0 + G2P_THREADS), pbuf[kbuf], &bar[kbuf]);
+      if (!mbar_wait(&bar[cur], phase[cur])) {
+        atomicOr(&st->status, DEV_TIMEOUT);
+        s_abort = 1;
+      }
+      phase[cur] ^= 1u;
+      pending = n0 < bend;
+      const float(*pb)[G2P_CHUNK_PAD] = pbuf[cur];
+      const unsigned int a0 = c0 & ~3u;
+      const unsigned int q = c0 + threadIdx.x;
+      const bool valid = q < bend && !s_abort;
       unsigned int key = 0xffffffffu;
       if (valid) {
-        float x = P.x[q], y = P.y[q], z = P.z[q];
-        const float vp[3] = {P.u[q], P.v[q], P.w[q]};
+        const unsigned int o = q - a0;
+        float x = pb[0][o], y = pb[1][o], z = pb[2][o];
+        const float vp[3] = {pb[3][o], pb[4][o], pb[5][o]};
         const int ci = cell_of(x, g.inv_dx, g.nx);
         const int cj = cell_of(y, g.inv_dx, g.ny);
         const int ck = cell_of(z, g.inv_dx, g.nz);
@@ -204,9 +308,15 @@ __global__ void __launch_bounds__(G2P_THREADS, 6) k_g2p(const Grid g, const Step
         B.key[q] = key;
         B.rank[q] = first + (unsigned)__popc(same & ((1u << lane) - 1u));
       }
+      __syncthreads();
+      if (s_abort) break;
     }
     __syncthreads();
+    if (s_abort) break;
   }
+  // a copy still in flight (only after an abort: the chunk issued into kbuf) is
+  // waited for, boundedly
+  if (pending && threadIdx.x == 0) (void)mbar_wait(&bar[kbuf], phase[kbuf]);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) speed2 = fmaxf(speed2, __shfl_xor_sync(0xffffffffu, speed2, o));
   if (lane == 0 && speed2 > 0.0f) atomicMax(&st->max_speed_bits, __float_as_uint(sqrtf(speed2)));
