@@ -39,6 +39,14 @@ WORKLOADS = {
                    precision="fp32", cg_tol=1e-6, ir_tol=1e-8),
     "dam32": dict(desc="dam break, 32^3, block x<0.25 y<0.5", n=32, scene="dam",
                   precision="fp32", cg_tol=1e-6, ir_tol=1e-8),
+    "dam64": dict(desc="dam break, 64^3, block x<0.25 y<0.5", n=64, scene="dam",
+                  precision="fp32", cg_tol=1e-6, ir_tol=1e-8),
+    "ddam128": dict(desc="double dam break, 128^3, blocks x<0.2 and x>0.8, y<0.5", n=128,
+                    scene="ddam", precision="fp32", cg_tol=1e-6, ir_tol=1e-8),
+    "drop128": dict(desc="water drop, 128^3, sphere r=0.2 at (0.5,0.6,0.5)", n=128,
+                    scene="drop", precision="fp32", cg_tol=1e-6, ir_tol=1e-8),
+    "drop104": dict(desc="water drop, 104^3, sphere r=0.2 at (0.5,0.6,0.5)", n=104,
+                    scene="drop", precision="fp32", cg_tol=1e-6, ir_tol=1e-8),
 }
 
 # With the multigrid preconditioner, per fluid cell of level 0 and iteration
@@ -89,6 +97,10 @@ def make_scene(w):
     from paper_2404_01931_gb300 import scenes as S
     if w["scene"] == "pool":
         return S.pool_drop(w["n"])
+    if w["scene"] == "ddam":
+        return S.double_dam_break(w["n"])
+    if w["scene"] == "drop":
+        return S.water_drop(w["n"])
     return S.dam_break(w["n"])
 
 
