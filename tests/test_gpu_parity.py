@@ -1,6 +1,6 @@
 """CUDA path vs the FP64 oracle, element by element, through the C ABI.
 
-Tolerances (the spec bar, FP32 path vs FP64 oracle): grid velocities and
+Tolerances (the parity bar, FP32 path vs FP64 oracle): grid velocities and
 pressure at relative L2 <= 1e-5 per step (velocity norms floored at g*dt*sqrt(n_faces)
 because a fluid at rest has |u| ~ 0), particle positions within 1e-4 of a cell after
 10 free-running steps.  Integer outputs (cell types, particle counts, ids) are exact.
