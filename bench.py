@@ -93,15 +93,17 @@ def stage_roofline(w, np_, nfl, stage_ms, steps, peak):
     return out
 
 
-def make_scene(w):
+def make_scene(w, n=None):
+    """The workload's scene at its grid edge (or at edge n)."""
     from paper_2404_01931_gb300 import scenes as S
+    n = w["n"] if n is None else n
     if w["scene"] == "pool":
-        return S.pool_drop(w["n"])
+        return S.pool_drop(n)
     if w["scene"] == "ddam":
-        return S.double_dam_break(w["n"])
+        return S.double_dam_break(n)
     if w["scene"] == "drop":
-        return S.water_drop(w["n"])
-    return S.dam_break(w["n"])
+        return S.water_drop(n)
+    return S.dam_break(n)
 
 
 def make_params(w):
@@ -188,6 +190,33 @@ def dist_setup():
     return ws, rank, local
 
 
+def _reduce(x, ws, op):
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda") if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
+    return float(t.item())
+
+
+def max_over_ranks(x, ws):
+    """The largest value over the ranks (the job's time is the slowest rank's)."""
+    import torch.distributed as dist
+    return _reduce(x, ws, dist.ReduceOp.MAX if ws > 1 else None)
+
+
+def sum_over_ranks(x, ws):
+    import torch.distributed as dist
+    return _reduce(x, ws, dist.ReduceOp.SUM if ws > 1 else None)
+
+
+def job_rate(units, seconds, ws):
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return sum_over_ranks(units, ws) / max_over_ranks(seconds, ws)
+
+
 def cpu_baseline(w, budget_s=25.0):
     """The FP64 oracle timed on this host's cores on a bounded sample of the workload."""
     import oracle as O
@@ -226,7 +255,7 @@ def run_reference(args, w):
     n = w["n"]
     # each step: one oracle step of the workload's scene at a bounded grid edge
     ns = min(n, 64)
-    sc = S.pool_drop(ns) if w["scene"] == "pool" else S.dam_break(ns)
+    sc = make_scene(w, ns)
     op = O.Params(n=(ns, ns, ns), dx=1.0 / ns,
                   cg_tol=w["ir_tol"] if w["precision"] == "mixed" else w["cg_tol"])
     st = [a.astype(np.float64) for a in sc.arrays()]
@@ -463,13 +492,10 @@ def main():
     if ws > 1:
         dist.barrier()
     ck = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms_local = e0.elapsed_time(e1)
+    ms = max_over_ranks(ms_local, ws)
     np_ = st.n_particles if args.ppc[0] or args.ppc[1] else np_
-    value = ws * np_ * args.steps / (ms / 1e3)
+    value = job_rate(np_ * args.steps, ms_local / 1e3, ws)
 
     # end to end: host (pinned) buffers in, one step, host buffers out, every step
     e2e = None
@@ -485,11 +511,7 @@ def main():
             sim.step(1)
             F.flip_read_particles(sim.h, *host)
         el = time.perf_counter() - t0
-        if ws > 1:
-            t = torch.tensor([el], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
-        e2e = {"value": ws * np_ * args.e2e_steps / el, "unit": "particle-steps/s",
+        e2e = {"value": job_rate(np_ * args.e2e_steps, el, ws), "unit": "particle-steps/s",
                "h2d_bytes_per_step": 24 * np_, "d2h_bytes_per_step": 24 * np_,
                "steps": args.e2e_steps}
 

@@ -1,0 +1,62 @@
+"""The multi-process path of bench.py (one replica per GPU, no collective on the
+data path): rank setup from the environment, the slowest rank's time and the
+whole-job rate over two gloo ranks on the CPU."""
+import os
+import socket
+import subprocess
+import sys
+import textwrap
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+CHILD = textwrap.dedent("""
+    import os, sys, json
+    sys.path.insert(0, {root!r})
+    import torch.distributed as dist
+    import bench
+    ws, rank, local = bench.dist_setup()
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    t = 1.0 + rank                      # rank 1 is the slower one
+    units = 100 * (rank + 1)
+    out = dict(ws=ws, rank=rank, local=local, tmax=bench.max_over_ranks(t, ws),
+               total=bench.sum_over_ranks(units, ws), rate=bench.job_rate(units, t, ws))
+    dist.barrier()
+    dist.destroy_process_group()
+    print(json.dumps(out))
+""")
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def test_two_gloo_ranks_reduce_time_and_rate():
+    import json
+    port = _free_port()
+    procs = []
+    for rank in range(2):
+        env = dict(os.environ, RANK=str(rank), WORLD_SIZE="2", LOCAL_RANK=str(rank),
+                   MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+        procs.append(subprocess.Popen([sys.executable, "-c", CHILD.format(root=ROOT)], env=env,
+                                      stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True))
+    outs = []
+    for p in procs:
+        out, err = p.communicate(timeout=120)
+        assert p.returncode == 0, err
+        outs.append(json.loads(out.strip().splitlines()[-1]))
+    for r, o in enumerate(outs):
+        assert (o["ws"], o["rank"], o["local"]) == (2, r, r)
+        assert o["tmax"] == 2.0                     # the slowest rank's time
+        assert o["total"] == 300.0                  # units summed over the ranks
+        assert o["rate"] == 150.0                   # whole-job units per second
+
+
+def test_single_process_needs_no_process_group():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(3.5, 1) == 3.5
+    assert bench.job_rate(100, 2.0, 1) == 50.0
