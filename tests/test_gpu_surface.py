@@ -183,3 +183,21 @@ def test_surface_argument_errors():
         buf = np.zeros(3, np.float32)
         rc = F.lib().flip_surface_read(s.h, F.SURF_FIELD, buf.ctypes.data, buf.nbytes, 0)
         assert rc == F.FLIP_E_SIZE
+
+
+def test_sdf_follows_a_reseeding_handle():
+    """The scalar field reads the handle's current particle count, which reseeding
+    changes from step to step; the drop's mesh stays closed."""
+    sc = S.water_drop(40)
+    fp = matched(40)[1]
+    fp.ppc_min, fp.ppc_max = 3, 12
+    with F.Simulation(fp, *sc.arrays()) as sim, F.Surface(F.surface_default_params(fp)) as s:
+        for _ in range(3):
+            rc, st = sim.step(4, stats=True)
+            assert rc == F.FLIP_OK
+            s.sdf(sim)
+            nv, nt = s.mesh()
+            tri = s.read(F.SURF_TRIANGLES)
+            e = Counter((int(a), int(b)) for t in tri for a, b in ((t[0], t[1]), (t[1], t[2]), (t[2], t[0])))
+            assert nt > 100 and all(c == 1 and e.get((b, a), 0) == 1 for (a, b), c in e.items())
+        assert st.n_particles == len(sim.read(F.PX))
