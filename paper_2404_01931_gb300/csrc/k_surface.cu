@@ -25,6 +25,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/flip_surface.h"
 #include "flip_kernels.cuh"
@@ -184,21 +185,29 @@ bool build_table(McTable& T) {
   return true;
 }
 
-std::once_flag g_table_once;
-int g_table_status = FLIP_OK;
+// The table is generated once per process and uploaded to each device that
+// creates a surface object (constant memory is per device).
+std::mutex g_table_mutex;
+bool g_table_built = false, g_table_ok = false;
+McTable g_table;
+std::vector<int> g_table_devices;
 
 int ensure_table() {
-  std::call_once(g_table_once, [] {
-    McTable T;
-    if (!build_table(T)) {
-      g_table_status = sfail(FLIP_E_CUDA, "marching-cubes table generation failed");
-      return;
-    }
-    const cudaError_t e = cudaMemcpyToSymbol(c_mc, &T, sizeof(T));
-    if (e != cudaSuccess) g_table_status = scuda(e, "cudaMemcpyToSymbol(case table)");
-  });
-  if (g_table_status != FLIP_OK) flip_set_last_error_("marching-cubes table unavailable");
-  return g_table_status;
+  std::lock_guard<std::mutex> lock(g_table_mutex);
+  if (!g_table_built) {
+    g_table_ok = build_table(g_table);
+    g_table_built = true;
+  }
+  if (!g_table_ok) return sfail(FLIP_E_CUDA, "marching-cubes table generation failed");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return scuda(e, "cudaGetDevice");
+  if (std::find(g_table_devices.begin(), g_table_devices.end(), dev) != g_table_devices.end())
+    return FLIP_OK;
+  e = cudaMemcpyToSymbol(c_mc, &g_table, sizeof(g_table));
+  if (e != cudaSuccess) return scuda(e, "cudaMemcpyToSymbol(case table)");
+  g_table_devices.push_back(dev);
+  return FLIP_OK;
 }
 
 // ------------------------------------------------------------------ geometry
