@@ -267,8 +267,9 @@ int flip_autotune_solver(flip_handle* h, int32_t steps_per_candidate, int32_t* n
 int flip_energy(flip_handle* h, double particle_mass, double out[3]);
 
 /* Device bytes a scene with these parameters and np particles holds (its arena;
- * what flip_create allocates).  0 when the parameters are invalid or no device
- * is usable.  Allocates nothing. */
+ * what flip_create allocates, particle arrays at the capacity max_particles
+ * implies).  0 when the parameters are invalid or no device is usable.
+ * Allocates nothing. */
 size_t flip_footprint_bytes(const flip_params* params, int64_t np);
 
 /* Size in bytes of a field of this handle. */
