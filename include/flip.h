@@ -72,11 +72,15 @@ enum {
 
 enum {
   FLIP_PRECOND_JACOBI = 0, /* diagonal preconditioner */
-  FLIP_PRECOND_MG = 1      /* one multigrid V-cycle per iteration: levels coarsened 2x
+  FLIP_PRECOND_MG = 1,     /* one multigrid V-cycle per iteration: levels coarsened 2x
                               per axis to an extent <= 4, red-black Gauss-Seidel
                               smoothing (Sec. 3.2.3), restriction (1/16) x sum of
                               the fluid children's residuals, correction 2x the
                               parent's value; symmetric positive definite */
+  FLIP_PRECOND_RBGS = 2    /* no CG: red-black Gauss-Seidel sweeps from p = 0 (the
+                              paper's GPU solver, Sec. 3.2.3) until
+                              ||b - A p|| <= cg_tol ||b||, checked every 8 sweep pairs;
+                              cg_max_iter caps the sweep pairs; FP32 precision only */
 };
 
 typedef struct {

@@ -63,6 +63,8 @@ def lib():
         L.oracle_mg_vcycle.argtypes = [P, vp, vp, vp, C.c_int, C.c_double]
         L.oracle_pcg_mg.argtypes = [P, vp, vp, C.c_double, C.c_int, C.c_int, C.c_double, vp, vp]
         L.oracle_pcg_mg.restype = C.c_int
+        L.oracle_rbgs.argtypes = [P, vp, vp, C.c_double, C.c_int, vp, vp]
+        L.oracle_rbgs.restype = C.c_int
         L.oracle_project.argtypes = [P, C.c_int, vp, vp, vp, vp]
         L.oracle_interp.argtypes = [P, C.c_int, vp, C.c_double, C.c_double, C.c_double]
         L.oracle_interp.restype = C.c_double
@@ -315,6 +317,19 @@ def pcg_mg(params: Params, type_, b, tol=None, max_iter=None, nu=MG_NU, omega=MG
     it = lib().oracle_pcg_mg(C.byref(P), _p(type_), _p(b), P.cg_tol if tol is None else tol,
                              P.cg_max_iter if max_iter is None else max_iter, int(nu),
                              float(omega), _p(x), C.byref(rel))
+    return x, it, rel.value
+
+
+def rbgs(params: Params, type_, b, tol=None, max_pairs=None):
+    """Red-black Gauss-Seidel as the solver (Sec. 3.2.3): (x, pairs or -1, rel)."""
+    L = lib()
+    P = params.c()
+    t = np.ascontiguousarray(type_, np.uint8)
+    bb = np.ascontiguousarray(b, np.float64)
+    x = np.zeros_like(bb)
+    rel = C.c_double(0.0)
+    it = L.oracle_rbgs(C.byref(P), _p(t), _p(bb), float(params.cg_tol if tol is None else tol),
+                       int(P.cg_max_iter if max_pairs is None else max_pairs), _p(x), C.byref(rel))
     return x, it, rel.value
 
 

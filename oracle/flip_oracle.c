@@ -459,9 +459,12 @@ static int step_with_dt(const oracle_params* P, int64_t np, double* x, double* y
     double rel = 0.0;
     int iters = 0;
     if (status == 0) {
-      iters = (P->preconditioner == 1)
-                  ? oracle_pcg_mg(P, type, b, P->cg_tol, P->cg_max_iter, P->mg_nu, P->mg_omega, p, &rel)
-                  : oracle_pcg(P, type, b, P->cg_tol, P->cg_max_iter, p, &rel);
+      if (P->preconditioner == 1)
+        iters = oracle_pcg_mg(P, type, b, P->cg_tol, P->cg_max_iter, P->mg_nu, P->mg_omega, p, &rel);
+      else if (P->preconditioner == 2)
+        iters = oracle_rbgs(P, type, b, P->cg_tol, P->cg_max_iter, p, &rel);
+      else
+        iters = oracle_pcg(P, type, b, P->cg_tol, P->cg_max_iter, p, &rel);
       if (iters < 0) status = 1;
       for (int d = 0; d < 3; ++d) oracle_project(P, d, us[d], p, type, un[d]);
       const double* unc[3] = {un[0], un[1], un[2]};
@@ -679,6 +682,47 @@ int oracle_pcg_mg(const oracle_params* P, const uint8_t* type, const double* b, 
   }
   if (rel_res) *rel_res = bnorm > 0.0 ? rnorm / bnorm : 0.0;
   free(r); free(zz); free(d); free(q);
+  mg_free(lv, L);
+  return result;
+}
+
+/* Sec. 3.2.3, the paper's GPU solver: red-black Gauss-Seidel sweeps on A x = b
+ * from x = 0 (red half-sweep, then black), the residual ||b - A x|| checked
+ * after every ORACLE_RBGS_CHECK sweep pairs against tol ||b||; at most max_pairs
+ * sweep pairs.  Returns the sweep pairs taken, or -1 at the cap. */
+int oracle_rbgs(const oracle_params* P, const uint8_t* type, const double* b, double tol,
+                int max_pairs, double* x, double* rel_res) {
+  const int64_t nc = oracle_n_cells(P);
+  mg_level lv[ORACLE_MG_MAX_LEVELS];
+  const int L = mg_build(P, type, lv);
+  mg_level* v = &lv[0];
+  double* ax = (double*)malloc(sizeof(double) * (size_t)nc);
+  for (int64_t c = 0; c < nc; ++c) {
+    v->b[c] = type[c] ? b[c] : 0.0;
+    v->x[c] = 0.0;
+  }
+  const double bnorm = sqrt(dot_fluid(nc, type, v->b, v->b));
+  double rnorm = bnorm;
+  int pairs = 0, result = 0;
+  if (bnorm > 0.0) {
+    result = -1;
+    while (pairs < max_pairs || pairs == 0) {
+      for (int s = 0; s < ORACLE_RBGS_CHECK; ++s) {
+        lv_half_sweep(v, 0);
+        lv_half_sweep(v, 1);
+      }
+      pairs += ORACLE_RBGS_CHECK;
+      oracle_apply_A(P, type, v->x, ax);
+      double rr = 0.0;
+      for (int64_t c = 0; c < nc; ++c)
+        if (type[c]) rr += (v->b[c] - ax[c]) * (v->b[c] - ax[c]);
+      rnorm = sqrt(rr);
+      if (rnorm <= tol * bnorm) { result = pairs; break; }
+    }
+  }
+  for (int64_t c = 0; c < nc; ++c) x[c] = type[c] ? v->x[c] : 0.0;
+  if (rel_res) *rel_res = bnorm > 0.0 ? rnorm / bnorm : 0.0;
+  free(ax);
   mg_free(lv, L);
   return result;
 }

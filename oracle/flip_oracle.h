@@ -40,7 +40,8 @@ typedef struct {
   double cg_tol;       /* PCG stop: ||r||_2 <= cg_tol * ||b||_2 */
   int32_t cg_max_iter; /* PCG iteration cap */
   int32_t advect_source; /* 0: advect with the blended particle velocity; 1: with the grid velocity */
-  int32_t preconditioner; /* 0: Jacobi (oracle_pcg); 1: multigrid V-cycle (oracle_pcg_mg) */
+  int32_t preconditioner; /* 0: Jacobi (oracle_pcg); 1: multigrid V-cycle (oracle_pcg_mg);
+                             2: red-black Gauss-Seidel as the solver (oracle_rbgs) */
   int32_t mg_nu;          /* multigrid: red-black sweep pairs before and after the correction */
   double mg_omega;        /* multigrid: over-correction of the coarse correction */
   double cfl;             /* Sec. 3.1.4 CFL number; 0: fixed dt */
@@ -133,6 +134,14 @@ void oracle_mg_vcycle(const oracle_params* P, const uint8_t* type, const double*
 /* PCG with the V-cycle preconditioner; same stopping rule as oracle_pcg. */
 int oracle_pcg_mg(const oracle_params* P, const uint8_t* type, const double* b, double tol,
                   int max_iter, int nu, double omega, double* x, double* rel_res);
+
+/* The paper's GPU solver (Sec. 3.2.3): red-black Gauss-Seidel sweeps from x = 0,
+ * ||b - A x|| <= tol ||b|| checked every ORACLE_RBGS_CHECK sweep pairs, at most
+ * max_pairs pairs (oracle_params.preconditioner == 2 in oracle_step).  Returns the
+ * pairs taken, or -1 at the cap. */
+#define ORACLE_RBGS_CHECK 8
+int oracle_rbgs(const oracle_params* P, const uint8_t* type, const double* b, double tol,
+                int max_pairs, double* x, double* rel_res);
 
 /* Eq. 5: pressure update of one component. */
 void oracle_project(const oracle_params* P, int comp, const double* u_star, const double* p,

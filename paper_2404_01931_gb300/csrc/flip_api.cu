@@ -184,8 +184,11 @@ int check_params(const flip_params* p, bool need_particles_prm) {
   if (p->precision == FLIP_PREC_MIXED_IR && (!(p->ir_tol > 0.0) || !(p->cg_tol < 1.0)))
     return fail(FLIP_E_ARG, "mixed mode needs ir_tol > 0 and a refinement trigger cg_tol < 1");
   if (need_particles_prm) {
-    if (p->preconditioner != FLIP_PRECOND_JACOBI && p->preconditioner != FLIP_PRECOND_MG)
+    if (p->preconditioner != FLIP_PRECOND_JACOBI && p->preconditioner != FLIP_PRECOND_MG &&
+        p->preconditioner != FLIP_PRECOND_RBGS)
       return fail(FLIP_E_ARG, "unknown preconditioner");
+    if (p->preconditioner == FLIP_PRECOND_RBGS && p->precision != FLIP_PREC_FP32)
+      return fail(FLIP_E_ARG, "the red-black Gauss-Seidel solver runs in FP32 precision only");
     if (p->preconditioner == FLIP_PRECOND_MG && (p->mg_smooth < 1 || p->mg_smooth > 8))
       return fail(FLIP_E_ARG, "mg_smooth must be in [1, 8]");
     if (p->warm_start != 0 && p->warm_start != 1)
@@ -349,7 +352,7 @@ void carve(flip_handle* h, Carver& cv) {
     h->b32 = cv.take<float>(nc);
   }
   h->partials = cv.take<double>((size_t)PCG_SLOTS * (size_t)h->pcg_blocks);
-  if (h->prm.preconditioner == FLIP_PRECOND_MG) {
+  if (h->prm.preconditioner != FLIP_PRECOND_JACOBI) {
     MgArgs& m = h->mg;
     for (int l = 0; l < m.nlev; ++l) {
       MgLevel& L = m.lv[l];
@@ -479,7 +482,7 @@ PcgArgs pcg_args(flip_handle* h) {
   a.timeout_ns = 5000000000ull;
   a.precond = h->prm.preconditioner;
   a.warm_start = h->prm.warm_start;
-  if (a.precond == FLIP_PRECOND_MG) {
+  if (a.precond != FLIP_PRECOND_JACOBI) {
     a.mg = h->mg;
     a.mg.lv[0].t = h->type;
   }
@@ -610,7 +613,7 @@ int flip_create(const flip_params* params, const float* x, const float* y, const
   }
   e = pcg_max_blocks(&h->pcg_blocks, &h->sm_count);
   if (e != cudaSuccess) return cleanup(cuda_fail(e, "occupancy query"));
-  if (params->preconditioner == FLIP_PRECOND_MG) {
+  if (params->preconditioner != FLIP_PRECOND_JACOBI) {
     e = pcg_mg_check_occupancy();
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "multigrid kernel occupancy"));
     setup_mg(h->mg, h->mg_dims, solver_params(*params));
@@ -717,7 +720,7 @@ int flip_step(flip_handle* h, int32_t nsteps, flip_stats* stats) {
     h->launches += 1;
     if (timed) FLIP_CUDA(cudaEventRecord(ev[3], s));
     const int nsb = h->solver_blocks > 0 ? h->solver_blocks : h->pcg_blocks;
-    if (pa.precond == FLIP_PRECOND_MG) FLIP_CUDA(launch_pcg_mg(pa, h->mixed, nsb, s));
+    if (pa.precond != FLIP_PRECOND_JACOBI) FLIP_CUDA(launch_pcg_mg(pa, h->mixed, nsb, s));
     else FLIP_CUDA(launch_pcg(pa, h->mixed, nsb, s));
     h->launches += 1;
     if (timed) FLIP_CUDA(cudaEventRecord(ev[4], s));
@@ -852,7 +855,7 @@ size_t flip_footprint_bytes(const flip_params* params, int64_t np) {
   for (int d = 0; d < 3; ++d) tmp.nf[d] = n_faces(tmp.g, d);
   tmp.mixed = params->precision == FLIP_PREC_MIXED_IR;
   if (pcg_max_blocks(&tmp.pcg_blocks, &tmp.sm_count) != cudaSuccess) return 0;
-  if (params->preconditioner == FLIP_PRECOND_MG) setup_mg(tmp.mg, tmp.mg_dims, *params);
+  if (params->preconditioner != FLIP_PRECOND_JACOBI) setup_mg(tmp.mg, tmp.mg_dims, *params);
   Carver measure;
   carve(&tmp, measure);
   return measure.off;
@@ -1301,7 +1304,7 @@ int flip_batch_step(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t ns
     const bool mixed = g & 1, mg = g & 2;
     std::vector<int> sc;
     for (int s = 0; s < n; ++s)
-      if (hs[s]->mixed == mixed && (hs[s]->prm.preconditioner == FLIP_PRECOND_MG) == mg)
+      if (hs[s]->mixed == mixed && (hs[s]->prm.preconditioner != FLIP_PRECOND_JACOBI) == mg)
         sc.push_back(s);
     for (size_t c = 0; c < sc.size(); c += (size_t)b->max_blocks) {
       Launch L{mixed, mg, {}, 0};

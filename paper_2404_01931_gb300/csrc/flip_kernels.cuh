@@ -53,6 +53,7 @@ __device__ __forceinline__ StepConsts step_consts(const StepConsts& K) {
 }
 
 constexpr int PCG_SLOTS = 7;
+constexpr int PRECOND_RBGS = 2;   // FLIP_PRECOND_RBGS: red-black Gauss-Seidel as the solver
 
 // Multigrid V-cycle preconditioner (levels coarsened 2x per axis until the
 // largest extent is <= 4; red-black Gauss-Seidel smoothing).

@@ -1567,12 +1567,98 @@ __device__ void solve_mg(const PcgArgs& A, Shared& sh, CtaMg& sm, SolveState& S)
   S.bnorm = bnorm;
 }
 
+// The paper's GPU solver (Sec. 3.2.3): red-black Gauss-Seidel sweeps on A p = b
+// from p = 0 (FP32), on the colour-split level-0 storage with the smoother's
+// half-sweeps, until ||b - A p|| <= tol ||b||; the residual is taken every
+// RBGS_CHECK sweep pairs and the sweep pairs are capped at max_iter.
+constexpr int RBGS_CHECK = 8;
+
+__device__ __noinline__ void solve_rbgs(const PcgArgs& A, Shared& sh, SolveState& S) {
+  const MgArgs& M = A.mg;
+  const MgLevel& L0 = M.lv[0];
+  const MgLevel& L1 = M.nlev > 1 ? M.lv[1] : M.lv[0];
+  float* z = L0.x;
+  float* r = L0.b;
+  if (!build_levels(A, sh)) { S.ok = false; return; }
+  {
+    FF bb;
+    for_fluid0(A, [&](const SCell& e, unsigned int, int n) {
+      const float bc = A.b32[n];
+      r[e.idx] = bc;
+      z[e.idx] = 0.0f;
+      bb.add_prod(bc, bc);
+    });
+    F2 v[1] = {f2_of(bb)};
+    publish<1>(A, 4, v, sh);
+  }
+  if (!gsync(A)) { S.ok = false; return; }
+  double bnorm = 0.0, rnorm = 0.0;
+  {
+    double s0[1];
+    gather<1>(A, 4, s0, sh);
+    if (threadIdx.x == 0) {
+      bnorm = sqrt(fmax(s0[0], 0.0));
+      rnorm = bnorm;
+      sh.flag = (bnorm == 0.0) ? 1 : 0;
+    }
+  }
+  __syncthreads();
+  bool conv = sh.flag == 1;
+  int it = 0;
+  while (!conv) {
+    for (int k = 0; k < RBGS_CHECK; ++k) {
+      sweep_split<NORMAL>(M, L0, L1, 0, 0, nullptr);
+      if (!gsync(A)) { S.ok = false; return; }
+      sweep_split<NORMAL>(M, L0, L1, 0, 1, nullptr);
+      if (!gsync(A)) { S.ok = false; return; }
+    }
+    it += RBGS_CHECK;
+    FF rr;
+    const SV v0 = sview(L0);
+    for_fluid0(A, [&](const SCell& e, unsigned int code, int) {
+      int nb[6];
+      snbr(v0, e, nb);
+      float xv[6];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) xv[q] = z[nb[q]];
+      const float rc = resid(A.s, code_cnt(code), code, r[e.idx], z[e.idx], xv);
+      rr.add_prod(rc, rc);
+    });
+    {
+      F2 v[1] = {f2_of(rr)};
+      publish<1>(A, 5, v, sh);
+    }
+    if (!gsync(A)) { S.ok = false; return; }
+    {
+      double s[1];
+      gather<1>(A, 5, s, sh);
+      if (threadIdx.x == 0) {
+        rnorm = sqrt(fmax(s[0], 0.0));
+        if (rnorm <= A.tol * bnorm) sh.flag = 1;
+        else if (it >= A.max_iter) sh.flag = 3;
+        else sh.flag = 0;
+      }
+    }
+    __syncthreads();
+    if (sh.flag == 1) conv = true;
+    if (sh.flag == 3) break;
+  }
+  for_fluid0(A, [&](const SCell& e, unsigned int, int n) { A.x32[n] = z[e.idx]; });
+  S.iters = it;
+  S.conv = conv;
+  S.rel = bnorm > 0.0 ? rnorm / bnorm : 0.0;
+  S.bnorm = bnorm;
+}
+
 template <bool MIXED>
 __device__ void solve_scene_mg(const PcgArgs& A, Shared& sh, CtaMg& sm) {
   const long long ncells = (long long)A.g.nx * A.g.ny * A.g.nz;
   const bool singular = A.check_singular && ((long long)A.stats->n_fluid == ncells);
   SolveState S;
-  if (!singular) solve_mg<MIXED>(A, sh, sm, S);
+  if (!singular) {
+    if (!MIXED && A.precond == PRECOND_RBGS) solve_rbgs(A, sh, S);
+    else solve_mg<MIXED>(A, sh, sm, S);
+  }
   if (team_rank() == 0 && threadIdx.x == 0) {
     int st = 0;
     if (singular) st |= DEV_SINGULAR;

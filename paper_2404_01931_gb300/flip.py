@@ -36,6 +36,7 @@ FLIP_ADVECT_PARTICLE = 0
 FLIP_ADVECT_GRID = 1
 FLIP_PRECOND_JACOBI = 0
 FLIP_PRECOND_MG = 1
+FLIP_PRECOND_RBGS = 2
 
 (PX, PY, PZ, PU, PV, PW, PID, U_OLD, V_OLD, W_OLD, U_NEW, V_NEW, W_NEW, PRESSURE,
  PRESSURE_F64, RHS, CELL_TYPE) = range(17)

@@ -190,3 +190,27 @@ def test_graph_replay_equals_plain_steps():
     for a, b_ in zip(plain, graph):
         for x, y in zip(a, b_):
             assert rel_l2(y, x, 1e-3) <= 1e-4
+
+
+def test_batch_with_a_gauss_seidel_scene():
+    """A scene using the red-black Gauss-Seidel solver shares the batched launch of
+    the multigrid scenes and takes the same pressure it takes alone."""
+    sc1 = S.dam_break(24, 0.4, 0.5)
+    sc2 = S.dam_break(32, 0.4, 0.5, seed=2)
+    fp1 = matched(24, preconditioner=F.FLIP_PRECOND_RBGS, cg_max_iter=5000, cg_tol=1e-4)[1]
+    fp2 = matched(32)[1]
+    alone = []
+    for fp, sc in ((fp1, sc1), (fp2, sc2)):
+        with F.Simulation(fp, *sc.arrays()) as sim:
+            sim.step(2)
+            alone.append(sim.read(F.PRESSURE_F64))
+    sims = [F.Simulation(fp1, *sc1.arrays()), F.Simulation(fp2, *sc2.arrays())]
+    try:
+        with F.Batch(2) as b:
+            rc, st = b.step(sims, 2, stats=True)
+            assert rc == F.FLIP_OK
+        for s, p in zip(sims, alone):
+            assert rel_l2(s.read(F.PRESSURE_F64), p) <= 1e-4
+    finally:
+        for s in sims:
+            s.close()

@@ -448,3 +448,34 @@ def test_solver_block_count_keeps_the_solution():
             sim.set_solver_blocks(100000)
         nb = sim.autotune_solver(1)
         assert nb >= 1
+
+
+@pytest.mark.parametrize("n", [48, (40, 24, 56)])
+def test_rbgs_solver_iterates_match_the_oracle(n):
+    """The paper's GPU solver (red-black Gauss-Seidel): after exactly 16 sweep pairs
+    (tolerance out of reach) the pressure equals the oracle's to FP32 rounding."""
+    sc = S.pool_drop(n) if np.isscalar(n) else S.random_velocities(
+        S.box(n, (0.0, 0.0, 0.0), (0.6, 0.45, 0.9), seed=3), 0.3, 5)
+    op, fp = matched(n, cg_tol=1e-30, cg_max_iter=16, preconditioner=F.FLIP_PRECOND_RBGS)
+    ref = O.step(op, *sc.arrays())
+    assert ref.cg_iterations == -1
+    with pytest.warns(RuntimeWarning):
+        got = gpu_step(fp, sc.arrays())
+    assert got["rc"] == F.FLIP_E_NOT_CONVERGED and got["stats"].cg_iterations == 16
+    assert rel_l2(got["p"], ref.pressure) <= 1e-5
+
+
+def test_rbgs_solver_converges_like_the_oracle():
+    sc = S.dam_break(32)
+    op, fp = matched(32, cg_tol=1e-4, cg_max_iter=20000, preconditioner=F.FLIP_PRECOND_RBGS)
+    ref = O.step(op, *sc.arrays())
+    got = gpu_step(fp, sc.arrays())
+    assert got["rc"] == F.FLIP_OK and ref.cg_iterations > 0
+    gi = got["stats"].cg_iterations
+    assert abs(gi - ref.cg_iterations) <= 8, (gi, ref.cg_iterations)
+    e = rel_l2(got["p"], ref.pressure)
+    assert e <= (1e-5 if gi == ref.cg_iterations else 1e-3), e
+    with pytest.raises(F.FlipError):
+        bad = matched(16, preconditioner=F.FLIP_PRECOND_RBGS)[1]
+        bad.precision = F.FLIP_PREC_MIXED_IR
+        F.Simulation(bad, *S.dam_break(16).arrays())

@@ -523,3 +523,57 @@ def test_pcg_mg_iterations_nearly_grid_independent(oracle_mod, n, cap):
     assert 0 < it_mg <= cap and it_mg * 6 < it_j, (it_mg, it_j)
     xj, _, _ = O.pcg(P, r.type, r.rhs, tol=1e-13, max_iter=20000)
     assert np.linalg.norm(x - xj) <= 1e-6 * np.linalg.norm(xj)
+
+
+# ------------------------------------------------------------ red-black Gauss-Seidel solver
+
+@pytest.mark.parametrize("n,seed", [((6, 5, 4), 1), ((8, 8, 8), 2)])
+def test_rbgs_matches_dense_solve(oracle_mod, n, seed):
+    O = oracle_mod
+    P = _params(O, n, dt=0.01, rho=2.0)
+    t = S.random_mask(n, 0.6, seed).astype(np.uint8)
+    A, fl = _dense_A(O, P, t)
+    rng = np.random.default_rng(seed)
+    b = np.zeros(t.shape)
+    b.ravel()[fl] = rng.normal(size=fl.size)
+    x, it, rel = O.rbgs(P, t, b, tol=1e-12, max_pairs=20000)
+    assert it > 0 and it % 8 == 0 and rel <= 1e-12
+    want = np.linalg.solve(A, b.ravel()[fl])
+    assert np.abs(x.ravel()[fl] - want).max() <= 1e-9 * np.abs(want).max()
+
+
+def test_rbgs_is_red_then_black_gauss_seidel(oracle_mod):
+    """Eight sweep pairs equal the textbook Gauss-Seidel on the assembled matrix with
+    the rows taken red (i+j+k even) first, then black."""
+    O = oracle_mod
+    n = (5, 4, 3)
+    P = _params(O, n, dt=0.02, rho=1.0)
+    t = S.random_mask(n, 0.7, 3).astype(np.uint8)
+    A, fl = _dense_A(O, P, t)
+    rng = np.random.default_rng(4)
+    b = np.zeros(t.shape)
+    b.ravel()[fl] = rng.normal(size=fl.size)
+    x, it, _ = O.rbgs(P, t, b, tol=1e-300, max_pairs=8)
+    assert it == -1
+    k, j, i = np.unravel_index(fl, t.shape)
+    red = ((i + j + k) % 2) == 0
+    order = np.concatenate([np.flatnonzero(red), np.flatnonzero(~red)])
+    y = np.zeros(fl.size)
+    bb = b.ravel()[fl]
+    for _ in range(8):
+        for r in order:
+            y[r] = (bb[r] - A[r] @ y + A[r, r] * y[r]) / A[r, r]
+    assert np.abs(x.ravel()[fl] - y).max() <= 1e-12 * max(np.abs(y).max(), 1e-300)
+
+
+def test_rbgs_cap_and_zero_rhs(oracle_mod):
+    O = oracle_mod
+    n = (6, 6, 6)
+    P = _params(O, n)
+    t = S.random_mask(n, 0.5, 7).astype(np.uint8)
+    b = np.zeros(t.shape)
+    x, it, rel = O.rbgs(P, t, b)
+    assert it == 0 and not x.any()
+    b.ravel()[np.flatnonzero(t.ravel())] = 1.0
+    x, it, rel = O.rbgs(P, t, b, tol=1e-30, max_pairs=24)
+    assert it == -1 and 0 < rel < 1
