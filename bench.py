@@ -430,6 +430,9 @@ def main():
                     help="adaptive time step with this CFL number (0: fixed dt = 1/240)")
     ap.add_argument("--ppc", type=int, nargs=2, default=(0, 0), metavar=("MIN", "MAX"),
                     help="reseed cells to at least MIN and at most MAX particles (0 0: off)")
+    ap.add_argument("--precond", default="mg", choices=["mg", "jacobi", "rbgs"],
+                    help="pressure solver: multigrid-preconditioned CG, Jacobi-PCG, or "
+                         "red-black Gauss-Seidel iterations (the paper's GPU solver; FP32)")
     ap.add_argument("--mg-smooth", type=int, default=2,
                     help="multigrid red-black sweep pairs before and after the correction")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
@@ -470,6 +473,10 @@ def main():
     prm.warm_start = 1 if args.warm_start else 0
     prm.cfl = args.cfl
     prm.mg_smooth = args.mg_smooth
+    prm.preconditioner = {"mg": F.FLIP_PRECOND_MG, "jacobi": F.FLIP_PRECOND_JACOBI,
+                          "rbgs": F.FLIP_PRECOND_RBGS}[args.precond]
+    if args.precond != "mg":
+        prm.cg_max_iter = 100000
     prm.ppc_min, prm.ppc_max = args.ppc
     sim = F.Simulation(prm, *sc.arrays())
     stream = torch.cuda.ExternalStream(sim.stream)
@@ -583,7 +590,7 @@ def main():
                        "l2": "inputs larger than L2 (particles + grids > 1 GB); no flush",
                        "pressure_start": "last solve's pressure (warm start)" if args.warm_start
                        else "zero (cold start)",
-                       "mg_smooth": args.mg_smooth,
+                       "mg_smooth": args.mg_smooth, "solver": args.precond,
                        "time_step": f"adaptive, CFL number {args.cfl}" if args.cfl > 0
                        else "fixed 1/240",
                        "reseeding": f"{args.ppc[0]}..{args.ppc[1]} particles per cell"
