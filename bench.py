@@ -67,6 +67,8 @@ MG_IR_BYTES_PER_SOLVE = 40
 # dram__bytes_write.sum of the first timed step's solve, a single-pass capture);
 # see profiles/k_pcg_mg_pool256_dram.md.  Reported for that workload only.
 PCG_DRAM_BYTES_POOL256 = 6.181e9
+# GB300's nominal HBM3e bandwidth, reported beside the measured copy bandwidth
+NOMINAL_HBM_GBS = 7900.0
 
 
 def stage_roofline(w, np_, nfl, stage_ms, steps, peak):
@@ -89,6 +91,7 @@ def stage_roofline(w, np_, nfl, stage_ms, steps, peak):
         t = stage_ms[k] / steps / 1e3
         gbs = b / t / 1e9 if t > 0 else None
         out[k] = {"achieved_gbs": gbs, "frac": gbs / peak if gbs else None,
+                  "frac_of_nominal": gbs / NOMINAL_HBM_GBS if gbs else None,
                   "algorithmic_bytes": b}
     return out
 
@@ -607,6 +610,8 @@ def main():
                          "bound": "hbm", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                         "nominal_peak": NOMINAL_HBM_GBS,
+                         "frac_of_nominal": (achieved / NOMINAL_HBM_GBS) if achieved else None,
                          "algorithmic_bytes_per_launch": pcg_bytes / args.steps,
                          "traffic": PCG_DRAM_BYTES_POOL256 if args.workload == "pool256"
                          else None},
