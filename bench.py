@@ -444,12 +444,16 @@ def main():
                     help="skip the surface-reconstruction measurement")
     ap.add_argument("--warm-start", action="store_true",
                     help="start every solve from the last solve's pressure (flip_params.warm_start)")
+    ap.add_argument("--precision", default=None, choices=["fp32", "mixed"],
+                    help="override the workload's precision (fp32: the plain FP32 form)")
     ap.add_argument("--cg-tol", type=float, default=None,
                     help="override the workload's cg_tol (mixed mode: refinement trigger)")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
     if args.cg_tol is not None:
         w["cg_tol"] = args.cg_tol
+    if args.precision is not None:
+        w["precision"] = args.precision
     if args.impl == "reference":
         return run_reference(args, w)
     if args.batch:
