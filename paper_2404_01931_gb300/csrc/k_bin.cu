@@ -108,6 +108,18 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_cell_local_scan(const Grid g, 
     const int j = j0 + ((2 * lane + h) & 7);
     if (j >= g.ny || k >= g.nz) continue;
     uint8_t* row = type + (size_t)g.nx * (j + (size_t)g.ny * k);
+    if (i0 + BRICK <= g.nx && (reinterpret_cast<uintptr_t>(row + i0) & 7u) == 0) {
+      // the row's eight types in one 8-byte store (byte x = cell i0 + x)
+      unsigned long long word = 0ull;
+#pragma unroll
+      for (int x = 0; x < 8; ++x) {
+        const bool f = c[8 * h + x] > 0u;
+        word |= (unsigned long long)f << (8 * x);
+        nfl += f;
+      }
+      *reinterpret_cast<unsigned long long*>(row + i0) = word;
+      continue;
+    }
 #pragma unroll
     for (int x = 0; x < 8; ++x) {
       const int i = i0 + x;
