@@ -133,8 +133,11 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_cell_local_scan(const Grid g, 
   if (lane == 0) b.brick_fluid[brick] = (unsigned)nfl;
 }
 
-// One CTA of 1024 threads walks all bricks in chunks: exclusive scan of the
-// brick totals (particle offsets), compaction of the bricks holding particles.
+// One CTA of 1024 threads walks all bricks in chunks of 8 per thread: exclusive
+// scan of the brick totals (particle offsets), compaction of the bricks holding
+// particles.  A thread scans its 8 consecutive bricks serially, the CTA scans the
+// thread totals.
+constexpr int BSCAN_PER = 8;
 __global__ void __launch_bounds__(1024) k_brick_scan(const Grid g, const BinView b, DevStats* st) {
   __shared__ unsigned int wc[32], wf[32];
   __shared__ unsigned int fl_tot;
@@ -142,12 +145,20 @@ __global__ void __launch_bounds__(1024) k_brick_scan(const Grid g, const BinView
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if (threadIdx.x == 0) fl_tot = 0;
   unsigned int run = 0, run_act = 0, fluid = 0;
-  for (unsigned int base = 0; base < nb; base += blockDim.x) {
-    const unsigned int idx = base + threadIdx.x;
-    const unsigned int c = idx < nb ? b.brick_count[idx] : 0u;
-    const unsigned int flag = c > 0u;
-    fluid += idx < nb ? b.brick_fluid[idx] : 0u;
-    unsigned int ic = c, iff = flag;
+  const unsigned int chunk = blockDim.x * BSCAN_PER;
+  for (unsigned int base = 0; base < nb; base += chunk) {
+    const unsigned int i0 = base + threadIdx.x * BSCAN_PER;
+    unsigned int c[BSCAN_PER];
+    unsigned int tc = 0, tf = 0;
+#pragma unroll
+    for (int q = 0; q < BSCAN_PER; ++q) {
+      const unsigned int idx = i0 + q;
+      c[q] = idx < nb ? b.brick_count[idx] : 0u;
+      fluid += idx < nb ? b.brick_fluid[idx] : 0u;
+      tc += c[q];
+      tf += c[q] > 0u;
+    }
+    unsigned int ic = tc, iff = tf;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const unsigned int t1 = __shfl_up_sync(0xffffffffu, ic, o);
@@ -156,16 +167,23 @@ __global__ void __launch_bounds__(1024) k_brick_scan(const Grid g, const BinView
     }
     if (lane == 31) { wc[warp] = ic; wf[warp] = iff; }
     __syncthreads();
-    unsigned int oc = 0, of = 0, tc = 0, tf = 0;
+    unsigned int oc = 0, of = 0, sc = 0, sf = 0;
     for (int w = 0; w < nw; ++w) {
       if (w < warp) { oc += wc[w]; of += wf[w]; }
-      tc += wc[w];
-      tf += wf[w];
+      sc += wc[w];
+      sf += wf[w];
     }
-    if (idx < nb) b.brick_start[idx] = run + oc + ic - c;
-    if (flag) b.active[run_act + of + iff - 1] = idx;
-    run += tc;
-    run_act += tf;
+    unsigned int pc = run + oc + ic - tc, pf = run_act + of + iff - tf;
+#pragma unroll
+    for (int q = 0; q < BSCAN_PER; ++q) {
+      const unsigned int idx = i0 + q;
+      if (idx >= nb) break;
+      b.brick_start[idx] = pc;
+      pc += c[q];
+      if (c[q]) b.active[pf++] = idx;
+    }
+    run += sc;
+    run_act += sf;
     __syncthreads();
   }
   atomicAdd(&fl_tot, fluid);

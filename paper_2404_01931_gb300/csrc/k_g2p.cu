@@ -125,8 +125,7 @@ __device__ __forceinline__ float pdiff(float hp, float hm) { return __fsub_rn(hp
 template <int D, bool PAIR>
 __device__ __forceinline__ void stage_faces(const Grid& g, const StepConsts& K, int b0, int b1,
                                             int b2, const float* __restrict__ uo,
-                                            const typename PTile<PAIR>::T* sp, float* su,
-                                            float* sd) {
+                                            const typename PTile<PAIR>::T* sp, float2* sud) {
   constexpr int TX = FaceTile<D>::X, TY = FaceTile<D>::Y, N = FaceTile<D>::N;
   const int o0 = (D == 0) ? b0 : b0 - 1, o1 = (D == 1) ? b1 : b1 - 1, o2 = (D == 2) ? b2 : b2 - 1;
   const int FX = g.nx + (D == 0), FY = g.ny + (D == 1), FZ = g.nz + (D == 2);
@@ -148,8 +147,7 @@ __device__ __forceinline__ void stage_faces(const Grid& g, const StepConsts& K, 
       }
       du = __fsub_rn(un, uov);
     }
-    su[t] = un;
-    sd[t] = du;
+    sud[t] = make_float2(un, du);
   }
 }
 
@@ -158,7 +156,7 @@ __device__ __forceinline__ void stage_faces(const Grid& g, const StepConsts& K, 
 template <int D>
 __device__ __forceinline__ void interp_tile(const Grid& g, float px, float py, float pz, int ci,
                                             int cj, int ck, int li, int lj, int lk,
-                                            const float* su, const float* sd, float& U,
+                                            const float2* sud, float& U,
                                             float& dU) {
   constexpr int TX = FaceTile<D>::X, TY = FaceTile<D>::Y;
   const AxisW ax = axis_weights<D, 0>(px, g.inv_dx, ci, g.nx);
@@ -176,8 +174,9 @@ __device__ __forceinline__ void interp_tile(const Grid& g, float px, float py, f
       for (int dx = 0; dx < 2; ++dx) {
         const float w = __fmul_rn(wx[dx], wyz);
         const int t = t0 + dx + TX * (dy + TY * dz);
-        s_u = __fmaf_rn(w, su[t], s_u);
-        s_d = __fmaf_rn(w, sd[t], s_d);
+        const float2 ud = sud[t];
+        s_u = __fmaf_rn(w, ud.x, s_u);
+        s_d = __fmaf_rn(w, ud.y, s_d);
       }
     }
   U = s_u;
@@ -196,8 +195,7 @@ __global__ void __launch_bounds__(G2P_THREADS, 5) k_g2p(const Grid g, const Step
   const StepConsts K = step_consts(K0);
   using PT = typename PTile<PAIR>::T;
   __shared__ PT sp[G2P_PTILE];
-  __shared__ float su[3][G2P_TILE];
-  __shared__ float sd[3][G2P_TILE];
+  __shared__ float2 sud[3][G2P_TILE];  // (u_new, u_new - u_old) per face node
   __shared__ __align__(16) float pbuf[2][6][G2P_CHUNK_PAD];
   __shared__ __align__(8) unsigned long long bar[2];
   __shared__ int s_abort;
@@ -237,9 +235,9 @@ __global__ void __launch_bounds__(G2P_THREADS, 5) k_g2p(const Grid g, const Step
       sp[t] = v;
     }
     __syncthreads();
-    stage_faces<0, PAIR>(g, K, b0, b1, b2, uo0, sp, su[0], sd[0]);
-    stage_faces<1, PAIR>(g, K, b0, b1, b2, uo1, sp, su[1], sd[1]);
-    stage_faces<2, PAIR>(g, K, b0, b1, b2, uo2, sp, su[2], sd[2]);
+    stage_faces<0, PAIR>(g, K, b0, b1, b2, uo0, sp, sud[0]);
+    stage_faces<1, PAIR>(g, K, b0, b1, b2, uo1, sp, sud[1]);
+    stage_faces<2, PAIR>(g, K, b0, b1, b2, uo2, sp, sud[2]);
     __syncthreads();
     // chunk loop: CTA-uniform trip count, so every lane takes part in the key match
     for (unsigned int c0 = bstart; c0 < bend; c0 += G2P_THREADS) {
@@ -275,9 +273,9 @@ __global__ void __launch_bounds__(G2P_THREADS, 5) k_g2p(const Grid g, const Step
         const int lj = min(max(cj - b1, 0), BRICK - 1);
         const int lk = min(max(ck - b2, 0), BRICK - 1);
         float U[3], dU[3];
-        interp_tile<0>(g, x, y, z, ci, cj, ck, li, lj, lk, su[0], sd[0], U[0], dU[0]);
-        interp_tile<1>(g, x, y, z, ci, cj, ck, li, lj, lk, su[1], sd[1], U[1], dU[1]);
-        interp_tile<2>(g, x, y, z, ci, cj, ck, li, lj, lk, su[2], sd[2], U[2], dU[2]);
+        interp_tile<0>(g, x, y, z, ci, cj, ck, li, lj, lk, sud[0], U[0], dU[0]);
+        interp_tile<1>(g, x, y, z, ci, cj, ck, li, lj, lk, sud[1], U[1], dU[1]);
+        interp_tile<2>(g, x, y, z, ci, cj, ck, li, lj, lk, sud[2], U[2], dU[2]);
         const float r = K.flip_ratio, r1 = 1.0f - K.flip_ratio;
         float vn[3], adv[3];
 #pragma unroll
