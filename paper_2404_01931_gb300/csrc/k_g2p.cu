@@ -164,7 +164,9 @@ __device__ __forceinline__ void interp_tile(const Grid& g, float px, float py, f
   const AxisW az = axis_weights<D, 2>(pz, g.inv_dx, ck, g.nz);
   const int t0 = (li + ax.off) + TX * ((lj + ay.off) + TY * (lk + az.off));
   const float wx[2] = {ax.w0, ax.w1}, wy[2] = {ay.w0, ay.w1}, wz[2] = {az.w0, az.w1};
-  float s_u = 0.0f, s_d = 0.0f;
+  // (U, dU) accumulate together: one packed two-lane FMA per node, each lane
+  // rounded like __fmaf_rn
+  float2 s = make_float2(0.0f, 0.0f);
 #pragma unroll
   for (int dz = 0; dz < 2; ++dz)
 #pragma unroll
@@ -174,13 +176,11 @@ __device__ __forceinline__ void interp_tile(const Grid& g, float px, float py, f
       for (int dx = 0; dx < 2; ++dx) {
         const float w = __fmul_rn(wx[dx], wyz);
         const int t = t0 + dx + TX * (dy + TY * dz);
-        const float2 ud = sud[t];
-        s_u = __fmaf_rn(w, ud.x, s_u);
-        s_d = __fmaf_rn(w, ud.y, s_d);
+        s = __ffma2_rn(make_float2(w, w), sud[t], s);
       }
     }
-  U = s_u;
-  dU = s_d;
+  U = s.x;
+  dU = s.y;
 }
 
 template <bool PAIR>

@@ -47,13 +47,15 @@ __device__ __forceinline__ void p2g_cell(const Grid& g, const PartView& P, unsig
                                          int lj, int lk, float* tnum, float* tden) {
   constexpr int NX = (D == 0) ? 2 : 3, NY = (D == 1) ? 2 : 3, NZ = (D == 2) ? 2 : 3;
   constexpr int TX = Tile<D>::X, TY = Tile<D>::Y;
-  float an[NZ][NY][NX], ad[NZ][NY][NX];
+  // (num, den) of a node accumulate together: one packed two-lane FMA per node,
+  // each lane rounded like __fmaf_rn
+  float2 acc[NZ][NY][NX];
 #pragma unroll
   for (int z = 0; z < NZ; ++z)
 #pragma unroll
     for (int y = 0; y < NY; ++y)
 #pragma unroll
-      for (int x = 0; x < NX; ++x) an[z][y][x] = ad[z][y][x] = 0.0f;
+      for (int x = 0; x < NX; ++x) acc[z][y][x] = make_float2(0.0f, 0.0f);
   const float* vel = (D == 0) ? P.u : (D == 1) ? P.v : P.w;
   for (unsigned int q = beg; q < end; ++q) {
     const float px = P.x[q], py = P.y[q], pz = P.z[q], pv = vel[q];
@@ -66,12 +68,10 @@ __device__ __forceinline__ void p2g_cell(const Grid& g, const PartView& P, unsig
 #pragma unroll
       for (int y = 0; y < NY; ++y) {
         const float wyz = __fmul_rn(wy[y], wz[z]);
-        const float t = __fmul_rn(wyz, pv);
+        const float2 tw = make_float2(__fmul_rn(wyz, pv), wyz);
 #pragma unroll
-        for (int x = 0; x < NX; ++x) {
-          an[z][y][x] = __fmaf_rn(wx[x], t, an[z][y][x]);
-          ad[z][y][x] = __fmaf_rn(wx[x], wyz, ad[z][y][x]);
-        }
+        for (int x = 0; x < NX; ++x)
+          acc[z][y][x] = __ffma2_rn(make_float2(wx[x], wx[x]), tw, acc[z][y][x]);
       }
   }
 #pragma unroll
@@ -80,10 +80,10 @@ __device__ __forceinline__ void p2g_cell(const Grid& g, const PartView& P, unsig
     for (int y = 0; y < NY; ++y)
 #pragma unroll
       for (int x = 0; x < NX; ++x)
-        if (ad[z][y][x] != 0.0f) {
+        if (acc[z][y][x].y != 0.0f) {
           const int t = (li + x) + TX * ((lj + y) + TY * (lk + z));
-          atomicAdd(tnum + t, an[z][y][x]);
-          atomicAdd(tden + t, ad[z][y][x]);
+          atomicAdd(tnum + t, acc[z][y][x].x);
+          atomicAdd(tden + t, acc[z][y][x].y);
         }
 }
 
