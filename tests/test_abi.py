@@ -99,6 +99,22 @@ def test_grid_size_checks(F):
         F.flip_create(p, x, x, x, x, x, x, allocator=None)
 
 
+def test_largest_grid_edge(F):
+    """Every face index must fit in 31 bits ((n+1)^3 < 2^31): 1289^3 passes the
+    parameter checks (and then needs a device), 1290^3 is refused before any device
+    call."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("host-only check (a GPU would allocate the grid)")
+    x = np.zeros(4, np.float32)
+    with pytest.raises(F.FlipError) as ei:
+        F.flip_create(F.default_params(1290), x, x, x, x, x, x, allocator=None)
+    assert ei.value.code == F.FLIP_E_ARG and "too large" in str(ei.value)
+    with pytest.raises(F.FlipError) as ei:
+        F.flip_create(F.default_params(1289), x, x, x, x, x, x, allocator=None)
+    assert ei.value.code == F.FLIP_E_NOGPU
+
+
 def test_mismatched_particle_arrays(F):
     p = F.default_params(16)
     with pytest.raises(ValueError):
