@@ -11,6 +11,9 @@
 // halo (9x10x10 nodes per component), and the CTA adds the tile to the global
 // (num, den) accumulators with vector float2 atomics.  The normalisation
 // num/den happens in k_finalize, which also clears the accumulators.
+// A warp takes 8 x-cells by 4 z-planes of one y-row, and the tile's planes are
+// TILE_PLANE = 104 nodes apart (8 mod 32 banks): the 32 lanes of every atomic
+// then fall on 32 different banks.
 #include "flip_kernels.cuh"
 
 namespace flipk {
@@ -24,7 +27,11 @@ struct Tile {
   static constexpr int Z = (D == 2) ? 9 : 10;
   static constexpr int N = X * Y * Z;
 };
-constexpr int TILE_PAD = 904;
+constexpr int TILE_PLANE = 104;              // >= X * Y of every component; 8 mod 32
+constexpr int TILE_PAD = 10 * TILE_PLANE;     // up to 10 planes
+static_assert(TILE_PLANE % 32 == 8, "lanes 8 apart in z must take the next 8 banks");
+static_assert(Tile<0>::X * Tile<0>::Y <= TILE_PLANE && Tile<1>::X * Tile<1>::Y <= TILE_PLANE &&
+                  Tile<2>::X * Tile<2>::Y <= TILE_PLANE, "a plane of the tile fits");
 
 // Weights of one axis over the node window of a cell: the component's own axis
 // has 2 nodes (c, c+1); the other axes 3 nodes (c-1, c, c+1).
@@ -46,7 +53,7 @@ __device__ __forceinline__ void p2g_cell(const Grid& g, const PartView& P, unsig
                                          unsigned int end, int ci, int cj, int ck, int li,
                                          int lj, int lk, float* tnum, float* tden) {
   constexpr int NX = (D == 0) ? 2 : 3, NY = (D == 1) ? 2 : 3, NZ = (D == 2) ? 2 : 3;
-  constexpr int TX = Tile<D>::X, TY = Tile<D>::Y;
+  constexpr int TX = Tile<D>::X;
   // (num, den) of a node accumulate together: one packed two-lane FMA per node,
   // each lane rounded like __fmaf_rn
   float2 acc[NZ][NY][NX];
@@ -81,7 +88,7 @@ __device__ __forceinline__ void p2g_cell(const Grid& g, const PartView& P, unsig
 #pragma unroll
       for (int x = 0; x < NX; ++x)
         if (acc[z][y][x].y != 0.0f) {
-          const int t = (li + x) + TX * ((lj + y) + TY * (lk + z));
+          const int t = (li + x) + TX * (lj + y) + TILE_PLANE * (lk + z);
           atomicAdd(tnum + t, acc[z][y][x].x);
           atomicAdd(tden + t, acc[z][y][x].y);
         }
@@ -94,11 +101,13 @@ __device__ __forceinline__ void flush_tile(const Grid& g, int b0, int b1, int b2
   const int o0 = (D == 0) ? b0 : b0 - 1, o1 = (D == 1) ? b1 : b1 - 1, o2 = (D == 2) ? b2 : b2 - 1;
   const int FX = g.nx + (D == 0), FY = g.ny + (D == 1), FZ = g.nz + (D == 2);
   for (int t = threadIdx.x; t < N; t += P2G_THREADS) {
-    const float dn = tden[t];
+    const int ta = t % TX, tb = (t / TX) % TY, tc = t / (TX * TY);
+    const int ts = ta + TX * tb + TILE_PLANE * tc;
+    const float dn = tden[ts];
     if (dn == 0.0f) continue;
-    const int a = o0 + t % TX, b = o1 + (t / TX) % TY, c = o2 + t / (TX * TY);
+    const int a = o0 + ta, b = o1 + tb, c = o2 + tc;
     if (a < 0 || b < 0 || c < 0 || a >= FX || b >= FY || c >= FZ) continue;
-    atomicAdd(acc + (a + FX * (b + FY * c)), make_float2(tnum[t], dn));
+    atomicAdd(acc + (a + FX * (b + FY * c)), make_float2(tnum[ts], dn));
   }
 }
 
@@ -119,12 +128,15 @@ __global__ void __launch_bounds__(P2G_THREADS, 4) k_p2g(const Grid g, const Part
     }
     __syncthreads();
     const unsigned int bstart = B.brick_start[brick], bend = B.brick_start[brick + 1];
-    for (int l = threadIdx.x; l < BRICK_CELLS; l += P2G_THREADS) {
+    static_assert(BRICK_CELLS == 2 * P2G_THREADS, "two passes of 8 x 8 x 4 cells");
+    for (int pass = 0; pass < 2; ++pass) {
+      const int li = threadIdx.x & 7, lk = ((threadIdx.x >> 3) & 3) + 4 * pass,
+                lj = threadIdx.x >> 5;
+      const int l = li + BRICK * (lj + BRICK * lk);
       const unsigned int key = brick * BRICK_CELLS + (unsigned)l;
       const unsigned int beg = bstart + B.local_start[key];
       const unsigned int end = (l < BRICK_CELLS - 1) ? bstart + B.local_start[key + 1] : bend;
       if (beg == end) continue;
-      const int li = l & 7, lj = (l >> 3) & 7, lk = l >> 6;
       const int ci = b0 + li, cj = b1 + lj, ck = b2 + lk;
       p2g_cell<0>(g, P, beg, end, ci, cj, ck, li, lj, lk, tnum[0], tden[0]);
       p2g_cell<1>(g, P, beg, end, ci, cj, ck, li, lj, lk, tnum[1], tden[1]);
