@@ -242,11 +242,35 @@ def cpu_baseline(w, budget_s=25.0):
                 st = [r.x, r.y, r.z, r.u, r.v, r.w]
                 steps += 1
             el = time.perf_counter() - t0
-            return {"value": sc.n_particles * steps / el, "unit": "particle-steps/s",
-                    "cores": O.num_threads(), "kind": "oracle",
-                    "sample": f"{steps} oracle step(s) of the same scene at {ns}^3 "
-                              f"({sc.n_particles} particles), FP64, {el:.1f} s"}
+            out = {"value": sc.n_particles * steps / el, "unit": "particle-steps/s",
+                   "cores": O.num_threads(), "kind": "oracle",
+                   "sample": f"{steps} oracle step(s) of the same scene at {ns}^3 "
+                             f"({sc.n_particles} particles), FP64, {el:.1f} s"}
+            out["single_thread"] = cpu_single_thread(w)
+            return out
     return None
+
+
+def cpu_single_thread(w):
+    """The same oracle on one host thread: one step of the scene at 64^3 (or the
+    workload's edge if smaller)."""
+    import oracle as O
+    from paper_2404_01931_gb300 import scenes as S
+    ns = min(w["n"], 64)
+    sc = S.pool_drop(ns) if w["scene"] == "pool" else S.dam_break(ns)
+    op = O.Params(n=(ns, ns, ns), dx=1.0 / ns, cg_tol=w["ir_tol"] if w["precision"] == "mixed"
+                  else w["cg_tol"])
+    cores = O.num_threads()
+    O.set_num_threads(1)
+    try:
+        t0 = time.perf_counter()
+        O.step(op, *sc.arrays(), fields=False)
+        el = time.perf_counter() - t0
+    finally:
+        O.set_num_threads(cores)
+    return {"value": sc.n_particles / el, "unit": "particle-steps/s", "cores": 1,
+            "sample": f"1 oracle step of the same scene at {ns}^3 ({sc.n_particles} "
+                      f"particles), FP64, one thread, {el:.1f} s"}
 
 
 def run_reference(args, w):

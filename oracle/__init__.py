@@ -77,6 +77,8 @@ def lib():
                                      C.POINTER(OracleFields), C.POINTER(OracleStats)]
         L.oracle_step_ex.restype = C.c_int
         L.oracle_num_threads.restype = C.c_int
+        L.oracle_set_num_threads.argtypes = [C.c_int]
+        L.oracle_set_num_threads.restype = None
         L.oracle_energy.argtypes = [C.c_int64, vp, vp, vp, vp, vp, vp, vp, C.c_double, vp]
         L.oracle_energy.restype = None
         L.oracle_blobby_kernel.argtypes = [C.c_double]
@@ -432,3 +434,8 @@ def marching_cubes(phi, origin, h, iso=0.0) -> Mesh:
 
 def num_threads() -> int:
     return int(lib().oracle_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads for the oracle's later OpenMP regions (for single-thread timings)."""
+    lib().oracle_set_num_threads(int(n))

@@ -29,6 +29,14 @@ int oracle_num_threads(void) {
 #endif
 }
 
+void oracle_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 int64_t oracle_n_cells(const oracle_params* P) {
   return (int64_t)P->n[0] * P->n[1] * P->n[2];
 }

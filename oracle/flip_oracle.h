@@ -206,6 +206,8 @@ int oracle_step_ex(const oracle_params* P, int64_t* np, int64_t capacity, double
                    oracle_stats* stats);
 
 int oracle_num_threads(void);
+/* Threads of the calling thread's later parallel regions (n > 0; timing only). */
+void oracle_set_num_threads(int n);
 
 #ifdef __cplusplus
 }

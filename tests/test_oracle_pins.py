@@ -577,3 +577,15 @@ def test_rbgs_cap_and_zero_rhs(oracle_mod):
     b.ravel()[np.flatnonzero(t.ravel())] = 1.0
     x, it, rel = O.rbgs(P, t, b, tol=1e-30, max_pairs=24)
     assert it == -1 and 0 < rel < 1
+
+
+def test_oracle_thread_count_setter():
+    """The single-thread timing of the bench's CPU baseline relies on the setter."""
+    import oracle as O
+    n0 = O.num_threads()
+    try:
+        O.set_num_threads(1)
+        assert O.num_threads() == 1
+    finally:
+        O.set_num_threads(n0)
+    assert O.num_threads() == n0
