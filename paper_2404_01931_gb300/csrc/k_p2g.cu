@@ -14,6 +14,8 @@
 // A warp takes 8 x-cells by 4 z-planes of one y-row, and the tile's planes are
 // TILE_PLANE = 104 nodes apart (8 mod 32 banks): the 32 lanes of every atomic
 // then fall on 32 different banks.
+#include <algorithm>
+
 #include "flip_kernels.cuh"
 
 namespace flipk {
@@ -178,15 +180,15 @@ __global__ void k_divergence(const Grid g, const StepConsts K0, const uint8_t* _
                              const float* __restrict__ uo2, float* b32, double* b64, float* x32,
                              double* x64, float2* pff, unsigned int* bar, DevStats* st) {
   const StepConsts K = step_consts(K0);
-  const long long nc = (long long)g.nx * g.ny * g.nz;
-  if (blockIdx.x == 0 && threadIdx.x < BAR_WORDS) {
-    bar[threadIdx.x] = 0u;  // the grid barrier's arrival counter and spare words
+  if (blockIdx.x == 0 && blockIdx.y == 0) {
+    // the grid barrier's arrival counter and spare words (a block may have 32 threads)
+    for (unsigned int t = threadIdx.x; t < BAR_WORDS; t += blockDim.x) bar[t] = 0u;
     if (threadIdx.x == 0) st->max_speed_bits = 0u;
   }
-  for (long long cl = blockIdx.x * (long long)blockDim.x + threadIdx.x; cl < nc;
-       cl += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)cl;
-    const int i = c % g.nx, j = (c / g.nx) % g.ny, k = c / (g.nx * g.ny);
+  // block (j, k) walks the x-row of cells (i, j, k): no index divisions
+  const int j = (int)blockIdx.x, k = (int)blockIdx.y;
+  for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+    const int c = i + g.nx * (j + g.ny * k);
     if (x32) x32[c] = 0.0f;
     if (x64) x64[c] = 0.0;
     if (pff) pff[c] = make_float2(0.0f, 0.0f);
@@ -306,9 +308,10 @@ void launch_divergence(const Grid& g, const StepConsts& k, const uint8_t* type,
                        const float* const uo[3], float* b32, double* b64, float* x32,
                        double* x64, float2* pff, unsigned int* bar, DevStats* st,
                        cudaStream_t s) {
-  const long long nc = (long long)g.nx * g.ny * g.nz;
-  k_divergence<<<grid_for(nc, 256), 256, 0, s>>>(g, k, type, uo[0], uo[1], uo[2], b32, b64, x32,
-                                                 x64, pff, bar, st);
+  // one block per x-row, threads along x (nx <= 2048, rows ny x nz <= 2048 x 2048)
+  const int threads = std::min(256, (g.nx + 31) / 32 * 32);
+  k_divergence<<<dim3((unsigned)g.ny, (unsigned)g.nz), threads, 0, s>>>(
+      g, k, type, uo[0], uo[1], uo[2], b32, b64, x32, x64, pff, bar, st);
 }
 
 void launch_u_new(const Grid& g, const StepConsts& k, int d, const float* uo, const float* p32,
