@@ -66,7 +66,7 @@ MG_IR_BYTES_PER_SOLVE = 40
 # DRAM traffic of one k_pcg_mg launch on the 256^3 pool (dram__bytes_read.sum +
 # dram__bytes_write.sum of the first timed step's solve, a single-pass capture);
 # see profiles/k_pcg_mg_pool256_dram.md.  Reported for that workload only.
-PCG_DRAM_BYTES_POOL256 = 6.181e9
+PCG_DRAM_BYTES_POOL256 = 7.603e9
 # GB300's nominal HBM3e bandwidth, reported beside the measured copy bandwidth
 NOMINAL_HBM_GBS = 7900.0
 
