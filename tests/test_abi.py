@@ -150,3 +150,26 @@ def test_default_params_are_valid_for_every_edge(F, n):
     with pytest.raises(F.FlipError) as ei:
         F.flip_create(p, x, x, x, x, x, x, allocator=None)
     assert ei.value.code == F.FLIP_E_NOGPU
+
+
+def test_no_library_no_fallback():
+    """Without the shared library every entry point raises: there is no CPU path."""
+    import subprocess
+    import sys
+    code = (
+        "import numpy as np\n"
+        "from paper_2404_01931_gb300 import flip as F\n"
+        "F.LIB_PATH = '/nonexistent/libflip_gb300.so'\n"
+        "x = np.zeros(4, np.float32)\n"
+        "for call in (lambda: F.lib(), lambda: F.default_params(16),\n"
+        "             lambda: F.flip_create(F.FlipParams(), x, x, x, x, x, x, allocator=None)):\n"
+        "    try:\n"
+        "        call()\n"
+        "    except RuntimeError as e:\n"
+        "        assert 'not built' in str(e), e\n"
+        "    else:\n"
+        "        raise SystemExit('an entry point ran without the library')\n"
+        "print('ok')\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout + r.stderr
