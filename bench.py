@@ -220,6 +220,20 @@ def job_rate(units, seconds, ws):
     return sum_over_ranks(units, ws) / max_over_ranks(seconds, ws)
 
 
+def shard_scenes(weights, n_ranks):
+    """Host-side router of independent scenes over ranks (one GPU each): longest
+    processing time first, each scene to the least-loaded rank (ties: the lower rank).
+    Deterministic, so every rank computes the same plan with no communication.
+    Returns each rank's scene indices in ascending order."""
+    load = [0.0] * n_ranks
+    out = [[] for _ in range(n_ranks)]
+    for i in sorted(range(len(weights)), key=lambda i: (-weights[i], i)):
+        r = min(range(n_ranks), key=lambda r: (load[r], r))
+        out[r].append(i)
+        load[r] += weights[i]
+    return [sorted(o) for o in out]
+
+
 def cpu_baseline(w, budget_s=25.0):
     """The FP64 oracle timed on this host's cores on a bounded sample of the workload."""
     import oracle as O
@@ -312,13 +326,23 @@ def run_batch(args):
     """64 independent dam-break scenes, edges {32,48,64,80,96} and fluid fraction
     0.2-0.5 by seed, stepped together (one batched solve launch per step)."""
     import torch
+    import torch.distributed as dist
 
     import __graft_entry__
-    __graft_entry__.build()
+    ws, rank, local = dist_setup()
+    if rank == 0 or ws == 1:
+        __graft_entry__.build()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist.barrier()
+        __graft_entry__.build()
     from paper_2404_01931_gb300 import flip as F
     from paper_2404_01931_gb300 import scenes as S
-    torch.cuda.set_device(0)
-    scenes = S.batch_scenes(args.batch, seed=0)
+    every = S.batch_scenes(args.batch, seed=0)
+    # N GPUs: the scenes are sharded by the router, with no data-path collective
+    mine = shard_scenes([sc.n_particles for sc in every], ws)[rank]
+    scenes = [every[i] for i in mine]
     sims = []
     for sc in scenes:
         p = F.default_params(sc.n[0])
@@ -331,37 +355,52 @@ def run_batch(args):
         b.step(sims, args.warmup)
     exponent = b.autotune(sims, 1) if args.autotune else 1.0
     torch.cuda.synchronize()
-    clocks = ClockSampler(0)
+    clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     rc, _ = b.step(sims, args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
     ck = clocks.stop()
-    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(e0.elapsed_time(e1), ws)
     # iteration counts and the solve time from one more step with statistics (untimed)
     rc_st, st = b.step(sims, 1, stats=True)
     rc = rc or rc_st
-    edges = sorted({sc.n[0] for sc in scenes})
+    edges = sorted({sc.n[0] for sc in every})
     # the same scenes stepped one at a time through flip_step (the plain per-scene form)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for sim in sims:
         sim.step(args.steps)
         sim.sync()
-    seq_s = time.perf_counter() - t0
-    seq_value = npart * args.steps / seq_s
-    out = {"metric": "FLIP particle-steps/s", "value": npart * args.steps / (ms / 1e3),
-           "unit": "particle-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+    seq_value = job_rate(npart * args.steps, time.perf_counter() - t0, ws)
+    units = sum_over_ranks(npart * args.steps, ws)
+    rc = int(max_over_ranks(rc, ws))
+    if rank != 0:
+        b.close()
+        for s in sims:
+            s.close()
+        return
+    npart_all = sum(sc.n_particles for sc in every)
+    out = {"metric": "FLIP particle-steps/s", "value": units / (ms / 1e3),
+           "unit": "particle-steps/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": f"batch of {len(scenes)} dam-break scenes, edges {edges}, "
-                                  "fluid fraction 0.2-0.5 by seed", "particles": npart,
-                      "cells": sum(int(np.prod(sc.n)) for sc in scenes),
-                      "precision": "FP32 (float-pair dot products)", "preconditioner": "multigrid"},
+           "config": {"workload": f"batch of {len(every)} dam-break scenes, edges {edges}, "
+                                  "fluid fraction 0.2-0.5 by seed", "particles": npart_all,
+                      "cells": sum(int(np.prod(sc.n)) for sc in every),
+                      "precision": "FP32 (float-pair dot products)", "preconditioner": "multigrid",
+                      "parallelism": f"scenes sharded over {ws} GPU(s) by the host-side router "
+                                     "(longest first to the least-loaded rank), one batch "
+                                     "per GPU, no data-path collective"},
            "team_exponent": exponent,
            "cg_iterations_per_scene_step": sum(s.cg_iterations for s in st) / len(st),
            "ms_pcg_per_step": st[0].ms_pcg,
@@ -378,61 +417,95 @@ def run_batch(args):
 
 def run_serve(args):
     """Step requests arriving as a Poisson process over resident scenes of uneven
-    size, served by the continuous-batching server."""
+    size, served by the continuous-batching server.  With N GPUs the router places
+    each scene on one rank (its server), and each rank serves the requests for its
+    scenes; latencies and totals are gathered on rank 0."""
     import torch
+    import torch.distributed as dist
 
     import __graft_entry__
-    __graft_entry__.build()
+    ws, rank, local = dist_setup()
+    if rank == 0 or ws == 1:
+        __graft_entry__.build()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist.barrier()
+        __graft_entry__.build()
     from paper_2404_01931_gb300 import flip as F
     from paper_2404_01931_gb300 import scenes as S
-    torch.cuda.set_device(0)
     rng = np.random.default_rng(0)
     lo, hi = 48, args.serve_max_edge
-    t_gen = time.perf_counter()
-    srv = F.Server(int(args.budget_gb * (1 << 30)), args.max_batch)
-    ids, npart = [], []
+    specs = []
     for k in range(args.serve):
         n = int(round(np.exp(rng.uniform(np.log(lo), np.log(hi)))))
-        f = rng.uniform(0.2, 0.5)
+        specs.append((n, rng.uniform(0.2, 0.5)))
+    mine = set(shard_scenes([n ** 3 * f for n, f in specs], ws)[rank])
+    t_gen = time.perf_counter()
+    srv = F.Server(int(args.budget_gb * (1 << 30)), args.max_batch)
+    sid, npart = {}, [0] * len(specs)
+    for k, (n, f) in enumerate(specs):
+        if k not in mine:
+            continue
         side = float(np.sqrt(f))
         sc = S.dam_break(n, side, side, seed=k)
         p = F.default_params(n)
         p.precision = F.FLIP_PREC_MIXED_IR
         p.cg_tol, p.ir_tol = 1e-3, 1e-8
-        ids.append(srv.add_scene(p, *sc.arrays()))
-        npart.append(sc.n_particles)
+        sid[k] = srv.add_scene(p, *sc.arrays())
+        npart[k] = sc.n_particles
     srv.drain()
     t_gen = time.perf_counter() - t_gen
     resident, used = srv.usage()
-    # Poisson arrivals, uniform scene choice
+    # Poisson arrivals, uniform scene choice (the same draws on every rank)
     gaps = rng.exponential(1.0 / args.rate, args.requests)
+    choice = rng.integers(0, len(specs), args.requests)
+    if ws > 1:
+        dist.barrier()
     start = srv.now() + 0.2
     arrivals = start + np.cumsum(gaps)
-    choice = rng.integers(0, len(ids), args.requests)
-    clocks = ClockSampler(0)
+    reqs = [q for q in range(args.requests) if int(choice[q]) in mine]
+    clocks = ClockSampler(local)
     clocks.start()
-    tickets = [srv.submit(ids[c], float(t)) for c, t in zip(choice, arrivals)]
+    tickets = [srv.submit(sid[int(choice[q])], float(arrivals[q])) for q in reqs]
     infos = [srv.wait(t) for t in tickets]
     ck = clocks.stop()
-    lat = np.array([i.t_done - i.t_arrival for i in infos]) * 1e3
-    served = sum(npart[c] for c in choice)
-    span = max(i.t_done for i in infos) - float(arrivals[0])
+    part = dict(lat=[(i.t_done - i.t_arrival) * 1e3 for i in infos],
+                batch=[i.batch_size for i in infos],
+                failed=int(sum(i.status != F.FLIP_OK for i in infos)),
+                served=float(sum(npart[int(choice[q])] for q in reqs)),
+                span=(max(i.t_done for i in infos) - float(arrivals[reqs[0]])) if reqs else 0.0,
+                resident=resident, used=used, particles=int(sum(npart)), setup=t_gen)
+    parts = [part]
+    if ws > 1:
+        parts = [None] * ws
+        dist.all_gather_object(parts, part)
+    srv.close()
+    if rank != 0:
+        return
+    lat = np.array([v for q in parts for v in q["lat"]])
+    span = max(q["span"] for q in parts)
+    served = sum(q["served"] for q in parts)
     out = {"metric": "FLIP particle-steps/s", "value": served / span, "unit": "particle-steps/s",
-           "n_gpus": 1, "steps": args.requests, "warmup": 0,
+           "n_gpus": ws, "steps": args.requests, "warmup": 0,
            "ms_per_step": span * 1e3 / args.requests, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": f"serving: {args.serve} resident dam-break scenes, edges "
                                   f"log-uniform in [{lo}, {hi}], Poisson arrivals at "
                                   f"{args.rate}/s, uniform scene choice, mixed precision",
                       "budget_gb": args.budget_gb, "max_batch": args.max_batch,
-                      "resident_scenes": resident, "resident_gb": used / (1 << 30),
-                      "particles_total": int(sum(npart)), "setup_s": round(t_gen, 1)},
+                      "resident_scenes": sum(q["resident"] for q in parts),
+                      "resident_gb": sum(q["used"] for q in parts) / (1 << 30),
+                      "particles_total": sum(q["particles"] for q in parts),
+                      "setup_s": round(max(q["setup"] for q in parts), 1),
+                      "parallelism": f"scenes placed on {ws} GPU(s) by the host-side router "
+                                     "(longest first to the least-loaded rank), one server "
+                                     "per GPU, no data-path collective"},
            "latency_ms": {"p50": float(np.percentile(lat, 50)),
                           "p99": float(np.percentile(lat, 99)), "max": float(lat.max())},
-           "mean_batch": float(np.mean([i.batch_size for i in infos])),
-           "failed": int(sum(i.status != F.FLIP_OK for i in infos)), "clocks": ck}
+           "mean_batch": float(np.mean([b for q in parts for b in q["batch"]])),
+           "failed": sum(q["failed"] for q in parts), "clocks": ck}
     print(json.dumps(out), flush=True)
-    srv.close()
 
 
 def main():

@@ -60,3 +60,66 @@ def test_single_process_needs_no_process_group():
     import bench
     assert bench.max_over_ranks(3.5, 1) == 3.5
     assert bench.job_rate(100, 2.0, 1) == 50.0
+
+
+def test_router_partitions_and_balances():
+    """The host-side router of batched and served scenes: every scene on exactly one
+    rank, the plan deterministic, and each rank's load within the largest scene of
+    the mean (longest-first greedy)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import numpy as np
+    rng = np.random.default_rng(5)
+    w = [int(v) for v in rng.integers(1, 1000, size=64)]
+    for n in (1, 2, 3, 4, 8):
+        plan = bench.shard_scenes(w, n)
+        assert plan == bench.shard_scenes(w, n)
+        flat = sorted(i for p in plan for i in p)
+        assert flat == list(range(len(w)))
+        loads = [sum(w[i] for i in p) for p in plan]
+        assert max(loads) - sum(w) / n <= max(w)
+    assert bench.shard_scenes([5, 5], 4) == [[0], [1], [], []]
+    assert bench.shard_scenes([], 2) == [[], []]
+
+
+ROUTER_CHILD = textwrap.dedent("""
+    import os, sys, json
+    sys.path.insert(0, {root!r})
+    import torch.distributed as dist
+    import bench
+    from paper_2404_01931_gb300 import scenes as S
+    ws, rank, local = bench.dist_setup()
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    every = S.batch_scenes(12, seed=0)
+    mine = bench.shard_scenes([sc.n_particles for sc in every], ws)[rank]
+    parts = [None] * ws
+    dist.all_gather_object(parts, mine)
+    units = sum(every[i].n_particles for i in mine)
+    out = dict(rank=rank, mine=mine, parts=parts, total=bench.sum_over_ranks(units, ws),
+               want=sum(sc.n_particles for sc in every))
+    dist.barrier()
+    dist.destroy_process_group()
+    print(json.dumps(out))
+""")
+
+
+def test_two_gloo_ranks_shard_the_batch():
+    """Each rank takes its share of the batch from the same plan, computed locally."""
+    import json
+    port = _free_port()
+    procs = []
+    for rank in range(2):
+        env = dict(os.environ, RANK=str(rank), WORLD_SIZE="2", LOCAL_RANK=str(rank),
+                   MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+        procs.append(subprocess.Popen([sys.executable, "-c", ROUTER_CHILD.format(root=ROOT)],
+                                      env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                                      text=True))
+    outs = []
+    for p in procs:
+        out, err = p.communicate(timeout=180)
+        assert p.returncode == 0, err
+        outs.append(json.loads(out.strip().splitlines()[-1]))
+    a, b = outs
+    assert a["parts"] == b["parts"] == [a["mine"], b["mine"]]
+    assert sorted(a["mine"] + b["mine"]) == list(range(12)) and not set(a["mine"]) & set(b["mine"])
+    assert a["total"] == b["total"] == a["want"]          # every particle counted once
