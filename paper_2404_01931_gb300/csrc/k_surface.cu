@@ -438,28 +438,46 @@ __global__ void __launch_bounds__(SDF_THREADS) k_sdf(const SGrid g, const SBins 
     s_beg[wid][lane] = incl - cnt;
     s_p0[wid][lane] = p0;
     __syncwarp();
-    float sk[SDF_G], s0[SDF_G], s1[SDF_G], s2[SDF_G];
+    // per corner q: (sum k, sum k ex) and (sum k ey, sum k ez); corners go in
+    // pairs through packed two-lane FP32 operations, each lane rounded like the
+    // scalar operation
+    static_assert(SDF_G % 2 == 0, "corners in pairs");
+    float2 a01[SDF_G], a23[SDF_G];
+    float2 xq[SDF_G / 2];  // minus the corners' x (P.x + (-x) rounds as P.x - x)
 #pragma unroll
-    for (int q = 0; q < SDF_G; ++q) sk[q] = s0[q] = s1[q] = s2[q] = 0.0f;
+    for (int q = 0; q < SDF_G; ++q) a01[q] = a23[q] = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int u = 0; u < SDF_G / 2; ++u)
+      xq[u] = make_float2(-(x0 + g.h * (float)(2 * u)), -(x0 + g.h * (float)(2 * u + 1)));
+    const float2 one = make_float2(1.0f, 1.0f), m_inv = make_float2(-B.inv_R2, -B.inv_R2);
     int r = 0;  // this lane's current row: only moves forward
     for (unsigned int f = lane; f < total; f += 32) {
       while (f >= s_end[wid][r]) ++r;
       const float4 P = pos[s_p0[wid][r] + (f - s_beg[wid][r])];
-      const float ey = P.y - yc, ez = P.z - zc;
-      const float r2 = ey * ey + ez * ez;
+      const float ey = __fsub_rn(P.y, yc), ez = __fsub_rn(P.z, zc);
+      const float r2 = __fmaf_rn(ez, ez, __fmul_rn(ey, ey));
+      const float2 eyz = make_float2(ey, ez);
 #pragma unroll
-      for (int q = 0; q < SDF_G; ++q) {
-        const float ex = P.x - (x0 + g.h * (float)q);
-        const float dd = ex * ex + r2;
-        if (q < ng && dd < B.R2) {
-          const float t = 1.0f - dd * B.inv_R2;
-          const float kk = t * t * t;
-          sk[q] += kk;
-          s0[q] += kk * ex;
-          s1[q] += kk * ey;
-          s2[q] += kk * ez;
-        }
+      for (int u = 0; u < SDF_G / 2; ++u) {
+        const float2 ex = __fadd2_rn(make_float2(P.x, P.x), xq[u]);
+        const float2 dd = __ffma2_rn(ex, ex, make_float2(r2, r2));
+        const float2 t = __ffma2_rn(dd, m_inv, one);
+        float2 kk = __fmul2_rn(__fmul2_rn(t, t), t);
+        if (!(2 * u < ng && dd.x < B.R2)) kk.x = 0.0f;
+        if (!(2 * u + 1 < ng && dd.y < B.R2)) kk.y = 0.0f;
+        a01[2 * u] = __ffma2_rn(make_float2(kk.x, kk.x), make_float2(1.0f, ex.x), a01[2 * u]);
+        a23[2 * u] = __ffma2_rn(make_float2(kk.x, kk.x), eyz, a23[2 * u]);
+        a01[2 * u + 1] = __ffma2_rn(make_float2(kk.y, kk.y), make_float2(1.0f, ex.y), a01[2 * u + 1]);
+        a23[2 * u + 1] = __ffma2_rn(make_float2(kk.y, kk.y), eyz, a23[2 * u + 1]);
       }
+    }
+    float sk[SDF_G], s0[SDF_G], s1[SDF_G], s2[SDF_G];
+#pragma unroll
+    for (int q = 0; q < SDF_G; ++q) {
+      sk[q] = a01[q].x;
+      s0[q] = a01[q].y;
+      s1[q] = a23[q].x;
+      s2[q] = a23[q].y;
     }
 #pragma unroll
     for (int q = 0; q < SDF_G; ++q) {
