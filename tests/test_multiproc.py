@@ -123,3 +123,22 @@ def test_two_gloo_ranks_shard_the_batch():
     assert a["parts"] == b["parts"] == [a["mine"], b["mine"]]
     assert sorted(a["mine"] + b["mine"]) == list(range(12)) and not set(a["mine"]) & set(b["mine"])
     assert a["total"] == b["total"] == a["want"]          # every particle counted once
+
+
+def test_clock_summary_from_nvidia_smi_lines():
+    """The bench's clock record: median SM clock, maximum clock, and the throttle
+    reasons seen active (a run with hw or thermal slowdown is rejected; sw_power_cap is
+    kept and noted)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    na = "Not Active"
+    lines = [f"0, 2070, 2070, 950.1, 0x0000000000000000, {na}, {na}, {na}, {na}",
+             f"0, 1980, 2070, 1390.0, 0x0000000000000004, {na}, {na}, {na}, Active",
+             f"0, 2070, 2070, 1001.2, 0x0000000000000000, {na}, {na}, {na}, {na}",
+             "garbage", "0, [N/A], 2070, 0, 0x0, x, x, x, x"]
+    s = bench.ClockSampler.summarize(lines)
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"],
+                 "samples": 3}
+    s = bench.ClockSampler.summarize([f"0, 1500, 2070, 800, 0x8, Active, {na}, Active, {na}"])
+    assert s["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"] and s["sm_mhz"] == 1500.0
+    assert bench.ClockSampler.summarize([])["sm_mhz"] is None
