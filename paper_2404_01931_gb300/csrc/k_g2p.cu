@@ -153,15 +153,19 @@ __device__ __forceinline__ void stage_faces(const Grid& g, const StepConsts& K, 
 
 // Interpolates component D of U and dU at a particle of cell (ci, cj, ck),
 // local (li, lj, lk) in the brick, from the staged tile.
+// The particle's weights on each axis, computed once: `face` for the component
+// whose faces are normal to that axis, `cen` (cell-centred nodes) for the others.
+struct PartW {
+  AxisW face[3], cen[3];
+};
+
 template <int D>
-__device__ __forceinline__ void interp_tile(const Grid& g, float px, float py, float pz, int ci,
-                                            int cj, int ck, int li, int lj, int lk,
-                                            const float2* sud, float& U,
-                                            float& dU) {
+__device__ __forceinline__ void interp_tile(const PartW& W, int li, int lj, int lk,
+                                            const float2* sud, float& U, float& dU) {
   constexpr int TX = FaceTile<D>::X, TY = FaceTile<D>::Y;
-  const AxisW ax = axis_weights<D, 0>(px, g.inv_dx, ci, g.nx);
-  const AxisW ay = axis_weights<D, 1>(py, g.inv_dx, cj, g.ny);
-  const AxisW az = axis_weights<D, 2>(pz, g.inv_dx, ck, g.nz);
+  const AxisW& ax = (D == 0) ? W.face[0] : W.cen[0];
+  const AxisW& ay = (D == 1) ? W.face[1] : W.cen[1];
+  const AxisW& az = (D == 2) ? W.face[2] : W.cen[2];
   const int t0 = (li + ax.off) + TX * ((lj + ay.off) + TY * (lk + az.off));
   const float wx[2] = {ax.w0, ax.w1}, wy[2] = {ay.w0, ay.w1}, wz[2] = {az.w0, az.w1};
   // (U, dU) accumulate together: one packed two-lane FMA per node, each lane
@@ -272,10 +276,17 @@ __global__ void __launch_bounds__(G2P_THREADS, 5) k_g2p(const Grid g, const Step
         const int li = min(max(ci - b0, 0), BRICK - 1);
         const int lj = min(max(cj - b1, 0), BRICK - 1);
         const int lk = min(max(ck - b2, 0), BRICK - 1);
+        PartW W;
+        W.face[0] = axis_weights<0, 0>(x, g.inv_dx, ci, g.nx);
+        W.face[1] = axis_weights<1, 1>(y, g.inv_dx, cj, g.ny);
+        W.face[2] = axis_weights<2, 2>(z, g.inv_dx, ck, g.nz);
+        W.cen[0] = axis_weights<1, 0>(x, g.inv_dx, ci, g.nx);
+        W.cen[1] = axis_weights<0, 1>(y, g.inv_dx, cj, g.ny);
+        W.cen[2] = axis_weights<0, 2>(z, g.inv_dx, ck, g.nz);
         float U[3], dU[3];
-        interp_tile<0>(g, x, y, z, ci, cj, ck, li, lj, lk, sud[0], U[0], dU[0]);
-        interp_tile<1>(g, x, y, z, ci, cj, ck, li, lj, lk, sud[1], U[1], dU[1]);
-        interp_tile<2>(g, x, y, z, ci, cj, ck, li, lj, lk, sud[2], U[2], dU[2]);
+        interp_tile<0>(W, li, lj, lk, sud[0], U[0], dU[0]);
+        interp_tile<1>(W, li, lj, lk, sud[1], U[1], dU[1]);
+        interp_tile<2>(W, li, lj, lk, sud[2], U[2], dU[2]);
         const float r = K.flip_ratio, r1 = 1.0f - K.flip_ratio;
         float vn[3], adv[3];
 #pragma unroll
