@@ -173,3 +173,34 @@ def test_no_library_no_fallback():
     r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
                        timeout=300)
     assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout + r.stderr
+
+
+def test_headers_compile_as_c_and_link(F, tmp_path):
+    """include/*.h are plain C (C11, -Wall -Werror) and a C program links against the
+    library and calls its host-only entry points (no device needed)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "abi_check.c"
+    src.write_text(
+        '#include "flip.h"\n#include "flip_server.h"\n#include "flip_surface.h"\n'
+        "#include <stdio.h>\n"
+        "int main(void) {\n"
+        "  flip_params p;\n"
+        "  flip_default_params(&p, 32, 32, 32);\n"
+        "  if (flip_abi_version() != FLIP_ABI_VERSION) return 1;\n"
+        "  if (p.n[0] != 32 || !(p.dx > 0.0)) return 2;\n"
+        "  if (flip_strerror(FLIP_E_ARG) == NULL) return 3;\n"
+        "  printf(\"ok %d\\n\", flip_abi_version());\n"
+        "  return 0;\n"
+        "}\n")
+    exe = tmp_path / "abi_check"
+    libdir = os.path.dirname(F.LIB_PATH)
+    r = subprocess.run([cc, "-std=c11", "-Wall", "-Wextra", "-Werror", "-I",
+                        os.path.join(ROOT, "include"), str(src), "-o", str(exe), "-L", libdir,
+                        "-lflip_gb300", f"-Wl,-rpath,{libdir}"], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.startswith("ok "), (r.returncode, r.stdout, r.stderr)
