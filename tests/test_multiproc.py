@@ -142,3 +142,22 @@ def test_clock_summary_from_nvidia_smi_lines():
     s = bench.ClockSampler.summarize([f"0, 1500, 2070, 800, 0x8, Active, {na}, Active, {na}"])
     assert s["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"] and s["sm_mhz"] == 1500.0
     assert bench.ClockSampler.summarize([])["sm_mhz"] is None
+
+
+def test_reference_arm_json_line():
+    """`bench.py --impl reference` (the FP64 oracle on the host cores) prints one JSON
+    line with the contract's keys; it needs no GPU."""
+    import json
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--workload", "dam32", "--steps", "2", "--warmup", "1"], cwd=ROOT,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+              "impl", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert (d["steps"], d["warmup"], d["n_gpus"]) == (2, 1, 1)
