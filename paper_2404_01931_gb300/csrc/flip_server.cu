@@ -276,10 +276,15 @@ int flip_server_submit(flip_server* s, int32_t scene, double t_arrival, int64_t*
 int flip_server_wait(flip_server* s, int64_t ticket, flip_request_info* info) {
   if (!s) return FLIP_E_ARG;
   std::unique_lock<std::mutex> lk(s->mu);
+  if (s->reqs.find(ticket) == s->reqs.end()) return FLIP_E_ARG;
+  // another waiter on the same ticket may collect it first: then this one ends too
+  s->cv_done.wait(lk, [&] {
+    auto w = s->reqs.find(ticket);
+    return w == s->reqs.end() || w->second.done;
+  });
   auto it = s->reqs.find(ticket);
   if (it == s->reqs.end()) return FLIP_E_ARG;
-  s->cv_done.wait(lk, [&] { return s->reqs[ticket].done; });
-  const Request& r = s->reqs[ticket];
+  const Request& r = it->second;
   if (info) {
     info->scene = r.scene;
     info->status = r.status;
