@@ -144,12 +144,16 @@ def test_server_and_batch_need_a_gpu(F):
 @pytest.mark.parametrize("n", [48, 49, 57, 83, 97, 191])
 def test_default_params_are_valid_for_every_edge(F, n):
     """1/(1/n) is not always n in FP64; the defaults must still pass the checks (the
-    create call then fails only for want of a GPU)."""
+    create call then succeeds on a GPU and fails only for want of one elsewhere)."""
     p = F.default_params(n)
-    x = np.zeros(4, np.float32)
-    with pytest.raises(F.FlipError) as ei:
-        F.flip_create(p, x, x, x, x, x, x, allocator=None)
-    assert ei.value.code == F.FLIP_E_NOGPU
+    x = np.full(4, 0.5, np.float32)
+    try:
+        h, _keep = F.flip_create(p, x, x, x, np.zeros(4, np.float32), np.zeros(4, np.float32),
+                                 np.zeros(4, np.float32), allocator=None)
+    except F.FlipError as e:
+        assert e.code == F.FLIP_E_NOGPU
+    else:
+        F.flip_destroy(h)
 
 
 def test_no_library_no_fallback():
@@ -204,3 +208,20 @@ def test_headers_compile_as_c_and_link(F, tmp_path):
     assert r.returncode == 0, r.stderr
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and r.stdout.startswith("ok "), (r.returncode, r.stdout, r.stderr)
+
+
+def test_surface_bin_grid_limit(F):
+    """The particle bins of the surface object are indexed in 32 bits: a search radius
+    too small for the sampling grid is refused before any device call; the defaults
+    at the largest grid pass the checks."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("host-only check (a GPU would allocate the bins)")
+    sp = F.surface_default_params(F.default_params(1024))
+    sp.search_radius, sp.radius = sp.h, 0.25 * sp.h        # 2053^3 bins
+    with pytest.raises(F.FlipError) as ei:
+        F.Surface(sp)
+    assert ei.value.code == F.FLIP_E_ARG and "bin grid" in str(ei.value)
+    with pytest.raises(F.FlipError) as ei:
+        F.Surface(F.surface_default_params(F.default_params(1024)))   # 1029^3 bins
+    assert ei.value.code == F.FLIP_E_NOGPU
