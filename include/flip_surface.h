@@ -63,7 +63,9 @@ typedef struct {
   double origin[3];      /* position of corner (0,0,0) */
   double h;              /* corner spacing (> 0) */
   double radius;         /* particle radius r (>= 0, < search_radius) */
-  double search_radius;  /* kernel support R (> 0) */
+  double search_radius;  /* kernel support R (> 0); the particle bins (edge R/2 over the
+                            sampling box widened by R per side) must number under 2^31,
+                            else flip_surface_create returns FLIP_E_ARG */
   double iso;            /* level set meshed (0: the surface phi = 0) */
 } flip_surface_params;
 

@@ -749,6 +749,16 @@ int flip_surface_create(const flip_surface_params* sp, void* stream, flip_surfac
   if (!std::isfinite(sp->iso)) return sfail(FLIP_E_ARG, "iso must be finite");
   for (int a = 0; a < 3; ++a)
     if (!std::isfinite(sp->origin[a])) return sfail(FLIP_E_ARG, "origin must be finite");
+  {
+    // particle bins (edge search_radius / 2) are indexed in 32 bits
+    const double bb = (double)(0.5f * (float)sp->search_radius);  // the bin edge used below
+    double nbins = 1.0;
+    for (int a = 0; a < 3; ++a)
+      nbins *= std::ceil((sp->n[a] * sp->h + 2.0 * sp->search_radius) / bb) + 1.0;
+    if (!(nbins <= 2147483647.0))
+      return sfail(FLIP_E_ARG, "bin grid too large (over 2^31 bins): search_radius is too small "
+                               "for the sampling grid");
+  }
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
     return sfail(FLIP_E_NOGPU, "no CUDA device");
