@@ -96,7 +96,8 @@ int flip_surface_set_field(flip_surface* s, const float* phi, int32_t src_is_dev
 
 /* Marching cubes over the current phi plus vertex normals.  Grows the output
  * buffers as needed and returns their sizes.  Synchronous.  FLIP_E_SIZE when
- * the mesh would have 2^31 or more vertices or triangles. */
+ * the mesh has 2^29 or more vertices (its triangles, at most 4 per vertex, must
+ * stay below 2^31 for int32 indices). */
 int flip_surface_mesh(flip_surface* s, int64_t* n_vertices, int64_t* n_triangles);
 
 /* Bytes of a field at the current sizes (0 for an unknown field). */

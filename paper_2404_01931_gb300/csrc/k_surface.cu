@@ -904,10 +904,14 @@ int flip_surface_mesh(flip_surface* s, int64_t* n_vertices, int64_t* n_triangles
   k_tile_scan<<<1, SC_THREADS, 0, st>>>(s->tile, ntiles, total);
   SURF_CUDA(cudaMemcpyAsync(s->htotal, total, sizeof(u64), cudaMemcpyDeviceToHost, st));
   SURF_CUDA(cudaStreamSynchronize(st));
+  // Vertices (crossing edges, at most 3 per corner) never exceed 2^32, so the low
+  // word is exact.  Each crossing edge is a vertex of one fan polygon in each of at
+  // most 4 cubes, and a k-gon gives k - 2 triangles, so triangles <= 4 * vertices:
+  // below 2^31 vertices / 4 the high word cannot have wrapped either.
   const long long nv = (long long)(*s->htotal & 0xffffffffull);
   const long long nt = (long long)(*s->htotal >> 32);
-  if (nv >= (1ll << 31) || nt >= (1ll << 31))
-    return sfail(FLIP_E_SIZE, "mesh too large for int32 indices");
+  if (4 * nv >= (1ll << 31) || nt >= (1ll << 31))
+    return sfail(FLIP_E_SIZE, "mesh too large for int32 indices (2^29 vertices or more)");
   if (nv > s->vcap) {
     s->vcap = 0;
     s->nv = 0;
