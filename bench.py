@@ -2,23 +2,31 @@
 
 Default workload: the drop-into-pool scene on a 256^3 MAC grid (pool depth 0.3 plus a
 sphere of radius 0.15 at (0.5, 0.7, 0.5), 8 particles per fluid cell, 42,266,944
-particles), mixed precision (FP32 PCG whose correction is folded into an FP64 solution,
-with the residual recomputed in FP64, to a relative residual of 1e-8), dt = 1/240, FLIP ratio 0.95, seed 0.  Inputs are synthetic
-(seeded jittered seeding), generated on the host.
+particles), mixed precision (FP32 multigrid-preconditioned CG on a correction that is
+folded into a float-pair (~48-bit) solution, with the residual recomputed in float pairs,
+to a relative residual of 1e-8; FP64 right-hand side and result), dt = 1/240, FLIP
+ratio 0.95, seed 0.  Inputs are synthetic (seeded jittered seeding), generated on the
+host.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload pool256|dam128|dam32]
   python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
 
 A "step" is one full FLIP step (bin, P2G, divergence, PCG, G2P).  Timing: W untimed
 steps, then K steps between CUDA events on the simulation's stream, bracketed by a
-barrier and a synchronize; the max over ranks is reported.  The particle and grid
-arrays (> 1 GB) are larger than the 129 MB L2, so no flush is needed between steps.
+barrier and a synchronize; the max over ranks is reported.  The library records CUDA
+events around every step and stage inside the timed call (read once after it), which
+give the per-step latency percentiles and the per-stage rooflines.  The particle and
+grid arrays (> 1 GB) are larger than the 129 MB L2, so no flush is needed between steps.
+Outside the timed region, the first step of the seeded scene is compared field by field
+with the FP64 oracle's (error_vs_oracle).
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -63,17 +71,60 @@ WORKLOADS = {
 MG_PCG_BYTES_PER_ITER = 92
 MG_IR_BYTES_PER_OUTER = 47
 MG_IR_BYTES_PER_SOLVE = 40
-# DRAM traffic of one k_pcg_mg launch on the 256^3 pool (dram__bytes_read.sum +
-# dram__bytes_write.sum of the first timed step's solve, a single-pass capture);
-# see profiles/k_pcg_mg_pool256_dram.md.  Reported for that workload only.
-PCG_DRAM_BYTES_POOL256 = 7.603e9
+# The method-level byte model of a Jacobi-style PCG iteration per fluid cell
+# (SpMV + dot 9 B, axpy + preconditioner + dot 25 B, p update 13 B) and of one
+# outer refinement of the mixed mode (the solution read and written at 8 B each,
+# the right-hand side read at 8 B, the residual written, neighbour reads: ~40 B):
+# the algorithmic bytes of `roofline`.  The preconditioner's own passes (the
+# V-cycle) are not algorithmic bytes of the method; the builder's model above
+# counts them and is reported beside it.
+SURVEY_PCG_BYTES_PER_ITER = 47
+SURVEY_IR_BYTES_PER_OUTER = 40
+# DRAM traffic of one k_pcg_mg launch on the 256^3 pool, read from the committed
+# single-pass ncu summary, which records the hash of the solver's sources it was
+# measured on; when the sources have changed since, the traffic is reported as null.
+PCG_PROFILE = os.path.join(ROOT, "profiles", "k_pcg_mg_pool256_dram.md")
+SOLVER_SOURCES = ("k_mg.cu", "pcg_common.cuh", "flip_kernels.cuh", "flip_internal.cuh")
 # GB300's nominal HBM3e bandwidth, reported beside the measured copy bandwidth
 NOMINAL_HBM_GBS = 7900.0
 
 
+def solver_source_hash():
+    """SHA-256 (first 16 hex digits) of the sources the persistent solve is built from."""
+    h = hashlib.sha256()
+    for name in SOLVER_SOURCES:
+        with open(os.path.join(ROOT, "paper_2404_01931_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_pcg_traffic():
+    """(bytes per launch, note): the DRAM traffic of the committed capture, when it was
+    taken on the current solver sources; else (None, why)."""
+    try:
+        text = open(PCG_PROFILE).read()
+    except OSError:
+        return None, "no committed capture"
+    vals = dict(re.findall(r"^(source_hash|dram_bytes_per_launch):\s*(\S+)", text, re.M))
+    if "source_hash" not in vals or "dram_bytes_per_launch" not in vals:
+        return None, "capture carries no source hash"
+    if vals["source_hash"] != solver_source_hash():
+        return None, (f"stale: captured on solver sources {vals['source_hash']}, "
+                      f"now {solver_source_hash()}")
+    return float(vals["dram_bytes_per_launch"]), f"ncu capture on sources {vals['source_hash']}"
+
+
 def stage_roofline(w, np_, nfl, stage_ms, steps, peak):
-    """Achieved HBM GB/s of the other stages: algorithmic bytes (models below) over
-    the live CUDA-event stage time, against the measured copy bandwidth.
+    """Achieved HBM GB/s of the other stages over the live CUDA-event stage time, against
+    the measured copy bandwidth, by two byte models.
+    The method's algorithmic bytes (`frac`):
+      bin:        56 B per particle (24 B read, key 4 B, 24 B written, histogram 4 B)
+                  + 8 B per cell
+      P2G:        24 B per particle + 21 B per cell (u*, v*, w* written 12 B, type 1 B,
+                  start/count 8 B)
+      divergence: 13 B per fluid cell
+      G2P:        48 B per particle + 17 B per cell
+    This build's traffic model (`frac_builder_model`):
       bin:        scatter 64 B per particle (key, rank, 28 B read, 28 B write) +
                   13 B per key (count read and clear, local start, cell type)
       P2G:        24 B per particle (positions and velocities, read once) +
@@ -84,15 +135,20 @@ def stage_roofline(w, np_, nfl, stage_ms, steps, peak):
     cells = n ** 3
     keys = (-(-n // 8) * 8) ** 3
     faces = 3 * (n + 1) * n * n
-    model = {"bin": 64 * np_ + 13 * keys, "p2g": 24 * np_ + 20 * faces,
-             "divergence": 41 * cells, "g2p": 56 * np_}
+    method = {"bin": 56 * np_ + 8 * cells, "p2g": 24 * np_ + 21 * cells,
+              "divergence": 13 * nfl, "g2p": 48 * np_ + 17 * cells}
+    builder = {"bin": 64 * np_ + 13 * keys, "p2g": 24 * np_ + 20 * faces,
+               "divergence": 41 * cells, "g2p": 56 * np_}
     out = {}
-    for k, b in model.items():
+    for k in method:
         t = stage_ms[k] / steps / 1e3
-        gbs = b / t / 1e9 if t > 0 else None
+        gbs = method[k] / t / 1e9 if t > 0 else None
+        gbs_b = builder[k] / t / 1e9 if t > 0 else None
         out[k] = {"achieved_gbs": gbs, "frac": gbs / peak if gbs else None,
                   "frac_of_nominal": gbs / NOMINAL_HBM_GBS if gbs else None,
-                  "algorithmic_bytes": b}
+                  "algorithmic_bytes": method[k],
+                  "frac_builder_model": gbs_b / peak if gbs_b else None,
+                  "builder_model_bytes": builder[k]}
     return out
 
 
@@ -238,6 +294,60 @@ def shard_scenes(weights, n_ranks):
         out[r].append(i)
         load[r] += weights[i]
     return [sorted(o) for o in out]
+
+
+def _rel_l2(a, b, floor=0.0):
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), floor, 1e-300))
+
+
+def first_step_fields(sim, F):
+    """Fields of a handle right after its first step: faces, pressure, right-hand side
+    and the particles in creation order."""
+    return {"u_old": [sim.read(f) for f in (F.U_OLD, F.V_OLD, F.W_OLD)],
+            "u_new": [sim.read(f) for f in (F.U_NEW, F.V_NEW, F.W_NEW)],
+            "p": sim.read(F.PRESSURE_F64), "rhs": sim.read(F.RHS),
+            "type": sim.read(F.CELL_TYPE), "particles": sim.particles()}
+
+
+def error_vs_oracle(w, sc, got):
+    """Per-field error of the GPU's first step of the seeded scene against the FP64
+    oracle's step from the same input, on the host, outside the timed region.  Mixed
+    mode is compared with a tight oracle solve (CG to 1e-11), FP32 mode with the
+    oracle's same solver and tolerance.  Velocity norms are floored at g dt sqrt(n)."""
+    import oracle as O
+    n = w["n"]
+    mixed = w["precision"] == "mixed"
+    op = O.Params(n=(n, n, n), dx=1.0 / n, cg_tol=1e-11 if mixed else w["cg_tol"],
+                  cg_max_iter=100000 if mixed else 0)
+    t0 = time.perf_counter()
+    ref = O.step(op, *sc.arrays())
+    el = time.perf_counter() - t0
+    gdt = 9.81 / 240
+    nf = (n + 1) * n * n
+    fl = gdt * np.sqrt(3 * nf)
+    x, y, z, u, v, wv = got["particles"]
+    out = {
+        "reference": "FP64 oracle step from the same seeded input, "
+                     + ("tight solve (CG to 1e-11)" if mixed else
+                        f"same multigrid-PCG to {w['cg_tol']:g}"),
+        "oracle_s": round(el, 1), "oracle_cores": O.num_threads(),
+        "cell_type_mismatches": int(np.count_nonzero(got["type"].ravel() != ref.type.ravel())),
+        "u_old_rel_l2": _rel_l2(np.concatenate([a.ravel() for a in got["u_old"]]),
+                                np.concatenate([a.ravel() for a in ref.u_old]), fl),
+        "rhs_rel_l2": _rel_l2(got["rhs"], ref.rhs),
+        "pressure_rel_l2": _rel_l2(got["p"], ref.pressure),
+        "u_new_rel_l2": _rel_l2(np.concatenate([a.ravel() for a in got["u_new"]]),
+                                np.concatenate([a.ravel() for a in ref.u_new]), fl),
+        "position_max_err_cells": float(np.abs(np.stack([x, y, z]).astype(np.float64)
+                                               - np.stack([ref.x, ref.y, ref.z])).max() * n),
+        "velocity_rel_l2": _rel_l2(np.stack([u, v, wv]), np.stack([ref.u, ref.v, ref.w]),
+                                   gdt * np.sqrt(3 * x.size)),
+        "bar": "relative L2 <= 1e-5 for grid velocities and pressure; positions within "
+               "1e-4 of a cell",
+    }
+    return out
 
 
 def cpu_baseline(w, budget_s=25.0):
@@ -521,8 +631,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="pool256", choices=sorted(WORKLOADS))
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-oracle-error", dest="oracle_error", action="store_false",
+                    help="skip the per-field comparison of the first step with the oracle")
     ap.add_argument("--batch", type=int, default=0,
                     help="run the batched form: this many dam-break scenes stepped together")
     ap.add_argument("--serve", type=int, default=0,
@@ -591,8 +703,20 @@ def main():
     sim = F.Simulation(prm, *sc.arrays())
     stream = torch.cuda.ExternalStream(sim.stream)
     np_ = sc.n_particles
-    if args.warmup > 0:
-        sim.step(args.warmup)
+    # the first step of the seeded scene, kept for the comparison with the oracle
+    # (computed after the timed region); it counts as a warm-up step
+    first = None
+    want_err = (args.oracle_error and rank == 0 and ws == 1 and not (args.ppc[0] or args.ppc[1])
+                and args.cfl == 0 and not args.warm_start and args.precond == "mg")
+    warm_left = args.warmup
+    if want_err and warm_left > 0:
+        sim.step(1, stats=True)
+        first = first_step_fields(sim, F)
+        warm_left -= 1
+    if warm_left > 1:
+        sim.step(warm_left - 1)
+    if warm_left > 0:
+        sim.step(1, stats=True)  # also sizes the library's pool of timing events
     sim.sync()
     clocks = ClockSampler(local)
     clocks.start()
@@ -609,6 +733,7 @@ def main():
     if ws > 1:
         dist.barrier()
     ck = clocks.stop()
+    step_ms = sim.step_times()
     ms_local = e0.elapsed_time(e1)
     ms = max_over_ranks(ms_local, ws)
     np_ = st.n_particles if args.ppc[0] or args.ppc[1] else np_
@@ -679,12 +804,20 @@ def main():
         if diag:
             diag["energy_frac_of_measured_hbm"] = diag["energy_bytes"] / (diag["energy_ms"] / 1e3) / 1e9 / peak
         mixed = w["precision"] == "mixed"
+        # the method's algorithmic bytes of the solves (SURVEY 8(d) model) and the
+        # builder's model that also counts the V-cycle's passes
+        survey_bytes = nfl * (SURVEY_PCG_BYTES_PER_ITER * st.cg_iterations
+                              + (SURVEY_IR_BYTES_PER_OUTER * st.ir_iterations if mixed else 0))
         pcg_bytes = nfl * (MG_PCG_BYTES_PER_ITER * st.cg_iterations
                            + (MG_IR_BYTES_PER_OUTER * st.ir_iterations
                               + MG_IR_BYTES_PER_SOLVE * args.steps if mixed else 0))
         stage_ms = {"bin": st.ms_bin, "p2g": st.ms_p2g, "divergence": st.ms_divergence,
                     "pcg": st.ms_pcg, "g2p": st.ms_g2p}
-        achieved = pcg_bytes / (st.ms_pcg / 1e3) / 1e9 if st.ms_pcg > 0 else None
+        t_pcg = st.ms_pcg / 1e3
+        achieved = survey_bytes / t_pcg / 1e9 if t_pcg > 0 else None
+        achieved_vc = pcg_bytes / t_pcg / 1e9 if t_pcg > 0 else None
+        traffic, traffic_note = (recorded_pcg_traffic() if args.workload == "pool256"
+                                 else (None, "captured for the 256^3 pool only"))
         out = {
             "metric": "FLIP particle-steps/s", "value": value, "unit": "particle-steps/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -712,16 +845,33 @@ def main():
             "ir_iterations_per_step": st.ir_iterations / args.steps,
             "rel_residual": st.cg_rel_residual, "rel_divergence": st.rel_divergence,
             "n_fluid_cells": nfl, "status": rc,
+            "latency_ms": {"p50": float(np.percentile(step_ms, 50)) if len(step_ms) else None,
+                           "p99": float(np.percentile(step_ms, 99)) if len(step_ms) else None,
+                           "max": float(step_ms.max()) if len(step_ms) else None,
+                           "mean": float(step_ms.mean()) if len(step_ms) else None,
+                           "samples": int(len(step_ms)),
+                           "what": "device time of each timed step (CUDA events around the "
+                                   "step's kernels on the simulation's stream)"},
             "roofline": {"kernel": "k_pcg_mg (persistent multigrid-preconditioned CG, "
                                    "whole solve per launch)",
                          "bound": "hbm", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
+                         "frac_survey": (achieved / peak) if achieved else None,
+                         "byte_model": f"{SURVEY_PCG_BYTES_PER_ITER} B per fluid cell per CG "
+                                       f"iteration + {SURVEY_IR_BYTES_PER_OUTER} B per fluid "
+                                       "cell per outer refinement",
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                          "nominal_peak": NOMINAL_HBM_GBS,
                          "frac_of_nominal": (achieved / NOMINAL_HBM_GBS) if achieved else None,
-                         "algorithmic_bytes_per_launch": pcg_bytes / args.steps,
-                         "traffic": PCG_DRAM_BYTES_POOL256 if args.workload == "pool256"
-                         else None},
+                         "algorithmic_bytes_per_launch": survey_bytes / args.steps,
+                         "with_vcycle_bytes": {
+                             "bytes_per_launch": pcg_bytes / args.steps,
+                             "achieved": achieved_vc,
+                             "frac": (achieved_vc / peak) if achieved_vc else None,
+                             "model": f"{MG_PCG_BYTES_PER_ITER} B per fluid cell per iteration "
+                                      "including the V-cycle's passes"},
+                         "traffic": traffic, "traffic_source": traffic_note,
+                         "solver_source_hash": solver_source_hash()},
             "stage_roofline": stage_roofline(w, np_, nfl, stage_ms, args.steps, peak),
             "gpu_launches": st.kernel_launches,
             "diagnostics": diag,
@@ -731,6 +881,8 @@ def main():
         }
         if not args.no_cpu_baseline and ws == 1:
             out["cpu_baseline"] = cpu_baseline(w)
+        if first is not None:
+            out["error_vs_oracle"] = error_vs_oracle(w, sc, first)
         print(json.dumps(out), flush=True)
     sim.close()
     if ws > 1:

@@ -58,11 +58,19 @@ enum {
 
 /* ------------------------------------------------------------ parameters */
 enum {
-  FLIP_PREC_FP32 = 0,     /* FP32 vectors and SpMV; dot products accumulated
-                             in FP32 pairs per thread, FP64 across threads */
-  FLIP_PREC_MIXED_IR = 1  /* as FP32 inside; FP64 solution and outer residual
-                             r = b - A x, refined without restarting the
-                             Krylov direction (reliable updates) */
+  FLIP_PREC_FP32 = 0,     /* FP32 vectors and SpMV.  Dot products: each thread
+                             accumulates exact FP32 products as a float pair
+                             (hi + lo, error-free transforms, ~48 significant
+                             bits), warps and CTAs add the pairs, and the CTAs'
+                             pairs are added in FP64 (flip_dot_f32 runs it) */
+  FLIP_PREC_MIXED_IR = 1  /* FP32 CG on a correction d inside; the solution x and
+                             the outer residual r = b - A x are carried as float
+                             pairs (~48 bits, not FP64) with the operator's scale
+                             as a pair too (flip_residual_pairs runs that
+                             residual), refined without restarting the Krylov
+                             direction (reliable updates).  The right-hand side
+                             enters as FP64 and the result leaves as FP64
+                             (FLIP_FIELD_PRESSURE_F64). */
 };
 
 enum {
@@ -245,6 +253,22 @@ int flip_read_particles(flip_handle* h, float* x, float* y, float* z, float* u, 
 int flip_write_particles(flip_handle* h, const float* x, const float* y, const float* z,
                          const float* u, const float* v, const float* w, int32_t src_is_device);
 
+/* Device time (ms) of each step of the last flip_step call that took stats, from
+ * the step's first kernel to its last (CUDA events on the handle's stream, read
+ * once after the call's steps were all enqueued).  Writes min(n, count) entries
+ * to ms (nullable) and returns count, the number of steps of that call (0 when
+ * no timed call was made), or -FLIP_E_ARG for a NULL handle. */
+int32_t flip_step_times(const flip_handle* h, double* ms, int32_t n);
+
+/* Limit (ns) of every bounded device-side wait of this handle's kernels: the grid
+ * barriers of the persistent solve and G2P's waits for its bulk copies of
+ * particles.  A wait that runs out sets the step's status to FLIP_E_TIMEOUT (the
+ * step's results are then not valid: rewrite the particles, flip_write_particles,
+ * before stepping again); G2P then waits for its copies in flight, up to 1 s, before
+ * its CTA leaves.  0 restores the defaults (5 s for a barrier, 1 s for a copy).
+ * FLIP_E_ARG for a NULL handle. */
+int flip_set_wait_timeout(flip_handle* h, uint64_t timeout_ns);
+
 /* CTAs of the scene's persistent solve kernel, in [1, the co-resident maximum]
  * (0, the default: one per SM).  Fewer CTAs mean fewer arrivals at each grid
  * barrier, which pays on small grids; the solution is the same up to the order
@@ -346,6 +370,33 @@ void flip_batch_destroy(flip_batch* b);
  * and *rel_residual (nullable) the final ||r||/||b||. */
 int flip_solve_pressure(const flip_params* params, const uint8_t* type, const float* b,
                         float* p, void* stream, int32_t* iterations, double* rel_residual);
+
+/* The two extended-precision steps of the mixed-precision solve, run on caller
+ * data so that their rounding can be checked against exact sums.  The paper runs
+ * its CG in one precision (Sec. 3.1.7); the GB300 build keeps the dot products
+ * and the refinement residual in float pairs instead of FP64 (FP32's rate, about
+ * 48 significant bits).
+ *
+ * flip_dot_f32: out = sum_i a[i] b[i] over n float32 entries (device arrays), as
+ * every CG dot product of this library is formed: the solver's CTA count splits
+ * [0, n) into contiguous slices (multiples of 32 long), each thread accumulates
+ * exact FP32 products in a float pair (TwoProduct by FMA, TwoSum), warps and the
+ * CTA add pairs, and one warp adds the CTAs' pairs in CTA order; the pair is
+ * returned as the FP64 value hi + lo.  Its error is at most about
+ * (m^2 + 3 L) u^2 sum_i |a[i] b[i]| with u = 2^-24, m the longest per-thread run
+ * and L the levels of the pair additions above it.  n in [0, 2^31-1]; scratch is
+ * allocated and freed on stream (cudaMallocAsync); waits for the stream.
+ *
+ * flip_residual_pairs: r = b - A x over the grid of params (natural layout,
+ * n_cells entries per array, device memory), with A the 7-point operator of
+ * Sec. 3.1.7 (scale s = dt/(rho dx^2), p = 0 in air, walls dropped), x, b, r as
+ * float pairs (hi, lo arrays) and s as a float pair: the per-cell function the
+ * mixed-mode multigrid solve applies in each refinement.  type[c] == 1 marks a
+ * fluid cell; r is 0 on the others.  Allocates nothing; waits for the stream. */
+int flip_dot_f32(const float* a, const float* b, int64_t n, double* out, void* stream);
+int flip_residual_pairs(const flip_params* params, const uint8_t* type, const float* x_hi,
+                        const float* x_lo, const float* b_hi, const float* b_lo, float* r_hi,
+                        float* r_lo, void* stream);
 
 /* Allocation-free variant of flip_solve_pressure, for callers that cannot
  * allocate device memory while they run: a plug-in whose device memory belongs

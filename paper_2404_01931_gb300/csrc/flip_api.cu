@@ -14,6 +14,7 @@
 #include <string>
 
 #include "../../include/flip.h"
+#include "flip_api_internal.cuh"
 #include "flip_kernels.cuh"
 
 using namespace flipk;
@@ -47,6 +48,11 @@ int cuda_fail(cudaError_t e, const char* what) {
   } while (0)
 
 constexpr size_t kAlign = 256;
+
+// Default limits of the bounded device-side waits: a grid barrier of the solve,
+// and G2P's wait for a bulk copy of particles (flip_set_wait_timeout changes both).
+constexpr unsigned long long kBarrierWaitNs = 5000000000ull;
+constexpr unsigned long long kG2pWaitNs = 1000000000ull;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
@@ -109,6 +115,11 @@ struct flip_handle {
   int solver_blocks = 0;      // CTAs of a single solve (0: pcg_blocks)
   int launches = 0;
   bool stepped = false;
+  unsigned long long wait_ns = 0;  // flip_set_wait_timeout (0: the defaults)
+  // timing of flip_step calls with statistics: 5 events per step plus one, kept
+  // for the handle's life so a timed call creates none once the pool is large enough
+  std::vector<cudaEvent_t> tev;
+  std::vector<double> step_ms;  // device time of each step of the last timed call
 };
 
 void flip_set_last_error_(const std::string& msg) { g_last_error = msg; }
@@ -264,6 +275,7 @@ StepConsts make_consts(const flip_params& p) {
   k.flip_ratio = (float)p.flip_ratio;
   k.advect_grid = p.advect_source == FLIP_ADVECT_GRID;
   k.dt = (float)p.dt;
+  k.wait_ns = kG2pWaitNs;
   return k;
 }
 
@@ -310,6 +322,7 @@ void setup_mg(MgArgs& m, int dims[MG_MAX_LEVELS][3], const flip_params& p) {
 void fill_pcg_tables(PcgArgs& a, const flip_params& p) {
   const double s = p.dt / (p.rho * p.dx * p.dx);
   a.s = (float)s;
+  a.s_lo = (float)(s - (double)a.s);
   a.s64 = s;
   for (int c = 0; c < 8; ++c) {
     a.diag_tab[c] = (float)(s * c);
@@ -479,7 +492,7 @@ PcgArgs pcg_args(flip_handle* h) {
   a.max_iter = h->prm.cg_max_iter;
   a.ir_max_iter = h->prm.ir_max_iter;
   a.check_singular = 1;
-  a.timeout_ns = 5000000000ull;
+  a.timeout_ns = h->wait_ns ? h->wait_ns : kBarrierWaitNs;
   a.precond = h->prm.preconditioner;
   a.warm_start = h->prm.warm_start;
   if (a.precond != FLIP_PRECOND_JACOBI) {
@@ -677,6 +690,8 @@ void flip_destroy(flip_handle* h) {
   }
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->hstats) cudaFreeHost(h->hstats);
+  for (cudaEvent_t e : h->tev)
+    if (e) cudaEventDestroy(e);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
@@ -686,18 +701,20 @@ int flip_step(flip_handle* h, int32_t nsteps, flip_stats* stats) {
   if (nsteps < 0) return fail(FLIP_E_ARG, "nsteps must be >= 0");
   const cudaStream_t s = h->stream;
   const bool timed = stats != nullptr;
-  cudaEvent_t ev[6] = {};
-  float ms[5] = {0, 0, 0, 0, 0};
-  float ms_total = 0.0f;
+  // Step st is bracketed by events E[5 st] .. E[5 st + 5] (its stages in between;
+  // a step's last event is the next step's first).  Nothing waits on them until
+  // every step is enqueued, so the host never stalls the stream inside the call.
   if (timed) {
-    for (auto& e : ev) FLIP_CUDA(cudaEventCreate(&e));
+    const size_t need = std::max<size_t>(5 * (size_t)nsteps + 1, 256);
+    while (h->tev.size() < need) {
+      cudaEvent_t e = nullptr;
+      FLIP_CUDA(cudaEventCreate(&e));
+      h->tev.push_back(e);
+    }
   }
+  cudaEvent_t* E = timed ? h->tev.data() : nullptr;
   const int launches0 = h->launches;
-  cudaEvent_t t_begin = nullptr, t_end = nullptr;
   if (timed) {
-    FLIP_CUDA(cudaEventCreate(&t_begin));
-    FLIP_CUDA(cudaEventCreate(&t_end));
-    FLIP_CUDA(cudaEventRecord(t_begin, s));
     FLIP_CUDA(cudaMemcpyAsync(&h->dstats->cg_iters_mark, &h->dstats->cg_iters_total,
                               2 * sizeof(long long), cudaMemcpyDeviceToDevice, s));
     FLIP_CUDA(cudaMemcpyAsync(&h->dstats->added_mark, &h->dstats->added_total,
@@ -707,7 +724,8 @@ int flip_step(flip_handle* h, int32_t nsteps, flip_stats* stats) {
   PcgArgs pa = pcg_args(h);
   int rc = FLIP_OK;
   for (int st = 0; st < nsteps; ++st) {
-    if (timed) FLIP_CUDA(cudaEventRecord(ev[0], s));
+    cudaEvent_t* ev = timed ? E + 5 * (size_t)st : nullptr;
+    if (timed && st == 0) FLIP_CUDA(cudaEventRecord(ev[0], s));
     launch_step_dt(h);
     launch_front(h, s);
     if (timed) FLIP_CUDA(cudaEventRecord(ev[1], s));
@@ -730,20 +748,29 @@ int flip_step(flip_handle* h, int32_t nsteps, flip_stats* stats) {
     launch_back(h, s);
     if (timed) FLIP_CUDA(cudaEventRecord(ev[5], s));
     FLIP_CUDA(cudaGetLastError());
-    if (timed) {
-      FLIP_CUDA(cudaEventSynchronize(ev[5]));
+    h->stepped = true;
+  }
+  if (timed) {
+    double ms[5] = {0, 0, 0, 0, 0};
+    double ms_total = 0.0;
+    h->step_ms.assign((size_t)nsteps, 0.0);
+    if (nsteps > 0) FLIP_CUDA(cudaEventSynchronize(E[5 * (size_t)nsteps]));
+    for (int st = 0; st < nsteps; ++st) {
+      const cudaEvent_t* ev = E + 5 * (size_t)st;
       for (int q = 0; q < 5; ++q) {
         float t = 0.0f;
         FLIP_CUDA(cudaEventElapsedTime(&t, ev[q], ev[q + 1]));
         ms[q] += t;
       }
+      float t = 0.0f;
+      FLIP_CUDA(cudaEventElapsedTime(&t, ev[0], ev[5]));
+      h->step_ms[(size_t)st] = t;
     }
-    h->stepped = true;
-  }
-  if (timed) {
-    FLIP_CUDA(cudaEventRecord(t_end, s));
-    FLIP_CUDA(cudaEventSynchronize(t_end));
-    FLIP_CUDA(cudaEventElapsedTime(&ms_total, t_begin, t_end));
+    if (nsteps > 0) {
+      float t = 0.0f;
+      FLIP_CUDA(cudaEventElapsedTime(&t, E[0], E[5 * (size_t)nsteps]));
+      ms_total = t;
+    }
     std::memset(stats, 0, sizeof(*stats));
     FLIP_CUDA(cudaMemsetAsync(h->norms, 0, 2 * sizeof(double), s));
     if (h->stepped) {
@@ -776,11 +803,23 @@ int flip_step(flip_handle* h, int32_t nsteps, flip_stats* stats) {
     stats->ms_pcg = ms[3];
     stats->ms_g2p = ms[4];
     stats->ms_total = ms_total;
-    for (auto& e : ev) cudaEventDestroy(e);
-    cudaEventDestroy(t_begin);
-    cudaEventDestroy(t_end);
   }
   return rc;
+}
+
+int flip_set_wait_timeout(flip_handle* h, uint64_t timeout_ns) {
+  if (!h) return fail(FLIP_E_ARG, "handle is NULL");
+  h->wait_ns = timeout_ns;
+  h->K.wait_ns = timeout_ns ? timeout_ns : kG2pWaitNs;
+  return FLIP_OK;
+}
+
+int32_t flip_step_times(const flip_handle* h, double* ms, int32_t n) {
+  if (!h) return -fail(FLIP_E_ARG, "handle is NULL");
+  const int32_t count = (int32_t)h->step_ms.size();
+  if (ms)
+    for (int32_t q = 0; q < std::min(n, count); ++q) ms[q] = h->step_ms[(size_t)q];
+  return count;
 }
 
 int flip_set_solver_blocks(flip_handle* h, int32_t nblocks) {
@@ -1042,8 +1081,9 @@ struct flip_batch {
   int* d_team_first = nullptr;   // [capacity + 1]
   int max_blocks = 0;
   std::vector<cudaEvent_t> ev;   // one per scene slot
-  cudaEvent_t ev_begin = nullptr, ev_pcg0 = nullptr, ev_pcg1 = nullptr, ev_end = nullptr;
+  cudaEvent_t ev_begin = nullptr, ev_end = nullptr;
   cudaEvent_t ev_solved = nullptr;
+  std::vector<cudaEvent_t> pev;  // timed calls: the batched solves' start and end per step
   double team_exponent = 1.0;    // team size proportional to particles^exponent
   // two steps of a fixed set of scenes captured as one CUDA graph (untimed calls)
   cudaGraphExec_t graph = nullptr;
@@ -1210,8 +1250,6 @@ int flip_batch_create(int32_t capacity, void* stream, flip_batch** out) {
     if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
       return bail(e, "cudaEventCreate");
   if ((e = cudaEventCreate(&b->ev_begin)) != cudaSuccess ||
-      (e = cudaEventCreate(&b->ev_pcg0)) != cudaSuccess ||
-      (e = cudaEventCreate(&b->ev_pcg1)) != cudaSuccess ||
       (e = cudaEventCreate(&b->ev_end)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&b->ev_solved, cudaEventDisableTiming)) != cudaSuccess)
     return bail(e, "cudaEventCreate");
@@ -1270,7 +1308,9 @@ void flip_batch_destroy(flip_batch* b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   for (auto ev : b->ev)
     if (ev) cudaEventDestroy(ev);
-  for (cudaEvent_t ev : {b->ev_begin, b->ev_pcg0, b->ev_pcg1, b->ev_end, b->ev_solved})
+  for (cudaEvent_t ev : {b->ev_begin, b->ev_end, b->ev_solved})
+    if (ev) cudaEventDestroy(ev);
+  for (cudaEvent_t ev : b->pev)
     if (ev) cudaEventDestroy(ev);
   if (b->graph) cudaGraphExecDestroy(b->graph);
   if (b->d_args) cudaFree(b->d_args);
@@ -1365,6 +1405,12 @@ int flip_batch_step(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t ns
   for (int s = 0; s < n; ++s) launches0[s] = hs[s]->launches;
   int batch_launches = 0;
   if (timed) {
+    // two events per step around the batched solves, read once after the call
+    while (b->pev.size() < 2 * (size_t)nsteps) {
+      cudaEvent_t e = nullptr;
+      FLIP_CUDA(cudaEventCreate(&e));
+      b->pev.push_back(e);
+    }
     FLIP_CUDA(cudaEventRecord(b->ev_begin, bs));
     for (int s = 0; s < n; ++s) {
       FLIP_CUDA(cudaMemcpyAsync(&hs[s]->dstats->cg_iters_mark, &hs[s]->dstats->cg_iters_total,
@@ -1377,6 +1423,7 @@ int flip_batch_step(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t ns
   FLIP_CUDA(cudaEventRecord(b->ev_solved, bs));
   for (int s = 0; s < n; ++s) FLIP_CUDA(cudaStreamWaitEvent(hs[s]->stream, b->ev_solved, 0));
   float ms_pcg = 0.0f;
+  int timed_steps = 0;
   // One step of every scene, enqueued on the scene streams and the batch stream.
   auto enqueue_step = [&]() -> int {
     for (int s = 0; s < n; ++s) {
@@ -1391,7 +1438,7 @@ int flip_batch_step(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t ns
       FLIP_CUDA(cudaEventRecord(b->ev[s], h->stream));
       FLIP_CUDA(cudaStreamWaitEvent(bs, b->ev[s], 0));
     }
-    if (timed) FLIP_CUDA(cudaEventRecord(b->ev_pcg0, bs));
+    if (timed) FLIP_CUDA(cudaEventRecord(b->pev[2 * (size_t)timed_steps], bs));
     for (size_t q = 0; q < launches.size(); ++q) {
       const Launch& L = launches[q];
       PcgBatch pb{b->d_args + L.arg0, d_bs[q], d_tf[q], (int)L.scenes.size()};
@@ -1400,7 +1447,7 @@ int flip_batch_step(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t ns
       else FLIP_CUDA(launch_pcg_batch(pb, L.mixed, nblk, bs));
       ++batch_launches;
     }
-    if (timed) FLIP_CUDA(cudaEventRecord(b->ev_pcg1, bs));
+    if (timed) FLIP_CUDA(cudaEventRecord(b->pev[2 * (size_t)timed_steps + 1], bs));
     FLIP_CUDA(cudaEventRecord(b->ev_solved, bs));
     for (int s = 0; s < n; ++s) {
       flip_handle* h = hs[s];
@@ -1413,12 +1460,7 @@ int flip_batch_step(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t ns
       h->stepped = true;
     }
     FLIP_CUDA(cudaGetLastError());
-    if (timed) {
-      FLIP_CUDA(cudaEventSynchronize(b->ev_pcg1));
-      float t = 0.0f;
-      FLIP_CUDA(cudaEventElapsedTime(&t, b->ev_pcg0, b->ev_pcg1));
-      ms_pcg += t;
-    }
+    if (timed) ++timed_steps;
     return FLIP_OK;
   };
   int done = 0;
@@ -1444,6 +1486,11 @@ int flip_batch_step(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t ns
   FLIP_CUDA(cudaEventSynchronize(b->ev_end));
   float ms_total = 0.0f;
   FLIP_CUDA(cudaEventElapsedTime(&ms_total, b->ev_begin, b->ev_end));
+  for (int st = 0; st < timed_steps; ++st) {
+    float t = 0.0f;
+    FLIP_CUDA(cudaEventElapsedTime(&t, b->pev[2 * (size_t)st], b->pev[2 * (size_t)st + 1]));
+    ms_pcg += t;
+  }
   int first_rc = FLIP_OK;
   for (int s = 0; s < n; ++s) {
     flip_handle* h = hs[s];
@@ -1553,7 +1600,7 @@ int flip_solve_pressure(const flip_params* params, const uint8_t* type, const fl
     a.tol = params->cg_tol;
     a.max_iter = params->cg_max_iter;
     a.check_singular = 1;
-    a.timeout_ns = 5000000000ull;
+    a.timeout_ns = kBarrierWaitNs;
     e = launch_pcg(a, false, blocks, s);
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(&hst, st, sizeof(DevStats), cudaMemcpyDeviceToHost, s);
@@ -1570,6 +1617,15 @@ int flip_solve_pressure(const flip_params* params, const uint8_t* type, const fl
 }  // extern "C"
 
 namespace flipk {
+int api_check_params(const flip_params* p, bool with_particles) {
+  return check_params(p, with_particles);
+}
+int api_check_device() { return check_device(); }
+Grid api_make_grid(const flip_params& p) { return make_grid(p); }
+void api_fill_pcg_tables(PcgArgs& a, const flip_params& p) { fill_pcg_tables(a, p); }
+int api_status_to_code(int dev_status) { return status_to_code(dev_status); }
+unsigned long long api_barrier_wait_ns() { return kBarrierWaitNs; }
+
 // The current particle buffer of a handle and its stream (for k_surface.cu).
 bool handle_particles(flip_handle* h, PartView* p, long long* np, cudaStream_t* s) {
   if (!h || refresh_np(h) != FLIP_OK) return false;

@@ -37,6 +37,7 @@ struct StepConsts {
                      // written by the step's first kernel, which replace gdt and
                      // dt; nullptr for a fixed step.  The solve then runs on the
                      // dt-free unknown q = dt p / (rho dx^2) (pscale = dx).
+  unsigned long long wait_ns;  // limit of G2P's bounded waits for its bulk copies
 };
 
 // The step constants a kernel uses: the host values, with g*dt and dt taken
@@ -118,7 +119,8 @@ struct PcgArgs {
   Grid g;
   float diag_tab[8];   // dt/(rho dx^2) * count
   float minv_tab[8];   // 1 / diag
-  float s;             // dt/(rho dx^2)
+  float s;             // dt/(rho dx^2) rounded to FP32
+  float s_lo;          // s64 - s rounded to FP32: (s, s_lo) is the scale as a float pair
   double s64;
   const uint8_t* type;
   const unsigned int* active;

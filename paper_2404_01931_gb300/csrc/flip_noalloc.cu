@@ -9,12 +9,15 @@
 // list, reduction slots, barrier, statistics) lives in one file-scope device
 // array of fixed size, reserved when the library's device code is loaded and held
 // by every GPU that loads it until the process exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
 #include <string>
 
 #include "../../include/flip.h"
+#include "flip_api_internal.cuh"
 #include "flip_kernels.cuh"
 
 using namespace flipk;
@@ -23,7 +26,7 @@ namespace {
 
 constexpr long long kMaxCells = FLIP_NOALLOC_MAX_CELLS;
 constexpr unsigned int kMaxBricks = FLIP_NOALLOC_MAX_BRICKS;
-constexpr int kMaxBlocks = 2048;
+constexpr int kMaxBlocks = 2048;  // reduction slots: one per co-resident solver CTA
 constexpr int kMaxDevices = 64;
 
 constexpr size_t kAlign = 256;
@@ -43,8 +46,42 @@ constexpr size_t kScratchBytes = kOffStats + al(sizeof(DevStats));
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
+// The array's device address per device, with the id of the context it was looked
+// up in: a context created after cudaDeviceReset may place the array elsewhere, so
+// a cached address is only used while the same context is current.
+struct ScratchAddr {
+  char* ptr = nullptr;
+  unsigned long long ctx = 0;
+};
 std::mutex g_mu;
-char* g_scratch_ptr[kMaxDevices] = {};
+ScratchAddr g_scratch[kMaxDevices];
+
+// Id of the current context (unique per context over the process's life), 0 when
+// none is current or the driver does not provide one.  Driver entry points are
+// taken through the runtime, so the library links no driver library.
+unsigned long long current_context_id() {
+  static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+  static PFN_cuCtxGetId_v12000 get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    cudaDriverEntryPointQueryResult q;
+    void* f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 4000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current = (PFN_cuCtxGetCurrent_v4000)f;
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = (PFN_cuCtxGetId_v12000)f;
+    cudaGetLastError();
+    looked_up = true;
+  }
+  if (!get_current || !get_id) return 0;
+  CUcontext c = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
 
 }  // namespace
 
@@ -58,59 +95,55 @@ extern "C" int flip_solve_pressure_noalloc(const flip_params* params, const uint
     flip_set_last_error_("flip_solve_pressure_noalloc: " + msg);
     return code;
   };
-  if (!params || !type || !b || !p) return err(FLIP_E_ARG, "params, type, b and p are required");
-  for (int a = 0; a < 3; ++a)
-    if (params->n[a] < 2 || params->n[a] > 2048) return err(FLIP_E_ARG, "n[a] must be in [2, 2048]");
-  if (params->precision != FLIP_PREC_FP32) return err(FLIP_E_ARG, "FP32 solver only");
-  if (!(params->dx > 0.0) || !(params->dt > 0.0) || !(params->rho > 0.0) ||
-      !(params->cg_tol > 0.0) || params->cg_max_iter < 1)
-    return err(FLIP_E_ARG, "dx, dt, rho, cg_tol must be > 0 and cg_max_iter >= 1");
+  // The same checks as flip_solve_pressure, so both refuse the same inputs.
+  if (int rc = api_check_params(params, false)) return rc;
+  if (params->precision != FLIP_PREC_FP32)
+    return err(FLIP_E_ARG, "runs the FP32 solver only");
+  if (!type || !b || !p) return err(FLIP_E_ARG, "type, b and p must be device pointers");
   const long long nc = (long long)params->n[0] * params->n[1] * params->n[2];
-  Grid g{};
-  g.nx = params->n[0];
-  g.ny = params->n[1];
-  g.nz = params->n[2];
-  g.bx = (g.nx + BRICK - 1) / BRICK;
-  g.by = (g.ny + BRICK - 1) / BRICK;
-  g.bz = (g.nz + BRICK - 1) / BRICK;
-  g.inv_dx = (float)(1.0 / params->dx);
-  g.dx = (float)params->dx;
+  const Grid g = api_make_grid(*params);
   const unsigned long long nb = (unsigned long long)g.bx * g.by * g.bz;
   // Sizes beyond the fixed scratch are refused before any device work.
   if (nc > kMaxCells || nb > kMaxBricks)
     return err(FLIP_E_SIZE, "grid of " + std::to_string(nc) + " cells / " + std::to_string(nb) +
                                 " bricks exceeds the fixed scratch (" + std::to_string(kMaxCells) +
                                 " cells, " + std::to_string(kMaxBricks) + " bricks)");
-
+  if (int rc = api_check_device()) return rc;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     cudaGetLastError();
     return err(FLIP_E_NOGPU, "no usable CUDA device");
   }
-  int major = 0, minor = 0;
-  if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess ||
-      major != 10 || minor != 3)
-    return err(FLIP_E_NOGPU, "built for sm_103a (GB300)");
   char* base = nullptr;
   {
-    // One-time set-up per device, with that device current: the host-side name of
-    // the array is only a stand-in, so its device address is looked up here.
+    // Set-up per device (and per context of that device), with the device
+    // current: the host-side name of the array is only a stand-in, so its device
+    // address is looked up here.  The first call on a device does it.
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_ptr[dev]) {
+    ScratchAddr& sa = g_scratch[dev];
+    const unsigned long long ctx = current_context_id();
+    if (!sa.ptr || ctx == 0 || ctx != sa.ctx) {
       void* ptr = nullptr;
       const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
       if (e != cudaSuccess || !ptr) {
         cudaGetLastError();
+        sa = ScratchAddr{};
         return err(FLIP_E_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
       }
-      g_scratch_ptr[dev] = (char*)ptr;
+      sa.ptr = (char*)ptr;
+      sa.ctx = current_context_id();  // the look-up made the device's context current
     }
-    base = g_scratch_ptr[dev];
+    base = sa.ptr;
   }
   int blocks = 0, sms = 0;
-  if (pcg_max_blocks(&blocks, &sms) != cudaSuccess || blocks > kMaxBlocks)
-    return err(FLIP_E_CUDA, "occupancy query failed");
+  if (cudaError_t e = pcg_max_blocks(&blocks, &sms); e != cudaSuccess) {
+    cudaGetLastError();
+    return err(FLIP_E_CUDA, std::string("occupancy query: ") + cudaGetErrorString(e));
+  }
+  if (blocks > kMaxBlocks)
+    return err(FLIP_E_CUDA, "the device holds " + std::to_string(blocks) +
+                                " co-resident solver CTAs, more than the fixed scratch's " +
+                                std::to_string(kMaxBlocks) + " reduction slots");
 
   const cudaStream_t s = (cudaStream_t)stream;
   float* r = (float*)(base + kOffR);
@@ -135,13 +168,7 @@ extern "C" int flip_solve_pressure_noalloc(const flip_params* params, const uint
   if (e == cudaSuccess) {
     PcgArgs a{};
     a.g = g;
-    const double sc = params->dt / (params->rho * params->dx * params->dx);
-    a.s = (float)sc;
-    a.s64 = sc;
-    for (int c = 0; c < 8; ++c) {
-      a.diag_tab[c] = (float)(sc * c);
-      a.minv_tab[c] = c > 0 ? (float)(1.0 / (sc * c)) : 0.0f;
-    }
+    api_fill_pcg_tables(a, *params);
     a.type = type;
     a.active = act;
     a.n_active = &st->n_active;
@@ -158,7 +185,7 @@ extern "C" int flip_solve_pressure_noalloc(const flip_params* params, const uint
     a.tol = params->cg_tol;
     a.max_iter = params->cg_max_iter;
     a.check_singular = 1;
-    a.timeout_ns = 5000000000ull;
+    a.timeout_ns = api_barrier_wait_ns();
     e = launch_pcg(a, false, blocks, s);
   }
   DevStats hst{};
@@ -167,8 +194,5 @@ extern "C" int flip_solve_pressure_noalloc(const flip_params* params, const uint
   if (e != cudaSuccess) return err(FLIP_E_CUDA, cudaGetErrorString(e));
   if (iterations) *iterations = hst.cg_iters;
   if (rel_residual) *rel_residual = hst.rel_res;
-  if (hst.status & DEV_TIMEOUT) return err(FLIP_E_TIMEOUT, "a device-side wait timed out");
-  if (hst.status & DEV_SINGULAR) return err(FLIP_E_ARG, "every cell is fluid: A is singular");
-  if (hst.status & DEV_NOT_CONVERGED) return err(FLIP_E_NOT_CONVERGED, "iteration cap reached");
-  return FLIP_OK;
+  return api_status_to_code(hst.status);
 }

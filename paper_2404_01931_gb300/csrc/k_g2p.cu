@@ -51,8 +51,10 @@ struct PTile<false> {
 // boundaries: a chunk [q0, q1) is copied as [q0 & ~3, (q1 + 3) & ~3), which stays
 // inside its array (every array of the arena is padded to 256 bytes).
 constexpr int G2P_CHUNK_PAD = G2P_THREADS + 8;
-constexpr unsigned long long G2P_WAIT_NS = 1000000000ull;  // a copy that takes longer
-                                                           // is reported as a timeout
+// After a wait has given up (StepConsts::wait_ns), the copies still in flight are
+// waited for once more, up to this limit, before the CTA leaves: its shared memory
+// must not be handed to another CTA while the copy engine still writes into it.
+constexpr unsigned long long G2P_DRAIN_NS = 1000000000ull;
 
 __device__ __forceinline__ unsigned int smem_u32(const void* p) {
   return (unsigned int)__cvta_generic_to_shared(p);
@@ -80,12 +82,13 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
   return ok != 0;
 }
 
-// Bounded wait for phase `parity` of the barrier; false after G2P_WAIT_NS.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned int parity) {
+// Bounded wait for phase `parity` of the barrier; false after limit_ns.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned int parity,
+                                          unsigned long long limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_timer_ns();
   while (!mbar_try_wait(bar, parity))
-    if (global_timer_ns() - t0 > G2P_WAIT_NS) return false;
+    if (global_timer_ns() - t0 > limit_ns) return false;
   return true;
 }
 
@@ -214,8 +217,8 @@ __global__ void __launch_bounds__(G2P_THREADS, 5) k_g2p(const Grid g, const Step
   }
   __syncthreads();
   unsigned int phase[2] = {0u, 0u};
-  unsigned int kbuf = 0;  // buffer of the next chunk
-  bool pending = false;   // a chunk copy is in flight
+  unsigned int kbuf = 0;                 // buffer of the next chunk
+  bool inflight[2] = {false, false};     // thread 0: a copy into the buffer is unwaited
   for (unsigned int bi = blockIdx.x; bi < nact; bi += gridDim.x) {
     const unsigned int brick = B.active[bi];
     const int b0 = (int)(brick % (unsigned)g.bx) * BRICK;
@@ -225,7 +228,7 @@ __global__ void __launch_bounds__(G2P_THREADS, 5) k_g2p(const Grid g, const Step
     // the brick's first chunk streams in while the tiles are staged
     if (threadIdx.x == 0 && bstart < bend) {
       issue_chunk(P, bstart, min(bend, bstart + G2P_THREADS), pbuf[kbuf], &bar[kbuf]);
-      pending = true;
+      inflight[kbuf] = true;
     }
     // pressure of cells [b - 1, b + 8] per axis (0 outside the grid: never used)
     for (int t = threadIdx.x; t < G2P_PTILE; t += G2P_THREADS) {
@@ -250,14 +253,19 @@ __global__ void __launch_bounds__(G2P_THREADS, 5) k_g2p(const Grid g, const Step
       // the next chunk goes into the other buffer, whose readers passed the
       // __syncthreads that ended the previous chunk
       const unsigned int n0 = c0 + G2P_THREADS;
-      if (threadIdx.x == 0 && n0 < bend)
+      if (threadIdx.x == 0 && n0 < bend) {
         issue_chunk(P, n0, min(bend, n0 + G2P_THREADS), pbuf[kbuf], &bar[kbuf]);
-      if (!mbar_wait(&bar[cur], phase[cur])) {
+        inflight[kbuf] = true;
+      }
+      // a thread whose wait gives up reads nothing of the chunk; one whose wait
+      // succeeded saw the whole chunk land
+      if (mbar_wait(&bar[cur], phase[cur], K.wait_ns)) {
+        phase[cur] ^= 1u;
+        inflight[cur] = false;
+      } else {
         atomicOr(&st->status, DEV_TIMEOUT);
         s_abort = 1;
       }
-      phase[cur] ^= 1u;
-      pending = n0 < bend;
       const float(*pb)[G2P_CHUNK_PAD] = pbuf[cur];
       const unsigned int a0 = c0 & ~3u;
       const unsigned int q = c0 + threadIdx.x;
@@ -323,9 +331,13 @@ __global__ void __launch_bounds__(G2P_THREADS, 5) k_g2p(const Grid g, const Step
     __syncthreads();
     if (s_abort) break;
   }
-  // a copy still in flight (only after an abort: the chunk issued into kbuf) is
-  // waited for, boundedly
-  if (pending && threadIdx.x == 0) (void)mbar_wait(&bar[kbuf], phase[kbuf]);
+  // After an abort, thread 0 drains the copies it issued and nobody waited for
+  // (the chunk whose wait gave up, the one issued after it), boundedly; the CTA's
+  // shared memory stays allocated until thread 0 leaves.
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+      if (inflight[k]) (void)mbar_wait(&bar[k], phase[k], G2P_DRAIN_NS);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) speed2 = fmaxf(speed2, __shfl_xor_sync(0xffffffffu, speed2, o));
   if (lane == 0 && speed2 > 0.0f) atomicMax(&st->max_speed_bits, __float_as_uint(sqrtf(speed2)));

@@ -1165,56 +1165,18 @@ __device__ __forceinline__ void for_fluid0(const PcgArgs& A, F&& f) {
   }
 }
 
-// ---------------------------------------------------------------- float pairs
-
-// Error-free transforms (Knuth's TwoSum, Dekker's FastTwoSum, the FMA product):
-// a value is carried as hi + lo, ~48 significant bits, all on the FP32 pipes
-// (GB300's FP64 pipe is narrow, and the refinement touches every fluid cell).
-__device__ __forceinline__ float2 two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bv = __fsub_rn(s, a);
-  return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bv)), __fsub_rn(b, bv)));
-}
-
-__device__ __forceinline__ float2 fast_two_sum(float a, float b) {  // |a| >= |b|
-  const float s = __fadd_rn(a, b);
-  return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
-}
-
-__device__ __forceinline__ float2 pair_add(float2 x, float2 y) {
-  const float2 t = two_sum(x.x, y.x);
-  return fast_two_sum(t.x, __fadd_rn(t.y, __fadd_rn(x.y, y.y)));
-}
-
-__device__ __forceinline__ float2 pair_neg(float2 x) { return make_float2(-x.x, -x.y); }
-
-// (hi, lo) * f for a float f, with the exact product of the hi parts.
-__device__ __forceinline__ float2 pair_mul(float2 x, float f) {
-  const float p = __fmul_rn(x.x, f);
-  const float e = __fmaf_rn(x.x, f, -p);
-  return fast_two_sum(p, __fmaf_rn(x.y, f, e));
-}
-
 // Residual b - A x of one level-0 cell with x and b as float pairs (split
-// layout), A x in difference form s ((cnt - nfl) x_c + sum_fluid (x_c - x_n)).
+// layout); the arithmetic is residual_pair_cell's.
 __device__ __forceinline__ float2 residual_pair(const SV& v, const float2* x2, const float2* b2,
-                                                const SCell& e, unsigned int code, float s) {
+                                                const SCell& e, unsigned int code, float s_hi,
+                                                float s_lo) {
   int nb[6];
   snbr(v, e, nb);
   const float2 xc = x2[e.idx];
   float2 xn[6];
 #pragma unroll
   for (int q = 0; q < 6; ++q) xn[q] = x2[nb[q]];
-  float2 acc = make_float2(0.0f, 0.0f);
-  int nfl = 0;
-#pragma unroll
-  for (int q = 0; q < 6; ++q) {
-    if (!((code >> q) & 1u)) continue;
-    acc = pair_add(acc, pair_add(xc, pair_neg(xn[q])));
-    ++nfl;
-  }
-  acc = pair_add(acc, pair_mul(xc, (float)(code_cnt(code) - nfl)));
-  return pair_add(b2[e.idx], pair_neg(pair_mul(acc, s)));
+  return residual_pair_cell(b2[e.idx], xc, xn, code & 63u, code_cnt(code), s_hi, s_lo);
 }
 
 // ---------------------------------------------------------------- set-up
@@ -1394,7 +1356,7 @@ __device__ void solve_mg(const PcgArgs& A, Shared& sh, CtaMg& sm, SolveState& S)
       if constexpr (MIXED) {
         if (warm) {
           bc = M.b2[e.idx].x;
-          const float2 rp = residual_pair(v0, M.x2, M.b2, e, code, s_a);
+          const float2 rp = residual_pair(v0, M.x2, M.b2, e, code, s_a, A.s_lo);
           rc = __fadd_rn(rp.x, rp.y);
         } else {
           const double b64 = A.b64[n];
@@ -1517,7 +1479,7 @@ __device__ void solve_mg(const PcgArgs& A, Shared& sh, CtaMg& sm, SolveState& S)
         const SV v0 = sview(L0);
         const float s_a = A.s;
         for_fluid0(A, [&](const SCell& e, unsigned int code, int) {
-          const float2 rp = residual_pair(v0, M.x2, M.b2, e, code, s_a);
+          const float2 rp = residual_pair(v0, M.x2, M.b2, e, code, s_a, A.s_lo);
           const float r32 = __fadd_rn(rp.x, rp.y);
           r[e.idx] = r32;
           if (e.idx < L0.half) z[e.idx] = gs_first(0, code_cnt(code), r32);

@@ -76,6 +76,64 @@ __device__ __forceinline__ void cta_sum(F2 (&v)[K], F2* scratch) {
   __syncthreads();
 }
 
+// ---------------------------------------------------------------- float pairs
+
+// Error-free transforms (Knuth's TwoSum, Dekker's FastTwoSum, the FMA product):
+// a value is carried as hi + lo, ~48 significant bits, all on the FP32 pipes
+// (GB300's FP64 pipe is narrow, and the refinement touches every fluid cell).
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bv = __fsub_rn(s, a);
+  return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bv)), __fsub_rn(b, bv)));
+}
+
+__device__ __forceinline__ float2 fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+
+__device__ __forceinline__ float2 pair_add(float2 x, float2 y) {
+  const float2 t = two_sum(x.x, y.x);
+  return fast_two_sum(t.x, __fadd_rn(t.y, __fadd_rn(x.y, y.y)));
+}
+
+__device__ __forceinline__ float2 pair_neg(float2 x) { return make_float2(-x.x, -x.y); }
+
+// (hi, lo) * f for a float f, with the exact product of the hi parts.
+__device__ __forceinline__ float2 pair_mul(float2 x, float f) {
+  const float p = __fmul_rn(x.x, f);
+  const float e = __fmaf_rn(x.x, f, -p);
+  return fast_two_sum(p, __fmaf_rn(x.y, f, e));
+}
+
+// (hi, lo) * (s_hi, s_lo): the exact product of the hi parts plus the two cross
+// terms (the lo * s_lo term is below the pair's precision).
+__device__ __forceinline__ float2 pair_mul_pair(float2 x, float s_hi, float s_lo) {
+  const float p = __fmul_rn(x.x, s_hi);
+  const float e = __fmaf_rn(x.x, s_hi, -p);
+  return fast_two_sum(p, __fmaf_rn(x.x, s_lo, __fmaf_rn(x.y, s_hi, e)));
+}
+
+// The mixed mode's residual of one cell, b - A x, with x, b and the operator's
+// scale s = dt/(rho dx^2) as float pairs (Sec. 3.1.7's 7-point row): A x in
+// difference form s ((cnt - nfl) x_c + sum over fluid neighbours (x_c - x_n)),
+// bit q of `fluid` set when neighbour q is fluid, cnt the non-wall neighbours.
+// The refinement of the multigrid solve and flip_residual_pairs both call it.
+__device__ __forceinline__ float2 residual_pair_cell(float2 b, float2 xc, const float2 (&xn)[6],
+                                                     unsigned int fluid, int cnt, float s_hi,
+                                                     float s_lo) {
+  float2 acc = make_float2(0.0f, 0.0f);
+  int nfl = 0;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    if (!((fluid >> q) & 1u)) continue;
+    acc = pair_add(acc, pair_add(xc, pair_neg(xn[q])));
+    ++nfl;
+  }
+  acc = pair_add(acc, pair_mul(xc, (float)(cnt - nfl)));
+  return pair_add(b, pair_neg(pair_mul_pair(acc, s_hi, s_lo)));
+}
+
 // ------------------------------------------------------------ cell ownership
 
 struct Chunk {

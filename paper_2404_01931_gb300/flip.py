@@ -175,6 +175,11 @@ def lib():
         L.flip_surface_destroy.argtypes = [vp]
         L.flip_surface_destroy.restype = None
         L.flip_surface_case_table.argtypes = [vp, vp]
+        L.flip_step_times.argtypes = [vp, vp, i32]
+        L.flip_step_times.restype = i32
+        L.flip_set_wait_timeout.argtypes = [vp, C.c_uint64]
+        L.flip_dot_f32.argtypes = [vp, vp, i64, C.POINTER(C.c_double), vp]
+        L.flip_residual_pairs.argtypes = [PP, vp, vp, vp, vp, vp, vp, vp, vp]
         if L.flip_abi_version() != 5:
             raise RuntimeError("libflip_gb300 ABI version mismatch")
         _lib = L
@@ -265,7 +270,12 @@ def flip_create(params: FlipParams, x, y, z, u, v, w, stream=None, allocator="to
             keep.append(ta)
             alloc_ptr = C.byref(ta.struct)
     elif allocator is not None:
-        raise ValueError("allocator must be 'torch' or None")
+        # any object holding a FlipAlloc in .struct (callbacks kept alive by it)
+        if not isinstance(getattr(allocator, "struct", None), FlipAlloc):
+            raise ValueError("allocator must be 'torch', None or an object with a FlipAlloc "
+                             ".struct")
+        keep.append(allocator)
+        alloc_ptr = C.byref(allocator.struct)
     h = C.c_void_p()
     rc = lib().flip_create(C.byref(params), *[C.c_void_p(b[0]) for b in bufs], np_, bufs[0][2],
                            alloc_ptr, C.c_void_p(stream or 0), C.byref(h))
@@ -340,13 +350,28 @@ def flip_destroy(h):
         lib().flip_destroy(h)
 
 
+def _grid_cells(params: FlipParams) -> int:
+    return int(params.n[0]) * int(params.n[1]) * int(params.n[2])
+
+
+def _solve_buffers(params: FlipParams, type_, b, p, name: str):
+    """Device pointers of the solve's arrays, each checked to hold one entry per
+    cell of params.n (the library reads and writes that many)."""
+    tp, tn, tdev, _ = _buf(type_, np.uint8)
+    bp, bn, bdev, _ = _buf(b, np.float32)
+    pp, pn, pdev, _ = _buf(p, np.float32)
+    nc = _grid_cells(params)
+    if tn != nc or bn != 4 * nc or pn != 4 * nc:
+        raise FlipError(FLIP_E_SIZE, f"{name}: type, b and p must hold {nc} cells each "
+                                     f"(got {tn}, {bn // 4}, {pn // 4})")
+    if not (tdev and bdev and pdev):
+        raise ValueError(f"{name} takes device buffers")
+    return tp, bp, pp
+
+
 def flip_solve_pressure(params: FlipParams, type_, b, p, stream=None):
     """A p = b on device tensors (uint8 types, float32 b and p); returns (status, iters, rel)."""
-    tp, _, tdev, _ = _buf(type_, np.uint8)
-    bp, _, bdev, _ = _buf(b, np.float32)
-    pp, _, pdev, _ = _buf(p, np.float32)
-    if not (tdev and bdev and pdev):
-        raise ValueError("flip_solve_pressure takes device buffers")
+    tp, bp, pp = _solve_buffers(params, type_, b, p, "flip_solve_pressure")
     it = C.c_int32(0)
     rel = C.c_double(0.0)
     rc = lib().flip_solve_pressure(C.byref(params), C.c_void_p(tp), C.c_void_p(bp),
@@ -360,11 +385,7 @@ def flip_solve_pressure_noalloc(params: FlipParams, type_, b, p, stream=None):
     allocate while they run (memory owned by a host application's allocator, or
     loops where cudaMalloc/cudaFree may not synchronise the device).  Grids up to
     FLIP_NOALLOC_MAX_CELLS cells.  Returns (status, iterations, rel_residual)."""
-    tp, _, tdev, _ = _buf(type_, np.uint8)
-    bp, _, bdev, _ = _buf(b, np.float32)
-    pp, _, pdev, _ = _buf(p, np.float32)
-    if not (tdev and bdev and pdev):
-        raise ValueError("flip_solve_pressure_noalloc takes device buffers")
+    tp, bp, pp = _solve_buffers(params, type_, b, p, "flip_solve_pressure_noalloc")
     it = C.c_int32(0)
     rel = C.c_double(0.0)
     rc = lib().flip_solve_pressure_noalloc(C.byref(params), C.c_void_p(tp), C.c_void_p(bp),
@@ -374,6 +395,36 @@ def flip_solve_pressure_noalloc(params: FlipParams, type_, b, p, stream=None):
 
 
 FLIP_NOALLOC_MAX_CELLS = 262144
+
+
+def flip_dot_f32(a, b, stream=None) -> float:
+    """sum a[i] b[i] of two float32 device tensors by the CG's reduction (float
+    pairs per thread, warp and CTA; FP64 at the end)."""
+    ap, an, adev, _ = _buf(a, np.float32)
+    bp, bn, bdev, _ = _buf(b, np.float32)
+    if an != bn:
+        raise FlipError(FLIP_E_SIZE, "a and b must have one length")
+    if an and not (adev and bdev):
+        raise ValueError("flip_dot_f32 takes device buffers")
+    out = C.c_double(0.0)
+    _check(lib().flip_dot_f32(C.c_void_p(ap), C.c_void_p(bp), an // 4, C.byref(out),
+                              C.c_void_p(stream or 0)))
+    return float(out.value)
+
+
+def flip_residual_pairs(params: FlipParams, type_, x_hi, x_lo, b_hi, b_lo, r_hi, r_lo,
+                        stream=None):
+    """r = b - A x in float pairs on the grid of params (the mixed-mode refinement's
+    residual); every array is a device tensor with one entry per cell."""
+    nc = _grid_cells(params)
+    tp, tn, tdev, _ = _buf(type_, np.uint8)
+    fl = [_buf(a, np.float32) for a in (x_hi, x_lo, b_hi, b_lo, r_hi, r_lo)]
+    if tn != nc or any(f[1] != 4 * nc for f in fl):
+        raise FlipError(FLIP_E_SIZE, f"flip_residual_pairs: every array must hold {nc} cells")
+    if not (tdev and all(f[2] for f in fl)):
+        raise ValueError("flip_residual_pairs takes device buffers")
+    _check(lib().flip_residual_pairs(C.byref(params), C.c_void_p(tp),
+                                     *[C.c_void_p(f[0]) for f in fl], C.c_void_p(stream or 0)))
 
 
 def flip_batch_create(capacity: int, stream=None):
@@ -609,6 +660,20 @@ class Simulation:
 
     def write(self, field: int, src):
         flip_write(self.h, field, src)
+
+    def step_times(self):
+        """Device ms of each step of the last step(..., stats=True) call (numpy)."""
+        n = int(lib().flip_step_times(self.h, None, 0))
+        if n < 0:
+            _check(-n)
+        out = np.zeros(n, np.float64)
+        if n:
+            lib().flip_step_times(self.h, out.ctypes.data_as(C.c_void_p), n)
+        return out
+
+    def set_wait_timeout(self, ns: int):
+        """Limit of the handle's bounded device-side waits (0: the defaults)."""
+        _check(lib().flip_set_wait_timeout(self.h, int(ns)))
 
     def set_solver_blocks(self, nblocks: int):
         _check(lib().flip_set_solver_blocks(self.h, int(nblocks)))

@@ -225,3 +225,59 @@ def test_surface_bin_grid_limit(F):
     with pytest.raises(F.FlipError) as ei:
         F.Surface(F.surface_default_params(F.default_params(1024)))   # 1029^3 bins
     assert ei.value.code == F.FLIP_E_NOGPU
+
+
+def test_solve_wrappers_check_buffer_sizes(F):
+    """The standalone solves read and write one entry per cell of params.n: a short
+    buffer is refused on the host before any device call."""
+    import torch
+    p = F.default_params(8)
+    nc = 8 ** 3
+    t = torch.zeros(nc, dtype=torch.uint8)
+    good = torch.zeros(nc, dtype=torch.float32)
+    short = torch.zeros(nc - 1, dtype=torch.float32)
+    for fn in (F.flip_solve_pressure, F.flip_solve_pressure_noalloc):
+        for args in ((t, short, good), (t, good, short), (t[:-1], good, good)):
+            with pytest.raises(F.FlipError) as ei:
+                fn(p, *args)
+            assert ei.value.code == F.FLIP_E_SIZE
+
+
+@pytest.mark.parametrize("field,value", [("dx", 0.3), ("dt", float("inf")), ("dx", 0.0),
+                                         ("rho", -1.0), ("cg_max_iter", 0),
+                                         ("precision", 1)])
+def test_both_solves_refuse_the_same_params(F, field, value):
+    """flip_solve_pressure and its allocation-free variant share their parameter
+    checks: both refuse (FLIP_E_ARG) before touching a device."""
+    p = F.default_params(8)
+    setattr(p, field, value)
+    L = F.lib()
+    it = ctypes.c_int32(0)
+    rel = ctypes.c_double(0.0)
+    args = (ctypes.byref(p), None, None, None, None, ctypes.byref(it), ctypes.byref(rel))
+    assert L.flip_solve_pressure(*args) == F.FLIP_E_ARG
+    assert L.flip_solve_pressure_noalloc(*args) == F.FLIP_E_ARG
+
+
+def test_precision_entry_points_check_arguments(F):
+    """flip_dot_f32 and flip_residual_pairs refuse bad arguments on the host."""
+    L = F.lib()
+    out = ctypes.c_double(0.0)
+    assert L.flip_dot_f32(None, None, -1, ctypes.byref(out), None) == F.FLIP_E_ARG
+    assert L.flip_dot_f32(None, None, 4, None, None) == F.FLIP_E_ARG
+    assert L.flip_dot_f32(None, None, 4, ctypes.byref(out), None) == F.FLIP_E_ARG
+    p = F.default_params(8)
+    p.dx = 0.3
+    assert L.flip_residual_pairs(ctypes.byref(p), *([None] * 7), None) == F.FLIP_E_ARG
+    p = F.default_params(8)
+    assert L.flip_residual_pairs(ctypes.byref(p), *([None] * 7), None) == F.FLIP_E_ARG
+    import torch
+    with pytest.raises(F.FlipError) as ei:
+        F.flip_dot_f32(torch.zeros(4), torch.zeros(5))
+    assert ei.value.code == F.FLIP_E_SIZE
+
+
+def test_handle_entry_points_refuse_null(F):
+    L = F.lib()
+    assert L.flip_step_times(None, None, 0) == -F.FLIP_E_ARG
+    assert L.flip_set_wait_timeout(None, 1000) == F.FLIP_E_ARG
