@@ -5,12 +5,17 @@
  *
  * The server keeps scenes resident on the current device, admits them by their
  * device footprint (flip_footprint_bytes) within a byte budget, and runs step
- * requests on a worker thread.  Each request asks for one FLIP step of one scene
- * and carries an arrival time.  Whenever the GPU finishes a batch, the worker
- * forms the next one from the requests that have arrived, one per scene, up to
- * max_batch scenes, oldest first, and advances them together with
- * flip_batch_step: requests that arrive while a batch runs join the next batch
- * (continuous batching), and the scenes of a batch share one solve launch.
+ * requests on worker threads.  Each request asks for one FLIP step of one scene
+ * and carries an arrival time.  Two batches can be in flight at once: while the
+ * GPU runs one, the launcher forms the next from the requests that have arrived
+ * for scenes not in flight, one per scene, up to max_batch scenes, oldest first,
+ * and enqueues it behind the first (the batch stepping of flip_batch_step: the
+ * scenes of a batch share one solve launch).  Requests that arrive while batches
+ * run join later batches (continuous batching); the next batch's binning and P2G
+ * overlap the previous batch's G2P on the device, and the solve launches of the
+ * two batches run one after the other.  A completer thread finishes each request
+ * as soon as its own scene's step is done on the device (an event on the scene's
+ * stream), not when its whole batch is. 
  *
  * Times are seconds on the server's clock (steady clock, 0 at creation).
  * Functions return FLIP_* status codes (include/flip.h) and are safe to call
@@ -32,8 +37,8 @@ typedef struct {
   int32_t scene;
   int32_t status;         /* FLIP_OK, or the step's condition (e.g. FLIP_E_NOT_CONVERGED) */
   double t_arrival;       /* when the request became eligible */
-  double t_start;         /* when its batch was launched */
-  double t_done;          /* when its batch had finished on the GPU */
+  double t_start;         /* when its batch was formed and enqueued */
+  double t_done;          /* when its scene's step had finished on the GPU */
   int32_t batch_size;     /* scenes in the batch that served it */
   int32_t reserved;
 } flip_request_info;

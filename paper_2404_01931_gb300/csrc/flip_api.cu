@@ -1320,9 +1320,19 @@ void flip_batch_destroy(flip_batch* b) {
   delete b;
 }
 
-int flip_batch_step(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t nsteps,
-                    flip_stats* stats) {
+}  // extern "C"
+
+namespace {
+
+// flip_batch_step; with join = false (untimed calls only) the batch stream does not
+// wait for the scenes' G2P at the end, so the next call's uploads and solve can be
+// enqueued behind this call's solve while its G2P still runs on the scene streams
+// (the server's overlapped batches).  The caller then learns of each scene's end
+// from an event on the scene's stream.
+int batch_step_impl(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t nsteps,
+                    flip_stats* stats, bool join) {
   if (!b || (!hs && n > 0)) return fail(FLIP_E_ARG, "batch or handles are NULL");
+  if (!join && stats) return fail(FLIP_E_ARG, "statistics need the joined form");
   if (n < 0 || n > b->capacity) return fail(FLIP_E_ARG, "n must be in [0, capacity]");
   if (nsteps < 0) return fail(FLIP_E_ARG, "nsteps must be >= 0");
   for (int s = 0; s < n; ++s) {
@@ -1477,10 +1487,11 @@ int flip_batch_step(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t ns
     if (int rc = enqueue_step()) return rc;
   for (void* p : tmp_alloc) FLIP_CUDA(cudaFreeAsync(p, bs));
   // the batch stream joins every scene stream at the end of the call
-  for (int s = 0; s < n; ++s) {
-    FLIP_CUDA(cudaEventRecord(b->ev[s], hs[s]->stream));
-    FLIP_CUDA(cudaStreamWaitEvent(bs, b->ev[s], 0));
-  }
+  if (join)
+    for (int s = 0; s < n; ++s) {
+      FLIP_CUDA(cudaEventRecord(b->ev[s], hs[s]->stream));
+      FLIP_CUDA(cudaStreamWaitEvent(bs, b->ev[s], 0));
+    }
   if (!timed) return FLIP_OK;
   FLIP_CUDA(cudaEventRecord(b->ev_end, bs));
   FLIP_CUDA(cudaEventSynchronize(b->ev_end));
@@ -1529,7 +1540,21 @@ int flip_batch_step(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t ns
   return first_rc;
 }
 
-}  // extern "C"
+}  // namespace
+
+extern "C" int flip_batch_step(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t nsteps,
+                               flip_stats* stats) {
+  return batch_step_impl(b, hs, n, nsteps, stats, true);
+}
+
+namespace flipk {
+// One step of the scenes on the batch, without the final join (see batch_step_impl).
+int batch_step_overlapped(flip_batch* b, flip_handle* const* hs, int n) {
+  return batch_step_impl(b, hs, n, 1, nullptr, false);
+}
+// The stream a handle's kernels run on.
+cudaStream_t handle_stream(const flip_handle* h) { return h ? h->stream : nullptr; }
+}  // namespace flipk
 
 extern "C" {
 

@@ -1,7 +1,12 @@
 // flip_server.cu — continuous-batching step server over resident scenes
-// (include/flip_server.h).  Host code only: a worker thread admits scenes by
-// footprint, forms batches from the requests that have arrived and runs them
-// with flip_batch_step; callers submit and wait through the C ABI.
+// (include/flip_server.h).  Host code only.  A launcher thread admits scenes by
+// footprint, forms batches from the requests that have arrived and enqueues them;
+// a completer thread waits for each scene's step on the device and completes its
+// request.  Two batch slots are in flight at once: while the GPU runs one batch,
+// the next is formed and enqueued behind it, so the device does not idle across
+// the host's round trip, and the next batch's binning and P2G overlap the
+// previous batch's G2P on the device.  The two slots share one stream for their
+// pressure solves, so the cooperative solve launches never run concurrently.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -20,6 +25,11 @@
 #include "../../include/flip_server.h"
 
 void flip_set_last_error_(const std::string& msg);
+
+namespace flipk {
+int batch_step_overlapped(flip_batch* b, flip_handle* const* hs, int n);
+cudaStream_t handle_stream(const flip_handle* h);
+}  // namespace flipk
 
 namespace {
 
@@ -43,6 +53,18 @@ struct Request {
   bool done = false;
 };
 
+constexpr int kSlots = 2;  // batches in flight at once
+
+// A batch enqueued on the device: its requests, their scenes' handles, and one
+// event per scene recorded on the scene's stream after its step.
+struct InFlight {
+  int slot = 0;
+  int launch_status = FLIP_OK;
+  std::vector<int64_t> tickets;
+  std::vector<flip_handle*> hs;
+  std::vector<cudaEvent_t> done;
+};
+
 }  // namespace
 
 struct flip_server {
@@ -62,8 +84,14 @@ struct flip_server {
   size_t used = 0;
   int resident = 0;
   bool stop = false;
-  flip_batch* batch = nullptr;
-  std::thread worker;
+  bool launcher_done = false;
+  cudaStream_t solve_stream = nullptr;  // shared by the slots' batched solves
+  flip_batch* slot[kSlots] = {};
+  bool slot_busy[kSlots] = {};
+  std::vector<cudaEvent_t> event_pool;  // per-scene completion events, reused
+  std::deque<InFlight> inflight;
+  std::condition_variable cv_inflight;
+  std::thread worker, completer;
 
   double now() const {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -127,6 +155,28 @@ struct flip_server {
     outstanding -= 1;
   }
 
+  int free_slot_locked() const {
+    for (int k = 0; k < kSlots; ++k)
+      if (!slot_busy[k]) return k;
+    return -1;
+  }
+
+  cudaEvent_t take_event_locked() {
+    if (!event_pool.empty()) {
+      cudaEvent_t e = event_pool.back();
+      event_pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return e;
+  }
+
+  // Launcher: forms batches from arrived requests of idle resident scenes and
+  // enqueues them on a free slot, without waiting for the device.
   void run() {
     cudaSetDevice(device);
     std::unique_lock<std::mutex> lk(mu);
@@ -144,12 +194,13 @@ struct flip_server {
           ++q;
         }
       }
+      const int k = free_slot_locked();
       const double t = now();
       std::vector<int64_t> pick;
       std::vector<flip_handle*> hs;
       std::set<int> in_batch;
       double next_arrival = -1.0;
-      for (auto q = queue.begin(); q != queue.end() && (int)pick.size() < max_batch;) {
+      for (auto q = queue.begin(); k >= 0 && q != queue.end() && (int)pick.size() < max_batch;) {
         const Request& r = reqs[*q];
         Scene& sc = scenes[r.scene];
         const bool ready = sc.h && !sc.in_flight && !in_batch.count(r.scene);
@@ -164,37 +215,77 @@ struct flip_server {
         }
       }
       if (pick.empty()) {
-        if (stop) {
+        if (stop && inflight.empty()) {
           // no request can run any more: finish the rest as refused
           for (int64_t q : queue) complete_locked(q, FLIP_E_ARG, now(), 0);
           queue.clear();
           cv_done.notify_all();
           break;
         }
-        if (next_arrival >= 0.0)
+        // woken by a submission, an admission, a completed batch (a free slot or an
+        // idle scene) or the next arrival time
+        if (k >= 0 && next_arrival >= 0.0)
           cv_work.wait_for(lk, std::chrono::duration<double>(std::max(0.0, next_arrival - t)));
         else
           cv_work.wait(lk);
         continue;
       }
-      for (size_t k = 0; k < pick.size(); ++k) {
-        reqs[pick[k]].t_start = t;
-        scenes[reqs[pick[k]].scene].in_flight = true;
+      InFlight f;
+      f.slot = k;
+      f.tickets = pick;
+      f.hs = hs;
+      for (size_t q = 0; q < pick.size(); ++q) {
+        reqs[pick[q]].t_start = t;
+        reqs[pick[q]].batch_size = (int)pick.size();
+        scenes[reqs[pick[q]].scene].in_flight = true;
+        f.done.push_back(take_event_locked());
       }
+      slot_busy[k] = true;
       lk.unlock();
-      int rc = flip_batch_step(batch, hs.data(), (int32_t)hs.size(), 1, nullptr);
-      std::vector<int> st(hs.size(), rc);
-      for (size_t k = 0; k < hs.size(); ++k) {
-        const int s2 = flip_sync(hs[k]);
-        if (rc == FLIP_OK) st[k] = s2;
-      }
-      const double t_done = now();
+      f.launch_status = flipk::batch_step_overlapped(slot[k], hs.data(), (int)hs.size());
+      for (size_t q = 0; q < hs.size(); ++q)
+        if (!f.done[q] || cudaEventRecord(f.done[q], flipk::handle_stream(hs[q])) != cudaSuccess) {
+          cudaGetLastError();
+          if (f.launch_status == FLIP_OK) f.launch_status = FLIP_E_CUDA;
+        }
       lk.lock();
-      for (size_t k = 0; k < pick.size(); ++k) {
-        scenes[reqs[pick[k]].scene].in_flight = false;
-        complete_locked(pick[k], st[k], t_done, (int)pick.size());
+      inflight.push_back(std::move(f));
+      cv_inflight.notify_one();
+    }
+    launcher_done = true;
+    cv_inflight.notify_one();
+  }
+
+  // Completer: waits for the scenes of the oldest batch in order, each on its own
+  // event, and completes each request as soon as its scene's step is done.
+  void complete() {
+    cudaSetDevice(device);
+    std::unique_lock<std::mutex> lk(mu);
+    for (;;) {
+      cv_inflight.wait(lk, [&] { return !inflight.empty() || launcher_done; });
+      if (inflight.empty()) break;
+      InFlight& f = inflight.front();
+      lk.unlock();
+      std::vector<int> st(f.hs.size(), f.launch_status);
+      for (size_t q = 0; q < f.hs.size(); ++q) {
+        if (f.done[q]) cudaEventSynchronize(f.done[q]);
+        // the scene's stream is idle now: its status word is read and cleared
+        const int s2 = flip_sync(f.hs[q]);
+        if (st[q] == FLIP_OK) st[q] = s2;
+        const double t_done = now();
+        lk.lock();
+        scenes[reqs[f.tickets[q]].scene].in_flight = false;
+        complete_locked(f.tickets[q], st[q], t_done, (int)f.hs.size());
+        if (f.done[q]) event_pool.push_back(f.done[q]);
+        f.done[q] = nullptr;
+        cv_done.notify_all();
+        cv_work.notify_one();  // the scene may take part in the next batch
+        lk.unlock();
       }
-      cv_done.notify_all();
+      lk.lock();
+      slot_busy[f.slot] = false;
+      inflight.pop_front();
+      cv_work.notify_one();
     }
   }
 };
@@ -219,12 +310,23 @@ int flip_server_create(size_t budget_bytes, int32_t max_batch, flip_server** out
     flip_set_last_error_("no CUDA device");
     return FLIP_E_NOGPU;
   }
-  const int rc = flip_batch_create(max_batch, nullptr, &s->batch);
-  if (rc != FLIP_OK) {
+  if (cudaStreamCreateWithFlags(&s->solve_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
     delete s;
-    return rc;
+    flip_set_last_error_("cudaStreamCreate failed");
+    return FLIP_E_CUDA;
+  }
+  for (int k = 0; k < kSlots; ++k) {
+    const int rc = flip_batch_create(max_batch, s->solve_stream, &s->slot[k]);
+    if (rc != FLIP_OK) {
+      for (int q = 0; q < k; ++q) flip_batch_destroy(s->slot[q]);
+      cudaStreamDestroy(s->solve_stream);
+      delete s;
+      return rc;
+    }
   }
   s->worker = std::thread([s] { s->run(); });
+  s->completer = std::thread([s] { s->complete(); });
   *out = s;
   return FLIP_OK;
 }
@@ -344,9 +446,15 @@ void flip_server_destroy(flip_server* s) {
     s->cv_work.notify_one();
   }
   if (s->worker.joinable()) s->worker.join();
+  if (s->completer.joinable()) s->completer.join();
   for (auto& kv : s->scenes)
     if (kv.second.h) flip_destroy(kv.second.h);
-  flip_batch_destroy(s->batch);
+  for (int k = 0; k < kSlots; ++k) flip_batch_destroy(s->slot[k]);
+  for (cudaEvent_t e : s->event_pool) cudaEventDestroy(e);
+  if (s->solve_stream) {
+    cudaStreamSynchronize(s->solve_stream);
+    cudaStreamDestroy(s->solve_stream);
+  }
   delete s;
 }
 

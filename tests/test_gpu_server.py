@@ -88,3 +88,53 @@ def test_admission_by_footprint():
         with pytest.raises(F.FlipError) as ei:
             srv.add_scene(fbig, *big.arrays())
         assert ei.value.code == F.FLIP_E_OOM
+
+
+def test_served_scenes_match_the_oracle():
+    """Each scene's served step equals the FP64 oracle's step from the same input at
+    the parity bar (positions within 1e-4 of a cell, velocities at relative L2 1e-5),
+    in a mix of scene sizes and precisions served as several overlapping batches."""
+    import oracle as O
+    from parity_util import rel_l2
+    scenes = [_scene(32, 11), _scene(40, 12, mixed=True), _scene(24, 13), _scene(48, 14)]
+    refs = []
+    for sc, fp in scenes:
+        op = matched(sc.n[0])[0]
+        if fp.precision == F.FLIP_PREC_MIXED_IR:
+            op.cg_tol, op.cg_max_iter = 1e-11, 100000
+        refs.append(O.step(op, *sc.arrays()))
+    with F.Server(budget_bytes=8 << 30, max_batch=2) as srv:
+        ids = [srv.add_scene(fp, *sc.arrays()) for sc, fp in scenes]
+        srv.drain()
+        t0 = srv.now() + 0.02
+        tickets = [srv.submit(sid, t0 + 0.001 * k) for k, sid in enumerate(ids)]
+        infos = [srv.wait(t) for t in tickets]
+        assert all(i.status == F.FLIP_OK for i in infos)
+        for sid, (sc, fp), ref in zip(ids, scenes, refs):
+            x, y, z, u, v, w = srv.particles(sid)
+            n = sc.n[0]
+            err = np.abs(np.stack([x, y, z]).astype(np.float64)
+                         - np.stack([ref.x, ref.y, ref.z])).max() * n
+            assert err <= 1e-4, (n, err)
+            vel = np.stack([u, v, w])
+            e = rel_l2(vel, np.stack([ref.u, ref.v, ref.w]), 9.81 / 240 * np.sqrt(vel.size))
+            assert e <= 1e-5, (n, e)
+
+
+def test_next_batch_is_enqueued_while_one_runs():
+    """With one scene per batch, the second scene's batch is formed and enqueued while
+    the first is still on the GPU (its start precedes the first one's completion), and
+    every request still completes with its own scene's step."""
+    scenes = [_scene(64, 20 + k) for k in range(4)]
+    with F.Server(budget_bytes=16 << 30, max_batch=1) as srv:
+        ids = [srv.add_scene(fp, *sc.arrays()) for sc, fp in scenes]
+        srv.drain()
+        for _ in range(2):  # warm the kernels and the events
+            for t in [srv.submit(i) for i in ids]:
+                srv.wait(t)
+        t = srv.now() + 0.01
+        tickets = [srv.submit(i, t) for i in ids]
+        infos = [srv.wait(k) for k in tickets]
+        assert all(i.status == F.FLIP_OK and i.batch_size == 1 for i in infos)
+        done = sorted(infos, key=lambda i: i.t_done)
+        assert done[1].t_start < done[0].t_done, [(i.t_start, i.t_done) for i in done]
