@@ -438,9 +438,28 @@ def run_reference(args, w):
     print(json.dumps(out), flush=True)
 
 
+def batch_stage_roofline(scenes, nfl_total, stage_ms, steps, peak):
+    """The stage rooflines of a batch (SURVEY 8(d) byte model, as stage_roofline),
+    summed over its scenes, over the fused form's batch-wide stage times."""
+    np_ = sum(sc.n_particles for sc in scenes)
+    cells = sum(int(np.prod(sc.n)) for sc in scenes)
+    model = {"bin": 56 * np_ + 8 * cells, "p2g": 24 * np_ + 21 * cells,
+             "divergence": 13 * nfl_total, "g2p": 48 * np_ + 17 * cells}
+    out = {}
+    for k, b in model.items():
+        t = stage_ms[k] / steps / 1e3
+        gbs = b / t / 1e9 if t > 0 else None
+        out[k] = {"achieved_gbs": gbs, "frac": gbs / peak if gbs else None,
+                  "algorithmic_bytes": b, "ms_per_step": stage_ms[k] / steps}
+    return out
+
+
 def run_batch(args):
     """64 independent dam-break scenes, edges {32,48,64,80,96} and fluid fraction
-    0.2-0.5 by seed, stepped together (one batched solve launch per step)."""
+    0.2-0.5 by seed, stepped together: the fused form (one launch per step kernel
+    for all scenes, one batched solve launch), mixed precision unless --precision
+    fp32.  Also times, on the same scenes: the fused form replayed as CUDA graphs,
+    the per-scene-launch form, and one flip_step per scene after another."""
     import torch
     import torch.distributed as dist
 
@@ -455,6 +474,7 @@ def run_batch(args):
         __graft_entry__.build()
     from paper_2404_01931_gb300 import flip as F
     from paper_2404_01931_gb300 import scenes as S
+    mixed = (args.precision or "mixed") == "mixed"
     every = S.batch_scenes(args.batch, seed=0)
     # N GPUs: the scenes are sharded by the router, with no data-path collective
     mine = shard_scenes([sc.n_particles for sc in every], ws)[rank]
@@ -462,34 +482,55 @@ def run_batch(args):
     sims = []
     for sc in scenes:
         p = F.default_params(sc.n[0])
+        if mixed:
+            p.precision = F.FLIP_PREC_MIXED_IR
+            p.cg_tol, p.ir_tol = 1e-3, 1e-8
         sims.append(F.Simulation(p, *sc.arrays()))
     npart = sum(sc.n_particles for sc in scenes)
-    stream = torch.cuda.Stream()  # the batched solves run here; it joins every scene
+    stream = torch.cuda.Stream()  # the batch's launches run here; it joins every scene
     b = F.Batch(len(sims), stream=stream.cuda_stream)
     # warm-up, then the autotuner picks the solve-team split on real steps
     if args.warmup:
         b.step(sims, args.warmup)
     exponent = b.autotune(sims, 1) if args.autotune else 1.0
+
+    def timed(k):
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc_, _ = b.step(sims, k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        return rc_, max_over_ranks(e0.elapsed_time(e1), ws)
+
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    if ws > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    rc, _ = b.step(sims, args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    if ws > 1:
-        dist.barrier()
+    rc, ms = timed(args.steps)
     ck = clocks.stop()
-    ms = max_over_ranks(e0.elapsed_time(e1), ws)
-    # iteration counts and the solve time from one more step with statistics (untimed)
+    # stage times and iteration counts from one more step with statistics (untimed)
     rc_st, st = b.step(sims, 1, stats=True)
     rc = rc or rc_st
+    nfl = sum(x.n_fluid_cells for x in st)
+    stage_ms = {"bin": st[0].ms_bin, "p2g": st[0].ms_p2g, "divergence": st[0].ms_divergence,
+                "pcg": st[0].ms_pcg, "g2p": st[0].ms_g2p}
+    launches_per_step = st[0].kernel_launches + sum(x.kernel_launches for x in st[1:])
+    # the same scenes: graph replay of the fused step, then per-scene launches
+    b.set_graphs(True)
+    b.step(sims, 2)
+    _, ms_graph = timed(args.steps - args.steps % 2)
+    graph_on = b.graph_active()
+    b.set_graphs(False)
+    b.set_fused(False)
+    b.step(sims, 1)
+    _, ms_unfused = timed(args.steps)
+    b.set_fused(True)
     edges = sorted({sc.n[0] for sc in every})
     # the same scenes stepped one at a time through flip_step (the plain per-scene form)
     torch.cuda.synchronize()
@@ -502,10 +543,12 @@ def run_batch(args):
     rc = int(max_over_ranks(rc, ws))
     if rank != 0:
         b.close()
-        for s in sims:
-            s.close()
+        for s_ in sims:
+            s_.close()
         return
+    peak, peak_kind = read_peaks()
     npart_all = sum(sc.n_particles for sc in every)
+    ksteps_graph = args.steps - args.steps % 2
     out = {"metric": "FLIP particle-steps/s", "value": units / (ms / 1e3),
            "unit": "particle-steps/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -513,26 +556,38 @@ def run_batch(args):
            "config": {"workload": f"batch of {len(every)} dam-break scenes, edges {edges}, "
                                   "fluid fraction 0.2-0.5 by seed", "particles": npart_all,
                       "cells": sum(int(np.prod(sc.n)) for sc in every),
-                      "precision": "FP32 (float-pair dot products)", "preconditioner": "multigrid",
+                      "precision": ("mixed: FP32 CG, float-pair solution and residual to 1e-8"
+                                    if mixed else "FP32 (float-pair dot products)"),
+                      "preconditioner": "multigrid",
+                      "form": "fused: one launch per step kernel for all scenes, one batched "
+                              "cooperative solve launch",
                       "parallelism": f"scenes sharded over {ws} GPU(s) by the host-side router "
                                      "(longest first to the least-loaded rank), one batch "
                                      "per GPU, no data-path collective"},
            "team_exponent": exponent,
-           "cg_iterations_per_scene_step": sum(s.cg_iterations for s in st) / len(st),
-           "ms_pcg_per_step": st[0].ms_pcg,
-           "max_rel_residual": max(s.cg_rel_residual for s in st), "status": rc,
-           "gpu_launches": sum(s.kernel_launches for s in st) * args.steps, "clocks": ck,
+           "cg_iterations_per_scene_step": sum(x.cg_iterations for x in st) / len(st),
+           "stages_ms_per_step": stage_ms,
+           "stage_roofline": batch_stage_roofline(scenes, nfl, stage_ms, 1, peak),
+           "max_rel_residual": max(x.cg_rel_residual for x in st), "status": rc,
+           "gpu_launches": launches_per_step * args.steps, "launches_per_step": launches_per_step,
+           "clocks": ck,
+           "graph_replay": {"value": units / args.steps * ksteps_graph / (ms_graph / 1e3),
+                            "ms_per_step": ms_graph / ksteps_graph, "graph_active": graph_on},
+           "per_scene_launches": {"value": units / (ms_unfused / 1e3),
+                                  "ms_per_step": ms_unfused / args.steps,
+                                  "what": "the same batch with every scene's step kernels "
+                                          "launched on its own stream"},
            "per_scene_sequential": {"value": seq_value, "unit": "particle-steps/s",
                                     "what": "the same scenes, one flip_step call per scene "
                                             "after another (host-timed, synchronised)"}}
     print(json.dumps(out), flush=True)
     b.close()
-    for s in sims:
-        s.close()
+    for s_ in sims:
+        s_.close()
 
 
 def serve_workload(srv_scenes, max_edge, rate, requests, budget_gb, max_batch, ws=1, rank=0,
-                   seed=0):
+                   seed=0, overlap=True):
     """Step requests arriving as a Poisson process (mean `rate` per second, uniform
     scene choice) over `srv_scenes` resident dam-break scenes with edges log-uniform
     in [48, max_edge] and fluid fraction 0.2-0.5 (mixed precision), served by the
@@ -551,6 +606,7 @@ def serve_workload(srv_scenes, max_edge, rate, requests, budget_gb, max_batch, w
     mine = set(shard_scenes([n ** 3 * f for n, f in specs], ws)[rank])
     t_gen = time.perf_counter()
     srv = F.Server(int(budget_gb * (1 << 30)), max_batch)
+    srv.set_overlap(overlap)
     sid, npart = {}, [0] * len(specs)
     for k, (n, f) in enumerate(specs):
         if k not in mine:
@@ -918,6 +974,10 @@ def main():
         sim.close()
         part = serve_workload(40, 96, 2000.0, 2000, 180.0, 64)
         out["served"] = serve_summary([part], 40, 96, 2000.0, 2000, 180.0, 64)
+        part = serve_workload(40, 96, 2000.0, 2000, 180.0, 64, overlap=False)
+        one = serve_summary([part], 40, 96, 2000.0, 2000, 180.0, 64)
+        out["served"]["one_batch_at_a_time"] = {k: one[k] for k in ("value", "latency_ms",
+                                                                  "mean_batch", "failed")}
     if rank == 0:
         print(json.dumps(out), flush=True)
     sim.close()

@@ -309,13 +309,19 @@ const char* flip_strerror(int status);
 const char* flip_last_error(void);
 
 /* ---------------------------------------------------------------- batches
- * Many independent scenes advanced together.  Per step: every scene's binning,
- * P2G and right-hand side run on the scene's own stream (concurrently across
- * scenes); then the pressure solves of all scenes run in one cooperative
- * launch per (precision, preconditioner) group, each scene on its own team of
- * CTAs sized by its particle count, with per-scene barriers, reductions and
- * convergence; then every scene's G2P runs on its own stream.  A scene's
- * results are those of flip_step up to the order of floating-point sums. */
+ * Many independent scenes advanced together.  Per step, in the fused form (the
+ * default when no scene of the call uses an adaptive time step or reseeding):
+ * each step kernel runs once for all scenes -- the two binning scans, the
+ * scatter, P2G, its normalisation and the right-hand side, each one launch over a
+ * table of the scenes in which every scene owns a range of CTAs -- then the
+ * pressure solves of all scenes run in one cooperative launch per (precision,
+ * preconditioner) group, each scene on its own team of CTAs sized by its particle
+ * count, with per-scene barriers, reductions and convergence, then G2P runs once
+ * per precision group.  About 9 launches per step whatever the number of scenes,
+ * all on the batch's stream.  Otherwise (or with flip_batch_set_fused(b, 0)) every
+ * scene's binning, P2G and right-hand side run on the scene's own stream, the
+ * solves as above, then every scene's G2P on its own stream.  A scene's results
+ * are those of flip_step up to the order of floating-point sums. */
 typedef struct flip_batch flip_batch;
 
 /* A batch runner for up to capacity scenes (capacity <= 4096).  It owns small
@@ -328,8 +334,9 @@ int flip_batch_create(int32_t capacity, void* stream, flip_batch** out);
  * device) by nsteps steps each.  Stream-ordered with respect to each scene's
  * stream.  stats (nullable) receives n entries, as flip_step's per scene, with
  * ms_total the wall time of the whole call and ms_pcg the time of the batched
- * solves; when stats is given the call waits and returns the first device-side
- * condition of any scene. */
+ * solves (in the fused form ms_bin, ms_p2g, ms_divergence and ms_g2p are the
+ * batch-wide stage times, every scene's stage being one launch); when stats is
+ * given the call waits and returns the first device-side condition of any scene. */
 int flip_batch_step(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t nsteps,
                     flip_stats* stats);
 
@@ -340,6 +347,10 @@ int flip_batch_step(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t ns
  * Default 0: on GB300 the replays measured slower than stream-ordered launches
  * (64 dam breaks: 12.2 against 11.5 ms per step). */
 int flip_batch_set_graphs(flip_batch* b, int32_t enable);
+
+/* enable = 1 (default): the fused form above where every scene allows it;
+ * 0: per-scene launches on the scenes' streams. */
+int flip_batch_set_fused(flip_batch* b, int32_t enable);
 
 /* 1 when a captured graph is cached (the last graph-eligible call used it). */
 int flip_batch_graph_active(const flip_batch* b);

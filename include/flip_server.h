@@ -68,6 +68,11 @@ int flip_server_wait(flip_server* s, int64_t ticket, flip_request_info* info);
 /* Blocks until every submitted request is done. */
 int flip_server_drain(flip_server* s);
 
+/* enable = 1 (the default): the next batch is formed and enqueued as soon as the
+ * previous batch's solve has finished, overlapping that batch's G2P.  enable = 0:
+ * one batch at a time; the next is formed when the previous one has completed. */
+int flip_server_set_overlap(flip_server* s, int32_t enable);
+
 /* Seconds since the server was created. */
 double flip_server_now(const flip_server* s);
 

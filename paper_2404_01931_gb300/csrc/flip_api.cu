@@ -1092,6 +1092,10 @@ struct flip_batch {
   int graph_batch_launches = 0;
   bool graph_off = false;           // capture failed once: use the plain path
   bool graphs = false;              // graph replay requested (flip_batch_set_graphs)
+  // one launch per step kernel across all scenes (flip_batch_set_fused)
+  bool fused = true;
+  SceneDev* d_scenes = nullptr;     // [2 * capacity]: the scene table for either buffer parity
+  unsigned int* d_first = nullptr;  // [kFusedLaunches * (capacity + 1)] CTA ranges
 };
 
 namespace {
@@ -1185,6 +1189,51 @@ int batch_graph_steps(flip_batch* b, flip_handle* const* hs, int n, int pairs,
   return 2 * pairs;
 }
 
+// The batched (fused) step kernels: CTA ranges of each launch, in this order.
+enum FusedLaunch { FL_SCAN = 0, FL_ONE, FL_SCATTER, FL_P2G, FL_FINALIZE, FL_DIV, FL_G2P,
+                   FL_G2P_MIXED, kFusedLaunches };
+
+// Scenes a fused step can take: fixed time step, no reseeding.
+bool fusable(const flip_handle* h) { return h->prm.cfl <= 0.0 && !reseeding(h); }
+
+// The table entry of a scene for a step that starts with particle buffer `cur`.
+SceneDev scene_dev(const flip_handle* h, int cur) {
+  SceneDev d{};
+  d.g = h->g;
+  d.K = h->K;
+  d.src = h->P[cur];
+  d.dst = h->P[1 - cur];
+  d.B = h->B;
+  d.type = h->type;
+  for (int a = 0; a < 3; ++a) {
+    d.acc[a] = h->acc[a];
+    d.uo[a] = h->uo[a];
+  }
+  d.b32 = h->b32;
+  d.b64 = h->b64;
+  d.x32 = h->mixed ? nullptr : h->x32;
+  d.x64 = h->x64;
+  d.pff = h->pff;
+  d.bar = h->bar;
+  d.st = h->dstats;
+  d.np = h->np;
+  d.nbricks = h->nbricks;
+  return d;
+}
+
+// first[] of a launch that splits `total` CTAs over the scenes in proportion to
+// their particles (at least one each).
+void share_ctas(const std::vector<flip_handle*>& hv, int total, unsigned int* first) {
+  long long tot = 0;
+  for (auto* h : hv) tot += std::max<long long>(h->np, 1);
+  first[0] = 0;
+  for (size_t q = 0; q < hv.size(); ++q) {
+    const long long want = (long long)std::llround((double)total * std::max<long long>(hv[q]->np, 1) /
+                                                   (double)std::max<long long>(tot, 1));
+    first[q + 1] = first[q] + (unsigned int)std::max<long long>(want, 1);
+  }
+}
+
 // Splits max_blocks CTAs over scenes in proportion to their particle counts
 // raised to `exponent`, at least one each (n <= max_blocks).  first has n+1
 // entries.
@@ -1243,7 +1292,10 @@ int flip_batch_create(int32_t capacity, void* stream, flip_batch** out) {
   }
   if ((e = cudaMalloc(&b->d_args, sizeof(PcgArgs) * (size_t)capacity)) != cudaSuccess ||
       (e = cudaMalloc(&b->d_block_scene, sizeof(int) * (size_t)b->max_blocks)) != cudaSuccess ||
-      (e = cudaMalloc(&b->d_team_first, sizeof(int) * (size_t)(capacity + 1))) != cudaSuccess)
+      (e = cudaMalloc(&b->d_team_first, sizeof(int) * (size_t)(capacity + 1))) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_scenes, sizeof(SceneDev) * 2 * (size_t)capacity)) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_first, sizeof(unsigned int) * kFusedLaunches *
+                                       (size_t)(capacity + 1))) != cudaSuccess)
     return bail(e, "cudaMalloc(batch)");
   b->ev.resize(capacity, nullptr);
   for (auto& ev : b->ev)
@@ -1262,6 +1314,12 @@ int flip_batch_graph_active(const flip_batch* b) { return (b && b->graph) ? 1 : 
 int flip_batch_set_graphs(flip_batch* b, int32_t enable) {
   if (!b) return fail(FLIP_E_ARG, "batch is NULL");
   b->graphs = enable != 0;
+  return FLIP_OK;
+}
+
+int flip_batch_set_fused(flip_batch* b, int32_t enable) {
+  if (!b) return fail(FLIP_E_ARG, "batch is NULL");
+  b->fused = enable != 0;
   return FLIP_OK;
 }
 
@@ -1316,6 +1374,8 @@ void flip_batch_destroy(flip_batch* b) {
   if (b->d_args) cudaFree(b->d_args);
   if (b->d_block_scene) cudaFree(b->d_block_scene);
   if (b->d_team_first) cudaFree(b->d_team_first);
+  if (b->d_scenes) cudaFree(b->d_scenes);
+  if (b->d_first) cudaFree(b->d_first);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
 }
@@ -1415,8 +1475,9 @@ int batch_step_impl(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t ns
   for (int s = 0; s < n; ++s) launches0[s] = hs[s]->launches;
   int batch_launches = 0;
   if (timed) {
-    // two events per step around the batched solves, read once after the call
-    while (b->pev.size() < 2 * (size_t)nsteps) {
+    // events per step around the batched solves (fused form: around every stage),
+    // read once after the call
+    while (b->pev.size() < 6 * (size_t)nsteps) {
       cudaEvent_t e = nullptr;
       FLIP_CUDA(cudaEventCreate(&e));
       b->pev.push_back(e);
@@ -1429,13 +1490,114 @@ int batch_step_impl(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t ns
                                 2 * sizeof(long long), cudaMemcpyDeviceToDevice, bs));
     }
   }
+  // Fused form: every step kernel of every scene in one launch on the batch
+  // stream, over a table of the scenes (single-precision scenes first, then the
+  // mixed ones, so G2P runs as one launch per precision).
+  bool fused = b->fused;
+  for (int s = 0; s < n; ++s) fused = fused && fusable(hs[s]);
+  std::vector<flip_handle*> order;
+  std::vector<unsigned int> first;
+  int n32 = 0;
+  std::vector<int> cur0(n);
+  for (int s = 0; s < n; ++s) cur0[s] = hs[s]->cur;
+  if (fused) {
+    // the batch stream starts after each scene stream's earlier work
+    for (int s = 0; s < n; ++s) {
+      FLIP_CUDA(cudaEventRecord(b->ev[s], hs[s]->stream));
+      FLIP_CUDA(cudaStreamWaitEvent(bs, b->ev[s], 0));
+    }
+    for (int s = 0; s < n; ++s)
+      if (!hs[s]->mixed) order.push_back(hs[s]);
+    n32 = (int)order.size();
+    for (int s = 0; s < n; ++s)
+      if (hs[s]->mixed) order.push_back(hs[s]);
+    std::vector<SceneDev> tab(2 * (size_t)n);
+    for (int q = 0; q < n; ++q) {
+      tab[q] = scene_dev(order[q], order[q]->cur);
+      tab[n + q] = scene_dev(order[q], 1 - order[q]->cur);
+    }
+    const size_t W = (size_t)n + 1;
+    first.assign(kFusedLaunches * W, 0u);
+    for (int q = 0; q < n; ++q) {
+      const flip_handle* h = order[q];
+      const long long faces = h->nf[0] + h->nf[1] + h->nf[2];
+      const unsigned int cnt[5] = {(h->nbricks + 7u) / 8u, 1u,
+                                   (unsigned int)((h->np + 511) / 512),
+                                   (unsigned int)((faces + 1023) / 1024),
+                                   (unsigned int)h->g.ny * (unsigned int)h->g.nz};
+      const int which[5] = {FL_SCAN, FL_ONE, FL_SCATTER, FL_FINALIZE, FL_DIV};
+      for (int k = 0; k < 5; ++k) first[which[k] * W + q + 1] = first[which[k] * W + q] + cnt[k];
+    }
+    share_ctas(order, order[0]->p2g_blocks, &first[FL_P2G * W]);
+    // G2P: one launch per precision group, each splitting the CTAs by particles
+    std::vector<flip_handle*> g32(order.begin(), order.begin() + n32),
+        gmx(order.begin() + n32, order.end());
+    if (!g32.empty()) share_ctas(g32, order[0]->g2p_blocks, &first[FL_G2P * W]);
+    if (!gmx.empty()) share_ctas(gmx, order[0]->g2p_blocks, &first[FL_G2P_MIXED * W]);
+    FLIP_CUDA(cudaMemcpyAsync(b->d_scenes, tab.data(), sizeof(SceneDev) * tab.size(),
+                              cudaMemcpyHostToDevice, bs));
+    FLIP_CUDA(cudaMemcpyAsync(b->d_first, first.data(), sizeof(unsigned int) * first.size(),
+                              cudaMemcpyHostToDevice, bs));
+  }
   // every scene stream starts after the call's uploads (and the begin event)
   FLIP_CUDA(cudaEventRecord(b->ev_solved, bs));
   for (int s = 0; s < n; ++s) FLIP_CUDA(cudaStreamWaitEvent(hs[s]->stream, b->ev_solved, 0));
   float ms_pcg = 0.0f;
+  float ms_stage[5] = {0, 0, 0, 0, 0};  // fused form: bin, P2G, divergence, solve, G2P
   int timed_steps = 0;
+  // One step of every scene in the fused form, all on the batch stream.
+  auto enqueue_fused = [&]() -> int {
+    const size_t W = (size_t)n + 1;
+    const int par = (hs[0]->cur == cur0[0]) ? 0 : 1;  // every scene flips its buffers per step
+    const SceneDev* tab = b->d_scenes + (size_t)par * n;
+    auto L = [&](int k, int off, int cnt) {
+      return BatchLaunch{tab + off, b->d_first + k * W + off, cnt};
+    };
+    auto total = [&](int k, int off, int cnt) { return first[k * W + off + cnt] - first[k * W + off]; };
+    cudaEvent_t* E = timed ? b->pev.data() + 6 * (size_t)timed_steps : nullptr;
+    if (timed) FLIP_CUDA(cudaEventRecord(E[0], bs));
+    launch_bin_batch(L(FL_SCAN, 0, n), total(FL_SCAN, 0, n), L(FL_ONE, 0, n), bs);
+    launch_scatter_batch(L(FL_SCATTER, 0, n), total(FL_SCATTER, 0, n), bs);
+    for (auto* h : order) h->cur = 1 - h->cur;
+    if (timed) FLIP_CUDA(cudaEventRecord(E[1], bs));
+    launch_p2g_batch(L(FL_P2G, 0, n), total(FL_P2G, 0, n), bs);
+    launch_finalize_batch(L(FL_FINALIZE, 0, n), total(FL_FINALIZE, 0, n), bs);
+    if (timed) FLIP_CUDA(cudaEventRecord(E[2], bs));
+    launch_divergence_batch(L(FL_DIV, 0, n), total(FL_DIV, 0, n), bs);
+    batch_launches += 6;
+    if (timed) FLIP_CUDA(cudaEventRecord(E[3], bs));
+    for (size_t q = 0; q < launches.size(); ++q) {
+      const Launch& Lq = launches[q];
+      PcgBatch pb{b->d_args + Lq.arg0, d_bs[q], d_tf[q], (int)Lq.scenes.size()};
+      const int nblk = first_all[tf_off[q] + (int)Lq.scenes.size()];
+      if (Lq.mg) FLIP_CUDA(launch_pcg_mg_batch(pb, Lq.mixed, nblk, bs));
+      else FLIP_CUDA(launch_pcg_batch(pb, Lq.mixed, nblk, bs));
+      ++batch_launches;
+    }
+    if (timed) FLIP_CUDA(cudaEventRecord(E[4], bs));
+    // G2P reads its scenes from the table offset by the group's first scene
+    if (n32 > 0) {
+      launch_g2p_batch(BatchLaunch{tab, b->d_first + FL_G2P * W, n32}, total(FL_G2P, 0, n32), false,
+                       bs);
+      ++batch_launches;
+    }
+    if (n32 < n) {
+      launch_g2p_batch(BatchLaunch{tab + n32, b->d_first + FL_G2P_MIXED * W, n - n32},
+                       total(FL_G2P_MIXED, 0, n - n32), true, bs);
+      ++batch_launches;
+    }
+    if (timed) FLIP_CUDA(cudaEventRecord(E[5], bs));
+    for (auto* h : order) {
+      ++h->steps_done;
+      h->stepped = true;
+    }
+    FLIP_CUDA(cudaGetLastError());
+    if (timed) ++timed_steps;
+    return FLIP_OK;
+  };
   // One step of every scene, enqueued on the scene streams and the batch stream.
   auto enqueue_step = [&]() -> int {
+    if (fused) return enqueue_fused();
     for (int s = 0; s < n; ++s) {
       flip_handle* h = hs[s];
       const float* uo[3] = {h->uo[0], h->uo[1], h->uo[2]};
@@ -1486,8 +1648,13 @@ int batch_step_impl(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t ns
   for (int st = done; st < nsteps; ++st)
     if (int rc = enqueue_step()) return rc;
   for (void* p : tmp_alloc) FLIP_CUDA(cudaFreeAsync(p, bs));
+  // fused: the scene streams continue after the batch stream's work
+  if (fused) {
+    FLIP_CUDA(cudaEventRecord(b->ev_solved, bs));
+    for (int s = 0; s < n; ++s) FLIP_CUDA(cudaStreamWaitEvent(hs[s]->stream, b->ev_solved, 0));
+  }
   // the batch stream joins every scene stream at the end of the call
-  if (join)
+  if (join && !fused)
     for (int s = 0; s < n; ++s) {
       FLIP_CUDA(cudaEventRecord(b->ev[s], hs[s]->stream));
       FLIP_CUDA(cudaStreamWaitEvent(bs, b->ev[s], 0));
@@ -1498,10 +1665,20 @@ int batch_step_impl(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t ns
   float ms_total = 0.0f;
   FLIP_CUDA(cudaEventElapsedTime(&ms_total, b->ev_begin, b->ev_end));
   for (int st = 0; st < timed_steps; ++st) {
-    float t = 0.0f;
-    FLIP_CUDA(cudaEventElapsedTime(&t, b->pev[2 * (size_t)st], b->pev[2 * (size_t)st + 1]));
-    ms_pcg += t;
+    if (fused) {
+      const cudaEvent_t* E = b->pev.data() + 6 * (size_t)st;
+      for (int q = 0; q < 5; ++q) {
+        float t = 0.0f;
+        FLIP_CUDA(cudaEventElapsedTime(&t, E[q], E[q + 1]));
+        ms_stage[q] += t;
+      }
+    } else {
+      float t = 0.0f;
+      FLIP_CUDA(cudaEventElapsedTime(&t, b->pev[2 * (size_t)st], b->pev[2 * (size_t)st + 1]));
+      ms_pcg += t;
+    }
   }
+  if (fused) ms_pcg = ms_stage[3];
   int first_rc = FLIP_OK;
   for (int s = 0; s < n; ++s) {
     flip_handle* h = hs[s];
@@ -1536,6 +1713,12 @@ int batch_step_impl(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t ns
     o->dt_last = h->prm.cfl > 0.0 ? d.dt_cur : h->prm.dt;
     o->ms_pcg = ms_pcg;
     o->ms_total = ms_total;
+    if (fused) {  // the batch-wide stage times (every scene's stages run in one launch)
+      o->ms_bin = ms_stage[0];
+      o->ms_p2g = ms_stage[1];
+      o->ms_divergence = ms_stage[2];
+      o->ms_g2p = ms_stage[4];
+    }
   }
   return first_rc;
 }

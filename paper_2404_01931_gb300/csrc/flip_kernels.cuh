@@ -53,6 +53,46 @@ __device__ __forceinline__ StepConsts step_consts(const StepConsts& K) {
   return k;
 }
 
+// One scene of a batched launch (several scenes' step kernels in one launch): what
+// the step kernels read, for one step (src is the particle buffer the binning
+// scatters from, dst the one it scatters into, which P2G and G2P then use).
+struct SceneDev {
+  Grid g;
+  StepConsts K;
+  PartView src, dst;
+  BinView B;
+  uint8_t* type;
+  float2* acc[3];
+  float* uo[3];
+  float* b32;
+  double* b64;
+  float* x32;
+  double* x64;
+  float2* pff;
+  unsigned int* bar;
+  DevStats* st;
+  long long np;
+  unsigned int nbricks;
+};
+
+// CTAs of a batched launch: scene s (of n) owns CTAs first[s] .. first[s+1]-1.
+struct BatchLaunch {
+  const SceneDev* scenes;
+  const unsigned int* first;
+  int n;
+};
+
+// The scene a CTA of a batched launch works on (binary search of first).
+__device__ __forceinline__ int batch_scene(const BatchLaunch& L, unsigned int cta) {
+  int lo = 0, hi = L.n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (L.first[mid] <= cta) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 constexpr int PCG_SLOTS = 7;
 constexpr int PRECOND_RBGS = 2;   // FLIP_PRECOND_RBGS: red-black Gauss-Seidel as the solver
 
@@ -206,6 +246,19 @@ void launch_scatter(const PartView& src, const PartView& dst, const BinView& b, 
                     cudaStream_t s, const long long* np_dev = nullptr,
                     unsigned int rank_max = ~0u);
 void launch_iota(int* id, long long np, cudaStream_t s);
+
+// Batched forms: every scene of the table in one launch per kernel (no
+// reseeding, fixed time step).  first[] per launch as above; `ctas` its total.
+// Per-scene CTA counts: cell_local_scan ceil(nbricks / 8); brick_scan one; scatter
+// ceil(np / 512); finalize ceil(faces / 1024); divergence ny * nz; P2G and G2P
+// any (each scene's CTAs stride over its active bricks).
+void launch_bin_batch(const BatchLaunch& L_scan, unsigned int ctas_scan, const BatchLaunch& L_one,
+                      cudaStream_t s);
+void launch_scatter_batch(const BatchLaunch& L, unsigned int ctas, cudaStream_t s);
+void launch_p2g_batch(const BatchLaunch& L, unsigned int ctas, cudaStream_t s);
+void launch_finalize_batch(const BatchLaunch& L, unsigned int ctas, cudaStream_t s);
+void launch_divergence_batch(const BatchLaunch& L, unsigned int ctas, cudaStream_t s);
+void launch_g2p_batch(const BatchLaunch& L, unsigned int ctas, bool pair, cudaStream_t s);
 
 // k_p2g.cu
 void launch_p2g(const Grid& g, const PartView& p, const BinView& b, float2* const acc[3],

@@ -2,11 +2,13 @@
 // (include/flip_server.h).  Host code only.  A launcher thread admits scenes by
 // footprint, forms batches from the requests that have arrived and enqueues them;
 // a completer thread waits for each scene's step on the device and completes its
-// request.  Two batch slots are in flight at once: while the GPU runs one batch,
-// the next is formed and enqueued behind it, so the device does not idle across
-// the host's round trip, and the next batch's binning and P2G overlap the
-// previous batch's G2P on the device.  The two slots share one stream for their
-// pressure solves, so the cooperative solve launches never run concurrently.
+// request.  Two batch slots are in flight at once: as soon as one batch's pressure
+// solve has finished on the device, the next batch is formed from the requests
+// that arrived meanwhile and enqueued, so its binning and P2G overlap the previous
+// batch's G2P and the device does not idle across the host's round trip.  Waiting
+// for the solve (rather than enqueueing at once) keeps batches large when the
+// device is busy.  The two slots share one stream for their pressure solves, so
+// the cooperative solve launches never run concurrently.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -91,6 +93,8 @@ struct flip_server {
   std::vector<cudaEvent_t> event_pool;  // per-scene completion events, reused
   std::deque<InFlight> inflight;
   std::condition_variable cv_inflight;
+  cudaEvent_t last_solve = nullptr;  // end of the newest batch's solve, until seen
+  bool overlap = true;               // flip_server_set_overlap
   std::thread worker, completer;
 
   double now() const {
@@ -194,6 +198,21 @@ struct flip_server {
           ++q;
         }
       }
+      // the next batch is formed once the newest batch's solve is done (its G2P
+      // may still run): requests that arrive during the solve join it
+      if (!overlap && !inflight.empty()) {  // one batch at a time: wait for its end
+        cv_work.wait(lk);
+        continue;
+      }
+      if (last_solve) {
+        cudaEvent_t e = last_solve;
+        lk.unlock();
+        cudaEventSynchronize(e);
+        lk.lock();
+        event_pool.push_back(e);
+        last_solve = nullptr;
+        continue;
+      }
       const int k = free_slot_locked();
       const double t = now();
       std::vector<int64_t> pick;
@@ -241,6 +260,7 @@ struct flip_server {
         f.done.push_back(take_event_locked());
       }
       slot_busy[k] = true;
+      cudaEvent_t solved = take_event_locked();
       lk.unlock();
       f.launch_status = flipk::batch_step_overlapped(slot[k], hs.data(), (int)hs.size());
       for (size_t q = 0; q < hs.size(); ++q)
@@ -248,7 +268,14 @@ struct flip_server {
           cudaGetLastError();
           if (f.launch_status == FLIP_OK) f.launch_status = FLIP_E_CUDA;
         }
+      // the solve stream's last work of the call is the batched solve
+      if (solved && cudaEventRecord(solved, solve_stream) != cudaSuccess) {
+        cudaGetLastError();
+        cudaEventDestroy(solved);
+        solved = nullptr;
+      }
       lk.lock();
+      last_solve = solved;
       inflight.push_back(std::move(f));
       cv_inflight.notify_one();
     }
@@ -410,6 +437,14 @@ int flip_server_drain(flip_server* s) {
 }
 
 double flip_server_now(const flip_server* s) { return s ? s->now() : 0.0; }
+
+int flip_server_set_overlap(flip_server* s, int32_t enable) {
+  if (!s) return FLIP_E_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->overlap = enable != 0;
+  s->cv_work.notify_one();
+  return FLIP_OK;
+}
 
 int flip_server_usage(flip_server* s, int32_t* resident, size_t* bytes) {
   if (!s) return FLIP_E_ARG;

@@ -45,13 +45,13 @@ constexpr int SCAN_THREADS = 256;
 
 // cmax: particles a cell keeps (reseeding's upper bound; ~0u when off); the
 // excess is counted into st->removed_total and dropped by the scatter.
-__global__ void __launch_bounds__(SCAN_THREADS) k_cell_local_scan(const Grid g, const BinView b,
-                                                                    uint8_t* __restrict__ type,
-                                                                    unsigned int nb,
-                                                                    unsigned int cmax,
-                                                                    DevStats* st) {
+// Body of one CTA (block `blk` of the scene's launch).
+__device__ __forceinline__ void cell_local_scan(const Grid& g, const BinView& b,
+                                                uint8_t* __restrict__ type, unsigned int nb,
+                                                unsigned int cmax, DevStats* st,
+                                                unsigned int blk) {
   const int lane = threadIdx.x & 31;
-  const unsigned int brick = blockIdx.x * (SCAN_THREADS / 32) + (threadIdx.x >> 5);
+  const unsigned int brick = blk * (SCAN_THREADS / 32) + (threadIdx.x >> 5);
   if (brick >= nb) return;
   const unsigned int key0 = brick * BRICK_CELLS + 16u * (unsigned)lane;
   uint4* cnt4 = reinterpret_cast<uint4*>(b.cell_count + key0);
@@ -133,12 +133,26 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_cell_local_scan(const Grid g, 
   if (lane == 0) b.brick_fluid[brick] = (unsigned)nfl;
 }
 
+__global__ void __launch_bounds__(SCAN_THREADS) k_cell_local_scan(const Grid g, const BinView b,
+                                                                    uint8_t* __restrict__ type,
+                                                                    unsigned int nb,
+                                                                    unsigned int cmax,
+                                                                    DevStats* st) {
+  cell_local_scan(g, b, type, nb, cmax, st, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_cell_local_scan_batch(const BatchLaunch L) {
+  const int s = batch_scene(L, blockIdx.x);
+  const SceneDev& S = L.scenes[s];
+  cell_local_scan(S.g, S.B, S.type, S.nbricks, ~0u, S.st, blockIdx.x - L.first[s]);
+}
+
 // One CTA of 1024 threads walks all bricks in chunks of 8 per thread: exclusive
 // scan of the brick totals (particle offsets), compaction of the bricks holding
 // particles.  A thread scans its 8 consecutive bricks serially, the CTA scans the
 // thread totals.
 constexpr int BSCAN_PER = 8;
-__global__ void __launch_bounds__(1024) k_brick_scan(const Grid g, const BinView b, DevStats* st) {
+__device__ __forceinline__ void brick_scan(const Grid& g, const BinView& b, DevStats* st) {
   __shared__ unsigned int wc[32], wf[32];
   __shared__ unsigned int fl_tot;
   const unsigned int nb = (unsigned)g.bx * g.by * g.bz;
@@ -196,15 +210,27 @@ __global__ void __launch_bounds__(1024) k_brick_scan(const Grid g, const BinView
   }
 }
 
+__global__ void __launch_bounds__(1024) k_brick_scan(const Grid g, const BinView b, DevStats* st) {
+  brick_scan(g, b, st);
+}
+
+// CTA s scans scene s.
+__global__ void __launch_bounds__(1024) k_brick_scan_batch(const BatchLaunch L) {
+  const SceneDev& S = L.scenes[blockIdx.x];
+  brick_scan(S.g, S.B, S.st);
+}
+
 // Two particles per thread (i and i + stride), so each thread has two
 // dependent gather chains (key -> offsets -> 7 moves) in flight.
 // np_dev (nullable): the source count in device memory, bounding np; particles
 // of rank >= rank_max in their cell are dropped (reseeding's upper bound).
-__global__ void k_scatter(const PartView src, const PartView dst, const BinView b, long long np,
-                          const long long* np_dev, unsigned int rank_max) {
+__device__ __forceinline__ void scatter(const PartView& src, const PartView& dst, const BinView& b,
+                                        long long np, const long long* np_dev,
+                                        unsigned int rank_max, unsigned int blk,
+                                        unsigned int nblk) {
   if (np_dev) np = min(np, *np_dev);
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  const long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long stride = (long long)nblk * blockDim.x;
+  const long long i0 = blk * (long long)blockDim.x + threadIdx.x;
   unsigned int d[2];
   bool ok[2];
 #pragma unroll
@@ -231,6 +257,18 @@ __global__ void k_scatter(const PartView src, const PartView dst, const BinView 
     dst.w[d[u]] = vw;
     dst.id[d[u]] = id;
   }
+}
+
+__global__ void k_scatter(const PartView src, const PartView dst, const BinView b, long long np,
+                          const long long* np_dev, unsigned int rank_max) {
+  scatter(src, dst, b, np, np_dev, rank_max, blockIdx.x, gridDim.x);
+}
+
+__global__ void k_scatter_batch(const BatchLaunch L) {
+  const int s = batch_scene(L, blockIdx.x);
+  const SceneDev& S = L.scenes[s];
+  scatter(S.src, S.dst, S.B, S.np, nullptr, ~0u, blockIdx.x - L.first[s],
+          L.first[s + 1] - L.first[s]);
 }
 
 __global__ void k_iota(int* id, long long np) {
@@ -261,6 +299,16 @@ void launch_scatter(const PartView& src, const PartView& dst, const BinView& b, 
                     cudaStream_t s, const long long* np_dev, unsigned int rank_max) {
   if (np > 0)
     k_scatter<<<blocks_for((np + 1) / 2, 256), 256, 0, s>>>(src, dst, b, np, np_dev, rank_max);
+}
+
+void launch_bin_batch(const BatchLaunch& L_scan, unsigned int ctas_scan, const BatchLaunch& L_one,
+                      cudaStream_t s) {
+  if (ctas_scan) k_cell_local_scan_batch<<<ctas_scan, SCAN_THREADS, 0, s>>>(L_scan);
+  if (L_one.n > 0) k_brick_scan_batch<<<(unsigned)L_one.n, 1024, 0, s>>>(L_one);
+}
+
+void launch_scatter_batch(const BatchLaunch& L, unsigned int ctas, cudaStream_t s) {
+  if (ctas) k_scatter_batch<<<ctas, 256, 0, s>>>(L);
 }
 
 void launch_iota(int* id, long long np, cudaStream_t s) {

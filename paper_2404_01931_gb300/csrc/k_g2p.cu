@@ -191,14 +191,11 @@ __device__ __forceinline__ void interp_tile(const PartW& W, int li, int lj, int 
 }
 
 template <bool PAIR>
-__global__ void __launch_bounds__(G2P_THREADS, 5) k_g2p(const Grid g, const StepConsts K0,
-                                                     const PartView P, const BinView B,
-                                                     const float* __restrict__ uo0,
-                                                     const float* __restrict__ uo1,
-                                                     const float* __restrict__ uo2,
-                                                     const float* __restrict__ p32,
-                                                     const float2* __restrict__ pff,
-                                                     DevStats* st) {
+__device__ __forceinline__ void g2p(const Grid& g, const StepConsts& K0, const PartView& P,
+                                    const BinView& B, const float* __restrict__ uo0,
+                                    const float* __restrict__ uo1, const float* __restrict__ uo2,
+                                    const float* __restrict__ p32, const float2* __restrict__ pff,
+                                    DevStats* st, unsigned int blk, unsigned int nblk) {
   const StepConsts K = step_consts(K0);
   using PT = typename PTile<PAIR>::T;
   __shared__ PT sp[G2P_PTILE];
@@ -219,7 +216,7 @@ __global__ void __launch_bounds__(G2P_THREADS, 5) k_g2p(const Grid g, const Step
   unsigned int phase[2] = {0u, 0u};
   unsigned int kbuf = 0;                 // buffer of the next chunk
   bool inflight[2] = {false, false};     // thread 0: a copy into the buffer is unwaited
-  for (unsigned int bi = blockIdx.x; bi < nact; bi += gridDim.x) {
+  for (unsigned int bi = blk; bi < nact; bi += nblk) {
     const unsigned int brick = B.active[bi];
     const int b0 = (int)(brick % (unsigned)g.bx) * BRICK;
     const int b1 = (int)((brick / (unsigned)g.bx) % (unsigned)g.by) * BRICK;
@@ -343,6 +340,26 @@ __global__ void __launch_bounds__(G2P_THREADS, 5) k_g2p(const Grid g, const Step
   if (lane == 0 && speed2 > 0.0f) atomicMax(&st->max_speed_bits, __float_as_uint(sqrtf(speed2)));
 }
 
+template <bool PAIR>
+__global__ void __launch_bounds__(G2P_THREADS, 5) k_g2p(const Grid g, const StepConsts K0,
+                                                     const PartView P, const BinView B,
+                                                     const float* __restrict__ uo0,
+                                                     const float* __restrict__ uo1,
+                                                     const float* __restrict__ uo2,
+                                                     const float* __restrict__ p32,
+                                                     const float2* __restrict__ pff,
+                                                     DevStats* st) {
+  g2p<PAIR>(g, K0, P, B, uo0, uo1, uo2, p32, pff, st, blockIdx.x, gridDim.x);
+}
+
+template <bool PAIR>
+__global__ void __launch_bounds__(G2P_THREADS, 5) k_g2p_batch(const BatchLaunch L) {
+  const int s = batch_scene(L, blockIdx.x);
+  const SceneDev& S = L.scenes[s];
+  g2p<PAIR>(S.g, S.K, S.dst, S.B, S.uo[0], S.uo[1], S.uo[2], S.x32, S.pff, S.st,
+            blockIdx.x - L.first[s], L.first[s + 1] - L.first[s]);
+}
+
 int g2p_blocks(int sm_count) {
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_g2p<true>, G2P_THREADS, 0) !=
@@ -352,6 +369,12 @@ int g2p_blocks(int sm_count) {
     per_sm = 1;
   }
   return sm_count * per_sm;
+}
+
+void launch_g2p_batch(const BatchLaunch& L, unsigned int ctas, bool pair, cudaStream_t s) {
+  if (!ctas) return;
+  if (pair) k_g2p_batch<true><<<ctas, G2P_THREADS, 0, s>>>(L);
+  else k_g2p_batch<false><<<ctas, G2P_THREADS, 0, s>>>(L);
 }
 
 void launch_g2p(const Grid& g, const StepConsts& k, const PartView& p, const BinView& b,

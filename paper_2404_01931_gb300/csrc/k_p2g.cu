@@ -113,13 +113,13 @@ __device__ __forceinline__ void flush_tile(const Grid& g, int b0, int b1, int b2
   }
 }
 
-__global__ void __launch_bounds__(P2G_THREADS, 4) k_p2g(const Grid g, const PartView P,
-                                                     const BinView B, float2* acc0, float2* acc1,
-                                                     float2* acc2, const DevStats* st) {
+__device__ __forceinline__ void p2g(const Grid& g, const PartView& P, const BinView& B,
+                                    float2* acc0, float2* acc1, float2* acc2, const DevStats* st,
+                                    unsigned int blk, unsigned int nblk) {
   __shared__ float tnum[3][TILE_PAD];
   __shared__ float tden[3][TILE_PAD];
   const unsigned int nact = st->n_active;
-  for (unsigned int bi = blockIdx.x; bi < nact; bi += gridDim.x) {
+  for (unsigned int bi = blk; bi < nact; bi += nblk) {
     const unsigned int brick = B.active[bi];
     const int b0 = (int)(brick % (unsigned)g.bx) * BRICK;
     const int b1 = (int)((brick / (unsigned)g.bx) % (unsigned)g.by) * BRICK;
@@ -152,14 +152,28 @@ __global__ void __launch_bounds__(P2G_THREADS, 4) k_p2g(const Grid g, const Part
   }
 }
 
+__global__ void __launch_bounds__(P2G_THREADS, 4) k_p2g(const Grid g, const PartView P,
+                                                     const BinView B, float2* acc0, float2* acc1,
+                                                     float2* acc2, const DevStats* st) {
+  p2g(g, P, B, acc0, acc1, acc2, st, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(P2G_THREADS, 4) k_p2g_batch(const BatchLaunch L) {
+  const int s = batch_scene(L, blockIdx.x);
+  const SceneDev& S = L.scenes[s];
+  p2g(S.g, S.dst, S.B, S.acc[0], S.acc[1], S.acc[2], S.st, blockIdx.x - L.first[s],
+      L.first[s + 1] - L.first[s]);
+}
+
 // u_old = num / den (0 where no particle reached the node); clears the
 // accumulators for the next step.
-__global__ void k_finalize(const Grid g, float2* acc0, float2* acc1, float2* acc2, float* uo0,
-                           float* uo1, float* uo2) {
+__device__ __forceinline__ void finalize(const Grid& g, float2* acc0, float2* acc1, float2* acc2,
+                                         float* uo0, float* uo1, float* uo2, unsigned int blk,
+                                         unsigned int nblk) {
   const long long n0 = n_faces(g, 0), n1 = n_faces(g, 1), n2 = n_faces(g, 2);
   const long long tot = n0 + n1 + n2;
-  for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < tot;
-       f += (long long)gridDim.x * blockDim.x) {
+  for (long long f = blk * (long long)blockDim.x + threadIdx.x; f < tot;
+       f += (long long)nblk * blockDim.x) {
     float2* acc;
     float* uo;
     long long idx;
@@ -172,21 +186,35 @@ __global__ void k_finalize(const Grid g, float2* acc0, float2* acc1, float2* acc
   }
 }
 
+__global__ void k_finalize(const Grid g, float2* acc0, float2* acc1, float2* acc2, float* uo0,
+                           float* uo1, float* uo2) {
+  finalize(g, acc0, acc1, acc2, uo0, uo1, uo2, blockIdx.x, gridDim.x);
+}
+
+__global__ void k_finalize_batch(const BatchLaunch L) {
+  const int s = batch_scene(L, blockIdx.x);
+  const SceneDev& S = L.scenes[s];
+  finalize(S.g, S.acc[0], S.acc[1], S.acc[2], S.uo[0], S.uo[1], S.uo[2], blockIdx.x - L.first[s],
+           L.first[s + 1] - L.first[s]);
+}
+
 // Gravity + walls give u* on the fly; b = -div u* (Eq. 6) in fluid cells.
 // Also starts the solve from p = 0 (every cell, so air cells hold p = 0) and
 // resets the grid barrier and the per-step max-speed word.
-__global__ void k_divergence(const Grid g, const StepConsts K0, const uint8_t* __restrict__ type,
-                             const float* __restrict__ uo0, const float* __restrict__ uo1,
-                             const float* __restrict__ uo2, float* b32, double* b64, float* x32,
-                             double* x64, float2* pff, unsigned int* bar, DevStats* st) {
+// Block (j, k) of a scene walks the x-row of cells (i, j, k): no index divisions.
+__device__ __forceinline__ void divergence(const Grid& g, const StepConsts& K0,
+                                           const uint8_t* __restrict__ type,
+                                           const float* __restrict__ uo0,
+                                           const float* __restrict__ uo1,
+                                           const float* __restrict__ uo2, float* b32, double* b64,
+                                           float* x32, double* x64, float2* pff,
+                                           unsigned int* bar, DevStats* st, int j, int k) {
   const StepConsts K = step_consts(K0);
-  if (blockIdx.x == 0 && blockIdx.y == 0) {
+  if (j == 0 && k == 0) {
     // the grid barrier's arrival counter and spare words (a block may have 32 threads)
     for (unsigned int t = threadIdx.x; t < BAR_WORDS; t += blockDim.x) bar[t] = 0u;
     if (threadIdx.x == 0) st->max_speed_bits = 0u;
   }
-  // block (j, k) walks the x-row of cells (i, j, k): no index divisions
-  const int j = (int)blockIdx.x, k = (int)blockIdx.y;
   for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
     const int c = i + g.nx * (j + g.ny * k);
     if (x32) x32[c] = 0.0f;
@@ -216,6 +244,23 @@ __global__ void k_divergence(const Grid g, const StepConsts K0, const uint8_t* _
       b64[c] = v;
     }
   }
+}
+
+__global__ void k_divergence(const Grid g, const StepConsts K0, const uint8_t* __restrict__ type,
+                             const float* __restrict__ uo0, const float* __restrict__ uo1,
+                             const float* __restrict__ uo2, float* b32, double* b64, float* x32,
+                             double* x64, float2* pff, unsigned int* bar, DevStats* st) {
+  divergence(g, K0, type, uo0, uo1, uo2, b32, b64, x32, x64, pff, bar, st, (int)blockIdx.x,
+             (int)blockIdx.y);
+}
+
+// CTA r of scene s takes row (j, k) = (r % ny, r / ny).
+__global__ void k_divergence_batch(const BatchLaunch L) {
+  const int s = batch_scene(L, blockIdx.x);
+  const SceneDev& S = L.scenes[s];
+  const int r = (int)(blockIdx.x - L.first[s]);
+  divergence(S.g, S.K, S.type, S.uo[0], S.uo[1], S.uo[2], S.b32, S.b64, S.x32, S.x64, S.pff, S.bar,
+             S.st, r % S.g.ny, r / S.g.ny);
 }
 
 template <int D, bool PAIR>
@@ -312,6 +357,18 @@ void launch_divergence(const Grid& g, const StepConsts& k, const uint8_t* type,
   const int threads = std::min(256, (g.nx + 31) / 32 * 32);
   k_divergence<<<dim3((unsigned)g.ny, (unsigned)g.nz), threads, 0, s>>>(
       g, k, type, uo[0], uo[1], uo[2], b32, b64, x32, x64, pff, bar, st);
+}
+
+void launch_p2g_batch(const BatchLaunch& L, unsigned int ctas, cudaStream_t s) {
+  if (ctas) k_p2g_batch<<<ctas, P2G_THREADS, 0, s>>>(L);
+}
+
+void launch_finalize_batch(const BatchLaunch& L, unsigned int ctas, cudaStream_t s) {
+  if (ctas) k_finalize_batch<<<ctas, 256, 0, s>>>(L);
+}
+
+void launch_divergence_batch(const BatchLaunch& L, unsigned int ctas, cudaStream_t s) {
+  if (ctas) k_divergence_batch<<<ctas, 128, 0, s>>>(L);
 }
 
 void launch_u_new(const Grid& g, const StepConsts& k, int d, const float* uo, const float* p32,

@@ -175,6 +175,8 @@ def lib():
         L.flip_surface_destroy.argtypes = [vp]
         L.flip_surface_destroy.restype = None
         L.flip_surface_case_table.argtypes = [vp, vp]
+        L.flip_server_set_overlap.argtypes = [vp, i32]
+        L.flip_batch_set_fused.argtypes = [vp, i32]
         L.flip_step_times.argtypes = [vp, vp, i32]
         L.flip_step_times.restype = i32
         L.flip_set_wait_timeout.argtypes = [vp, C.c_uint64]
@@ -459,6 +461,10 @@ class Batch:
     def set_graphs(self, enable: bool):
         _check(lib().flip_batch_set_graphs(self.b, int(bool(enable))))
 
+    def set_fused(self, enable: bool):
+        """One launch per step kernel across all scenes (default) or per-scene launches."""
+        _check(lib().flip_batch_set_fused(self.b, int(bool(enable))))
+
     def graph_active(self) -> bool:
         return bool(lib().flip_batch_graph_active(self.b))
 
@@ -524,6 +530,10 @@ class Server:
 
     def drain(self):
         _check(lib().flip_server_drain(self.s))
+
+    def set_overlap(self, enable: bool):
+        """Overlapped batches (default) or one batch at a time."""
+        _check(lib().flip_server_set_overlap(self.s, int(bool(enable))))
 
     def now(self) -> float:
         return float(lib().flip_server_now(self.s))

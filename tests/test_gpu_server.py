@@ -122,11 +122,13 @@ def test_served_scenes_match_the_oracle():
 
 
 def test_next_batch_is_enqueued_while_one_runs():
-    """With one scene per batch, the second scene's batch is formed and enqueued while
-    the first is still on the GPU (its start precedes the first one's completion), and
-    every request still completes with its own scene's step."""
-    scenes = [_scene(64, 20 + k) for k in range(4)]
-    with F.Server(budget_bytes=16 << 30, max_batch=1) as srv:
+    """With one scene per batch, the second batch is formed and enqueued as soon as the
+    first batch's solve is done, while the first scene's G2P (13 M particles) still
+    runs: its start precedes the first scene's completion.  Every request completes
+    with its own scene's step."""
+    big = S.dam_break(128, 0.9, 0.9, seed=30)
+    scenes = [(big, matched(128)[1])] + [_scene(32, 31 + k) for k in range(3)]
+    with F.Server(budget_bytes=32 << 30, max_batch=1) as srv:
         ids = [srv.add_scene(fp, *sc.arrays()) for sc, fp in scenes]
         srv.drain()
         for _ in range(2):  # warm the kernels and the events
@@ -136,5 +138,7 @@ def test_next_batch_is_enqueued_while_one_runs():
         tickets = [srv.submit(i, t) for i in ids]
         infos = [srv.wait(k) for k in tickets]
         assert all(i.status == F.FLIP_OK and i.batch_size == 1 for i in infos)
-        done = sorted(infos, key=lambda i: i.t_done)
-        assert done[1].t_start < done[0].t_done, [(i.t_start, i.t_done) for i in done]
+        first = min(infos, key=lambda i: i.t_start)
+        second = min((i for i in infos if i is not first), key=lambda i: i.t_start)
+        assert first.scene == ids[0]
+        assert second.t_start < first.t_done, (second.t_start, first.t_done)
