@@ -1190,8 +1190,10 @@ int batch_graph_steps(flip_batch* b, flip_handle* const* hs, int n, int pairs,
 }
 
 // The batched (fused) step kernels: CTA ranges of each launch, in this order.
-enum FusedLaunch { FL_SCAN = 0, FL_ONE, FL_SCATTER, FL_P2G, FL_FINALIZE, FL_DIV, FL_G2P,
-                   FL_G2P_MIXED, kFusedLaunches };
+// FL_ACT is the running sum of the scenes' active bricks, written on the device
+// each step, which P2G and G2P share out.
+enum FusedLaunch { FL_SCAN = 0, FL_ONE, FL_SCATTER, FL_FINALIZE, FL_DIV, FL_ACT,
+                   kFusedLaunches };
 
 // Scenes a fused step can take: fixed time step, no reseeding.
 bool fusable(const flip_handle* h) { return h->prm.cfl <= 0.0 && !reseeding(h); }
@@ -1219,19 +1221,6 @@ SceneDev scene_dev(const flip_handle* h, int cur) {
   d.np = h->np;
   d.nbricks = h->nbricks;
   return d;
-}
-
-// first[] of a launch that splits `total` CTAs over the scenes in proportion to
-// their particles (at least one each).
-void share_ctas(const std::vector<flip_handle*>& hv, int total, unsigned int* first) {
-  long long tot = 0;
-  for (auto* h : hv) tot += std::max<long long>(h->np, 1);
-  first[0] = 0;
-  for (size_t q = 0; q < hv.size(); ++q) {
-    const long long want = (long long)std::llround((double)total * std::max<long long>(hv[q]->np, 1) /
-                                                   (double)std::max<long long>(tot, 1));
-    first[q + 1] = first[q] + (unsigned int)std::max<long long>(want, 1);
-  }
 }
 
 // Splits max_blocks CTAs over scenes in proportion to their particle counts
@@ -1528,12 +1517,6 @@ int batch_step_impl(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t ns
       const int which[5] = {FL_SCAN, FL_ONE, FL_SCATTER, FL_FINALIZE, FL_DIV};
       for (int k = 0; k < 5; ++k) first[which[k] * W + q + 1] = first[which[k] * W + q] + cnt[k];
     }
-    share_ctas(order, order[0]->p2g_blocks, &first[FL_P2G * W]);
-    // G2P: one launch per precision group, each splitting the CTAs by particles
-    std::vector<flip_handle*> g32(order.begin(), order.begin() + n32),
-        gmx(order.begin() + n32, order.end());
-    if (!g32.empty()) share_ctas(g32, order[0]->g2p_blocks, &first[FL_G2P * W]);
-    if (!gmx.empty()) share_ctas(gmx, order[0]->g2p_blocks, &first[FL_G2P_MIXED * W]);
     FLIP_CUDA(cudaMemcpyAsync(b->d_scenes, tab.data(), sizeof(SceneDev) * tab.size(),
                               cudaMemcpyHostToDevice, bs));
     FLIP_CUDA(cudaMemcpyAsync(b->d_first, first.data(), sizeof(unsigned int) * first.size(),
@@ -1556,15 +1539,17 @@ int batch_step_impl(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t ns
     auto total = [&](int k, int off, int cnt) { return first[k * W + off + cnt] - first[k * W + off]; };
     cudaEvent_t* E = timed ? b->pev.data() + 6 * (size_t)timed_steps : nullptr;
     if (timed) FLIP_CUDA(cudaEventRecord(E[0], bs));
+    unsigned int* act = b->d_first + FL_ACT * W;  // the active bricks' running sum
     launch_bin_batch(L(FL_SCAN, 0, n), total(FL_SCAN, 0, n), L(FL_ONE, 0, n), bs);
+    launch_active_prefix(tab, n, act, bs);
     launch_scatter_batch(L(FL_SCATTER, 0, n), total(FL_SCATTER, 0, n), bs);
     for (auto* h : order) h->cur = 1 - h->cur;
     if (timed) FLIP_CUDA(cudaEventRecord(E[1], bs));
-    launch_p2g_batch(L(FL_P2G, 0, n), total(FL_P2G, 0, n), bs);
+    launch_p2g_batch(BatchLaunch{tab, act, n}, (unsigned)order[0]->p2g_blocks, bs);
     launch_finalize_batch(L(FL_FINALIZE, 0, n), total(FL_FINALIZE, 0, n), bs);
     if (timed) FLIP_CUDA(cudaEventRecord(E[2], bs));
     launch_divergence_batch(L(FL_DIV, 0, n), total(FL_DIV, 0, n), bs);
-    batch_launches += 6;
+    batch_launches += 7;
     if (timed) FLIP_CUDA(cudaEventRecord(E[3], bs));
     for (size_t q = 0; q < launches.size(); ++q) {
       const Launch& Lq = launches[q];
@@ -1577,13 +1562,12 @@ int batch_step_impl(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t ns
     if (timed) FLIP_CUDA(cudaEventRecord(E[4], bs));
     // G2P reads its scenes from the table offset by the group's first scene
     if (n32 > 0) {
-      launch_g2p_batch(BatchLaunch{tab, b->d_first + FL_G2P * W, n32}, total(FL_G2P, 0, n32), false,
-                       bs);
+      launch_g2p_batch(BatchLaunch{tab, act, n32}, (unsigned)order[0]->g2p_blocks, false, bs);
       ++batch_launches;
     }
     if (n32 < n) {
-      launch_g2p_batch(BatchLaunch{tab + n32, b->d_first + FL_G2P_MIXED * W, n - n32},
-                       total(FL_G2P_MIXED, 0, n - n32), true, bs);
+      launch_g2p_batch(BatchLaunch{tab + n32, act + n32, n - n32},
+                       (unsigned)order[0]->g2p_blocks, true, bs);
       ++batch_launches;
     }
     if (timed) FLIP_CUDA(cudaEventRecord(E[5], bs));

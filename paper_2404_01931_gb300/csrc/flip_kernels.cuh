@@ -250,11 +250,14 @@ void launch_iota(int* id, long long np, cudaStream_t s);
 // Batched forms: every scene of the table in one launch per kernel (no
 // reseeding, fixed time step).  first[] per launch as above; `ctas` its total.
 // Per-scene CTA counts: cell_local_scan ceil(nbricks / 8); brick_scan one; scatter
-// ceil(np / 512); finalize ceil(faces / 1024); divergence ny * nz; P2G and G2P
-// any (each scene's CTAs stride over its active bricks).
+// ceil(np / 512); finalize ceil(faces / 1024); divergence ny * nz.
 void launch_bin_batch(const BatchLaunch& L_scan, unsigned int ctas_scan, const BatchLaunch& L_one,
                       cudaStream_t s);
 void launch_scatter_batch(const BatchLaunch& L, unsigned int ctas, cudaStream_t s);
+// P2G and G2P take L.first from launch_active_prefix (device-computed running sum
+// of the scenes' active bricks; entries first[0] .. first[n] of the scenes given)
+// and share all those bricks over `ctas` CTAs.
+void launch_active_prefix(const SceneDev* scenes, int n, unsigned int* out, cudaStream_t s);
 void launch_p2g_batch(const BatchLaunch& L, unsigned int ctas, cudaStream_t s);
 void launch_finalize_batch(const BatchLaunch& L, unsigned int ctas, cudaStream_t s);
 void launch_divergence_batch(const BatchLaunch& L, unsigned int ctas, cudaStream_t s);

@@ -190,154 +190,179 @@ __device__ __forceinline__ void interp_tile(const PartW& W, int li, int lj, int 
   dU = s.y;
 }
 
+// Shared memory of a G2P CTA: the brick's staged tiles and the particle buffers.
 template <bool PAIR>
-__device__ __forceinline__ void g2p(const Grid& g, const StepConsts& K0, const PartView& P,
-                                    const BinView& B, const float* __restrict__ uo0,
-                                    const float* __restrict__ uo1, const float* __restrict__ uo2,
-                                    const float* __restrict__ p32, const float2* __restrict__ pff,
-                                    DevStats* st, unsigned int blk, unsigned int nblk) {
-  const StepConsts K = step_consts(K0);
-  using PT = typename PTile<PAIR>::T;
-  __shared__ PT sp[G2P_PTILE];
-  __shared__ float2 sud[3][G2P_TILE];  // (u_new, u_new - u_old) per face node
-  __shared__ __align__(16) float pbuf[2][6][G2P_CHUNK_PAD];
-  __shared__ __align__(8) unsigned long long bar[2];
-  __shared__ int s_abort;
-  const int lane = threadIdx.x & 31;
-  const unsigned int nact = st->n_active;
-  float speed2 = 0.0f;
+struct G2pShared {
+  typename PTile<PAIR>::T sp[G2P_PTILE];
+  float2 sud[3][G2P_TILE];  // (u_new, u_new - u_old) per face node
+  __align__(16) float pbuf[2][6][G2P_CHUNK_PAD];
+  __align__(8) unsigned long long bar[2];
+  int abort;
+};
+
+// A CTA's streaming state, kept across bricks (and across scenes in a batched
+// launch): the mbarrier phases, the buffer of the next chunk, and (thread 0) which
+// buffers have a copy that nobody has waited for.
+struct G2pCta {
+  unsigned int phase[2] = {0u, 0u};
+  unsigned int kbuf = 0;
+  bool inflight[2] = {false, false};
+};
+
+template <bool PAIR>
+__device__ __forceinline__ void g2p_init(G2pShared<PAIR>& sh) {
   if (threadIdx.x == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    mbar_init(&sh.bar[0], 1);
+    mbar_init(&sh.bar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    s_abort = 0;
+    sh.abort = 0;
   }
   __syncthreads();
-  unsigned int phase[2] = {0u, 0u};
-  unsigned int kbuf = 0;                 // buffer of the next chunk
-  bool inflight[2] = {false, false};     // thread 0: a copy into the buffer is unwaited
-  for (unsigned int bi = blk; bi < nact; bi += nblk) {
-    const unsigned int brick = B.active[bi];
-    const int b0 = (int)(brick % (unsigned)g.bx) * BRICK;
-    const int b1 = (int)((brick / (unsigned)g.bx) % (unsigned)g.by) * BRICK;
-    const int b2 = (int)(brick / ((unsigned)g.bx * (unsigned)g.by)) * BRICK;
-    const unsigned int bstart = B.brick_start[brick], bend = B.brick_start[brick + 1];
-    // the brick's first chunk streams in while the tiles are staged
-    if (threadIdx.x == 0 && bstart < bend) {
-      issue_chunk(P, bstart, min(bend, bstart + G2P_THREADS), pbuf[kbuf], &bar[kbuf]);
-      inflight[kbuf] = true;
-    }
-    // pressure of cells [b - 1, b + 8] per axis (0 outside the grid: never used)
-    for (int t = threadIdx.x; t < G2P_PTILE; t += G2P_THREADS) {
-      const int i = b0 - 1 + t % 10, j = b1 - 1 + (t / 10) % 10, k = b2 - 1 + t / 100;
-      PT v{};
-      if (i >= 0 && j >= 0 && k >= 0 && i < g.nx && j < g.ny && k < g.nz) {
-        const int c = i + g.nx * (j + g.ny * k);
-        if constexpr (PAIR) v = pff[c];
-        else v = p32[c];
-      }
-      sp[t] = v;
-    }
-    __syncthreads();
-    stage_faces<0, PAIR>(g, K, b0, b1, b2, uo0, sp, sud[0]);
-    stage_faces<1, PAIR>(g, K, b0, b1, b2, uo1, sp, sud[1]);
-    stage_faces<2, PAIR>(g, K, b0, b1, b2, uo2, sp, sud[2]);
-    __syncthreads();
-    // chunk loop: CTA-uniform trip count, so every lane takes part in the key match
-    for (unsigned int c0 = bstart; c0 < bend; c0 += G2P_THREADS) {
-      const unsigned int cur = kbuf;
-      kbuf ^= 1u;
-      // the next chunk goes into the other buffer, whose readers passed the
-      // __syncthreads that ended the previous chunk
-      const unsigned int n0 = c0 + G2P_THREADS;
-      if (threadIdx.x == 0 && n0 < bend) {
-        issue_chunk(P, n0, min(bend, n0 + G2P_THREADS), pbuf[kbuf], &bar[kbuf]);
-        inflight[kbuf] = true;
-      }
-      // a thread whose wait gives up reads nothing of the chunk; one whose wait
-      // succeeded saw the whole chunk land
-      if (mbar_wait(&bar[cur], phase[cur], K.wait_ns)) {
-        phase[cur] ^= 1u;
-        inflight[cur] = false;
-      } else {
-        atomicOr(&st->status, DEV_TIMEOUT);
-        s_abort = 1;
-      }
-      const float(*pb)[G2P_CHUNK_PAD] = pbuf[cur];
-      const unsigned int a0 = c0 & ~3u;
-      const unsigned int q = c0 + threadIdx.x;
-      const bool valid = q < bend && !s_abort;
-      unsigned int key = 0xffffffffu;
-      if (valid) {
-        const unsigned int o = q - a0;
-        float x = pb[0][o], y = pb[1][o], z = pb[2][o];
-        const float vp[3] = {pb[3][o], pb[4][o], pb[5][o]};
-        const int ci = cell_of(x, g.inv_dx, g.nx);
-        const int cj = cell_of(y, g.inv_dx, g.ny);
-        const int ck = cell_of(z, g.inv_dx, g.nz);
-        // the particle's cell lies in this brick (its key was taken by the
-        // same cell_of on the same coordinates); the clamp only keeps the
-        // shared-memory indices in range
-        const int li = min(max(ci - b0, 0), BRICK - 1);
-        const int lj = min(max(cj - b1, 0), BRICK - 1);
-        const int lk = min(max(ck - b2, 0), BRICK - 1);
-        PartW W;
-        W.face[0] = axis_weights<0, 0>(x, g.inv_dx, ci, g.nx);
-        W.face[1] = axis_weights<1, 1>(y, g.inv_dx, cj, g.ny);
-        W.face[2] = axis_weights<2, 2>(z, g.inv_dx, ck, g.nz);
-        W.cen[0] = axis_weights<1, 0>(x, g.inv_dx, ci, g.nx);
-        W.cen[1] = axis_weights<0, 1>(y, g.inv_dx, cj, g.ny);
-        W.cen[2] = axis_weights<0, 2>(z, g.inv_dx, ck, g.nz);
-        float U[3], dU[3];
-        interp_tile<0>(W, li, lj, lk, sud[0], U[0], dU[0]);
-        interp_tile<1>(W, li, lj, lk, sud[1], U[1], dU[1]);
-        interp_tile<2>(W, li, lj, lk, sud[2], U[2], dU[2]);
-        const float r = K.flip_ratio, r1 = 1.0f - K.flip_ratio;
-        float vn[3], adv[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          vn[d] = __fadd_rn(__fmul_rn(r, __fadd_rn(vp[d], dU[d])), __fmul_rn(r1, U[d]));
-          adv[d] = K.advect_grid ? U[d] : vn[d];
-        }
-        x = fminf(fmaxf(__fmaf_rn(K.dt, adv[0], x), g.skin), g.hi[0]);
-        y = fminf(fmaxf(__fmaf_rn(K.dt, adv[1], y), g.skin), g.hi[1]);
-        z = fminf(fmaxf(__fmaf_rn(K.dt, adv[2], z), g.skin), g.hi[2]);
-        P.x[q] = x;
-        P.y[q] = y;
-        P.z[q] = z;
-        P.u[q] = vn[0];
-        P.v[q] = vn[1];
-        P.w[q] = vn[2];
-        speed2 = fmaxf(speed2, vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2]);
-        key = brick_key(g, cell_of(x, g.inv_dx, g.nx), cell_of(y, g.inv_dx, g.ny),
-                        cell_of(z, g.inv_dx, g.nz));
-      }
-      // one histogram atomic per distinct key of the warp
-      const unsigned int same = __match_any_sync(0xffffffffu, key);
-      const int leader = __ffs(same) - 1;
-      unsigned int first = 0u;
-      if (valid && lane == leader) first = atomicAdd(B.cell_count + key, (unsigned)__popc(same));
-      first = __shfl_sync(0xffffffffu, first, leader);
-      if (valid) {
-        B.key[q] = key;
-        B.rank[q] = first + (unsigned)__popc(same & ((1u << lane) - 1u));
-      }
-      __syncthreads();
-      if (s_abort) break;
-    }
-    __syncthreads();
-    if (s_abort) break;
+}
+
+// One brick of one scene.  CTA-uniform; returns false once a wait has given up
+// (DEV_TIMEOUT set in the scene's status), after which the CTA takes no more bricks.
+template <bool PAIR>
+__device__ __forceinline__ bool g2p_brick(const Grid& g, const StepConsts& K, const PartView& P,
+                                          const BinView& B, const float* __restrict__ uo0,
+                                          const float* __restrict__ uo1,
+                                          const float* __restrict__ uo2,
+                                          const float* __restrict__ p32,
+                                          const float2* __restrict__ pff, DevStats* st,
+                                          unsigned int brick, G2pShared<PAIR>& sh, G2pCta& cs,
+                                          float& speed2) {
+  using PT = typename PTile<PAIR>::T;
+  const int lane = threadIdx.x & 31;
+  const int b0 = (int)(brick % (unsigned)g.bx) * BRICK;
+  const int b1 = (int)((brick / (unsigned)g.bx) % (unsigned)g.by) * BRICK;
+  const int b2 = (int)(brick / ((unsigned)g.bx * (unsigned)g.by)) * BRICK;
+  const unsigned int bstart = B.brick_start[brick], bend = B.brick_start[brick + 1];
+  // the brick's first chunk streams in while the tiles are staged
+  if (threadIdx.x == 0 && bstart < bend) {
+    issue_chunk(P, bstart, min(bend, bstart + G2P_THREADS), sh.pbuf[cs.kbuf], &sh.bar[cs.kbuf]);
+    cs.inflight[cs.kbuf] = true;
   }
-  // After an abort, thread 0 drains the copies it issued and nobody waited for
-  // (the chunk whose wait gave up, the one issued after it), boundedly; the CTA's
-  // shared memory stays allocated until thread 0 leaves.
+  // pressure of cells [b - 1, b + 8] per axis (0 outside the grid: never used)
+  for (int t = threadIdx.x; t < G2P_PTILE; t += G2P_THREADS) {
+    const int i = b0 - 1 + t % 10, j = b1 - 1 + (t / 10) % 10, k = b2 - 1 + t / 100;
+    PT v{};
+    if (i >= 0 && j >= 0 && k >= 0 && i < g.nx && j < g.ny && k < g.nz) {
+      const int c = i + g.nx * (j + g.ny * k);
+      if constexpr (PAIR) v = pff[c];
+      else v = p32[c];
+    }
+    sh.sp[t] = v;
+  }
+  __syncthreads();
+  stage_faces<0, PAIR>(g, K, b0, b1, b2, uo0, sh.sp, sh.sud[0]);
+  stage_faces<1, PAIR>(g, K, b0, b1, b2, uo1, sh.sp, sh.sud[1]);
+  stage_faces<2, PAIR>(g, K, b0, b1, b2, uo2, sh.sp, sh.sud[2]);
+  __syncthreads();
+  // chunk loop: CTA-uniform trip count, so every lane takes part in the key match
+  for (unsigned int c0 = bstart; c0 < bend; c0 += G2P_THREADS) {
+    const unsigned int cur = cs.kbuf;
+    cs.kbuf ^= 1u;
+    // the next chunk goes into the other buffer, whose readers passed the
+    // __syncthreads that ended the previous chunk
+    const unsigned int n0 = c0 + G2P_THREADS;
+    if (threadIdx.x == 0 && n0 < bend) {
+      issue_chunk(P, n0, min(bend, n0 + G2P_THREADS), sh.pbuf[cs.kbuf], &sh.bar[cs.kbuf]);
+      cs.inflight[cs.kbuf] = true;
+    }
+    // a thread whose wait gives up reads nothing of the chunk; one whose wait
+    // succeeded saw the whole chunk land
+    if (mbar_wait(&sh.bar[cur], cs.phase[cur], K.wait_ns)) {
+      cs.phase[cur] ^= 1u;
+      cs.inflight[cur] = false;
+    } else {
+      atomicOr(&st->status, DEV_TIMEOUT);
+      sh.abort = 1;
+    }
+    const float(*pb)[G2P_CHUNK_PAD] = sh.pbuf[cur];
+    const unsigned int a0 = c0 & ~3u;
+    const unsigned int q = c0 + threadIdx.x;
+    const bool valid = q < bend && !sh.abort;
+    unsigned int key = 0xffffffffu;
+    if (valid) {
+      const unsigned int o = q - a0;
+      float x = pb[0][o], y = pb[1][o], z = pb[2][o];
+      const float vp[3] = {pb[3][o], pb[4][o], pb[5][o]};
+      const int ci = cell_of(x, g.inv_dx, g.nx);
+      const int cj = cell_of(y, g.inv_dx, g.ny);
+      const int ck = cell_of(z, g.inv_dx, g.nz);
+      // the particle's cell lies in this brick (its key was taken by the
+      // same cell_of on the same coordinates); the clamp only keeps the
+      // shared-memory indices in range
+      const int li = min(max(ci - b0, 0), BRICK - 1);
+      const int lj = min(max(cj - b1, 0), BRICK - 1);
+      const int lk = min(max(ck - b2, 0), BRICK - 1);
+      PartW W;
+      W.face[0] = axis_weights<0, 0>(x, g.inv_dx, ci, g.nx);
+      W.face[1] = axis_weights<1, 1>(y, g.inv_dx, cj, g.ny);
+      W.face[2] = axis_weights<2, 2>(z, g.inv_dx, ck, g.nz);
+      W.cen[0] = axis_weights<1, 0>(x, g.inv_dx, ci, g.nx);
+      W.cen[1] = axis_weights<0, 1>(y, g.inv_dx, cj, g.ny);
+      W.cen[2] = axis_weights<0, 2>(z, g.inv_dx, ck, g.nz);
+      float U[3], dU[3];
+      interp_tile<0>(W, li, lj, lk, sh.sud[0], U[0], dU[0]);
+      interp_tile<1>(W, li, lj, lk, sh.sud[1], U[1], dU[1]);
+      interp_tile<2>(W, li, lj, lk, sh.sud[2], U[2], dU[2]);
+      const float r = K.flip_ratio, r1 = 1.0f - K.flip_ratio;
+      float vn[3], adv[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        vn[d] = __fadd_rn(__fmul_rn(r, __fadd_rn(vp[d], dU[d])), __fmul_rn(r1, U[d]));
+        adv[d] = K.advect_grid ? U[d] : vn[d];
+      }
+      x = fminf(fmaxf(__fmaf_rn(K.dt, adv[0], x), g.skin), g.hi[0]);
+      y = fminf(fmaxf(__fmaf_rn(K.dt, adv[1], y), g.skin), g.hi[1]);
+      z = fminf(fmaxf(__fmaf_rn(K.dt, adv[2], z), g.skin), g.hi[2]);
+      P.x[q] = x;
+      P.y[q] = y;
+      P.z[q] = z;
+      P.u[q] = vn[0];
+      P.v[q] = vn[1];
+      P.w[q] = vn[2];
+      speed2 = fmaxf(speed2, vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2]);
+      key = brick_key(g, cell_of(x, g.inv_dx, g.nx), cell_of(y, g.inv_dx, g.ny),
+                      cell_of(z, g.inv_dx, g.nz));
+    }
+    // one histogram atomic per distinct key of the warp
+    const unsigned int same = __match_any_sync(0xffffffffu, key);
+    const int leader = __ffs(same) - 1;
+    unsigned int first = 0u;
+    if (valid && lane == leader) first = atomicAdd(B.cell_count + key, (unsigned)__popc(same));
+    first = __shfl_sync(0xffffffffu, first, leader);
+    if (valid) {
+      B.key[q] = key;
+      B.rank[q] = first + (unsigned)__popc(same & ((1u << lane) - 1u));
+    }
+    __syncthreads();
+    if (sh.abort) break;
+  }
+  __syncthreads();
+  return !sh.abort;
+}
+
+// After an abort, thread 0 drains the copies it issued and nobody waited for
+// (the chunk whose wait gave up, the one issued after it), boundedly; the CTA's
+// shared memory stays allocated until thread 0 leaves.
+template <bool PAIR>
+__device__ __forceinline__ void g2p_drain(G2pShared<PAIR>& sh, const G2pCta& cs) {
   if (threadIdx.x == 0)
 #pragma unroll
     for (int k = 0; k < 2; ++k)
-      if (inflight[k]) (void)mbar_wait(&bar[k], phase[k], G2P_DRAIN_NS);
+      if (cs.inflight[k]) (void)mbar_wait(&sh.bar[k], cs.phase[k], G2P_DRAIN_NS);
+}
+
+// The largest particle speed a CTA saw in a scene, into the scene's statistics.
+// CTA-uniform (every warp takes part).
+__device__ __forceinline__ void g2p_flush_speed(float& speed2, DevStats* st) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) speed2 = fmaxf(speed2, __shfl_xor_sync(0xffffffffu, speed2, o));
-  if (lane == 0 && speed2 > 0.0f) atomicMax(&st->max_speed_bits, __float_as_uint(sqrtf(speed2)));
+  if ((threadIdx.x & 31) == 0 && speed2 > 0.0f)
+    atomicMax(&st->max_speed_bits, __float_as_uint(sqrtf(speed2)));
+  speed2 = 0.0f;
 }
 
 template <bool PAIR>
@@ -349,15 +374,47 @@ __global__ void __launch_bounds__(G2P_THREADS, 5) k_g2p(const Grid g, const Step
                                                      const float* __restrict__ p32,
                                                      const float2* __restrict__ pff,
                                                      DevStats* st) {
-  g2p<PAIR>(g, K0, P, B, uo0, uo1, uo2, p32, pff, st, blockIdx.x, gridDim.x);
+  __shared__ G2pShared<PAIR> sh;
+  const StepConsts K = step_consts(K0);
+  const unsigned int nact = st->n_active;
+  g2p_init(sh);
+  G2pCta cs;
+  float speed2 = 0.0f;
+  for (unsigned int bi = blockIdx.x; bi < nact; bi += gridDim.x)
+    if (!g2p_brick<PAIR>(g, K, P, B, uo0, uo1, uo2, p32, pff, st, B.active[bi], sh, cs, speed2))
+      break;
+  g2p_drain(sh, cs);
+  g2p_flush_speed(speed2, st);
 }
 
+// All scenes' active bricks as one list (L.first from k_active_prefix): the CTAs
+// share every scene's bricks evenly.  A CTA that gives up on a wait marks every
+// scene whose bricks it leaves undone.
 template <bool PAIR>
 __global__ void __launch_bounds__(G2P_THREADS, 5) k_g2p_batch(const BatchLaunch L) {
-  const int s = batch_scene(L, blockIdx.x);
-  const SceneDev& S = L.scenes[s];
-  g2p<PAIR>(S.g, S.K, S.dst, S.B, S.uo[0], S.uo[1], S.uo[2], S.x32, S.pff, S.st,
-            blockIdx.x - L.first[s], L.first[s + 1] - L.first[s]);
+  __shared__ G2pShared<PAIR> sh;
+  g2p_init(sh);
+  G2pCta cs;
+  float speed2 = 0.0f;
+  int cur = -1;
+  const unsigned int g0 = L.first[0], g1 = L.first[L.n];
+  unsigned int gb = g0 + blockIdx.x;
+  for (; gb < g1; gb += gridDim.x) {
+    const int s = batch_scene(L, gb);
+    const SceneDev& S = L.scenes[s];
+    if (s != cur) {
+      if (cur >= 0) g2p_flush_speed(speed2, L.scenes[cur].st);
+      cur = s;
+    }
+    if (!g2p_brick<PAIR>(S.g, step_consts(S.K), S.dst, S.B, S.uo[0], S.uo[1], S.uo[2], S.x32,
+                         S.pff, S.st, S.B.active[gb - L.first[s]], sh, cs, speed2))
+      break;
+  }
+  g2p_drain(sh, cs);
+  if (cur >= 0) g2p_flush_speed(speed2, L.scenes[cur].st);
+  if (gb < g1 && threadIdx.x == 0)  // aborted: the scenes of the bricks left undone
+    for (gb += gridDim.x; gb < g1; gb += gridDim.x)
+      atomicOr(&L.scenes[batch_scene(L, gb)].st->status, DEV_TIMEOUT);
 }
 
 int g2p_blocks(int sm_count) {

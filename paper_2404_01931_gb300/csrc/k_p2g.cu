@@ -113,56 +113,77 @@ __device__ __forceinline__ void flush_tile(const Grid& g, int b0, int b1, int b2
   }
 }
 
-__device__ __forceinline__ void p2g(const Grid& g, const PartView& P, const BinView& B,
-                                    float2* acc0, float2* acc1, float2* acc2, const DevStats* st,
-                                    unsigned int blk, unsigned int nblk) {
-  __shared__ float tnum[3][TILE_PAD];
-  __shared__ float tden[3][TILE_PAD];
-  const unsigned int nact = st->n_active;
-  for (unsigned int bi = blk; bi < nact; bi += nblk) {
-    const unsigned int brick = B.active[bi];
-    const int b0 = (int)(brick % (unsigned)g.bx) * BRICK;
-    const int b1 = (int)((brick / (unsigned)g.bx) % (unsigned)g.by) * BRICK;
-    const int b2 = (int)(brick / ((unsigned)g.bx * (unsigned)g.by)) * BRICK;
-    for (int t = threadIdx.x; t < 3 * TILE_PAD; t += P2G_THREADS) {
-      (&tnum[0][0])[t] = 0.0f;
-      (&tden[0][0])[t] = 0.0f;
-    }
-    __syncthreads();
-    const unsigned int bstart = B.brick_start[brick], bend = B.brick_start[brick + 1];
-    static_assert(BRICK_CELLS == 2 * P2G_THREADS, "two passes of 8 x 8 x 4 cells");
-    for (int pass = 0; pass < 2; ++pass) {
-      const int li = threadIdx.x & 7, lk = ((threadIdx.x >> 3) & 3) + 4 * pass,
-                lj = threadIdx.x >> 5;
-      const int l = li + BRICK * (lj + BRICK * lk);
-      const unsigned int key = brick * BRICK_CELLS + (unsigned)l;
-      const unsigned int beg = bstart + B.local_start[key];
-      const unsigned int end = (l < BRICK_CELLS - 1) ? bstart + B.local_start[key + 1] : bend;
-      if (beg == end) continue;
-      const int ci = b0 + li, cj = b1 + lj, ck = b2 + lk;
-      p2g_cell<0>(g, P, beg, end, ci, cj, ck, li, lj, lk, tnum[0], tden[0]);
-      p2g_cell<1>(g, P, beg, end, ci, cj, ck, li, lj, lk, tnum[1], tden[1]);
-      p2g_cell<2>(g, P, beg, end, ci, cj, ck, li, lj, lk, tnum[2], tden[2]);
-    }
-    __syncthreads();
-    flush_tile<0>(g, b0, b1, b2, tnum[0], tden[0], acc0);
-    flush_tile<1>(g, b0, b1, b2, tnum[1], tden[1], acc1);
-    flush_tile<2>(g, b0, b1, b2, tnum[2], tden[2], acc2);
-    __syncthreads();
+// One brick: zero the tiles, splat its cells' particles, add the tiles to the
+// global accumulators.  CTA-uniform; ends with a __syncthreads.
+__device__ __forceinline__ void p2g_brick(const Grid& g, const PartView& P, const BinView& B,
+                                          float2* acc0, float2* acc1, float2* acc2,
+                                          unsigned int brick, float (*tnum)[TILE_PAD],
+                                          float (*tden)[TILE_PAD]) {
+  const int b0 = (int)(brick % (unsigned)g.bx) * BRICK;
+  const int b1 = (int)((brick / (unsigned)g.bx) % (unsigned)g.by) * BRICK;
+  const int b2 = (int)(brick / ((unsigned)g.bx * (unsigned)g.by)) * BRICK;
+  for (int t = threadIdx.x; t < 3 * TILE_PAD; t += P2G_THREADS) {
+    (&tnum[0][0])[t] = 0.0f;
+    (&tden[0][0])[t] = 0.0f;
   }
+  __syncthreads();
+  const unsigned int bstart = B.brick_start[brick], bend = B.brick_start[brick + 1];
+  static_assert(BRICK_CELLS == 2 * P2G_THREADS, "two passes of 8 x 8 x 4 cells");
+  for (int pass = 0; pass < 2; ++pass) {
+    const int li = threadIdx.x & 7, lk = ((threadIdx.x >> 3) & 3) + 4 * pass,
+              lj = threadIdx.x >> 5;
+    const int l = li + BRICK * (lj + BRICK * lk);
+    const unsigned int key = brick * BRICK_CELLS + (unsigned)l;
+    const unsigned int beg = bstart + B.local_start[key];
+    const unsigned int end = (l < BRICK_CELLS - 1) ? bstart + B.local_start[key + 1] : bend;
+    if (beg == end) continue;
+    const int ci = b0 + li, cj = b1 + lj, ck = b2 + lk;
+    p2g_cell<0>(g, P, beg, end, ci, cj, ck, li, lj, lk, tnum[0], tden[0]);
+    p2g_cell<1>(g, P, beg, end, ci, cj, ck, li, lj, lk, tnum[1], tden[1]);
+    p2g_cell<2>(g, P, beg, end, ci, cj, ck, li, lj, lk, tnum[2], tden[2]);
+  }
+  __syncthreads();
+  flush_tile<0>(g, b0, b1, b2, tnum[0], tden[0], acc0);
+  flush_tile<1>(g, b0, b1, b2, tnum[1], tden[1], acc1);
+  flush_tile<2>(g, b0, b1, b2, tnum[2], tden[2], acc2);
+  __syncthreads();
 }
 
 __global__ void __launch_bounds__(P2G_THREADS, 4) k_p2g(const Grid g, const PartView P,
                                                      const BinView B, float2* acc0, float2* acc1,
                                                      float2* acc2, const DevStats* st) {
-  p2g(g, P, B, acc0, acc1, acc2, st, blockIdx.x, gridDim.x);
+  __shared__ float tnum[3][TILE_PAD];
+  __shared__ float tden[3][TILE_PAD];
+  const unsigned int nact = st->n_active;
+  for (unsigned int bi = blockIdx.x; bi < nact; bi += gridDim.x)
+    p2g_brick(g, P, B, acc0, acc1, acc2, B.active[bi], tnum, tden);
 }
 
+// All scenes' active bricks as one list: L.first holds the running sum of the
+// scenes' active-brick counts (k_active_prefix), so the CTAs share the bricks of
+// every scene evenly whatever their sizes.
 __global__ void __launch_bounds__(P2G_THREADS, 4) k_p2g_batch(const BatchLaunch L) {
-  const int s = batch_scene(L, blockIdx.x);
-  const SceneDev& S = L.scenes[s];
-  p2g(S.g, S.dst, S.B, S.acc[0], S.acc[1], S.acc[2], S.st, blockIdx.x - L.first[s],
-      L.first[s + 1] - L.first[s]);
+  __shared__ float tnum[3][TILE_PAD];
+  __shared__ float tden[3][TILE_PAD];
+  const unsigned int g0 = L.first[0], g1 = L.first[L.n];
+  for (unsigned int gb = g0 + blockIdx.x; gb < g1; gb += gridDim.x) {
+    const int s = batch_scene(L, gb);
+    const SceneDev& S = L.scenes[s];
+    p2g_brick(S.g, S.dst, S.B, S.acc[0], S.acc[1], S.acc[2], S.B.active[gb - L.first[s]], tnum,
+              tden);
+  }
+}
+
+// The running sum of the scenes' active-brick counts (their binning's result):
+// out[0] = 0, out[s + 1] = out[s] + n_active of scene s.  One thread.
+__global__ void k_active_prefix(const SceneDev* scenes, int n, unsigned int* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  unsigned int run = 0;
+  out[0] = 0;
+  for (int s = 0; s < n; ++s) {
+    run += scenes[s].st->n_active;
+    out[s + 1] = run;
+  }
 }
 
 // u_old = num / den (0 where no particle reached the node); clears the
@@ -357,6 +378,10 @@ void launch_divergence(const Grid& g, const StepConsts& k, const uint8_t* type,
   const int threads = std::min(256, (g.nx + 31) / 32 * 32);
   k_divergence<<<dim3((unsigned)g.ny, (unsigned)g.nz), threads, 0, s>>>(
       g, k, type, uo[0], uo[1], uo[2], b32, b64, x32, x64, pff, bar, st);
+}
+
+void launch_active_prefix(const SceneDev* scenes, int n, unsigned int* out, cudaStream_t s) {
+  if (n > 0) k_active_prefix<<<1, 32, 0, s>>>(scenes, n, out);
 }
 
 void launch_p2g_batch(const BatchLaunch& L, unsigned int ctas, cudaStream_t s) {
