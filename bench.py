@@ -681,7 +681,8 @@ def run_serve(args):
     clocks = ClockSampler(local)
     clocks.start()
     part = serve_workload(args.serve, args.serve_max_edge, args.rate, args.requests,
-                          args.budget_gb, args.max_batch, ws, rank)
+                          args.budget_gb, args.max_batch, ws, rank,
+                          overlap=not args.serve_serial)
     ck = clocks.stop()
     parts = [part]
     if ws > 1:
@@ -703,7 +704,8 @@ def run_serve(args):
                                      "(longest first to the least-loaded rank), one server "
                                      "per GPU, no data-path collective"},
            "latency_ms": sv["latency_ms"], "mean_batch": sv["mean_batch"],
-           "failed": sv["failed"], "clocks": ck}
+           "failed": sv["failed"], "clocks": ck,
+           "batches": "one at a time" if args.serve_serial else "overlapped"}
     print(json.dumps(out), flush=True)
 
 
@@ -723,6 +725,8 @@ def main():
     ap.add_argument("--serve", type=int, default=0,
                     help="run the serving form over this many resident scenes")
     ap.add_argument("--serve-max-edge", type=int, default=192)
+    ap.add_argument("--serve-serial", action="store_true",
+                    help="serving: one batch at a time instead of overlapped batches")
     ap.add_argument("--rate", type=float, default=2000.0, help="request arrivals per second")
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--budget-gb", type=float, default=180.0)

@@ -1721,6 +1721,8 @@ int batch_step_overlapped(flip_batch* b, flip_handle* const* hs, int n) {
 }
 // The stream a handle's kernels run on.
 cudaStream_t handle_stream(const flip_handle* h) { return h ? h->stream : nullptr; }
+// The device address of a handle's sticky status word (DEV_* bits).
+int* handle_status_word(const flip_handle* h) { return h ? &h->dstats->status : nullptr; }
 }  // namespace flipk
 
 extern "C" {

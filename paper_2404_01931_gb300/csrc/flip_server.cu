@@ -31,6 +31,8 @@ void flip_set_last_error_(const std::string& msg);
 namespace flipk {
 int batch_step_overlapped(flip_batch* b, flip_handle* const* hs, int n);
 cudaStream_t handle_stream(const flip_handle* h);
+int* handle_status_word(const flip_handle* h);
+int api_status_to_code(int dev_status);
 }  // namespace flipk
 
 namespace {
@@ -43,7 +45,7 @@ struct Scene {
   flip_handle* h = nullptr;    // resident when non-null
   int create_status = FLIP_OK; // failure of the admission, if any
   bool remove = false;
-  bool in_flight = false;
+  int in_flight = 0;             // batches in flight that step this scene
   int pending = 0;             // requests queued or running
 };
 
@@ -58,7 +60,8 @@ struct Request {
 constexpr int kSlots = 2;  // batches in flight at once
 
 // A batch enqueued on the device: its requests, their scenes' handles, and one
-// event per scene recorded on the scene's stream after its step.
+// event per scene recorded on the scene's stream after its step and after the
+// copy of the scene's status word into the slot's pinned status array.
 struct InFlight {
   int slot = 0;
   int launch_status = FLIP_OK;
@@ -90,6 +93,7 @@ struct flip_server {
   cudaStream_t solve_stream = nullptr;  // shared by the slots' batched solves
   flip_batch* slot[kSlots] = {};
   bool slot_busy[kSlots] = {};
+  int* slot_status[kSlots] = {};  // pinned: each scene's status word after its step
   std::vector<cudaEvent_t> event_pool;  // per-scene completion events, reused
   std::deque<InFlight> inflight;
   std::condition_variable cv_inflight;
@@ -222,7 +226,10 @@ struct flip_server {
       for (auto q = queue.begin(); k >= 0 && q != queue.end() && (int)pick.size() < max_batch;) {
         const Request& r = reqs[*q];
         Scene& sc = scenes[r.scene];
-        const bool ready = sc.h && !sc.in_flight && !in_batch.count(r.scene);
+        // a scene whose step is still in flight may take part in the next batch
+        // in the overlapped mode: its work is ordered on its stream (and the shared
+        // solve stream), and each step's status is captured in stream order
+        const bool ready = sc.h && (overlap || sc.in_flight == 0) && !in_batch.count(r.scene);
         if (ready && r.t_arrival <= t) {
           pick.push_back(*q);
           hs.push_back(sc.h);
@@ -256,18 +263,26 @@ struct flip_server {
       for (size_t q = 0; q < pick.size(); ++q) {
         reqs[pick[q]].t_start = t;
         reqs[pick[q]].batch_size = (int)pick.size();
-        scenes[reqs[pick[q]].scene].in_flight = true;
+        scenes[reqs[pick[q]].scene].in_flight += 1;
         f.done.push_back(take_event_locked());
       }
       slot_busy[k] = true;
       cudaEvent_t solved = take_event_locked();
       lk.unlock();
       f.launch_status = flipk::batch_step_overlapped(slot[k], hs.data(), (int)hs.size());
-      for (size_t q = 0; q < hs.size(); ++q)
-        if (!f.done[q] || cudaEventRecord(f.done[q], flipk::handle_stream(hs[q])) != cudaSuccess) {
+      for (size_t q = 0; q < hs.size(); ++q) {
+        // the step's status word, read and cleared in stream order, then its event
+        const cudaStream_t hs_q = flipk::handle_stream(hs[q]);
+        int* word = flipk::handle_status_word(hs[q]);
+        if (!f.done[q] ||
+            cudaMemcpyAsync(slot_status[k] + q, word, sizeof(int), cudaMemcpyDeviceToHost,
+                            hs_q) != cudaSuccess ||
+            cudaMemsetAsync(word, 0, sizeof(int), hs_q) != cudaSuccess ||
+            cudaEventRecord(f.done[q], hs_q) != cudaSuccess) {
           cudaGetLastError();
           if (f.launch_status == FLIP_OK) f.launch_status = FLIP_E_CUDA;
         }
+      }
       // the solve stream's last work of the call is the batched solve
       if (solved && cudaEventRecord(solved, solve_stream) != cudaSuccess) {
         cudaGetLastError();
@@ -295,13 +310,14 @@ struct flip_server {
       lk.unlock();
       std::vector<int> st(f.hs.size(), f.launch_status);
       for (size_t q = 0; q < f.hs.size(); ++q) {
-        if (f.done[q]) cudaEventSynchronize(f.done[q]);
-        // the scene's stream is idle now: its status word is read and cleared
-        const int s2 = flip_sync(f.hs[q]);
+        int s2 = FLIP_E_CUDA;
+        if (f.done[q] && cudaEventSynchronize(f.done[q]) == cudaSuccess)
+          s2 = flipk::api_status_to_code(slot_status[f.slot][q]);
+        cudaGetLastError();
         if (st[q] == FLIP_OK) st[q] = s2;
         const double t_done = now();
         lk.lock();
-        scenes[reqs[f.tickets[q]].scene].in_flight = false;
+        scenes[reqs[f.tickets[q]].scene].in_flight -= 1;
         complete_locked(f.tickets[q], st[q], t_done, (int)f.hs.size());
         if (f.done[q]) event_pool.push_back(f.done[q]);
         f.done[q] = nullptr;
@@ -344,9 +360,18 @@ int flip_server_create(size_t budget_bytes, int32_t max_batch, flip_server** out
     return FLIP_E_CUDA;
   }
   for (int k = 0; k < kSlots; ++k) {
-    const int rc = flip_batch_create(max_batch, s->solve_stream, &s->slot[k]);
+    int rc = flip_batch_create(max_batch, s->solve_stream, &s->slot[k]);
+    if (rc == FLIP_OK &&
+        cudaMallocHost((void**)&s->slot_status[k], sizeof(int) * (size_t)max_batch) != cudaSuccess) {
+      cudaGetLastError();
+      flip_batch_destroy(s->slot[k]);
+      rc = FLIP_E_OOM;
+    }
     if (rc != FLIP_OK) {
-      for (int q = 0; q < k; ++q) flip_batch_destroy(s->slot[q]);
+      for (int q = 0; q < k; ++q) {
+        flip_batch_destroy(s->slot[q]);
+        cudaFreeHost(s->slot_status[q]);
+      }
       cudaStreamDestroy(s->solve_stream);
       delete s;
       return rc;
@@ -484,7 +509,10 @@ void flip_server_destroy(flip_server* s) {
   if (s->completer.joinable()) s->completer.join();
   for (auto& kv : s->scenes)
     if (kv.second.h) flip_destroy(kv.second.h);
-  for (int k = 0; k < kSlots; ++k) flip_batch_destroy(s->slot[k]);
+  for (int k = 0; k < kSlots; ++k) {
+    flip_batch_destroy(s->slot[k]);
+    if (s->slot_status[k]) cudaFreeHost(s->slot_status[k]);
+  }
   for (cudaEvent_t e : s->event_pool) cudaEventDestroy(e);
   if (s->solve_stream) {
     cudaStreamSynchronize(s->solve_stream);
