@@ -288,6 +288,7 @@ void setup_mg(MgArgs& m, int dims[MG_MAX_LEVELS][3], const flip_params& p) {
   m.lgrid = m.nlev;
   for (int l = 0; l < m.nlev; ++l) {
     MgLevel& L = m.lv[l];
+    L.lvl = l;
     L.nx = dims[l][0];
     L.ny = dims[l][1];
     L.nz = dims[l][2];

@@ -182,8 +182,9 @@ __device__ __forceinline__ void st_release_gpu(unsigned int* p, unsigned int v) 
 
 // Grid-wide barrier for a cooperative launch (all CTAs co-resident).  bar[0]
 // counts arrivals and is never reset inside a launch: the k-th barrier of a CTA
-// ends when the counter reaches k * nblocks, which the CTA learns from the value
-// its own arrival returned.  Arrival is a release add and the wait an acquire
+// ends when the counter reaches k * nblocks, k counted per CTA in s_bar_gen
+// (zeroed at kernel entry by team_enter).  Arrival is a release reduction (no
+// value comes back, so the CTA starts polling at once) and the wait an acquire
 // load, so every write before the barrier (ordered by __syncthreads before
 // thread 0's release) is visible to every thread after it.  The caller resets
 // bar[0] to 0 before the launch; the rest of the BAR_WORDS-word block is spare.
@@ -192,10 +193,10 @@ __device__ __forceinline__ void st_release_gpu(unsigned int* p, unsigned int v) 
 // returns false too.  Callers stop their loop on false, so no CTA is left waiting.
 constexpr unsigned int BAR_WORDS = 64;
 
-__device__ __forceinline__ unsigned int atom_add_release_gpu(unsigned int* p, unsigned int v) {
-  unsigned int old;
-  asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-  return old;
+__shared__ unsigned int s_bar_gen;
+
+__device__ __forceinline__ void red_add_release_gpu(unsigned int* p, unsigned int v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 __device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* status, unsigned int nblocks,
@@ -204,8 +205,9 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* status, uns
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    const unsigned int old = atom_add_release_gpu(bar, 1u);
-    const unsigned int target = (old / nblocks + 1u) * nblocks;
+    const unsigned int target = (s_bar_gen + 1u) * nblocks;
+    s_bar_gen += 1u;
+    red_add_release_gpu(bar, 1u);
     const unsigned long long t0 = global_timer_ns();
     while ((int)(ld_acquire_gpu(bar) - target) < 0) {
       if (*(volatile int*)status & DEV_TIMEOUT) { ok = 0; break; }

@@ -114,6 +114,7 @@ constexpr float MG_OMEGA = 2.0f;      // over-correction of the coarse correctio
 // neighbour address inside the array.  The CTA-local levels (l >= lgrid) use the
 // natural x-fastest layout.
 struct MgLevel {
+  int lvl;            // this level's index
   int nx, ny, nz, ncells;
   float inv_scnt[8];  // 1 / (s_l * count), s_l = dt / (rho (2^l dx)^2)
   float s;

@@ -55,20 +55,34 @@ __device__ __forceinline__ void load_tables(const MgArgs& M) {
   __syncthreads();
 }
 
+// Each CTA's slice of a level's active segments is the same in every pass of a
+// solve, so after the lists are built the CTA copies its slices into shared
+// memory (as many levels as SEG_CACHE holds, level 0 first): the first load of
+// every item of a pass, the segment, is then a shared-memory read.  s_segc[l] is
+// the copy of level l's slice (nullptr: read the list in global memory) and
+// s_segb[l] the index of its first segment.
+constexpr int SEG_CACHE = 1024;
+__shared__ const int4* s_segc[MG_MAX_LEVELS];
+__shared__ int s_segb[MG_MAX_LEVELS];
+
 // The fields of a colour-split level a pass uses, read once into registers at
 // the start of the pass (the level descriptions live in parameter or shared
 // memory and would otherwise be re-read through generic pointers per cell).
+// Segment t of the level is seg[t - seg_base].
 struct SV {
   float* x;
   float* b;
   uint16_t* code;
   const int4* seg;
+  int seg_base;
   int nx, ny, hx, half, margin, pl;
   float s;
 };
 
 __device__ __forceinline__ SV sview(const MgLevel& L) {
-  return SV{L.x, L.b, L.code16, L.seg, L.nx, L.ny, L.hx, L.half, L.margin, L.hx * L.ny, L.s};
+  const int4* c = s_segc[L.lvl];
+  return SV{L.x, L.b, L.code16, c ? c : L.seg, c ? s_segb[L.lvl] : 0, L.nx, L.ny, L.hx,
+            L.half, L.margin, L.hx * L.ny, L.s};
 }
 
 // The same for the level whose x a correction reads (colour-split or natural).
@@ -190,12 +204,11 @@ struct PCell {
 };
 
 template <class LV>
-__device__ __forceinline__ PCell pcell(const LV& L, const int4* seg, int2 q, unsigned int pair,
-                                       int c, int lane) {
+__device__ __forceinline__ PCell pcell(const LV& L, int2 q, unsigned int pair, int c, int lane) {
   int sq = q.x + 2 * (int)pair + (lane >> 4);
   const bool seg_ok = sq < q.y;
   if (!seg_ok) sq = q.x;
-  const int4 sg = seg[sq];
+  const int4 sg = L.seg[sq - L.seg_base];
   PCell e;
   e.j = sg.z;
   e.k = sg.w;
@@ -391,7 +404,7 @@ __device__ __noinline__ void sweep_split_v(const MgArgs& M, const MgLevel& L, co
       it.first, it.end, PCG_WARPS,
       [&](unsigned int t, bool ok) {
         S st;
-        st.e = pcell(v, v.seg, q, t, colour, lane);
+        st.e = pcell(v, q, t, colour, lane);
         st.e.okA &= ok;
         st.e.okB &= ok;
         st.code2 = *reinterpret_cast<const unsigned int*>(v.code + st.e.idx);
@@ -454,7 +467,7 @@ __device__ __noinline__ void sweep_split_s(const MgArgs& M, const MgLevel& L, co
   run_batched<U>(
       it.first, it.end, PCG_WARPS,
       [&](unsigned int t, bool ok) {
-        const SCell e = scell(v, v.seg[t], colour, lane);
+        const SCell e = scell(v, v.seg[t - v.seg_base], colour, lane);
         GsIn s;
         s.i = e.i;
         s.j = e.j;
@@ -558,7 +571,7 @@ __device__ __noinline__ void restrict_split(const MgLevel& Fl, const MgLevel& Cl
   const int fnz = Fl.nz;
   const Items it = seg_items(Cl, 1);
   for (unsigned int t = it.first; t < it.end; t += PCG_WARPS) {
-    const int4 sg = C.seg[t];
+    const int4 sg = C.seg[t - C.seg_base];
     const int J = sg.z, K = sg.w;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -939,7 +952,7 @@ __device__ __noinline__ void phase_a_v(const PcgArgs& A, const float* pold, floa
   const Items it = pair_items(q, 2);
   FF acc;
   for (unsigned int t = it.first; t < it.end; t += PCG_WARPS) {
-    const PCell e = pcell(v, v.seg, q, t >> 1, (int)(t & 1u), lane);
+    const PCell e = pcell(v, q, t >> 1, (int)(t & 1u), lane);
     const unsigned int code2 = *reinterpret_cast<const unsigned int*>(v.code + e.idx);
     const float2 zc = *reinterpret_cast<const float2*>(z + e.idx);
     const float2 pc = *reinterpret_cast<const float2*>(pold + e.idx);
@@ -998,7 +1011,7 @@ __device__ __noinline__ void phase_b_v(const PcgArgs& A, const float* pnew, floa
       [&](unsigned int t, bool ok) {
         S st;
         st.c = (int)(t & 1u);
-        st.e = pcell(v, v.seg, q, t >> 1, st.c, lane);
+        st.e = pcell(v, q, t >> 1, st.c, lane);
         st.e.okA &= ok;
         st.e.okB &= ok;
         st.code2 = *reinterpret_cast<const unsigned int*>(v.code + st.e.idx);
@@ -1055,7 +1068,7 @@ __device__ __noinline__ void phase_a_s(const PcgArgs& A, const float* pold, floa
   run_batched<1>(
       it.first, it.end, PCG_WARPS,
       [&](unsigned int t, bool ok) {
-        const SCell e = scell(v, v.seg[t >> 1], (int)(t & 1u), lane);
+        const SCell e = scell(v, v.seg[(int)(t >> 1) - v.seg_base], (int)(t & 1u), lane);
         S s;
         s.idx = e.idx;
         s.ok = e.ok && ok;
@@ -1112,7 +1125,7 @@ __device__ __noinline__ void phase_b_s(const PcgArgs& A, const float* pnew, floa
   run_batched<2>(
       it.first, it.end, PCG_WARPS,
       [&](unsigned int t, bool ok) {
-        const SCell e = scell(v, v.seg[t >> 1], (int)(t & 1u), lane);
+        const SCell e = scell(v, v.seg[(int)(t >> 1) - v.seg_base], (int)(t & 1u), lane);
         S s;
         s.idx = e.idx;
         s.c = (int)(t & 1u);
@@ -1154,10 +1167,11 @@ __device__ __forceinline__ void phase_b(const PcgArgs& A, const float* pnew, flo
 template <class F>
 __device__ __forceinline__ void for_fluid0(const PcgArgs& A, F&& f) {
   const MgLevel& L0 = A.mg.lv[0];
+  const SV v0 = sview(L0);
   const int lane = threadIdx.x & 31;
   const Items it = seg_items(L0, 2);
   for (unsigned int t = it.first; t < it.end; t += PCG_WARPS) {
-    const SCell e = scell(L0, L0.seg[t >> 1], (int)(t & 1u), lane);
+    const SCell e = scell(v0, v0.seg[(int)(t >> 1) - v0.seg_base], (int)(t & 1u), lane);
     if (!e.ok) continue;
     const unsigned int code = L0.code16[e.idx];
     if (!(code & CODE_SELF)) continue;
@@ -1313,6 +1327,35 @@ __device__ __noinline__ bool build_levels(const PcgArgs& A, Shared& sh) {
   return gsync(A);
 }
 
+// Copies this CTA's slice of each grid-wide level's segment list into the
+// shared-memory cache, level 0 first, while it fits (after build_levels).
+__device__ __noinline__ void seg_cache_fill(const MgArgs& M, int4* cache) {
+  int used = 0;
+  for (int l = 0; l < M.lgrid; ++l) {
+    const MgLevel& L = M.lv[l];
+    const int2 q = seg_slice(L);
+    const int n = q.y - q.x;
+    const bool fits = used + n <= SEG_CACHE;
+    if (fits)
+      for (int i = threadIdx.x; i < n; i += PCG_THREADS) cache[used + i] = L.seg[q.x + i];
+    if (threadIdx.x == 0) {
+      s_segc[l] = fits ? cache + used : nullptr;
+      s_segb[l] = q.x;
+    }
+    if (fits) used += n;
+  }
+  __syncthreads();
+}
+
+// The shared-memory cache of the segment slices sits after the CTA-local levels
+// in the kernel's dynamic shared memory.
+constexpr size_t MG_DYN_CTA = (sizeof(CtaMg) + 15) / 16 * 16;
+constexpr size_t MG_DYN_BYTES = MG_DYN_CTA + sizeof(int4) * SEG_CACHE;
+
+__device__ __forceinline__ int4* seg_cache_of(unsigned char* dyn) {
+  return reinterpret_cast<int4*>(dyn + MG_DYN_CTA);
+}
+
 struct SolveState {
   int iters = 0;
   int refinements = 0;
@@ -1327,13 +1370,14 @@ struct SolveState {
 // recomputed residual's norm (refinement).  A slot's readers always pass another barrier before the slot
 // is written again.
 template <bool MIXED>
-__device__ void solve_mg(const PcgArgs& A, Shared& sh, CtaMg& sm, SolveState& S) {
+__device__ void solve_mg(const PcgArgs& A, Shared& sh, CtaMg& sm, int4* segc, SolveState& S) {
   const MgArgs& M = A.mg;
   const MgLevel& L0 = M.lv[0];
   float* d = M.d0;
   float* z = L0.x;
   float* r = L0.b;
   if (!build_levels(A, sh)) { S.ok = false; return; }
+  seg_cache_fill(M, segc);
   if (M.nlev > 1 && team_rank() == 0) cta_levels_init(M, sm);
   // ---- start: r = b (cold) or b - A x0 (warm start from the last solve's x),
   // p_old = 0, first red half-sweep of the V-cycle; mixed mode: b as a float pair,
@@ -1535,13 +1579,14 @@ __device__ void solve_mg(const PcgArgs& A, Shared& sh, CtaMg& sm, SolveState& S)
 // RBGS_CHECK sweep pairs and the sweep pairs are capped at max_iter.
 constexpr int RBGS_CHECK = 8;
 
-__device__ __noinline__ void solve_rbgs(const PcgArgs& A, Shared& sh, SolveState& S) {
+__device__ __noinline__ void solve_rbgs(const PcgArgs& A, Shared& sh, int4* segc, SolveState& S) {
   const MgArgs& M = A.mg;
   const MgLevel& L0 = M.lv[0];
   const MgLevel& L1 = M.nlev > 1 ? M.lv[1] : M.lv[0];
   float* z = L0.x;
   float* r = L0.b;
   if (!build_levels(A, sh)) { S.ok = false; return; }
+  seg_cache_fill(M, segc);
   {
     FF bb;
     for_fluid0(A, [&](const SCell& e, unsigned int, int n) {
@@ -1613,13 +1658,17 @@ __device__ __noinline__ void solve_rbgs(const PcgArgs& A, Shared& sh, SolveState
 }
 
 template <bool MIXED>
-__device__ void solve_scene_mg(const PcgArgs& A, Shared& sh, CtaMg& sm) {
+__device__ void solve_scene_mg(const PcgArgs& A, Shared& sh, unsigned char* dyn) {
+  CtaMg& sm = *reinterpret_cast<CtaMg*>(dyn);
+  int4* segc = seg_cache_of(dyn);
+  if (threadIdx.x < MG_MAX_LEVELS) s_segc[threadIdx.x] = nullptr;  // no cache until filled
+  __syncthreads();
   const long long ncells = (long long)A.g.nx * A.g.ny * A.g.nz;
   const bool singular = A.check_singular && ((long long)A.stats->n_fluid == ncells);
   SolveState S;
   if (!singular) {
-    if (!MIXED && A.precond == PRECOND_RBGS) solve_rbgs(A, sh, S);
-    else solve_mg<MIXED>(A, sh, sm, S);
+    if (!MIXED && A.precond == PRECOND_RBGS) solve_rbgs(A, sh, segc, S);
+    else solve_mg<MIXED>(A, sh, sm, segc, S);
   }
   if (team_rank() == 0 && threadIdx.x == 0) {
     int st = 0;
@@ -1639,10 +1688,9 @@ template <bool MIXED>
 __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg_mg(const __grid_constant__ PcgArgs A) {
   __shared__ Shared sh;
   extern __shared__ __align__(16) unsigned char mg_dyn[];
-  CtaMg& sm = *reinterpret_cast<CtaMg*>(mg_dyn);
   team_enter(blockIdx.x, gridDim.x);
   load_tables(A.mg);
-  solve_scene_mg<MIXED>(A, sh, sm);
+  solve_scene_mg<MIXED>(A, sh, mg_dyn);
 }
 
 // Several scenes in one launch: CTA b works on scene block_scene[b], in the team
@@ -1651,11 +1699,10 @@ template <bool MIXED>
 __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg_mg_batch(const __grid_constant__ PcgBatch B) {
   __shared__ Shared sh;
   extern __shared__ __align__(16) unsigned char mg_dyn[];
-  CtaMg& sm = *reinterpret_cast<CtaMg*>(mg_dyn);
   const int s = B.block_scene[blockIdx.x];
   team_enter(blockIdx.x - B.team_first[s], B.team_first[s + 1] - B.team_first[s]);
   load_tables(B.args[s].mg);
-  solve_scene_mg<MIXED>(B.args[s], sh, sm);
+  solve_scene_mg<MIXED>(B.args[s], sh, mg_dyn);
 }
 
 }  // namespace
@@ -1677,18 +1724,18 @@ cudaError_t launch_pcg_mg(const PcgArgs& a, bool mixed, int nblocks, cudaStream_
   void* args[] = {const_cast<PcgArgs*>(&a)};
   if (mixed)
     return cudaLaunchCooperativeKernel((const void*)k_pcg_mg<true>, dim3(nblocks),
-                                       dim3(PCG_THREADS), args, sizeof(CtaMg), s);
+                                       dim3(PCG_THREADS), args, MG_DYN_BYTES, s);
   return cudaLaunchCooperativeKernel((const void*)k_pcg_mg<false>, dim3(nblocks),
-                                     dim3(PCG_THREADS), args, sizeof(CtaMg), s);
+                                     dim3(PCG_THREADS), args, MG_DYN_BYTES, s);
 }
 
 cudaError_t launch_pcg_mg_batch(const PcgBatch& b, bool mixed, int nblocks, cudaStream_t s) {
   void* args[] = {const_cast<PcgBatch*>(&b)};
   if (mixed)
     return cudaLaunchCooperativeKernel((const void*)k_pcg_mg_batch<true>, dim3(nblocks),
-                                       dim3(PCG_THREADS), args, sizeof(CtaMg), s);
+                                       dim3(PCG_THREADS), args, MG_DYN_BYTES, s);
   return cudaLaunchCooperativeKernel((const void*)k_pcg_mg_batch<false>, dim3(nblocks),
-                                     dim3(PCG_THREADS), args, sizeof(CtaMg), s);
+                                     dim3(PCG_THREADS), args, MG_DYN_BYTES, s);
 }
 
 // Opts the kernels in to the dynamic shared memory of the CTA-local levels and
@@ -1698,10 +1745,10 @@ cudaError_t pcg_mg_check_occupancy() {
                         (const void*)k_pcg_mg_batch<false>, (const void*)k_pcg_mg_batch<true>};
   for (const void* f : fns) {
     cudaError_t e =
-        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CtaMg));
+        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MG_DYN_BYTES);
     if (e != cudaSuccess) return e;
     int a = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, f, PCG_THREADS, sizeof(CtaMg));
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, f, PCG_THREADS, MG_DYN_BYTES);
     if (e != cudaSuccess) return e;
     if (a < 1) return cudaErrorInvalidConfiguration;
   }

@@ -23,6 +23,7 @@ __device__ __forceinline__ void team_enter(unsigned int rank, unsigned int size)
   if (threadIdx.x == 0) {
     s_team_rank = rank;
     s_team_size = size;
+    s_bar_gen = 0u;  // grid barriers passed in this launch
   }
   __syncthreads();
 }
