@@ -467,6 +467,12 @@ def test_rbgs_solver_iterates_match_the_oracle(n):
 
 
 def test_rbgs_solver_converges_like_the_oracle():
+    """Run to a relative residual of 1e-4: the sweep counts agree within one check
+    interval (the residual is taken every 8 sweep pairs, and FP32 rounding can move the
+    stopping check by one interval).  With equal counts the pressures agree at the
+    parity bar; with counts one interval apart they differ by what 8 sweep pairs
+    change near the tolerance, up to kappa(A) * 1e-4 ~ 1e-3.  The arithmetic itself
+    is pinned by the fixed-count test above."""
     sc = S.dam_break(32)
     op, fp = matched(32, cg_tol=1e-4, cg_max_iter=20000, preconditioner=F.FLIP_PRECOND_RBGS)
     ref = O.step(op, *sc.arrays())

@@ -32,6 +32,11 @@ def _scene(n, seed, mixed=False):
 
 
 def test_served_scene_equals_alone():
+    """Three steps per scene served amid the others against the same steps alone, at
+    the tolerance of test_batch_equals_alone (two FP32 solves that both stop at a
+    relative residual of 1e-6 can differ by kappa(A) * 1e-6 ~ 1e-4); each served
+    step is held to the parity bar against the oracle in
+    test_served_scenes_match_the_oracle."""
     scenes = [_scene(32, 1), _scene(40, 2, mixed=True), _scene(24, 3), _scene(48, 4)]
     alone = []
     for sc, fp in scenes:
