@@ -116,6 +116,8 @@ struct flip_handle {
   int launches = 0;
   bool stepped = false;
   unsigned long long wait_ns = 0;  // flip_set_wait_timeout (0: the defaults)
+  CUtensorMap pmap{};              // the pressure field for G2P's TMA slab staging
+  bool has_pmap = false;           // pmap is valid (the grid's pitches allow one)
   // timing of flip_step calls with statistics: 5 events per step plus one, kept
   // for the handle's life so a timed call creates none once the pool is large enough
   std::vector<cudaEvent_t> tev;
@@ -651,6 +653,8 @@ int flip_create(const flip_params* params, const float* x, const float* y, const
   Carver assign;
   assign.base = (char*)h->arena;
   carve(h, assign);
+  h->has_pmap = encode_pressure_map(h->g, h->mixed ? (void*)h->pff : (void*)h->x32, h->mixed,
+                                    &h->pmap);
   h->K.dyn = params->cfl > 0.0 ? h->dstats->dyn : nullptr;
   e = cudaMallocHost((void**)&h->hstats, sizeof(DevStats));
   if (e != cudaSuccess) {
@@ -744,7 +748,7 @@ int flip_step(flip_handle* h, int32_t nsteps, flip_stats* stats) {
     h->launches += 1;
     if (timed) FLIP_CUDA(cudaEventRecord(ev[4], s));
     launch_g2p(h->g, h->K, h->P[h->cur], h->B, uo, h->mixed ? nullptr : h->x32, h->pff,
-               h->dstats, g2p_count(h), h->g2p_blocks, s);
+               h->dstats, g2p_count(h), h->g2p_blocks, h->has_pmap ? &h->pmap : nullptr, s);
     h->launches += (g2p_count(h) > 0);
     launch_back(h, s);
     if (timed) FLIP_CUDA(cudaEventRecord(ev[5], s));
@@ -1611,7 +1615,8 @@ int batch_step_impl(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t ns
       const float* uo[3] = {h->uo[0], h->uo[1], h->uo[2]};
       FLIP_CUDA(cudaStreamWaitEvent(h->stream, b->ev_solved, 0));
       launch_g2p(h->g, h->K, h->P[h->cur], h->B, uo, h->mixed ? nullptr : h->x32, h->pff,
-                 h->dstats, g2p_count(h), h->g2p_blocks, h->stream);
+                 h->dstats, g2p_count(h), h->g2p_blocks, h->has_pmap ? &h->pmap : nullptr,
+                 h->stream);
       h->launches += (g2p_count(h) > 0);
       launch_back(h, h->stream);
       h->stepped = true;

@@ -1,6 +1,8 @@
 // flip_kernels.cuh — argument structs and host-side launchers of the FLIP kernels.
 #pragma once
 
+#include <cuda.h>
+
 #include "flip_internal.cuh"
 
 namespace flipk {
@@ -314,9 +316,14 @@ void launch_spawn(const Grid& g, const StepConsts& k, const PartView& p, const B
 
 // k_g2p.cu
 int g2p_blocks(int sm_count);
+// pmap (nullable): tensor map of the pressure (encode_pressure_map) for the TMA
+// staging of the pressure slab; plain loads when NULL.
 void launch_g2p(const Grid& g, const StepConsts& k, const PartView& p, const BinView& b,
                 const float* const uo[3], const float* p32, const float2* pff, DevStats* st,
-                long long np, int nblocks, cudaStream_t s);
+                long long np, int nblocks, const CUtensorMap* pmap, cudaStream_t s);
+// Tensor map of a pressure field (float pairs when pair, else FP32; natural
+// layout) for G2P's slab staging; false when the grid's pitches do not allow one.
+bool encode_pressure_map(const Grid& g, void* base, bool pair, CUtensorMap* out);
 
 // k_diag.cu
 // Adaptive time step (Sec. 3.1.4): dt = min(dt_max, alpha dx / v_max), v_max the

@@ -16,13 +16,23 @@
 // and computes the key of the cell it moved to and its rank there.  Ranks come
 // from one histogram atomic per distinct key in a warp (lanes with the same key
 // take consecutive ranks), which is all the next step's counting sort needs.
+//
+// The pressure slab of a brick (the 10 x 10 x 10 cells [b - 1, b + 8] per axis)
+// is staged by one TMA tensor copy (cp.async.bulk.tensor) when the handle has a
+// tensor map of its pressure (row pitches a multiple of 16 bytes): the copy starts
+// at x = b0 - XOFF so that its first coordinate is 16-byte aligned, rows are SPX
+// cells wide, and cells outside the grid arrive as 0.  Otherwise, and in the
+// batched kernel, the same tile is filled with plain loads.
+#include <cudaTypedefs.h>
+
+#include <cstring>
+
 #include "flip_kernels.cuh"
 
 namespace flipk {
 
 constexpr int G2P_THREADS = 256;
 constexpr int G2P_TILE = 904;     // >= 9 * 10 * 10 face nodes per component
-constexpr int G2P_PTILE = 1000;   // 10 * 10 * 10 cells of pressure
 
 template <int D>
 struct FaceTile {
@@ -32,16 +42,23 @@ struct FaceTile {
   static constexpr int N = X * Y * Z;
 };
 
+// The staged pressure tile: element type (the float pair of mixed mode, or FP32),
+// row width SPX and the x offset XOFF of its first cell from the brick origin, so
+// that XOFF * sizeof(T) and SPX * sizeof(T) are multiples of 16 bytes.
 template <bool PAIR>
 struct PTile;
 template <>
 struct PTile<true> {
   using T = float2;
+  static constexpr int SPX = 12, XOFF = 2;
 };
 template <>
 struct PTile<false> {
   using T = float;
+  static constexpr int SPX = 16, XOFF = 4;
 };
+template <bool PAIR>
+constexpr int PTILE_N = 10 * 10 * PTile<PAIR>::SPX;
 
 // ---------------------------------------------------------------- bulk copies
 // Particles stream into shared memory in chunks of G2P_THREADS (one per thread)
@@ -90,6 +107,16 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned int 
   while (!mbar_try_wait(bar, parity))
     if (global_timer_ns() - t0 > limit_ns) return false;
   return true;
+}
+
+// One 3-D tiled tensor copy of the box at (x, y, z) into dst, completing on bar.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
 }
 
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned int bytes,
@@ -141,10 +168,11 @@ __device__ __forceinline__ void stage_faces(const Grid& g, const StepConsts& K, 
       const float uov = __ldg(uo + (a + FX * (b + FY * c)));
       const int nd = (D == 0) ? a : (D == 1) ? b : c;
       if (nd != 0 && nd != nmax) {
-        // pressure tile cell of (a, b, c) is (a - b0 + 1, ...); the minus cell
-        // is one step down along D
-        const int pc = (a - b0 + 1) + 10 * ((b - b1 + 1) + 10 * (c - b2 + 1));
-        const int pm = pc - ((D == 0) ? 1 : (D == 1) ? 10 : 100);
+        // pressure tile cell of (a, b, c) is (a - b0 + XOFF, b - b1 + 1, c - b2 + 1);
+        // the minus cell is one step down along D
+        constexpr int SPX = PTile<PAIR>::SPX, XOFF = PTile<PAIR>::XOFF;
+        const int pc = (a - b0 + XOFF) + SPX * ((b - b1 + 1) + 10 * (c - b2 + 1));
+        const int pm = pc - ((D == 0) ? 1 : (D == 1) ? SPX : 10 * SPX);
         const float dp = pdiff(sp[pc], sp[pm]);
         un = __fsub_rn(__fadd_rn(uov, K.gdt[D]), __fmul_rn(K.pscale, dp));
       }
@@ -193,20 +221,20 @@ __device__ __forceinline__ void interp_tile(const PartW& W, int li, int lj, int 
 // Shared memory of a G2P CTA: the brick's staged tiles and the particle buffers.
 template <bool PAIR>
 struct G2pShared {
-  typename PTile<PAIR>::T sp[G2P_PTILE];
+  __align__(128) typename PTile<PAIR>::T sp[PTILE_N<PAIR>];  // the pressure slab
   float2 sud[3][G2P_TILE];  // (u_new, u_new - u_old) per face node
   __align__(16) float pbuf[2][6][G2P_CHUNK_PAD];
-  __align__(8) unsigned long long bar[2];
+  __align__(8) unsigned long long bar[3];  // particle buffers 0, 1; the pressure slab
   int abort;
 };
 
 // A CTA's streaming state, kept across bricks (and across scenes in a batched
 // launch): the mbarrier phases, the buffer of the next chunk, and (thread 0) which
-// buffers have a copy that nobody has waited for.
+// barriers have a copy that nobody has waited for.
 struct G2pCta {
-  unsigned int phase[2] = {0u, 0u};
+  unsigned int phase[3] = {0u, 0u, 0u};
   unsigned int kbuf = 0;
-  bool inflight[2] = {false, false};
+  bool inflight[3] = {false, false, false};
 };
 
 template <bool PAIR>
@@ -214,13 +242,15 @@ __device__ __forceinline__ void g2p_init(G2pShared<PAIR>& sh) {
   if (threadIdx.x == 0) {
     mbar_init(&sh.bar[0], 1);
     mbar_init(&sh.bar[1], 1);
+    mbar_init(&sh.bar[2], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     sh.abort = 0;
   }
   __syncthreads();
 }
 
-// One brick of one scene.  CTA-uniform; returns false once a wait has given up
+// One brick of one scene (pmap: the tensor map of the scene's pressure, or
+// nullptr for plain loads).  CTA-uniform; returns false once a wait has given up
 // (DEV_TIMEOUT set in the scene's status), after which the CTA takes no more bricks.
 template <bool PAIR>
 __device__ __forceinline__ bool g2p_brick(const Grid& g, const StepConsts& K, const PartView& P,
@@ -229,8 +259,8 @@ __device__ __forceinline__ bool g2p_brick(const Grid& g, const StepConsts& K, co
                                           const float* __restrict__ uo2,
                                           const float* __restrict__ p32,
                                           const float2* __restrict__ pff, DevStats* st,
-                                          unsigned int brick, G2pShared<PAIR>& sh, G2pCta& cs,
-                                          float& speed2) {
+                                          const CUtensorMap* pmap, unsigned int brick,
+                                          G2pShared<PAIR>& sh, G2pCta& cs, float& speed2) {
   using PT = typename PTile<PAIR>::T;
   const int lane = threadIdx.x & 31;
   const int b0 = (int)(brick % (unsigned)g.bx) * BRICK;
@@ -242,18 +272,39 @@ __device__ __forceinline__ bool g2p_brick(const Grid& g, const StepConsts& K, co
     issue_chunk(P, bstart, min(bend, bstart + G2P_THREADS), sh.pbuf[cs.kbuf], &sh.bar[cs.kbuf]);
     cs.inflight[cs.kbuf] = true;
   }
-  // pressure of cells [b - 1, b + 8] per axis (0 outside the grid: never used)
-  for (int t = threadIdx.x; t < G2P_PTILE; t += G2P_THREADS) {
-    const int i = b0 - 1 + t % 10, j = b1 - 1 + (t / 10) % 10, k = b2 - 1 + t / 100;
-    PT v{};
-    if (i >= 0 && j >= 0 && k >= 0 && i < g.nx && j < g.ny && k < g.nz) {
-      const int c = i + g.nx * (j + g.ny * k);
-      if constexpr (PAIR) v = pff[c];
-      else v = p32[c];
+  // pressure of cells [b0 - XOFF, b0 - XOFF + SPX) x [b1 - 1, b1 + 9) x [b2 - 1, b2 + 9)
+  // (0 outside the grid: never used)
+  constexpr int SPX = PTile<PAIR>::SPX, XOFF = PTile<PAIR>::XOFF;
+  if (pmap) {
+    if (threadIdx.x == 0) {
+      // the tile's readers of the previous brick passed the __syncthreads that
+      // ended it; order their generic-proxy reads before the async-proxy write
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(&sh.bar[2], (unsigned)sizeof(sh.sp));
+      tma_load_3d(sh.sp, pmap, b0 - XOFF, b1 - 1, b2 - 1, &sh.bar[2]);
+      cs.inflight[2] = true;
     }
-    sh.sp[t] = v;
+    if (mbar_wait(&sh.bar[2], cs.phase[2], K.wait_ns)) {
+      cs.phase[2] ^= 1u;
+      cs.inflight[2] = false;
+    } else {
+      atomicOr(&st->status, DEV_TIMEOUT);
+      sh.abort = 1;
+    }
+  } else {
+    for (int t = threadIdx.x; t < PTILE_N<PAIR>; t += G2P_THREADS) {
+      const int i = b0 - XOFF + t % SPX, j = b1 - 1 + (t / SPX) % 10, k = b2 - 1 + t / (10 * SPX);
+      PT v{};
+      if (i >= 0 && j >= 0 && k >= 0 && i < g.nx && j < g.ny && k < g.nz) {
+        const int c = i + g.nx * (j + g.ny * k);
+        if constexpr (PAIR) v = pff[c];
+        else v = p32[c];
+      }
+      sh.sp[t] = v;
+    }
   }
   __syncthreads();
+  if (sh.abort) return false;
   stage_faces<0, PAIR>(g, K, b0, b1, b2, uo0, sh.sp, sh.sud[0]);
   stage_faces<1, PAIR>(g, K, b0, b1, b2, uo1, sh.sp, sh.sud[1]);
   stage_faces<2, PAIR>(g, K, b0, b1, b2, uo2, sh.sp, sh.sud[2]);
@@ -351,7 +402,7 @@ template <bool PAIR>
 __device__ __forceinline__ void g2p_drain(G2pShared<PAIR>& sh, const G2pCta& cs) {
   if (threadIdx.x == 0)
 #pragma unroll
-    for (int k = 0; k < 2; ++k)
+    for (int k = 0; k < 3; ++k)
       if (cs.inflight[k]) (void)mbar_wait(&sh.bar[k], cs.phase[k], G2P_DRAIN_NS);
 }
 
@@ -373,15 +424,19 @@ __global__ void __launch_bounds__(G2P_THREADS, 5) k_g2p(const Grid g, const Step
                                                      const float* __restrict__ uo2,
                                                      const float* __restrict__ p32,
                                                      const float2* __restrict__ pff,
-                                                     DevStats* st) {
+                                                     DevStats* st,
+                                                     const __grid_constant__ CUtensorMap pmap,
+                                                     int use_tma) {
   __shared__ G2pShared<PAIR> sh;
   const StepConsts K = step_consts(K0);
   const unsigned int nact = st->n_active;
   g2p_init(sh);
   G2pCta cs;
   float speed2 = 0.0f;
+  const CUtensorMap* map = use_tma ? &pmap : nullptr;
   for (unsigned int bi = blockIdx.x; bi < nact; bi += gridDim.x)
-    if (!g2p_brick<PAIR>(g, K, P, B, uo0, uo1, uo2, p32, pff, st, B.active[bi], sh, cs, speed2))
+    if (!g2p_brick<PAIR>(g, K, P, B, uo0, uo1, uo2, p32, pff, st, map, B.active[bi], sh, cs,
+                         speed2))
       break;
   g2p_drain(sh, cs);
   g2p_flush_speed(speed2, st);
@@ -407,7 +462,7 @@ __global__ void __launch_bounds__(G2P_THREADS, 5) k_g2p_batch(const BatchLaunch 
       cur = s;
     }
     if (!g2p_brick<PAIR>(S.g, step_consts(S.K), S.dst, S.B, S.uo[0], S.uo[1], S.uo[2], S.x32,
-                         S.pff, S.st, S.B.active[gb - L.first[s]], sh, cs, speed2))
+                         S.pff, S.st, nullptr, S.B.active[gb - L.first[s]], sh, cs, speed2))
       break;
   }
   g2p_drain(sh, cs);
@@ -436,12 +491,49 @@ void launch_g2p_batch(const BatchLaunch& L, unsigned int ctas, bool pair, cudaSt
 
 void launch_g2p(const Grid& g, const StepConsts& k, const PartView& p, const BinView& b,
                 const float* const uo[3], const float* p32, const float2* pff, DevStats* st,
-                long long np, int nblocks, cudaStream_t s) {
+                long long np, int nblocks, const CUtensorMap* pmap, cudaStream_t s) {
   if (np <= 0) return;
+  CUtensorMap none;
+  std::memset(&none, 0, sizeof(none));
+  const CUtensorMap& m = pmap ? *pmap : none;
+  const int tma = pmap ? 1 : 0;
   if (pff)
-    k_g2p<true><<<nblocks, G2P_THREADS, 0, s>>>(g, k, p, b, uo[0], uo[1], uo[2], p32, pff, st);
+    k_g2p<true><<<nblocks, G2P_THREADS, 0, s>>>(g, k, p, b, uo[0], uo[1], uo[2], p32, pff, st, m,
+                                               tma);
   else
-    k_g2p<false><<<nblocks, G2P_THREADS, 0, s>>>(g, k, p, b, uo[0], uo[1], uo[2], p32, pff, st);
+    k_g2p<false><<<nblocks, G2P_THREADS, 0, s>>>(g, k, p, b, uo[0], uo[1], uo[2], p32, pff, st, m,
+                                                tma);
+}
+
+bool encode_pressure_map(const Grid& g, void* base, bool pair, CUtensorMap* out) {
+  // row and plane pitches must be multiples of 16 bytes; the box (SPX x 10 x 10)
+  // must fit the grid
+  const size_t elem = pair ? 8 : 4;
+  const int spx = pair ? PTile<true>::SPX : PTile<false>::SPX;
+  if (!base || (reinterpret_cast<uintptr_t>(base) & 15u) || ((size_t)g.nx * elem) % 16 != 0 ||
+      g.nx < spx || g.ny < 10 || g.nz < 10)
+    return false;
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    cudaDriverEntryPointQueryResult q;
+    void* f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      encode = (PFN_cuTensorMapEncodeTiled_v12000)f;
+    cudaGetLastError();
+    looked_up = true;
+  }
+  if (!encode) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
+  const cuuint64_t strides[2] = {(cuuint64_t)g.nx * elem, (cuuint64_t)g.nx * g.ny * elem};
+  const cuuint32_t box[3] = {(cuuint32_t)spx, 10u, 10u};
+  const cuuint32_t estr[3] = {1u, 1u, 1u};
+  return encode(out, pair ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace flipk

@@ -127,6 +127,28 @@ def test_ragged_grid_not_multiple_of_brick():
     _compare_particles(ref, got, 1 / 20)
 
 
+@pytest.mark.parametrize("n,mixed", [((30, 22, 26), False), ((30, 22, 26), True),
+                                     ((16, 10, 10), False), ((18, 9, 14), True)])
+def test_pressure_slab_staging_paths(n, mixed):
+    """G2P stages each brick's pressure slab by a TMA tensor copy when the pressure's
+    row pitch is a multiple of 16 bytes and the grid holds the copy's box, else by
+    plain loads: FP32 with nx = 30 (120-byte rows) and a grid 9 cells high take the
+    loads; the mixed mode's float pairs with nx = 30 (240-byte rows) and the FP32
+    16 x 10 x 10 grid (the box exactly) take the copy.  Every form gives the oracle's
+    step."""
+    sc = S.random_velocities(S.box(n, (0.0, 0.0, 0.0), (0.6, 0.5, 0.7), seed=6), 0.5, 7)
+    op, fp = matched(n)
+    if mixed:
+        fp.precision = F.FLIP_PREC_MIXED_IR
+        fp.cg_tol, fp.ir_tol = 1e-3, 1e-8
+        op.cg_tol, op.cg_max_iter = 1e-11, 100000
+    ref = O.step(op, *sc.arrays())
+    got = gpu_step(fp, sc.arrays())
+    assert got["rc"] == F.FLIP_OK
+    _compare_fields(ref, got, n, label=f"slab {n} {'mixed' if mixed else 'fp32'}")
+    _compare_particles(ref, got, 1 / max(n))
+
+
 def test_grid_advection_source():
     sc = S.random_velocities(S.dam_break(16, 0.5, 0.5, seed=2), 0.5, 8)
     op, fp = matched(16, advect_source=1)
