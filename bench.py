@@ -587,7 +587,7 @@ def run_batch(args):
 
 
 def serve_workload(srv_scenes, max_edge, rate, requests, budget_gb, max_batch, ws=1, rank=0,
-                   seed=0, overlap=True):
+                   seed=0, overlap=True, fused=True):
     """Step requests arriving as a Poisson process (mean `rate` per second, uniform
     scene choice) over `srv_scenes` resident dam-break scenes with edges log-uniform
     in [48, max_edge] and fluid fraction 0.2-0.5 (mixed precision), served by the
@@ -607,6 +607,7 @@ def serve_workload(srv_scenes, max_edge, rate, requests, budget_gb, max_batch, w
     t_gen = time.perf_counter()
     srv = F.Server(int(budget_gb * (1 << 30)), max_batch)
     srv.set_overlap(overlap)
+    srv.set_fused(fused)
     sid, npart = {}, [0] * len(specs)
     for k, (n, f) in enumerate(specs):
         if k not in mine:
@@ -682,7 +683,7 @@ def run_serve(args):
     clocks.start()
     part = serve_workload(args.serve, args.serve_max_edge, args.rate, args.requests,
                           args.budget_gb, args.max_batch, ws, rank,
-                          overlap=not args.serve_serial)
+                          overlap=not args.serve_serial, fused=not args.serve_per_scene)
     ck = clocks.stop()
     parts = [part]
     if ws > 1:
@@ -705,7 +706,8 @@ def run_serve(args):
                                      "per GPU, no data-path collective"},
            "latency_ms": sv["latency_ms"], "mean_batch": sv["mean_batch"],
            "failed": sv["failed"], "clocks": ck,
-           "batches": "one at a time" if args.serve_serial else "overlapped"}
+           "batches": "one at a time" if args.serve_serial else "overlapped",
+           "batch_form": "per-scene launches" if args.serve_per_scene else "fused"}
     print(json.dumps(out), flush=True)
 
 
@@ -727,6 +729,8 @@ def main():
     ap.add_argument("--serve-max-edge", type=int, default=192)
     ap.add_argument("--serve-serial", action="store_true",
                     help="serving: one batch at a time instead of overlapped batches")
+    ap.add_argument("--serve-per-scene", action="store_true",
+                    help="serving: per-scene launches inside each batch instead of fused ones")
     ap.add_argument("--rate", type=float, default=2000.0, help="request arrivals per second")
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--budget-gb", type=float, default=180.0)

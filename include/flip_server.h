@@ -73,6 +73,12 @@ int flip_server_drain(flip_server* s);
  * one batch at a time; the next is formed when the previous one has completed. */
 int flip_server_set_overlap(flip_server* s, int32_t enable);
 
+/* The batches' form (flip_batch_set_fused): 1 (default) fused, one launch per step
+ * kernel for all the batch's scenes, which then complete together; 0 per-scene
+ * launches on the scenes' streams, each scene completing as its own G2P ends.  Set
+ * it while no request is queued. */
+int flip_server_set_fused(flip_server* s, int32_t enable);
+
 /* Seconds since the server was created. */
 double flip_server_now(const flip_server* s);
 

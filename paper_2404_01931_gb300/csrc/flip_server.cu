@@ -463,6 +463,14 @@ int flip_server_drain(flip_server* s) {
 
 double flip_server_now(const flip_server* s) { return s ? s->now() : 0.0; }
 
+int flip_server_set_fused(flip_server* s, int32_t enable) {
+  if (!s) return FLIP_E_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);  // the launcher holds mu while it forms a batch
+  for (int k = 0; k < kSlots; ++k)
+    if (int rc = flip_batch_set_fused(s->slot[k], enable)) return rc;
+  return FLIP_OK;
+}
+
 int flip_server_set_overlap(flip_server* s, int32_t enable) {
   if (!s) return FLIP_E_ARG;
   std::lock_guard<std::mutex> lk(s->mu);

@@ -176,6 +176,7 @@ def lib():
         L.flip_surface_destroy.restype = None
         L.flip_surface_case_table.argtypes = [vp, vp]
         L.flip_server_set_overlap.argtypes = [vp, i32]
+        L.flip_server_set_fused.argtypes = [vp, i32]
         L.flip_batch_set_fused.argtypes = [vp, i32]
         L.flip_step_times.argtypes = [vp, vp, i32]
         L.flip_step_times.restype = i32
@@ -530,6 +531,10 @@ class Server:
 
     def drain(self):
         _check(lib().flip_server_drain(self.s))
+
+    def set_fused(self, enable: bool):
+        """Fused batches (default) or per-scene launches inside each batch."""
+        _check(lib().flip_server_set_fused(self.s, int(bool(enable))))
 
     def set_overlap(self, enable: bool):
         """Overlapped batches (default) or one batch at a time."""
