@@ -282,3 +282,36 @@ def test_fused_and_per_scene_forms_agree():
         for a, c in zip(base, out[key]):
             for x, y in zip(a, c):
                 assert rel_l2(y, x, 1e-3) <= 1e-4, key
+
+
+def test_fused_batch_edge_scenes():
+    """The fused form over degenerate and many scenes: an empty scene, a one-particle
+    scene, grids smaller than a brick and not a multiple of it, and 300 small scenes in
+    one call (the binary search over the CTA ranges and the flat brick list).  Every
+    non-empty scene matches the oracle's step; the empty one stays empty."""
+    specs = [S.dam_break(16), S.box((4, 5, 6), (0.0, 0.0, 0.0), (0.5, 0.6, 1.0), seed=2),
+             S.box((9, 17, 11), (0.1, 0.0, 0.2), (0.8, 0.4, 0.9), seed=3)]
+    one = S.box(8, (0.0, 0.0, 0.0), (0.125, 0.125, 0.125), density=1, seed=4)
+    assert one.n_particles == 1
+    specs.append(one)
+    specs += [S.dam_break(8, 0.5, 0.5, seed=10 + k) for k in range(296)]
+    empty = np.zeros(0, np.float32)
+    sims = [F.Simulation(matched(8)[1], empty, empty, empty, empty, empty, empty)]
+    sims += [F.Simulation(matched(sc.n)[1], *sc.arrays()) for sc in specs]
+    try:
+        with F.Batch(len(sims)) as b:
+            rc, st = b.step(sims, 1, stats=True)
+            assert rc == F.FLIP_OK
+        assert st[0].n_particles == 0 and st[0].n_fluid_cells == 0
+        for k in (1, 2, 3, 4, 5, 150, 299):
+            sc, sim = specs[k - 1], sims[k]
+            op = matched(sc.n)[0]
+            ref = O.step(op, *sc.arrays())
+            x, y, z, u, v, w = sim.particles()
+            err = np.abs(np.stack([x, y, z]).astype(np.float64)
+                         - np.stack([ref.x, ref.y, ref.z])).max() * max(sc.n)
+            assert err <= 1e-4, (k, err)
+            assert rel_l2(sim.read(F.PRESSURE_F64), ref.pressure) <= 1e-5, k
+    finally:
+        for s_ in sims:
+            s_.close()
