@@ -489,10 +489,13 @@ def run_batch(args):
     npart = sum(sc.n_particles for sc in scenes)
     stream = torch.cuda.Stream()  # the batch's launches run here; it joins every scene
     b = F.Batch(len(sims), stream=stream.cuda_stream)
-    # warm-up, then the autotuner picks the solve-team split on real steps
+    b.set_fused(not args.batch_per_scene)
+    # warm-up, then the autotuner picks the solve-team split and the step's form
+    # (fused or per-scene launches, stream-ordered or graph-replayed) on real steps
     if args.warmup:
         b.step(sims, args.warmup)
     exponent = b.autotune(sims, 1) if args.autotune else 1.0
+    form = b.form()
 
     def timed(k):
         torch.cuda.synchronize()
@@ -508,38 +511,46 @@ def run_batch(args):
             dist.barrier()
         return rc_, max_over_ranks(e0.elapsed_time(e1), ws)
 
+    def form_name(fused, graphs):
+        return ("fused" if fused else "per-scene launches") + (", graph replay" if graphs else "")
+
+    ksteps = args.steps - args.steps % 2  # graph replays run pairs of steps
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    rc, ms = timed(args.steps)
+    rc, ms = timed(ksteps)
     ck = clocks.stop()
-    # stage times and iteration counts from one more step with statistics (untimed)
+    units = sum_over_ranks(npart * ksteps, ws)
+    # the other forms on the same scenes (each warmed by a 2-step call)
+    forms = {}
+    for fused, graphs in ((True, False), (True, True), (False, False), (False, True)):
+        if (fused, graphs) == form:
+            continue
+        b.set_fused(fused)
+        b.set_graphs(graphs)
+        b.step(sims, 2)
+        _, t = timed(ksteps)
+        forms[form_name(fused, graphs)] = {"ms_per_step": t / ksteps, "value": units / (t / 1e3)}
+    # stage times (the fused form's batch-wide stages) and iteration counts from one
+    # more step with statistics (untimed)
+    b.set_graphs(form[1])
+    b.set_fused(True)
     rc_st, st = b.step(sims, 1, stats=True)
+    b.set_fused(form[0])
     rc = rc or rc_st
     nfl = sum(x.n_fluid_cells for x in st)
     stage_ms = {"bin": st[0].ms_bin, "p2g": st[0].ms_p2g, "divergence": st[0].ms_divergence,
                 "pcg": st[0].ms_pcg, "g2p": st[0].ms_g2p}
-    launches_per_step = st[0].kernel_launches + sum(x.kernel_launches for x in st[1:])
-    # the same scenes: graph replay of the fused step, then per-scene launches
-    b.set_graphs(True)
-    b.step(sims, 2)
-    _, ms_graph = timed(args.steps - args.steps % 2)
-    graph_on = b.graph_active()
-    b.set_graphs(False)
-    b.set_fused(False)
-    b.step(sims, 1)
-    _, ms_unfused = timed(args.steps)
-    b.set_fused(True)
+    fused_launches = st[0].kernel_launches + sum(x.kernel_launches for x in st[1:])
     edges = sorted({sc.n[0] for sc in every})
     # the same scenes stepped one at a time through flip_step (the plain per-scene form)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for sim in sims:
-        sim.step(args.steps)
+        sim.step(ksteps)
         sim.sync()
-    seq_value = job_rate(npart * args.steps, time.perf_counter() - t0, ws)
-    units = sum_over_ranks(npart * args.steps, ws)
+    seq_value = job_rate(npart * ksteps, time.perf_counter() - t0, ws)
     rc = int(max_over_ranks(rc, ws))
     if rank != 0:
         b.close()
@@ -548,10 +559,15 @@ def run_batch(args):
         return
     peak, peak_kind = read_peaks()
     npart_all = sum(sc.n_particles for sc in every)
-    ksteps_graph = args.steps - args.steps % 2
+    # kernels per step of the timed form.  Fused: the statistics step's count minus its
+    # one statistics kernel per scene (7 stage launches, the solves, one G2P since all
+    # scenes share a precision).  Per-scene: 7 per scene (2 scans, scatter, P2G,
+    # normalisation, divergence, G2P) plus the same solves.
+    solves = fused_launches - len(sims) - 7 - 1
+    launches_per_step = (fused_launches - len(sims)) if form[0] else 7 * len(sims) + solves
     out = {"metric": "FLIP particle-steps/s", "value": units / (ms / 1e3),
-           "unit": "particle-steps/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "unit": "particle-steps/s", "n_gpus": ws, "steps": ksteps, "warmup": args.warmup,
+           "ms_per_step": ms / ksteps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": f"batch of {len(every)} dam-break scenes, edges {edges}, "
                                   "fluid fraction 0.2-0.5 by seed", "particles": npart_all,
@@ -559,8 +575,8 @@ def run_batch(args):
                       "precision": ("mixed: FP32 CG, float-pair solution and residual to 1e-8"
                                     if mixed else "FP32 (float-pair dot products)"),
                       "preconditioner": "multigrid",
-                      "form": "fused: one launch per step kernel for all scenes, one batched "
-                              "cooperative solve launch",
+                      "form": form_name(*form) + (" (chosen by the autotuner)" if args.autotune
+                                                  else ""),
                       "parallelism": f"scenes sharded over {ws} GPU(s) by the host-side router "
                                      "(longest first to the least-loaded rank), one batch "
                                      "per GPU, no data-path collective"},
@@ -568,15 +584,11 @@ def run_batch(args):
            "cg_iterations_per_scene_step": sum(x.cg_iterations for x in st) / len(st),
            "stages_ms_per_step": stage_ms,
            "stage_roofline": batch_stage_roofline(scenes, nfl, stage_ms, 1, peak),
+           "stages_form": "fused (one statistics step)",
            "max_rel_residual": max(x.cg_rel_residual for x in st), "status": rc,
-           "gpu_launches": launches_per_step * args.steps, "launches_per_step": launches_per_step,
+           "gpu_launches": launches_per_step * ksteps, "launches_per_step": launches_per_step,
            "clocks": ck,
-           "graph_replay": {"value": units / args.steps * ksteps_graph / (ms_graph / 1e3),
-                            "ms_per_step": ms_graph / ksteps_graph, "graph_active": graph_on},
-           "per_scene_launches": {"value": units / (ms_unfused / 1e3),
-                                  "ms_per_step": ms_unfused / args.steps,
-                                  "what": "the same batch with every scene's step kernels "
-                                          "launched on its own stream"},
+           "other_forms": forms,
            "per_scene_sequential": {"value": seq_value, "unit": "particle-steps/s",
                                     "what": "the same scenes, one flip_step call per scene "
                                             "after another (host-timed, synchronised)"}}
@@ -747,6 +759,8 @@ def main():
                          "red-black Gauss-Seidel iterations (the paper's GPU solver; FP32)")
     ap.add_argument("--mg-smooth", type=int, default=2,
                     help="multigrid red-black sweep pairs before and after the correction")
+    ap.add_argument("--batch-per-scene", action="store_true",
+                    help="batch mode: time the per-scene-launch form (the fused form beside it)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="batch mode: keep the default solve-team split")
     ap.add_argument("--no-surface", dest="surface", action="store_false",

@@ -1117,6 +1117,7 @@ int batch_graph_steps(flip_batch* b, flip_handle* const* hs, int n, int pairs,
   const cudaStream_t bs = b->stream;
   std::vector<unsigned long long> key;
   key.push_back((unsigned long long)n);
+  key.push_back(b->fused ? 1ull : 0ull);  // the form the graph captured
   for (int s = 0; s < n; ++s) {
     key.push_back((unsigned long long)(uintptr_t)hs[s]);
     key.push_back((unsigned long long)hs[s]->serial);
@@ -1352,7 +1353,59 @@ int flip_batch_autotune(flip_batch* b, flip_handle* const* hs, int32_t n,
   }
   b->team_exponent = best;
   if (exponent) *exponent = best;
+  // Then the step's form: fused or per-scene launches, each stream-ordered or
+  // replayed as CUDA graphs, timed over 2 * steps_per_candidate untimed steps with
+  // events on the batch stream (the call joins every scene stream at its end),
+  // after one 2-step call that warms the form (and captures its graph).
+  struct Form {
+    bool fused, graphs;
+  };
+  static const Form forms[4] = {{true, false}, {true, true}, {false, false}, {false, true}};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  FLIP_CUDA(cudaEventCreate(&e0));
+  FLIP_CUDA(cudaEventCreate(&e1));
+  Form bf{b->fused, b->graphs};
+  float bf_ms = -1.0f;
+  int rc = FLIP_OK;
+  for (const Form& f : forms) {
+    b->fused = f.fused;
+    b->graphs = f.graphs;
+    rc = flip_batch_step(b, hs, n, 2, nullptr);
+    cudaError_t e = rc == FLIP_OK ? cudaEventRecord(e0, b->stream) : cudaSuccess;
+    if (rc == FLIP_OK && e == cudaSuccess) rc = flip_batch_step(b, hs, n, 2 * steps_per_candidate, nullptr);
+    if (rc == FLIP_OK && e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+    if (rc == FLIP_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (rc == FLIP_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (rc == FLIP_OK && e != cudaSuccess) rc = cuda_fail(e, "flip_batch_autotune timing");
+    if (rc != FLIP_OK) break;
+    if (bf_ms < 0.0f || ms < bf_ms) {
+      bf = f;
+      bf_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->fused = bf.fused;
+  b->graphs = bf.graphs;
+  if (rc != FLIP_OK) return rc;
+  // the device-side conditions of the untimed calls
+  for (int s = 0; s < n; ++s) {
+    const int r2 = flip_sync(hs[s]);
+    if (r2 == FLIP_E_NOT_CONVERGED || r2 == FLIP_E_CAPACITY) {
+      if (first_warning == FLIP_OK) first_warning = r2;
+    } else if (r2 != FLIP_OK) {
+      return r2;
+    }
+  }
   return first_warning;
+}
+
+int flip_batch_get_form(const flip_batch* b, int32_t* fused, int32_t* graphs) {
+  if (!b) return fail(FLIP_E_ARG, "batch is NULL");
+  if (fused) *fused = b->fused ? 1 : 0;
+  if (graphs) *graphs = b->graphs ? 1 : 0;
+  return FLIP_OK;
 }
 
 void flip_batch_destroy(flip_batch* b) {

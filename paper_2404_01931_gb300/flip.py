@@ -178,6 +178,7 @@ def lib():
         L.flip_server_set_overlap.argtypes = [vp, i32]
         L.flip_server_set_fused.argtypes = [vp, i32]
         L.flip_batch_set_fused.argtypes = [vp, i32]
+        L.flip_batch_get_form.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
         L.flip_step_times.argtypes = [vp, vp, i32]
         L.flip_step_times.restype = i32
         L.flip_set_wait_timeout.argtypes = [vp, C.c_uint64]
@@ -465,6 +466,12 @@ class Batch:
     def set_fused(self, enable: bool):
         """One launch per step kernel across all scenes (default) or per-scene launches."""
         _check(lib().flip_batch_set_fused(self.b, int(bool(enable))))
+
+    def form(self):
+        """(fused, graphs): the form the batch's steps take."""
+        f, g = C.c_int32(0), C.c_int32(0)
+        _check(lib().flip_batch_get_form(self.b, C.byref(f), C.byref(g)))
+        return bool(f.value), bool(g.value)
 
     def graph_active(self) -> bool:
         return bool(lib().flip_batch_graph_active(self.b))
