@@ -150,20 +150,22 @@ def test_batch_with_adaptive_step_and_reseeding():
 
 
 def test_autotune_picks_a_candidate_and_keeps_results():
-    """The autotuner advances the scenes by real steps and leaves a split in force;
-    the scenes then step as they would with any split (a split changes only the
-    order of floating-point sums)."""
+    """The autotuner advances the scenes by real steps (7 for the split, 4 x (2 + 2)
+    for the forms) and leaves a split and a form in force; the scenes then step as
+    they would with any split and form (these change only the order of
+    floating-point sums)."""
     mix = _mix()[:4]
     sims = [F.Simulation(fp, *sc.arrays()) for n, sc, op, fp in mix]
     ref = []
     for n, sc, op, fp in mix:
         with F.Simulation(fp, *sc.arrays()) as sim:
-            sim.step(9)
+            sim.step(7 + 4 * (2 + 2) + 2)
             ref.append(sim.read(F.PRESSURE_F64))
     try:
         with F.Batch(len(sims)) as b:
             a = b.autotune(sims, 1)
             assert a in (0.5, 0.75, 1.0, 1.25, 1.5, 2.0, 2.5)
+            assert b.form() in ((True, False), (True, True), (False, False), (False, True))
             rc, st = b.step(sims, 2, stats=True)
             assert rc == F.FLIP_OK
             for sim, p in zip(sims, ref):
