@@ -359,16 +359,18 @@ int flip_batch_graph_active(const flip_batch* b);
  * its particle count raised to `exponent` (default 1; in [0, 3]). */
 int flip_batch_set_team_exponent(flip_batch* b, double exponent);
 
-/* Autotuner of that split and of the step's form: for each exponent in {0.5,
+/* Autotuner of that split and of the step's form.  For each exponent in {0.5,
  * 0.75, 1, 1.25, 1.5, 2, 2.5} it advances the scenes by steps_per_candidate real
  * steps through flip_batch_step, timing the batched solves with CUDA events, and
  * keeps the exponent whose solves took least time (written to *exponent,
  * nullable).  Then, with that split, it times the four forms of the step -- fused
  * or per-scene launches, each stream-ordered or replayed as CUDA graphs -- over
  * 2 * steps_per_candidate steps each (after a 2-step call that warms the form) and
- * keeps the fastest (flip_batch_get_form tells which).  The scenes advance by
- * 7 * steps_per_candidate + 4 * (2 + 2 * steps_per_candidate) steps in all.
- * Returns the first error, else the first warning, else FLIP_OK. */
+ * keeps the fastest (flip_batch_get_form tells which).  Since the scenes evolve
+ * while they are timed, every candidate is timed twice, in forward then reverse
+ * order, and the two times added.  The scenes advance by 14 * steps_per_candidate
+ * + 8 * (2 + 2 * steps_per_candidate) steps in all.  Returns the first error, else
+ * the first warning, else FLIP_OK. */
 int flip_batch_autotune(flip_batch* b, flip_handle* const* hs, int32_t n,
                         int32_t steps_per_candidate, double* exponent);
 

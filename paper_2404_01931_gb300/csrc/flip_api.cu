@@ -1329,28 +1329,33 @@ int flip_batch_autotune(flip_batch* b, flip_handle* const* hs, int32_t n,
                         int32_t steps_per_candidate, double* exponent) {
   if (!b) return fail(FLIP_E_ARG, "batch is NULL");
   if (steps_per_candidate < 1) return fail(FLIP_E_ARG, "steps_per_candidate must be >= 1");
+  // The scenes evolve while they are timed (a spreading fluid covers more cells), so
+  // each candidate is timed twice, in the order c1..cK then cK..c1, and the two
+  // times are added: a cost that drifts linearly with the step cancels out of the
+  // comparison.
   static const double cand[] = {0.5, 0.75, 1.0, 1.25, 1.5, 2.0, 2.5};
+  constexpr int NC = 7;
   std::vector<flip_stats> st((size_t)std::max(n, 1));
-  double best = b->team_exponent;
-  float best_ms = 0.0f;
-  bool have = false;
+  const double keep = b->team_exponent;
+  double sum_ms[NC] = {};
   int first_warning = FLIP_OK;
-  for (double a : cand) {
-    b->team_exponent = a;
-    const int rc = flip_batch_step(b, hs, n, steps_per_candidate, st.data());
-    if (rc == FLIP_E_NOT_CONVERGED || rc == FLIP_E_CAPACITY) {
-      if (first_warning == FLIP_OK) first_warning = rc;
-    } else if (rc != FLIP_OK) {
-      b->team_exponent = best;
-      return rc;
+  for (int pass = 0; pass < 2; ++pass)
+    for (int q = 0; q < NC; ++q) {
+      const int c = pass == 0 ? q : NC - 1 - q;
+      b->team_exponent = cand[c];
+      const int rc = flip_batch_step(b, hs, n, steps_per_candidate, st.data());
+      if (rc == FLIP_E_NOT_CONVERGED || rc == FLIP_E_CAPACITY) {
+        if (first_warning == FLIP_OK) first_warning = rc;
+      } else if (rc != FLIP_OK) {
+        b->team_exponent = keep;
+        return rc;
+      }
+      sum_ms[c] += n > 0 ? st[0].ms_pcg : 0.0;
     }
-    const float ms = n > 0 ? (float)st[0].ms_pcg : 0.0f;
-    if (!have || ms < best_ms) {
-      best = a;
-      best_ms = ms;
-      have = true;
-    }
-  }
+  int bc = 0;
+  for (int c = 1; c < NC; ++c)
+    if (sum_ms[c] < sum_ms[bc]) bc = c;
+  const double best = cand[bc];
   b->team_exponent = best;
   if (exponent) *exponent = best;
   // Then the step's form: fused or per-scene launches, each stream-ordered or
@@ -1364,10 +1369,12 @@ int flip_batch_autotune(flip_batch* b, flip_handle* const* hs, int32_t n,
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   FLIP_CUDA(cudaEventCreate(&e0));
   FLIP_CUDA(cudaEventCreate(&e1));
-  Form bf{b->fused, b->graphs};
-  float bf_ms = -1.0f;
+  const Form keep_form{b->fused, b->graphs};
+  float form_ms[4] = {0.0f, 0.0f, 0.0f, 0.0f};
   int rc = FLIP_OK;
-  for (const Form& f : forms) {
+  for (int t = 0; t < 8 && rc == FLIP_OK; ++t) {  // forms 0..3 then 3..0, times added
+    const int fi = t < 4 ? t : 7 - t;
+    const Form& f = forms[fi];
     b->fused = f.fused;
     b->graphs = f.graphs;
     rc = flip_batch_step(b, hs, n, 2, nullptr);
@@ -1378,17 +1385,20 @@ int flip_batch_autotune(flip_batch* b, flip_handle* const* hs, int32_t n,
     float ms = 0.0f;
     if (rc == FLIP_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
     if (rc == FLIP_OK && e != cudaSuccess) rc = cuda_fail(e, "flip_batch_autotune timing");
-    if (rc != FLIP_OK) break;
-    if (bf_ms < 0.0f || ms < bf_ms) {
-      bf = f;
-      bf_ms = ms;
-    }
+    if (rc == FLIP_OK) form_ms[fi] += ms;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  b->fused = bf.fused;
-  b->graphs = bf.graphs;
-  if (rc != FLIP_OK) return rc;
+  if (rc != FLIP_OK) {
+    b->fused = keep_form.fused;
+    b->graphs = keep_form.graphs;
+    return rc;
+  }
+  int bf = 0;
+  for (int fi = 1; fi < 4; ++fi)
+    if (form_ms[fi] < form_ms[bf]) bf = fi;
+  b->fused = forms[bf].fused;
+  b->graphs = forms[bf].graphs;
   // the device-side conditions of the untimed calls
   for (int s = 0; s < n; ++s) {
     const int r2 = flip_sync(hs[s]);
