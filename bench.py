@@ -489,7 +489,7 @@ def run_batch(args):
     npart = sum(sc.n_particles for sc in scenes)
     stream = torch.cuda.Stream()  # the batch's launches run here; it joins every scene
     b = F.Batch(len(sims), stream=stream.cuda_stream)
-    b.set_fused(not args.batch_per_scene)
+    b.set_fused(args.batch_fused)
     # warm-up, then the autotuner picks the solve-team split and the step's form
     # (fused or per-scene launches, stream-ordered or graph-replayed) on real steps
     if args.warmup:
@@ -613,7 +613,7 @@ def run_batch(args):
 
 
 def serve_workload(srv_scenes, max_edge, rate, requests, budget_gb, max_batch, ws=1, rank=0,
-                   seed=0, overlap=True, fused=True):
+                   seed=0, overlap=True, fused=False):
     """Step requests arriving as a Poisson process (mean `rate` per second, uniform
     scene choice) over `srv_scenes` resident dam-break scenes with edges log-uniform
     in [48, max_edge] and fluid fraction 0.2-0.5 (mixed precision), served by the
@@ -709,7 +709,7 @@ def run_serve(args):
     clocks.start()
     part = serve_workload(args.serve, args.serve_max_edge, args.rate, args.requests,
                           args.budget_gb, args.max_batch, ws, rank,
-                          overlap=not args.serve_serial, fused=not args.serve_per_scene)
+                          overlap=not args.serve_serial, fused=args.serve_fused)
     ck = clocks.stop()
     parts = [part]
     if ws > 1:
@@ -733,7 +733,7 @@ def run_serve(args):
            "latency_ms": sv["latency_ms"], "mean_batch": sv["mean_batch"],
            "failed": sv["failed"], "clocks": ck,
            "batches": "one at a time" if args.serve_serial else "overlapped",
-           "batch_form": "per-scene launches" if args.serve_per_scene else "fused"}
+           "batch_form": "fused" if args.serve_fused else "per-scene launches"}
     print(json.dumps(out), flush=True)
 
 
@@ -755,8 +755,8 @@ def main():
     ap.add_argument("--serve-max-edge", type=int, default=192)
     ap.add_argument("--serve-serial", action="store_true",
                     help="serving: one batch at a time instead of overlapped batches")
-    ap.add_argument("--serve-per-scene", action="store_true",
-                    help="serving: per-scene launches inside each batch instead of fused ones")
+    ap.add_argument("--serve-fused", action="store_true",
+                    help="serving: fused batches instead of per-scene launches inside each")
     ap.add_argument("--rate", type=float, default=2000.0, help="request arrivals per second")
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--budget-gb", type=float, default=180.0)
@@ -773,8 +773,8 @@ def main():
                          "red-black Gauss-Seidel iterations (the paper's GPU solver; FP32)")
     ap.add_argument("--mg-smooth", type=int, default=2,
                     help="multigrid red-black sweep pairs before and after the correction")
-    ap.add_argument("--batch-per-scene", action="store_true",
-                    help="batch mode: time the per-scene-launch form (the fused form beside it)")
+    ap.add_argument("--batch-fused", action="store_true",
+                    help="batch mode without the autotuner: start from the fused form")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="batch mode: keep the default solve-team split")
     ap.add_argument("--no-surface", dest="surface", action="store_false",

@@ -309,19 +309,21 @@ const char* flip_strerror(int status);
 const char* flip_last_error(void);
 
 /* ---------------------------------------------------------------- batches
- * Many independent scenes advanced together.  Per step, in the fused form (the
- * default when no scene of the call uses an adaptive time step or reseeding):
- * each step kernel runs once for all scenes -- the two binning scans, the
- * scatter, P2G, its normalisation and the right-hand side, each one launch over a
- * table of the scenes in which every scene owns a range of CTAs -- then the
- * pressure solves of all scenes run in one cooperative launch per (precision,
- * preconditioner) group, each scene on its own team of CTAs sized by its particle
- * count, with per-scene barriers, reductions and convergence, then G2P runs once
- * per precision group.  About 9 launches per step whatever the number of scenes,
- * all on the batch's stream.  Otherwise (or with flip_batch_set_fused(b, 0)) every
- * scene's binning, P2G and right-hand side run on the scene's own stream, the
- * solves as above, then every scene's G2P on its own stream.  A scene's results
- * are those of flip_step up to the order of floating-point sums. */
+ * Many independent scenes advanced together.  The pressure solves of all scenes
+ * run in one cooperative launch per (precision, preconditioner) group, each scene
+ * on its own team of CTAs sized by its particle count, with per-scene barriers,
+ * reductions and convergence.  The other step kernels take one of two forms:
+ *   per-scene (the default): every scene's binning, P2G and right-hand side run on
+ *     the scene's own stream before the solves, and its G2P on its own stream
+ *     after them, so the stages of different scenes overlap on the device;
+ *   fused (flip_batch_set_fused(b, 1), when no scene of the call uses an adaptive
+ *     time step or reseeding): each step kernel runs once for all scenes -- the two
+ *     binning scans, the scatter, P2G (over one flat list of every scene's active
+ *     bricks), its normalisation and the right-hand side, each one launch over a
+ *     table of the scenes -- and G2P once per precision group: about 9 launches
+ *     per step whatever the number of scenes, all on the batch's stream.
+ * flip_batch_autotune times both (and their graph replays) and keeps the faster.
+ * A scene's results are those of flip_step up to the order of floating-point sums. */
 typedef struct flip_batch flip_batch;
 
 /* A batch runner for up to capacity scenes (capacity <= 4096).  It owns small
@@ -348,8 +350,8 @@ int flip_batch_step(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t ns
  * (64 dam breaks: 12.2 against 11.5 ms per step). */
 int flip_batch_set_graphs(flip_batch* b, int32_t enable);
 
-/* enable = 1 (default): the fused form above where every scene allows it;
- * 0: per-scene launches on the scenes' streams. */
+/* enable = 1: the fused form above where every scene allows it; 0 (default):
+ * per-scene launches on the scenes' streams. */
 int flip_batch_set_fused(flip_batch* b, int32_t enable);
 
 /* 1 when a captured graph is cached (the last graph-eligible call used it). */

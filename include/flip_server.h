@@ -73,9 +73,9 @@ int flip_server_drain(flip_server* s);
  * one batch at a time; the next is formed when the previous one has completed. */
 int flip_server_set_overlap(flip_server* s, int32_t enable);
 
-/* The batches' form (flip_batch_set_fused): 1 (default) fused, one launch per step
- * kernel for all the batch's scenes, which then complete together; 0 per-scene
- * launches on the scenes' streams, each scene completing as its own G2P ends.  Set
+/* The batches' form (flip_batch_set_fused): 0 (default) per-scene launches on the
+ * scenes' streams, each scene completing as its own G2P ends; 1 fused, one launch
+ * per step kernel for all the batch's scenes, which then complete together.  Set
  * it while no request is queued. */
 int flip_server_set_fused(flip_server* s, int32_t enable);
 

@@ -464,7 +464,7 @@ class Batch:
         _check(lib().flip_batch_set_graphs(self.b, int(bool(enable))))
 
     def set_fused(self, enable: bool):
-        """One launch per step kernel across all scenes (default) or per-scene launches."""
+        """One launch per step kernel across all scenes, or per-scene launches (default)."""
         _check(lib().flip_batch_set_fused(self.b, int(bool(enable))))
 
     def form(self):
@@ -540,7 +540,7 @@ class Server:
         _check(lib().flip_server_drain(self.s))
 
     def set_fused(self, enable: bool):
-        """Fused batches (default) or per-scene launches inside each batch."""
+        """Fused batches, or per-scene launches inside each batch (default)."""
         _check(lib().flip_server_set_fused(self.s, int(bool(enable))))
 
     def set_overlap(self, enable: bool):

@@ -241,6 +241,7 @@ def test_fused_batch_matches_the_oracle_per_scene():
     sims = [F.Simulation(fp, *sc.arrays()) for n, sc, op, fp in mix]
     try:
         with F.Batch(len(sims)) as b:
+            b.set_fused(True)
             rc, st = b.step(sims, 1, stats=True)
             assert rc == F.FLIP_OK
             # one launch per kernel for all scenes, not ~8 per scene: 7 for the binning,
@@ -306,6 +307,7 @@ def test_fused_batch_edge_scenes():
     sims += [F.Simulation(matched(sc.n)[1], *sc.arrays()) for sc in specs]
     try:
         with F.Batch(len(sims)) as b:
+            b.set_fused(True)
             rc, st = b.step(sims, 1, stats=True)
             assert rc == F.FLIP_OK
         assert st[0].n_particles == 0 and st[0].n_fluid_cells == 0

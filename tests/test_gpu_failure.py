@@ -160,15 +160,18 @@ def _fields(sim):
             sim.particles())
 
 
-def test_batch_isolates_a_failing_scene():
-    """A scene whose solve is refused (singular: every cell fluid) in a batch: the
-    batch reports FLIP_E_ARG, and the other scenes still equal the oracle's step."""
+@pytest.mark.parametrize("fused", [False, True])
+def test_batch_isolates_a_failing_scene(fused):
+    """A scene whose solve is refused (singular: every cell fluid) in a batch, in
+    either form: the batch reports FLIP_E_ARG, and the other scenes still equal the
+    oracle's step."""
     good = [S.dam_break(24), S.dam_break(32, 0.4, 0.6)]
     bad = _singular_box(16)
     scenes = [good[0], bad, good[1]]
     sims = [F.Simulation(matched(sc.n[0])[1], *sc.arrays()) for sc in scenes]
     try:
         with F.Batch(4) as b:
+            b.set_fused(fused)
             with pytest.raises(F.FlipError) as ei:
                 b.step(sims, 1, stats=True)
             assert ei.value.code == F.FLIP_E_ARG
