@@ -565,10 +565,16 @@ __device__ __forceinline__ float restrict_sum(const SV& F, int fnz, int I, int J
 
 // Colour-split F -> colour-split C, over C's active segments; lanes take the
 // segment's 64 cells in x order (so the fine red slots they read are contiguous).
+// The pass also makes C's first red half-sweep from zero, x = b / (s_C n) on C's
+// red fluid cells, which needs only the b it has just computed: C's
+// pre-smoothing then starts with the black half-sweep, and the cycle meets one
+// grid barrier fewer per level (the values are those the separate half-sweep
+// computes; the slots of C's non-fluid cells, never read unmasked, are left).
 __device__ __noinline__ void restrict_split(const MgLevel& Fl, const MgLevel& Cl) {
   const int lane = threadIdx.x & 31;
   const SV F = sview(Fl), C = sview(Cl);
   const int fnz = Fl.nz;
+  const int lc = Cl.lvl;
   const Items it = seg_items(Cl, 1);
   for (unsigned int t = it.first; t < it.end; t += PCG_WARPS) {
     const int4 sg = C.seg[t - C.seg_base];
@@ -577,9 +583,13 @@ __device__ __noinline__ void restrict_split(const MgLevel& Fl, const MgLevel& Cl
     for (int h = 0; h < 2; ++h) {
       const int I = sg.y * (2 * SEG_SLOTS) + h * 32 + lane;
       if (I >= C.nx) continue;
-      const int ci = ((I + J + K) & 1) * C.half + C.margin + C.hx * sg.x + (I >> 1);
-      if (!(C.code[ci] & CODE_SELF)) continue;
-      C.b[ci] = restrict_sum(F, fnz, I, J, K);
+      const int red = ((I + J + K) & 1) == 0;
+      const int ci = (1 - red) * C.half + C.margin + C.hx * sg.x + (I >> 1);
+      const unsigned int code = C.code[ci];
+      if (!(code & CODE_SELF)) continue;
+      const float bc = restrict_sum(F, fnz, I, J, K);
+      C.b[ci] = bc;
+      if (red) C.x[ci] = gs_first(lc, code_cnt(code), bc);
     }
   }
 }
@@ -606,13 +616,13 @@ __device__ __forceinline__ bool gsync(const PcgArgs& A) {
   return grid_barrier(A.bar, A.status, team_size(), A.timeout_ns);
 }
 
-// Pre-smoothing from zero and restriction, colour-split level l -> l+1.
+// Pre-smoothing from zero and restriction, colour-split level l -> l+1.  The
+// first red half-sweep from zero was made by the restriction into level l
+// (restrict_split), behind the barrier that followed it.
 __device__ __forceinline__ bool down_split(const PcgArgs& A, int l) {
   const MgArgs& M = A.mg;
   const MgLevel& L = M.lv[l];
   const MgLevel& C = M.lv[l + 1];
-  sweep_split<FIRST>(M, L, C, l, 0, nullptr);
-  if (!gsync(A)) return false;
   sweep_split<NORMAL>(M, L, C, l, 1, nullptr);
   if (!gsync(A)) return false;
   for (int s = 1; s < M.nu; ++s) {
