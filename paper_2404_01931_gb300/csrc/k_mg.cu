@@ -29,9 +29,10 @@
 // The correction is never written: the first post-smoothing half-sweep (black)
 // reads its red neighbours plus omega times their parents' values, and the red
 // half-sweep that follows overwrites the red cells anyway.  The first red
-// half-sweep from zero only needs the residual, so at level 0 it is fused into
-// the phase that produces the residual.  The last black and the last red
-// half-sweeps of level 0 also accumulate r.z.
+// half-sweep from zero only needs the residual, so it is fused into the pass
+// that produces it: at level 0 the CG phase that updates r, at a grid-wide
+// coarse level the restriction.  The last black and the last red half-sweeps of
+// level 0 also accumulate r.z.
 #include "pcg_common.cuh"
 
 namespace flipk {
