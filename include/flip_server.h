@@ -60,9 +60,10 @@ int flip_server_add_scene(flip_server* s, const flip_params* params, const float
 int flip_server_submit(flip_server* s, int32_t scene, double t_arrival, int64_t* ticket);
 
 /* Blocks until the request is done; fills *info (nullable), then forgets the
- * ticket.  Returns the request's status (FLIP_E_NOT_CONVERGED, a warning, as
- * FLIP_OK), or FLIP_E_ARG for an unknown ticket or one another caller has
- * already collected. */
+ * ticket.  Returns the request's status, the two warnings (FLIP_E_NOT_CONVERGED,
+ * FLIP_E_CAPACITY: the step is committed) as FLIP_OK with info->status keeping
+ * them, or FLIP_E_ARG for an unknown ticket or one another caller has already
+ * collected. */
 int flip_server_wait(flip_server* s, int64_t ticket, flip_request_info* info);
 
 /* Blocks until every submitted request is done. */

@@ -450,7 +450,8 @@ int flip_server_wait(flip_server* s, int64_t ticket, flip_request_info* info) {
   }
   const int st = r.status;
   s->reqs.erase(ticket);
-  return st == FLIP_E_NOT_CONVERGED ? FLIP_OK : st;
+  // the two warnings (the step is committed) read as success; info->status keeps them
+  return (st == FLIP_E_NOT_CONVERGED || st == FLIP_E_CAPACITY) ? FLIP_OK : st;
 }
 
 int flip_server_drain(flip_server* s) {
