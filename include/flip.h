@@ -282,6 +282,28 @@ int flip_set_solver_blocks(flip_handle* h, int32_t nblocks);
  * first warning, else FLIP_OK. */
 int flip_autotune_solver(flip_handle* h, int32_t steps_per_candidate, int32_t* nblocks);
 
+/* Launch shapes of the scene's particle transfers (Sec. 3.1.6, 3.1.8): the grids
+ * of the P2G and G2P kernels are p2g_per_sm and g2p_per_sm CTAs per SM (0: the
+ * defaults, 8 for P2G and G2P's co-resident count).  Both kernels loop over the
+ * active bricks, so any count gives the same step (up to the order of P2G's
+ * floating-point sums); more CTAs than fit at once let the scheduler balance
+ * bricks of uneven particle counts.  The best count depends on the scene.
+ * FLIP_E_ARG for a NULL handle or a count outside [0, 64]. */
+int flip_set_transfer_ctas(flip_handle* h, int32_t p2g_per_sm, int32_t g2p_per_sm);
+
+/* The CTAs per SM in use (defaults resolved); either pointer may be NULL. */
+int flip_get_transfer_ctas(const flip_handle* h, int32_t* p2g_per_sm, int32_t* g2p_per_sm);
+
+/* Autotuner of those shapes: for the pairs (P2G, G2P) = (4, c), (8, 2c), (16, 4c)
+ * CTAs per SM (c: G2P's co-resident count) it takes steps_per_candidate real
+ * steps through flip_step, in that order and then in reverse (the scene evolves
+ * while it is timed), adds each stage's CUDA-event times, and keeps for each
+ * stage the count that took least time (written to the nullable outputs).  The
+ * scene advances by 6 * steps_per_candidate steps.  Returns the first error, else
+ * the first warning, else FLIP_OK. */
+int flip_autotune_transfers(flip_handle* h, int32_t steps_per_candidate, int32_t* p2g_per_sm,
+                            int32_t* g2p_per_sm);
+
 /* Total mechanical energy of the particles, the quantity the paper follows over
  * a run to compare its CPU and GPU versions (Sec. 4, Fig. 10).  With particle
  * mass m = particle_mass and the handle's gravity g:
@@ -368,11 +390,15 @@ int flip_batch_set_team_exponent(flip_batch* b, double exponent);
  * nullable).  Then, with that split, it times the four forms of the step -- fused
  * or per-scene launches, each stream-ordered or replayed as CUDA graphs -- over
  * 2 * steps_per_candidate steps each (after a 2-step call that warms the form) and
- * keeps the fastest (flip_batch_get_form tells which).  Since the scenes evolve
- * while they are timed, every candidate is timed twice, in forward then reverse
- * order, and the two times added.  The scenes advance by 14 * steps_per_candidate
- * + 8 * (2 + 2 * steps_per_candidate) steps in all.  Returns the first error, else
- * the first warning, else FLIP_OK. */
+ * keeps the fastest (flip_batch_get_form tells which).  Last, with that form, it
+ * times the transfers' launch shapes (the candidate pairs of
+ * flip_autotune_transfers, set on every scene) over steps_per_candidate steps
+ * each: in the fused form each stage keeps its fastest count by the batch-wide
+ * stage times, in the per-scene form the pair with the least wall time is kept.
+ * Since the scenes evolve while they are timed, every candidate is timed twice,
+ * in forward then reverse order, and the two times added.  The scenes advance by
+ * 20 * steps_per_candidate + 8 * (2 + 2 * steps_per_candidate) steps in all.
+ * Returns the first error, else the first warning, else FLIP_OK. */
 int flip_batch_autotune(flip_batch* b, flip_handle* const* hs, int32_t n,
                         int32_t steps_per_candidate, double* exponent);
 

@@ -112,6 +112,7 @@ struct flip_handle {
   void* tmp = nullptr;
   size_t tmp_bytes = 0;
   int pcg_blocks = 0, sm_count = 0, p2g_blocks = 0, g2p_blocks = 0;
+  int p2g_per_sm = 0, g2p_per_sm = 0;  // flip_set_transfer_ctas (0: the defaults)
   int solver_blocks = 0;      // CTAs of a single solve (0: pcg_blocks)
   int launches = 0;
   bool stepped = false;
@@ -125,6 +126,17 @@ struct flip_handle {
 };
 
 void flip_set_last_error_(const std::string& msg) { g_last_error = msg; }
+
+// P2G's default grid: 8 CTAs per SM, twice the co-resident 4, so that CTAs
+// taking heavy bricks are balanced by the scheduler (the kernel loops over the
+// active bricks; measured 8 % faster than one wave on a 128^3 dam break, equal on
+// the 256^3 pool).  G2P's: its co-resident count.
+constexpr int kP2gPerSm = 8;
+
+void set_transfer_grids(flip_handle* h) {
+  h->p2g_blocks = h->sm_count * (h->p2g_per_sm > 0 ? h->p2g_per_sm : kP2gPerSm);
+  h->g2p_blocks = h->g2p_per_sm > 0 ? h->sm_count * h->g2p_per_sm : g2p_blocks(h->sm_count);
+}
 
 extern "C" {
 
@@ -634,8 +646,7 @@ int flip_create(const flip_params* params, const float* x, const float* y, const
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "multigrid kernel occupancy"));
     setup_mg(h->mg, h->mg_dims, solver_params(*params));
   }
-  h->p2g_blocks = h->sm_count * 4;
-  h->g2p_blocks = g2p_blocks(h->sm_count);
+  set_transfer_grids(h);
 
   Carver measure;
   carve(h, measure);
@@ -859,6 +870,87 @@ int flip_autotune_solver(flip_handle* h, int32_t steps_per_candidate, int32_t* n
   }
   h->solver_blocks = best;
   if (nblocks) *nblocks = best;
+  return first_warning;
+}
+
+int flip_set_transfer_ctas(flip_handle* h, int32_t p2g_per_sm, int32_t g2p_per_sm) {
+  if (!h) return fail(FLIP_E_ARG, "handle is NULL");
+  if (p2g_per_sm < 0 || p2g_per_sm > 64 || g2p_per_sm < 0 || g2p_per_sm > 64)
+    return fail(FLIP_E_ARG, "CTAs per SM must be in [0, 64]");
+  h->p2g_per_sm = p2g_per_sm;
+  h->g2p_per_sm = g2p_per_sm;
+  set_transfer_grids(h);
+  return FLIP_OK;
+}
+
+int flip_get_transfer_ctas(const flip_handle* h, int32_t* p2g_per_sm, int32_t* g2p_per_sm) {
+  if (!h) return fail(FLIP_E_ARG, "handle is NULL");
+  const int sm = std::max(h->sm_count, 1);
+  if (p2g_per_sm) *p2g_per_sm = h->p2g_blocks / sm;
+  if (g2p_per_sm) *g2p_per_sm = h->g2p_blocks / sm;
+  return FLIP_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// The candidates of the launch-shape autotuners: P2G at 4, 8 and 16 CTAs per SM,
+// G2P at 1, 2 and 4 times its co-resident count, taken in pairs (the two stages are
+// timed apart, so each keeps its own best).
+struct TransferCand {
+  int p2g, g2p;
+};
+
+void transfer_candidates(TransferCand (&c)[3]) {
+  const int g = g2p_blocks(1);  // G2P's co-resident CTAs per SM
+  c[0] = {4, g};
+  c[1] = {8, 2 * g};
+  c[2] = {16, 4 * g};
+}
+
+}  // namespace
+
+extern "C" {
+
+int flip_autotune_transfers(flip_handle* h, int32_t steps_per_candidate, int32_t* p2g_per_sm,
+                            int32_t* g2p_per_sm) {
+  if (!h) return fail(FLIP_E_ARG, "handle is NULL");
+  if (steps_per_candidate < 1) return fail(FLIP_E_ARG, "steps_per_candidate must be >= 1");
+  TransferCand cand[3];
+  transfer_candidates(cand);
+  const int keep_p = h->p2g_per_sm, keep_g = h->g2p_per_sm;
+  double p_ms[3] = {}, g_ms[3] = {};
+  int first_warning = FLIP_OK;
+  // forward then reverse (the scene evolves while it is timed)
+  for (int t = 0; t < 6; ++t) {
+    const int c = t < 3 ? t : 5 - t;
+    h->p2g_per_sm = cand[c].p2g;
+    h->g2p_per_sm = cand[c].g2p;
+    set_transfer_grids(h);
+    flip_stats st;
+    const int rc = flip_step(h, steps_per_candidate, &st);
+    if (rc == FLIP_E_NOT_CONVERGED || rc == FLIP_E_CAPACITY) {
+      if (first_warning == FLIP_OK) first_warning = rc;
+    } else if (rc != FLIP_OK) {
+      h->p2g_per_sm = keep_p;
+      h->g2p_per_sm = keep_g;
+      set_transfer_grids(h);
+      return rc;
+    }
+    p_ms[c] += st.ms_p2g;
+    g_ms[c] += st.ms_g2p;
+  }
+  int bp = 0, bg = 0;
+  for (int c = 1; c < 3; ++c) {
+    if (p_ms[c] < p_ms[bp]) bp = c;
+    if (g_ms[c] < g_ms[bg]) bg = c;
+  }
+  h->p2g_per_sm = cand[bp].p2g;
+  h->g2p_per_sm = cand[bg].g2p;
+  set_transfer_grids(h);
+  if (p2g_per_sm) *p2g_per_sm = cand[bp].p2g;
+  if (g2p_per_sm) *g2p_per_sm = cand[bg].g2p;
   return first_warning;
 }
 
@@ -1124,6 +1216,8 @@ int batch_graph_steps(flip_batch* b, flip_handle* const* hs, int n, int pairs,
     key.push_back((unsigned long long)(uintptr_t)hs[s]);
     key.push_back((unsigned long long)hs[s]->serial);
     key.push_back((unsigned long long)hs[s]->cur);
+    key.push_back((unsigned long long)hs[s]->p2g_blocks);  // the captured launch shapes
+    key.push_back((unsigned long long)hs[s]->g2p_blocks);
   }
   for (int v : first_all) key.push_back((unsigned long long)v);
   // the batch stream starts after every scene stream's earlier work
@@ -1401,6 +1495,52 @@ int flip_batch_autotune(flip_batch* b, flip_handle* const* hs, int32_t n,
     if (form_ms[fi] < form_ms[bf]) bf = fi;
   b->fused = forms[bf].fused;
   b->graphs = forms[bf].graphs;
+  // Then the transfers' launch shapes, the same for every scene: each candidate
+  // pair over steps_per_candidate steps with statistics, forward then reverse.  In
+  // the fused form each stage keeps its fastest count by the batch-wide stage
+  // times; in the per-scene form (stages on the scenes' streams, overlapping) the
+  // pair whose calls took least wall time is kept.
+  TransferCand tc[3];
+  transfer_candidates(tc);
+  std::vector<int> keep_p(n), keep_g(n);
+  for (int s = 0; s < n; ++s) {
+    keep_p[s] = hs[s]->p2g_per_sm;
+    keep_g[s] = hs[s]->g2p_per_sm;
+  }
+  double p_ms[3] = {}, g_ms[3] = {};
+  for (int t = 0; t < 6; ++t) {
+    const int c = t < 3 ? t : 5 - t;
+    for (int s = 0; s < n; ++s) {
+      hs[s]->p2g_per_sm = tc[c].p2g;
+      hs[s]->g2p_per_sm = tc[c].g2p;
+      set_transfer_grids(hs[s]);
+    }
+    rc = flip_batch_step(b, hs, n, steps_per_candidate, st.data());
+    if (rc == FLIP_E_NOT_CONVERGED || rc == FLIP_E_CAPACITY) {
+      if (first_warning == FLIP_OK) first_warning = rc;
+    } else if (rc != FLIP_OK) {
+      for (int s = 0; s < n; ++s) {
+        hs[s]->p2g_per_sm = keep_p[s];
+        hs[s]->g2p_per_sm = keep_g[s];
+        set_transfer_grids(hs[s]);
+      }
+      return rc;
+    }
+    if (n > 0) {
+      p_ms[c] += b->fused ? st[0].ms_p2g : st[0].ms_total;
+      g_ms[c] += b->fused ? st[0].ms_g2p : st[0].ms_total;
+    }
+  }
+  int bp = 0, bg = 0;
+  for (int c = 1; c < 3; ++c) {
+    if (p_ms[c] < p_ms[bp]) bp = c;
+    if (g_ms[c] < g_ms[bg]) bg = c;
+  }
+  for (int s = 0; s < n; ++s) {
+    hs[s]->p2g_per_sm = tc[bp].p2g;
+    hs[s]->g2p_per_sm = tc[bg].g2p;
+    set_transfer_grids(hs[s]);
+  }
   // the device-side conditions of the untimed calls
   for (int s = 0; s < n; ++s) {
     const int r2 = flip_sync(hs[s]);

@@ -158,6 +158,9 @@ def lib():
         L.flip_energy.argtypes = [vp, C.c_double, C.POINTER(C.c_double)]
         L.flip_set_solver_blocks.argtypes = [vp, i32]
         L.flip_autotune_solver.argtypes = [vp, i32, C.POINTER(i32)]
+        L.flip_set_transfer_ctas.argtypes = [vp, i32, i32]
+        L.flip_get_transfer_ctas.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
+        L.flip_autotune_transfers.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32)]
         L.flip_batch_set_team_exponent.argtypes = [vp, C.c_double]
         L.flip_batch_graph_active.argtypes = [vp]
         L.flip_batch_set_graphs.argtypes = [vp, i32]
@@ -705,6 +708,24 @@ class Simulation:
         out = C.c_int32(0)
         _check(lib().flip_autotune_solver(self.h, int(steps_per_candidate), C.byref(out)))
         return int(out.value)
+
+    def set_transfer_ctas(self, p2g_per_sm: int, g2p_per_sm: int):
+        """CTAs per SM of the P2G and G2P launches (0: the defaults)."""
+        _check(lib().flip_set_transfer_ctas(self.h, int(p2g_per_sm), int(g2p_per_sm)))
+
+    def transfer_ctas(self):
+        """(P2G, G2P) CTAs per SM in use."""
+        p, g = C.c_int32(0), C.c_int32(0)
+        _check(lib().flip_get_transfer_ctas(self.h, C.byref(p), C.byref(g)))
+        return int(p.value), int(g.value)
+
+    def autotune_transfers(self, steps_per_candidate: int = 1):
+        """Chooses the P2G and G2P launch shapes by timing real steps (the scene
+        advances by 6 * steps_per_candidate steps); returns (P2G, G2P) CTAs per SM."""
+        p, g = C.c_int32(0), C.c_int32(0)
+        _check(lib().flip_autotune_transfers(self.h, int(steps_per_candidate), C.byref(p),
+                                             C.byref(g)))
+        return int(p.value), int(g.value)
 
     def energy(self, particle_mass: float):
         """(kinetic, potential, total) energy of the particles (Sec. 4, Fig. 10)."""

@@ -151,9 +151,10 @@ def test_batch_with_adaptive_step_and_reseeding():
 
 def test_autotune_picks_a_candidate_and_keeps_results():
     """The autotuner advances the scenes by real steps (2 x 7 for the split, 2 x 4 x
-    (2 + 2) for the forms) and leaves a split and a form in force; from the initial
-    particles again, the scenes then step as they do alone (a split and a form change
-    only the order of floating-point sums)."""
+    (2 + 2) for the forms, 2 x 3 for the transfers' launch shapes) and leaves a
+    split, a form and launch shapes in force; from the initial particles again, the
+    scenes then step as they do alone (these change only the order of
+    floating-point sums)."""
     mix = _mix()[:4]
     sims = [F.Simulation(fp, *sc.arrays()) for n, sc, op, fp in mix]
     ref = []
@@ -166,7 +167,11 @@ def test_autotune_picks_a_candidate_and_keeps_results():
             a = b.autotune(sims, 1)
             assert a in (0.5, 0.75, 1.0, 1.25, 1.5, 2.0, 2.5)
             assert b.form() in ((True, False), (True, True), (False, False), (False, True))
-            # the autotuner took 14 + 8 * 4 = 46 steps; start the scenes again
+            shapes = {sim.transfer_ctas() for sim in sims}
+            assert len(shapes) == 1                 # the same shapes on every scene
+            p2g, g2p = shapes.pop()
+            assert p2g in (4, 8, 16) and g2p >= 1
+            # the autotuner took 14 + 8 * 4 + 6 = 52 steps; start the scenes again
             for sim, (n, sc, op, fp) in zip(sims, mix):
                 ids = sim.read(F.PID)
                 F.flip_write_particles(sim.h, *[np.ascontiguousarray(x[ids]) for x in sc.arrays()])

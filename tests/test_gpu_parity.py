@@ -473,6 +473,34 @@ def test_solver_block_count_keeps_the_solution():
         assert nb >= 1
 
 
+def test_transfer_launch_shapes_keep_the_step():
+    """The P2G and G2P grid sizes (set, or autotuned) change at most the order of
+    P2G's sums: the step still equals the oracle's at the parity bar."""
+    sc = S.dam_break(40, 0.45, 0.5, seed=3)
+    op, fp = matched(40)
+    ref = O.step(op, *sc.arrays())
+    for shape in ((1, 1), (16, 20), (0, 0)):
+        with F.Simulation(fp, *sc.arrays()) as sim:
+            sim.set_transfer_ctas(*shape)
+            p2g, g2p = sim.transfer_ctas()
+            assert p2g == (shape[0] or 8) and g2p >= 1
+            rc, st = sim.step(1, stats=True)
+            assert rc == F.FLIP_OK
+            assert rel_l2(sim.read(F.U_OLD), ref.u_old[0], face_floor(40)) <= 1e-5
+            assert rel_l2(sim.read(F.PRESSURE_F64), ref.pressure) <= 1e-5
+            x, y, z = sim.particles(by_id=True)[:3]
+            err = np.abs(np.stack([x, y, z]).astype(np.float64)
+                         - np.stack([ref.x, ref.y, ref.z])).max() * 40
+            assert err <= 1e-4, (shape, err)
+    with F.Simulation(fp, *sc.arrays()) as sim:
+        for bad in ((-1, 0), (0, 65)):
+            with pytest.raises(F.FlipError):
+                sim.set_transfer_ctas(*bad)
+        p2g, g2p = sim.autotune_transfers(1)
+        assert p2g in (4, 8, 16) and g2p >= 1
+        assert sim.transfer_ctas() == (p2g, g2p)
+
+
 @pytest.mark.parametrize("n", [48, (40, 24, 56)])
 def test_rbgs_solver_iterates_match_the_oracle(n):
     """The paper's GPU solver (red-black Gauss-Seidel): after exactly 16 sweep pairs
