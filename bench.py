@@ -776,7 +776,8 @@ def main():
     ap.add_argument("--batch-fused", action="store_true",
                     help="batch mode without the autotuner: start from the fused form")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
-                    help="batch mode: keep the default solve-team split")
+                    help="skip the autotuners (one scene: the P2G/G2P launch shapes; "
+                         "batch: the solve-team split, the form and the launch shapes)")
     ap.add_argument("--no-surface", dest="surface", action="store_false",
                     help="skip the surface-reconstruction measurement")
     ap.add_argument("--warm-start", action="store_true",
@@ -835,6 +836,15 @@ def main():
         sim.step(1, stats=True)
         first = first_step_fields(sim, F)
         warm_left -= 1
+    # the launch shapes of P2G and G2P, chosen on this scene by the autotuner (6
+    # untimed steps); the scene then starts again from its seeded particles and
+    # takes the warm-up steps, so the timed steps are those of the run without it
+    shapes = None
+    if args.autotune and not (args.ppc[0] or args.ppc[1]) and args.cfl == 0:
+        shapes = sim.autotune_transfers(1)
+        ids = sim.read(F.PID)
+        F.flip_write_particles(sim.h, *[np.ascontiguousarray(a[ids]) for a in sc.arrays()])
+        warm_left = args.warmup
     if warm_left > 1:
         sim.step(warm_left - 1)
     if warm_left > 0:
@@ -956,6 +966,9 @@ def main():
                        "pressure_start": "last solve's pressure (warm start)" if args.warm_start
                        else "zero (cold start)",
                        "mg_smooth": args.mg_smooth, "solver": args.precond,
+                       "transfer_ctas_per_sm": dict(zip(("p2g", "g2p"), sim.transfer_ctas()),
+                                                    chosen_by="autotuner (6 untimed steps)"
+                                                    if shapes else "defaults"),
                        "time_step": f"adaptive, CFL number {args.cfl}" if args.cfl > 0
                        else "fixed 1/240",
                        "reseeding": f"{args.ppc[0]}..{args.ppc[1]} particles per cell"
