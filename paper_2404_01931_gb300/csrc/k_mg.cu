@@ -782,41 +782,62 @@ __device__ __noinline__ void cta_levels_init(const MgArgs& M, CtaMg& sm) {
     }
   }
   __syncthreads();
+  // Per level: each thread takes a contiguous run of cells, counts its fluid cells
+  // of each colour (the two counts packed in one word: a level has fewer than 2^16
+  // cells), a block-wide exclusive scan gives each run its place, and the runs
+  // write their entries: colour 0's list then colour 1's, each in cell order.
+  __shared__ unsigned int s_scan[PCG_WARPS];
   int pos = 0;  // next free list entry (same value in every thread)
   for (int l = M.lgrid; l < M.nlev; ++l) {
-    const int n = M.lv[l].ncells, nx = sm.nx[l], ny = sm.ny[l];
-    for (int c = threadIdx.x; c < n; c += PCG_THREADS) sm.code[sm.base[l] + c] = M.lv[l].code[c];
+    const int n = M.lv[l].ncells, nx = sm.nx[l], ny = sm.ny[l], bl = sm.base[l];
+    for (int c = threadIdx.x; c < n; c += PCG_THREADS) sm.code[bl + c] = M.lv[l].code[c];
     __syncthreads();
-    for (int colour = 0; colour < 2; ++colour) {
-      if (threadIdx.x == 0) sm.off[l][colour] = pos;
-      for (int c0 = 0; c0 < n; c0 += PCG_THREADS) {
-        const int c = c0 + (int)threadIdx.x;
-        int i = 0, j = 0, k = 0;
-        bool f = false;
-        if (c < n) {
-          i = c % nx;
-          j = (c / nx) % ny;
-          k = c / (nx * ny);
-          f = (sm.code[sm.base[l] + c] & CODE_SELF) && ((i + j + k) & 1) == colour;
-        }
-        const unsigned int bal = __ballot_sync(0xffffffffu, f);
-        if (lane == 0) s_wc[warp] = __popc(bal);
-        __syncthreads();
-        int before = 0, tot = 0;
-        for (int w = 0; w < PCG_WARPS; ++w) {
-          before += (w < warp) ? (int)s_wc[w] : 0;
-          tot += (int)s_wc[w];
-        }
-        if (f)
-          sm.list[pos + before + __popc(bal & ((1u << lane) - 1u))] =
-              (uint16_t)(i | (j << sm.bx[l]) | (k << (sm.bx[l] + sm.by[l])));
-        pos += tot;
-        __syncthreads();
-      }
+    const int per = (n + PCG_THREADS - 1) / PCG_THREADS;
+    const int c0 = min(n, (int)threadIdx.x * per), c1 = min(n, c0 + per);
+    unsigned int mine = 0;  // colour 0 in the low half, colour 1 in the high half
+    for (int c = c0; c < c1; ++c) {
+      const int i = c % nx, j = (c / nx) % ny, k = c / (nx * ny);
+      if (sm.code[bl + c] & CODE_SELF) mine += ((i + j + k) & 1) ? 0x10000u : 1u;
     }
-    if (threadIdx.x == 0) sm.off[l][2] = pos;
+    unsigned int inc = mine;  // inclusive scan over the warp, then over the warps
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned int v = __shfl_up_sync(0xffffffffu, inc, d);
+      if (lane >= d) inc += v;
+    }
+    if (lane == 31) s_scan[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+      const unsigned int t = lane < PCG_WARPS ? s_scan[lane] : 0u;
+      unsigned int w = t;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const unsigned int v = __shfl_up_sync(0xffffffffu, w, d);
+        if (lane >= d) w += v;
+      }
+      if (lane < PCG_WARPS) s_scan[lane] = w - t;  // exclusive, per warp
+      const unsigned int tot = __shfl_sync(0xffffffffu, w, 31);
+      if (lane == 0) s_wc[0] = tot;
+    }
+    __syncthreads();
+    const unsigned int before = s_scan[warp] + inc - mine, tot = s_wc[0];
+    const int n0 = (int)(tot & 0xffffu), n1 = (int)(tot >> 16);
+    int p0 = pos + (int)(before & 0xffffu), p1 = pos + n0 + (int)(before >> 16);
+    for (int c = c0; c < c1; ++c) {
+      if (!(sm.code[bl + c] & CODE_SELF)) continue;
+      const int i = c % nx, j = (c / nx) % ny, k = c / (nx * ny);
+      const uint16_t e = (uint16_t)(i | (j << sm.bx[l]) | (k << (sm.bx[l] + sm.by[l])));
+      if ((i + j + k) & 1) sm.list[p1++] = e;
+      else sm.list[p0++] = e;
+    }
+    if (threadIdx.x == 0) {
+      sm.off[l][0] = pos;
+      sm.off[l][1] = pos + n0;
+      sm.off[l][2] = pos + n0 + n1;
+    }
+    pos += n0 + n1;
+    __syncthreads();
   }
-  __syncthreads();
 }
 
 // The same cycle pieces as for the grid-wide levels, inside CTA 0.
