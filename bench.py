@@ -591,6 +591,7 @@ def run_batch(args):
                       "preconditioner": "multigrid",
                       "form": form_name(*form) + (" (chosen by the autotuner)" if args.autotune
                                                   else ""),
+                      "transfer_ctas_per_sm": dict(zip(("p2g", "g2p"), sims[0].transfer_ctas())),
                       "parallelism": f"scenes sharded over {ws} GPU(s) by the host-side router "
                                      "(longest first to the least-loaded rank), one batch "
                                      "per GPU, no data-path collective"},
