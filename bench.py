@@ -410,8 +410,13 @@ def run_reference(args, w):
     import oracle as O
     from paper_2404_01931_gb300 import scenes as S
     n = w["n"]
-    # each step: one oracle step of the workload's scene at a bounded grid edge
-    ns = min(n, 64)
+    # each step: one oracle step of the workload's scene, on the workload's own grid
+    # when the K + W steps fit about three minutes of the host's cores (the oracle
+    # takes ~6.6 s per step at 256^3 on 16 cores, ~0.09 s at 64^3, about in
+    # proportion to the cells), else on the largest halved grid that does
+    ns = n
+    while ns > 16 and (args.steps + args.warmup) * 6.6 * (ns / 256.0) ** 3 > 180.0:
+        ns //= 2
     sc = make_scene(w, ns)
     op = O.Params(n=(ns, ns, ns), dx=1.0 / ns,
                   cg_tol=w["ir_tol"] if w["precision"] == "mixed" else w["cg_tol"])
