@@ -78,8 +78,8 @@ MG_IR_BYTES_PER_SOLVE = 40
 # the algorithmic bytes of `roofline`.  The preconditioner's own passes (the
 # V-cycle) are not algorithmic bytes of the method; the builder's model above
 # counts them and is reported beside it.
-SURVEY_PCG_BYTES_PER_ITER = 47
-SURVEY_IR_BYTES_PER_OUTER = 40
+METHOD_PCG_BYTES_PER_ITER = 47
+METHOD_IR_BYTES_PER_OUTER = 40
 # DRAM traffic of one k_pcg_mg launch on the 256^3 pool, read from the committed
 # single-pass ncu summary, which records the hash of the solver's sources it was
 # measured on; when the sources have changed since, the traffic is reported as null.
@@ -117,7 +117,7 @@ def recorded_pcg_traffic():
 def stage_roofline(w, np_, nfl, stage_ms, steps, peak):
     """Achieved HBM GB/s of the other stages over the live CUDA-event stage time, against
     the measured copy bandwidth, by two byte models.
-    The method's algorithmic bytes (SURVEY 8(d); `frac`):
+    The method's algorithmic bytes (`frac`):
       bin:        56 B per particle (24 B read, key 4 B, 24 B written, histogram 4 B)
                   + 8 B per cell
       P2G:        24 B per particle + 21 B per cell (u*, v*, w* written 12 B, type 1 B,
@@ -444,7 +444,7 @@ def run_reference(args, w):
 
 
 def batch_stage_roofline(scenes, nfl_total, stage_ms, steps, peak):
-    """The stage rooflines of a batch (SURVEY 8(d) byte model, as stage_roofline),
+    """The stage rooflines of a batch (the method's byte model, as stage_roofline),
     summed over its scenes, over the fused form's batch-wide stage times."""
     np_ = sum(sc.n_particles for sc in scenes)
     cells = sum(int(np.prod(sc.n)) for sc in scenes)
@@ -942,17 +942,18 @@ def main():
         if diag:
             diag["energy_frac_of_measured_hbm"] = diag["energy_bytes"] / (diag["energy_ms"] / 1e3) / 1e9 / peak
         mixed = w["precision"] == "mixed"
-        # the method's algorithmic bytes of the solves (SURVEY 8(d) model) and the
-        # builder's model that also counts the V-cycle's passes
-        survey_bytes = nfl * (SURVEY_PCG_BYTES_PER_ITER * st.cg_iterations
-                              + (SURVEY_IR_BYTES_PER_OUTER * st.ir_iterations if mixed else 0))
+        # the method's algorithmic bytes of the solves (47 B per fluid cell per CG
+        # iteration + 40 B per refinement) and the build's model that also counts
+        # the V-cycle's passes
+        method_bytes = nfl * (METHOD_PCG_BYTES_PER_ITER * st.cg_iterations
+                              + (METHOD_IR_BYTES_PER_OUTER * st.ir_iterations if mixed else 0))
         pcg_bytes = nfl * (MG_PCG_BYTES_PER_ITER * st.cg_iterations
                            + (MG_IR_BYTES_PER_OUTER * st.ir_iterations
                               + MG_IR_BYTES_PER_SOLVE * args.steps if mixed else 0))
         stage_ms = {"bin": st.ms_bin, "p2g": st.ms_p2g, "divergence": st.ms_divergence,
                     "pcg": st.ms_pcg, "g2p": st.ms_g2p}
         t_pcg = st.ms_pcg / 1e3
-        achieved = survey_bytes / t_pcg / 1e9 if t_pcg > 0 else None
+        achieved = method_bytes / t_pcg / 1e9 if t_pcg > 0 else None
         achieved_vc = pcg_bytes / t_pcg / 1e9 if t_pcg > 0 else None
         traffic, traffic_note = (recorded_pcg_traffic() if args.workload == "pool256"
                                  else (None, "captured for the 256^3 pool only"))
@@ -998,13 +999,13 @@ def main():
                          "bound": "hbm", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
                          "frac_survey": (achieved / peak) if achieved else None,
-                         "byte_model": f"{SURVEY_PCG_BYTES_PER_ITER} B per fluid cell per CG "
-                                       f"iteration + {SURVEY_IR_BYTES_PER_OUTER} B per fluid "
+                         "byte_model": f"{METHOD_PCG_BYTES_PER_ITER} B per fluid cell per CG "
+                                       f"iteration + {METHOD_IR_BYTES_PER_OUTER} B per fluid "
                                        "cell per outer refinement",
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                          "nominal_peak": NOMINAL_HBM_GBS,
                          "frac_of_nominal": (achieved / NOMINAL_HBM_GBS) if achieved else None,
-                         "algorithmic_bytes_per_launch": survey_bytes / args.steps,
+                         "algorithmic_bytes_per_launch": method_bytes / args.steps,
                          "with_vcycle_bytes": {
                              "bytes_per_launch": pcg_bytes / args.steps,
                              "achieved": achieved_vc,
