@@ -37,7 +37,49 @@
 
 namespace flipk {
 
+// Solve trace, in builds with -DFLIP_SOLVE_TRACE only (compiled out otherwise):
+// thread 0 of the team's first CTA stamps the global timer after each phase of
+// a solve into flip_trace_ns[slot] (slots below), each stamp taken after the grid
+// barrier that ends its phase; flip_solve_trace copies them to the host.
+#ifdef FLIP_SOLVE_TRACE
+__device__ unsigned long long flip_trace_ns[64];
+#define SOLVE_TRACE(slot) trace_stamp(slot)
+#else
+#define SOLVE_TRACE(slot) ((void)0)
+#endif
+
+enum TraceSlot {
+  TR_ENTRY = 0,       // kernel entry
+  TR_TABLES = 1,      // shared tables loaded
+  TR_BFLAG = 2,       // block flags cleared
+  TR_FLAGS = 2,       // + l: fluid flags of level l (l = 1 .. 11) built
+  TR_SEG_COUNT = 14,  // active segments counted
+  TR_SEG_WRITE = 15,  // active-segment lists written
+  TR_CODES = 16,      // neighbour codes built
+  TR_SEG_CACHE = 17,  // segment slices cached
+  TR_CTA_LISTS = 18,  // CTA-local lists built (CTA 0)
+  TR_START = 19,      // start pass (r, z, b) done
+  TR_ITER = 20,       // + 3 i, + 1, + 2: V-cycle, phase A, phase B of iteration i (i < 3)
+  TR_LOOP_END = 29,   // CG loop left
+  TR_END = 30,        // solution written
+  TR_EXIT = 31,       // kernel exit
+  TR_V_PRE1 = 32,     // the V-cycle's pieces (the last V-cycle of the solve):
+  TR_V_PRE = 33,      //   level-0 pre-smoothing (first black, the rest),
+  TR_V_RESTRICT = 34, //   restriction 0 -> 1,
+  TR_V_DOWN = 34,     //   + l: level l's pre-smoothing and restriction (l = 1 .. 11),
+  TR_V_CTA = 46,      //   the CTA-local levels,
+  TR_V_UP = 46,       //   + l: level l's correction and post-smoothing (l = 1 .. 11),
+  TR_V_CORRECT = 58,  //   level-0 correction and first black half-sweep,
+  TR_V_POST = 59      //   the rest of level 0's post-smoothing but the last red
+};
+
 namespace {
+
+#ifdef FLIP_SOLVE_TRACE
+__device__ __forceinline__ void trace_stamp(int slot) {
+  if (team_rank() == 0 && threadIdx.x == 0) flip_trace_ns[slot] = global_timer_ns();
+}
+#endif
 
 constexpr unsigned int CODE_SELF = 64u;
 constexpr int SEG_SLOTS = 32;  // slots of one colour per segment (a warp)
@@ -940,29 +982,39 @@ __device__ bool vcycle_rest(const PcgArgs& A, CtaMg& sm, FF& rz) {
   const MgLevel& L1 = M.lv[1];
   sweep_split<NORMAL>(M, L0, L1, 0, 1, nullptr);
   if (!gsync(A)) return false;
+  SOLVE_TRACE(TR_V_PRE1);
   for (int s = 1; s < M.nu; ++s) {
     sweep_split<NORMAL>(M, L0, L1, 0, 0, nullptr);
     if (!gsync(A)) return false;
     sweep_split<NORMAL>(M, L0, L1, 0, 1, nullptr);
     if (!gsync(A)) return false;
   }
+  SOLVE_TRACE(TR_V_PRE);
   if (L1.split) restrict_split(L0, L1);
   else restrict_split_nat(L0, L1);
   if (!gsync(A)) return false;
-  for (int l = 1; l < M.lgrid; ++l)
+  SOLVE_TRACE(TR_V_RESTRICT);
+  for (int l = 1; l < M.lgrid; ++l) {
     if (!down_split(A, l)) return false;
+    SOLVE_TRACE(TR_V_DOWN + min(l, 11));
+  }
   if (team_rank() == 0) cta_cycle(A, sm);
   if (!gsync(A)) return false;
-  for (int l = M.lgrid - 1; l >= 1; --l)
+  SOLVE_TRACE(TR_V_CTA);
+  for (int l = M.lgrid - 1; l >= 1; --l) {
     if (!up_split(A, l)) return false;
+    SOLVE_TRACE(TR_V_UP + min(l, 11));
+  }
   sweep_split<CORRECT>(M, L0, L1, 0, 1, M.nu == 1 ? &rz : nullptr);
   if (!gsync(A)) return false;
+  SOLVE_TRACE(TR_V_CORRECT);
   for (int s = 1; s < M.nu; ++s) {
     sweep_split<NORMAL>(M, L0, L1, 0, 0, nullptr);
     if (!gsync(A)) return false;
     sweep_split<NORMAL>(M, L0, L1, 0, 1, s + 1 == M.nu ? &rz : nullptr);
     if (!gsync(A)) return false;
   }
+  SOLVE_TRACE(TR_V_POST);
   sweep_split<NORMAL>(M, L0, L1, 0, 0, &rz);  // the last red half-sweep
   return true;
 }
@@ -1258,6 +1310,7 @@ __device__ __noinline__ bool build_levels(const PcgArgs& A, Shared& sh) {
     for (int c = p.begin; c < p.end; c += p.stride) L.bflag[c] = 0;
   }
   if (!gsync(A)) return false;
+  SOLVE_TRACE(TR_BFLAG);
   for (int l = 1; l < M.nlev; ++l) {
     const MgLevel& F = M.lv[l - 1];
     const MgLevel& C = M.lv[l];
@@ -1273,6 +1326,7 @@ __device__ __noinline__ bool build_levels(const PcgArgs& A, Shared& sh) {
       if (f && C.split) C.bflag[(i >> 3) + C.nbx * ((j >> 3) + C.nby * (k >> 3))] = 1;
     }
     if (!gsync(A)) return false;
+    SOLVE_TRACE(TR_FLAGS + min(l, 11));
   }
   // active segments: count per CTA, then write them in segment order
   __shared__ unsigned int s_wsum[PCG_WARPS];
@@ -1298,6 +1352,7 @@ __device__ __noinline__ bool build_levels(const PcgArgs& A, Shared& sh) {
     __syncthreads();
   }
   if (!gsync(A)) return false;
+  SOLVE_TRACE(TR_SEG_COUNT);
   for (int l = 0; l < M.lgrid; ++l) {
     const MgLevel& L = M.lv[l];
     const int nsegs = L.nw * L.ny * L.nz;
@@ -1339,6 +1394,7 @@ __device__ __noinline__ bool build_levels(const PcgArgs& A, Shared& sh) {
     }
   }
   if (!gsync(A)) return false;
+  SOLVE_TRACE(TR_SEG_WRITE);
   // codes: split levels over their active segments, CTA-local levels over all cells
   for (int l = 0; l < M.lgrid; ++l) {
     const MgLevel& L = M.lv[l];
@@ -1356,7 +1412,9 @@ __device__ __noinline__ bool build_levels(const PcgArgs& A, Shared& sh) {
       L.code[c] = (uint8_t)(make_code(L, L.t, cl.i, cl.j, cl.k) & 0x7fu);
     }
   }
-  return gsync(A);
+  const bool ok = gsync(A);
+  SOLVE_TRACE(TR_CODES);
+  return ok;
 }
 
 // Copies this CTA's slice of each grid-wide level's segment list into the
@@ -1410,7 +1468,9 @@ __device__ void solve_mg(const PcgArgs& A, Shared& sh, CtaMg& sm, int4* segc, So
   float* r = L0.b;
   if (!build_levels(A, sh)) { S.ok = false; return; }
   seg_cache_fill(M, segc);
+  SOLVE_TRACE(TR_SEG_CACHE);
   if (M.nlev > 1 && team_rank() == 0) cta_levels_init(M, sm);
+  SOLVE_TRACE(TR_CTA_LISTS);
   // ---- start: r = b (cold) or b - A x0 (warm start from the last solve's x),
   // p_old = 0, first red half-sweep of the V-cycle; mixed mode: b as a float pair,
   // the correction d = 0, and x = 0 unless warm
@@ -1466,6 +1526,7 @@ __device__ void solve_mg(const PcgArgs& A, Shared& sh, CtaMg& sm, int4* segc, So
     publish<2>(A, 4, v, sh);
   }
   if (!gsync(A)) { S.ok = false; return; }
+  SOLVE_TRACE(TR_START);
   double rz = 0.0, bnorm = 0.0, rnorm = 0.0, rmax = 0.0;
   const double target = MIXED ? A.ir_tol : A.tol;
   {
@@ -1490,6 +1551,7 @@ __device__ void solve_mg(const PcgArgs& A, Shared& sh, CtaMg& sm, int4* segc, So
       publish<1>(A, 3, v, sh);
     }
     if (!gsync(A)) { S.ok = false; return; }
+    if (it < 3) SOLVE_TRACE(TR_ITER + 3 * it);
     {
       double s[1];
       gather<1>(A, 3, s, sh);
@@ -1513,6 +1575,7 @@ __device__ void solve_mg(const PcgArgs& A, Shared& sh, CtaMg& sm, int4* segc, So
       publish<1>(A, 0, v, sh);
     }
     if (!gsync(A)) { S.ok = false; return; }
+    if (it <= 3) SOLVE_TRACE(TR_ITER + 3 * (it - 1) + 1);
     {
       double s[1];
       gather<1>(A, 0, s, sh);
@@ -1528,6 +1591,7 @@ __device__ void solve_mg(const PcgArgs& A, Shared& sh, CtaMg& sm, int4* segc, So
       publish<1>(A, 1, v, sh);
     }
     if (!gsync(A)) { S.ok = false; return; }
+    if (it <= 3) SOLVE_TRACE(TR_ITER + 3 * (it - 1) + 2);
     {
       double s[1];
       gather<1>(A, 1, s, sh);
@@ -1582,6 +1646,7 @@ __device__ void solve_mg(const PcgArgs& A, Shared& sh, CtaMg& sm, int4* segc, So
     }
     if (sh.flag == 1) { conv = true; break; }
   }
+  SOLVE_TRACE(TR_LOOP_END);
   // ---- the solution in natural layout: the FP32 pressure, or the float pair
   // (for G2P) and its FP64 value
   if constexpr (MIXED) {
@@ -1598,6 +1663,7 @@ __device__ void solve_mg(const PcgArgs& A, Shared& sh, CtaMg& sm, int4* segc, So
   } else {
     for_fluid0(A, [&](const SCell& e, unsigned int, int n) { A.x32[n] = d[e.idx]; });
   }
+  SOLVE_TRACE(TR_END);
   S.iters = it;
   S.refinements = refinements;
   S.conv = conv;
@@ -1721,8 +1787,11 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg_mg(const __grid_constant
   __shared__ Shared sh;
   extern __shared__ __align__(16) unsigned char mg_dyn[];
   team_enter(blockIdx.x, gridDim.x);
+  SOLVE_TRACE(TR_ENTRY);
   load_tables(A.mg);
+  SOLVE_TRACE(TR_TABLES);
   solve_scene_mg<MIXED>(A, sh, mg_dyn);
+  SOLVE_TRACE(TR_EXIT);
 }
 
 // Several scenes in one launch: CTA b works on scene block_scene[b], in the team
@@ -1788,3 +1857,15 @@ cudaError_t pcg_mg_check_occupancy() {
 }
 
 }  // namespace flipk
+
+#ifdef FLIP_SOLVE_TRACE
+// The stamps of the last solve (nanoseconds of the global timer; slots of
+// flipk::TraceSlot; 0 where no stamp was taken since the library was loaded).
+extern "C" int flip_solve_trace(unsigned long long* out, int n) {
+  if (!out || n < 1 || n > 64) return 1;
+  return cudaMemcpyFromSymbol(out, flipk::flip_trace_ns, sizeof(unsigned long long) * (size_t)n) ==
+                 cudaSuccess
+             ? 0
+             : 3;
+}
+#endif
