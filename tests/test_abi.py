@@ -281,3 +281,19 @@ def test_handle_entry_points_refuse_null(F):
     L = F.lib()
     assert L.flip_step_times(None, None, 0) == -F.FLIP_E_ARG
     assert L.flip_set_wait_timeout(None, 1000) == F.FLIP_E_ARG
+
+
+def test_solve_trace_variant_compiles(tmp_path):
+    """The solver's trace hooks (-DFLIP_SOLVE_TRACE) compile, and the trace entry
+    point exists only in that variant (the normal build compiles the hooks out)."""
+    import subprocess
+    from paper_2404_01931_gb300 import build_lib
+    src = os.path.join(build_lib.CSRC, "k_mg.cu")
+    for trace in (True, False):
+        obj = str(tmp_path / f"k_mg_{int(trace)}.o")
+        cmd = [build_lib.nvcc(), *build_lib._flags(["-DFLIP_SOLVE_TRACE"] if trace else []),
+               "-c", src, "-o", obj]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr[-2000:]
+        nm = subprocess.run(["nm", "-g", obj], capture_output=True, text=True).stdout
+        assert ("flip_solve_trace" in nm) == trace
