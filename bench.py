@@ -175,6 +175,9 @@ def make_params(w):
     return p
 
 
+L2_BYTES = 126 << 20  # GB300 L2 (129 MB nominal, 126 MiB as reported)
+
+
 def read_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -747,6 +750,9 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--flush-l2", choices=("auto", "always", "never"), default="auto",
+                    help="write a buffer twice the L2 before every timed step (auto: when "
+                         "the scene's device footprint is under 1 GB)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="pool256", choices=sorted(WORKLOADS))
@@ -862,17 +868,40 @@ def main():
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    rc, st = sim.step(args.steps, stats=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
+    # scenes whose device footprint is under 1 GB could be served from the 126 MB L2
+    # across steps: then a buffer twice the L2 is written before every timed step
+    # (outside the step's own CUDA events, which time it)
+    footprint = F.flip_footprint_bytes(prm, np_)
+    flush = args.flush_l2 == "always" or (args.flush_l2 == "auto" and footprint < (1 << 30))
+    if flush:
+        scrub = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device="cuda")
+        st = F.FlipStats()
+        step_ms = []
+        last = [f for f, _ in F.FlipStats._fields_ if not (f.startswith("ms_") or f in (
+            "cg_iterations", "ir_iterations", "kernel_launches", "particles_added",
+            "particles_removed", "steps"))]
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                scrub.zero_()
+            rc, s1 = sim.step(1, stats=True)
+            step_ms.extend(sim.step_times().tolist())
+            for f, _ in F.FlipStats._fields_:
+                setattr(st, f, getattr(s1, f) if f in last else getattr(st, f) + getattr(s1, f))
+        torch.cuda.synchronize()
+        step_ms = np.asarray(step_ms, np.float64)
+        ms_local = float(step_ms.sum())
+    else:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc, st = sim.step(args.steps, stats=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms = sim.step_times()
+        ms_local = e0.elapsed_time(e1)
     if ws > 1:
         dist.barrier()
     ck = clocks.stop()
-    step_ms = sim.step_times()
-    ms_local = e0.elapsed_time(e1)
     ms = max_over_ranks(ms_local, ws)
     np_ = st.n_particles if args.ppc[0] or args.ppc[1] else np_
     value = job_rate(np_ * args.steps, ms_local / 1e3, ws)
@@ -969,7 +998,11 @@ def main():
                        "ir_tol": w["ir_tol"], "cg_tol": w["cg_tol"], "dt": 1 / 240,
                        "flip_ratio": 0.95, "seed": 0,
                        "parallelism": f"{ws} independent replica(s), one per GPU",
-                       "l2": "inputs larger than L2 (particles + grids > 1 GB); no flush",
+                       "l2": (f"L2 flushed before every timed step (a {2 * L2_BYTES >> 20} MB "
+                              f"buffer written; device footprint {footprint / 2**20:.0f} MB); "
+                              "value from the steps' own CUDA events") if flush else
+                             (f"inputs larger than L2 (device footprint {footprint / 2**30:.2f} GB); "
+                              "no flush"),
                        "pressure_start": "last solve's pressure (warm start)" if args.warm_start
                        else "zero (cold start)",
                        "mg_smooth": args.mg_smooth, "solver": args.precond,
