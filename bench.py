@@ -495,6 +495,8 @@ def run_batch(args):
             p.cg_tol, p.ir_tol = 1e-3, 1e-8
         sims.append(F.Simulation(p, *sc.arrays()))
     npart = sum(sc.n_particles for sc in scenes)
+    footprint = sum(F.flip_footprint_bytes(sim.params, sc.n_particles)
+                    for sim, sc in zip(sims, scenes))
     stream = torch.cuda.Stream()  # the batch's launches run here; it joins every scene
     b = F.Batch(len(sims), stream=stream.cuda_stream)
     b.set_fused(args.batch_fused)
@@ -600,6 +602,8 @@ def run_batch(args):
                       "form": form_name(*form) + (" (chosen by the autotuner)" if args.autotune
                                                   else ""),
                       "transfer_ctas_per_sm": dict(zip(("p2g", "g2p"), sims[0].transfer_ctas())),
+                      "l2": f"inputs larger than L2 ({footprint / 2**30:.2f} GB on the device "
+                            "for the batch); no flush",
                       "parallelism": f"scenes sharded over {ws} GPU(s) by the host-side router "
                                      "(longest first to the least-loaded rank), one batch "
                                      "per GPU, no data-path collective"},
@@ -736,6 +740,8 @@ def run_serve(args):
                       "max_batch": args.max_batch, "resident_scenes": sv["resident_scenes"],
                       "resident_gb": sv["resident_gb"], "particles_total": sv["particles_total"],
                       "setup_s": sv["setup_s"],
+                      "l2": f"inputs larger than L2 ({sv['resident_gb']:.1f} GB of resident "
+                            "scenes); no flush",
                       "parallelism": f"scenes placed on {ws} GPU(s) by the host-side router "
                                      "(longest first to the least-loaded rank), one server "
                                      "per GPU, no data-path collective"},
