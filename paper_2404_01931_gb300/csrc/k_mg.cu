@@ -406,27 +406,25 @@ __device__ __forceinline__ void parent_values(const PV& C, int nx, int ny, int n
 template <int MODE>
 __device__ __forceinline__ bool gs_apply(float* x, int l, float omega, GsIn& s, float& v) {
   if (!s.ok || !(s.code & CODE_SELF)) return false;
-  const int cnt = code_cnt(s.code);
-  if constexpr (MODE == FIRST) {
-    v = gs_first(l, cnt, s.b);
-  } else {
-    if constexpr (MODE == CORRECT) {
+  if constexpr (MODE == CORRECT) {
 #pragma unroll
-      for (int q = 0; q < 6; ++q)
-        if ((s.code >> q) & 1u) s.xv[q] = __fmaf_rn(omega, s.pv[q], s.xv[q]);
-    }
-    v = gs_sum(l, cnt, s.code, s.b, s.xv);
+    for (int q = 0; q < 6; ++q)
+      if ((s.code >> q) & 1u) s.xv[q] = __fmaf_rn(omega, s.pv[q], s.xv[q]);
   }
+  v = gs_sum(l, code_cnt(s.code), s.code, s.b, s.xv);
   x[s.idx] = v;
   return true;
 }
 
 // Half-sweep of one colour over colour-split level l (description L; C is level
 // l+1, read in CORRECT mode).  With rz, also accumulates b x over the updated
-// cells.  Paired form: slots that are not fluid cells of the grid get 0.
+// cells.  Paired form: slots that are not fluid cells of the grid get 0.  (A
+// grid-wide level never sweeps from zero here: its first red half-sweep is made
+// by the pass that produces its right-hand side.)
 template <int MODE>
 __device__ __noinline__ void sweep_split_v(const MgArgs& M, const MgLevel& L, const MgLevel& C,
                                          int l, int colour, FF* rz) {
+  static_assert(MODE != FIRST, "grid-wide levels start from the fused first half-sweep");
   constexpr int U = (MODE == CORRECT) ? 1 : 2;
   const int lane = threadIdx.x & 31;
   const SV v = sview(L);
@@ -452,7 +450,7 @@ __device__ __noinline__ void sweep_split_v(const MgArgs& M, const MgLevel& L, co
         st.e.okB &= ok;
         st.code2 = *reinterpret_cast<const unsigned int*>(v.code + st.e.idx);
         st.b = *reinterpret_cast<const float2*>(v.b + st.e.idx);
-        if constexpr (MODE != FIRST) st.n = load_nbr2(v, v.x, st.e);
+        st.n = load_nbr2(v, v.x, st.e);
         if constexpr (MODE == CORRECT) {
           parent_values(cv, v.nx, v.ny, nz, min(st.e.iA, v.nx - 1), st.e.j, st.e.k, st.pvA);
           parent_values(cv, v.nx, v.ny, nz, min(st.e.iA + 2, v.nx - 1), st.e.j, st.e.k, st.pvB);
@@ -467,21 +465,15 @@ __device__ __noinline__ void sweep_split_v(const MgArgs& M, const MgLevel& L, co
           const unsigned int code = h == 0 ? (st.code2 & 0xffffu) : (st.code2 >> 16);
           const bool ok = (h == 0 ? st.e.okA : st.e.okB) && (code & CODE_SELF);
           const float bc = h == 0 ? st.b.x : st.b.y;
-          const int cnt = code_cnt(code);
-          float val;
-          if constexpr (MODE == FIRST) {
-            val = gs_first(l, cnt, bc);
-          } else {
-            float xv[6];
-            nbr_of(st.n, h, xv);
-            if constexpr (MODE == CORRECT) {
+          float xv[6];
+          nbr_of(st.n, h, xv);
+          if constexpr (MODE == CORRECT) {
 #pragma unroll
-              for (int u = 0; u < 6; ++u)
-                if ((code >> u) & 1u)
-                  xv[u] = __fmaf_rn(omega, h == 0 ? st.pvA[u] : st.pvB[u], xv[u]);
-            }
-            val = gs_sum(l, cnt, code, bc, xv);
+            for (int u = 0; u < 6; ++u)
+              if ((code >> u) & 1u)
+                xv[u] = __fmaf_rn(omega, h == 0 ? st.pvA[u] : st.pvB[u], xv[u]);
           }
+          const float val = gs_sum(l, code_cnt(code), code, bc, xv);
           out[h] = ok ? val : 0.0f;
           if (ok && rz) acc.add_prod(bc, val);
         }
@@ -499,6 +491,7 @@ __device__ __noinline__ void sweep_split_v(const MgArgs& M, const MgLevel& L, co
 template <int MODE>
 __device__ __noinline__ void sweep_split_s(const MgArgs& M, const MgLevel& L, const MgLevel& C,
                                          int l, int colour, FF* rz) {
+  static_assert(MODE != FIRST, "grid-wide levels start from the fused first half-sweep");
   constexpr int U = (MODE == CORRECT) ? 1 : 2;
   const int lane = threadIdx.x & 31;
   const SV v = sview(L);
@@ -519,12 +512,10 @@ __device__ __noinline__ void sweep_split_s(const MgArgs& M, const MgLevel& L, co
         s.ok = e.ok && ok;
         s.code = v.code[e.idx];
         s.b = v.b[e.idx];
-        if constexpr (MODE != FIRST) {
-          int nb[6];
-          snbr(v, e, nb);
+        int nb[6];
+        snbr(v, e, nb);
 #pragma unroll
-          for (int q = 0; q < 6; ++q) s.xv[q] = v.x[nb[q]];
-        }
+        for (int q = 0; q < 6; ++q) s.xv[q] = v.x[nb[q]];
         if constexpr (MODE == CORRECT)
           parent_values(cv, v.nx, v.ny, nz, min(e.i, v.nx - 1), e.j, e.k, s.pv);
         return s;
