@@ -421,7 +421,7 @@ __device__ __forceinline__ bool gs_apply(float* x, int l, float omega, GsIn& s, 
 // cells.  Paired form: slots that are not fluid cells of the grid get 0.  (A
 // grid-wide level never sweeps from zero here: its first red half-sweep is made
 // by the pass that produces its right-hand side.)
-template <int MODE>
+template <int MODE, bool RZ>
 __device__ __noinline__ void sweep_split_v(const MgArgs& M, const MgLevel& L, const MgLevel& C,
                                          int l, int colour, FF* rz) {
   static_assert(MODE != FIRST, "grid-wide levels start from the fused first half-sweep");
@@ -431,6 +431,7 @@ __device__ __noinline__ void sweep_split_v(const MgArgs& M, const MgLevel& L, co
   const PV cv = pview(C);
   const int nz = L.nz;
   const float omega = M.omega;
+  const float inv6 = s_inv_cnt[6], invs6 = s_inv_scnt[l][6];
   const int2 q = seg_slice(L);
   const Items it = pair_items(q, 1);
   struct S {
@@ -460,6 +461,32 @@ __device__ __noinline__ void sweep_split_v(const MgArgs& M, const MgLevel& L, co
       [&](S&) {},
       [&](S& st) {
         float out[2];
+        {
+          // a warp whose cells are all fluid with six fluid neighbours (the bulk of
+          // the liquid): gs_sum's operations in its order, without masks or tables
+          // (and the correction of every neighbour in CORRECT mode)
+          const bool full = (st.code2 & 0x007f007fu) == 0x007f007fu && st.e.okA && st.e.okB;
+          if (__all_sync(0xffffffffu, full)) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              float xv[6];
+              nbr_of(st.n, h, xv);
+              if constexpr (MODE == CORRECT) {
+#pragma unroll
+                for (int u = 0; u < 6; ++u)
+                  xv[u] = __fmaf_rn(omega, h == 0 ? st.pvA[u] : st.pvB[u], xv[u]);
+              }
+              float sum = 0.0f;
+#pragma unroll
+              for (int u = 0; u < 6; ++u) sum = __fadd_rn(sum, xv[u]);
+              const float bc = h == 0 ? st.b.x : st.b.y;
+              out[h] = __fmaf_rn(sum, inv6, __fmul_rn(bc, invs6));
+              if (RZ) acc.add_prod(bc, out[h]);
+            }
+            *reinterpret_cast<float2*>(v.x + st.e.idx) = make_float2(out[0], out[1]);
+            return;
+          }
+        }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const unsigned int code = h == 0 ? (st.code2 & 0xffffu) : (st.code2 >> 16);
@@ -475,12 +502,12 @@ __device__ __noinline__ void sweep_split_v(const MgArgs& M, const MgLevel& L, co
           }
           const float val = gs_sum(l, code_cnt(code), code, bc, xv);
           out[h] = ok ? val : 0.0f;
-          if (ok && rz) acc.add_prod(bc, val);
+          if (RZ && ok) acc.add_prod(bc, val);
         }
         if (st.e.okA || st.e.okB)
           *reinterpret_cast<float2*>(v.x + st.e.idx) = make_float2(out[0], out[1]);
       });
-  if (rz) {
+  if constexpr (RZ) {
     rz->add_prod(acc.hi, 1.0f);
     rz->add_prod(acc.lo, 1.0f);
   }
@@ -542,7 +569,12 @@ __device__ __forceinline__ bool use_pairs(const MgLevel& L) {
 template <int MODE>
 __device__ __forceinline__ void sweep_split(const MgArgs& M, const MgLevel& L, const MgLevel& C,
                                             int l, int colour, FF* rz) {
-  if (use_pairs(L)) sweep_split_v<MODE>(M, L, C, l, colour, rz);
+  if (use_pairs(L)) {
+    // the r.z accumulation only where asked (its registers would make the other
+    // half-sweeps spill)
+    if (rz) sweep_split_v<MODE, true>(M, L, C, l, colour, rz);
+    else sweep_split_v<MODE, false>(M, L, C, l, colour, nullptr);
+  }
   else sweep_split_s<MODE>(M, L, C, l, colour, rz);
 }
 
@@ -1034,6 +1066,27 @@ __device__ __noinline__ void phase_a_v(const PcgArgs& A, const float* pold, floa
     const Nbr2 nz = load_nbr2(v, z, e);
     const Nbr2 np = load_nbr2(v, pold, e);
     float pn[2], qn[2];
+    // a warp whose cells are all fluid with six fluid neighbours: the same
+    // operations in the same order without the masks (nfl = count = 6)
+    const bool full = (code2 & 0x007f007fu) == 0x007f007fu && e.okA && e.okB;
+    if (__all_sync(0xffffffffu, full)) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float zv[6], pv[6];
+        nbr_of(nz, h, zv);
+        nbr_of(np, h, pv);
+        const float p_c = __fmaf_rn(beta, h == 0 ? pc.x : pc.y, h == 0 ? zc.x : zc.y);
+        float d = 0.0f;
+#pragma unroll
+        for (int u = 0; u < 6; ++u) d = __fadd_rn(d, __fsub_rn(p_c, __fmaf_rn(beta, pv[u], zv[u])));
+        pn[h] = p_c;
+        qn[h] = __fmul_rn(s_a, __fmaf_rn(0.0f, p_c, d));
+        acc.add_prod(p_c, qn[h]);
+      }
+      *reinterpret_cast<float2*>(pnew + e.idx) = make_float2(pn[0], pn[1]);
+      *reinterpret_cast<float2*>(q0 + e.idx) = make_float2(qn[0], qn[1]);
+      continue;
+    }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const unsigned int code = h == 0 ? (code2 & 0xffffu) : (code2 >> 16);
