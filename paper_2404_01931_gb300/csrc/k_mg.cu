@@ -82,6 +82,7 @@ __device__ __forceinline__ void trace_stamp(int slot) {
 #endif
 
 constexpr unsigned int CODE_SELF = 64u;
+constexpr unsigned int CODE_FULL = 0x67fu;  // fluid, six fluid neighbours, count 6
 constexpr int SEG_SLOTS = 32;  // slots of one colour per segment (a warp)
 
 // Gauss-Seidel coefficients per level, copied to shared memory at kernel start:
@@ -380,6 +381,15 @@ __device__ __forceinline__ float resid(float s, int cnt, unsigned int code, floa
   return __fsub_rn(bc, __fmul_rn(s, __fmaf_rn((float)(cnt - nfl), xc, d)));
 }
 
+// resid for a cell whose six neighbours are all fluid (code CODE_FULL): the same
+// operations without the masks (cnt - nfl = 0).
+__device__ __forceinline__ float resid_full(float s, float bc, float xc, const float (&xv)[6]) {
+  float d = 0.0f;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) d = __fadd_rn(d, __fsub_rn(xc, xv[q]));
+  return __fsub_rn(bc, __fmul_rn(s, __fmaf_rn(0.0f, xc, d)));
+}
+
 // ---------------------------------------------------------------- sweeps
 
 struct GsIn {
@@ -647,13 +657,38 @@ __device__ __noinline__ void restrict_split(const MgLevel& Fl, const MgLevel& Cl
     const int J = sg.z, K = sg.w;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
+      // every lane takes part (a lane past the row's end on its last cell, whose
+      // result it drops), so that a warp can vote
       const int I = sg.y * (2 * SEG_SLOTS) + h * 32 + lane;
-      if (I >= C.nx) continue;
-      const int red = ((I + J + K) & 1) == 0;
-      const int ci = (1 - red) * C.half + C.margin + C.hx * sg.x + (I >> 1);
+      const bool in = I < C.nx;
+      const int Ic = in ? I : C.nx - 1;
+      const int red = ((Ic + J + K) & 1) == 0;
+      const int ci = (1 - red) * C.half + C.margin + C.hx * sg.x + (Ic >> 1);
       const unsigned int code = C.code[ci];
-      if (!(code & CODE_SELF)) continue;
-      const float bc = restrict_sum(F, fnz, I, J, K);
+      // restrict_sum's sum over the red children; a pair of children that is all
+      // interior fluid cells in every lane is added without the masks
+      float sum = 0.0f;
+#pragma unroll
+      for (int hz = 0; hz < 2; ++hz) {
+        ChildIn ch[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) child_load(F, fnz, Ic, J, K, q, hz, ch[q]);
+        const bool full = ch[0].ok && ch[1].ok && ch[0].code == CODE_FULL && ch[1].code == CODE_FULL;
+        if (__all_sync(0xffffffffu, full)) {
+#pragma unroll
+          for (int q = 0; q < 2; ++q)
+            sum = __fadd_rn(sum, resid_full(F.s, ch[q].b, ch[q].xc, ch[q].xv));
+        } else {
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const ChildIn& c = ch[q];
+            if (!c.ok || !(c.code & CODE_SELF)) continue;
+            sum = __fadd_rn(sum, resid(F.s, code_cnt(c.code), c.code, c.b, c.xc, c.xv));
+          }
+        }
+      }
+      if (!in || !(code & CODE_SELF)) continue;
+      const float bc = __fmul_rn(sum, 0.0625f);
       C.b[ci] = bc;
       if (red) C.x[ci] = gs_first(lc, code_cnt(code), bc);
     }
@@ -1125,6 +1160,7 @@ __device__ __noinline__ void phase_b_v(const PcgArgs& A, const float* pnew, floa
   float* d0 = M.d0;
   const float* q0 = M.q0;
   const int lane = threadIdx.x & 31;
+  const float invs6 = s_inv_scnt[0][6];
   const int2 q = seg_slice(M.lv[0]);
   const Items it = pair_items(q, 2);
   struct S {
@@ -1152,6 +1188,25 @@ __device__ __noinline__ void phase_b_v(const PcgArgs& A, const float* pnew, floa
       [&](S&) {},
       [&](S& st) {
         float dn[2], rn[2], zn[2];
+        // a warp whose cells are all fluid with six fluid neighbours: no selects
+        const bool full = (st.code2 & 0xffffffffu) == (CODE_FULL | (CODE_FULL << 16)) &&
+                          st.e.okA && st.e.okB;
+        if (__all_sync(0xffffffffu, full)) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const float dd = h == 0 ? st.d.x : st.d.y, pp = h == 0 ? st.p.x : st.p.y;
+            const float qq = h == 0 ? st.qq.x : st.qq.y, r0 = h == 0 ? st.r.x : st.r.y;
+            const float rc = __fmaf_rn(-alpha, qq, r0);
+            dn[h] = __fmaf_rn(alpha, pp, dd);
+            rn[h] = rc;
+            zn[h] = __fmul_rn(rc, invs6);
+            acc.add_prod(rc, rc);
+          }
+          *reinterpret_cast<float2*>(d0 + st.e.idx) = make_float2(dn[0], dn[1]);
+          *reinterpret_cast<float2*>(v.b + st.e.idx) = make_float2(rn[0], rn[1]);
+          if (st.c == 0) *reinterpret_cast<float2*>(v.x + st.e.idx) = make_float2(zn[0], zn[1]);
+          return;
+        }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const unsigned int code = h == 0 ? (st.code2 & 0xffffu) : (st.code2 >> 16);
