@@ -83,6 +83,10 @@ __device__ __forceinline__ void trace_stamp(int slot) {
 
 constexpr unsigned int CODE_SELF = 64u;
 constexpr unsigned int CODE_FULL = 0x67fu;  // fluid, six fluid neighbours, count 6
+// Both cells of a slot pair's codes (16 bits each) are CODE_FULL.
+__device__ __forceinline__ bool pair_full(unsigned int code2) {
+  return code2 == (CODE_FULL | (CODE_FULL << 16));
+}
 constexpr int SEG_SLOTS = 32;  // slots of one colour per segment (a warp)
 
 // Gauss-Seidel coefficients per level, copied to shared memory at kernel start:
@@ -475,7 +479,7 @@ __device__ __noinline__ void sweep_split_v(const MgArgs& M, const MgLevel& L, co
           // a warp whose cells are all fluid with six fluid neighbours (the bulk of
           // the liquid): gs_sum's operations in its order, without masks or tables
           // (and the correction of every neighbour in CORRECT mode)
-          const bool full = (st.code2 & 0x007f007fu) == 0x007f007fu && st.e.okA && st.e.okB;
+          const bool full = pair_full(st.code2) && st.e.okA && st.e.okB;
           if (__all_sync(0xffffffffu, full)) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -1103,7 +1107,7 @@ __device__ __noinline__ void phase_a_v(const PcgArgs& A, const float* pold, floa
     float pn[2], qn[2];
     // a warp whose cells are all fluid with six fluid neighbours: the same
     // operations in the same order without the masks (nfl = count = 6)
-    const bool full = (code2 & 0x007f007fu) == 0x007f007fu && e.okA && e.okB;
+    const bool full = pair_full(code2) && e.okA && e.okB;
     if (__all_sync(0xffffffffu, full)) {
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
@@ -1189,8 +1193,7 @@ __device__ __noinline__ void phase_b_v(const PcgArgs& A, const float* pnew, floa
       [&](S& st) {
         float dn[2], rn[2], zn[2];
         // a warp whose cells are all fluid with six fluid neighbours: no selects
-        const bool full = (st.code2 & 0xffffffffu) == (CODE_FULL | (CODE_FULL << 16)) &&
-                          st.e.okA && st.e.okB;
+        const bool full = pair_full(st.code2) && st.e.okA && st.e.okB;
         if (__all_sync(0xffffffffu, full)) {
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
