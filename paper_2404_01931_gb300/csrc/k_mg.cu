@@ -540,6 +540,7 @@ __device__ __noinline__ void sweep_split_s(const MgArgs& M, const MgLevel& L, co
   const int nz = L.nz;
   const float omega = M.omega;
   const Items it = seg_items(L, 1);
+  const float inv6 = s_inv_cnt[6], invs6 = s_inv_scnt[l][6];
   FF acc;
   run_batched<U>(
       it.first, it.end, PCG_WARPS,
@@ -563,6 +564,21 @@ __device__ __noinline__ void sweep_split_s(const MgArgs& M, const MgLevel& L, co
       },
       [&](GsIn&) {},
       [&](GsIn& s) {
+        // a warp whose cells are all fluid with six fluid neighbours: gs_apply's
+        // operations in its order, without the masks
+        if (__all_sync(0xffffffffu, s.ok && s.code == CODE_FULL)) {
+          if constexpr (MODE == CORRECT) {
+#pragma unroll
+            for (int q = 0; q < 6; ++q) s.xv[q] = __fmaf_rn(omega, s.pv[q], s.xv[q]);
+          }
+          float sum = 0.0f;
+#pragma unroll
+          for (int q = 0; q < 6; ++q) sum = __fadd_rn(sum, s.xv[q]);
+          const float xv = __fmaf_rn(sum, inv6, __fmul_rn(s.b, invs6));
+          v.x[s.idx] = xv;
+          if (rz) acc.add_prod(s.b, xv);
+          return;
+        }
         float xv;
         if (gs_apply<MODE>(v.x, l, omega, s, xv) && rz) acc.add_prod(s.b, xv);
       });
