@@ -70,7 +70,8 @@ enum TraceSlot {
   TR_V_CTA = 46,      //   the CTA-local levels,
   TR_V_UP = 46,       //   + l: level l's correction and post-smoothing (l = 1 .. 11),
   TR_V_CORRECT = 58,  //   level-0 correction and first black half-sweep,
-  TR_V_POST = 59      //   the rest of level 0's post-smoothing but the last red
+  TR_V_POST = 59,     //   the rest of level 0's post-smoothing but the last red
+  TR_REFINE = 60      // + 0, 1, 2: the first refinement's start, x += d, residual
 };
 
 namespace {
@@ -1564,6 +1565,119 @@ __device__ __forceinline__ int4* seg_cache_of(unsigned char* dyn) {
   return reinterpret_cast<int4*>(dyn + MG_DYN_CTA);
 }
 
+// The mixed mode's refinement, over level 0's slot pairs with two items in flight
+// per warp (the per-cell arithmetic of the single-slot form, so the same values).
+// refine_update: x += d as float pairs on fluid cells, d = 0 there.
+__device__ __noinline__ void refine_update(const PcgArgs& A) {
+  const MgArgs& M = A.mg;
+  const SV v = sview(M.lv[0]);
+  float* d0 = M.d0;
+  float2* x2 = M.x2;
+  const int lane = threadIdx.x & 31;
+  const int2 q = seg_slice(M.lv[0]);
+  const Items it = pair_items(q, 2);
+  struct S {
+    PCell e;
+    unsigned int code2;
+    float2 d;
+    float4 x;  // the two slots' (hi, lo)
+  };
+  run_batched<2>(
+      it.first, it.end, PCG_WARPS,
+      [&](unsigned int t, bool ok) {
+        S st;
+        st.e = pcell(v, q, t >> 1, (int)(t & 1u), lane);
+        st.e.okA &= ok;
+        st.e.okB &= ok;
+        st.code2 = *reinterpret_cast<const unsigned int*>(v.code + st.e.idx);
+        st.d = *reinterpret_cast<const float2*>(d0 + st.e.idx);
+        st.x = *reinterpret_cast<const float4*>(x2 + st.e.idx);
+        return st;
+      },
+      [&](S&) {},
+      [&](S& st) {
+        if (!(st.e.okA || st.e.okB)) return;
+        const bool fa = st.e.okA && (st.code2 & CODE_SELF);
+        const bool fb = st.e.okB && ((st.code2 >> 16) & CODE_SELF);
+        const float2 ta = two_sum(st.x.x, st.d.x), tb = two_sum(st.x.z, st.d.y);
+        const float2 xa = fast_two_sum(ta.x, __fadd_rn(ta.y, st.x.y));
+        const float2 xb = fast_two_sum(tb.x, __fadd_rn(tb.y, st.x.w));
+        *reinterpret_cast<float4*>(x2 + st.e.idx) =
+            make_float4(fa ? xa.x : st.x.x, fa ? xa.y : st.x.y, fb ? xb.x : st.x.z,
+                        fb ? xb.y : st.x.w);
+        *reinterpret_cast<float2*>(d0 + st.e.idx) =
+            make_float2(fa ? 0.0f : st.d.x, fb ? 0.0f : st.d.y);
+      });
+}
+
+// refine_residual: r = b - A x in float pairs (residual_pair_cell) on fluid cells,
+// the next V-cycle's first red half-sweep z = r / (s n) on red ones, and r.r.
+__device__ __noinline__ void refine_residual(const PcgArgs& A, FF& rr) {
+  const MgArgs& M = A.mg;
+  const MgLevel& L0 = M.lv[0];
+  const SV v = sview(L0);
+  const float2* x2 = M.x2;
+  const float2* b2 = M.b2;
+  float* r = L0.b;
+  float* z = L0.x;
+  const float s_hi = A.s, s_lo = A.s_lo;
+  const int lane = threadIdx.x & 31;
+  const int2 q = seg_slice(L0);
+  const Items it = pair_items(q, 2);
+  FF acc;
+  for (unsigned int t = it.first; t < it.end; t += PCG_WARPS) {
+    const int c = (int)(t & 1u);
+    const PCell e = pcell(v, q, t >> 1, c, lane);
+    const unsigned int code2 = *reinterpret_cast<const unsigned int*>(v.code + e.idx);
+    const float4 bb = *reinterpret_cast<const float4*>(b2 + e.idx);
+    const float4 xc = *reinterpret_cast<const float4*>(x2 + e.idx);
+    // the other colour around the pair: slots s, s + 1 of this row, the one beyond
+    // (s - 1 or s + 2), and the pairs in the rows and planes next door
+    const float4 m = *reinterpret_cast<const float4*>(x2 + e.ob);
+    const float2 ex = x2[e.ob - 1 + 3 * e.par];
+    const float4 ym = *reinterpret_cast<const float4*>(x2 + e.ob - v.hx);
+    const float4 yp = *reinterpret_cast<const float4*>(x2 + e.ob + v.hx);
+    const float4 zm = *reinterpret_cast<const float4*>(x2 + e.ob - v.pl);
+    const float4 zp = *reinterpret_cast<const float4*>(x2 + e.ob + v.pl);
+    // a warp whose cells are all fluid with six fluid neighbours: the same cell
+    // function with the mask and the count known
+    const bool full = __all_sync(0xffffffffu, pair_full(code2) && e.okA && e.okB);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const unsigned int code = h == 0 ? (code2 & 0xffffu) : (code2 >> 16);
+      if (!full && (!(h == 0 ? e.okA : e.okB) || !(code & CODE_SELF))) continue;
+      const float2 m0 = make_float2(m.x, m.y), m1 = make_float2(m.z, m.w);
+      float2 xn[6];
+      if (h == 0) {
+        xn[0] = e.par ? m0 : ex;
+        xn[1] = e.par ? m1 : m0;
+        xn[2] = make_float2(ym.x, ym.y);
+        xn[3] = make_float2(yp.x, yp.y);
+        xn[4] = make_float2(zm.x, zm.y);
+        xn[5] = make_float2(zp.x, zp.y);
+      } else {
+        xn[0] = e.par ? m1 : m0;
+        xn[1] = e.par ? ex : m1;
+        xn[2] = make_float2(ym.z, ym.w);
+        xn[3] = make_float2(yp.z, yp.w);
+        xn[4] = make_float2(zm.z, zm.w);
+        xn[5] = make_float2(zp.z, zp.w);
+      }
+      const float2 bc = h == 0 ? make_float2(bb.x, bb.y) : make_float2(bb.z, bb.w);
+      const float2 xcc = h == 0 ? make_float2(xc.x, xc.y) : make_float2(xc.z, xc.w);
+      const float2 rp = full ? residual_pair_cell(bc, xcc, xn, 63u, 6, s_hi, s_lo)
+                             : residual_pair_cell(bc, xcc, xn, code & 63u, code_cnt(code), s_hi,
+                                                  s_lo);
+      const float r32 = __fadd_rn(rp.x, rp.y);
+      r[e.idx + h] = r32;
+      if (c == 0) z[e.idx + h] = gs_first(0, full ? 6 : code_cnt(code), r32);
+      acc.add_prod(r32, r32);
+    }
+  }
+  rr.add_prod(acc.hi, 1.0f);
+  rr.add_prod(acc.lo, 1.0f);
+}
+
 struct SolveState {
   int iters = 0;
   int refinements = 0;
@@ -1727,25 +1841,16 @@ __device__ void solve_mg(const PcgArgs& A, Shared& sh, CtaMg& sm, int4* segc, So
       if (sh.flag == 2) {
         // ---- refinement: x += d, d = 0; r = b - A x in float pairs (+ first red
         // half-sweep)
-        for_fluid0(A, [&](const SCell& e, unsigned int, int) {
-          const float2 t = two_sum(M.x2[e.idx].x, d[e.idx]);
-          M.x2[e.idx] = fast_two_sum(t.x, __fadd_rn(t.y, M.x2[e.idx].y));
-          d[e.idx] = 0.0f;
-        });
+        if (refinements == 0) SOLVE_TRACE(TR_REFINE);
+        refine_update(A);
         if (!gsync(A)) { S.ok = false; return; }
+        if (refinements == 0) SOLVE_TRACE(TR_REFINE + 1);
         FF rr64;
-        const SV v0 = sview(L0);
-        const float s_a = A.s;
-        for_fluid0(A, [&](const SCell& e, unsigned int code, int) {
-          const float2 rp = residual_pair(v0, M.x2, M.b2, e, code, s_a, A.s_lo);
-          const float r32 = __fadd_rn(rp.x, rp.y);
-          r[e.idx] = r32;
-          if (e.idx < L0.half) z[e.idx] = gs_first(0, code_cnt(code), r32);
-          rr64.add_prod(r32, r32);
-        });
+        refine_residual(A, rr64);
         F2 v[1] = {f2_of(rr64)};
         publish<1>(A, 5, v, sh);
         if (!gsync(A)) { S.ok = false; return; }
+        if (refinements == 0) SOLVE_TRACE(TR_REFINE + 2);
         double s[1];
         gather<1>(A, 5, s, sh);
         ++refinements;

@@ -33,6 +33,8 @@ VCYCLE = {32: "level 0: first black half-sweep", 33: "level 0: rest of pre-smoot
           59: "level 0: post-smoothing but the last red"}
 VCYCLE.update({34 + l: f"level {l}: down" for l in range(1, 12)})
 VCYCLE.update({46 + l: f"level {l}: up" for l in range(1, 12)})
+REFINE = [(60, "first refinement: entered"), (61, "first refinement: x += d"),
+          (62, "first refinement: residual b - A x")]
 
 
 def main(argv=None):
@@ -72,6 +74,10 @@ def main(argv=None):
                 if t[slot] >= t0 > 0:  # stamped during this solve
                     print(f"| {name} | {(t[slot] - prev) / 1e3:.1f} | {(t[slot] - t0) / 1e3:.1f} |")
                     prev = t[slot]
+            if all(t[s] >= t0 > 0 for s, _ in REFINE):
+                print("\n| first refinement (mixed precision) | µs |\n|---|---|")
+                for (a, _), (b, name) in zip(REFINE, REFINE[1:]):
+                    print(f"| {name.split(': ')[1]} | {(t[b] - t[a]) / 1e3:.1f} |")
             pieces = sorted((s for s in VCYCLE if t[s] >= t0 > 0), key=lambda s: t[s])
             if pieces:
                 print("\n| last V-cycle: piece | µs |\n|---|---|")
