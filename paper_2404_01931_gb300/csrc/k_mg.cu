@@ -797,6 +797,14 @@ struct CtaMg {
   float s[MG_MAX_LEVELS];
 };
 
+// CTA 0's CTA-local levels sit at the start of the kernel's dynamic shared memory;
+// reached through this (not a pointer argument) the compiler addresses them as
+// shared memory.
+__device__ __forceinline__ CtaMg& cta_mg() {
+  extern __shared__ __align__(16) unsigned char mg_dyn[];
+  return *reinterpret_cast<CtaMg*>(mg_dyn);
+}
+
 __device__ __forceinline__ int bits_for(int n) {  // bits of n - 1 (0 for n = 1)
   return n > 1 ? 32 - __clz(n - 1) : 0;
 }
@@ -817,76 +825,104 @@ __device__ __forceinline__ CtaCell cta_cell(const CtaMg& sm, int l, unsigned int
 
 // Half-sweep of one colour over CTA-local level l (parents on level l + 1).
 template <int MODE>
-__device__ __noinline__ void sweep_cta(const MgArgs& M, CtaMg& sm, int l, int colour) {
+__device__ __noinline__ void sweep_cta(float omega, int l, int colour) {
+  static_assert(MODE != FIRST, "the first half-sweep of a CTA-local level comes with its b");
+  CtaMg& sm = cta_mg();
   const int nx = sm.nx[l], ny = sm.ny[l], nz = sm.nz[l], sy = nx, sz = nx * ny;
   float* x = sm.x + sm.base[l];
   const float* b = sm.b + sm.base[l];
   const uint8_t* code = sm.code + sm.base[l];
   const int e1 = sm.off[l][colour + 1];
-  const float omega = M.omega;
   for (int e = sm.off[l][colour] + (int)threadIdx.x; e < e1; e += PCG_THREADS) {
     const CtaCell p = cta_cell(sm, l, sm.list[e]);
     const int cnt = (p.i > 0) + (p.i < nx - 1) + (p.j > 0) + (p.j < ny - 1) + (p.k > 0) +
                     (p.k < nz - 1);
-    if constexpr (MODE == FIRST) {
-      x[p.c] = gs_first(l, cnt, b[p.c]);
-    } else {
-      const unsigned int cd = code[p.c];
-      const int off[6] = {-1, 1, -sy, sy, -sz, sz};
-      float xv[6];
+    const unsigned int cd = code[p.c];
+    const int off[6] = {-1, 1, -sy, sy, -sz, sz};
+    float xv[6];
 #pragma unroll
-      for (int q = 0; q < 6; ++q) xv[q] = ((cd >> q) & 1u) ? x[p.c + off[q]] : 0.0f;
-      if constexpr (MODE == CORRECT) {
-        const float* px = sm.x + sm.base[l + 1];
-        const int pnx = sm.nx[l + 1], pny = sm.ny[l + 1];
-        const int di[6] = {-1, 1, 0, 0, 0, 0}, dj[6] = {0, 0, -1, 1, 0, 0}, dk[6] = {0, 0, 0, 0, -1, 1};
+    for (int q = 0; q < 6; ++q) xv[q] = ((cd >> q) & 1u) ? x[p.c + off[q]] : 0.0f;
+    if constexpr (MODE == CORRECT) {
+      const float* px = sm.x + sm.base[l + 1];
+      const int pnx = sm.nx[l + 1], pny = sm.ny[l + 1];
+      const int di[6] = {-1, 1, 0, 0, 0, 0}, dj[6] = {0, 0, -1, 1, 0, 0}, dk[6] = {0, 0, 0, 0, -1, 1};
 #pragma unroll
-        for (int q = 0; q < 6; ++q)
-          if ((cd >> q) & 1u) {
-            const int pi = (p.i + di[q]) >> 1, pj = (p.j + dj[q]) >> 1, pk = (p.k + dk[q]) >> 1;
-            xv[q] = __fmaf_rn(omega, px[pi + pnx * (pj + pny * pk)], xv[q]);
-          }
-      }
-      x[p.c] = gs_sum(l, cnt, cd, b[p.c], xv);
+      for (int q = 0; q < 6; ++q)
+        if ((cd >> q) & 1u) {
+          const int pi = (p.i + di[q]) >> 1, pj = (p.j + dj[q]) >> 1, pk = (p.k + dk[q]) >> 1;
+          xv[q] = __fmaf_rn(omega, px[pi + pnx * (pj + pny * pk)], xv[q]);
+        }
     }
+    x[p.c] = gs_sum(l, cnt, cd, b[p.c], xv);
   }
 }
 
 // b_{l+1} = (1/16) sum of the red fluid children's residuals, over level l+1's
-// fluid cells (both colours).
-__device__ __noinline__ void restrict_cta(CtaMg& sm, int l) {
+// fluid cells (both colours), and the first red half-sweep of level l+1 from
+// zero: x = gs_first(b) on its red cells.  Four consecutive lanes take the four
+// red children of one coarse cell, and the group's first lane adds their
+// residuals in child order.
+__device__ __noinline__ void restrict_cta(int l) {
+  CtaMg& sm = cta_mg();
   const int nx = sm.nx[l], ny = sm.ny[l], nz = sm.nz[l], sy = nx, sz = nx * ny;
+  const int cnx = sm.nx[l + 1], cny = sm.ny[l + 1], cnz = sm.nz[l + 1];
   const float* x = sm.x + sm.base[l];
   const float* b = sm.b + sm.base[l];
   const uint8_t* code = sm.code + sm.base[l];
   float* cb = sm.b + sm.base[l + 1];
+  float* cx = sm.x + sm.base[l + 1];
   const float sl = sm.s[l];
-  const int e1 = sm.off[l + 1][2];
-  for (int e = sm.off[l + 1][0] + (int)threadIdx.x; e < e1; e += PCG_THREADS) {
-    const CtaCell P = cta_cell(sm, l + 1, sm.list[e]);
-    float sum = 0.0f;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int dy = q & 1, dz = q >> 1, dx = (dy + dz) & 1;
+  const int e0 = sm.off[l + 1][0], ered = sm.off[l + 1][1];
+  const int n4 = 4 * (sm.off[l + 1][2] - e0);
+  const int lane = threadIdx.x & 31;
+  for (int e4 = (int)threadIdx.x; e4 - lane < n4; e4 += PCG_THREADS) {  // warp-uniform bound
+    const bool live = e4 < n4;
+    float r = 0.0f;
+    bool has = false;
+    CtaCell P = {0, 0, 0, 0};
+    if (live) {
+      P = cta_cell(sm, l + 1, sm.list[e0 + (e4 >> 2)]);
+      const int q = e4 & 3, dy = q & 1, dz = q >> 1, dx = (dy + dz) & 1;
       const int i = 2 * P.i + dx, j = 2 * P.j + dy, k = 2 * P.k + dz;
-      if (i >= nx || j >= ny || k >= nz) continue;
-      const int fc = i + nx * (j + ny * k);
-      const unsigned int cd = code[fc];
-      if (!(cd & CODE_SELF)) continue;
-      const int off[6] = {-1, 1, -sy, sy, -sz, sz};
-      float xv[6];
+      if (i < nx && j < ny && k < nz) {
+        const int fc = i + nx * (j + ny * k);
+        const unsigned int cd = code[fc];
+        if (cd & CODE_SELF) {
+          const int off[6] = {-1, 1, -sy, sy, -sz, sz};
+          float xv[6];
 #pragma unroll
-      for (int u = 0; u < 6; ++u) xv[u] = ((cd >> u) & 1u) ? x[fc + off[u]] : 0.0f;
-      const int cnt = (i > 0) + (i < nx - 1) + (j > 0) + (j < ny - 1) + (k > 0) + (k < nz - 1);
-      sum = __fadd_rn(sum, resid(sl, cnt, cd, b[fc], x[fc], xv));
+          for (int u = 0; u < 6; ++u) xv[u] = ((cd >> u) & 1u) ? x[fc + off[u]] : 0.0f;
+          const int cnt = (i > 0) + (i < nx - 1) + (j > 0) + (j < ny - 1) + (k > 0) + (k < nz - 1);
+          r = resid(sl, cnt, cd, b[fc], x[fc], xv);
+          has = true;
+        }
+      }
     }
-    cb[P.c] = __fmul_rn(sum, 0.0625f);
+    const unsigned int hm = __ballot_sync(0xffffffffu, has) >> (lane & ~3);
+    const float r1 = __shfl_down_sync(0xffffffffu, r, 1);
+    const float r2 = __shfl_down_sync(0xffffffffu, r, 2);
+    const float r3 = __shfl_down_sync(0xffffffffu, r, 3);
+    if (live && (e4 & 3) == 0) {
+      float sum = 0.0f;
+      if (hm & 1u) sum = __fadd_rn(sum, r);
+      if (hm & 2u) sum = __fadd_rn(sum, r1);
+      if (hm & 4u) sum = __fadd_rn(sum, r2);
+      if (hm & 8u) sum = __fadd_rn(sum, r3);
+      const float bc = __fmul_rn(sum, 0.0625f);
+      cb[P.c] = bc;
+      if (e0 + (e4 >> 2) < ered) {
+        const int cnt = (P.i > 0) + (P.i < cnx - 1) + (P.j > 0) + (P.j < cny - 1) + (P.k > 0) +
+                        (P.k < cnz - 1);
+        cx[P.c] = gs_first(l + 1, cnt, bc);
+      }
+    }
   }
 }
 
 // Points the shared level descriptions at the shared arrays, loads the codes and
 // builds the fluid-cell lists (once per solve, after build_levels).  CTA 0 only.
-__device__ __noinline__ void cta_levels_init(const MgArgs& M, CtaMg& sm) {
+__device__ __noinline__ void cta_levels_init(const MgArgs& M) {
+  CtaMg& sm = cta_mg();
   __shared__ unsigned int s_wc[PCG_WARPS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
@@ -961,52 +997,41 @@ __device__ __noinline__ void cta_levels_init(const MgArgs& M, CtaMg& sm) {
   }
 }
 
-// The same cycle pieces as for the grid-wide levels, inside CTA 0.
-__device__ __forceinline__ void down_cta(const MgArgs& M, CtaMg& sm, int l) {
-  sweep_cta<FIRST>(M, sm, l, 0);
-  __syncthreads();
-  sweep_cta<NORMAL>(M, sm, l, 1);
+// The same cycle pieces as for the grid-wide levels, inside CTA 0.  The first
+// red half-sweep of a level (from zero) is done where its b is made: in the
+// copy-in for level lgrid, in the restriction for the levels below.
+__device__ __forceinline__ void down_cta(const MgArgs& M, int l) {
+  sweep_cta<NORMAL>(M.omega, l, 1);
   __syncthreads();
   for (int s = 1; s < M.nu; ++s) {
-    sweep_cta<NORMAL>(M, sm, l, 0);
+    sweep_cta<NORMAL>(M.omega, l, 0);
     __syncthreads();
-    sweep_cta<NORMAL>(M, sm, l, 1);
+    sweep_cta<NORMAL>(M.omega, l, 1);
     __syncthreads();
   }
-  restrict_cta(sm, l);
+  restrict_cta(l);
   __syncthreads();
 }
 
-__device__ __forceinline__ void up_cta(const MgArgs& M, CtaMg& sm, int l) {
-  sweep_cta<CORRECT>(M, sm, l, 1);
+__device__ __forceinline__ void up_cta(const MgArgs& M, int l) {
+  sweep_cta<CORRECT>(M.omega, l, 1);
   __syncthreads();
-  sweep_cta<NORMAL>(M, sm, l, 0);
+  sweep_cta<NORMAL>(M.omega, l, 0);
   __syncthreads();
   for (int s = 1; s < M.nu; ++s) {
-    sweep_cta<NORMAL>(M, sm, l, 1);
+    sweep_cta<NORMAL>(M.omega, l, 1);
     __syncthreads();
-    sweep_cta<NORMAL>(M, sm, l, 0);
+    sweep_cta<NORMAL>(M.omega, l, 0);
     __syncthreads();
   }
 }
 
 // The coarsest level: MG_COARSE_SWEEPS (red, black) pairs from zero, then as many
-// (black, red) pairs.
-__device__ __forceinline__ void coarsest_cta(const MgArgs& M, CtaMg& sm, int l) {
-  sweep_cta<FIRST>(M, sm, l, 0);
-  __syncthreads();
-  sweep_cta<NORMAL>(M, sm, l, 1);
-  __syncthreads();
-  for (int s = 1; s < MG_COARSE_SWEEPS; ++s) {
-    sweep_cta<NORMAL>(M, sm, l, 0);
-    __syncthreads();
-    sweep_cta<NORMAL>(M, sm, l, 1);
-    __syncthreads();
-  }
-  for (int s = 0; s < MG_COARSE_SWEEPS; ++s) {
-    sweep_cta<NORMAL>(M, sm, l, 1);
-    __syncthreads();
-    sweep_cta<NORMAL>(M, sm, l, 0);
+// (black, red) pairs, run as one alternating sequence: the second of the two black
+// half-sweeps in the middle would repeat the first on the same red values.
+__device__ __forceinline__ void coarsest_cta(const MgArgs& M, int l) {
+  for (int h = 1; h < 4 * MG_COARSE_SWEEPS - 1; ++h) {  // black, red, ..., red
+    sweep_cta<NORMAL>(M.omega, l, h & 1);
     __syncthreads();
   }
 }
@@ -1014,17 +1039,45 @@ __device__ __forceinline__ void coarsest_cta(const MgArgs& M, CtaMg& sm, int l) 
 // Levels [lgrid, nlev) inside CTA 0, from the right-hand side that the grid-wide
 // restriction left in level lgrid's global b; leaves level lgrid's x in global
 // memory for the correction of level lgrid - 1.
-__device__ __noinline__ void cta_cycle(const PcgArgs& A, CtaMg& sm) {
+__device__ __noinline__ void cta_cycle(const PcgArgs& A) {
   const MgArgs& M = A.mg;
+  CtaMg& sm = cta_mg();
   const int lg = M.lgrid;
   const int n = M.lv[lg].ncells;
   const float* gb = M.lv[lg].b;
   float* gx = M.lv[lg].x;
-  for (int c = threadIdx.x; c < n; c += PCG_THREADS) sm.b[sm.base[lg] + c] = gb[c];
+  // b of level lgrid (all loads of a thread before its stores), and the first red
+  // half-sweep of level lgrid from zero on the same values
+  constexpr int U = 4;
+  float* sb = sm.b + sm.base[lg];
+  for (int c0 = threadIdx.x; c0 < n; c0 += U * PCG_THREADS) {
+    float v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int c = c0 + u * PCG_THREADS;
+      v[u] = c < n ? gb[c] : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int c = c0 + u * PCG_THREADS;
+      if (c < n) sb[c] = v[u];
+    }
+  }
+  {
+    const int nx = sm.nx[lg], ny = sm.ny[lg], nz = sm.nz[lg];
+    float* sx = sm.x + sm.base[lg];
+    const int e1 = sm.off[lg][1];
+    for (int e = sm.off[lg][0] + (int)threadIdx.x; e < e1; e += PCG_THREADS) {
+      const CtaCell p = cta_cell(sm, lg, sm.list[e]);
+      const int cnt = (p.i > 0) + (p.i < nx - 1) + (p.j > 0) + (p.j < ny - 1) + (p.k > 0) +
+                      (p.k < nz - 1);
+      sx[p.c] = gs_first(lg, cnt, gb[p.c]);
+    }
+  }
   __syncthreads();
-  for (int l = lg; l < M.nlev - 1; ++l) down_cta(M, sm, l);
-  coarsest_cta(M, sm, M.nlev - 1);
-  for (int l = M.nlev - 2; l >= lg; --l) up_cta(M, sm, l);
+  for (int l = lg; l < M.nlev - 1; ++l) down_cta(M, l);
+  coarsest_cta(M, M.nlev - 1);
+  for (int l = M.nlev - 2; l >= lg; --l) up_cta(M, l);
   for (int c = threadIdx.x; c < n; c += PCG_THREADS) gx[c] = sm.x[sm.base[lg] + c];
 }
 
@@ -1033,7 +1086,7 @@ __device__ __noinline__ void cta_cycle(const PcgArgs& A, CtaMg& sm) {
 // The last black and the last red half-sweeps of level 0 accumulate r.z over
 // their cells into rz.  The caller publishes rz and meets the next barrier.
 // Returns false if a barrier failed.
-__device__ bool vcycle_rest(const PcgArgs& A, CtaMg& sm, FF& rz) {
+__device__ bool vcycle_rest(const PcgArgs& A, FF& rz) {
   const MgArgs& M = A.mg;
   const MgLevel& L0 = M.lv[0];
   if (M.nlev == 1) {  // level 0 is the coarsest level
@@ -1077,7 +1130,7 @@ __device__ bool vcycle_rest(const PcgArgs& A, CtaMg& sm, FF& rz) {
     if (!down_split(A, l)) return false;
     SOLVE_TRACE(TR_V_DOWN + min(l, 11));
   }
-  if (team_rank() == 0) cta_cycle(A, sm);
+  if (team_rank() == 0) cta_cycle(A);
   if (!gsync(A)) return false;
   SOLVE_TRACE(TR_V_CTA);
   for (int l = M.lgrid - 1; l >= 1; --l) {
@@ -1692,7 +1745,7 @@ struct SolveState {
 // recomputed residual's norm (refinement).  A slot's readers always pass another barrier before the slot
 // is written again.
 template <bool MIXED>
-__device__ void solve_mg(const PcgArgs& A, Shared& sh, CtaMg& sm, int4* segc, SolveState& S) {
+__device__ void solve_mg(const PcgArgs& A, Shared& sh, int4* segc, SolveState& S) {
   const MgArgs& M = A.mg;
   const MgLevel& L0 = M.lv[0];
   float* d = M.d0;
@@ -1701,7 +1754,7 @@ __device__ void solve_mg(const PcgArgs& A, Shared& sh, CtaMg& sm, int4* segc, So
   if (!build_levels(A, sh)) { S.ok = false; return; }
   seg_cache_fill(M, segc);
   SOLVE_TRACE(TR_SEG_CACHE);
-  if (M.nlev > 1 && team_rank() == 0) cta_levels_init(M, sm);
+  if (M.nlev > 1 && team_rank() == 0) cta_levels_init(M);
   SOLVE_TRACE(TR_CTA_LISTS);
   // ---- start: r = b (cold) or b - A x0 (warm start from the last solve's x),
   // p_old = 0, first red half-sweep of the V-cycle; mixed mode: b as a float pair,
@@ -1777,7 +1830,7 @@ __device__ void solve_mg(const PcgArgs& A, Shared& sh, CtaMg& sm, int4* segc, So
   float* pnew = M.pb0;
   while (!conv) {
     FF rzp;
-    if (!vcycle_rest(A, sm, rzp)) { S.ok = false; return; }
+    if (!vcycle_rest(A, rzp)) { S.ok = false; return; }
     {
       F2 v[1] = {f2_of(rzp)};
       publish<1>(A, 3, v, sh);
@@ -1980,7 +2033,6 @@ __device__ __noinline__ void solve_rbgs(const PcgArgs& A, Shared& sh, int4* segc
 
 template <bool MIXED>
 __device__ void solve_scene_mg(const PcgArgs& A, Shared& sh, unsigned char* dyn) {
-  CtaMg& sm = *reinterpret_cast<CtaMg*>(dyn);
   int4* segc = seg_cache_of(dyn);
   if (threadIdx.x < MG_MAX_LEVELS) s_segc[threadIdx.x] = nullptr;  // no cache until filled
   __syncthreads();
@@ -1989,7 +2041,7 @@ __device__ void solve_scene_mg(const PcgArgs& A, Shared& sh, unsigned char* dyn)
   SolveState S;
   if (!singular) {
     if (!MIXED && A.precond == PRECOND_RBGS) solve_rbgs(A, sh, segc, S);
-    else solve_mg<MIXED>(A, sh, sm, segc, S);
+    else solve_mg<MIXED>(A, sh, segc, S);
   }
   if (team_rank() == 0 && threadIdx.x == 0) {
     int st = 0;
