@@ -90,6 +90,14 @@ struct flip_handle {
   int cur = 0;
   BinView B;
   uint8_t* type = nullptr;
+  // the bricks near the liquid (launch_finalize_near): marks kept across steps,
+  // this step's list; near_stale after a step of the fused batch form, whose
+  // whole-grid kernels leave the marks behind (the next step sweeps the grid)
+  uint8_t* hmark = nullptr;
+  unsigned int* hrow = nullptr;
+  unsigned int* hlist = nullptr;
+  unsigned int* hlist_n = nullptr;
+  bool near_stale = false;
   float2* acc[3] = {nullptr, nullptr, nullptr};
   float* uo[3] = {nullptr, nullptr, nullptr};
   float* b32 = nullptr;
@@ -367,6 +375,10 @@ void carve(flip_handle* h, Carver& cv) {
   h->B.brick_start = cv.take<unsigned int>(nb + 1);
   h->B.active = cv.take<unsigned int>(nb);
   h->type = cv.take<uint8_t>(nc);
+  h->hmark = cv.take<uint8_t>(nb);
+  h->hrow = cv.take<unsigned int>((nb + 31) / 32);  // brick-rows <= bricks
+  h->hlist = cv.take<unsigned int>(nb);
+  h->hlist_n = cv.take<unsigned int>(1);
   for (int d = 0; d < 3; ++d) {
     h->acc[d] = cv.take<float2>((size_t)h->nf[d]);
     h->uo[d] = cv.take<float>((size_t)h->nf[d]);
@@ -746,11 +758,15 @@ int flip_step(flip_handle* h, int32_t nsteps, flip_stats* stats) {
     launch_front(h, s);
     if (timed) FLIP_CUDA(cudaEventRecord(ev[1], s));
     launch_p2g(h->g, h->P[h->cur], h->B, h->acc, h->dstats, h->p2g_blocks, s);
-    launch_finalize(h->g, h->acc, h->uo, s);
-    h->launches += 2;
+    FLIP_CUDA(launch_finalize_near(h->g, h->B.brick_count, h->hmark, h->hrow, h->hlist,
+                                   h->hlist_n, h->acc, h->uo, h->bar, h->dstats, h->sm_count,
+                                   h->near_stale, s));
+    h->launches += 3;
     if (timed) FLIP_CUDA(cudaEventRecord(ev[2], s));
-    launch_divergence(h->g, h->K, h->type, uo, h->b32, h->b64, h->x32, h->x64, h->pff, h->bar,
-                      h->dstats, s);
+    launch_divergence_near(h->g, h->K, h->type, uo, h->b32, h->b64, h->x32, h->x64, h->pff,
+                           h->bar, h->dstats, h->hlist, h->hlist_n, h->sm_count, h->near_stale,
+                           s);
+    h->near_stale = false;
     h->launches += 1;
     if (timed) FLIP_CUDA(cudaEventRecord(ev[3], s));
     const int nsb = h->solver_blocks > 0 ? h->solver_blocks : h->pcg_blocks;
@@ -1218,6 +1234,7 @@ int batch_graph_steps(flip_batch* b, flip_handle* const* hs, int n, int pairs,
     key.push_back((unsigned long long)hs[s]->cur);
     key.push_back((unsigned long long)hs[s]->p2g_blocks);  // the captured launch shapes
     key.push_back((unsigned long long)hs[s]->g2p_blocks);
+    key.push_back(hs[s]->near_stale ? 1ull : 0ull);  // whether the first step sweeps the grid
   }
   for (int v : first_all) key.push_back((unsigned long long)v);
   // the batch stream starts after every scene stream's earlier work
@@ -1784,6 +1801,7 @@ int batch_step_impl(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t ns
     for (auto* h : order) {
       ++h->steps_done;
       h->stepped = true;
+      h->near_stale = true;  // the whole-grid batch kernels ran, not the marks
     }
     FLIP_CUDA(cudaGetLastError());
     if (timed) ++timed_steps;
@@ -1797,10 +1815,14 @@ int batch_step_impl(flip_batch* b, flip_handle* const* hs, int32_t n, int32_t ns
       const float* uo[3] = {h->uo[0], h->uo[1], h->uo[2]};
       launch_front(h, h->stream);
       launch_p2g(h->g, h->P[h->cur], h->B, h->acc, h->dstats, h->p2g_blocks, h->stream);
-      launch_finalize(h->g, h->acc, h->uo, h->stream);
-      launch_divergence(h->g, h->K, h->type, uo, h->b32, h->b64, h->x32, h->x64, h->pff, h->bar,
-                        h->dstats, h->stream);
-      h->launches += 3;
+      FLIP_CUDA(launch_finalize_near(h->g, h->B.brick_count, h->hmark, h->hrow, h->hlist,
+                                     h->hlist_n, h->acc, h->uo, h->bar, h->dstats, h->sm_count,
+                                     h->near_stale, h->stream));
+      launch_divergence_near(h->g, h->K, h->type, uo, h->b32, h->b64, h->x32, h->x64, h->pff,
+                             h->bar, h->dstats, h->hlist, h->hlist_n, h->sm_count,
+                             h->near_stale, h->stream);
+      h->near_stale = false;
+      h->launches += 4;
       FLIP_CUDA(cudaEventRecord(b->ev[s], h->stream));
       FLIP_CUDA(cudaStreamWaitEvent(bs, b->ev[s], 0));
     }

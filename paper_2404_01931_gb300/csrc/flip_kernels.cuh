@@ -274,6 +274,22 @@ void launch_divergence(const Grid& g, const StepConsts& k, const uint8_t* type,
                        const float* const uo[3], float* b32, double* b64, float* x32,
                        double* x64, float2* pff, unsigned int* bar, DevStats* st,
                        cudaStream_t s);
+// finalize and divergence over the bricks within one brick of an active brick,
+// this step's or last step's (full: the whole-grid kernels, after which the marks
+// are current again), walked as whole x-rows of the brick-rows holding such a
+// brick.  launch_finalize_near marks the bricks (hmark: [nbricks], kept across
+// steps), lists the brick-rows (rowflag: [ceil(by bz / 32)] words; list: [by bz];
+// list_n: one word), resets the step words and finalizes: two kernels;
+// launch_divergence_near: one.
+cudaError_t launch_finalize_near(const Grid& g, const unsigned int* brick_count, uint8_t* hmark,
+                                 unsigned int* rowflag, unsigned int* list, unsigned int* list_n,
+                                 float2* const acc[3], float* const uo[3], unsigned int* bar,
+                                 DevStats* st, int sm_count, bool full, cudaStream_t s);
+void launch_divergence_near(const Grid& g, const StepConsts& k, const uint8_t* type,
+                            const float* const uo[3], float* b32, double* b64, float* x32,
+                            double* x64, float2* pff, unsigned int* bar, DevStats* st,
+                            const unsigned int* list, const unsigned int* list_n, int sm_count,
+                            bool full, cudaStream_t s);
 void launch_u_new(const Grid& g, const StepConsts& k, int d, const float* uo, const float* p32,
                   const float2* pff, float* out, cudaStream_t s);
 void launch_div_norms(const Grid& g, const StepConsts& k, const uint8_t* type,

@@ -187,7 +187,14 @@ __global__ void k_active_prefix(const SceneDev* scenes, int n, unsigned int* out
 }
 
 // u_old = num / den (0 where no particle reached the node); clears the
-// accumulators for the next step.
+// accumulator for the next step.
+__device__ __forceinline__ void finalize_face(float2* acc, float* uo, long long idx) {
+  const float2 v = acc[idx];
+  uo[idx] = (v.y != 0.0f) ? __fdiv_rn(v.x, v.y) : 0.0f;
+  if (v.x != 0.0f || v.y != 0.0f) acc[idx] = make_float2(0.0f, 0.0f);  // empty faces stay clear
+}
+
+// Every face of the grid.
 __device__ __forceinline__ void finalize(const Grid& g, float2* acc0, float2* acc1, float2* acc2,
                                          float* uo0, float* uo1, float* uo2, unsigned int blk,
                                          unsigned int nblk) {
@@ -201,9 +208,7 @@ __device__ __forceinline__ void finalize(const Grid& g, float2* acc0, float2* ac
     if (f < n0) { acc = acc0; uo = uo0; idx = f; }
     else if (f < n0 + n1) { acc = acc1; uo = uo1; idx = f - n0; }
     else { acc = acc2; uo = uo2; idx = f - n0 - n1; }
-    const float2 v = acc[idx];
-    uo[idx] = (v.y != 0.0f) ? __fdiv_rn(v.x, v.y) : 0.0f;
-    if (v.x != 0.0f || v.y != 0.0f) acc[idx] = make_float2(0.0f, 0.0f);  // empty faces stay clear
+    finalize_face(acc, uo, idx);
   }
 }
 
@@ -219,10 +224,53 @@ __global__ void k_finalize_batch(const BatchLaunch L) {
            L.first[s + 1] - L.first[s]);
 }
 
-// Gravity + walls give u* on the fly; b = -div u* (Eq. 6) in fluid cells.
-// Also starts the solve from p = 0 (every cell, so air cells hold p = 0) and
-// resets the grid barrier and the per-step max-speed word.
-// Block (j, k) of a scene walks the x-row of cells (i, j, k): no index divisions.
+// Gravity + walls give u* on the fly; b = -div u* (Eq. 6) in fluid cells (0
+// elsewhere), and the solve's start p = 0 (every cell, so air cells hold p = 0).
+__device__ __forceinline__ void divergence_cell(const Grid& g, const StepConsts& K,
+                                                const uint8_t* __restrict__ type,
+                                                const float* __restrict__ uo0,
+                                                const float* __restrict__ uo1,
+                                                const float* __restrict__ uo2, float* b32,
+                                                double* b64, float* x32, double* x64,
+                                                float2* pff, int i, int j, int k) {
+  const int c = i + g.nx * (j + g.ny * k);
+  if (x32) x32[c] = 0.0f;
+  if (x64) x64[c] = 0.0;
+  if (pff) pff[c] = make_float2(0.0f, 0.0f);
+  const bool fluid = (type[c] == 1);
+  const int fu = i + (g.nx + 1) * (j + g.ny * k);
+  const int fv = i + g.nx * (j + (g.ny + 1) * k);
+  const int fw = c;
+  const float uL = (i == 0) ? 0.0f : __fadd_rn(uo0[fu], K.gdt[0]);
+  const float uR = (i + 1 == g.nx) ? 0.0f : __fadd_rn(uo0[fu + 1], K.gdt[0]);
+  const float vB = (j == 0) ? 0.0f : __fadd_rn(uo1[fv], K.gdt[1]);
+  const float vT = (j + 1 == g.ny) ? 0.0f : __fadd_rn(uo1[fv + g.nx], K.gdt[1]);
+  const float wK = (k == 0) ? 0.0f : __fadd_rn(uo2[fw], K.gdt[2]);
+  const float wF = (k + 1 == g.nz) ? 0.0f : __fadd_rn(uo2[fw + g.nx * g.ny], K.gdt[2]);
+  if (b32) {
+    const float d = __fadd_rn(__fadd_rn(__fsub_rn(uR, uL), __fsub_rn(vT, vB)), __fsub_rn(wF, wK));
+    b32[c] = fluid ? -__fmul_rn(d, g.inv_dx) : 0.0f;
+  }
+  if (b64) {
+    // the FP64 pipe is narrow: warps without a fluid cell skip the FP64 work
+    double v = 0.0;
+    if (__ballot_sync(__activemask(), fluid)) {
+      const double d = ((double)uR - (double)uL) + ((double)vT - (double)vB) + ((double)wF - (double)wK);
+      v = fluid ? -d * (double)g.inv_dx : 0.0;
+    }
+    b64[c] = v;
+  }
+}
+
+// The grid barrier's arrival counter and spare words, and the per-step max-speed
+// word, reset before the solve (a block may have 32 threads).
+__device__ __forceinline__ void reset_step_words(unsigned int* bar, DevStats* st) {
+  for (unsigned int t = threadIdx.x; t < BAR_WORDS; t += blockDim.x) bar[t] = 0u;
+  if (threadIdx.x == 0) st->max_speed_bits = 0u;
+}
+
+// Every cell: block (j, k) of a scene walks the x-row of cells (i, j, k), no
+// index divisions; the first block also resets the step words.
 __device__ __forceinline__ void divergence(const Grid& g, const StepConsts& K0,
                                            const uint8_t* __restrict__ type,
                                            const float* __restrict__ uo0,
@@ -231,40 +279,9 @@ __device__ __forceinline__ void divergence(const Grid& g, const StepConsts& K0,
                                            float* x32, double* x64, float2* pff,
                                            unsigned int* bar, DevStats* st, int j, int k) {
   const StepConsts K = step_consts(K0);
-  if (j == 0 && k == 0) {
-    // the grid barrier's arrival counter and spare words (a block may have 32 threads)
-    for (unsigned int t = threadIdx.x; t < BAR_WORDS; t += blockDim.x) bar[t] = 0u;
-    if (threadIdx.x == 0) st->max_speed_bits = 0u;
-  }
-  for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
-    const int c = i + g.nx * (j + g.ny * k);
-    if (x32) x32[c] = 0.0f;
-    if (x64) x64[c] = 0.0;
-    if (pff) pff[c] = make_float2(0.0f, 0.0f);
-    const bool fluid = (type[c] == 1);
-    const int fu = i + (g.nx + 1) * (j + g.ny * k);
-    const int fv = i + g.nx * (j + (g.ny + 1) * k);
-    const int fw = c;
-    const float uL = (i == 0) ? 0.0f : __fadd_rn(uo0[fu], K.gdt[0]);
-    const float uR = (i + 1 == g.nx) ? 0.0f : __fadd_rn(uo0[fu + 1], K.gdt[0]);
-    const float vB = (j == 0) ? 0.0f : __fadd_rn(uo1[fv], K.gdt[1]);
-    const float vT = (j + 1 == g.ny) ? 0.0f : __fadd_rn(uo1[fv + g.nx], K.gdt[1]);
-    const float wK = (k == 0) ? 0.0f : __fadd_rn(uo2[fw], K.gdt[2]);
-    const float wF = (k + 1 == g.nz) ? 0.0f : __fadd_rn(uo2[fw + g.nx * g.ny], K.gdt[2]);
-    if (b32) {
-      const float d = __fadd_rn(__fadd_rn(__fsub_rn(uR, uL), __fsub_rn(vT, vB)), __fsub_rn(wF, wK));
-      b32[c] = fluid ? -__fmul_rn(d, g.inv_dx) : 0.0f;
-    }
-    if (b64) {
-      // the FP64 pipe is narrow: warps without a fluid cell skip the FP64 work
-      double v = 0.0;
-      if (__ballot_sync(__activemask(), fluid)) {
-        const double d = ((double)uR - (double)uL) + ((double)vT - (double)vB) + ((double)wF - (double)wK);
-        v = fluid ? -d * (double)g.inv_dx : 0.0;
-      }
-      b64[c] = v;
-    }
-  }
+  if (j == 0 && k == 0) reset_step_words(bar, st);
+  for (int i = threadIdx.x; i < g.nx; i += blockDim.x)
+    divergence_cell(g, K, type, uo0, uo1, uo2, b32, b64, x32, x64, pff, i, j, k);
 }
 
 __global__ void k_divergence(const Grid g, const StepConsts K0, const uint8_t* __restrict__ type,
@@ -282,6 +299,109 @@ __global__ void k_divergence_batch(const BatchLaunch L) {
   const int r = (int)(blockIdx.x - L.first[s]);
   divergence(S.g, S.K, S.type, S.uo[0], S.uo[1], S.uo[2], S.b32, S.b64, S.x32, S.x64, S.pff, S.bar,
              S.st, r % S.g.ny, r / S.g.ny);
+}
+
+// ---------------------------------------------------------------- bricks near the liquid
+//
+// After P2G only the faces of the active bricks' tiles (the brick and a one-node
+// halo) can hold a sum, and only fluid cells (in active bricks) get a nonzero b or
+// p.  So finalize and divergence need only visit the bricks within one brick of
+// an active brick (this step's set S), plus last step's set, whose faces and cells
+// they return to zero: outside S of the last step every face and cell is zero
+// already (the arena starts zeroed, and each step re-zeroes what leaves S).  A
+// face belongs to the cell at its node index (the last node along an axis to the
+// last cell), and the passes walk whole x-rows of cells: every row of a brick-row
+// (bricks (*, J, K)) that holds a brick to visit, so that their loads and stores
+// stream along x as in the full sweep.  Each face and cell visited gets the full
+// sweep's arithmetic: the fields come out the same.
+//
+// hmark[b]: bit 1 = b in S this step, bit 0 = b in S last step.
+
+// S, and the list of brick-rows to visit (rowflag: zero on entry, one bit per
+// brick-row; list_n: zero on entry); block 0 also resets the step words (the full
+// divergence's job).
+__global__ void k_halo_bricks(const Grid g, const unsigned int* __restrict__ brick_count,
+                              uint8_t* hmark, unsigned int* rowflag, unsigned int* list,
+                              unsigned int* list_n, unsigned int* bar, DevStats* st) {
+  if (blockIdx.x == 0) reset_step_words(bar, st);
+  const int nb = g.bx * g.by * g.bz;
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+    const int I = b % g.bx, J = (b / g.bx) % g.by, K = b / (g.bx * g.by);
+    bool near = false;
+    for (int dk = -1; dk <= 1 && !near; ++dk)
+      for (int dj = -1; dj <= 1 && !near; ++dj)
+        for (int di = -1; di <= 1 && !near; ++di) {
+          const int i = I + di, j = J + dj, k = K + dk;
+          if (i < 0 || j < 0 || k < 0 || i >= g.bx || j >= g.by || k >= g.bz) continue;
+          near = brick_count[i + g.bx * (j + g.by * k)] > 0u;
+        }
+    const unsigned int m = ((near ? 1u : 0u) << 1) | ((unsigned)hmark[b] >> 1);
+    hmark[b] = (uint8_t)m;
+    if (m != 0u) {
+      const unsigned int row = (unsigned)(J + g.by * K);
+      const unsigned int bit = 1u << (row & 31u);
+      // the first to flag a brick-row lists it
+      if (!(atomicOr(rowflag + (row >> 5), bit) & bit)) list[atomicAdd(list_n, 1u)] = row;
+    }
+  }
+}
+
+// Cell row u of the listed brick-rows (64 per brick-row): (j, k), or false past
+// the grid.
+__device__ __forceinline__ bool listed_row(const Grid& g, const unsigned int* list,
+                                           unsigned int u, int& j, int& k) {
+  const unsigned int row = list[u >> 6];
+  const int J = (int)(row % (unsigned)g.by), K = (int)(row / (unsigned)g.by);
+  j = J * BRICK + (int)(u & 7u);
+  k = K * BRICK + (int)((u >> 3) & 7u);
+  return j < g.ny && k < g.nz;
+}
+
+// The faces of cell row (j, k): u at nodes (0 .. nx, j, k); v at (0 .. nx-1, j, k)
+// and, on the last row, (.., ny, k); w at (.., j, k) and, on the last plane,
+// (.., j, nz).
+__device__ __forceinline__ void finalize_row(const Grid& g, int j, int k, float2* acc0,
+                                             float2* acc1, float2* acc2, float* uo0, float* uo1,
+                                             float* uo2) {
+  const long long ru = (long long)(g.nx + 1) * (j + (long long)g.ny * k);
+  for (int i = threadIdx.x; i <= g.nx; i += blockDim.x) finalize_face(acc0, uo0, ru + i);
+  const int nv = (j + 1 == g.ny) ? 2 : 1, nw = (k + 1 == g.nz) ? 2 : 1;
+  for (int q = 0; q < nv; ++q) {
+    const long long rv = (long long)g.nx * ((j + q) + (long long)(g.ny + 1) * k);
+    for (int i = threadIdx.x; i < g.nx; i += blockDim.x) finalize_face(acc1, uo1, rv + i);
+  }
+  for (int q = 0; q < nw; ++q) {
+    const long long rw = (long long)g.nx * (j + (long long)g.ny * (k + q));
+    for (int i = threadIdx.x; i < g.nx; i += blockDim.x) finalize_face(acc2, uo2, rw + i);
+  }
+}
+
+__global__ void k_finalize_rows(const Grid g, float2* acc0, float2* acc1, float2* acc2,
+                                float* uo0, float* uo1, float* uo2,
+                                const unsigned int* __restrict__ list,
+                                const unsigned int* __restrict__ list_n) {
+  const unsigned int n = *list_n * 64u;
+  for (unsigned int u = blockIdx.x; u < n; u += gridDim.x) {
+    int j, k;
+    if (listed_row(g, list, u, j, k)) finalize_row(g, j, k, acc0, acc1, acc2, uo0, uo1, uo2);
+  }
+}
+
+__global__ void k_divergence_rows(const Grid g, const StepConsts K0,
+                                  const uint8_t* __restrict__ type,
+                                  const float* __restrict__ uo0, const float* __restrict__ uo1,
+                                  const float* __restrict__ uo2, float* b32, double* b64,
+                                  float* x32, double* x64, float2* pff,
+                                  const unsigned int* __restrict__ list,
+                                  const unsigned int* __restrict__ list_n) {
+  const StepConsts K = step_consts(K0);
+  const unsigned int n = *list_n * 64u;
+  for (unsigned int u = blockIdx.x; u < n; u += gridDim.x) {
+    int j, k;
+    if (!listed_row(g, list, u, j, k)) continue;
+    for (int i = threadIdx.x; i < g.nx; i += blockDim.x)
+      divergence_cell(g, K, type, uo0, uo1, uo2, b32, b64, x32, x64, pff, i, j, k);
+  }
 }
 
 template <int D, bool PAIR>
@@ -378,6 +498,40 @@ void launch_divergence(const Grid& g, const StepConsts& k, const uint8_t* type,
   const int threads = std::min(256, (g.nx + 31) / 32 * 32);
   k_divergence<<<dim3((unsigned)g.ny, (unsigned)g.nz), threads, 0, s>>>(
       g, k, type, uo[0], uo[1], uo[2], b32, b64, x32, x64, pff, bar, st);
+}
+
+cudaError_t launch_finalize_near(const Grid& g, const unsigned int* brick_count, uint8_t* hmark,
+                                 unsigned int* rowflag, unsigned int* list, unsigned int* list_n,
+                                 float2* const acc[3], float* const uo[3], unsigned int* bar,
+                                 DevStats* st, int sm_count, bool full, cudaStream_t s) {
+  const long long nb = (long long)g.bx * g.by * g.bz;
+  const size_t rows = (size_t)g.by * g.bz;
+  cudaError_t e = cudaMemsetAsync(rowflag, 0, sizeof(unsigned int) * ((rows + 31) / 32), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(list_n, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  k_halo_bricks<<<(unsigned)std::min<long long>((nb + 255) / 256, 4LL * sm_count), 256, 0, s>>>(
+      g, brick_count, hmark, rowflag, list, list_n, bar, st);
+  if (full) {
+    launch_finalize(g, acc, uo, s);
+  } else {
+    k_finalize_rows<<<(unsigned)(16 * sm_count), 256, 0, s>>>(g, acc[0], acc[1], acc[2], uo[0],
+                                                            uo[1], uo[2], list, list_n);
+  }
+  return cudaSuccess;
+}
+
+void launch_divergence_near(const Grid& g, const StepConsts& k, const uint8_t* type,
+                            const float* const uo[3], float* b32, double* b64, float* x32,
+                            double* x64, float2* pff, unsigned int* bar, DevStats* st,
+                            const unsigned int* list, const unsigned int* list_n, int sm_count,
+                            bool full, cudaStream_t s) {
+  if (full) {
+    launch_divergence(g, k, type, uo, b32, b64, x32, x64, pff, bar, st, s);
+    return;
+  }
+  const int threads = std::min(256, (g.nx + 31) / 32 * 32);
+  k_divergence_rows<<<(unsigned)(16 * sm_count), threads, 0, s>>>(
+      g, k, type, uo[0], uo[1], uo[2], b32, b64, x32, x64, pff, list, list_n);
 }
 
 void launch_active_prefix(const SceneDev* scenes, int n, unsigned int* out, cudaStream_t s) {

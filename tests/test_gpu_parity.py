@@ -228,6 +228,84 @@ def test_ballistic_blob_gpu():
     np.testing.assert_allclose(np.stack([x, y, z], 1), want, atol=1e-6)
 
 
+def _fields_of(sim):
+    return {"u_old": [sim.read(f) for f in (F.U_OLD, F.V_OLD, F.W_OLD)],
+            "u_new": [sim.read(f) for f in (F.U_NEW, F.V_NEW, F.W_NEW)],
+            "p": sim.read(F.PRESSURE_F64), "rhs": sim.read(F.RHS),
+            "type": sim.read(F.CELL_TYPE)}
+
+
+def _near_liquid(types, n):
+    """Per cell of an n^3 grid of 8^3 bricks: its brick is within one brick (27
+    neighbours) of a brick holding a fluid cell.  Indexed [k, j, i]."""
+    nb = n // 8
+    occ = types.reshape(nb, 8, nb, 8, nb, 8).any(axis=(1, 3, 5))
+    pad = np.pad(occ, 1)
+    near = np.zeros_like(occ)
+    for dk in range(3):
+        for dj in range(3):
+            for di in range(3):
+                near |= pad[dk:dk + nb, dj:dj + nb, di:di + nb]
+    return np.repeat(np.repeat(np.repeat(near, 8, 0), 8, 1), 8, 2)
+
+
+@pytest.mark.parametrize("via_fused_batch", [False, True])
+def test_fields_stay_exact_where_the_liquid_has_left(via_fused_batch):
+    """The finalize and divergence passes visit only the bricks within one brick of
+    the liquid, this step's or last step's.  A blob thrown across the grid leaves
+    bricks empty behind it; in the step after that (alone, or after steps in the
+    fused batch form, whose whole-grid kernels leave the brick marks behind) every
+    face and cell away from the liquid holds exactly 0 -- no value of an earlier
+    step survives -- and the rest equals the oracle's step from the same particles.
+    (FP32 rounding of the blob's fast bulk motion, |u| ~ 8, is not small against its
+    divergence, so b and p are compared against floors on the scale of |u| / dx.)"""
+    n = 40
+    r = S.random_velocities(S.box(n, (0.1, 0.3, 0.3), (0.3, 0.5, 0.5), seed=4), 0.5, 5)
+    sc = S.Scene(r.n, r.dx, r.x, r.y, r.z, r.u + np.float32(8.0), r.v + np.float32(1.0), r.w,
+                 r.fluid_mask, r.name)
+    op, fp = matched(n)
+    with F.Simulation(fp, *sc.arrays()) as sim:
+        if via_fused_batch:
+            with F.Batch(1) as b:
+                b.set_fused(True)
+                assert b.step([sim], 12)[0] == F.FLIP_OK
+        else:
+            assert sim.step(12)[0] == F.FLIP_OK
+        x, y, z, u, v, w = sim.particles()
+        # bricks of 0.2 along x: the blob started in bricks 0-1 and is now past 0.4,
+        # so brick 0 is more than one brick from the liquid
+        assert x.min() > 0.4
+        ref = O.step(op, x, y, z, u, v, w)
+        rc, st = sim.step(1, stats=True)
+        assert rc == F.FLIP_OK
+        got = _fields_of(sim)
+        got["particles"] = sim.particles()
+    assert np.array_equal(got["type"].reshape(ref.type.shape), ref.type)
+    near = _near_liquid(got["type"].reshape(n, n, n) == 1, n)
+    assert not near[:, :, :8].any()  # the test's premise: brick 0 along x is away
+    far = ~near
+    # exact zeros away from the liquid: faces by the cell at their node index
+    assert not got["rhs"].reshape(n, n, n)[far].any()
+    assert not got["p"].reshape(n, n, n)[far].any()
+    for d in range(3):
+        shape = [n, n, n]
+        shape[2 - d] += 1
+        f = got["u_old"][d].reshape(shape)
+        idx = [slice(None)] * 3
+        idx[2 - d] = slice(0, n)
+        assert not f[tuple(idx)][far].any(), d
+    # the values near the liquid
+    for dd in range(3):
+        assert rel_l2(got["u_old"][dd], ref.u_old[dd], face_floor(n)) <= 1e-5, dd
+    nfl = max(int(ref.type.sum()), 1)
+    umax = max(float(np.abs(a).max()) for a in ref.u_old)
+    b_floor = umax * n * np.sqrt(nfl)
+    assert rel_l2(got["rhs"], ref.rhs, b_floor) <= 1e-5
+    p_floor = b_floor / (n * n) * op.rho / op.dt
+    assert rel_l2(got["p"], ref.pressure, p_floor) <= 1e-5
+    _compare_particles(ref, got, 1 / n)
+
+
 # ------------------------------------------------------------- edge cases
 
 def test_empty_scene():
