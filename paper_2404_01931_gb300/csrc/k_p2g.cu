@@ -10,7 +10,8 @@
 // they can reach, then adds them to a shared-memory tile of the brick plus its
 // halo (9x10x10 nodes per component), and the CTA adds the tile to the global
 // (num, den) accumulators with vector float2 atomics.  The normalisation
-// num/den happens in k_finalize, which also clears the accumulators.
+// num/den happens in k_finalize_rows (over the rows near the liquid; k_finalize
+// sweeps the whole grid), which also clears the accumulators.
 // A warp takes 8 x-cells by 4 z-planes of one y-row, and the tile's planes are
 // TILE_PLANE = 104 nodes apart (8 mod 32 banks): the 32 lanes of every atomic
 // then fall on 32 different banks.
