@@ -225,6 +225,12 @@ __global__ void k_finalize_batch(const BatchLaunch L) {
            L.first[s + 1] - L.first[s]);
 }
 
+// The rounding error of s = fl(a + b) (Knuth's TwoSum): a + b = s + err exactly.
+__device__ __forceinline__ float two_sum_err(float a, float b, float s) {
+  const float bv = __fsub_rn(s, a);
+  return __fadd_rn(__fsub_rn(a, __fsub_rn(s, bv)), __fsub_rn(b, bv));
+}
+
 // Gravity + walls give u* on the fly; b = -div u* (Eq. 6) in fluid cells (0
 // elsewhere), and the solve's start p = 0 (every cell, so air cells hold p = 0).
 __device__ __forceinline__ void divergence_cell(const Grid& g, const StepConsts& K,
@@ -253,10 +259,22 @@ __device__ __forceinline__ void divergence_cell(const Grid& g, const StepConsts&
     b32[c] = fluid ? -__fmul_rn(d, g.inv_dx) : 0.0f;
   }
   if (b64) {
-    // the FP64 pipe is narrow: warps without a fluid cell skip the FP64 work
+    // the FP64 pipe is narrow: warps without a fluid cell skip the FP64 work, and a
+    // difference of two floats whose FP32 result is exact (Knuth's TwoSum error is
+    // 0) is the FP64 difference too, so one conversion stands for two conversions
+    // and a subtraction (the same bits)
     double v = 0.0;
-    if (__ballot_sync(__activemask(), fluid)) {
-      const double d = ((double)uR - (double)uL) + ((double)vT - (double)vB) + ((double)wF - (double)wK);
+    const unsigned int am = __activemask();
+    if (__ballot_sync(am, fluid)) {
+      const float su = __fsub_rn(uR, uL), sv = __fsub_rn(vT, vB), sw = __fsub_rn(wF, wK);
+      const bool exact = two_sum_err(uR, -uL, su) == 0.0f && two_sum_err(vT, -vB, sv) == 0.0f &&
+                         two_sum_err(wF, -wK, sw) == 0.0f;
+      double d;
+      if (__all_sync(am, exact)) {
+        d = ((double)su + (double)sv) + (double)sw;
+      } else {
+        d = ((double)uR - (double)uL) + ((double)vT - (double)vB) + ((double)wF - (double)wK);
+      }
       v = fluid ? -d * (double)g.inv_dx : 0.0;
     }
     b64[c] = v;
