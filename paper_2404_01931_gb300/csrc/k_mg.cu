@@ -137,11 +137,11 @@ __device__ __forceinline__ SV sview(const MgLevel& L) {
 // The same for the level whose x a correction reads (colour-split or natural).
 struct PV {
   const float* x;
-  int split, nx, ny, hx, half, margin;
+  int split, nx, ny, nz, hx, half, margin;
 };
 
 __device__ __forceinline__ PV pview(const MgLevel& C) {
-  return PV{C.x, C.split, C.nx, C.ny, C.hx, C.half, C.margin};
+  return PV{C.x, C.split, C.nx, C.ny, C.nz, C.hx, C.half, C.margin};
 }
 
 // Runs items first, first + stride, ... < end in batches of U: pre(e, ok)
@@ -418,6 +418,42 @@ __device__ __forceinline__ void parent_values(const PV& C, int nx, int ny, int n
   for (int q = 0; q < 6; ++q) pv[q] = C.x[level_index(C, pi[q] >> 1, pj[q] >> 1, pk[q] >> 1)];
 }
 
+// The coarse values that the corrections of a slot pair's two cells (A at x = iA,
+// B at iA + 2) read.  The twelve neighbours' parents are seven coarse cells: three
+// in the pair's coarse row (x = s - 1 + par .. s + 1 + par, which hold A's and B's
+// own parents, s and s + 1), and for A and B the parent in the other y row and in
+// the other z plane (a neighbour's parent is the cell's own but for one neighbour
+// per axis).  pr = {row x3, y-row A, y-row B, z-plane A, z-plane B}; coordinates of
+// off-grid neighbours (never read unmasked) are clamped into the level.
+template <class E>
+__device__ __forceinline__ void pair_parents(const PV& C, const E& e, float (&pr)[7]) {
+  const int J = e.j >> 1, K = e.k >> 1;
+  const int Jy = min(max((e.j & 1) ? J + 1 : J - 1, 0), C.ny - 1);
+  const int Kz = min(max((e.k & 1) ? K + 1 : K - 1, 0), C.nz - 1);
+  const int a = min(e.s, C.nx - 1), b = min(e.s + 1, C.nx - 1);
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+    pr[q] = C.x[level_index(C, min(max(e.s - 1 + e.par + q, 0), C.nx - 1), J, K)];
+  pr[3] = C.x[level_index(C, a, Jy, K)];
+  pr[4] = C.x[level_index(C, b, Jy, K)];
+  pr[5] = C.x[level_index(C, a, J, Kz)];
+  pr[6] = C.x[level_index(C, b, J, Kz)];
+}
+
+// The six neighbour parents (parent_values' order) of cell h (0: A, 1: B) of the
+// pair, from pair_parents' seven values.
+__device__ __forceinline__ void pair_parents_of(const float (&pr)[7], int par, int j, int k,
+                                                int h, float (&pv)[6]) {
+  const float own = (h == 0) ? (par ? pr[0] : pr[1]) : (par ? pr[1] : pr[2]);
+  const float oy = (h == 0) ? pr[3] : pr[4], oz = (h == 0) ? pr[5] : pr[6];
+  pv[0] = (h == 0) ? pr[0] : pr[1];
+  pv[1] = (h == 0) ? pr[1] : pr[2];
+  pv[2] = (j & 1) ? own : oy;
+  pv[3] = (j & 1) ? oy : own;
+  pv[4] = (k & 1) ? own : oz;
+  pv[5] = (k & 1) ? oz : own;
+}
+
 template <int MODE>
 __device__ __forceinline__ bool gs_apply(float* x, int l, float omega, GsIn& s, float& v) {
   if (!s.ok || !(s.code & CODE_SELF)) return false;
@@ -444,7 +480,6 @@ __device__ __noinline__ void sweep_split_v(const MgArgs& M, const MgLevel& L, co
   const int lane = threadIdx.x & 31;
   const SV v = sview(L);
   const PV cv = pview(C);
-  const int nz = L.nz;
   const float omega = M.omega;
   const float inv6 = s_inv_cnt[6], invs6 = s_inv_scnt[l][6];
   const int2 q = seg_slice(L);
@@ -454,7 +489,7 @@ __device__ __noinline__ void sweep_split_v(const MgArgs& M, const MgLevel& L, co
     unsigned int code2;
     float2 b;
     Nbr2 n;
-    float pvA[6], pvB[6];
+    float pr[MODE == CORRECT ? 7 : 1];
   };
   FF acc;
   run_batched<U>(
@@ -467,10 +502,7 @@ __device__ __noinline__ void sweep_split_v(const MgArgs& M, const MgLevel& L, co
         st.code2 = *reinterpret_cast<const unsigned int*>(v.code + st.e.idx);
         st.b = *reinterpret_cast<const float2*>(v.b + st.e.idx);
         st.n = load_nbr2(v, v.x, st.e);
-        if constexpr (MODE == CORRECT) {
-          parent_values(cv, v.nx, v.ny, nz, min(st.e.iA, v.nx - 1), st.e.j, st.e.k, st.pvA);
-          parent_values(cv, v.nx, v.ny, nz, min(st.e.iA + 2, v.nx - 1), st.e.j, st.e.k, st.pvB);
-        }
+        if constexpr (MODE == CORRECT) pair_parents(cv, st.e, st.pr);
         return st;
       },
       [&](S&) {},
@@ -487,9 +519,10 @@ __device__ __noinline__ void sweep_split_v(const MgArgs& M, const MgLevel& L, co
               float xv[6];
               nbr_of(st.n, h, xv);
               if constexpr (MODE == CORRECT) {
+                float pv[6];
+                pair_parents_of(st.pr, st.e.par, st.e.j, st.e.k, h, pv);
 #pragma unroll
-                for (int u = 0; u < 6; ++u)
-                  xv[u] = __fmaf_rn(omega, h == 0 ? st.pvA[u] : st.pvB[u], xv[u]);
+                for (int u = 0; u < 6; ++u) xv[u] = __fmaf_rn(omega, pv[u], xv[u]);
               }
               float sum = 0.0f;
 #pragma unroll
@@ -510,10 +543,11 @@ __device__ __noinline__ void sweep_split_v(const MgArgs& M, const MgLevel& L, co
           float xv[6];
           nbr_of(st.n, h, xv);
           if constexpr (MODE == CORRECT) {
+            float pv[6];
+            pair_parents_of(st.pr, st.e.par, st.e.j, st.e.k, h, pv);
 #pragma unroll
             for (int u = 0; u < 6; ++u)
-              if ((code >> u) & 1u)
-                xv[u] = __fmaf_rn(omega, h == 0 ? st.pvA[u] : st.pvB[u], xv[u]);
+              if ((code >> u) & 1u) xv[u] = __fmaf_rn(omega, pv[u], xv[u]);
           }
           const float val = gs_sum(l, code_cnt(code), code, bc, xv);
           out[h] = ok ? val : 0.0f;
